@@ -1,0 +1,295 @@
+"""Pins of the oracle's DG operators against closed forms and invariants (no GPU).
+
+Each test ties an operator of Sec. 3.2 of the paper to a fact that the
+mathematics fixes, chosen so that a dropped term, a wrong sign, a wrong index
+or a transposed block fails at least one of them:
+  mass          integrals of polynomials, exact inverse
+  Laplace       symmetry, PSD with the constants as null space, consistency
+                with -Laplacian on polynomials, closed-form energies of a
+                piecewise-constant and a sawtooth field (penalty and both
+                symmetric face terms), spectral convergence on sin(x)
+  div / grad    D^T = -G, annihilation of constants, consistency on polynomials
+  convective    conservation, constants, a two-cell LLF closed form,
+                consistency on polynomials, Taylor-Green closed form
+  diagnostics   kinetic energy 1/8 and dissipation 3 nu / 4 of Taylor-Green
+"""
+import numpy as np
+import pytest
+
+from oracle import dg, rules
+
+PI = np.pi
+
+
+def rand(shape, seed):
+    return np.random.default_rng(seed).uniform(-1, 1, shape)
+
+
+def interior_cells(mesh):
+    """Cells whose closure does not touch the periodic seam."""
+    ok = np.ones(mesh.E, dtype=bool)
+    for a in range(3):
+        ok &= (mesh.ijk[a] > 0) & (mesh.ijk[a] < mesh.n[a] - 1)
+    return np.nonzero(ok)[0]
+
+
+def cell_moments(space, f, extra=4):
+    """int_e phi_i f dx for every cell, by an independent tensor Gauss rule
+    with N + extra points (f a callable of x, y, z)."""
+    m = space.mesh
+    g, w = rules.gauss(space.N + extra)
+    V, _ = rules.lagrange(space.nodes, g)
+    Phi = dg.tensor3(V, V, V)
+    W = np.kron(w, np.kron(w, w)) * np.prod(m.h)
+    Q = len(g)
+    q = np.arange(Q ** 3)
+    loc = [g[q % Q], g[(q // Q) % Q], g[q // (Q * Q)]]
+    X = [m.lo[a] + (m.ijk[a][:, None] + loc[a][None, :]) * m.h[a] for a in range(3)]
+    F = f(*X)
+    return (F * W[None, :]) @ Phi
+
+
+# --------------------------------------------------------------------- mass
+@pytest.mark.parametrize("k", [1, 2, 3, 5])
+def test_mass_integrals(k):
+    m = dg.Mesh((3, 2, 4))
+    s = dg.Space(m, k)
+    M = dg.Mass(s)
+    one = np.ones((m.E, s.ndofs_cell))
+    assert abs(np.sum(one * M.apply(one)) - (2 * PI) ** 3) < 1e-11
+    if k >= 2:
+        x2 = s.interpolate(lambda x, y, z: x * x)
+        assert abs(np.sum(one * M.apply(x2)) - (2 * PI) ** 2 * 2 * PI ** 3 / 3) < 1e-10
+        xy = s.interpolate(lambda x, y, z: x * y)
+        assert abs(np.sum(xy * M.apply(xy)) - 2 * PI * (2 * PI ** 3 / 3) ** 2) < 1e-9
+    x = rand((m.E, s.ndofs_cell), k)
+    assert np.max(np.abs(M.apply_inverse(M.apply(x)) - x)) < 1e-12
+
+
+# ------------------------------------------------------------------ Laplace
+@pytest.mark.parametrize("n,k", [((2, 2, 2), 2), ((1, 2, 3), 3), ((4, 4, 4), 3), ((2, 2, 2), 5)])
+def test_laplace_symmetric_psd_nullspace(n, k):
+    m = dg.Mesh(n)
+    s = dg.Space(m, k)
+    A = dg.Laplace(s).matrix()
+    nrm = np.max(np.abs(A))
+    assert np.max(np.abs(A - A.T)) <= 1e-13 * nrm
+    ev = np.linalg.eigvalsh(0.5 * (A + A.T))
+    assert abs(ev[0]) < 1e-11 * ev[-1]
+    assert ev[1] > 1e-6 * ev[-1]
+    assert np.max(np.abs(A @ np.ones(A.shape[0]))) < 1e-12 * nrm
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_laplace_consistency_polynomial(k):
+    m = dg.Mesh((4, 3, 4))
+    s = dg.Space(m, k)
+    L = dg.Laplace(s)
+    c = rand(6, 10 + k)
+    p = lambda x, y, z: (c[0] * x ** k + c[1] * x * y ** (k - 1) + c[2] * y * z
+                         + c[3] * z ** k * x ** (k - 2) + c[4] * (x + y + z))
+    # -Laplacian of p, written out
+    def mlap(x, y, z):
+        r = -(c[0] * k * (k - 1) * x ** (k - 2) + c[1] * x * (k - 1) * (k - 2) * y ** max(k - 3, 0)
+              + c[3] * (k * (k - 1) * z ** (k - 2) * x ** (k - 2)
+                        + z ** k * (k - 2) * (k - 3) * x ** max(k - 4, 0)))
+        return r
+    y = L.apply(s.interpolate(p))
+    ref = cell_moments(s, mlap)
+    cells = interior_cells(m)
+    assert len(cells) > 0
+    err = np.max(np.abs(y[cells] - ref[cells]))
+    assert err < 1e-11 * max(1.0, np.max(np.abs(ref[cells])))
+
+
+@pytest.mark.parametrize("k,pf", [(1, 1.0), (3, 1.0), (4, 2.5)])
+def test_laplace_penalty_energy(k, pf):
+    """Piecewise constant field: only tau [p]^2 survives."""
+    m = dg.Mesh((3, 2, 4), lo=(-1.0, 0.0, -2.0), hi=(2.0, 1.0, 2.0))
+    s = dg.Space(m, k)
+    L = dg.Laplace(s, penalty_factor=pf)
+    cval = rand(m.E, 3)
+    P = np.repeat(cval[:, None], s.ndofs_cell, axis=1)
+    energy = np.sum(P * L.apply(P))
+    ref = 0.0
+    for a in range(3):
+        tau = pf * (k + 1) ** 2 / m.h[a]
+        area = np.prod([m.h[b] for b in range(3) if b != a])
+        ref += tau * area * np.sum((cval - cval[m.neighbor(a, +1)]) ** 2)
+    assert abs(energy - ref) < 1e-11 * abs(ref)
+
+
+@pytest.mark.parametrize("k,axis", [(1, 0), (2, 1), (3, 2), (5, 0)])
+def test_laplace_sawtooth_energy(k, axis):
+    """p = distance from the cell's lower face along `axis`:
+    energy = V - 2 sum_F h |F| + tau h^2 sum_F |F| over faces normal to axis."""
+    m = dg.Mesh((2, 3, 2), lo=(0.0, 0.0, 0.0), hi=(1.0, 1.5, 3.0))
+    s = dg.Space(m, k)
+    L = dg.Laplace(s)
+    X = s.node_coords()[axis]
+    P = X - (m.lo[axis] + m.ijk[axis][:, None] * m.h[axis])
+    energy = np.sum(P * L.apply(P))
+    h = m.h[axis]
+    area = np.prod([m.h[b] for b in range(3) if b != axis])
+    tau = (k + 1) ** 2 / h
+    ref = m.volume + m.E * area * (-2.0 * h + tau * h * h)
+    assert abs(energy - ref) < 1e-11 * abs(ref)
+
+
+def test_laplace_spectral_convergence():
+    """sin(x)cos(z) is an eigenfunction of -Laplacian with eigenvalue 2: the
+    discrete Rayleigh quotient converges to it at a high rate, and pointwise
+    M^-1 L u converges to 2u (at the lifted-jump rate h^(k-1))."""
+    rq, errs = [], []
+    for n in (2, 4):
+        m = dg.Mesh(n)
+        s = dg.Space(m, 3)
+        u = s.interpolate(lambda x, y, z: np.sin(x) * np.cos(z))
+        Lu = dg.Laplace(s).apply(u)
+        rq.append(abs(np.sum(u * Lu) / np.sum(u * dg.Mass(s).apply(u)) - 2.0))
+    assert rq[1] < rq[0] / 30.0 and rq[1] < 1e-3
+    for n in (8, 16):
+        m = dg.Mesh((n, 1, n))
+        s = dg.Space(m, 3)
+        u = s.interpolate(lambda x, y, z: np.sin(x) * np.cos(z))
+        v = dg.Mass(s).apply_inverse(dg.Laplace(s).apply(u))
+        errs.append(np.max(np.abs(v - 2.0 * u)))
+    assert errs[1] < errs[0] / 3.0 and errs[1] < 0.02
+
+
+def test_viscous_is_nu_laplace():
+    m = dg.Mesh(2)
+    s = dg.Space(m, 2)
+    x = rand((m.E, s.ndofs_cell), 0)
+    nu = 1.0 / 1600
+    assert np.max(np.abs(dg.Viscous(s, nu).apply(x) - nu * dg.Laplace(s).apply(x))) < 1e-16
+
+
+@pytest.mark.parametrize("n", [(1, 1, 1), (2, 1, 3)])
+def test_laplace_diagonal(n):
+    m = dg.Mesh(n)
+    s = dg.Space(m, 2)
+    L = dg.Laplace(s)
+    assert np.max(np.abs(L.diagonal().ravel() - np.diag(L.matrix()))) < 1e-12
+
+
+# --------------------------------------------------------------- div / grad
+@pytest.mark.parametrize("n,ku", [((2, 2, 2), 2), ((1, 2, 3), 3), ((3, 3, 2), 4)])
+def test_divergence_gradient_adjoint(n, ku):
+    m = dg.Mesh(n)
+    su, sp = dg.Space(m, ku), dg.Space(m, ku - 1)
+    D, G = dg.Divergence(su, sp), dg.Gradient(su, sp)
+    nu_, np_ = su.size, sp.size
+    Dm = np.stack([D.apply(e.reshape(3, m.E, -1)).ravel() for e in np.eye(3 * nu_)], 1)
+    Gm = np.stack([G.apply(e.reshape(m.E, -1)).ravel() for e in np.eye(np_)], 1)
+    assert np.max(np.abs(Dm.T + Gm)) < 1e-13 * np.max(np.abs(Dm))
+    assert np.max(np.abs(Dm @ np.ones(3 * nu_))) < 1e-12 * np.max(np.abs(Dm))
+    assert np.max(np.abs(Gm @ np.ones(np_))) < 1e-12 * np.max(np.abs(Gm))
+
+
+@pytest.mark.parametrize("ku", [2, 3, 4])
+def test_divergence_gradient_consistency(ku):
+    m = dg.Mesh((4, 3, 3))
+    su, sp = dg.Space(m, ku), dg.Space(m, ku - 1)
+    c = rand(4, ku)
+    ux = lambda x, y, z: c[0] * x ** ku + y * z
+    uy = lambda x, y, z: c[1] * x * y ** (ku - 1) + z
+    uz = lambda x, y, z: c[2] * z ** ku * y
+    divu = lambda x, y, z: (c[0] * ku * x ** (ku - 1) + c[1] * (ku - 1) * x * y ** (ku - 2)
+                            + c[2] * ku * z ** (ku - 1) * y)
+    U = np.stack([su.interpolate(f) for f in (ux, uy, uz)])
+    cells = interior_cells(m)
+    y = dg.Divergence(su, sp).apply(U)
+    ref = cell_moments(sp, divu)
+    assert np.max(np.abs(y[cells] - ref[cells])) < 1e-11 * np.max(np.abs(ref[cells]))
+    kp = ku - 1
+    p = lambda x, y, z: c[3] * x ** kp * y + z ** kp + x * y * z
+    grads = [lambda x, y, z: c[3] * kp * x ** (kp - 1) * y + y * z,
+             lambda x, y, z: c[3] * x ** kp + x * z,
+             lambda x, y, z: kp * z ** (kp - 1) + x * y]
+    g = dg.Gradient(su, sp).apply(sp.interpolate(p))
+    for a in range(3):
+        ref = cell_moments(su, grads[a])
+        assert np.max(np.abs(g[a][cells] - ref[cells])) < 1e-11 * np.max(np.abs(ref[cells]))
+
+
+# --------------------------------------------------------------- convective
+@pytest.mark.parametrize("n,k", [((2, 2, 2), 2), ((3, 1, 2), 3), ((2, 2, 2), 5)])
+def test_convective_conservation_and_constants(n, k):
+    m = dg.Mesh(n)
+    s = dg.Space(m, k)
+    C = dg.Convective(s)
+    U = rand((3, m.E, s.ndofs_cell), 7)
+    Y = C.apply(U)
+    scale = np.max(np.abs(Y))
+    assert np.max(np.abs(Y.sum(axis=(1, 2)))) < 1e-12 * scale * Y[0].size
+    const = np.stack([np.full((m.E, s.ndofs_cell), v) for v in (0.3, -1.2, 2.0)])
+    assert np.max(np.abs(C.apply(const))) < 1e-12
+
+
+def test_convective_two_cell_llf():
+    """u = (a,0,0) on cell 0 and (b,0,0) on cell 1 of a 2x1x1 mesh: summing the
+    x-component over the nodes of cell 0 leaves only the LLF jump terms,
+    area * 2 max(|a|,|b|) (a - b)."""
+    m = dg.Mesh((2, 1, 1), lo=(0, 0, 0), hi=(2.0, 1.0, 1.0))
+    s = dg.Space(m, 2)
+    a, b = 0.7, -1.3
+    U = np.zeros((3, m.E, s.ndofs_cell))
+    U[0][0], U[0][1] = a, b
+    Y = dg.Convective(s).apply(U)
+    area = m.h[1] * m.h[2]
+    assert abs(Y[0][0].sum() - area * 2 * max(abs(a), abs(b)) * (a - b)) < 1e-13
+    assert abs(Y[0][1].sum() + area * 2 * max(abs(a), abs(b)) * (a - b)) < 1e-13
+    assert np.max(np.abs(Y[1:])) < 1e-14
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_convective_consistency_polynomial(k):
+    m = dg.Mesh((3, 3, 4))
+    s = dg.Space(m, k)
+    c = rand(3, 20 + k)
+    f = [lambda x, y, z: c[0] * x ** k + y, lambda x, y, z: c[1] * y * x + z ** k,
+         lambda x, y, z: c[2] * z * y ** (k - 1) + x]
+    U = np.stack([s.interpolate(g) for g in f])
+    Y = dg.Convective(s).apply(U)
+    # div(u (x) u)_c = sum_d d_d (u_c u_d), by central differences of exact
+    # polynomials is too crude; use the product rule with exact derivatives
+    der = {
+        (0, 0): lambda x, y, z: c[0] * k * x ** (k - 1), (0, 1): lambda x, y, z: 1.0 + 0 * x,
+        (0, 2): lambda x, y, z: 0 * x, (1, 0): lambda x, y, z: c[1] * y,
+        (1, 1): lambda x, y, z: c[1] * x, (1, 2): lambda x, y, z: k * z ** (k - 1),
+        (2, 0): lambda x, y, z: 1.0 + 0 * x,
+        (2, 1): lambda x, y, z: c[2] * z * (k - 1) * y ** (k - 2), (2, 2): lambda x, y, z: c[2] * y ** (k - 1)}
+    cells = interior_cells(m)
+    for comp in range(3):
+        def rhs(x, y, z, comp=comp):
+            u = [g(x, y, z) for g in f]
+            divu = sum(der[(d, d)](x, y, z) for d in range(3))
+            adv = sum(u[d] * der[(comp, d)](x, y, z) for d in range(3))
+            return adv + u[comp] * divu
+        ref = cell_moments(s, rhs, extra=k + 2)
+        assert np.max(np.abs(Y[comp][cells] - ref[cells])) < 1e-11 * np.max(np.abs(ref[cells]))
+
+
+def test_convective_taylor_green_closed_form():
+    errs = []
+    for n in (4, 8):
+        m = dg.Mesh(n)
+        s = dg.Space(m, 3)
+        U = np.stack(s.interpolate(dg.taylor_green))
+        V = dg.Mass(s).apply_inverse(dg.Convective(s).apply(U))
+        X = s.node_coords()
+        ref = np.stack([0.5 * np.sin(2 * X[0]) * np.cos(X[2]) ** 2,
+                        0.5 * np.sin(2 * X[1]) * np.cos(X[2]) ** 2, 0 * X[0]])
+        errs.append(np.max(np.abs(V - ref)))
+    assert errs[1] < errs[0] / 6.0 and errs[1] < 0.02
+
+
+# -------------------------------------------------------------- diagnostics
+def test_taylor_green_energy_and_dissipation():
+    nu = 1.0 / 1600
+    m = dg.Mesh(8)
+    s = dg.Space(m, 4)
+    U = np.stack(s.interpolate(dg.taylor_green))
+    assert abs(dg.kinetic_energy(s, U) - 0.125) < 1e-4
+    assert abs(dg.dissipation_rate(s, U, nu) / nu - 0.75) < 1e-3
