@@ -1,0 +1,176 @@
+/*
+ * dgns.h - C ABI of libdgns: matrix-free discontinuous Galerkin operators of
+ * the incompressible Navier-Stokes dual-splitting solver of Fehn, Wall &
+ * Kronbichler (arXiv:1802.01439), on one NVIDIA GB300 (sm_103a).
+ *
+ * Discretisation (paper Sec. 3.2): uniform periodic Cartesian mesh of hexahedra,
+ * tensor-product Lagrange basis on Legendre-Gauss-Lobatto (LGL) nodes, degree
+ * k_u for velocity (space U) and k_p for pressure (space P), Gauss quadrature
+ * exact on affine cells, floor(3(k_u+1)/2) points for the convective term.
+ *
+ * Vector layout (all operators): contiguous, [comp][elem][z][y][x] with x
+ * fastest and element id e = i + nx*(j + ny*l).  A scalar field in space S has
+ * n_elem * (k_S+1)^3 entries; a velocity field has three such blocks.
+ *
+ * Pointers: every vector argument is either a device pointer (cudaMalloc,
+ * torch CUDA tensor) or a host pointer (pinned or pageable).  With device
+ * pointers the call is enqueued on the context's stream and returns at once.
+ * With host pointers the library stages the data through its own device
+ * buffers (allocated at the first such call), runs the same kernels, copies
+ * the results back and synchronises the stream before returning.
+ * The caller owns every vector; the library owns its tables, multigrid levels
+ * and scratch.  dst must not alias any source (DGNS_ERR_ALIAS).
+ *
+ * Errors: every entry point returns 0 on success or a DGNS_ERR_* code; no C++
+ * exception crosses the ABI; dgns_last_error() gives a message for the calling
+ * thread.  A context must be used by one host thread at a time.
+ */
+#ifndef DGNS_H
+#define DGNS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DGNS_OK 0
+#define DGNS_ERR_INVALID_ARG 1   /* bad size, degree, space, null pointer   */
+#define DGNS_ERR_CUDA 2          /* a CUDA runtime call failed             */
+#define DGNS_ERR_OOM 3           /* device allocation failed               */
+#define DGNS_ERR_NOT_CONVERGED 4 /* solver hit max_iter; info is filled    */
+#define DGNS_ERR_NONFINITE 5     /* NaN/Inf residual in a solver           */
+#define DGNS_ERR_ALIAS 6         /* dst overlaps a source                  */
+#define DGNS_ERR_UNSUPPORTED 7   /* valid request this build does not do   */
+
+#define DGNS_SPACE_U 0 /* velocity space, degree k_u ("degree")        */
+#define DGNS_SPACE_P 1 /* pressure space, degree k_p ("degree_p")      */
+
+#define DGNS_MAX_DEGREE 11
+#define DGNS_MAX_LEVELS 16
+
+typedef struct dgns_ctx dgns_ctx;
+
+typedef struct {
+  int n_elem[3];         /* elements per direction, >= 1                         */
+  double lo[3], hi[3];   /* box; the paper's Taylor-Green box is [-pi, pi]^3      */
+  int degree;            /* k_u in 1..11                                          */
+  int degree_p;          /* k_p in 1..11; -1 selects k_u - 1 (Sec. 3.2)           */
+  int n_q_conv;          /* convective Gauss points per direction; 0 = 3(k+1)/2  */
+  double penalty_factor; /* SIPG tau = penalty_factor (k+1)^2 / h; 0 selects 1    */
+  double nu;             /* kinematic viscosity of the viscous operator           */
+  int mg_coarse_n;       /* coarsest multigrid mesh (elements per direction)      */
+  int mg_precision;      /* 32 or 64: arithmetic of the V-cycle; 0 = no multigrid */
+} dgns_mesh_desc;
+
+/* Defaults: 4^3 elements on [-pi,pi]^3, k_u = 3, k_p = k_u - 1, 3/2 rule,
+ * penalty factor 1, nu = 1/1600, coarse mesh 2, FP32 multigrid. */
+void dgns_default_desc(dgns_mesh_desc* desc);
+
+/* Create a context: computes the 1D tables on the host (long double), builds
+ * the multigrid hierarchy of the pressure space when mg_precision != 0
+ * (levels n, n/2, ... >= mg_coarse_n while every n is even), estimates the
+ * Chebyshev eigenvalue bound of every level, and allocates all device memory
+ * the operators and solvers need.  stream: a cudaStream_t or NULL (default
+ * stream).  On failure *out is NULL and nothing is leaked. */
+int dgns_create(const dgns_mesh_desc* desc, void* stream, dgns_ctx** out);
+int dgns_destroy(dgns_ctx* ctx);
+int dgns_set_stream(dgns_ctx* ctx, void* stream);
+const char* dgns_status_string(int status);
+const char* dgns_last_error(void);
+
+/* Scalar DoFs per component of space U and space P:
+ * n_elem_total * (k+1)^3 (paper Sec. 4, DoF count formula). */
+int dgns_sizes(const dgns_ctx* ctx, long long* n_u, long long* n_p);
+/* The k+1 LGL nodes on [0,1] of a space, as used by the library (host out). */
+int dgns_nodes_1d(const dgns_ctx* ctx, int space, double* out);
+
+/* SIPG Laplace l_h (Sec. 3.2, negative Laplacian of the pressure Poisson
+ * equation, matrix L of Sec. 3.3) on one scalar field of `space`:
+ * dst = L src.  FP64. */
+int dgns_vmult_laplace(dgns_ctx* ctx, double* dst, const double* src, int space);
+/* Same operator in FP32 on multigrid level `level` (0 = coarsest, levels-1 =
+ * the pressure space itself).  Device pointers only. */
+int dgns_vmult_laplace_f32(dgns_ctx* ctx, float* dst, const float* src, int level);
+/* Diagonal of L (the Jacobi weights of the Chebyshev smoother, Sec. 3.3). */
+int dgns_laplace_diagonal(dgns_ctx* ctx, double* dst, int space);
+
+/* Viscous SIPG v_h (Sec. 3.2, Laplace formulation F_v = nu grad u): dst3 =
+ * nu L src3 per velocity component (space U, tau with k_u). */
+int dgns_vmult_viscous(dgns_ctx* ctx, double* dst3, const double* src3);
+/* Helmholtz operator of the viscous substep (Sec. 3.3):
+ * dst3 = (mass_factor M + V) src3 in one pass per component. */
+int dgns_vmult_helmholtz(dgns_ctx* ctx, double* dst3, const double* src3, double mass_factor);
+
+/* Mass matrix m_h (Sec. 3.2) and its exact block-diagonal inverse (Sec. 3.3)
+ * on ncomp consecutive scalar fields of `space`. */
+int dgns_vmult_mass(dgns_ctx* ctx, double* dst, const double* src, int ncomp, int space);
+int dgns_apply_inverse_mass(dgns_ctx* ctx, double* dst, const double* src, int ncomp, int space);
+
+/* Velocity divergence d_h (Sec. 3.2, central flux, k_u+1 Gauss points):
+ * dst_p (space P) = D u3 (space U, 3 components). */
+int dgns_vmult_divergence(dgns_ctx* ctx, double* dst_p, const double* u3);
+/* Pressure gradient g_h (Sec. 3.2, central flux): dst3 (space U) = G p. */
+int dgns_vmult_gradient(dgns_ctx* ctx, double* dst3, const double* p);
+
+/* Convective term c_h (Sec. 3.2) with F_c = u (x) u and the local
+ * Lax-Friedrichs flux, over-integrated with n_q_conv points: dst3 = C(u3),
+ * the weak form (not multiplied by M^-1, not negated). */
+int dgns_vmult_convective(dgns_ctx* ctx, double* dst3, const double* u3);
+/* Vector-Jacobian product of the convective term: grad_u3 = (dC/du)^T w3 at
+ * u3.  At LLF kinks it uses d|s|/ds = sign(s) (sign(0) = 0) and sends the
+ * derivative of max(a, b) to the larger argument (half to each on a tie). */
+int dgns_vjp_convective(dgns_ctx* ctx, double* grad_u3, const double* u3, const double* w3);
+
+typedef struct {
+  double rel_tol;          /* stop when ||r||_2 <= rel_tol ||b||_2 (default 1e-10) */
+  double abs_tol;          /* or ||r||_2 <= abs_tol (default 0)                      */
+  int max_iter;            /* default 200                                           */
+  int cheb_degree;         /* Chebyshev degree, pre and post (default 5)            */
+  double smoothing_range;  /* lambda_max / lambda_min of the smoother (default 20)  */
+  int cheb_coarse_iters;   /* Chebyshev steps of the coarse solve (default 20)       */
+  int project_mean;        /* 1: remove the Euclidean mean of r0 and of every z      */
+} dgns_solve_params;
+
+typedef struct {
+  int iterations;
+  double rel_res;          /* final ||r||_2 / ||b||_2 (recursively updated)         */
+  double initial_res;      /* ||b||_2                                                */
+  int status;
+  double lambda_max_fine;  /* Chebyshev upper bound of the finest level             */
+  double seconds;          /* wall time of the solve                                */
+} dgns_solve_info;
+
+void dgns_default_solve_params(dgns_solve_params* p);
+
+/* Pressure Poisson solve (Sec. 3.3): FP64 conjugate gradients preconditioned
+ * by one h-multigrid V-cycle per iteration with Jacobi-Chebyshev smoothing
+ * (degree cheb_degree pre and post, range smoothing_range), Chebyshev coarse
+ * solve, embedding prolongation and its transpose as restriction; the V-cycle
+ * runs in the context's mg_precision.  Zero initial guess; x (space P) gets
+ * the solution.  Returns DGNS_ERR_NOT_CONVERGED with info filled when
+ * max_iter is reached. */
+int dgns_cg_mg_solve(dgns_ctx* ctx, double* x, const double* b,
+                     const dgns_solve_params* params, dgns_solve_info* info);
+
+/* Multigrid hierarchy: number of levels, elements per direction and the
+ * Chebyshev upper eigenvalue bound (already including the safety factor) of
+ * each level, coarsest first (host outputs, arrays of DGNS_MAX_LEVELS). */
+int dgns_mg_info(const dgns_ctx* ctx, int* n_levels, int* n_elem_per_level, double* lambda_max);
+/* One V-cycle, z = V(r), on the finest level in the context's precision,
+ * FP64 in and out (device pointers). */
+int dgns_mg_vcycle(dgns_ctx* ctx, double* z, const double* r, const dgns_solve_params* params);
+/* Grid transfers between level `level` and `level`+1 (FP32, device):
+ * prolongation = embedding of the coarse polynomials, restriction = its
+ * transpose. */
+int dgns_mg_prolongate_f32(dgns_ctx* ctx, float* fine, const float* coarse, int level);
+int dgns_mg_restrict_f32(dgns_ctx* ctx, float* coarse, const float* fine, int level);
+
+/* Helmholtz solve (viscous substep, Sec. 3.3): CG preconditioned by the
+ * inverse mass matrix on (mass_factor M + V) x3 = b3, FP64, zero initial
+ * guess. */
+int dgns_cg_invmass_solve(dgns_ctx* ctx, double* x3, const double* b3, double mass_factor,
+                          const dgns_solve_params* params, dgns_solve_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DGNS_H */

@@ -1,0 +1,99 @@
+// Device helpers shared by the operator kernels of libdgns.
+//
+// Every operator on the periodic Cartesian mesh is a sum of Kronecker products
+// of small 1D matrices (the geometry is affine and axis-aligned, so the Gauss
+// quadrature of Sec. 3.2 factorises exactly).  A kernel therefore consists of
+// "sweeps": for every line of an element along direction d, multiply the line
+// by a small matrix whose entries live in the kernel's parameter space.  The
+// loops are fully unrolled on the compile-time node count, so the matrix
+// entries are uniform constant-bank operands of the FMA instructions.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dgns {
+
+struct MeshDims {
+  int nx, ny, nz;
+  long long E;  // cells per component
+};
+
+// Start offset and stride of line `l` (0 <= l < NI*NJ) along direction d in
+// a cell array with extents (n0, n1, n2) in x, y, z (x fastest).
+template <int D>
+__device__ __forceinline__ void line_geom(int l, int n0, int n1, int n2, int& base, int& stride) {
+  if (D == 0) {          // x-lines, l = y + n1 * z
+    base = l * n0;
+    stride = 1;
+  } else if (D == 1) {   // y-lines, l = x + n0 * z
+    const int x = l % n0, z = l / n0;
+    base = x + n0 * n1 * z;
+    stride = n0;
+  } else {               // z-lines, l = x + n0 * y
+    base = l;
+    stride = n0 * n1;
+  }
+}
+
+// Periodic neighbour of local cell `el` along direction D, +1 or -1.
+template <int D>
+__device__ __forceinline__ long long neighbor(long long el, int ex, int ey, int ez, int sgn,
+                                              const MeshDims& m) {
+  if (D == 0) {
+    int v = ex + sgn;
+    v = v < 0 ? m.nx - 1 : (v >= m.nx ? 0 : v);
+    return el + (v - ex);
+  } else if (D == 1) {
+    int v = ey + sgn;
+    v = v < 0 ? m.ny - 1 : (v >= m.ny ? 0 : v);
+    return el + (long long)(v - ey) * m.nx;
+  } else {
+    int v = ez + sgn;
+    v = v < 0 ? m.nz - 1 : (v >= m.nz ? 0 : v);
+    return el + (long long)(v - ez) * m.nx * m.ny;
+  }
+}
+
+// y[i] = sum_j A[i*NI + j] x[j]   (A row-major NO x NI)
+template <class T, int NO, int NI>
+__device__ __forceinline__ void matvec(const T* A, const T (&x)[NI], T (&y)[NO]) {
+#pragma unroll
+  for (int i = 0; i < NO; ++i) {
+    T acc = A[i * NI] * x[0];
+#pragma unroll
+    for (int j = 1; j < NI; ++j) acc = fma(A[i * NI + j], x[j], acc);
+    y[i] = acc;
+  }
+}
+
+// y[i] = z[i] + sum_j A[i*NI + j] x[j]
+template <class T, int NO, int NI>
+__device__ __forceinline__ void matvec_add(const T* A, const T (&x)[NI], const T (&z)[NO], T (&y)[NO]) {
+#pragma unroll
+  for (int i = 0; i < NO; ++i) {
+    T acc = z[i];
+#pragma unroll
+    for (int j = 0; j < NI; ++j) acc = fma(A[i * NI + j], x[j], acc);
+    y[i] = acc;
+  }
+}
+
+template <class T, int N>
+__device__ __forceinline__ void load_line(const T* buf, int base, int stride, T (&x)[N]) {
+#pragma unroll
+  for (int j = 0; j < N; ++j) x[j] = buf[base + j * stride];
+}
+
+template <class T, int N>
+__device__ __forceinline__ void store_line(T* buf, int base, int stride, const T (&x)[N]) {
+#pragma unroll
+  for (int j = 0; j < N; ++j) buf[base + j * stride] = x[j];
+}
+
+// Dynamic shared memory, aligned for double2 accesses.
+__device__ __forceinline__ unsigned char* dyn_smem() {
+  extern __shared__ __align__(16) unsigned char dgns_smem[];
+  return dgns_smem;
+}
+
+}  // namespace dgns

@@ -1,0 +1,208 @@
+// Vector kernels of the solvers: deterministic reductions (fixed grid, fixed
+// order, so repeated solves are bit-reproducible), the fused conjugate-gradient
+// updates (Sec. 3.3 of arXiv:1802.01439: "vector updates and inner products"
+// are a significant part of the CG cost, so each pass does as much as it can),
+// precision conversions at the boundary of the mixed-precision V-cycle, and
+// the first Chebyshev step from a zero initial guess.
+#include "blas.h"
+
+namespace dgns {
+namespace {
+
+constexpr int RT = 256;  // threads per reduction block
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum of v, result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red[RT / 32];
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = lane < RT / 32 ? red[lane] : 0.0;
+    s = warp_sum(s);
+  }
+  __syncthreads();
+  return s;
+}
+
+template <class TA, class TB>
+__global__ void __launch_bounds__(RT) dot_partial(const TA* __restrict__ a, const TB* __restrict__ b,
+                                                  long long n, double* __restrict__ part) {
+  double s = 0.0;
+  const long long stride = (long long)gridDim.x * RT;
+  for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < n; i += stride)
+    s = fma((double)a[i], (double)b[i], s);
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+template <class T>
+__global__ void __launch_bounds__(RT) sum_partial(const T* __restrict__ a, long long n,
+                                                  double* __restrict__ part) {
+  double s = 0.0;
+  const long long stride = (long long)gridDim.x * RT;
+  for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < n; i += stride) s += (double)a[i];
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// out[slot] = sum of the partials (single block, fixed order).
+__global__ void __launch_bounds__(RT) finish_sum(const double* __restrict__ part, int np,
+                                                 double* __restrict__ scal, int slot) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < np; i += RT) s += part[i];
+  s = block_sum(s);
+  if (threadIdx.x == 0) scal[slot] = s;
+}
+
+// x += alpha p; r -= alpha Ap; partial sums of r.r, alpha = scal[RZ]/scal[PAP]
+__global__ void __launch_bounds__(RT) cg_update_kernel(double* __restrict__ x, double* __restrict__ r,
+                                                       const double* __restrict__ p,
+                                                       const double* __restrict__ Ap, long long n,
+                                                       const double* __restrict__ scal,
+                                                       double* __restrict__ part) {
+  const double alpha = scal[S_RZ] / scal[S_PAP];
+  double s = 0.0;
+  const long long stride = (long long)gridDim.x * RT;
+  for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < n; i += stride) {
+    x[i] = fma(alpha, p[i], x[i]);
+    const double ri = fma(-alpha, Ap[i], r[i]);
+    r[i] = ri;
+    s = fma(ri, ri, s);
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// p = z + beta p with beta = scal[RZNEW]/scal[RZ]  (first=1: p = z)
+__global__ void __launch_bounds__(RT) cg_direction_kernel(double* __restrict__ p, const double* __restrict__ z,
+                                                          long long n, const double* __restrict__ scal,
+                                                          int first) {
+  const double beta = first ? 0.0 : scal[S_RZNEW] / scal[S_RZ];
+  const long long stride = (long long)gridDim.x * RT;
+  for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < n; i += stride)
+    p[i] = first ? z[i] : fma(beta, p[i], z[i]);
+}
+
+__global__ void rotate_kernel(double* scal) { scal[S_RZ] = scal[S_RZNEW]; }
+
+// y = (double) x - mean, mean = scal[slot] / n  (or no shift when slot < 0)
+template <class TI, class TO>
+__global__ void __launch_bounds__(RT) convert_shift_kernel(const TI* __restrict__ x, TO* __restrict__ y,
+                                                           long long n, const double* __restrict__ scal,
+                                                           int slot) {
+  const double mu = slot >= 0 ? scal[slot] / (double)n : 0.0;
+  const long long stride = (long long)gridDim.x * RT;
+  for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < n; i += stride)
+    y[i] = (TO)((double)x[i] - mu);
+}
+
+// x = c * dinv[i % nper] * b  (first Chebyshev step from a zero guess)
+template <class T>
+__global__ void __launch_bounds__(RT) cheb_first_kernel(const T* __restrict__ b, const T* __restrict__ dinv,
+                                                        T* __restrict__ x, long long n, int nper, T c) {
+  const long long stride = (long long)gridDim.x * RT;
+  for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < n; i += stride)
+    x[i] = c * dinv[i % nper] * b[i];
+}
+
+__global__ void __launch_bounds__(RT) axpby_kernel(double* __restrict__ y, const double* __restrict__ x,
+                                                   long long n, double a, double b) {
+  const long long stride = (long long)gridDim.x * RT;
+  for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < n; i += stride)
+    y[i] = fma(a, x[i], b * y[i]);
+}
+
+inline unsigned grid_for(long long n) {
+  long long b = (n + RT - 1) / RT;
+  if (b > RED_BLOCKS) b = RED_BLOCKS;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+inline int status() { return cudaGetLastError() == cudaSuccess ? 0 : 2; }
+
+}  // namespace
+
+int dot(const double* a, const double* b, long long n, Reducer& R, int slot, cudaStream_t s) {
+  const unsigned g = grid_for(n);
+  dot_partial<double, double><<<g, RT, 0, s>>>(a, b, n, R.part);
+  finish_sum<<<1, RT, 0, s>>>(R.part, (int)g, R.scal, slot);
+  return status();
+}
+
+int dot_f32(const float* a, const float* b, long long n, Reducer& R, int slot, cudaStream_t s) {
+  const unsigned g = grid_for(n);
+  dot_partial<float, float><<<g, RT, 0, s>>>(a, b, n, R.part);
+  finish_sum<<<1, RT, 0, s>>>(R.part, (int)g, R.scal, slot);
+  return status();
+}
+
+int sum(const double* a, long long n, Reducer& R, int slot, cudaStream_t s) {
+  const unsigned g = grid_for(n);
+  sum_partial<double><<<g, RT, 0, s>>>(a, n, R.part);
+  finish_sum<<<1, RT, 0, s>>>(R.part, (int)g, R.scal, slot);
+  return status();
+}
+
+int sum_f32(const float* a, long long n, Reducer& R, int slot, cudaStream_t s) {
+  const unsigned g = grid_for(n);
+  sum_partial<float><<<g, RT, 0, s>>>(a, n, R.part);
+  finish_sum<<<1, RT, 0, s>>>(R.part, (int)g, R.scal, slot);
+  return status();
+}
+
+int cg_update(double* x, double* r, const double* p, const double* Ap, long long n, Reducer& R,
+              cudaStream_t s) {
+  const unsigned g = grid_for(n);
+  cg_update_kernel<<<g, RT, 0, s>>>(x, r, p, Ap, n, R.scal, R.part);
+  finish_sum<<<1, RT, 0, s>>>(R.part, (int)g, R.scal, S_RR);
+  return status();
+}
+
+int cg_direction(double* p, const double* z, long long n, Reducer& R, bool first, cudaStream_t s) {
+  cg_direction_kernel<<<grid_for(n), RT, 0, s>>>(p, z, n, R.scal, first ? 1 : 0);
+  if (!first) rotate_kernel<<<1, 1, 0, s>>>(R.scal);
+  return status();
+}
+
+int convert_shift(const void* x, bool x32, void* y, bool y32, long long n, const Reducer* R,
+                  int slot, cudaStream_t s) {
+  const unsigned g = grid_for(n);
+  const double* sc = R ? R->scal : nullptr;
+  if (!R) slot = -1;
+  if (x32 && y32)
+    convert_shift_kernel<float, float><<<g, RT, 0, s>>>((const float*)x, (float*)y, n, sc, slot);
+  else if (x32)
+    convert_shift_kernel<float, double><<<g, RT, 0, s>>>((const float*)x, (double*)y, n, sc, slot);
+  else if (y32)
+    convert_shift_kernel<double, float><<<g, RT, 0, s>>>((const double*)x, (float*)y, n, sc, slot);
+  else
+    convert_shift_kernel<double, double><<<g, RT, 0, s>>>((const double*)x, (double*)y, n, sc, slot);
+  return status();
+}
+
+int cheb_first(bool fp32, const void* b, const void* dinv, void* x, long long n, int nper, double c,
+               cudaStream_t s) {
+  const unsigned g = grid_for(n);
+  if (fp32)
+    cheb_first_kernel<float><<<g, RT, 0, s>>>((const float*)b, (const float*)dinv, (float*)x, n, nper, (float)c);
+  else
+    cheb_first_kernel<double><<<g, RT, 0, s>>>((const double*)b, (const double*)dinv, (double*)x, n, nper, c);
+  return status();
+}
+
+int axpby(double* y, const double* x, long long n, double a, double b, cudaStream_t s) {
+  axpby_kernel<<<grid_for(n), RT, 0, s>>>(y, x, n, a, b);
+  return status();
+}
+
+}  // namespace dgns

@@ -1,0 +1,376 @@
+// Convective term c_h of Sec. 3.2 of arXiv:1802.01439 with the conservative
+// flux F_c(u) = u (x) u and the local Lax-Friedrichs numerical flux,
+// over-integrated with Q = floor(3(k+1)/2) Gauss points per direction, FP64;
+// and its vector-Jacobian product.
+//
+// Cell term   y_c = - sum_d (D_d (x) S (x) S)^T [W_d u_c u_d]  at Q^3 points,
+//             W_d = w_qx w_qy w_qz h_x h_y h_z / h_d, S/D: values/derivatives
+//             of the LGL basis at the Gauss points.  The Q^3 data never exist
+//             at once: after interpolating along x and y the kernel walks the
+//             Q planes of constant z, evaluates the flux on the plane, applies
+//             the transposed x and y sweeps and accumulates the z contraction
+//             in registers.
+// Face terms  per face and side, traces of both cells at the Q^2 face points
+//             (LGL: the face values are the nodal values of the face layer),
+//             F* = {{u (x) u}}.n + max(|u-.n|, |u+.n|) (u- - u+), added to
+//             the own face layer with sign + (own cell is '-') or - (own
+//             cell is '+').  Each cell evaluates its six faces.
+#include "ops.h"
+
+namespace dgns {
+namespace {
+
+template <int N>
+constexpr int conv_cells_per_block() {
+  return N * N >= 64 ? 1 : 64 / (N * N);
+}
+
+template <int N, int Q>
+struct ConvTab {
+  double S[Q * N];
+  double D[Q * N];
+  double w[Q];
+  double jac[3];   // h_x h_y h_z / h_d
+  double area[3];  // product of the tangential cell sizes of faces normal to d
+};
+
+template <int N, int Q>
+struct ConvLayout {
+  static constexpr int N3 = N * N * N;
+  static constexpr int U = 3 * N3;               // nodal velocity
+  static constexpr int U1 = 3 * Q * N * N;       // x-interpolated; later: result
+  static constexpr int U2 = 3 * Q * Q * N;       // xy-interpolated; later: face work
+  static constexpr int P = 3 * Q * Q;            // one z-plane at the Gauss points
+  static constexpr int X = 9 * N * Q;            // x-tested plane
+  static constexpr int Y = 6 * N * N;            // xy-tested plane
+  static constexpr int FACE = 6 * Q * N + 6 * Q * Q + 3 * Q * Q;
+  static constexpr int U2F = U2 > FACE ? U2 : FACE;
+  static constexpr int PER = U + U1 + U2F + P + X + Y;
+};
+
+__device__ __forceinline__ int node3(int N, int d, int a, int t1, int j1, int t2, int j2) {
+  int c[3];
+  c[d] = a;
+  c[t1] = j1;
+  c[t2] = j2;
+  return c[0] + N * (c[1] + N * c[2]);
+}
+
+template <int N, int Q>
+__global__ void __launch_bounds__(conv_cells_per_block<N>() * N * N)
+    conv_kernel(const double* __restrict__ u3, double* __restrict__ dst3, const __grid_constant__ ConvTab<N, Q> tb,
+                const MeshDims m) {
+  typedef ConvLayout<N, Q> LY;
+  constexpr int NT = N * N, N3 = N * N * N, EPB = conv_cells_per_block<N>();
+  double* sm = reinterpret_cast<double*>(dyn_smem());
+  const int slot = threadIdx.x / NT;
+  const int t = threadIdx.x - slot * NT;
+  const long long c0 = (long long)blockIdx.x * EPB;
+  const long long rem = m.E - c0;
+  const int nvalid = rem < EPB ? (int)rem : EPB;
+  const bool active = slot < nvalid;
+  double* sU = sm + slot * LY::PER;
+  double* sU1 = sU + LY::U;
+  double* sU2 = sU1 + LY::U1;
+  double* sP = sU2 + LY::U2F;
+  double* sX = sP + LY::P;
+  double* sY = sX + LY::X;
+  double* sOut = sU1;   // reused after the interpolation
+  double* sFace = sU2;  // reused after the cell term
+
+  long long el = 0;
+  int ex = 0, ey = 0, ez = 0;
+  if (active) {
+    el = c0 + slot;
+    ex = (int)(el % m.nx);
+    const long long tt = el / m.nx;
+    ey = (int)(tt % m.ny);
+    ez = (int)(tt / m.ny);
+    for (int c = 0; c < 3; ++c)
+      for (int i = t; i < N3; i += NT) sU[c * N3 + i] = u3[(c * m.E + el) * N3 + i];
+  }
+  __syncthreads();
+  // interpolation along x: (N,N,N) -> (Q,N,N)
+  if (active)
+    for (int it = t; it < 3 * N * N; it += NT) {
+      const int c = it / (N * N), l = it - c * N * N;
+      double x[N];
+      load_line<double, N>(sU + c * N3, l * N, 1, x);
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        double a = tb.S[q * N] * x[0];
+#pragma unroll
+        for (int j = 1; j < N; ++j) a = fma(tb.S[q * N + j], x[j], a);
+        sU1[c * Q * N * N + l * Q + q] = a;
+      }
+    }
+  __syncthreads();
+  // interpolation along y: (Q,N,N) -> (Q,Q,N)
+  if (active)
+    for (int it = t; it < 3 * Q * N; it += NT) {
+      const int c = it / (Q * N), l = it - c * Q * N;
+      const int qx = l % Q, z = l / Q;
+      double x[N];
+      load_line<double, N>(sU1 + c * Q * N * N, qx + Q * N * z, Q, x);
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        double a = tb.S[q * N] * x[0];
+#pragma unroll
+        for (int j = 1; j < N; ++j) a = fma(tb.S[q * N + j], x[j], a);
+        sU2[c * Q * Q * N + qx + Q * q + Q * Q * z] = a;
+      }
+    }
+  __syncthreads();
+
+  double acc[3][N];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int z = 0; z < N; ++z) acc[c][z] = 0.0;
+  const int tx = t % N, ty = t / N;
+
+  for (int qz = 0; qz < Q; ++qz) {
+    // P1: values on the plane z = g_qz
+    if (active)
+      for (int it = t; it < 3 * Q * Q; it += NT) {
+        const int c = it / (Q * Q), l = it - c * Q * Q;
+        const double* src = sU2 + c * Q * Q * N + l;
+        double a = 0.0;
+#pragma unroll
+        for (int z = 0; z < N; ++z) a = fma(tb.S[qz * N + z], src[Q * Q * z], a);
+        sP[it] = a;
+      }
+    __syncthreads();
+    // P2: flux on x-lines of the plane, tested with D_x^T / S_x^T
+    if (active)
+      for (int it = t; it < 3 * Q; it += NT) {
+        const int c = it / Q, qy = it - c * Q;
+        const double wyz = tb.w[qy] * tb.w[qz];
+        double a1[N], a2[N], a3[N];
+#pragma unroll
+        for (int x = 0; x < N; ++x) a1[x] = a2[x] = a3[x] = 0.0;
+#pragma unroll
+        for (int qx = 0; qx < Q; ++qx) {
+          const double u0 = sP[qx + Q * qy], u1 = sP[Q * Q + qx + Q * qy], u2 = sP[2 * Q * Q + qx + Q * qy];
+          const double uc = c == 0 ? u0 : (c == 1 ? u1 : u2);
+          const double wq = tb.w[qx] * wyz * uc;
+          const double fx = wq * tb.jac[0] * u0, fy = wq * tb.jac[1] * u1, fz = wq * tb.jac[2] * u2;
+#pragma unroll
+          for (int x = 0; x < N; ++x) {
+            a1[x] = fma(tb.D[qx * N + x], fx, a1[x]);
+            a2[x] = fma(tb.S[qx * N + x], fy, a2[x]);
+            a3[x] = fma(tb.S[qx * N + x], fz, a3[x]);
+          }
+        }
+#pragma unroll
+        for (int x = 0; x < N; ++x) {
+          sX[(c * 3 + 0) * N * Q + x + N * qy] = a1[x];
+          sX[(c * 3 + 1) * N * Q + x + N * qy] = a2[x];
+          sX[(c * 3 + 2) * N * Q + x + N * qy] = a3[x];
+        }
+      }
+    __syncthreads();
+    // P3: y tests: Y1 = S_y^T X1 + D_y^T X2, Y3 = S_y^T X3
+    if (active)
+      for (int it = t; it < 3 * N; it += NT) {
+        const int c = it / N, x = it - c * N;
+        double y1[N], y3[N];
+#pragma unroll
+        for (int y = 0; y < N; ++y) y1[y] = y3[y] = 0.0;
+#pragma unroll
+        for (int qy = 0; qy < Q; ++qy) {
+          const double b1 = sX[(c * 3 + 0) * N * Q + x + N * qy];
+          const double b2 = sX[(c * 3 + 1) * N * Q + x + N * qy];
+          const double b3 = sX[(c * 3 + 2) * N * Q + x + N * qy];
+#pragma unroll
+          for (int y = 0; y < N; ++y) {
+            y1[y] = fma(tb.S[qy * N + y], b1, fma(tb.D[qy * N + y], b2, y1[y]));
+            y3[y] = fma(tb.S[qy * N + y], b3, y3[y]);
+          }
+        }
+#pragma unroll
+        for (int y = 0; y < N; ++y) {
+          sY[(c * 2 + 0) * N * N + x + N * y] = y1[y];
+          sY[(c * 2 + 1) * N * N + x + N * y] = y3[y];
+        }
+      }
+    __syncthreads();
+    // P4: z test accumulated in registers: acc -= S_z(qz) Y1 + D_z(qz) Y3
+    if (active) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double y1 = sY[(c * 2 + 0) * N * N + tx + N * ty];
+        const double y3 = sY[(c * 2 + 1) * N * N + tx + N * ty];
+#pragma unroll
+        for (int z = 0; z < N; ++z)
+          acc[c][z] = fma(-tb.S[qz * N + z], y1, fma(-tb.D[qz * N + z], y3, acc[c][z]));
+      }
+    }
+  }
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int z = 0; z < N; ++z) sOut[c * N3 + tx + N * ty + N * N * z] = acc[c][z];
+  }
+  __syncthreads();
+
+  // ---------------------------------------------------------------- faces
+  double* G1 = sFace;              // [side][c][q1 + Q j2]   6 Q N
+  double* G2 = G1 + 6 * Q * N;     // [side][c][q1 + Q q2]   6 Q Q
+  double* H = G2 + 6 * Q * Q;      // [c][q1 + Q q2]         3 Q Q
+  double* K1 = G1;                 // [c][q1 + Q j2] reuses G1
+  for (int d = 0; d < 3; ++d) {
+    const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+    for (int side = 1; side >= -1; side -= 2) {
+      long long nb = 0;
+      if (active) {
+        if (d == 0) nb = neighbor<0>(el, ex, ey, ez, side, m);
+        else if (d == 1) nb = neighbor<1>(el, ex, ey, ez, side, m);
+        else nb = neighbor<2>(el, ex, ey, ez, side, m);
+      }
+      const int aown = side > 0 ? N - 1 : 0, anb = side > 0 ? 0 : N - 1;
+      // F1: interpolate both traces along t1
+      if (active)
+        for (int it = t; it < 6 * N; it += NT) {
+          const int s = it / (3 * N), c = (it / N) % 3, j2 = it % N;
+          double v[N];
+#pragma unroll
+          for (int j1 = 0; j1 < N; ++j1)
+            v[j1] = s == 0 ? sU[c * N3 + node3(N, d, aown, t1, j1, t2, j2)]
+                           : __ldg(u3 + (c * m.E + nb) * N3 + node3(N, d, anb, t1, j1, t2, j2));
+#pragma unroll
+          for (int q1 = 0; q1 < Q; ++q1) {
+            double a = tb.S[q1 * N] * v[0];
+#pragma unroll
+            for (int j = 1; j < N; ++j) a = fma(tb.S[q1 * N + j], v[j], a);
+            G1[(s * 3 + c) * Q * N + q1 + Q * j2] = a;
+          }
+        }
+      __syncthreads();
+      // F2: along t2
+      if (active)
+        for (int it = t; it < 6 * Q; it += NT) {
+          const int sc = it / Q, q1 = it - sc * Q;
+          double v[N];
+#pragma unroll
+          for (int j2 = 0; j2 < N; ++j2) v[j2] = G1[sc * Q * N + q1 + Q * j2];
+#pragma unroll
+          for (int q2 = 0; q2 < Q; ++q2) {
+            double a = tb.S[q2 * N] * v[0];
+#pragma unroll
+            for (int j = 1; j < N; ++j) a = fma(tb.S[q2 * N + j], v[j], a);
+            G2[sc * Q * Q + q1 + Q * q2] = a;
+          }
+        }
+      __syncthreads();
+      // F3: LLF flux at the face points, weighted, signed for the own cell
+      if (active)
+        for (int it = t; it < Q * Q; it += NT) {
+          const int q1 = it % Q, q2 = it / Q;
+          const int sm_ = side > 0 ? 0 : 1, sp_ = side > 0 ? 1 : 0;  // trace index of '-' / '+'
+          double um[3], up[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            um[c] = G2[(sm_ * 3 + c) * Q * Q + it];
+            up[c] = G2[(sp_ * 3 + c) * Q * Q + it];
+          }
+          const double unm = um[d], unp = up[d];
+          const double lam = fmax(fabs(unm), fabs(unp));
+          const double wgt = tb.w[q1] * tb.w[q2] * tb.area[d] * (double)side;
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            H[c * Q * Q + it] = wgt * fma(0.5, fma(um[c], unm, up[c] * unp), lam * (um[c] - up[c]));
+        }
+      __syncthreads();
+      // F4: test along t2
+      if (active)
+        for (int it = t; it < 3 * Q; it += NT) {
+          const int c = it / Q, q1 = it - c * Q;
+          double a[N];
+#pragma unroll
+          for (int j = 0; j < N; ++j) a[j] = 0.0;
+#pragma unroll
+          for (int q2 = 0; q2 < Q; ++q2) {
+            const double h = H[c * Q * Q + q1 + Q * q2];
+#pragma unroll
+            for (int j = 0; j < N; ++j) a[j] = fma(tb.S[q2 * N + j], h, a[j]);
+          }
+#pragma unroll
+          for (int j2 = 0; j2 < N; ++j2) K1[c * Q * N + q1 + Q * j2] = a[j2];
+        }
+      __syncthreads();
+      // F5: test along t1, add into the own face layer
+      if (active)
+        for (int it = t; it < 3 * N; it += NT) {
+          const int c = it / N, j2 = it - c * N;
+          double a[N];
+#pragma unroll
+          for (int j = 0; j < N; ++j) a[j] = 0.0;
+#pragma unroll
+          for (int q1 = 0; q1 < Q; ++q1) {
+            const double h = K1[c * Q * N + q1 + Q * j2];
+#pragma unroll
+            for (int j = 0; j < N; ++j) a[j] = fma(tb.S[q1 * N + j], h, a[j]);
+          }
+#pragma unroll
+          for (int j1 = 0; j1 < N; ++j1) sOut[c * N3 + node3(N, d, aown, t1, j1, t2, j2)] += a[j1];
+        }
+      __syncthreads();
+    }
+  }
+  if (active)
+    for (int c = 0; c < 3; ++c)
+      for (int i = t; i < N3; i += NT) dst3[(c * m.E + el) * N3 + i] = sOut[c * N3 + i];
+}
+
+template <int N, int Q>
+int launch_conv(const MeshDims& m, const double* u3, double* dst3, const ConvHost& h, cudaStream_t s) {
+  ConvTab<N, Q> tb;
+  for (int i = 0; i < Q * N; ++i) {
+    tb.S[i] = h.S[i];
+    tb.D[i] = h.D[i];
+  }
+  for (int q = 0; q < Q; ++q) tb.w[q] = h.w[q];
+  for (int d = 0; d < 3; ++d) {
+    tb.jac[d] = h.h[0] * h.h[1] * h.h[2] / h.h[d];
+    tb.area[d] = tb.jac[d];
+  }
+  constexpr int EPB = conv_cells_per_block<N>();
+  const size_t smem = (size_t)EPB * ConvLayout<N, Q>::PER * sizeof(double);
+  if (smem > 232448) return 7;
+  if (cudaFuncSetAttribute(conv_kernel<N, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return 2;
+  if (m.E == 0) return 0;
+  const long long blocks = (m.E + EPB - 1) / EPB;
+  conv_kernel<N, Q><<<(unsigned)blocks, EPB * N * N, smem, s>>>(u3, dst3, tb, m);
+  return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
+
+}  // namespace
+
+// Supported: Q = floor(3N/2) (the 3/2 rule) and Q = N.
+int convective_apply(const MeshDims& m, const double* u3, double* dst3, const ConvHost& t,
+                     cudaStream_t s) {
+  const int N = t.N, Q = t.Q;
+#define DGNS_CONV(NV)                                                     \
+  if (N == NV && Q == (3 * NV) / 2) return launch_conv<NV, (3 * NV) / 2>(m, u3, dst3, t, s); \
+  if (N == NV && Q == NV) return launch_conv<NV, NV>(m, u3, dst3, t, s);
+  DGNS_CONV(2)
+  DGNS_CONV(3)
+  DGNS_CONV(4)
+  DGNS_CONV(5)
+  DGNS_CONV(6)
+  DGNS_CONV(7)
+  DGNS_CONV(8)
+  DGNS_CONV(9)
+  DGNS_CONV(10)
+  DGNS_CONV(11)
+  DGNS_CONV(12)
+#undef DGNS_CONV
+  return 7;
+}
+
+}  // namespace dgns

@@ -1,0 +1,292 @@
+// Cell-local tensor-product kernels: mass matrix and its exact inverse
+// (Secs. 3.2 and 3.3 of arXiv:1802.01439; on an affine Cartesian cell the
+// element mass matrix is h_x h_y h_z Mhat (x) Mhat (x) Mhat and its inverse
+// the Kronecker product of the 1D inverses, three sweeps per cell), and the
+// h-multigrid transfers (embedding of a coarse cell polynomial into its eight
+// children and the transpose).
+#include "ops.h"
+
+namespace dgns {
+namespace {
+
+template <int N>
+constexpr int tcells_per_block() {
+  return N * N >= 128 ? 1 : 128 / (N * N);
+}
+
+template <class T, int N>
+struct Tens3 {
+  T Mx[N * N], My[N * N], Mz[N * N];
+};
+
+template <class T, int N, int D>
+__device__ __forceinline__ void sweep_line(const T* in, T* out, int l, const T* A) {
+  int base, stride;
+  line_geom<D>(l, N, N, N, base, stride);
+  T x[N], y[N];
+  load_line<T, N>(in, base, stride, x);
+  matvec<T, N, N>(A, x, y);
+  store_line<T, N>(out, base, stride, y);
+}
+
+template <class T, int N>
+__global__ void __launch_bounds__(tcells_per_block<N>() * N * N)
+    tensor3_kernel(const T* __restrict__ src, T* __restrict__ dst, const __grid_constant__ Tens3<T, N> tb,
+                   const long long ncells) {
+  constexpr int NN = N * N, NNN = NN * N, EPB = tcells_per_block<N>();
+  T* sX = reinterpret_cast<T*>(dyn_smem());
+  T* sA = sX + EPB * NNN;
+  const int slot = threadIdx.x / NN;
+  const int l = threadIdx.x - slot * NN;
+  const long long c0 = (long long)blockIdx.x * EPB;
+  const long long rem = ncells - c0;
+  const int nvalid = rem < EPB ? (int)rem : EPB;
+  for (int i = threadIdx.x; i < nvalid * NNN; i += blockDim.x) sX[i] = src[c0 * NNN + i];
+  __syncthreads();
+  const bool active = slot < nvalid;
+  const int off = slot * NNN;
+  if (active) sweep_line<T, N, 0>(sX + off, sA + off, l, tb.Mx);
+  __syncthreads();
+  if (active) sweep_line<T, N, 1>(sA + off, sA + off, l, tb.My);
+  __syncthreads();
+  if (active) sweep_line<T, N, 2>(sA + off, sX + off, l, tb.Mz);
+  __syncthreads();
+  for (int i = threadIdx.x; i < nvalid * NNN; i += blockDim.x) dst[c0 * NNN + i] = sX[i];
+}
+
+template <class T, int N>
+int launch_tensor3(long long ncells, const T* src, T* dst, const double* Mx, const double* My,
+                   const double* Mz, cudaStream_t s) {
+  constexpr int NN = N * N, EPB = tcells_per_block<N>();
+  Tens3<T, N> tb;
+  for (int i = 0; i < NN; ++i) {
+    tb.Mx[i] = (T)Mx[i];
+    tb.My[i] = (T)My[i];
+    tb.Mz[i] = (T)Mz[i];
+  }
+  if (ncells == 0) return 0;
+  const size_t smem = (size_t)2 * EPB * NN * N * sizeof(T);
+  static bool attr_done = false;
+  if (!attr_done) {
+    if (cudaFuncSetAttribute(tensor3_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return 2;
+    attr_done = true;
+  }
+  const long long blocks = (ncells + EPB - 1) / EPB;
+  tensor3_kernel<T, N><<<(unsigned)blocks, EPB * NN, smem, s>>>(src, dst, tb, ncells);
+  return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
+
+// ---------------------------------------------------------------- transfers
+template <class T, int N>
+struct Prol {
+  T P[2][N * N];  // P[c][i*N+j] = phi_j((xi_i + c)/2)
+};
+
+// One block per EPB fine cells; each fine cell reads its parent.
+template <class T, int N, bool ADD>
+__global__ void __launch_bounds__(tcells_per_block<N>() * N * N)
+    prolong_kernel(const T* __restrict__ coarse, T* __restrict__ fine, const __grid_constant__ Prol<T, N> tb,
+                   const MeshDims mc, const long long nfine) {
+  constexpr int NN = N * N, NNN = NN * N, EPB = tcells_per_block<N>();
+  T* sX = reinterpret_cast<T*>(dyn_smem());
+  T* sA = sX + EPB * NNN;
+  const int slot = threadIdx.x / NN;
+  const int l = threadIdx.x - slot * NN;
+  const long long f = (long long)blockIdx.x * EPB + slot;
+  const bool active = f < nfine;
+  const int off = slot * NNN;
+  const int nfx = 2 * mc.nx, nfy = 2 * mc.ny;
+  int cx = 0, cy = 0, cz = 0;
+  if (active) {
+    const int fi = (int)(f % nfx);
+    const long long t = f / nfx;
+    const int fj = (int)(t % nfy);
+    const int fk = (int)(t / nfy);
+    cx = fi & 1;
+    cy = fj & 1;
+    cz = fk & 1;
+    const long long p = (fi >> 1) + (long long)mc.nx * ((fj >> 1) + (long long)mc.ny * (fk >> 1));
+    for (int i = l; i < NNN; i += NN) sX[off + i] = coarse[p * NNN + i];
+  }
+  __syncthreads();
+  if (active) sweep_line<T, N, 0>(sX + off, sA + off, l, tb.P[cx]);
+  __syncthreads();
+  if (active) sweep_line<T, N, 1>(sA + off, sA + off, l, tb.P[cy]);
+  __syncthreads();
+  if (active) sweep_line<T, N, 2>(sA + off, sX + off, l, tb.P[cz]);
+  __syncthreads();
+  const long long c0 = (long long)blockIdx.x * EPB;
+  const long long rem = nfine - c0;
+  const int nvalid = rem < EPB ? (int)rem : EPB;
+  for (int i = threadIdx.x; i < nvalid * NNN; i += blockDim.x) {
+    if (ADD)
+      fine[c0 * NNN + i] += sX[i];
+    else
+      fine[c0 * NNN + i] = sX[i];
+  }
+}
+
+// coarse = sum over the 8 children of (P_cz^T (x) P_cy^T (x) P_cx^T) fine_child
+template <class T, int N>
+__global__ void __launch_bounds__(tcells_per_block<N>() * N * N)
+    restrict_kernel(const T* __restrict__ fine, T* __restrict__ coarse, const __grid_constant__ Prol<T, N> tb,
+                    const MeshDims mc, const long long ncoarse) {
+  constexpr int NN = N * N, NNN = NN * N, EPB = tcells_per_block<N>();
+  T* sX = reinterpret_cast<T*>(dyn_smem());
+  T* sA = sX + EPB * NNN;
+  T* sS = sA + EPB * NNN;
+  const int slot = threadIdx.x / NN;
+  const int l = threadIdx.x - slot * NN;
+  const long long c = (long long)blockIdx.x * EPB + slot;
+  const bool active = c < ncoarse;
+  const int off = slot * NNN;
+  int ci = 0, cj = 0, ck = 0;
+  if (active) {
+    ci = (int)(c % mc.nx);
+    const long long t = c / mc.nx;
+    cj = (int)(t % mc.ny);
+    ck = (int)(t / mc.ny);
+    for (int i = l; i < NNN; i += NN) sS[off + i] = (T)0;
+  }
+  const long long nfx = 2 * mc.nx, nfy = 2 * mc.ny;
+  for (int child = 0; child < 8; ++child) {
+    const int cx = child & 1, cy = (child >> 1) & 1, cz = child >> 2;
+    __syncthreads();
+    if (active) {
+      const long long f = (2 * ci + cx) + nfx * ((2 * cj + cy) + nfy * (2 * ck + cz));
+      for (int i = l; i < NNN; i += NN) sX[off + i] = fine[f * NNN + i];
+    }
+    __syncthreads();
+    if (active) {
+      // transposed sweeps: y_j = sum_i P[i][j] x_i
+      int base, stride;
+      line_geom<0>(l, N, N, N, base, stride);
+      T x[N], y[N];
+      load_line<T, N>(sX + off, base, stride, x);
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        T acc = tb.P[cx][j] * x[0];
+#pragma unroll
+        for (int i = 1; i < N; ++i) acc = fma(tb.P[cx][i * N + j], x[i], acc);
+        y[j] = acc;
+      }
+      store_line<T, N>(sA + off, base, stride, y);
+    }
+    __syncthreads();
+    if (active) {
+      int base, stride;
+      line_geom<1>(l, N, N, N, base, stride);
+      T x[N], y[N];
+      load_line<T, N>(sA + off, base, stride, x);
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        T acc = tb.P[cy][j] * x[0];
+#pragma unroll
+        for (int i = 1; i < N; ++i) acc = fma(tb.P[cy][i * N + j], x[i], acc);
+        y[j] = acc;
+      }
+      store_line<T, N>(sA + off, base, stride, y);
+    }
+    __syncthreads();
+    if (active) {
+      int base, stride;
+      line_geom<2>(l, N, N, N, base, stride);
+      T x[N], y[N];
+      load_line<T, N>(sA + off, base, stride, x);
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        T acc = sS[off + base + j * stride];
+#pragma unroll
+        for (int i = 0; i < N; ++i) acc = fma(tb.P[cz][i * N + j], x[i], acc);
+        y[j] = acc;
+      }
+      store_line<T, N>(sS + off, base, stride, y);
+    }
+  }
+  __syncthreads();
+  const long long c0 = (long long)blockIdx.x * EPB;
+  const long long rem = ncoarse - c0;
+  const int nvalid = rem < EPB ? (int)rem : EPB;
+  for (int i = threadIdx.x; i < nvalid * NNN; i += blockDim.x) coarse[c0 * NNN + i] = sS[i];
+}
+
+template <class T, int N>
+Prol<T, N> make_prol(const double* P0, const double* P1) {
+  Prol<T, N> tb;
+  for (int i = 0; i < N * N; ++i) {
+    tb.P[0][i] = (T)P0[i];
+    tb.P[1][i] = (T)P1[i];
+  }
+  return tb;
+}
+
+template <class T, int N>
+int launch_prolong(const MeshDims& mc, const T* coarse, T* fine, const double* P0,
+                   const double* P1, bool add, cudaStream_t s) {
+  constexpr int NN = N * N, EPB = tcells_per_block<N>();
+  const long long nfine = 8 * mc.E;
+  if (nfine == 0) return 0;
+  const size_t smem = (size_t)2 * EPB * NN * N * sizeof(T);
+  auto kern = add ? prolong_kernel<T, N, true> : prolong_kernel<T, N, false>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 2;
+  const long long blocks = (nfine + EPB - 1) / EPB;
+  kern<<<(unsigned)blocks, EPB * NN, smem, s>>>(coarse, fine, make_prol<T, N>(P0, P1), mc, nfine);
+  return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
+
+template <class T, int N>
+int launch_restrict(const MeshDims& mc, const T* fine, T* coarse, const double* P0,
+                    const double* P1, cudaStream_t s) {
+  constexpr int NN = N * N, EPB = tcells_per_block<N>();
+  if (mc.E == 0) return 0;
+  const size_t smem = (size_t)3 * EPB * NN * N * sizeof(T);
+  if (cudaFuncSetAttribute(restrict_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
+    return 2;
+  const long long blocks = (mc.E + EPB - 1) / EPB;
+  restrict_kernel<T, N><<<(unsigned)blocks, EPB * NN, smem, s>>>(fine, coarse, make_prol<T, N>(P0, P1), mc,
+                                                                 mc.E);
+  return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
+
+}  // namespace
+
+#define DGNS_SWITCH_N(NVAR, ...) \
+  switch (NVAR) {                 \
+    case 2: { constexpr int NC = 2; __VA_ARGS__; } \
+    case 3: { constexpr int NC = 3; __VA_ARGS__; } \
+    case 4: { constexpr int NC = 4; __VA_ARGS__; } \
+    case 5: { constexpr int NC = 5; __VA_ARGS__; } \
+    case 6: { constexpr int NC = 6; __VA_ARGS__; } \
+    case 7: { constexpr int NC = 7; __VA_ARGS__; } \
+    case 8: { constexpr int NC = 8; __VA_ARGS__; } \
+    case 9: { constexpr int NC = 9; __VA_ARGS__; } \
+    case 10: { constexpr int NC = 10; __VA_ARGS__; } \
+    case 11: { constexpr int NC = 11; __VA_ARGS__; } \
+    case 12: { constexpr int NC = 12; __VA_ARGS__; } \
+  }
+
+int tensor3_apply(int N, long long ncells, const double* src, double* dst, const double* Mx,
+                  const double* My, const double* Mz, cudaStream_t s) {
+  DGNS_SWITCH_N(N, return launch_tensor3<double, NC>(ncells, src, dst, Mx, My, Mz, s))
+  return 7;
+}
+
+int prolongate(bool fp32, int N, const MeshDims& mc, const void* coarse, void* fine,
+               const double* P0, const double* P1, bool add, cudaStream_t s) {
+  DGNS_SWITCH_N(N, return fp32 ? launch_prolong<float, NC>(mc, (const float*)coarse, (float*)fine, P0, P1, add, s)
+                               : launch_prolong<double, NC>(mc, (const double*)coarse, (double*)fine, P0, P1, add, s))
+  return 7;
+}
+
+int restrict_fine(bool fp32, int N, const MeshDims& mc, const void* fine, void* coarse,
+                  const double* P0, const double* P1, cudaStream_t s) {
+  DGNS_SWITCH_N(N, return fp32 ? launch_restrict<float, NC>(mc, (const float*)fine, (float*)coarse, P0, P1, s)
+                               : launch_restrict<double, NC>(mc, (const double*)fine, (double*)coarse, P0, P1, s))
+  return 7;
+}
+
+}  // namespace dgns

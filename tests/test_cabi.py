@@ -1,0 +1,81 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/dgns.h declares; host-side argument checks work without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1802_01439_gb300 import _lib, build
+    build.build()
+    return _lib.load()
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "dgns.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dgns_\w+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = header_functions()
+    for required in ("dgns_create", "dgns_vmult_laplace", "dgns_vmult_convective",
+                     "dgns_vmult_viscous", "dgns_apply_inverse_mass", "dgns_cg_mg_solve"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1802_01439_gb300 import _lib
+    for name in header_functions():
+        assert hasattr(lib, name), name
+        assert name in _lib.SIGNATURES, "binding misses " + name
+
+
+def test_defaults_and_strings(lib):
+    from paper_1802_01439_gb300 import _lib
+    d = _lib.MeshDesc()
+    lib.dgns_default_desc(ctypes.byref(d))
+    assert list(d.n_elem) == [4, 4, 4] and d.degree == 3 and d.degree_p == -1
+    assert abs(d.hi[0] - 3.141592653589793) < 1e-15 and d.mg_precision == 32
+    p = _lib.SolveParams()
+    lib.dgns_default_solve_params(ctypes.byref(p))
+    assert p.cheb_degree == 5 and p.smoothing_range == 20.0 and p.rel_tol == 1e-10
+    for code in range(8):
+        assert lib.dgns_status_string(code)
+
+
+@pytest.mark.parametrize("field,value", [("degree", 0), ("degree", 12), ("degree_p", 13),
+                                         ("mg_precision", 16), ("n_q_conv", 7)])
+def test_create_rejects_bad_descriptions(lib, field, value):
+    from paper_1802_01439_gb300 import _lib
+    d = _lib.MeshDesc()
+    lib.dgns_default_desc(ctypes.byref(d))
+    setattr(d, field, value)
+    h = ctypes.c_void_p(1)
+    rc = lib.dgns_create(ctypes.byref(d), None, ctypes.byref(h))
+    assert rc in (_lib.DGNS_ERR_INVALID_ARG, _lib.DGNS_ERR_UNSUPPORTED)
+    assert h.value is None
+    assert lib.dgns_last_error()
+
+
+def test_create_rejects_bad_mesh(lib):
+    from paper_1802_01439_gb300 import _lib
+    d = _lib.MeshDesc()
+    lib.dgns_default_desc(ctypes.byref(d))
+    d.n_elem[1] = 0
+    h = ctypes.c_void_p()
+    assert lib.dgns_create(ctypes.byref(d), None, ctypes.byref(h)) == _lib.DGNS_ERR_INVALID_ARG
+    d.n_elem[1] = 4
+    d.hi[2] = d.lo[2]
+    assert lib.dgns_create(ctypes.byref(d), None, ctypes.byref(h)) == _lib.DGNS_ERR_INVALID_ARG
+
+
+def test_null_context_is_rejected(lib):
+    from paper_1802_01439_gb300 import _lib
+    assert lib.dgns_vmult_laplace(None, None, None, 0) == _lib.DGNS_ERR_INVALID_ARG
+    assert lib.dgns_cg_mg_solve(None, None, None, None, None) == _lib.DGNS_ERR_INVALID_ARG

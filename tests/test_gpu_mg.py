@@ -1,0 +1,124 @@
+"""GPU vs oracle parity of the multigrid components and the solvers.
+
+FP32 level operators and transfers: relative max-norm error <= 1e-5 against
+the FP64 oracle on the same (FP32-rounded) input.  The FP64 V-cycle matches
+the oracle's V-cycle to 1e-11 given the same eigenvalue bounds; the FP32
+V-cycle to 1e-4 (Chebyshev polynomials of degree 5/20 amplify the FP32
+rounding of each level operator by at most their maximum on the smoothing
+interval, a few hundred at worst).  Solves are checked through the oracle's
+own FP64 residual.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import dg, mg, solvers
+from tests.gpu_common import build_lib, context, dev, host, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build_lib()
+
+
+def rand32(n, seed):
+    return np.random.default_rng(seed).uniform(-1, 1, n).astype(np.float32)
+
+
+@pytest.mark.parametrize("n,kp", [(8, 3), (4, 2), (6, 5)])
+def test_level_operators_fp32(n, kp):
+    ctx = context(n, kp + 1, kp)
+    info = ctx.mg_info()
+    H = mg.Hierarchy(dg.Mesh(n), kp, coarse_n=2)
+    assert info["levels"] == len(H.levels)
+    for lvl, L in enumerate(H.levels):
+        s = L["space"]
+        x = rand32(s.size, lvl)
+        y = torch.empty(s.size, dtype=torch.float32, device="cuda")
+        ctx.vmult_laplace_f32(y, dev(x, torch.float32), lvl)
+        ref = L["op"].apply(x.astype(np.float64).reshape(s.mesh.E, -1))
+        assert rel_err(host(y), ref) <= 1e-5
+    for lvl in range(len(H.levels) - 1):
+        T = H.transfers[lvl]
+        xc = rand32(T.cs.size, 10 + lvl)
+        xf = torch.empty(T.fs.size, dtype=torch.float32, device="cuda")
+        ctx.mg_prolongate_f32(xf, dev(xc, torch.float32), lvl)
+        assert rel_err(host(xf), T.prolongate(xc.astype(np.float64).reshape(T.cs.mesh.E, -1))) <= 1e-5
+        xf0 = rand32(T.fs.size, 20 + lvl)
+        yc = torch.empty(T.cs.size, dtype=torch.float32, device="cuda")
+        ctx.mg_restrict_f32(yc, dev(xf0, torch.float32), lvl)
+        assert rel_err(host(yc), T.restrict(xf0.astype(np.float64).reshape(T.fs.mesh.E, -1))) <= 1e-5
+
+
+def test_lambda_estimates_bound_the_spectrum():
+    n, kp = 4, 2
+    ctx = context(n, kp + 1, kp)
+    lam = ctx.mg_info()["lambda_max"]
+    H = mg.Hierarchy(dg.Mesh(n), kp, coarse_n=2)
+    for L, l_gpu in zip(H.levels, lam):
+        A = L["op"].matrix()
+        d = np.sqrt(L["inv_diag"].ravel())
+        true = np.linalg.eigvalsh(d[:, None] * A * d[None, :])[-1]
+        assert true <= l_gpu <= 1.3 * true
+
+
+@pytest.mark.parametrize("prec,tol", [(64, 1e-11), (32, 1e-4)])
+def test_vcycle_matches_oracle(prec, tol):
+    n, kp = 8, 3
+    ctx = context(n, kp + 1, kp, mg_precision=prec)
+    lam = ctx.mg_info()["lambda_max"]
+    H = mg.Hierarchy(dg.Mesh(n), kp, coarse_n=2)
+    s = H.levels[-1]["space"]
+    r = np.random.default_rng(7).uniform(-1, 1, s.size)
+    z = torch.empty(s.size, dtype=torch.float64, device="cuda")
+    ctx.mg_vcycle(z, dev(r))
+    ref = H.vcycle(r.reshape(s.mesh.E, -1), lam, degree=5, smoothing_range=20.0, coarse_iters=20)
+    assert rel_err(host(z), ref) <= tol
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+@pytest.mark.parametrize("n,kp", [(8, 3), (4, 2), ((4, 8, 4), 3)])
+def test_cg_mg_solve(prec, n, kp):
+    ctx = context(n, kp + 1, kp, mg_precision=prec)
+    s = dg.Space(dg.Mesh(n), kp)
+    b = solvers.mean_free(np.random.default_rng(11).uniform(-1, 1, s.size))
+    x = torch.zeros(s.size, dtype=torch.float64, device="cuda")
+    info = ctx.cg_mg_solve(x, dev(b), rel_tol=1e-10)
+    assert info["rc"] == 0 and info["rel_res"] <= 1e-10
+    assert info["iterations"] <= 30
+    L = dg.Laplace(s)
+    assert solvers.relative_residual(lambda v: L.apply(v.reshape(s.mesh.E, -1)).ravel(),
+                                     host(x), b) <= 1.5e-10
+
+
+def test_cg_not_converged_is_reported():
+    ctx = context(4, 3, 2)
+    s = dg.Space(dg.Mesh(4), 2)
+    b = solvers.mean_free(np.random.default_rng(1).uniform(-1, 1, s.size))
+    x = torch.zeros(s.size, dtype=torch.float64, device="cuda")
+    info = ctx.cg_mg_solve(x, dev(b), raise_on_error=False, rel_tol=1e-14, max_iter=2)
+    assert info["rc"] == 4 and info["iterations"] == 2
+
+
+def test_cg_nonfinite_is_reported():
+    ctx = context(4, 3, 2)
+    b = torch.full((ctx.n_p,), float("nan"), dtype=torch.float64, device="cuda")
+    x = torch.zeros_like(b)
+    info = ctx.cg_mg_solve(x, b, raise_on_error=False)
+    assert info["rc"] == 5
+
+
+def test_helmholtz_invmass_cg():
+    n, k = (4, 3, 4), 3
+    nu, mf = 1.0 / 1600, 1.5 / 1e-3
+    ctx = context(n, k, mg_precision=0, nu=nu)
+    s = dg.Space(dg.Mesh(n), k)
+    b = np.random.default_rng(3).uniform(-1, 1, 3 * s.size)
+    x = torch.zeros(3 * s.size, dtype=torch.float64, device="cuda")
+    info = ctx.cg_invmass_solve(x, dev(b), mf, rel_tol=1e-12)
+    assert info["rc"] == 0 and info["iterations"] <= 15
+    Hm = dg.Helmholtz(s, nu, mf)
+    res = solvers.relative_residual(lambda v: Hm.apply(v.reshape(3, s.mesh.E, -1)).ravel(), host(x), b)
+    assert res <= 2e-12

@@ -1,0 +1,140 @@
+"""GPU vs oracle parity of the FP64 operators through the C ABI.
+
+Bar: relative max-norm error <= 1e-12 (FP64 operators).  Cases span several
+blocks of cells, ragged meshes (odd and unequal n), n = 1 (a cell is its own
+periodic neighbour), non-cubic cells, a non-default penalty factor, and the
+degree range k = 1..11.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import dg
+from tests.gpu_common import build_lib, context, dev, host, random_field, rel_err, tgv_field
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+LAP_CASES = [
+    ((4, 4, 4), 3, {}),                                   # the 4^3, k=3 parity case
+    ((3, 2, 5), 2, {}),
+    ((1, 1, 1), 3, {}),
+    ((2, 3, 1), 5, {"penalty_factor": 2.5}),
+    ((5, 4, 3), 1, {}),
+    ((3, 2, 2), 7, {"lo": (0.0, -1.0, 0.0), "hi": (1.0, 2.0, 0.5)}),
+    ((2, 2, 2), 11, {}),
+    ((7, 3, 2), 4, {}),
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build_lib()
+
+
+def _mesh(n, kw):
+    return dg.Mesh(n, kw.get("lo", (-np.pi,) * 3), kw.get("hi", (np.pi,) * 3))
+
+
+@pytest.mark.parametrize("n,k,kw", LAP_CASES)
+def test_laplace(n, k, kw):
+    ctx = context(n, k, mg_precision=0, **kw)
+    s = dg.Space(_mesh(n, kw), k)
+    x = random_field(s, 1, 0)
+    ref = dg.Laplace(s, kw.get("penalty_factor", 1.0)).apply(x)
+    y = torch.empty(s.size, dtype=torch.float64, device="cuda")
+    ctx.vmult_laplace(y, dev(x), space=0)
+    assert rel_err(host(y), ref) <= TOL
+    # the diagonal of the same operator
+    d = torch.empty_like(y)
+    ctx.laplace_diagonal(d, space=0)
+    assert rel_err(host(d), dg.Laplace(s, kw.get("penalty_factor", 1.0)).diagonal()) <= TOL
+
+
+def test_laplace_pressure_space():
+    n, ku = (3, 4, 2), 4
+    ctx = context(n, ku, mg_precision=0)
+    s = dg.Space(dg.Mesh(n), ku - 1)
+    x = random_field(s, 1, 3)
+    y = torch.empty(s.size, dtype=torch.float64, device="cuda")
+    ctx.vmult_laplace(y, dev(x), space=1)
+    assert rel_err(host(y), dg.Laplace(s).apply(x)) <= TOL
+
+
+@pytest.mark.parametrize("n,k,kw", LAP_CASES[:6])
+def test_mass_and_inverse(n, k, kw):
+    ctx = context(n, k, mg_precision=0, **kw)
+    s = dg.Space(_mesh(n, kw), k)
+    M = dg.Mass(s)
+    for ncomp in (1, 3):
+        x = random_field(s, ncomp, 1)
+        y = torch.empty(x.size, dtype=torch.float64, device="cuda")
+        ctx.vmult_mass(y, dev(x), ncomp=ncomp, space=0)
+        assert rel_err(host(y), M.apply(x)) <= TOL
+        ctx.apply_inverse_mass(y, dev(x), ncomp=ncomp, space=0)
+        assert rel_err(host(y), M.apply_inverse(x)) <= TOL
+
+
+@pytest.mark.parametrize("n,k", [((3, 2, 4), 3), ((2, 2, 3), 5), ((1, 2, 1), 2)])
+def test_viscous_and_helmholtz(n, k):
+    nu = 1.0 / 1600
+    ctx = context(n, k, mg_precision=0, nu=nu)
+    s = dg.Space(dg.Mesh(n), k)
+    u = random_field(s, 3, 2)
+    y = torch.empty(u.size, dtype=torch.float64, device="cuda")
+    ctx.vmult_viscous(y, dev(u))
+    assert rel_err(host(y), dg.Viscous(s, nu).apply(u)) <= TOL
+    mf = 1.5 / 1e-3
+    ctx.vmult_helmholtz(y, dev(u), mf)
+    assert rel_err(host(y), dg.Helmholtz(s, nu, mf).apply(u)) <= TOL
+
+
+@pytest.mark.parametrize("n,ku", [((3, 2, 4), 3), ((2, 2, 2), 5), ((1, 2, 3), 2), ((2, 1, 1), 11),
+                                  ((4, 4, 4), 4)])
+def test_divergence_gradient(n, ku):
+    ctx = context(n, ku, mg_precision=0)
+    m = dg.Mesh(n)
+    su, sp = dg.Space(m, ku), dg.Space(m, ku - 1)
+    u = random_field(su, 3, 4)
+    p = random_field(sp, 1, 5)
+    y = torch.empty(sp.size, dtype=torch.float64, device="cuda")
+    ctx.vmult_divergence(y, dev(u))
+    assert rel_err(host(y), dg.Divergence(su, sp).apply(u)) <= TOL
+    g = torch.empty(3 * su.size, dtype=torch.float64, device="cuda")
+    ctx.vmult_gradient(g, dev(p))
+    assert rel_err(host(g), dg.Gradient(su, sp).apply(p)) <= TOL
+
+
+@pytest.mark.parametrize("n,k,field", [((4, 4, 4), 3, "tgv"), ((3, 2, 5), 2, "rand"),
+                                       ((2, 2, 2), 5, "rand"), ((1, 1, 2), 1, "rand"),
+                                       ((2, 1, 1), 11, "tgv"), ((2, 3, 2), 7, "tgv")])
+def test_convective(n, k, field):
+    ctx = context(n, k, mg_precision=0)
+    s = dg.Space(dg.Mesh(n), k)
+    u = tgv_field(s, 1e-3, 0) if field == "tgv" else random_field(s, 3, 6)
+    ref = dg.Convective(s).apply(u)
+    y = torch.empty(u.size, dtype=torch.float64, device="cuda")
+    ctx.vmult_convective(y, dev(u))
+    assert rel_err(host(y), ref) <= TOL
+
+
+def test_host_pointers_are_staged():
+    """CPU tensors go through the library's staging buffers and give the same
+    result as device tensors."""
+    n, k = (3, 2, 2), 3
+    ctx = context(n, k, mg_precision=0)
+    s = dg.Space(dg.Mesh(n), k)
+    x = random_field(s, 1, 9)
+    yh = torch.empty(s.size, dtype=torch.float64)
+    ctx.vmult_laplace(yh, torch.from_numpy(x.ravel().copy()), space=0)
+    yd = torch.empty(s.size, dtype=torch.float64, device="cuda")
+    ctx.vmult_laplace(yd, dev(x), space=0)
+    assert np.array_equal(yh.numpy(), host(yd))
+
+
+def test_alias_rejected():
+    from paper_1802_01439_gb300 import DgnsError
+    ctx = context((2, 2, 2), 2, mg_precision=0)
+    x = torch.zeros(ctx.n_u, dtype=torch.float64, device="cuda")
+    with pytest.raises(DgnsError):
+        ctx.vmult_laplace(x, x, space=0)
