@@ -1,0 +1,392 @@
+"""Benchmark of the matrix-free DG operator set on one GB300.
+
+Workload (the paper's Taylor-Green setting, Sec. 4): periodic cube
+[-pi, pi]^3 with 32^3 hexahedra, k_u = 3 (2,097,152 scalar DoFs per velocity
+component), k_p = 2, 3/2-rule convective quadrature (6 points), nu = 1/1600;
+velocity = Taylor-Green field at the LGL nodes + 1e-3 seeded uniform noise.
+One step evaluates the full FP64 operator set once, chained as in the
+dual-splitting substeps (Sec. 3.3):
+    c = C(u);  uh = M^-1 c;  d = D uh;  l = L d;  g = G l;  v = (m M + V) uh
+Throughput = operator DoFs per second, where each evaluation counts the DoFs
+of the vector it acts on (the paper's N_dofs / t_wall per operator, Sec. 4.4):
+12 n_u + 2 n_p = 26,935,296 per step.
+
+L2 is flushed (a 256 MiB write) before every timed step; step times come from
+CUDA events on the launching stream.  After the timed steps, bench.py also
+times the pressure Poisson solve of the 64^3, k_p = 3 workload to relative
+residual 1e-10 with the FP32 and the FP64 V-cycle (outside the timed region).
+
+--impl reference times the CPU oracle (test infrastructure, plain FP64
+numpy/LAPACK with explicit element and face matrices) on the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_ELEM = 32
+K_U = 3
+K_P = 2
+NU = 1.0 / 1600
+MASS_FACTOR = 1.5 / 1e-3        # gamma_0 / dt of BDF2 with dt = 1e-3
+WORKLOAD = ("full FP64 operator set (C, M^-1, D, L, G, mM+V) on 32^3 hex cells, k_u=3, k_p=2, "
+            "q_conv=6, Taylor-Green + 1e-3 noise, periodic [-pi,pi]^3")
+METRIC = "DG operator eval DoFs/s (FP64)"
+FP64_PEAK_TFLOPS = 1.258  # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25)
+
+
+# ----------------------------------------------------------- flop counts
+def conv_flops_per_cell(N, Q):
+    """FP64 flops (FMA = 2) of the convective kernel per cell, counted from
+    its loops (cell term by z-planes, six faces per cell)."""
+    f = 2 * (3 * Q * N ** 3 + 3 * Q * Q * N * N)                      # interpolation x, y
+    f += Q * (2 * 3 * Q * Q * N + 3 * Q * Q * (8 + 2 * 3 * N)        # plane values, flux + x test
+              + 2 * 9 * N * N * Q + 2 * 6 * N ** 3)                   # y test, z accumulation
+    f += 6 * (2 * 6 * Q * N * N + 2 * 6 * Q * Q * N + 20 * Q * Q     # face traces, LLF flux
+              + 2 * 3 * Q * Q * N + 2 * 3 * Q * N * N + 3 * N * N)    # face tests
+    return f
+
+
+def lap_flops_per_cell(N):
+    """8 sweeps + neighbour terms: N^2 lines x (3 (N^2 + 4N) + 5 N^2) FMA."""
+    return 2 * N * N * (3 * (N * N + 4 * N) + 5 * N * N)
+
+
+# ------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            dev = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0"
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", dev, "--query-gpu=" + q, "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------ GPU arm
+def gpu_arm(args, rank, world):
+    import torch
+
+    from paper_1802_01439_gb300 import Context, inputs
+    import __graft_entry__
+
+    __graft_entry__.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    ctx = Context(N_ELEM, K_U, K_P, nu=NU, mg_precision=0)
+    nu_, np_ = ctx.n_u, ctx.n_p
+    pi = np.pi
+    u_host = inputs.taylor_green((N_ELEM,) * 3, (-pi,) * 3, (pi,) * 3, ctx.nodes_1d(0),
+                                 noise=1e-3, seed=0).ravel()
+    f64 = dict(dtype=torch.float64, device=dev)
+    u = torch.from_numpy(u_host).to(dev)
+    c, uh, g, v = (torch.empty(3 * nu_, **f64) for _ in range(4))
+    d, lp = torch.empty(np_, **f64), torch.empty(np_, **f64)
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
+    dofs_per_step = 12 * nu_ + 2 * np_
+    ev = {k: [torch.cuda.Event(enable_timing=True) for _ in range(2)] for k in
+          ("C", "Minv", "D", "L", "G", "H")}
+    tsum = {k: 0.0 for k in ev}
+
+    def step(timed):
+        ops = [("C", lambda: ctx.vmult_convective(c, u)),
+               ("Minv", lambda: ctx.apply_inverse_mass(uh, c, ncomp=3, space=0)),
+               ("D", lambda: ctx.vmult_divergence(d, uh)),
+               ("L", lambda: ctx.vmult_laplace(lp, d, space=1)),
+               ("G", lambda: ctx.vmult_gradient(g, lp)),
+               ("H", lambda: ctx.vmult_helmholtz(v, uh, MASS_FACTOR))]
+        for name, fn in ops:
+            if timed:
+                ev[name][0].record(stream)
+            fn()
+            if timed:
+                ev[name][1].record(stream)
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = ClockSampler()
+    clocks.start()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step_ms = []
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        s0.record(stream)
+        step(True)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(s0.elapsed_time(s1))
+        for name in ev:
+            tsum[name] += ev[name][0].elapsed_time(ev[name][1])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    barrier(world)
+    clk = clocks.stop()
+    ms = sum(step_ms) / len(step_ms)
+    ms = max_over_ranks(ms, world)
+    value = world * dofs_per_step / (ms * 1e-3)
+
+    # end to end through the public API with host buffers: the input velocity
+    # comes from pinned host memory through the C ABI's staging, the last
+    # result goes back to pinned host memory; copies are inside the timing.
+    u_pin = torch.from_numpy(u_host).pin_memory()
+    v_pin = torch.empty(3 * nu_, dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for it in range(args.warmup + max(3, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.vmult_convective(c, u_pin)
+        ctx.apply_inverse_mass(uh, c, ncomp=3, space=0)
+        ctx.vmult_divergence(d, uh)
+        ctx.vmult_laplace(lp, d, space=1)
+        ctx.vmult_gradient(g, lp)
+        ctx.vmult_helmholtz(v_pin, uh, MASS_FACTOR)
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e = max_over_ranks(sum(e2e_ms) / len(e2e_ms), world)
+
+    # roofline of the dominant kernel (the convective kernel): FP64 ALU bound
+    N, Q = K_U + 1, (3 * (K_U + 1)) // 2
+    conv_ms = tsum["C"] / args.steps
+    conv_flops = conv_flops_per_cell(N, Q) * N_ELEM ** 3
+    achieved = conv_flops / (conv_ms * 1e-3) / 1e12
+    per_op = {k: round(dofs / (tsum[k] / args.steps * 1e-3), 1) for k, dofs in
+              (("C", 3 * nu_), ("Minv", 3 * nu_), ("D", 3 * nu_), ("L", np_), ("G", np_), ("H", 3 * nu_))}
+    share = {k: round(tsum[k] / sum(tsum.values()), 4) for k in tsum}
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "DoFs/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (Taylor-Green + seeded noise)",
+        "config": {"workload": WORKLOAD, "n_elem": N_ELEM, "degree_u": K_U, "degree_p": K_P,
+                   "dofs_per_step": dofs_per_step, "l2": "flushed (256 MiB write) before every step",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "per_operator_dofs_per_s": per_op, "time_share": share,
+        "roofline": {"kernel": "conv_kernel<4,6>", "bound": "alu", "achieved": round(achieved, 4),
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
+                     "traffic": None, "flops_per_launch": conv_flops,
+                     "peak_source": "FP64 ALU: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz"},
+        "e2e": {"value": round(world * dofs_per_step / (e2e * 1e-3), 1), "unit": "DoFs/s",
+                "h2d_bytes_per_step": 3 * nu_ * 8, "d2h_bytes_per_step": 3 * nu_ * 8},
+        "gpu_launches": 6 * args.steps,
+        "timed_block_wall_s": round(wall, 4),
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(sample_n=N_ELEM, repeats=5)
+    ctx.close()
+    if not args.no_solve and rank == 0:
+        line["poisson_solve"] = poisson_solve()
+    return line
+
+
+def poisson_solve():
+    """Pressure Poisson solve of the 64^3, k_p = 3 workload: b = D u_TG (k_u = 4)
+    + 1e-3 noise, Euclidean zero mean; FP64 CG + FP32 V-cycle vs FP64 V-cycle."""
+    import torch
+
+    from paper_1802_01439_gb300 import Context, inputs
+    n, kp = 64, 3
+    pi = np.pi
+    cu = Context(n, kp + 1, kp, mg_precision=0)
+    uh = torch.from_numpy(inputs.taylor_green((n,) * 3, (-pi,) * 3, (pi,) * 3, cu.nodes_1d(0)).ravel()).cuda()
+    b = torch.empty(cu.n_p, dtype=torch.float64, device="cuda")
+    cu.vmult_divergence(b, uh)
+    del uh
+    cu.close()
+    b += 1e-3 * torch.from_numpy(inputs.uniform(1, b.numel())).cuda()
+    b -= b.mean()
+    out = {"workload": "64^3 cells, k_p=3 (16,777,216 DoFs), rel. res. 1e-10, zero initial guess"}
+    for prec in (32, 64):
+        ctx = Context(n, kp + 1, kp, mg_precision=prec)
+        x = torch.zeros(ctx.n_p, dtype=torch.float64, device="cuda")
+        ctx.cg_mg_solve(x, b, rel_tol=1e-10)            # warm-up
+        times = []
+        for _ in range(3):
+            x.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = ctx.cg_mg_solve(x, b, rel_tol=1e-10)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        out["fp%d_vcycle" % prec] = {"seconds": round(min(times), 5), "iterations": info["iterations"],
+                                     "rel_res": info["rel_res"], "levels": ctx.mg_info()["levels"]}
+        ctx.close()
+        del x
+    out["speedup_mixed_vs_fp64"] = round(out["fp64_vcycle"]["seconds"] / out["fp32_vcycle"]["seconds"], 3)
+    return out
+
+
+# ------------------------------------------------------------ CPU oracle
+def oracle_step_runner(n):
+    """The oracle's operators on an n^3 sample of the workload; returns
+    (run_one_step, dofs_per_step)."""
+    from oracle import dg, rules
+    from paper_1802_01439_gb300 import inputs
+    m = dg.Mesh(n)
+    su, sp = dg.Space(m, K_U), dg.Space(m, K_P)
+    C, Mu = dg.Convective(su), dg.Mass(su)
+    D, G = dg.Divergence(su, sp), dg.Gradient(su, sp)
+    L, H = dg.Laplace(sp), dg.Helmholtz(su, NU, MASS_FACTOR)
+    u = inputs.taylor_green(m.n, m.lo, m.hi, rules.lgl_nodes(K_U), noise=1e-3, seed=0)
+
+    def run():
+        c = C.apply(u)
+        uh = Mu.apply_inverse(c)
+        d = D.apply(uh)
+        lp = L.apply(d)
+        G.apply(lp)
+        H.apply(uh)
+
+    return run, 12 * su.size + 2 * sp.size
+
+
+def oracle_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        return max([i.get("num_threads", 1) for i in info] + [1])
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(sample_n=N_ELEM, repeats=5):
+    run, dofs = oracle_step_runner(sample_n)
+    run()
+    t = []
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        run()
+        t.append(time.perf_counter() - t0)
+    return {"value": round(dofs / min(t), 1), "unit": "DoFs/s", "cores": oracle_threads(), "kind": "oracle",
+            "sample": "oracle (numpy/LAPACK FP64, explicit element and face matrices) on %d^3 cells of the "
+                      "same k_u=3/k_p=2 operator set, best of %d steps" % (sample_n, repeats)}
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return None
+    run, dofs = oracle_step_runner(N_ELEM)
+    for _ in range(args.warmup):
+        run()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        run()
+    sec = (time.perf_counter() - t0) / args.steps
+    value = dofs / sec
+    cores = oracle_threads()
+    sample = "oracle (numpy/LAPACK FP64) on the full 32^3, k_u=3/k_p=2 operator set, mean of the timed steps"
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "DoFs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (Taylor-Green + seeded noise)",
+            "config": {"workload": WORKLOAD, "n_elem": N_ELEM, "degree_u": K_U, "degree_p": K_P},
+            "cpu_baseline": {"value": round(value, 1), "unit": "DoFs/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 1), "unit": "DoFs/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+# ------------------------------------------------------------ driver
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="dgns", choices=["dgns", "reference"])
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        line = reference_arm(args, rank, world)
+        if line:
+            print(json.dumps(line), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    line = gpu_arm(args, rank, world)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

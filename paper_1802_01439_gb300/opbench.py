@@ -1,0 +1,118 @@
+"""Per-operator throughput of libdgns on one GPU (DoFs/s vs degree).
+
+    python -m paper_1802_01439_gb300.opbench --op laplace --k 3 --n 64 --reps 20
+    python -m paper_1802_01439_gb300.opbench --sweep      # k = 2..11 at ~16.8M DoFs
+
+Each repetition is timed with CUDA events on the launching stream after an
+L2 flush (256 MiB write).  Inputs: uniform[-1, 1] (seeded) for the linear
+operators, the Taylor-Green field + 1e-3 noise for the convective term.
+Prints one JSON line per (operator, k).  DoFs are those of the input vector.
+"""
+import argparse
+import json
+import os
+import sys
+
+import numpy as np
+import torch
+
+if __package__ in (None, ""):
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+from paper_1802_01439_gb300 import Context, inputs  # noqa: E402
+
+# elements per direction giving ~16.8M scalar DoFs for k = 2..11
+SWEEP_N = {2: 85, 3: 64, 4: 51, 5: 43, 6: 37, 7: 32, 8: 28, 9: 26, 10: 23, 11: 21}
+OPS = ["laplace", "laplace32", "convective", "viscous", "helmholtz", "invmass", "mass",
+       "divergence", "gradient"]
+
+
+def run(op, k, n, reps, warmup, ku=None):
+    dev = torch.device("cuda")
+    # scalar operators act on space U of a context with degree k
+    kk = ku if ku is not None else k
+    kp = max(kk - 1, 1)
+    mg = 32 if op == "laplace32" else 0
+    if op == "laplace32":       # FP32 level operator: pressure space of degree k
+        ctx = Context(n, k, k, mg_precision=32, mg_coarse_n=n)
+    else:
+        ctx = Context(n, kk, kp, mg_precision=mg)
+    nu, np_ = ctx.n_u, ctx.n_p
+    f64 = dict(dtype=torch.float64, device=dev)
+    rng = lambda m, s: torch.from_numpy(inputs.uniform(s, m)).to(dev)
+    if op == "laplace":
+        x, y, dofs = rng(nu, 0), torch.empty(nu, **f64), nu
+        fn = lambda: ctx.vmult_laplace(y, x, space=0)
+        nbytes = 16 * nu
+    elif op == "laplace32":
+        x = rng(np_, 0).float()
+        y, dofs = torch.empty_like(x), np_
+        fn = lambda: ctx.vmult_laplace_f32(y, x, 0)
+        nbytes = 8 * np_
+    elif op == "convective":
+        u = torch.from_numpy(inputs.taylor_green((n,) * 3, (-np.pi,) * 3, (np.pi,) * 3, ctx.nodes_1d(0),
+                                                 noise=1e-3, seed=0).ravel()).to(dev)
+        y, dofs = torch.empty(3 * nu, **f64), 3 * nu
+        fn = lambda: ctx.vmult_convective(y, u)
+        nbytes = 16 * 3 * nu
+    elif op in ("viscous", "helmholtz"):
+        x, y, dofs = rng(3 * nu, 0), torch.empty(3 * nu, **f64), 3 * nu
+        fn = (lambda: ctx.vmult_viscous(y, x)) if op == "viscous" else (lambda: ctx.vmult_helmholtz(y, x, 1500.0))
+        nbytes = 16 * 3 * nu
+    elif op in ("invmass", "mass"):
+        x, y, dofs = rng(3 * nu, 0), torch.empty(3 * nu, **f64), 3 * nu
+        fn = (lambda: ctx.apply_inverse_mass(y, x, 3, 0)) if op == "invmass" else (lambda: ctx.vmult_mass(y, x, 3, 0))
+        nbytes = 16 * 3 * nu
+    elif op == "divergence":
+        x, y, dofs = rng(3 * nu, 0), torch.empty(np_, **f64), 3 * nu
+        fn = lambda: ctx.vmult_divergence(y, x)
+        nbytes = 8 * (3 * nu + np_)
+    elif op == "gradient":
+        x, y, dofs = rng(np_, 0), torch.empty(3 * nu, **f64), np_
+        fn = lambda: ctx.vmult_gradient(y, x)
+        nbytes = 8 * (3 * nu + np_)
+    else:
+        raise ValueError(op)
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = float(np.mean(ts))
+    ctx.close()
+    return {"op": op, "k": k, "n_elem": n, "dofs": dofs, "ms_mean": round(ms, 5),
+            "ms_min": round(float(np.min(ts)), 5), "dofs_per_s": round(dofs / (ms * 1e-3), 1),
+            "algorithmic_GBps": round(nbytes / (ms * 1e-3) / 1e9, 1)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--op", default="laplace", choices=OPS)
+    ap.add_argument("--k", type=int, default=3)
+    ap.add_argument("--n", type=int, default=0)
+    ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--sweep", action="store_true")
+    ap.add_argument("--ops", default="laplace,convective,laplace32,invmass,helmholtz")
+    a = ap.parse_args()
+    if a.sweep:
+        for op in a.ops.split(","):
+            for k, n in SWEEP_N.items():
+                if op == "convective" and k > 9:
+                    n = {10: 20, 11: 18}[k]
+                print(json.dumps(run(op, k, n, a.reps, a.warmup)), flush=True)
+        return
+    n = a.n or SWEEP_N.get(a.k, 32)
+    print(json.dumps(run(a.op, a.k, n, a.reps, a.warmup)), flush=True)
+
+
+if __name__ == "__main__":
+    main()

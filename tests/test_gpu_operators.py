@@ -38,7 +38,7 @@ def _mesh(n, kw):
 
 @pytest.mark.parametrize("n,k,kw", LAP_CASES)
 def test_laplace(n, k, kw):
-    ctx = context(n, k, mg_precision=0, **kw)
+    ctx = context(n, k, k, mg_precision=0, **kw)
     s = dg.Space(_mesh(n, kw), k)
     x = random_field(s, 1, 0)
     ref = dg.Laplace(s, kw.get("penalty_factor", 1.0)).apply(x)
@@ -63,7 +63,7 @@ def test_laplace_pressure_space():
 
 @pytest.mark.parametrize("n,k,kw", LAP_CASES[:6])
 def test_mass_and_inverse(n, k, kw):
-    ctx = context(n, k, mg_precision=0, **kw)
+    ctx = context(n, k, k, mg_precision=0, **kw)
     s = dg.Space(_mesh(n, kw), k)
     M = dg.Mass(s)
     for ncomp in (1, 3):
@@ -109,7 +109,7 @@ def test_divergence_gradient(n, ku):
                                        ((2, 2, 2), 5, "rand"), ((1, 1, 2), 1, "rand"),
                                        ((2, 1, 1), 11, "tgv"), ((2, 3, 2), 7, "tgv")])
 def test_convective(n, k, field):
-    ctx = context(n, k, mg_precision=0)
+    ctx = context(n, k, max(k - 1, 1), mg_precision=0)
     s = dg.Space(dg.Mesh(n), k)
     u = tgv_field(s, 1e-3, 0) if field == "tgv" else random_field(s, 3, 6)
     ref = dg.Convective(s).apply(u)
