@@ -360,7 +360,7 @@ def max_over_ranks(x, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="dgns", choices=["dgns", "reference"])
     ap.add_argument("--no-solve", action="store_true")
