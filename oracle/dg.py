@@ -374,6 +374,51 @@ class Convective:
         return Y
 
 
+    def vjp(self, U, Wt):
+        """Vector-Jacobian product (dC/dU)^T Wt, written out pointwise.
+
+        Cell: with g_cd(q) = sum_i Wt_c,i d_d phi_i(q), the cell part of
+        <Wt, C(U)> is -sum_q W sum_cd g_cd u_c u_d, whose derivative in u_e(q)
+        is -W sum_d (g_ed + g_de) u_d; it is tested with phi_j.
+        Face: <Wt, face part> = sum wf sum_c (Wt^-_c - Wt^+_c) F*_c; the
+        derivative of F* in u^- and u^+ follows from the product rule, with
+        d|s|/ds = sign(s) and d max(a, b) sent to the larger argument (half to
+        each on a tie)."""
+        m = self.space.mesh
+        U = np.asarray(U, dtype=np.float64)
+        Wt = np.asarray(Wt, dtype=np.float64)
+        uq = [U[c] @ self.Phi.T for c in range(3)]
+        g = [[Wt[c] @ self.dPhi[d].T for d in range(3)] for c in range(3)]
+        G = np.zeros_like(U)
+        for e in range(3):
+            ge = -self.W[None, :] * sum((g[e][d] + g[d][e]) * uq[d] for d in range(3))
+            G[e] += ge @ self.Phi
+        em = np.arange(m.E)
+        for axis in range(3):
+            vm, vp, wf = self.face[axis]
+            ep = m.neighbor(axis, +1)
+            um = [U[c][em] @ vm.T for c in range(3)]
+            up = [U[c][ep] @ vp.T for c in range(3)]
+            jw = [Wt[c][em] @ vm.T - Wt[c][ep] @ vp.T for c in range(3)]
+            unm, unp = um[axis], up[axis]
+            am, ap = np.abs(unm), np.abs(unp)
+            lam = np.maximum(am, ap)
+            sm = np.where(am > ap, np.sign(unm), np.where(am == ap, 0.5 * np.sign(unm), 0.0))
+            sp = np.where(ap > am, np.sign(unp), np.where(am == ap, 0.5 * np.sign(unp), 0.0))
+            jw_um = sum(jw[c] * um[c] for c in range(3))
+            jw_up = sum(jw[c] * up[c] for c in range(3))
+            jw_du = sum(jw[c] * (um[c] - up[c]) for c in range(3))
+            for e in range(3):
+                gm = 0.5 * jw[e] * unm + lam * jw[e]
+                gp = 0.5 * jw[e] * unp - lam * jw[e]
+                if e == axis:
+                    gm = gm + 0.5 * jw_um + sm * jw_du
+                    gp = gp + 0.5 * jw_up + sp * jw_du
+                G[e][em] += (gm * wf[None, :]) @ vm
+                G[e][ep] += (gp * wf[None, :]) @ vp
+        return G
+
+
 # ----------------------------------------------------------------------------
 # Diagnostics of Sec. 4.2: kinetic energy and dissipation rate, with the
 # element-wise (broken) gradient and k_u + 1 Gauss points.

@@ -293,3 +293,43 @@ def test_taylor_green_energy_and_dissipation():
     U = np.stack(s.interpolate(dg.taylor_green))
     assert abs(dg.kinetic_energy(s, U) - 0.125) < 1e-4
     assert abs(dg.dissipation_rate(s, U, nu) / nu - 0.75) < 1e-3
+
+
+@pytest.mark.parametrize("n,k,field", [((2, 2, 2), 2, "rand"), ((3, 1, 2), 3, "tgv"), ((1, 2, 1), 4, "rand")])
+def test_convective_vjp_adjoint_identity(n, k, field):
+    """<w, J v> = <J^T w, v>, with J v from central differences of C, which
+    are exact for the quadratic cell term and for the LLF term away from its
+    kinks (a small step crosses none for these seeded fields)."""
+    m = dg.Mesh(n)
+    s = dg.Space(m, k)
+    C = dg.Convective(s)
+    if field == "tgv":
+        U = np.stack(s.interpolate(dg.taylor_green)) + 1e-3 * rand((3, m.E, s.ndofs_cell), 1)
+    else:
+        U = rand((3, m.E, s.ndofs_cell), 2)
+    V = rand(U.shape, 3)
+    Wt = rand(U.shape, 4)
+    # near-zero normal velocities of the Taylor-Green field put LLF kinks close
+    # to the base point: a smaller step keeps the difference quotient exact
+    eps = 1e-8 if field == "tgv" else 1e-6
+    Jv = (C.apply(U + eps * V) - C.apply(U - eps * V)) / (2 * eps)
+    lhs = np.sum(Wt * Jv)
+    rhs = np.sum(C.vjp(U, Wt) * V)
+    assert abs(lhs - rhs) < 1e-8 * np.sum(np.abs(Wt * Jv))
+
+
+def test_convective_vjp_quadratic_exact():
+    """Without kinks (u.n of one sign everywhere and |u-.n| > |u+.n| on all
+    faces is not needed: use a field whose LLF lambda is constant), C is
+    quadratic and C(u+v) - C(u-v) = 2 J(u) v exactly."""
+    m = dg.Mesh((2, 2, 2))
+    s = dg.Space(m, 2)
+    C = dg.Convective(s)
+    # constant (1, 1, 1) plus a tiny perturbation keeps lambda = |u.n| on the
+    # side with the larger value; compare with a large step on the cell term
+    U = np.ones((3, m.E, s.ndofs_cell)) * 3.0 + 0.1 * rand((3, m.E, s.ndofs_cell), 5)
+    V = 0.1 * rand(U.shape, 6)
+    Wt = rand(U.shape, 7)
+    eps = 1e-3
+    Jv = (C.apply(U + eps * V) - C.apply(U - eps * V)) / (2 * eps)
+    assert abs(np.sum(Wt * Jv) - np.sum(C.vjp(U, Wt) * V)) < 1e-10 * np.sum(np.abs(Wt * Jv))
