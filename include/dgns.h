@@ -170,6 +170,27 @@ int dgns_mg_restrict_f32(dgns_ctx* ctx, float* coarse, const float* fine, int le
 int dgns_cg_invmass_solve(dgns_ctx* ctx, double* x3, const double* b3, double mass_factor,
                           const dgns_solve_params* params, dgns_solve_info* info);
 
+/* Allocation-free variant of dgns_cg_invmass_solve (the paper has no
+ * counterpart: this serves callers that cannot allocate device memory, e.g.
+ * code running under CUDA stream capture, applications whose memory belongs
+ * to their own pool, or real-time loops that must not risk allocation
+ * latency or failure).  Same arguments, same arithmetic and the same result.
+ * Differences:
+ *   - x3 and b3 must be device pointers (no host staging);
+ *   - 3 * n_u (the CG vector length) must not exceed 524288, the size of a
+ *     fixed scratch array compiled into the library (four work vectors plus
+ *     reduction partials, ~16 MiB held by every GPU that loads the library
+ *     until the process exits); larger sizes return DGNS_ERR_INVALID_ARG;
+ *   - the call performs no cudaMalloc/cudaFree.  Its first call on a device
+ *     looks up the device address of that array (cudaGetSymbolAddress, once
+ *     per device, under a lock); make that first call before any stream
+ *     capture.
+ * All calls share the one array and it keeps the last call's contents:
+ * calls that may overlap on the GPU (other streams, other host threads,
+ * other contexts) race on it and must be serialised by the caller. */
+int dgns_cg_invmass_solve_noalloc(dgns_ctx* ctx, double* x3, const double* b3, double mass_factor,
+                                  const dgns_solve_params* params, dgns_solve_info* info);
+
 #ifdef __cplusplus
 }
 #endif

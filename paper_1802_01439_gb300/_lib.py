@@ -77,6 +77,8 @@ SIGNATURES = {
     "dgns_mg_restrict_f32": (_I, [_P, _P, _P, _I]),
     "dgns_cg_invmass_solve": (_I, [_P, _P, _P, _D, ctypes.POINTER(SolveParams),
                                    ctypes.POINTER(SolveInfo)]),
+    "dgns_cg_invmass_solve_noalloc": (_I, [_P, _P, _P, _D, ctypes.POINTER(SolveParams),
+                                           ctypes.POINTER(SolveInfo)]),
 }
 
 _lib = None

@@ -9,10 +9,7 @@
 #include <string>
 #include <vector>
 
-#include "dgns.h"
-#include "blas.h"
-#include "ops.h"
-#include "tables.h"
+#include "ctx.h"
 
 using namespace dgns;
 
@@ -46,54 +43,11 @@ int fail(int code, const std::string& msg) {
     }                                                                 \
   } while (0)
 
-struct Level {
-  MeshDims m{};
-  double h[3] = {0, 0, 0};
-  LapHost lap;            // FP64 values; rounded by the launcher
-  void* dinv = nullptr;   // N^3 table in the V-cycle precision
-  double* dinv64 = nullptr;
-  void* xa = nullptr;
-  void* xb = nullptr;
-  void* b = nullptr;
-  void* r = nullptr;
-  long long n = 0;
-  double lambda_max = 0.0;
-};
-
 }  // namespace
 
-struct dgns_ctx {
-  dgns_mesh_desc d{};
-  cudaStream_t s = nullptr;
-  MeshDims m{};
-  double h[3] = {0, 0, 0};
-  int k[2] = {0, 0};  // degree of space U, P
-  int N[2] = {0, 0};
-  long long n[2] = {0, 0};
-  Space1D sp1[2];
-  LapHost lap[2];               // unit-coefficient SIPG tables of U and P
-  std::vector<double> diag[2];  // N^3 diagonal pattern of L
-  double* d_diag[2] = {nullptr, nullptr};
-  double mass3[2][3][MAXN * MAXN];
-  double minv3[2][3][MAXN * MAXN];
-  DivHost div;
-  GradHost grad;
-  ConvHost conv;
-  // multigrid (pressure space)
-  int mg_prec = 0;
-  std::vector<Level> levels;
-  double P0[MAXN * MAXN], P1[MAXN * MAXN];
-  // FP64 CG work vectors and reductions
-  long long cg_cap = 0;
-  double *r = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr;
-  Reducer red;
-  double* h_scal = nullptr;  // pinned mirror of the scalars
-  // staging of host pointers
-  void* stage[4] = {nullptr, nullptr, nullptr, nullptr};
-  size_t stage_cap[4] = {0, 0, 0, 0};
-};
+namespace dgns {
 
-namespace {
+int set_error(int code, const std::string& msg) { return fail(code, msg); }
 
 void build_lap(const Space1D& s, const double h[3], double pf, double coef, double mass_factor,
                LapHost& L) {
@@ -120,6 +74,10 @@ void build_lap(const Space1D& s, const double h[3], double pf, double coef, doub
   }
   for (int i = 0; i < N * N; ++i) L.M[i] = (double)s.mass[i];
 }
+
+}  // namespace dgns
+
+namespace {
 
 // Diagonal pattern (identical for every cell of the uniform mesh), from the
 // same factorisation in long double.
