@@ -120,6 +120,21 @@ int dgns_vmult_convective(dgns_ctx* ctx, double* dst3, const double* u3);
  * derivative of max(a, b) to the larger argument (half to each on a tie). */
 int dgns_vjp_convective(dgns_ctx* ctx, double* grad_u3, const double* u3, const double* w3);
 
+/* Dissipation rate of the resolved scales, eps = nu / |Omega| int grad u : grad u
+ * (Sec. 4.2), with the element-wise (broken) gradient and k_u+1 Gauss points:
+ * *eps_out (host) = eps(u3).  Synchronises the stream. */
+int dgns_dissipation(dgns_ctx* ctx, const double* u3, double* eps_out);
+/* Its gradient: grad3 = d eps / d u3 = (2 nu / |Omega|) K u3 per component,
+ * K the broken stiffness matrix (cell terms of l_h only). */
+int dgns_dissipation_grad(dgns_ctx* ctx, double* grad3, const double* u3);
+
+/* Vector helpers of the time stepper (device pointers, context stream):
+ * y = a x + b y over n entries (b = 0 ignores the prior contents of y; x may
+ * equal y), and *out (host) = (a, b) over n entries
+ * (deterministic fixed-order reduction; synchronises the stream). */
+int dgns_axpby(dgns_ctx* ctx, double* y, const double* x, long long n, double a, double b);
+int dgns_dot(dgns_ctx* ctx, const double* a, const double* b, long long n, double* out);
+
 typedef struct {
   double rel_tol;          /* stop when ||r||_2 <= rel_tol ||b||_2 (default 1e-10) */
   double abs_tol;          /* or ||r||_2 <= abs_tol (default 0)                      */

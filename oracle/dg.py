@@ -438,6 +438,13 @@ def dissipation_rate(space, U, nu):
     return nu * tot / space.mesh.volume
 
 
+def dissipation_gradient(space, U, nu):
+    """d eps / d U = (2 nu / V) K U per component, K the broken stiffness."""
+    _, dPhi, W = _cell_tables(space, space.N)
+    K = sum(dP.T @ (W[:, None] * dP) for dP in dPhi)
+    return 2.0 * nu / space.mesh.volume * np.stack([U[c] @ K.T for c in range(3)])
+
+
 def taylor_green(x, y, z):
     """Taylor-Green initial velocity with U0 = L = 1 (Sec. 4)."""
     return (np.sin(x) * np.cos(y) * np.cos(z),

@@ -1,0 +1,71 @@
+"""BDF2 dual-splitting time step (oracle; test infrastructure).
+
+Sec. 3.1 of the paper (four substeps of the dual splitting scheme with BDF
+order J = 2 and extrapolation of the convective term) in the matrix form of
+Sec. 3.3, with the readings: gamma0 = 3/2, alpha = (2, -1/2), beta = (2, -1)
+(the first step BDF1: gamma0 = alpha0 = beta0 = 1); the projection substep
+without the divergence and continuity penalty terms (plain L2 projection).
+The linear systems are solved exactly with dense factorisations (small
+meshes only): the pressure by the eigen-decomposition pseudo-inverse of the
+singular periodic Laplacian, the Helmholtz problem by a dense Cholesky solve.
+"""
+import numpy as np
+
+from . import dg
+
+
+class DualSplitting:
+    def __init__(self, mesh, ku, nu, dt, penalty_factor=1.0):
+        self.su, self.sp = dg.Space(mesh, ku), dg.Space(mesh, ku - 1)
+        self.C = dg.Convective(self.su)
+        self.M = dg.Mass(self.su)
+        self.D = dg.Divergence(self.su, self.sp)
+        self.G = dg.Gradient(self.su, self.sp)
+        self.nu, self.dt = nu, dt
+        self.pf = penalty_factor
+        L = dg.Laplace(self.sp, penalty_factor).matrix()
+        w, V = np.linalg.eigh(0.5 * (L + L.T))
+        keep = w > 1e-10 * w[-1]
+        self.Lpinv = (V[:, keep] / w[keep]) @ V[:, keep].T
+        self._H = {}
+
+    def helmholtz_solve(self, mf, B):
+        if mf not in self._H:
+            H = dg.Helmholtz(self.su, self.nu, mf, self.pf)
+            n, E = self.su.size, self.su.mesh.E
+            A = np.empty((n, n))
+            for j in range(n):
+                e = np.zeros(n)
+                e[j] = 1.0
+                A[:, j] = H.apply(e.reshape(1, E, -1)).ravel()
+            self._H[mf] = np.linalg.cholesky(0.5 * (A + A.T))
+        Lc = self._H[mf]
+        E = self.su.mesh.E
+        out = []
+        for c in range(3):
+            y = np.linalg.solve(Lc, B[c].ravel())
+            out.append(np.linalg.solve(Lc.T, y).reshape(E, -1))
+        return np.stack(out)
+
+    def step(self, u, u_prev, c_prev, first):
+        dt = self.dt
+        if first:
+            g0, a, b = 1.0, (1.0, 0.0), (1.0, 0.0)
+        else:
+            g0, a, b = 1.5, (2.0, -0.5), (2.0, -1.0)
+        c = self.C.apply(u)
+        cc = b[0] * c + (b[1] * c_prev if not first else 0.0)
+        hist = a[0] * u + (a[1] * u_prev if not first else 0.0)
+        uh = (hist - dt * self.M.apply_inverse(cc)) / g0
+        rhs = -(g0 / dt) * self.D.apply(uh)
+        p = (self.Lpinv @ rhs.ravel()).reshape(rhs.shape)
+        uhh = uh - (dt / g0) * self.M.apply_inverse(self.G.apply(p))
+        u_new = self.helmholtz_solve(g0 / dt, (g0 / dt) * self.M.apply(uhh))
+        return u_new, c
+
+    def run(self, u0, nsteps):
+        u, u_prev, c_prev = u0, u0, u0
+        for n in range(nsteps):
+            u_next, c = self.step(u, u_prev, c_prev, n == 0)
+            u_prev, u, c_prev = u, u_next, c
+        return u

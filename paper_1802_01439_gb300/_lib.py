@@ -69,6 +69,10 @@ SIGNATURES = {
     "dgns_vmult_gradient": (_I, [_P, _P, _P]),
     "dgns_vmult_convective": (_I, [_P, _P, _P]),
     "dgns_vjp_convective": (_I, [_P, _P, _P, _P]),
+    "dgns_dissipation": (_I, [_P, _P, ctypes.POINTER(_D)]),
+    "dgns_dissipation_grad": (_I, [_P, _P, _P]),
+    "dgns_axpby": (_I, [_P, _P, _P, _LL, _D, _D]),
+    "dgns_dot": (_I, [_P, _P, _P, _LL, ctypes.POINTER(_D)]),
     "dgns_default_solve_params": (None, [ctypes.POINTER(SolveParams)]),
     "dgns_cg_mg_solve": (_I, [_P, _P, _P, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo)]),
     "dgns_mg_info": (_I, [_P, ctypes.POINTER(_I), _P, _P]),

@@ -156,6 +156,31 @@ class Context:
                                            self._vec(u3, n, name="u3"), self._vec(w3, n, name="w3")))
         return grad_u3
 
+    def dissipation(self, u3):
+        out = ctypes.c_double()
+        check(self.lib.dgns_dissipation(self.h, self._vec(u3, 3 * self.n_u, name="u3"), ctypes.byref(out)))
+        return out.value
+
+    def dissipation_grad(self, grad3, u3):
+        n = 3 * self.n_u
+        check(self.lib.dgns_dissipation_grad(self.h, self._vec(grad3, n, name="grad3"),
+                                             self._vec(u3, n, name="u3")))
+        return grad3
+
+    def axpby(self, y, x, a, b):
+        """y = a x + b y (device tensors of equal size)."""
+        n = y.numel()
+        check(self.lib.dgns_axpby(self.h, self._vec(y, n, name="y"), self._vec(x, n, name="x"),
+                                  n, float(a), float(b)))
+        return y
+
+    def dot(self, a, b):
+        out = ctypes.c_double()
+        n = a.numel()
+        check(self.lib.dgns_dot(self.h, self._vec(a, n, name="a"), self._vec(b, n, name="b"), n,
+                                ctypes.byref(out)))
+        return out.value
+
     # ------------------------------------------------------------ solvers
     @staticmethod
     def solve_params(**kw):

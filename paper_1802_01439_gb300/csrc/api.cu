@@ -807,7 +807,100 @@ int dgns_vjp_convective(dgns_ctx* c, double* grad_u3, const double* u3, const do
   g_err.clear();
   if (!c) return fail(DGNS_ERR_INVALID_ARG, "ctx is null");
   DG_NONNULL(grad_u3, u3, w3);
-  return fail(DGNS_ERR_UNSUPPORTED, "convective VJP is not built yet");
+  const size_t bu = (size_t)c->n[0] * 3 * sizeof(double);
+  if (overlaps(grad_u3, bu, u3, bu) || overlaps(grad_u3, bu, w3, bu))
+    return fail(DGNS_ERR_ALIAS, "grad_u3 overlaps an input");
+  Staged st(c);
+  const void* su;
+  const void* sw;
+  void* d;
+  DG_TRY(st.in(u3, bu, &su));
+  DG_TRY(st.in(w3, bu, &sw));
+  DG_TRY(st.out(grad_u3, bu, &d));
+  int rc = convective_vjp(c->m, (const double*)su, (const double*)sw, (double*)d, c->conv, c->s);
+  if (rc == 7) return fail(DGNS_ERR_UNSUPPORTED, "convective VJP: supported for k <= 7");
+  DG_TRY(rc);
+  return st.finish();
+}
+
+// Broken stiffness (cell terms of the SIPG form only) scaled by `coef`.
+static void build_broken_stiffness(const dgns_ctx* c, double coef, LapHost& L) {
+  build_lap(c->sp1[0], c->h, c->d.penalty_factor, coef, 0.0, L);
+  const Space1D& s = c->sp1[0];
+  const int N = s.N;
+  for (int d = 0; d < 3; ++d) {
+    ld ht = 1.0L;
+    for (int e = 0; e < 3; ++e)
+      if (e != d) ht *= (ld)c->h[e];
+    for (int i = 0; i < N * N; ++i) L.A0[d][i] = (double)((ld)coef * ht * s.stiff[i] / (ld)c->h[d]);
+    for (int i = 0; i < N; ++i) L.cr[d][i] = L.cl[d][i] = L.gr[d][i] = L.gl[d][i] = 0.0;
+  }
+}
+
+int dgns_dissipation_grad(dgns_ctx* c, double* grad3, const double* u3) {
+  g_err.clear();
+  if (!c) return fail(DGNS_ERR_INVALID_ARG, "ctx is null");
+  DG_NONNULL(grad3, u3);
+  const size_t bu = (size_t)c->n[0] * 3 * sizeof(double);
+  if (overlaps(grad3, bu, u3, bu)) return fail(DGNS_ERR_ALIAS, "grad3 overlaps u3");
+  Staged st(c);
+  const void* s;
+  void* d;
+  DG_TRY(st.in(u3, bu, &s));
+  DG_TRY(st.out(grad3, bu, &d));
+  double vol = 1.0;
+  for (int i = 0; i < 3; ++i) vol *= c->d.hi[i] - c->d.lo[i];
+  LapHost K;
+  build_broken_stiffness(c, 2.0 * c->d.nu / vol, K);
+  DG_TRY(laplace_apply(false, c->m, 3, s, d, K, EPI_NONE, EpiHost(), c->s));
+  return st.finish();
+}
+
+int dgns_dissipation(dgns_ctx* c, const double* u3, double* eps_out) {
+  g_err.clear();
+  if (!c) return fail(DGNS_ERR_INVALID_ARG, "ctx is null");
+  DG_NONNULL(u3, eps_out);
+  const long long n = 3 * c->n[0];
+  DG_TRY(alloc_cg(c, n));
+  Staged st(c);
+  const void* s;
+  DG_TRY(st.in(u3, (size_t)n * sizeof(double), &s));
+  double vol = 1.0;
+  for (int i = 0; i < 3; ++i) vol *= c->d.hi[i] - c->d.lo[i];
+  LapHost K;
+  build_broken_stiffness(c, c->d.nu / vol, K);
+  DG_TRY(laplace_apply(false, c->m, 3, s, c->Ap, K, EPI_NONE, EpiHost(), c->s));
+  DG_TRY(dot((const double*)s, c->Ap, n, c->red, S_T1, c->s));
+  DG_TRY(read_scalars(c));
+  *eps_out = c->h_scal[S_T1];
+  return st.finish();
+}
+
+int dgns_axpby(dgns_ctx* c, double* y, const double* x, long long n, double a, double b) {
+  g_err.clear();
+  if (!c) return fail(DGNS_ERR_INVALID_ARG, "ctx is null");
+  DG_NONNULL(y, x);
+  if (n < 0) return fail(DGNS_ERR_INVALID_ARG, "n < 0");
+  if (!is_device_ptr(y) || !is_device_ptr(x)) return fail(DGNS_ERR_INVALID_ARG, "device pointers only");
+  if (n == 0) return 0;
+  DG_TRY(axpby(y, x, n, a, b, c->s));
+  return 0;
+}
+
+int dgns_dot(dgns_ctx* c, const double* a, const double* b, long long n, double* out) {
+  g_err.clear();
+  if (!c) return fail(DGNS_ERR_INVALID_ARG, "ctx is null");
+  DG_NONNULL(a, b, out);
+  if (n < 0) return fail(DGNS_ERR_INVALID_ARG, "n < 0");
+  if (!is_device_ptr(a) || !is_device_ptr(b)) return fail(DGNS_ERR_INVALID_ARG, "device pointers only");
+  if (n == 0) {
+    *out = 0.0;
+    return 0;
+  }
+  DG_TRY(dot(a, b, n, c->red, S_T1, c->s));
+  DG_TRY(read_scalars(c));
+  *out = c->h_scal[S_T1];
+  return 0;
 }
 
 int dgns_mg_info(const dgns_ctx* c, int* n_levels, int* n_elem_per_level, double* lambda_max) {

@@ -114,11 +114,12 @@ __global__ void __launch_bounds__(RT) cheb_first_kernel(const T* __restrict__ b,
     x[i] = c * dinv[i % nper] * b[i];
 }
 
-__global__ void __launch_bounds__(RT) axpby_kernel(double* __restrict__ y, const double* __restrict__ x,
+// x may alias y (element-wise, each entry read before it is written)
+__global__ void __launch_bounds__(RT) axpby_kernel(double* y, const double* x,
                                                    long long n, double a, double b) {
   const long long stride = (long long)gridDim.x * RT;
   for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < n; i += stride)
-    y[i] = fma(a, x[i], b * y[i]);
+    y[i] = b == 0.0 ? a * x[i] : fma(a, x[i], b * y[i]);  // b = 0 ignores y's contents
 }
 
 inline unsigned grid_for(long long n) {

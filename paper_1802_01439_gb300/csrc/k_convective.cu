@@ -349,6 +349,382 @@ int launch_conv(const MeshDims& m, const double* u3, double* dst3, const ConvHos
   return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }
 
+
+// ------------------------------------------------------------------- VJP
+// grad_u = (dC/du)^T w.  Cell: with g_cd(q) = sum_i w_c,i d_d phi_i(q), the
+// cell part of <w, C(u)> is -sum_q W sum_cd g_cd u_c u_d, whose derivative
+// in u_e(q) is -W sum_d (g_ed + g_de) u_d, tested with phi.  Faces: the
+// product rule on the LLF flux, d|s| = sign(s) (sign(0) = 0), d max sent to
+// the larger argument (half to each on a tie).
+template <int N, int Q>
+struct VjpLayout {
+  static constexpr int N3 = N * N * N;
+  static constexpr int UW = 6 * N3;              // u and w, nodal
+  static constexpr int L1 = 9 * Q * N * N;       // x-sweeps (u: S; w: S, D); later: result
+  static constexpr int L2 = 12 * Q * Q * N;      // xy-sweeps (u: SS; w: DS, SD, SS); later: faces
+  static constexpr int FACE = 12 * Q * N + 12 * Q * Q + 3 * Q * Q;
+  static constexpr int L2F = L2 > FACE ? L2 : FACE;
+  static constexpr int P = 12 * Q * Q;           // plane: u (3) and g (9)
+  static constexpr int X = 3 * N * Q;
+  static constexpr int Y = 3 * N * N;
+  static constexpr int PER = UW + L1 + L2F + P + X + Y;
+};
+
+template <int N, int Q>
+__global__ void __launch_bounds__(conv_cells_per_block<N>() * N * N)
+    conv_vjp_kernel(const double* __restrict__ u3, const double* __restrict__ w3, double* __restrict__ dst3,
+                    const __grid_constant__ ConvTab<N, Q> tb, const MeshDims m) {
+  typedef VjpLayout<N, Q> LY;
+  constexpr int NT = N * N, N3 = N * N * N, EPB = conv_cells_per_block<N>();
+  constexpr int QNN = Q * N * N, QQN = Q * Q * N, QQ = Q * Q;
+  double* sm = reinterpret_cast<double*>(dyn_smem());
+  const int slot = threadIdx.x / NT;
+  const int t = threadIdx.x - slot * NT;
+  const long long c0 = (long long)blockIdx.x * EPB;
+  const long long rem = m.E - c0;
+  const int nvalid = rem < EPB ? (int)rem : EPB;
+  const bool active = slot < nvalid;
+  double* sUW = sm + slot * LY::PER;   // u: [0, 3N3), w: [3N3, 6N3)
+  double* sL1 = sUW + LY::UW;          // u_S (3), w_S (3), w_D (3) : each Q N N
+  double* sL2 = sL1 + LY::L1;          // u_SS (3), w_DS (3), w_SD (3), w_SS (3) : each Q Q N
+  double* sP = sL2 + LY::L2F;          // u (3 Q Q), g (9 Q Q)
+  double* sX = sP + LY::P;
+  double* sY = sX + LY::X;
+  double* sOut = sL1;
+  double* sFace = sL2;
+
+  long long el = 0;
+  int ex = 0, ey = 0, ez = 0;
+  if (active) {
+    el = c0 + slot;
+    ex = (int)(el % m.nx);
+    const long long tt = el / m.nx;
+    ey = (int)(tt % m.ny);
+    ez = (int)(tt / m.ny);
+    for (int c = 0; c < 3; ++c)
+      for (int i = t; i < N3; i += NT) {
+        sUW[c * N3 + i] = u3[(c * m.E + el) * N3 + i];
+        sUW[(3 + c) * N3 + i] = w3[(c * m.E + el) * N3 + i];
+      }
+  }
+  __syncthreads();
+  // x-sweeps: u_S, w_S, w_D
+  if (active)
+    for (int it = t; it < 6 * N * N; it += NT) {
+      const int f = it / (N * N), l = it - f * N * N;   // f < 3: u_c, else w_(f-3)
+      double x[N];
+      load_line<double, N>(sUW + f * N3, l * N, 1, x);
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        double a = tb.S[q * N] * x[0], b = tb.D[q * N] * x[0];
+#pragma unroll
+        for (int j = 1; j < N; ++j) {
+          a = fma(tb.S[q * N + j], x[j], a);
+          b = fma(tb.D[q * N + j], x[j], b);
+        }
+        sL1[f * QNN + l * Q + q] = a;                     // u_S (f<3) or w_S (f>=3)
+        if (f >= 3) sL1[(f + 3) * QNN + l * Q + q] = b;    // w_D
+      }
+    }
+  __syncthreads();
+  // y-sweeps: u_SS, w_DS (from w_D), w_SD and w_SS (from w_S)
+  if (active)
+    for (int it = t; it < 6 * Q * N; it += NT) {
+      const int f = it / (Q * N), l = it - f * Q * N;
+      const int qx = l % Q, z = l / Q;
+      double x[N];
+      if (f < 3) {
+        load_line<double, N>(sL1 + f * QNN, qx + Q * N * z, Q, x);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          double a = tb.S[q * N] * x[0];
+#pragma unroll
+          for (int j = 1; j < N; ++j) a = fma(tb.S[q * N + j], x[j], a);
+          sL2[f * QQN + qx + Q * q + QQ * z] = a;
+        }
+      } else {
+        const int c = f - 3;
+        double y[N];
+        load_line<double, N>(sL1 + (3 + c) * QNN, qx + Q * N * z, Q, x);   // w_S
+        load_line<double, N>(sL1 + (6 + c) * QNN, qx + Q * N * z, Q, y);   // w_D
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          double ds = tb.S[q * N] * y[0], sd = tb.D[q * N] * x[0], ss = tb.S[q * N] * x[0];
+#pragma unroll
+          for (int j = 1; j < N; ++j) {
+            ds = fma(tb.S[q * N + j], y[j], ds);
+            sd = fma(tb.D[q * N + j], x[j], sd);
+            ss = fma(tb.S[q * N + j], x[j], ss);
+          }
+          sL2[(3 + c) * QQN + qx + Q * q + QQ * z] = ds;
+          sL2[(6 + c) * QQN + qx + Q * q + QQ * z] = sd;
+          sL2[(9 + c) * QQN + qx + Q * q + QQ * z] = ss;
+        }
+      }
+    }
+  __syncthreads();
+
+  double acc[3][N];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int z = 0; z < N; ++z) acc[c][z] = 0.0;
+  const int tx = t % N, ty = t / N;
+  for (int qz = 0; qz < Q; ++qz) {
+    // P1: u (3) and g_cd (9) on the plane; g_cx from w_DS, g_cy from w_SD
+    // (both S in z), g_cz from w_SS (D in z)
+    if (active)
+      for (int it = t; it < 12 * QQ; it += NT) {
+        const int f = it / QQ, l = it - f * QQ;
+        const double* src;
+        bool dz = false;
+        if (f < 3) {
+          src = sL2 + f * QQN;
+        } else {
+          const int c = (f - 3) / 3, d = (f - 3) % 3;
+          src = sL2 + (d == 0 ? 3 + c : (d == 1 ? 6 + c : 9 + c)) * QQN;
+          dz = d == 2;
+        }
+        src += l;
+        double a = 0.0;
+        if (dz) {
+#pragma unroll
+          for (int z = 0; z < N; ++z) a = fma(tb.D[qz * N + z], src[QQ * z], a);
+        } else {
+#pragma unroll
+          for (int z = 0; z < N; ++z) a = fma(tb.S[qz * N + z], src[QQ * z], a);
+        }
+        sP[it] = a;
+      }
+    __syncthreads();
+    // P2: pointwise -W sum_d (g_ed + g_de) u_d, with reference derivatives
+    // scaled by jac[d] = h_x h_y h_z / h_d; result overwrites u on the plane
+    if (active)
+      for (int it = t; it < QQ; it += NT) {
+        const int qx = it % Q, qy = it / Q;
+        const double w3q = tb.w[qx] * tb.w[qy] * tb.w[qz];
+        double u[3], g[3][3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) u[c] = sP[c * QQ + it];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) g[c][d] = tb.jac[d] * sP[(3 + 3 * c + d) * QQ + it];
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+          double a = 0.0;
+#pragma unroll
+          for (int d = 0; d < 3; ++d) a = fma(g[e][d] + g[d][e], u[d], a);
+          sP[e * QQ + it] = -w3q * a;
+        }
+      }
+    __syncthreads();
+    // P3: x test
+    if (active)
+      for (int it = t; it < 3 * Q; it += NT) {
+        const int c = it / Q, qy = it - c * Q;
+        double a[N];
+#pragma unroll
+        for (int x = 0; x < N; ++x) a[x] = 0.0;
+#pragma unroll
+        for (int qx = 0; qx < Q; ++qx) {
+          const double gv = sP[c * QQ + qx + Q * qy];
+#pragma unroll
+          for (int x = 0; x < N; ++x) a[x] = fma(tb.S[qx * N + x], gv, a[x]);
+        }
+#pragma unroll
+        for (int x = 0; x < N; ++x) sX[c * N * Q + x + N * qy] = a[x];
+      }
+    __syncthreads();
+    // P4: y test
+    if (active)
+      for (int it = t; it < 3 * N; it += NT) {
+        const int c = it / N, x = it - c * N;
+        double a[N];
+#pragma unroll
+        for (int y = 0; y < N; ++y) a[y] = 0.0;
+#pragma unroll
+        for (int qy = 0; qy < Q; ++qy) {
+          const double b = sX[c * N * Q + x + N * qy];
+#pragma unroll
+          for (int y = 0; y < N; ++y) a[y] = fma(tb.S[qy * N + y], b, a[y]);
+        }
+#pragma unroll
+        for (int y = 0; y < N; ++y) sY[c * N * N + x + N * y] = a[y];
+      }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double yv = sY[c * N * N + tx + N * ty];
+#pragma unroll
+        for (int z = 0; z < N; ++z) acc[c][z] = fma(tb.S[qz * N + z], yv, acc[c][z]);
+      }
+    }
+  }
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int z = 0; z < N; ++z) sOut[c * N3 + tx + N * ty + N * N * z] = acc[c][z];
+  }
+  __syncthreads();
+
+  // ---------------------------------------------------------------- faces
+  // traces: index f = (side s, field v, comp c) -> s*6 + v*3 + c, v: 0 = u, 1 = w
+  double* G1 = sFace;                 // [f][q1 + Q j2]   12 Q N
+  double* G2 = G1 + 12 * Q * N;       // [f][q1 + Q q2]   12 Q Q
+  double* H = G2 + 12 * QQ;           // [c][q1 + Q q2]   3 Q Q
+  double* K1 = G1;
+  for (int d = 0; d < 3; ++d) {
+    const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+    for (int side = 1; side >= -1; side -= 2) {
+      long long nb = 0;
+      if (active) {
+        if (d == 0) nb = neighbor<0>(el, ex, ey, ez, side, m);
+        else if (d == 1) nb = neighbor<1>(el, ex, ey, ez, side, m);
+        else nb = neighbor<2>(el, ex, ey, ez, side, m);
+      }
+      const int aown = side > 0 ? N - 1 : 0, anb = side > 0 ? 0 : N - 1;
+      if (active)
+        for (int it = t; it < 12 * N; it += NT) {
+          const int f = it / N, j2 = it - f * N;
+          const int s = f / 6, v = (f / 3) % 2, c = f % 3;
+          const double* gsrc = v == 0 ? u3 : w3;
+          double val[N];
+#pragma unroll
+          for (int j1 = 0; j1 < N; ++j1)
+            val[j1] = s == 0 ? sUW[(v * 3 + c) * N3 + node3(N, d, aown, t1, j1, t2, j2)]
+                             : __ldg(gsrc + (c * m.E + nb) * N3 + node3(N, d, anb, t1, j1, t2, j2));
+#pragma unroll
+          for (int q1 = 0; q1 < Q; ++q1) {
+            double a = tb.S[q1 * N] * val[0];
+#pragma unroll
+            for (int j = 1; j < N; ++j) a = fma(tb.S[q1 * N + j], val[j], a);
+            G1[f * Q * N + q1 + Q * j2] = a;
+          }
+        }
+      __syncthreads();
+      if (active)
+        for (int it = t; it < 12 * Q; it += NT) {
+          const int f = it / Q, q1 = it - f * Q;
+          double val[N];
+#pragma unroll
+          for (int j2 = 0; j2 < N; ++j2) val[j2] = G1[f * Q * N + q1 + Q * j2];
+#pragma unroll
+          for (int q2 = 0; q2 < Q; ++q2) {
+            double a = tb.S[q2 * N] * val[0];
+#pragma unroll
+            for (int j = 1; j < N; ++j) a = fma(tb.S[q2 * N + j], val[j], a);
+            G2[f * QQ + q1 + Q * q2] = a;
+          }
+        }
+      __syncthreads();
+      if (active)
+        for (int it = t; it < QQ; it += NT) {
+          const int q1 = it % Q, q2 = it / Q;
+          const int sm_ = side > 0 ? 0 : 1, sp_ = side > 0 ? 1 : 0;  // trace side of '-' / '+'
+          double um[3], up[3], jw[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            um[c] = G2[(sm_ * 6 + c) * QQ + it];
+            up[c] = G2[(sp_ * 6 + c) * QQ + it];
+            jw[c] = G2[(sm_ * 6 + 3 + c) * QQ + it] - G2[(sp_ * 6 + 3 + c) * QQ + it];
+          }
+          const double unm = um[d], unp = up[d];
+          const double am = fabs(unm), ap = fabs(unp);
+          const double lam = fmax(am, ap);
+          const double sgm = unm > 0.0 ? 1.0 : (unm < 0.0 ? -1.0 : 0.0);
+          const double sgp = unp > 0.0 ? 1.0 : (unp < 0.0 ? -1.0 : 0.0);
+          const double smx = am > ap ? sgm : (am == ap ? 0.5 * sgm : 0.0);
+          const double spx = ap > am ? sgp : (am == ap ? 0.5 * sgp : 0.0);
+          double jum = 0.0, jup = 0.0, jdu = 0.0;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            jum = fma(jw[c], um[c], jum);
+            jup = fma(jw[c], up[c], jup);
+            jdu = fma(jw[c], um[c] - up[c], jdu);
+          }
+          const double wgt = tb.w[q1] * tb.w[q2] * tb.area[d];
+#pragma unroll
+          for (int e = 0; e < 3; ++e) {
+            double g;
+            if (side > 0) {
+              g = (0.5 * unm + lam) * jw[e];
+              if (e == d) g += 0.5 * jum + smx * jdu;
+            } else {
+              g = (0.5 * unp - lam) * jw[e];
+              if (e == d) g += 0.5 * jup + spx * jdu;
+            }
+            H[e * QQ + it] = wgt * g;
+          }
+        }
+      __syncthreads();
+      if (active)
+        for (int it = t; it < 3 * Q; it += NT) {
+          const int c = it / Q, q1 = it - c * Q;
+          double a[N];
+#pragma unroll
+          for (int j = 0; j < N; ++j) a[j] = 0.0;
+#pragma unroll
+          for (int q2 = 0; q2 < Q; ++q2) {
+            const double h = H[c * QQ + q1 + Q * q2];
+#pragma unroll
+            for (int j = 0; j < N; ++j) a[j] = fma(tb.S[q2 * N + j], h, a[j]);
+          }
+#pragma unroll
+          for (int j2 = 0; j2 < N; ++j2) K1[c * Q * N + q1 + Q * j2] = a[j2];
+        }
+      __syncthreads();
+      if (active)
+        for (int it = t; it < 3 * N; it += NT) {
+          const int c = it / N, j2 = it - c * N;
+          double a[N];
+#pragma unroll
+          for (int j = 0; j < N; ++j) a[j] = 0.0;
+#pragma unroll
+          for (int q1 = 0; q1 < Q; ++q1) {
+            const double h = K1[c * Q * N + q1 + Q * j2];
+#pragma unroll
+            for (int j = 0; j < N; ++j) a[j] = fma(tb.S[q1 * N + j], h, a[j]);
+          }
+#pragma unroll
+          for (int j1 = 0; j1 < N; ++j1) sOut[c * N3 + node3(N, d, aown, t1, j1, t2, j2)] += a[j1];
+        }
+      __syncthreads();
+    }
+  }
+  if (active)
+    for (int c = 0; c < 3; ++c)
+      for (int i = t; i < N3; i += NT) dst3[(c * m.E + el) * N3 + i] = sOut[c * N3 + i];
+}
+
+template <int N, int Q>
+int launch_conv_vjp(const MeshDims& m, const double* u3, const double* w3, double* dst3, const ConvHost& h,
+                    cudaStream_t s) {
+  ConvTab<N, Q> tb;
+  for (int i = 0; i < Q * N; ++i) {
+    tb.S[i] = h.S[i];
+    tb.D[i] = h.D[i];
+  }
+  for (int q = 0; q < Q; ++q) tb.w[q] = h.w[q];
+  for (int d = 0; d < 3; ++d) {
+    tb.jac[d] = h.h[0] * h.h[1] * h.h[2] / h.h[d];
+    tb.area[d] = tb.jac[d];
+  }
+  constexpr int EPB = conv_cells_per_block<N>();
+  const size_t smem = (size_t)EPB * VjpLayout<N, Q>::PER * sizeof(double);
+  if (smem > 232448) return 7;
+  if (cudaFuncSetAttribute(conv_vjp_kernel<N, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return 2;
+  if (m.E == 0) return 0;
+  const long long blocks = (m.E + EPB - 1) / EPB;
+  conv_vjp_kernel<N, Q><<<(unsigned)blocks, EPB * N * N, smem, s>>>(u3, w3, dst3, tb, m);
+  return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
+
 }  // namespace
 
 // Supported: Q = floor(3N/2) (the 3/2 rule) and Q = N.
@@ -370,6 +746,25 @@ int convective_apply(const MeshDims& m, const double* u3, double* dst3, const Co
   DGNS_CONV(11)
   DGNS_CONV(12)
 #undef DGNS_CONV
+  return 7;
+}
+
+// The VJP kernel keeps u, w and their partial sweeps in shared memory:
+// k <= 7 (N <= 8).
+int convective_vjp(const MeshDims& m, const double* u3, const double* w3, double* dst3, const ConvHost& t,
+                   cudaStream_t s) {
+  const int N = t.N, Q = t.Q;
+#define DGNS_CONV_VJP(NV)                                                                          \
+  if (N == NV && Q == (3 * NV) / 2) return launch_conv_vjp<NV, (3 * NV) / 2>(m, u3, w3, dst3, t, s); \
+  if (N == NV && Q == NV) return launch_conv_vjp<NV, NV>(m, u3, w3, dst3, t, s);
+  DGNS_CONV_VJP(2)
+  DGNS_CONV_VJP(3)
+  DGNS_CONV_VJP(4)
+  DGNS_CONV_VJP(5)
+  DGNS_CONV_VJP(6)
+  DGNS_CONV_VJP(7)
+  DGNS_CONV_VJP(8)
+#undef DGNS_CONV_VJP
   return 7;
 }
 

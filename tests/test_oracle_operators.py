@@ -333,3 +333,16 @@ def test_convective_vjp_quadratic_exact():
     eps = 1e-3
     Jv = (C.apply(U + eps * V) - C.apply(U - eps * V)) / (2 * eps)
     assert abs(np.sum(Wt * Jv) - np.sum(C.vjp(U, Wt) * V)) < 1e-10 * np.sum(np.abs(Wt * Jv))
+
+
+def test_dissipation_gradient_matches_difference_quotient():
+    nu = 1.0 / 1600
+    m = dg.Mesh((2, 3, 2))
+    s = dg.Space(m, 3)
+    U = rand((3, m.E, s.ndofs_cell), 8)
+    V = rand(U.shape, 9)
+    eps = 1e-3   # the functional is quadratic: the central difference is exact
+    fd = (dg.dissipation_rate(s, U + eps * V, nu) - dg.dissipation_rate(s, U - eps * V, nu)) / (2 * eps)
+    g = dg.dissipation_gradient(s, U, nu)
+    assert abs(np.sum(g * V) - fd) < 1e-12 * abs(fd)
+    assert abs(0.5 * np.sum(g * U) - dg.dissipation_rate(s, U, nu)) < 1e-13 * dg.dissipation_rate(s, U, nu)
