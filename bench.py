@@ -43,6 +43,11 @@ WORKLOAD = ("full FP64 operator set (C, M^-1, D, L, G, mM+V) on 32^3 hex cells, 
             "q_conv=6, Taylor-Green + 1e-3 noise, periodic [-pi,pi]^3")
 METRIC = "DG operator eval DoFs/s (FP64)"
 FP64_PEAK_TFLOPS = 1.258  # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25)
+FP32_PEAK_TFLOPS = 80.6   # 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz (probe: 73.3)
+# FP32 flops the double-float emulation spends per FP64 flop of the algorithm:
+# an emulated FMA (2 FP64 flops) is an exact product (FMUL + 3 FFMA) plus a
+# two-sum and two adds (8 FADD) = 15 FP32 flops.
+DF_FP32_PER_FP64 = 7.5
 
 
 # ----------------------------------------------------------- flop counts
@@ -122,7 +127,7 @@ def gpu_arm(args, rank, world):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
-    ctx = Context(N_ELEM, K_U, K_P, nu=NU, mg_precision=0)
+    ctx = Context(N_ELEM, K_U, K_P, nu=NU, mg_precision=0, fp64_mode=args.fp64_mode)
     nu_, np_ = ctx.n_u, ctx.n_p
     pi = np.pi
     u_host = inputs.taylor_green((N_ELEM,) * 3, (-pi,) * 3, (pi,) * 3, ctx.nodes_1d(0),
@@ -198,39 +203,88 @@ def gpu_arm(args, rank, world):
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e = max_over_ranks(sum(e2e_ms) / len(e2e_ms), world)
 
-    # roofline of the dominant kernel (the convective kernel): FP64 ALU bound
+    # roofline of the dominant kernel (the convective kernel): ALU bound, on
+    # the FP64 pipe (native) or on the FP32 pipe (double-float)
     N, Q = K_U + 1, (3 * (K_U + 1)) // 2
     conv_ms = tsum["C"] / args.steps
     conv_flops = conv_flops_per_cell(N, Q) * N_ELEM ** 3
-    achieved = conv_flops / (conv_ms * 1e-3) / 1e12
+    if args.fp64_mode == 1:
+        kname = "conv_kernel<DF64,4,6>"
+        achieved = DF_FP32_PER_FP64 * conv_flops / (conv_ms * 1e-3) / 1e12
+        peak, psrc = FP32_PEAK_TFLOPS, ("FP32 ALU: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz; achieved counts "
+                                        "7.5 FP32 flops of the double-float emulation per FP64 flop")
+        fl = DF_FP32_PER_FP64 * conv_flops
+    else:
+        kname = "conv_kernel<F64,4,6>"
+        achieved = conv_flops / (conv_ms * 1e-3) / 1e12
+        peak, psrc = FP64_PEAK_TFLOPS, "FP64 ALU: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz"
+        fl = conv_flops
     per_op = {k: round(dofs / (tsum[k] / args.steps * 1e-3), 1) for k, dofs in
               (("C", 3 * nu_), ("Minv", 3 * nu_), ("D", 3 * nu_), ("L", np_), ("G", np_), ("H", 3 * nu_))}
     share = {k: round(tsum[k] / sum(tsum.values()), 4) for k in tsum}
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "DoFs/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.fp64_mode == 0 else "f64 via double-float (2 x f32, 48-bit significand; "
+                 "parity <= 1e-12 with the FP64 oracle) in the convective and SIPG kernels, native f64 elsewhere",
         "data": "synthetic (Taylor-Green + seeded noise)",
         "config": {"workload": WORKLOAD, "n_elem": N_ELEM, "degree_u": K_U, "degree_p": K_P,
                    "dofs_per_step": dofs_per_step, "l2": "flushed (256 MiB write) before every step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "per_operator_dofs_per_s": per_op, "time_share": share,
-        "roofline": {"kernel": "conv_kernel<4,6>", "bound": "alu", "achieved": round(achieved, 4),
-                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
-                     "traffic": None, "flops_per_launch": conv_flops,
-                     "peak_source": "FP64 ALU: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz"},
+        "roofline": {"kernel": kname, "bound": "alu", "achieved": round(achieved, 4),
+                     "peak": peak, "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                     "traffic": None, "flops_per_launch": fl, "peak_source": psrc},
         "e2e": {"value": round(world * dofs_per_step / (e2e * 1e-3), 1), "unit": "DoFs/s",
                 "h2d_bytes_per_step": 3 * nu_ * 8, "d2h_bytes_per_step": 3 * nu_ * 8},
         "gpu_launches": 6 * args.steps,
         "timed_block_wall_s": round(wall, 4),
         "clocks": clk,
     }
+    ctx.close()
+    if args.fp64_mode == 1:
+        line["native_fp64"] = native_fp64_step(u, min(args.steps, 20), flush)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sample_n=N_ELEM, repeats=5)
-    ctx.close()
     if not args.no_solve and rank == 0:
         line["poisson_solve"] = poisson_solve()
     return line
+
+
+def native_fp64_step(u, steps, flush):
+    """The same operator-set step with native FP64 kernels everywhere."""
+    import torch
+
+    from paper_1802_01439_gb300 import Context
+    ctx = Context(N_ELEM, K_U, K_P, nu=NU, mg_precision=0, fp64_mode=0)
+    nu_, np_ = ctx.n_u, ctx.n_p
+    f64 = dict(dtype=torch.float64, device=u.device)
+    c, uh, g, v = (torch.empty(3 * nu_, **f64) for _ in range(4))
+    d, lp = torch.empty(np_, **f64), torch.empty(np_, **f64)
+
+    def step():
+        ctx.vmult_convective(c, u)
+        ctx.apply_inverse_mass(uh, c, ncomp=3, space=0)
+        ctx.vmult_divergence(d, uh)
+        ctx.vmult_laplace(lp, d, space=1)
+        ctx.vmult_gradient(g, lp)
+        ctx.vmult_helmholtz(v, uh, MASS_FACTOR)
+
+    for _ in range(3):
+        step()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        e0.record()
+        step()
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    ctx.close()
+    t = sum(ms) / len(ms)
+    return {"value": round((12 * nu_ + 2 * np_) / (t * 1e-3), 1), "ms_per_step": round(t, 4), "steps": steps}
 
 
 def poisson_solve():
@@ -331,7 +385,8 @@ def reference_arm(args, rank, world):
     sample = "oracle (numpy/LAPACK FP64) on the full 32^3, k_u=3/k_p=2 operator set, mean of the timed steps"
     return {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "DoFs/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec * 1e3, 3),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64",
             "data": "synthetic (Taylor-Green + seeded noise)",
             "config": {"workload": WORKLOAD, "n_elem": N_ELEM, "degree_u": K_U, "degree_p": K_P},
             "cpu_baseline": {"value": round(value, 1), "unit": "DoFs/s", "cores": cores, "kind": "oracle",
@@ -365,6 +420,8 @@ def main():
     ap.add_argument("--impl", default="dgns", choices=["dgns", "reference"])
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-mode", type=int, default=1,
+                    help="1: double-float convective/SIPG kernels (default); 0: native FP64 everywhere")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -59,6 +59,11 @@ typedef struct {
   double nu;             /* kinematic viscosity of the viscous operator           */
   int mg_coarse_n;       /* coarsest multigrid mesh (elements per direction)      */
   int mg_precision;      /* 32 or 64: arithmetic of the V-cycle; 0 = no multigrid */
+  int fp64_mode;         /* arithmetic of the FP64 convective and SIPG-type         */
+                         /* (Laplace, viscous, Helmholtz, the CG matvecs) kernels:  */
+                         /* 0 native FP64; 1 double-float (pairs of FP32 with a     */
+                         /* 48-bit significand on the FP32 pipe, which GB300 runs  */
+                         /* 61x faster; parity with FP64 to 1e-12 relative)        */
 } dgns_mesh_desc;
 
 /* Defaults: 4^3 elements on [-pi,pi]^3, k_u = 3, k_p = k_u - 1, 3/2 rule,

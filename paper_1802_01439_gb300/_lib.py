@@ -27,7 +27,8 @@ class MeshDesc(ctypes.Structure):
                 ("hi", ctypes.c_double * 3), ("degree", ctypes.c_int),
                 ("degree_p", ctypes.c_int), ("n_q_conv", ctypes.c_int),
                 ("penalty_factor", ctypes.c_double), ("nu", ctypes.c_double),
-                ("mg_coarse_n", ctypes.c_int), ("mg_precision", ctypes.c_int)]
+                ("mg_coarse_n", ctypes.c_int), ("mg_precision", ctypes.c_int),
+                ("fp64_mode", ctypes.c_int)]
 
 
 class SolveParams(ctypes.Structure):

@@ -25,7 +25,7 @@ class Context:
 
     def __init__(self, n_elem, degree, degree_p=-1, lo=(-torch.pi,) * 3, hi=(torch.pi,) * 3,
                  n_q_conv=0, penalty_factor=1.0, nu=1.0 / 1600, mg_coarse_n=2, mg_precision=32,
-                 stream=None):
+                 fp64_mode=0, stream=None):
         self.lib = _lib.load()
         if isinstance(n_elem, int):
             n_elem = (n_elem,) * 3
@@ -42,6 +42,7 @@ class Context:
         d.nu = float(nu)
         d.mg_coarse_n = int(mg_coarse_n)
         d.mg_precision = int(mg_precision)
+        d.fp64_mode = int(fp64_mode)
         self.desc = d
         if stream is None and torch.cuda.is_available():
             stream = torch.cuda.current_stream()

@@ -541,6 +541,7 @@ int dgns_create(const dgns_mesh_desc* desc, void* stream, dgns_ctx** out) {
   }
   if (d.mg_precision != 0 && d.mg_precision != 32 && d.mg_precision != 64)
     return fail(DGNS_ERR_INVALID_ARG, "mg_precision must be 0, 32 or 64");
+  if (d.fp64_mode != 0 && d.fp64_mode != 1) return fail(DGNS_ERR_INVALID_ARG, "fp64_mode must be 0 or 1");
   const int Q = d.n_q_conv > 0 ? d.n_q_conv : (3 * (d.degree + 1)) / 2;
   if (Q != (3 * (d.degree + 1)) / 2 && Q != d.degree + 1)
     return fail(DGNS_ERR_UNSUPPORTED, "n_q_conv must be floor(3(k+1)/2) or k+1");
@@ -678,7 +679,7 @@ static int lap_like(dgns_ctx* c, double* dst, const double* src, int space, int 
     build_lap(c->sp1[space], h, c->d.penalty_factor, coef, mass_factor, scaled);
     tab = &scaled;
   }
-  DG_TRY(laplace_apply(false, c->m, ncomp, s, d, *tab, EPI_NONE, EpiHost(), c->s));
+  DG_TRY(laplace_apply(false, c->m, ncomp, s, d, *tab, EPI_NONE, EpiHost(), c->s, c->d.fp64_mode == 1));
   return st.finish();
 }
 
@@ -797,7 +798,7 @@ int dgns_vmult_convective(dgns_ctx* c, double* dst3, const double* u3) {
   void* d;
   DG_TRY(st.in(u3, bu, &s));
   DG_TRY(st.out(dst3, bu, &d));
-  int rc = convective_apply(c->m, (const double*)s, (double*)d, c->conv, c->s);
+  int rc = convective_apply(c->m, (const double*)s, (double*)d, c->conv, c->d.fp64_mode == 1, c->s);
   if (rc == 7) return fail(DGNS_ERR_UNSUPPORTED, "convective kernel: unsupported (k, n_q_conv)");
   DG_TRY(rc);
   return st.finish();
@@ -992,7 +993,7 @@ int dgns_cg_mg_solve(dgns_ctx* c, double* x, const double* b, const dgns_solve_p
     int it = 0;
     status = DGNS_ERR_NOT_CONVERGED;
     while (it < prm.max_iter) {
-      DG_TRY(laplace_apply(false, c->m, 1, c->p, c->Ap, A, EPI_NONE, EpiHost(), c->s));
+      DG_TRY(laplace_apply(false, c->m, 1, c->p, c->Ap, A, EPI_NONE, EpiHost(), c->s, c->d.fp64_mode == 1));
       DG_TRY(dot(c->p, c->Ap, n, c->red, S_PAP, c->s));
       DG_TRY(cg_update(X, c->r, c->p, c->Ap, n, c->red, c->s));
       DG_TRY(read_scalars(c));
@@ -1064,7 +1065,7 @@ int dgns_cg_invmass_solve(dgns_ctx* c, double* x3, const double* b3, double mass
     double res = 1.0;
     status = DGNS_ERR_NOT_CONVERGED;
     while (it < prm.max_iter) {
-      DG_TRY(laplace_apply(false, c->m, 3, c->p, c->Ap, H, EPI_NONE, EpiHost(), c->s));
+      DG_TRY(laplace_apply(false, c->m, 3, c->p, c->Ap, H, EPI_NONE, EpiHost(), c->s, c->d.fp64_mode == 1));
       DG_TRY(dot(c->p, c->Ap, n, c->red, S_PAP, c->s));
       DG_TRY(cg_update(X, c->r, c->p, c->Ap, n, c->red, c->s));
       DG_TRY(read_scalars(c));

@@ -1,0 +1,185 @@
+// Arithmetic policies of the FP64 operator kernels.
+//
+// F64    native double precision (the FP64 pipe: 2 FMA/clk/SM on GB300).
+// DF64   "double-float": a value is an unevaluated sum hi + lo of two floats
+//        (48-bit significand), evaluated on the FP32 pipe, which is 61x
+//        faster than the FP64 pipe on GB300.  Products use the FMA-based
+//        exact product (Dekker / Karp-Markstein), sums Knuth's two-sum;
+//        dot products accumulate lazily: the running sum of the leading
+//        products is kept error-free with two-sum, all rounding errors and
+//        low-order cross terms collect in a float that is folded in once at
+//        the end (in the spirit of Ogita, Rump & Oishi's Dot2).  Relative
+//        accuracy about 2^-47 of the sum of |terms|, against 2^-53 for FP64.
+//        All float operations use the _rn intrinsics, which the compiler never
+//        contracts into FMAs, so the error-free transformations stay exact.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace dgns {
+
+struct df64 {
+  float hi, lo;
+};
+
+struct F32 {
+  typedef float G;     // type in global memory
+  typedef float V;
+  typedef float Acc;
+  static constexpr bool emulated = false;
+  __device__ __forceinline__ static V from_double(double x) { return (float)x; }
+  __device__ __forceinline__ static V load(const float* p) { return __ldg(p); }
+  __device__ __forceinline__ static double to_double(V x) { return x; }
+  __host__ static V make(double x) { return (float)x; }
+  __device__ __forceinline__ static void acc_zero(Acc& a) { a = 0.0f; }
+  __device__ __forceinline__ static void acc_set(Acc& a, V x) { a = x; }
+  __device__ __forceinline__ static void acc_fma(Acc& a, V c, V x) { a = fmaf(c, x, a); }
+  __device__ __forceinline__ static V acc_get(const Acc& a) { return a; }
+  __device__ __forceinline__ static G store(V x) { return x; }
+};
+
+struct F64 {
+  typedef double G;    // type in global memory
+  typedef double V;    // value
+  typedef double Acc;  // dot-product accumulator
+  static constexpr bool emulated = false;
+  __device__ __forceinline__ static V from_double(double x) { return x; }
+  __device__ __forceinline__ static V load(const double* p) { return __ldg(p); }
+  __device__ __forceinline__ static double to_double(V x) { return x; }
+  __host__ static V make(double x) { return x; }
+  __device__ __forceinline__ static V zero() { return 0.0; }
+  __device__ __forceinline__ static void acc_zero(Acc& a) { a = 0.0; }
+  __device__ __forceinline__ static void acc_set(Acc& a, V x) { a = x; }
+  __device__ __forceinline__ static void acc_fma(Acc& a, V c, V x) { a = fma(c, x, a); }
+  __device__ __forceinline__ static V acc_get(const Acc& a) { return a; }
+  __device__ __forceinline__ static V add(V a, V b) { return a + b; }
+  __device__ __forceinline__ static V sub(V a, V b) { return a - b; }
+  __device__ __forceinline__ static V mul(V a, V b) { return a * b; }
+  __device__ __forceinline__ static V neg(V a) { return -a; }
+  __device__ __forceinline__ static V fmadd(V a, V b, V c) { return fma(a, b, c); }
+  __device__ __forceinline__ static V half(V a) { return 0.5 * a; }
+  __device__ __forceinline__ static V absval(V a) { return fabs(a); }
+  __device__ __forceinline__ static bool greater(V a, V b) { return a > b; }
+  __device__ __forceinline__ static bool equal(V a, V b) { return a == b; }
+  __device__ __forceinline__ static int sign(V a) { return a > 0.0 ? 1 : (a < 0.0 ? -1 : 0); }
+  __device__ __forceinline__ static G store(V x) { return x; }
+};
+
+struct DF64 {
+  typedef double G;
+  typedef df64 V;
+  struct Acc {
+    float s, e;
+  };
+  static constexpr bool emulated = true;
+
+  __device__ __forceinline__ static void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  }
+  __device__ __forceinline__ static V renorm(float s, float e) {
+    V r;
+    r.hi = __fadd_rn(s, e);
+    r.lo = __fsub_rn(e, __fsub_rn(r.hi, s));
+    return r;
+  }
+  __device__ __forceinline__ static V from_double(double x) {
+    V r;
+    r.hi = __double2float_rn(x);
+    r.lo = __double2float_rn(x - (double)r.hi);
+    return r;
+  }
+  // Split of a double held in global memory, by integer operations only (no
+  // FP64 instruction): hi = sign, exponent and the leading 23 fraction bits
+  // (truncated), lo = the remaining 29 fraction bits rounded to a float, same
+  // sign.  |hi + lo - x| <= 2^-47 |x| for 2^-74 <= |x| < 2^127; below 2^-74
+  // lo is dropped (absolute error < 2^-97), below 2^-126 the value is zero.
+  __device__ __forceinline__ static V load(const double* p) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(__ldg(p));
+    const unsigned h = (unsigned)(b >> 32), l = (unsigned)b;
+    const unsigned sgn = h & 0x80000000u;
+    const int e = (int)((h >> 20) & 0x7FFu);
+    const unsigned m23 = ((h & 0xFFFFFu) << 3) | (l >> 29);
+    V r;
+    r.hi = e >= 897 ? __uint_as_float(sgn | ((unsigned)(e - 896) << 23) | m23) : 0.0f;
+    const float rest = __uint2float_rn(l & 0x1FFFFFFFu);
+    const float scale = __uint_as_float((unsigned)(e >= 949 ? e - 948 : 1) << 23);
+    r.lo = e >= 949 ? __uint_as_float(__float_as_uint(__fmul_rn(rest, scale)) | sgn) : 0.0f;
+    return r;
+  }
+  __device__ __forceinline__ static double to_double(V x) { return (double)x.hi + (double)x.lo; }
+  __device__ __forceinline__ static G store(V x) { return to_double(x); }
+  __host__ static V make(double x) {
+    V r;
+    r.hi = (float)x;
+    r.lo = (float)(x - (double)r.hi);
+    return r;
+  }
+  __device__ __forceinline__ static V zero() {
+    V r;
+    r.hi = 0.0f;
+    r.lo = 0.0f;
+    return r;
+  }
+  __device__ __forceinline__ static void acc_zero(Acc& a) {
+    a.s = 0.0f;
+    a.e = 0.0f;
+  }
+  __device__ __forceinline__ static void acc_set(Acc& a, V x) {
+    a.s = x.hi;
+    a.e = x.lo;
+  }
+  // a += c * x
+  __device__ __forceinline__ static void acc_fma(Acc& a, V c, V x) {
+    const float p = __fmul_rn(c.hi, x.hi);
+    float pe = __fmaf_rn(c.hi, x.hi, -p);
+    pe = __fmaf_rn(c.hi, x.lo, pe);
+    pe = __fmaf_rn(c.lo, x.hi, pe);
+    float s, e;
+    two_sum(a.s, p, s, e);
+    a.s = s;
+    a.e = __fadd_rn(a.e, __fadd_rn(e, pe));
+  }
+  __device__ __forceinline__ static V acc_get(const Acc& a) {
+    V r;
+    two_sum(a.s, a.e, r.hi, r.lo);
+    return r;
+  }
+  __device__ __forceinline__ static V add(V a, V b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    return renorm(s, e);
+  }
+  __device__ __forceinline__ static V neg(V a) {
+    a.hi = -a.hi;
+    a.lo = -a.lo;
+    return a;
+  }
+  __device__ __forceinline__ static V sub(V a, V b) { return add(a, neg(b)); }
+  __device__ __forceinline__ static V mul(V a, V b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return renorm(p, e);
+  }
+  // a * b + c
+  __device__ __forceinline__ static V fmadd(V a, V b, V c) {
+    Acc t;
+    acc_set(t, c);
+    acc_fma(t, a, b);
+    return acc_get(t);
+  }
+  __device__ __forceinline__ static V half(V a) {
+    a.hi *= 0.5f;
+    a.lo *= 0.5f;
+    return a;
+  }
+  __device__ __forceinline__ static V absval(V a) { return a.hi < 0.0f ? neg(a) : a; }
+  __device__ __forceinline__ static bool greater(V a, V b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+  __device__ __forceinline__ static bool equal(V a, V b) { return a.hi == b.hi && a.lo == b.lo; }
+  __device__ __forceinline__ static int sign(V a) { return a.hi > 0.0f ? 1 : (a.hi < 0.0f ? -1 : 0); }
+};
+
+}  // namespace dgns

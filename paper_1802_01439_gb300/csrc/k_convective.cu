@@ -15,6 +15,7 @@
 //             F* = {{u (x) u}}.n + max(|u-.n|, |u+.n|) (u- - u+), added to
 //             the own face layer with sign + (own cell is '-') or - (own
 //             cell is '+').  Each cell evaluates its six faces.
+#include "arith.cuh"
 #include "ops.h"
 
 namespace dgns {
@@ -40,12 +41,14 @@ struct ConvLayout {
   static constexpr int U = 3 * N3;               // nodal velocity
   static constexpr int U1 = 3 * Q * N * N;       // x-interpolated; later: result
   static constexpr int U2 = 3 * Q * Q * N;       // xy-interpolated; later: face work
-  static constexpr int P = 3 * Q * Q;            // one z-plane at the Gauss points
+  static constexpr int P = 6 * Q * Q;            // one z-plane: u and the weighted u
   static constexpr int X = 9 * N * Q;            // x-tested plane
   static constexpr int Y = 6 * N * N;            // xy-tested plane
   static constexpr int FACE = 6 * Q * N + 6 * Q * Q + 3 * Q * Q;
   static constexpr int U2F = U2 > FACE ? U2 : FACE;
-  static constexpr int PER = U + U1 + U2F + P + X + Y;
+  static constexpr int PXY = P + X + Y;
+  static constexpr int UP = U > PXY ? U : PXY;   // nodal u first, plane work later
+  static constexpr int PER = UP + U1 + U2F;
 };
 
 __device__ __forceinline__ int node3(int N, int d, int a, int t1, int j1, int t2, int j2) {
@@ -56,27 +59,49 @@ __device__ __forceinline__ int node3(int N, int d, int a, int t1, int j1, int t2
   return c[0] + N * (c[1] + N * c[2]);
 }
 
-template <int N, int Q>
+template <class V, int N, int Q>
+struct ConvTabT {
+  V S[Q * N];
+  V D[Q * N];
+  V w[Q];
+  V jac[3];
+  V area[3];
+};
+
+// Forward convective kernel for an arithmetic policy A (F64 or DF64): loads
+// and stores are double; all arithmetic is A's.  Loops over Gauss points are
+// kept rolled (inner loops over the node index stay unrolled): fully unrolled
+// double-float code overflows the instruction cache.
+template <class A, int N, int Q>
 __global__ void __launch_bounds__(conv_cells_per_block<N>() * N * N)
-    conv_kernel(const double* __restrict__ u3, double* __restrict__ dst3, const __grid_constant__ ConvTab<N, Q> tb,
-                const MeshDims m) {
+    conv_kernel(const double* __restrict__ u3, double* __restrict__ dst3,
+                const __grid_constant__ ConvTabT<typename A::V, N, Q> tb, const MeshDims m) {
+  typedef typename A::V V;
+  typedef typename A::Acc Acc;
   typedef ConvLayout<N, Q> LY;
+  static_assert(sizeof(V) == sizeof(double), "8-byte values");
   constexpr int NT = N * N, N3 = N * N * N, EPB = conv_cells_per_block<N>();
-  double* sm = reinterpret_cast<double*>(dyn_smem());
+  V* sm = reinterpret_cast<V*>(dyn_smem());
   const int slot = threadIdx.x / NT;
   const int t = threadIdx.x - slot * NT;
   const long long c0 = (long long)blockIdx.x * EPB;
   const long long rem = m.E - c0;
   const int nvalid = rem < EPB ? (int)rem : EPB;
   const bool active = slot < nvalid;
-  double* sU = sm + slot * LY::PER;
-  double* sU1 = sU + LY::U;
-  double* sU2 = sU1 + LY::U1;
-  double* sP = sU2 + LY::U2F;
-  double* sX = sP + LY::P;
-  double* sY = sX + LY::X;
-  double* sOut = sU1;   // reused after the interpolation
-  double* sFace = sU2;  // reused after the cell term
+  V* sS = sm + EPB * LY::PER;    // copies of the 1D tables (work items that
+  V* sD = sS + Q * N;            // index them by thread read shared memory)
+  for (int i = threadIdx.x; i < Q * N; i += blockDim.x) {
+    sS[i] = tb.S[i];
+    sD[i] = tb.D[i];
+  }
+  V* sU = sm + slot * LY::PER;   // nodal u, dead after the x interpolation
+  V* sP = sU;                    // plane work reuses it
+  V* sX = sP + LY::P;
+  V* sY = sX + LY::X;
+  V* sU1 = sU + LY::UP;
+  V* sU2 = sU1 + LY::U1;
+  V* sOut = sU1;   // reused after the interpolation
+  V* sFace = sU2;  // reused after the cell term
 
   long long el = 0;
   int ex = 0, ey = 0, ez = 0;
@@ -87,21 +112,22 @@ __global__ void __launch_bounds__(conv_cells_per_block<N>() * N * N)
     ey = (int)(tt % m.ny);
     ez = (int)(tt / m.ny);
     for (int c = 0; c < 3; ++c)
-      for (int i = t; i < N3; i += NT) sU[c * N3 + i] = u3[(c * m.E + el) * N3 + i];
+      for (int i = t; i < N3; i += NT) sU[c * N3 + i] = A::from_double(u3[(c * m.E + el) * N3 + i]);
   }
   __syncthreads();
   // interpolation along x: (N,N,N) -> (Q,N,N)
   if (active)
     for (int it = t; it < 3 * N * N; it += NT) {
       const int c = it / (N * N), l = it - c * N * N;
-      double x[N];
-      load_line<double, N>(sU + c * N3, l * N, 1, x);
-#pragma unroll
+      V x[N];
+      load_line<V, N>(sU + c * N3, l * N, 1, x);
+#pragma unroll 1
       for (int q = 0; q < Q; ++q) {
-        double a = tb.S[q * N] * x[0];
+        Acc a;
+        A::acc_zero(a);
 #pragma unroll
-        for (int j = 1; j < N; ++j) a = fma(tb.S[q * N + j], x[j], a);
-        sU1[c * Q * N * N + l * Q + q] = a;
+        for (int j = 0; j < N; ++j) A::acc_fma(a, tb.S[q * N + j], x[j]);
+        sU1[c * Q * N * N + l * Q + q] = A::acc_get(a);
       }
     }
   __syncthreads();
@@ -110,88 +136,91 @@ __global__ void __launch_bounds__(conv_cells_per_block<N>() * N * N)
     for (int it = t; it < 3 * Q * N; it += NT) {
       const int c = it / (Q * N), l = it - c * Q * N;
       const int qx = l % Q, z = l / Q;
-      double x[N];
-      load_line<double, N>(sU1 + c * Q * N * N, qx + Q * N * z, Q, x);
-#pragma unroll
+      V x[N];
+      load_line<V, N>(sU1 + c * Q * N * N, qx + Q * N * z, Q, x);
+#pragma unroll 1
       for (int q = 0; q < Q; ++q) {
-        double a = tb.S[q * N] * x[0];
+        Acc a;
+        A::acc_zero(a);
 #pragma unroll
-        for (int j = 1; j < N; ++j) a = fma(tb.S[q * N + j], x[j], a);
-        sU2[c * Q * Q * N + qx + Q * q + Q * Q * z] = a;
+        for (int j = 0; j < N; ++j) A::acc_fma(a, tb.S[q * N + j], x[j]);
+        sU2[c * Q * Q * N + qx + Q * q + Q * Q * z] = A::acc_get(a);
       }
     }
   __syncthreads();
 
-  double acc[3][N];
+  Acc acc[3][N];
 #pragma unroll
   for (int c = 0; c < 3; ++c)
 #pragma unroll
-    for (int z = 0; z < N; ++z) acc[c][z] = 0.0;
+    for (int z = 0; z < N; ++z) A::acc_zero(acc[c][z]);
   const int tx = t % N, ty = t / N;
 
   for (int qz = 0; qz < Q; ++qz) {
-    // P1: values on the plane z = g_qz
+    // P1: u and the weighted u_d w_qx w_qy w_qz h_x h_y h_z / h_d on the
+    // plane z = g_qz
     if (active)
       for (int it = t; it < 3 * Q * Q; it += NT) {
         const int c = it / (Q * Q), l = it - c * Q * Q;
-        const double* src = sU2 + c * Q * Q * N + l;
-        double a = 0.0;
+        const V* src = sU2 + c * Q * Q * N + l;
+        Acc a;
+        A::acc_zero(a);
 #pragma unroll
-        for (int z = 0; z < N; ++z) a = fma(tb.S[qz * N + z], src[Q * Q * z], a);
-        sP[it] = a;
+        for (int z = 0; z < N; ++z) A::acc_fma(a, tb.S[qz * N + z], src[Q * Q * z]);
+        const V u = A::acc_get(a);
+        const int qx = l % Q, qy = l / Q;
+        const V w3 = A::mul(A::mul(tb.w[qx], tb.w[qy]), tb.w[qz]);
+        sP[it] = u;
+        sP[3 * Q * Q + it] = A::mul(A::mul(w3, tb.jac[c]), u);
       }
     __syncthreads();
-    // P2: flux on x-lines of the plane, tested with D_x^T / S_x^T
+    // P2: flux F_cd = u_c (weighted u_d) on x-lines, tested with D_x^T (d = x)
+    // or S_x^T (d = y, z); one work item per (c, d, qy)
     if (active)
-      for (int it = t; it < 3 * Q; it += NT) {
-        const int c = it / Q, qy = it - c * Q;
-        const double wyz = tb.w[qy] * tb.w[qz];
-        double a1[N], a2[N], a3[N];
+      for (int it = t; it < 9 * Q; it += NT) {
+        const int cd = it / Q, qy = it - cd * Q;
+        const int c = cd / 3, d = cd - 3 * c;
+        const V* T = d == 0 ? sD : sS;
+        Acc a[N];
 #pragma unroll
-        for (int x = 0; x < N; ++x) a1[x] = a2[x] = a3[x] = 0.0;
-#pragma unroll
+        for (int x = 0; x < N; ++x) A::acc_zero(a[x]);
+#pragma unroll 1
         for (int qx = 0; qx < Q; ++qx) {
-          const double u0 = sP[qx + Q * qy], u1 = sP[Q * Q + qx + Q * qy], u2 = sP[2 * Q * Q + qx + Q * qy];
-          const double uc = c == 0 ? u0 : (c == 1 ? u1 : u2);
-          const double wq = tb.w[qx] * wyz * uc;
-          const double fx = wq * tb.jac[0] * u0, fy = wq * tb.jac[1] * u1, fz = wq * tb.jac[2] * u2;
+          const int pt = qx + Q * qy;
+          const V f = A::mul(sP[c * Q * Q + pt], sP[(3 + d) * Q * Q + pt]);
 #pragma unroll
-          for (int x = 0; x < N; ++x) {
-            a1[x] = fma(tb.D[qx * N + x], fx, a1[x]);
-            a2[x] = fma(tb.S[qx * N + x], fy, a2[x]);
-            a3[x] = fma(tb.S[qx * N + x], fz, a3[x]);
-          }
+          for (int x = 0; x < N; ++x) A::acc_fma(a[x], T[qx * N + x], f);
         }
 #pragma unroll
-        for (int x = 0; x < N; ++x) {
-          sX[(c * 3 + 0) * N * Q + x + N * qy] = a1[x];
-          sX[(c * 3 + 1) * N * Q + x + N * qy] = a2[x];
-          sX[(c * 3 + 2) * N * Q + x + N * qy] = a3[x];
-        }
+        for (int x = 0; x < N; ++x) sX[cd * N * Q + x + N * qy] = A::acc_get(a[x]);
       }
     __syncthreads();
     // P3: y tests: Y1 = S_y^T X1 + D_y^T X2, Y3 = S_y^T X3
     if (active)
       for (int it = t; it < 3 * N; it += NT) {
         const int c = it / N, x = it - c * N;
-        double y1[N], y3[N];
+        Acc y1[N], y3[N];
 #pragma unroll
-        for (int y = 0; y < N; ++y) y1[y] = y3[y] = 0.0;
-#pragma unroll
+        for (int y = 0; y < N; ++y) {
+          A::acc_zero(y1[y]);
+          A::acc_zero(y3[y]);
+        }
+#pragma unroll 1
         for (int qy = 0; qy < Q; ++qy) {
-          const double b1 = sX[(c * 3 + 0) * N * Q + x + N * qy];
-          const double b2 = sX[(c * 3 + 1) * N * Q + x + N * qy];
-          const double b3 = sX[(c * 3 + 2) * N * Q + x + N * qy];
+          const V b1 = sX[(c * 3 + 0) * N * Q + x + N * qy];
+          const V b2 = sX[(c * 3 + 1) * N * Q + x + N * qy];
+          const V b3 = sX[(c * 3 + 2) * N * Q + x + N * qy];
 #pragma unroll
           for (int y = 0; y < N; ++y) {
-            y1[y] = fma(tb.S[qy * N + y], b1, fma(tb.D[qy * N + y], b2, y1[y]));
-            y3[y] = fma(tb.S[qy * N + y], b3, y3[y]);
+            A::acc_fma(y1[y], tb.D[qy * N + y], b2);
+            A::acc_fma(y1[y], tb.S[qy * N + y], b1);
+            A::acc_fma(y3[y], tb.S[qy * N + y], b3);
           }
         }
 #pragma unroll
         for (int y = 0; y < N; ++y) {
-          sY[(c * 2 + 0) * N * N + x + N * y] = y1[y];
-          sY[(c * 2 + 1) * N * N + x + N * y] = y3[y];
+          sY[(c * 2 + 0) * N * N + x + N * y] = A::acc_get(y1[y]);
+          sY[(c * 2 + 1) * N * N + x + N * y] = A::acc_get(y3[y]);
         }
       }
     __syncthreads();
@@ -199,11 +228,13 @@ __global__ void __launch_bounds__(conv_cells_per_block<N>() * N * N)
     if (active) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const double y1 = sY[(c * 2 + 0) * N * N + tx + N * ty];
-        const double y3 = sY[(c * 2 + 1) * N * N + tx + N * ty];
+        const V y1 = sY[(c * 2 + 0) * N * N + tx + N * ty];
+        const V y3 = sY[(c * 2 + 1) * N * N + tx + N * ty];
 #pragma unroll
-        for (int z = 0; z < N; ++z)
-          acc[c][z] = fma(-tb.S[qz * N + z], y1, fma(-tb.D[qz * N + z], y3, acc[c][z]));
+        for (int z = 0; z < N; ++z) {
+          A::acc_fma(acc[c][z], A::neg(tb.D[qz * N + z]), y3);
+          A::acc_fma(acc[c][z], A::neg(tb.S[qz * N + z]), y1);
+        }
       }
     }
   }
@@ -212,15 +243,15 @@ __global__ void __launch_bounds__(conv_cells_per_block<N>() * N * N)
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
-      for (int z = 0; z < N; ++z) sOut[c * N3 + tx + N * ty + N * N * z] = acc[c][z];
+      for (int z = 0; z < N; ++z) sOut[c * N3 + tx + N * ty + N * N * z] = A::acc_get(acc[c][z]);
   }
   __syncthreads();
 
   // ---------------------------------------------------------------- faces
-  double* G1 = sFace;              // [side][c][q1 + Q j2]   6 Q N
-  double* G2 = G1 + 6 * Q * N;     // [side][c][q1 + Q q2]   6 Q Q
-  double* H = G2 + 6 * Q * Q;      // [c][q1 + Q q2]         3 Q Q
-  double* K1 = G1;                 // [c][q1 + Q j2] reuses G1
+  V* G1 = sFace;              // [side][c][q1 + Q j2]   6 Q N
+  V* G2 = G1 + 6 * Q * N;     // [side][c][q1 + Q q2]   6 Q Q
+  V* H = G2 + 6 * Q * Q;      // [c][q1 + Q q2]         3 Q Q
+  V* K1 = G1;                 // [c][q1 + Q j2] reuses G1
   for (int d = 0; d < 3; ++d) {
     const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
     for (int side = 1; side >= -1; side -= 2) {
@@ -235,17 +266,18 @@ __global__ void __launch_bounds__(conv_cells_per_block<N>() * N * N)
       if (active)
         for (int it = t; it < 6 * N; it += NT) {
           const int s = it / (3 * N), c = (it / N) % 3, j2 = it % N;
-          double v[N];
+          V v[N];
 #pragma unroll
           for (int j1 = 0; j1 < N; ++j1)
-            v[j1] = s == 0 ? sU[c * N3 + node3(N, d, aown, t1, j1, t2, j2)]
-                           : __ldg(u3 + (c * m.E + nb) * N3 + node3(N, d, anb, t1, j1, t2, j2));
-#pragma unroll
+            v[j1] = A::from_double(s == 0 ? __ldg(u3 + (c * m.E + el) * N3 + node3(N, d, aown, t1, j1, t2, j2))
+                                          : __ldg(u3 + (c * m.E + nb) * N3 + node3(N, d, anb, t1, j1, t2, j2)));
+#pragma unroll 1
           for (int q1 = 0; q1 < Q; ++q1) {
-            double a = tb.S[q1 * N] * v[0];
+            Acc a;
+            A::acc_zero(a);
 #pragma unroll
-            for (int j = 1; j < N; ++j) a = fma(tb.S[q1 * N + j], v[j], a);
-            G1[(s * 3 + c) * Q * N + q1 + Q * j2] = a;
+            for (int j = 0; j < N; ++j) A::acc_fma(a, tb.S[q1 * N + j], v[j]);
+            G1[(s * 3 + c) * Q * N + q1 + Q * j2] = A::acc_get(a);
           }
         }
       __syncthreads();
@@ -253,15 +285,16 @@ __global__ void __launch_bounds__(conv_cells_per_block<N>() * N * N)
       if (active)
         for (int it = t; it < 6 * Q; it += NT) {
           const int sc = it / Q, q1 = it - sc * Q;
-          double v[N];
+          V v[N];
 #pragma unroll
           for (int j2 = 0; j2 < N; ++j2) v[j2] = G1[sc * Q * N + q1 + Q * j2];
-#pragma unroll
+#pragma unroll 1
           for (int q2 = 0; q2 < Q; ++q2) {
-            double a = tb.S[q2 * N] * v[0];
+            Acc a;
+            A::acc_zero(a);
 #pragma unroll
-            for (int j = 1; j < N; ++j) a = fma(tb.S[q2 * N + j], v[j], a);
-            G2[sc * Q * Q + q1 + Q * q2] = a;
+            for (int j = 0; j < N; ++j) A::acc_fma(a, tb.S[q2 * N + j], v[j]);
+            G2[sc * Q * Q + q1 + Q * q2] = A::acc_get(a);
           }
         }
       __syncthreads();
@@ -270,85 +303,90 @@ __global__ void __launch_bounds__(conv_cells_per_block<N>() * N * N)
         for (int it = t; it < Q * Q; it += NT) {
           const int q1 = it % Q, q2 = it / Q;
           const int sm_ = side > 0 ? 0 : 1, sp_ = side > 0 ? 1 : 0;  // trace index of '-' / '+'
-          double um[3], up[3];
+          V um[3], up[3];
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             um[c] = G2[(sm_ * 3 + c) * Q * Q + it];
             up[c] = G2[(sp_ * 3 + c) * Q * Q + it];
           }
-          const double unm = um[d], unp = up[d];
-          const double lam = fmax(fabs(unm), fabs(unp));
-          const double wgt = tb.w[q1] * tb.w[q2] * tb.area[d] * (double)side;
+          const V unm = um[d], unp = up[d];
+          const V am = A::absval(unm), ap = A::absval(unp);
+          const V lam = A::greater(am, ap) ? am : ap;
+          V wgt = A::mul(A::mul(tb.w[q1], tb.w[q2]), tb.area[d]);
+          if (side < 0) wgt = A::neg(wgt);
+          // 0.5 (u-_c un- + u+_c un+), the halving is exact
+          const V hm = A::half(unm), hp = A::half(unp);
 #pragma unroll
-          for (int c = 0; c < 3; ++c)
-            H[c * Q * Q + it] = wgt * fma(0.5, fma(um[c], unm, up[c] * unp), lam * (um[c] - up[c]));
+          for (int c = 0; c < 3; ++c) {
+            Acc f;
+            A::acc_zero(f);
+            A::acc_fma(f, um[c], hm);
+            A::acc_fma(f, up[c], hp);
+            A::acc_fma(f, lam, A::sub(um[c], up[c]));
+            H[c * Q * Q + it] = A::mul(wgt, A::acc_get(f));
+          }
         }
       __syncthreads();
-      // F4: test along t2
+      // F4: test along t2; one work item per (c, q1, j2)
       if (active)
-        for (int it = t; it < 3 * Q; it += NT) {
-          const int c = it / Q, q1 = it - c * Q;
-          double a[N];
-#pragma unroll
-          for (int j = 0; j < N; ++j) a[j] = 0.0;
-#pragma unroll
-          for (int q2 = 0; q2 < Q; ++q2) {
-            const double h = H[c * Q * Q + q1 + Q * q2];
-#pragma unroll
-            for (int j = 0; j < N; ++j) a[j] = fma(tb.S[q2 * N + j], h, a[j]);
-          }
-#pragma unroll
-          for (int j2 = 0; j2 < N; ++j2) K1[c * Q * N + q1 + Q * j2] = a[j2];
+        for (int it = t; it < 3 * Q * N; it += NT) {
+          const int c = it / (Q * N), r = it - c * Q * N;
+          const int j2 = r / Q, q1 = r - j2 * Q;
+          Acc a;
+          A::acc_zero(a);
+#pragma unroll 1
+          for (int q2 = 0; q2 < Q; ++q2) A::acc_fma(a, sS[q2 * N + j2], H[c * Q * Q + q1 + Q * q2]);
+          K1[c * Q * N + q1 + Q * j2] = A::acc_get(a);
         }
       __syncthreads();
       // F5: test along t1, add into the own face layer
       if (active)
         for (int it = t; it < 3 * N; it += NT) {
           const int c = it / N, j2 = it - c * N;
-          double a[N];
+          Acc a[N];
 #pragma unroll
-          for (int j = 0; j < N; ++j) a[j] = 0.0;
-#pragma unroll
+          for (int j1 = 0; j1 < N; ++j1) A::acc_set(a[j1], sOut[c * N3 + node3(N, d, aown, t1, j1, t2, j2)]);
+#pragma unroll 1
           for (int q1 = 0; q1 < Q; ++q1) {
-            const double h = K1[c * Q * N + q1 + Q * j2];
+            const V h = K1[c * Q * N + q1 + Q * j2];
 #pragma unroll
-            for (int j = 0; j < N; ++j) a[j] = fma(tb.S[q1 * N + j], h, a[j]);
+            for (int j = 0; j < N; ++j) A::acc_fma(a[j], tb.S[q1 * N + j], h);
           }
 #pragma unroll
-          for (int j1 = 0; j1 < N; ++j1) sOut[c * N3 + node3(N, d, aown, t1, j1, t2, j2)] += a[j1];
+          for (int j1 = 0; j1 < N; ++j1) sOut[c * N3 + node3(N, d, aown, t1, j1, t2, j2)] = A::acc_get(a[j1]);
         }
       __syncthreads();
     }
   }
   if (active)
     for (int c = 0; c < 3; ++c)
-      for (int i = t; i < N3; i += NT) dst3[(c * m.E + el) * N3 + i] = sOut[c * N3 + i];
+      for (int i = t; i < N3; i += NT) dst3[(c * m.E + el) * N3 + i] = A::to_double(sOut[c * N3 + i]);
 }
 
-template <int N, int Q>
+template <class A, int N, int Q>
 int launch_conv(const MeshDims& m, const double* u3, double* dst3, const ConvHost& h, cudaStream_t s) {
-  ConvTab<N, Q> tb;
+  ConvTabT<typename A::V, N, Q> tb;
   for (int i = 0; i < Q * N; ++i) {
-    tb.S[i] = h.S[i];
-    tb.D[i] = h.D[i];
+    tb.S[i] = A::make(h.S[i]);
+    tb.D[i] = A::make(h.D[i]);
   }
-  for (int q = 0; q < Q; ++q) tb.w[q] = h.w[q];
+  for (int q = 0; q < Q; ++q) tb.w[q] = A::make(h.w[q]);
   for (int d = 0; d < 3; ++d) {
-    tb.jac[d] = h.h[0] * h.h[1] * h.h[2] / h.h[d];
-    tb.area[d] = tb.jac[d];
+    const double j = h.h[0] * h.h[1] * h.h[2] / h.h[d];
+    tb.jac[d] = A::make(j);
+    tb.area[d] = A::make(j);
   }
   constexpr int EPB = conv_cells_per_block<N>();
-  const size_t smem = (size_t)EPB * ConvLayout<N, Q>::PER * sizeof(double);
+  const size_t smem = ((size_t)EPB * ConvLayout<N, Q>::PER + 2 * Q * N) * sizeof(double);
   if (smem > 232448) return 7;
-  if (cudaFuncSetAttribute(conv_kernel<N, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+  if (cudaFuncSetAttribute(conv_kernel<A, N, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return 2;
   if (m.E == 0) return 0;
   const long long blocks = (m.E + EPB - 1) / EPB;
-  conv_kernel<N, Q><<<(unsigned)blocks, EPB * N * N, smem, s>>>(u3, dst3, tb, m);
+  conv_kernel<A, N, Q><<<(unsigned)blocks, EPB * N * N, smem, s>>>(u3, dst3, tb, m);
   return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }
-
 
 // ------------------------------------------------------------------- VJP
 // grad_u = (dC/du)^T w.  Cell: with g_cd(q) = sum_i w_c,i d_d phi_i(q), the
@@ -727,13 +765,17 @@ int launch_conv_vjp(const MeshDims& m, const double* u3, const double* w3, doubl
 
 }  // namespace
 
-// Supported: Q = floor(3N/2) (the 3/2 rule) and Q = N.
-int convective_apply(const MeshDims& m, const double* u3, double* dst3, const ConvHost& t,
+// Supported: Q = floor(3N/2) (the 3/2 rule) and Q = N; arithmetic FP64 or
+// double-float (emulated = true).
+int convective_apply(const MeshDims& m, const double* u3, double* dst3, const ConvHost& t, bool emulated,
                      cudaStream_t s) {
   const int N = t.N, Q = t.Q;
-#define DGNS_CONV(NV)                                                     \
-  if (N == NV && Q == (3 * NV) / 2) return launch_conv<NV, (3 * NV) / 2>(m, u3, dst3, t, s); \
-  if (N == NV && Q == NV) return launch_conv<NV, NV>(m, u3, dst3, t, s);
+#define DGNS_CONV(NV)                                                                             \
+  if (N == NV && Q == (3 * NV) / 2)                                                               \
+    return emulated ? launch_conv<DF64, NV, (3 * NV) / 2>(m, u3, dst3, t, s)                      \
+                    : launch_conv<F64, NV, (3 * NV) / 2>(m, u3, dst3, t, s);                      \
+  if (N == NV && Q == NV)                                                                         \
+    return emulated ? launch_conv<DF64, NV, NV>(m, u3, dst3, t, s) : launch_conv<F64, NV, NV>(m, u3, dst3, t, s);
   DGNS_CONV(2)
   DGNS_CONV(3)
   DGNS_CONV(4)

@@ -19,24 +19,25 @@
 // and three work arrays are staged in shared memory; neighbour lines are read
 // directly from global memory (they are L2 resident).  Global loads and
 // stores of the own cells are coalesced over the block's contiguous cells.
+#include "arith.cuh"
 #include "ops.h"
 
 namespace dgns {
 namespace {
 
-template <class T, int N>
+template <class V, int N>
 struct LapTab {
-  T A0[3][N * N];
-  T M[N * N];
-  T cr[3][N], cl[3][N], gr[3][N], gl[3][N];
+  V A0[3][N * N];
+  V M[N * N];
+  V cr[3][N], cl[3][N], gr[3][N], gl[3][N];
 };
 
-template <class T>
+template <class G>
 struct EpiArgs {
-  const T* b;
-  const T* xprev;
-  const T* dinv;
-  T c1, c2;
+  const G* b;
+  const G* xprev;
+  const G* dinv;
+  G c1, c2;
 };
 
 template <int N>
@@ -45,71 +46,135 @@ constexpr int cells_per_block() {
 }
 
 // One line of T_d x for the own cell, with the neighbour terms.
-template <class T, int N, int D>
-__device__ __forceinline__ void sipg_line(const T* X, T* out, const T* __restrict__ nbR,
-                                          const T* __restrict__ nbL, int l,
-                                          const LapTab<T, N>& tb) {
+template <class A, int N, int D>
+__device__ __forceinline__ void sipg_line(const typename A::V* X, typename A::V* out,
+                                          const typename A::G* __restrict__ nbR,
+                                          const typename A::G* __restrict__ nbL, int l,
+                                          const LapTab<typename A::V, N>& tb) {
+  typedef typename A::V V;
+  typedef typename A::Acc Acc;
   int base, stride;
   line_geom<D>(l, N, N, N, base, stride);
-  T x[N], r[N], lf[N], y[N];
-  load_line<T, N>(X, base, stride, x);
+  V x[N], r[N], lf[N];
+  Acc y[N];
+  load_line<V, N>(X, base, stride, x);
 #pragma unroll
   for (int j = 0; j < N; ++j) {
-    r[j] = __ldg(nbR + base + j * stride);
-    lf[j] = __ldg(nbL + base + j * stride);
+    r[j] = A::load(nbR + base + j * stride);
+    lf[j] = A::load(nbL + base + j * stride);
   }
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    T acc = tb.cr[D][i] * r[0];
-    acc = fma(tb.cl[D][i], lf[N - 1], acc);
+    A::acc_zero(y[i]);
+    A::acc_fma(y[i], tb.cr[D][i], r[0]);
+    A::acc_fma(y[i], tb.cl[D][i], lf[N - 1]);
 #pragma unroll
-    for (int j = 0; j < N; ++j) acc = fma(tb.A0[D][i * N + j], x[j], acc);
-    y[i] = acc;
+    for (int j = 0; j < N; ++j) A::acc_fma(y[i], tb.A0[D][i * N + j], x[j]);
   }
 #pragma unroll
   for (int j = 0; j < N; ++j) {
-    y[N - 1] = fma(tb.gr[D][j], r[j], y[N - 1]);
-    y[0] = fma(tb.gl[D][j], lf[j], y[0]);
+    A::acc_fma(y[N - 1], tb.gr[D][j], r[j]);
+    A::acc_fma(y[0], tb.gl[D][j], lf[j]);
   }
-  store_line<T, N>(out, base, stride, y);
+#pragma unroll
+  for (int i = 0; i < N; ++i) out[base + i * stride] = A::acc_get(y[i]);
+}
+
+// Same, with the neighbour lines already in registers.
+template <class A, int N, int D>
+__device__ __forceinline__ void sipg_line_pre(const typename A::V* X, typename A::V* out,
+                                              const typename A::V (&r)[N], const typename A::V (&lf)[N], int l,
+                                              const LapTab<typename A::V, N>& tb) {
+  typedef typename A::V V;
+  typedef typename A::Acc Acc;
+  int base, stride;
+  line_geom<D>(l, N, N, N, base, stride);
+  V x[N];
+  Acc y[N];
+  load_line<V, N>(X, base, stride, x);
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    A::acc_zero(y[i]);
+    A::acc_fma(y[i], tb.cr[D][i], r[0]);
+    A::acc_fma(y[i], tb.cl[D][i], lf[N - 1]);
+#pragma unroll
+    for (int j = 0; j < N; ++j) A::acc_fma(y[i], tb.A0[D][i * N + j], x[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    A::acc_fma(y[N - 1], tb.gr[D][j], r[j]);
+    A::acc_fma(y[0], tb.gl[D][j], lf[j]);
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) out[base + i * stride] = A::acc_get(y[i]);
+}
+
+template <class A, int N, int D>
+__device__ __forceinline__ void load_nb_lines(const typename A::G* __restrict__ nbR,
+                                              const typename A::G* __restrict__ nbL, int l,
+                                              typename A::V (&r)[N], typename A::V (&lf)[N]) {
+  int base, stride;
+  line_geom<D>(l, N, N, N, base, stride);
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    r[j] = A::load(nbR + base + j * stride);
+    lf[j] = A::load(nbL + base + j * stride);
+  }
+}
+
+// Neighbour lines are prefetched into registers before the own cells are
+// staged, so both global-memory latencies overlap (small N only: 6N values
+// per thread).
+template <int N>
+constexpr bool prefetch_neighbours() {
+  return N <= 6;
 }
 
 // One line of out = M_d in (+ add).
-template <class T, int N, int D, bool ADD>
-__device__ __forceinline__ void mass_line(const T* in, const T* add, T* out, int l, const T* M) {
+template <class A, int N, int D, bool ADD>
+__device__ __forceinline__ void mass_line(const typename A::V* in, const typename A::V* add,
+                                          typename A::V* out, int l, const typename A::V* M) {
+  typedef typename A::V V;
+  typedef typename A::Acc Acc;
   int base, stride;
   line_geom<D>(l, N, N, N, base, stride);
-  T x[N], y[N];
-  load_line<T, N>(in, base, stride, x);
-  if (ADD) {
-    T z[N];
-    load_line<T, N>(add, base, stride, z);
-    matvec_add<T, N, N>(M, x, z, y);
-  } else {
-    matvec<T, N, N>(M, x, y);
+  V x[N];
+  Acc y[N];
+  load_line<V, N>(in, base, stride, x);
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    if (ADD)
+      A::acc_set(y[i], add[base + i * stride]);
+    else
+      A::acc_zero(y[i]);
+#pragma unroll
+    for (int j = 0; j < N; ++j) A::acc_fma(y[i], M[i * N + j], x[j]);
   }
-  store_line<T, N>(out, base, stride, y);
+#pragma unroll
+  for (int i = 0; i < N; ++i) out[base + i * stride] = A::acc_get(y[i]);
 }
 
-template <class T, int N, int EPI>
+template <class A, int N, int EPI>
 __global__ void __launch_bounds__(cells_per_block<N>() * N * N)
-    sipg_kernel(const T* __restrict__ src, T* __restrict__ dst, const __grid_constant__ LapTab<T, N> tb,
-                const MeshDims m, const long long ncells, const EpiArgs<T> ea) {
+    sipg_kernel(const typename A::G* __restrict__ src, typename A::G* __restrict__ dst,
+                const __grid_constant__ LapTab<typename A::V, N> tb, const MeshDims m, const long long ncells,
+                const EpiArgs<typename A::G> ea) {
+  typedef typename A::V V;
+  typedef typename A::G G;
   constexpr int NN = N * N, NNN = NN * N, EPB = cells_per_block<N>();
-  T* sX = reinterpret_cast<T*>(dyn_smem());
-  T* sA = sX + EPB * NNN;
-  T* sB = sA + EPB * NNN;
-  T* sC = sB + EPB * NNN;
+  V* sX = reinterpret_cast<V*>(dyn_smem());
+  V* sA = sX + EPB * NNN;
+  V* sB = sA + EPB * NNN;
+  V* sC = sB + EPB * NNN;
   const int slot = threadIdx.x / NN;
   const int l = threadIdx.x - slot * NN;
   const long long c0 = (long long)blockIdx.x * EPB;
   const long long rem = ncells - c0;
   const int nvalid = rem < EPB ? (int)rem : EPB;
-  const T* gsrc = src + c0 * NNN;
-  for (int i = threadIdx.x; i < nvalid * NNN; i += blockDim.x) sX[i] = gsrc[i];
-  __syncthreads();
+  const G* gsrc = src + c0 * NNN;
   const bool active = slot < nvalid;
   const int off = slot * NNN;
+  const G* nb[6] = {src, src, src, src, src, src};   // +x, -x, +y, -y, +z, -z
   if (active) {
     const long long cell = c0 + slot;
     const long long comp = cell / m.E;
@@ -118,84 +183,117 @@ __global__ void __launch_bounds__(cells_per_block<N>() * N * N)
     const long long t = el / m.nx;
     const int ey = (int)(t % m.ny);
     const int ez = (int)(t / m.ny);
-    const T* cb = src + comp * m.E * NNN;
-    sipg_line<T, N, 0>(sX + off, sA + off, cb + neighbor<0>(el, ex, ey, ez, +1, m) * NNN,
-                       cb + neighbor<0>(el, ex, ey, ez, -1, m) * NNN, l, tb);
-    sipg_line<T, N, 1>(sX + off, sB + off, cb + neighbor<1>(el, ex, ey, ez, +1, m) * NNN,
-                       cb + neighbor<1>(el, ex, ey, ez, -1, m) * NNN, l, tb);
-    sipg_line<T, N, 2>(sX + off, sC + off, cb + neighbor<2>(el, ex, ey, ez, +1, m) * NNN,
-                       cb + neighbor<2>(el, ex, ey, ez, -1, m) * NNN, l, tb);
+    const G* cb = src + comp * m.E * NNN;
+    nb[0] = cb + neighbor<0>(el, ex, ey, ez, +1, m) * NNN;
+    nb[1] = cb + neighbor<0>(el, ex, ey, ez, -1, m) * NNN;
+    nb[2] = cb + neighbor<1>(el, ex, ey, ez, +1, m) * NNN;
+    nb[3] = cb + neighbor<1>(el, ex, ey, ez, -1, m) * NNN;
+    nb[4] = cb + neighbor<2>(el, ex, ey, ez, +1, m) * NNN;
+    nb[5] = cb + neighbor<2>(el, ex, ey, ez, -1, m) * NNN;
+  }
+  if constexpr (prefetch_neighbours<N>()) {
+    V r0[N], l0[N], r1[N], l1[N], r2[N], l2[N];
+    if (active) {
+      load_nb_lines<A, N, 0>(nb[0], nb[1], l, r0, l0);
+      load_nb_lines<A, N, 1>(nb[2], nb[3], l, r1, l1);
+      load_nb_lines<A, N, 2>(nb[4], nb[5], l, r2, l2);
+    }
+    for (int i = threadIdx.x; i < nvalid * NNN; i += blockDim.x) sX[i] = A::load(gsrc + i);
+    __syncthreads();
+    if (active) {
+      sipg_line_pre<A, N, 0>(sX + off, sA + off, r0, l0, l, tb);
+      sipg_line_pre<A, N, 1>(sX + off, sB + off, r1, l1, l, tb);
+      sipg_line_pre<A, N, 2>(sX + off, sC + off, r2, l2, l, tb);
+    }
+  } else {
+    for (int i = threadIdx.x; i < nvalid * NNN; i += blockDim.x) sX[i] = A::load(gsrc + i);
+    __syncthreads();
+    if (active) {
+      sipg_line<A, N, 0>(sX + off, sA + off, nb[0], nb[1], l, tb);
+      sipg_line<A, N, 1>(sX + off, sB + off, nb[2], nb[3], l, tb);
+      sipg_line<A, N, 2>(sX + off, sC + off, nb[4], nb[5], l, tb);
+    }
   }
   __syncthreads();
   if (active) {
-    mass_line<T, N, 0, false>(sB + off, nullptr, sB + off, l, tb.M);  // M_x T_y x
-    mass_line<T, N, 1, false>(sC + off, nullptr, sC + off, l, tb.M);  // M_y T_z x
+    mass_line<A, N, 0, false>(sB + off, nullptr, sB + off, l, tb.M);  // M_x T_y x
+    mass_line<A, N, 1, false>(sC + off, nullptr, sC + off, l, tb.M);  // M_y T_z x
   }
   __syncthreads();
   if (active) {
-    mass_line<T, N, 1, true>(sA + off, sB + off, sA + off, l, tb.M);  // M_y T_x x + M_x T_y x
-    mass_line<T, N, 0, false>(sC + off, nullptr, sC + off, l, tb.M);  // M_x M_y T_z x
+    mass_line<A, N, 1, true>(sA + off, sB + off, sA + off, l, tb.M);  // M_y T_x x + M_x T_y x
+    mass_line<A, N, 0, false>(sC + off, nullptr, sC + off, l, tb.M);  // M_x M_y T_z x
   }
   __syncthreads();
-  if (active) mass_line<T, N, 2, true>(sA + off, sC + off, sB + off, l, tb.M);
+  if (active) mass_line<A, N, 2, true>(sA + off, sC + off, sB + off, l, tb.M);
   __syncthreads();
-  T* gdst = dst + c0 * NNN;
+  G* gdst = dst + c0 * NNN;
   for (int i = threadIdx.x; i < nvalid * NNN; i += blockDim.x) {
-    const T y = sB[i];
-    if (EPI == EPI_NONE) {
-      gdst[i] = y;
-    } else if (EPI == EPI_RESID) {
-      gdst[i] = ea.b[c0 * NNN + i] - y;
+    if constexpr (EPI == EPI_NONE) {
+      gdst[i] = A::store(sB[i]);
     } else {
-      const T x = sX[i];
-      const T r = ea.b[c0 * NNN + i] - y;
-      T v = fma(ea.c2 * ea.dinv[i % NNN], r, x);
-      // x_{k+1} = x_k + c1 (x_k - x_{k-1}) + c2 D^-1 (b - A x_k); a null
-      // xprev stands for a zero previous iterate
-      if (ea.c1 != (T)0) v = fma(ea.c1, x - (ea.xprev ? ea.xprev[c0 * NNN + i] : (T)0), v);
-      gdst[i] = v;
+      // plain float / double policies only
+      const G y = sB[i];
+      if constexpr (EPI == EPI_RESID) {
+        gdst[i] = ea.b[c0 * NNN + i] - y;
+      } else {
+        const G x = sX[i];
+        const G r = ea.b[c0 * NNN + i] - y;
+        G v = fma(ea.c2 * ea.dinv[i % NNN], r, x);
+        // x_{k+1} = x_k + c1 (x_k - x_{k-1}) + c2 D^-1 (b - A x_k); a null
+        // xprev stands for a zero previous iterate
+        if (ea.c1 != (G)0) v = fma(ea.c1, x - (ea.xprev ? ea.xprev[c0 * NNN + i] : (G)0), v);
+        gdst[i] = v;
+      }
     }
   }
 }
 
-template <class T, int N, int EPI>
-int launch_sipg(const MeshDims& m, int ncomp, const T* src, T* dst, const LapHost& h,
+template <class A, int N, int EPI>
+int launch_sipg(const MeshDims& m, int ncomp, const typename A::G* src, typename A::G* dst, const LapHost& h,
                 const EpiHost& eh, cudaStream_t s) {
+  typedef typename A::G G;
   constexpr int NN = N * N, EPB = cells_per_block<N>();
-  LapTab<T, N> tb;
+  LapTab<typename A::V, N> tb;
   for (int d = 0; d < 3; ++d) {
-    for (int i = 0; i < NN; ++i) tb.A0[d][i] = (T)h.A0[d][i];
+    for (int i = 0; i < NN; ++i) tb.A0[d][i] = A::make(h.A0[d][i]);
     for (int i = 0; i < N; ++i) {
-      tb.cr[d][i] = (T)h.cr[d][i];
-      tb.cl[d][i] = (T)h.cl[d][i];
-      tb.gr[d][i] = (T)h.gr[d][i];
-      tb.gl[d][i] = (T)h.gl[d][i];
+      tb.cr[d][i] = A::make(h.cr[d][i]);
+      tb.cl[d][i] = A::make(h.cl[d][i]);
+      tb.gr[d][i] = A::make(h.gr[d][i]);
+      tb.gl[d][i] = A::make(h.gl[d][i]);
     }
   }
-  for (int i = 0; i < NN; ++i) tb.M[i] = (T)h.M[i];
-  EpiArgs<T> ea{(const T*)eh.b, (const T*)eh.xprev, (const T*)eh.dinv, (T)eh.c1, (T)eh.c2};
+  for (int i = 0; i < NN; ++i) tb.M[i] = A::make(h.M[i]);
+  EpiArgs<G> ea{(const G*)eh.b, (const G*)eh.xprev, (const G*)eh.dinv, (G)eh.c1, (G)eh.c2};
   const long long ncells = m.E * ncomp;
   if (ncells == 0) return 0;
   const long long blocks = (ncells + EPB - 1) / EPB;
-  const size_t smem = (size_t)4 * EPB * NN * N * sizeof(T);
+  const size_t smem = (size_t)4 * EPB * NN * N * sizeof(typename A::V);
   static bool attr_done = false;
   if (!attr_done) {
-    if (cudaFuncSetAttribute(sipg_kernel<T, N, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(sipg_kernel<A, N, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
       return 2;
     attr_done = true;
   }
-  sipg_kernel<T, N, EPI><<<(unsigned)blocks, EPB * NN, smem, s>>>(src, dst, tb, m, ncells, ea);
+  sipg_kernel<A, N, EPI><<<(unsigned)blocks, EPB * NN, smem, s>>>(src, dst, tb, m, ncells, ea);
   return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }
 
-template <class T, int N>
+template <class A, int N>
 int launch_sipg_epi(const MeshDims& m, int ncomp, const void* src, void* dst, const LapHost& h,
                     int epi, const EpiHost& eh, cudaStream_t s) {
-  switch (epi) {
-    case EPI_NONE: return launch_sipg<T, N, EPI_NONE>(m, ncomp, (const T*)src, (T*)dst, h, eh, s);
-    case EPI_RESID: return launch_sipg<T, N, EPI_RESID>(m, ncomp, (const T*)src, (T*)dst, h, eh, s);
-    case EPI_CHEB: return launch_sipg<T, N, EPI_CHEB>(m, ncomp, (const T*)src, (T*)dst, h, eh, s);
+  typedef typename A::G G;
+  if constexpr (A::emulated) {
+    if (epi != EPI_NONE) return 7;
+    return launch_sipg<A, N, EPI_NONE>(m, ncomp, (const G*)src, (G*)dst, h, eh, s);
+  } else {
+    switch (epi) {
+      case EPI_NONE: return launch_sipg<A, N, EPI_NONE>(m, ncomp, (const G*)src, (G*)dst, h, eh, s);
+      case EPI_RESID: return launch_sipg<A, N, EPI_RESID>(m, ncomp, (const G*)src, (G*)dst, h, eh, s);
+      case EPI_CHEB: return launch_sipg<A, N, EPI_CHEB>(m, ncomp, (const G*)src, (G*)dst, h, eh, s);
+    }
   }
   return 1;
 }
@@ -211,11 +309,12 @@ __global__ void broadcast_kernel(const T* __restrict__ table, T* __restrict__ ds
 }  // namespace
 
 int laplace_apply(bool fp32, const MeshDims& m, int ncomp, const void* src, void* dst,
-                  const LapHost& tab, int epi, const EpiHost& ea, cudaStream_t s) {
-#define DGNS_CASE(NV)                                                                  \
-  case NV:                                                                             \
-    return fp32 ? launch_sipg_epi<float, NV>(m, ncomp, src, dst, tab, epi, ea, s)      \
-                : launch_sipg_epi<double, NV>(m, ncomp, src, dst, tab, epi, ea, s);
+                  const LapHost& tab, int epi, const EpiHost& ea, cudaStream_t s, bool emulated) {
+#define DGNS_CASE(NV)                                                                           \
+  case NV:                                                                                      \
+    return fp32 ? launch_sipg_epi<F32, NV>(m, ncomp, src, dst, tab, epi, ea, s)                 \
+                : (emulated ? launch_sipg_epi<DF64, NV>(m, ncomp, src, dst, tab, epi, ea, s)    \
+                            : launch_sipg_epi<F64, NV>(m, ncomp, src, dst, tab, epi, ea, s));
   switch (tab.N) {
     DGNS_CASE(2)
     DGNS_CASE(3)

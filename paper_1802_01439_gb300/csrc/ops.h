@@ -34,8 +34,10 @@ struct EpiHost {
 
 // dst = L src on ncomp scalar fields (cells of component c follow those of
 // component c-1); `fp32` selects float data, else double.
+// emulated (double data only): double-float arithmetic on the FP32 pipe,
+// EPI_NONE only.
 int laplace_apply(bool fp32, const MeshDims& m, int ncomp, const void* src, void* dst,
-                  const LapHost& tab, int epi, const EpiHost& ea, cudaStream_t s);
+                  const LapHost& tab, int epi, const EpiHost& ea, cudaStream_t s, bool emulated = false);
 
 // dst[cell][i] = table[i] for every cell (broadcast of a per-cell pattern).
 int broadcast_cells(bool fp32, long long ncells, int nper, const void* table, void* dst,
@@ -79,7 +81,8 @@ struct ConvHost {
   double w[18];          // Gauss weights on [0,1]
   double h[3];
 };
-int convective_apply(const MeshDims& m, const double* u3, double* dst3, const ConvHost& t,
+// emulated: double-float arithmetic on the FP32 pipe (else native FP64)
+int convective_apply(const MeshDims& m, const double* u3, double* dst3, const ConvHost& t, bool emulated,
                      cudaStream_t s);
 int convective_vjp(const MeshDims& m, const double* u3, const double* w3, double* dst3,
                    const ConvHost& t, cudaStream_t s);

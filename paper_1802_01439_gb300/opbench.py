@@ -27,7 +27,7 @@ OPS = ["laplace", "laplace32", "convective", "viscous", "helmholtz", "invmass", 
        "divergence", "gradient"]
 
 
-def run(op, k, n, reps, warmup, ku=None):
+def run(op, k, n, reps, warmup, ku=None, fp64_mode=0):
     dev = torch.device("cuda")
     # scalar operators act on space U of a context with degree k
     kk = ku if ku is not None else k
@@ -36,7 +36,7 @@ def run(op, k, n, reps, warmup, ku=None):
     if op == "laplace32":       # FP32 level operator: pressure space of degree k
         ctx = Context(n, k, k, mg_precision=32, mg_coarse_n=n)
     else:
-        ctx = Context(n, kk, kp, mg_precision=mg)
+        ctx = Context(n, kk, kp, mg_precision=mg, fp64_mode=fp64_mode)
     nu, np_ = ctx.n_u, ctx.n_p
     f64 = dict(dtype=torch.float64, device=dev)
     rng = lambda m, s: torch.from_numpy(inputs.uniform(s, m)).to(dev)
@@ -88,7 +88,7 @@ def run(op, k, n, reps, warmup, ku=None):
         ts.append(e0.elapsed_time(e1))
     ms = float(np.mean(ts))
     ctx.close()
-    return {"op": op, "k": k, "n_elem": n, "dofs": dofs, "ms_mean": round(ms, 5),
+    return {"op": op, "k": k, "n_elem": n, "fp64_mode": fp64_mode, "dofs": dofs, "ms_mean": round(ms, 5),
             "ms_min": round(float(np.min(ts)), 5), "dofs_per_s": round(dofs / (ms * 1e-3), 1),
             "algorithmic_GBps": round(nbytes / (ms * 1e-3) / 1e9, 1)}
 
@@ -101,6 +101,7 @@ def main():
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--sweep", action="store_true")
+    ap.add_argument("--fp64-mode", type=int, default=0, help="0 native FP64, 1 double-float")
     ap.add_argument("--ops", default="laplace,convective,laplace32,invmass,helmholtz")
     a = ap.parse_args()
     if a.sweep:
@@ -108,10 +109,10 @@ def main():
             for k, n in SWEEP_N.items():
                 if op == "convective" and k > 9:
                     n = {10: 20, 11: 18}[k]
-                print(json.dumps(run(op, k, n, a.reps, a.warmup)), flush=True)
+                print(json.dumps(run(op, k, n, a.reps, a.warmup, fp64_mode=a.fp64_mode)), flush=True)
         return
     n = a.n or SWEEP_N.get(a.k, 32)
-    print(json.dumps(run(a.op, a.k, n, a.reps, a.warmup)), flush=True)
+    print(json.dumps(run(a.op, a.k, n, a.reps, a.warmup, fp64_mode=a.fp64_mode)), flush=True)
 
 
 if __name__ == "__main__":

@@ -36,9 +36,11 @@ def _mesh(n, kw):
     return dg.Mesh(n, kw.get("lo", (-np.pi,) * 3), kw.get("hi", (np.pi,) * 3))
 
 
+@pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("n,k,kw", LAP_CASES)
-def test_laplace(n, k, kw):
-    ctx = context(n, k, k, mg_precision=0, **kw)
+def test_laplace(n, k, kw, mode):
+    """mode 0: native FP64; mode 1: double-float arithmetic (FP32 pipe)."""
+    ctx = context(n, k, k, mg_precision=0, fp64_mode=mode, **kw)
     s = dg.Space(_mesh(n, kw), k)
     x = random_field(s, 1, 0)
     ref = dg.Laplace(s, kw.get("penalty_factor", 1.0)).apply(x)
@@ -75,10 +77,11 @@ def test_mass_and_inverse(n, k, kw):
         assert rel_err(host(y), M.apply_inverse(x)) <= TOL
 
 
+@pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("n,k", [((3, 2, 4), 3), ((2, 2, 3), 5), ((1, 2, 1), 2)])
-def test_viscous_and_helmholtz(n, k):
+def test_viscous_and_helmholtz(n, k, mode):
     nu = 1.0 / 1600
-    ctx = context(n, k, mg_precision=0, nu=nu)
+    ctx = context(n, k, mg_precision=0, nu=nu, fp64_mode=mode)
     s = dg.Space(dg.Mesh(n), k)
     u = random_field(s, 3, 2)
     y = torch.empty(u.size, dtype=torch.float64, device="cuda")
@@ -105,11 +108,14 @@ def test_divergence_gradient(n, ku):
     assert rel_err(host(g), dg.Gradient(su, sp).apply(p)) <= TOL
 
 
+@pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("n,k,field", [((4, 4, 4), 3, "tgv"), ((3, 2, 5), 2, "rand"),
                                        ((2, 2, 2), 5, "rand"), ((1, 1, 2), 1, "rand"),
-                                       ((2, 1, 1), 11, "tgv"), ((2, 3, 2), 7, "tgv")])
-def test_convective(n, k, field):
-    ctx = context(n, k, max(k - 1, 1), mg_precision=0)
+                                       ((2, 1, 1), 11, "tgv"), ((2, 3, 2), 7, "tgv"),
+                                       ((5, 3, 2), 4, "tgv"), ((2, 2, 1), 9, "rand")])
+def test_convective(n, k, field, mode):
+    """mode 0: native FP64; mode 1: double-float arithmetic (FP32 pipe)."""
+    ctx = context(n, k, max(k - 1, 1), mg_precision=0, fp64_mode=mode)
     s = dg.Space(dg.Mesh(n), k)
     u = tgv_field(s, 1e-3, 0) if field == "tgv" else random_field(s, 3, 6)
     ref = dg.Convective(s).apply(u)
@@ -138,3 +144,17 @@ def test_alias_rejected():
     x = torch.zeros(ctx.n_u, dtype=torch.float64, device="cuda")
     with pytest.raises(DgnsError):
         ctx.vmult_laplace(x, x, space=0)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("n,k", [((8, 8, 8), 3), ((6, 4, 4), 5)])
+def test_laplace_smooth_field(n, k, mode):
+    """Smooth input: the stiffness sweeps cancel (L u ~ h^2 |terms|), the
+    hardest case for the relative error."""
+    ctx = context(n, k, k, mg_precision=0, fp64_mode=mode)
+    s = dg.Space(dg.Mesh(n), k)
+    x = s.interpolate(lambda x, y, z: np.sin(x) * np.cos(y) * np.cos(2 * z) + 0.3)
+    ref = dg.Laplace(s).apply(x)
+    y = torch.empty(s.size, dtype=torch.float64, device="cuda")
+    ctx.vmult_laplace(y, dev(x), space=0)
+    assert rel_err(host(y), ref) <= TOL
