@@ -82,7 +82,7 @@ class ClockSampler:
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
             dev = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0"
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", dev, "--query-gpu=" + q, "--format=csv,noheader,nounits", "-lms", "100"],
+                ["nvidia-smi", "-i", dev, "--query-gpu=" + q, "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None

@@ -379,11 +379,19 @@ void free_ctx(dgns_ctx* c) {
   cudaFree(c->red.scal);
   if (c->h_scal) cudaFreeHost(c->h_scal);
   for (int i = 0; i < 4; ++i) cudaFree(c->stage[i]);
+  if (c->vc_exec) cudaGraphExecDestroy(c->vc_exec);
+  if (c->gs) cudaStreamDestroy(c->gs);
   delete c;
 }
 
 int alloc_cg(dgns_ctx* c, long long n) {
   if (n <= c->cg_cap) return 0;
+  // the captured V-cycle graph refers to the old work vectors
+  if (c->vc_exec) {
+    cudaStreamSynchronize(c->s);
+    cudaGraphExecDestroy(c->vc_exec);
+    c->vc_exec = nullptr;
+  }
   cudaFree(c->r);
   cudaFree(c->z);
   cudaFree(c->p);
@@ -473,6 +481,49 @@ int precondition(dgns_ctx* c, const double* r, double* z, const dgns_solve_param
     DG_TRY(sum(z, n, c->red, S_SUM, c->s));
     DG_TRY(convert_shift(z, false, z, false, n, &c->red, S_SUM, c->s));
   }
+  return 0;
+}
+
+// The CG preconditioner r -> z on the context's work vectors, replayed from a
+// CUDA graph: one V-cycle is ~10 launches per level, and on the coarse levels
+// launch latency dominates.  The first call for a parameter set runs eagerly
+// (it also sets kernel attributes), then captures the same sequence.
+int precondition_cg(dgns_ctx* c, const dgns_solve_params* prm, long long n) {
+  if (c->mg_prec == 0 || c->levels.empty()) return precondition(c, c->r, c->z, prm, n);
+  const bool same = c->vc_exec && c->vc_key[0] == prm->cheb_degree && c->vc_key[1] == prm->cheb_coarse_iters &&
+                    c->vc_key[2] == prm->project_mean && c->vc_range == prm->smoothing_range;
+  if (same) {
+    DG_CUDA(cudaGraphLaunch(c->vc_exec, c->s));
+    return 0;
+  }
+  DG_TRY(precondition(c, c->r, c->z, prm, n));
+  if (!c->gs) DG_CUDA(cudaStreamCreateWithFlags(&c->gs, cudaStreamNonBlocking));
+  if (c->vc_exec) {
+    cudaGraphExecDestroy(c->vc_exec);
+    c->vc_exec = nullptr;
+  }
+  cudaStream_t saved = c->s;
+  DG_CUDA(cudaStreamBeginCapture(c->gs, cudaStreamCaptureModeThreadLocal));
+  c->s = c->gs;
+  const int rc = precondition(c, c->r, c->z, prm, n);
+  c->s = saved;
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c->gs, &g);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(DGNS_ERR_CUDA, std::string("V-cycle capture: ") + cudaGetErrorString(e));
+  const cudaError_t e2 = cudaGraphInstantiate(&c->vc_exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e2 != cudaSuccess) {
+    c->vc_exec = nullptr;
+    return fail(DGNS_ERR_CUDA, std::string("V-cycle graph: ") + cudaGetErrorString(e2));
+  }
+  c->vc_key[0] = prm->cheb_degree;
+  c->vc_key[1] = prm->cheb_coarse_iters;
+  c->vc_key[2] = prm->project_mean;
+  c->vc_range = prm->smoothing_range;
   return 0;
 }
 
@@ -745,7 +796,8 @@ static int mass_like(dgns_ctx* c, double* dst, const double* src, int ncomp, int
   DG_TRY(st.in(src, bytes, &s));
   DG_TRY(st.out(dst, bytes, &d));
   const double(*T)[MAXN * MAXN] = inverse ? c->minv3[space] : c->mass3[space];
-  DG_TRY(tensor3_apply(c->N[space], c->m.E * ncomp, (const double*)s, (double*)d, T[0], T[1], T[2], c->s));
+  DG_TRY(tensor3_apply(c->N[space], c->m.E * ncomp, (const double*)s, (double*)d, T[0], T[1], T[2], c->s,
+                       c->d.fp64_mode == 1));
   return st.finish();
 }
 
@@ -768,7 +820,7 @@ int dgns_vmult_divergence(dgns_ctx* c, double* dst_p, const double* u3) {
   void* d;
   DG_TRY(st.in(u3, bu, &s));
   DG_TRY(st.out(dst_p, bp, &d));
-  DG_TRY(divergence_apply(c->m, (const double*)s, (double*)d, c->div, c->s));
+  DG_TRY(divergence_apply(c->m, (const double*)s, (double*)d, c->div, c->s, c->d.fp64_mode == 1));
   return st.finish();
 }
 
@@ -783,7 +835,7 @@ int dgns_vmult_gradient(dgns_ctx* c, double* dst3, const double* p) {
   void* d;
   DG_TRY(st.in(p, bp, &s));
   DG_TRY(st.out(dst3, bu, &d));
-  DG_TRY(gradient_apply(c->m, (const double*)s, (double*)d, c->grad, c->s));
+  DG_TRY(gradient_apply(c->m, (const double*)s, (double*)d, c->grad, c->s, c->d.fp64_mode == 1));
   return st.finish();
 }
 
@@ -986,7 +1038,7 @@ int dgns_cg_mg_solve(dgns_ctx* c, double* x, const double* b, const dgns_solve_p
     inf.rel_res = 0.0;
     if (!std::isfinite(nb)) status = fail(DGNS_ERR_NONFINITE, "non-finite right-hand side");
   } else {
-    DG_TRY(precondition(c, c->r, c->z, &prm, n));
+    DG_TRY(precondition_cg(c, &prm, n));
     DG_TRY(cg_direction(c->p, c->z, n, c->red, true, c->s));
     DG_TRY(dot(c->r, c->z, n, c->red, S_RZ, c->s));
     double res = 1.0;
@@ -1008,7 +1060,7 @@ int dgns_cg_mg_solve(dgns_ctx* c, double* x, const double* b, const dgns_solve_p
         status = DGNS_OK;
         break;
       }
-      DG_TRY(precondition(c, c->r, c->z, &prm, n));
+      DG_TRY(precondition_cg(c, &prm, n));
       DG_TRY(dot(c->r, c->z, n, c->red, S_RZNEW, c->s));
       DG_TRY(cg_direction(c->p, c->z, n, c->red, false, c->s));
     }

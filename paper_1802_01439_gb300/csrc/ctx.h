@@ -64,6 +64,12 @@ struct dgns_ctx {
   double *r = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr;
   dgns::Reducer red;
   double* h_scal = nullptr;  // pinned mirror of the scalars
+  // CUDA graph of one preconditioner application (r -> z on the CG work
+  // vectors), captured on a private stream and replayed on s
+  cudaStream_t gs = nullptr;
+  cudaGraphExec_t vc_exec = nullptr;
+  int vc_key[3] = {0, 0, 0};
+  double vc_range = 0.0;
   // staging of host pointers
   void* stage[4] = {nullptr, nullptr, nullptr, nullptr};
   size_t stage_cap[4] = {0, 0, 0, 0};

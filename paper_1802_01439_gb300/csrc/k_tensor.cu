@@ -4,6 +4,7 @@
 // the Kronecker product of the 1D inverses, three sweeps per cell), and the
 // h-multigrid transfers (embedding of a coarse cell polynomial into its eight
 // children and the transpose).
+#include "arith.cuh"
 #include "ops.h"
 
 namespace dgns {
@@ -14,9 +15,9 @@ constexpr int tcells_per_block() {
   return N * N >= 128 ? 1 : 128 / (N * N);
 }
 
-template <class T, int N>
+template <class V, int N>
 struct Tens3 {
-  T Mx[N * N], My[N * N], Mz[N * N];
+  V Mx[N * N], My[N * N], Mz[N * N];
 };
 
 template <class T, int N, int D>
@@ -29,52 +30,73 @@ __device__ __forceinline__ void sweep_line(const T* in, T* out, int l, const T* 
   store_line<T, N>(out, base, stride, y);
 }
 
-template <class T, int N>
+template <class A, int N, int D>
+__device__ __forceinline__ void sweep_line_p(const typename A::V* in, typename A::V* out, int l,
+                                             const typename A::V* M) {
+  typedef typename A::V V;
+  typedef typename A::Acc Acc;
+  int base, stride;
+  line_geom<D>(l, N, N, N, base, stride);
+  V x[N];
+  load_line<V, N>(in, base, stride, x);
+  Acc y[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    A::acc_zero(y[i]);
+#pragma unroll
+    for (int j = 0; j < N; ++j) A::acc_fma(y[i], M[i * N + j], x[j]);
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) out[base + i * stride] = A::acc_get(y[i]);
+}
+
+template <class A, int N>
 __global__ void __launch_bounds__(tcells_per_block<N>() * N * N)
-    tensor3_kernel(const T* __restrict__ src, T* __restrict__ dst, const __grid_constant__ Tens3<T, N> tb,
-                   const long long ncells) {
+    tensor3_kernel(const typename A::G* __restrict__ src, typename A::G* __restrict__ dst,
+                   const __grid_constant__ Tens3<typename A::V, N> tb, const long long ncells) {
+  typedef typename A::V V;
   constexpr int NN = N * N, NNN = NN * N, EPB = tcells_per_block<N>();
-  T* sX = reinterpret_cast<T*>(dyn_smem());
-  T* sA = sX + EPB * NNN;
+  V* sX = reinterpret_cast<V*>(dyn_smem());
+  V* sA = sX + EPB * NNN;
   const int slot = threadIdx.x / NN;
   const int l = threadIdx.x - slot * NN;
   const long long c0 = (long long)blockIdx.x * EPB;
   const long long rem = ncells - c0;
   const int nvalid = rem < EPB ? (int)rem : EPB;
-  for (int i = threadIdx.x; i < nvalid * NNN; i += blockDim.x) sX[i] = src[c0 * NNN + i];
+  for (int i = threadIdx.x; i < nvalid * NNN; i += blockDim.x) sX[i] = A::load(src + c0 * NNN + i);
   __syncthreads();
   const bool active = slot < nvalid;
   const int off = slot * NNN;
-  if (active) sweep_line<T, N, 0>(sX + off, sA + off, l, tb.Mx);
+  if (active) sweep_line_p<A, N, 0>(sX + off, sA + off, l, tb.Mx);
   __syncthreads();
-  if (active) sweep_line<T, N, 1>(sA + off, sA + off, l, tb.My);
+  if (active) sweep_line_p<A, N, 1>(sA + off, sA + off, l, tb.My);
   __syncthreads();
-  if (active) sweep_line<T, N, 2>(sA + off, sX + off, l, tb.Mz);
+  if (active) sweep_line_p<A, N, 2>(sA + off, sX + off, l, tb.Mz);
   __syncthreads();
-  for (int i = threadIdx.x; i < nvalid * NNN; i += blockDim.x) dst[c0 * NNN + i] = sX[i];
+  for (int i = threadIdx.x; i < nvalid * NNN; i += blockDim.x) dst[c0 * NNN + i] = A::store(sX[i]);
 }
 
-template <class T, int N>
-int launch_tensor3(long long ncells, const T* src, T* dst, const double* Mx, const double* My,
+template <class A, int N>
+int launch_tensor3(long long ncells, const double* src, double* dst, const double* Mx, const double* My,
                    const double* Mz, cudaStream_t s) {
   constexpr int NN = N * N, EPB = tcells_per_block<N>();
-  Tens3<T, N> tb;
+  Tens3<typename A::V, N> tb;
   for (int i = 0; i < NN; ++i) {
-    tb.Mx[i] = (T)Mx[i];
-    tb.My[i] = (T)My[i];
-    tb.Mz[i] = (T)Mz[i];
+    tb.Mx[i] = A::make(Mx[i]);
+    tb.My[i] = A::make(My[i]);
+    tb.Mz[i] = A::make(Mz[i]);
   }
   if (ncells == 0) return 0;
-  const size_t smem = (size_t)2 * EPB * NN * N * sizeof(T);
+  const size_t smem = (size_t)2 * EPB * NN * N * sizeof(double);
   static bool attr_done = false;
   if (!attr_done) {
-    if (cudaFuncSetAttribute(tensor3_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(tensor3_kernel<A, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
       return 2;
     attr_done = true;
   }
   const long long blocks = (ncells + EPB - 1) / EPB;
-  tensor3_kernel<T, N><<<(unsigned)blocks, EPB * NN, smem, s>>>(src, dst, tb, ncells);
+  tensor3_kernel<A, N><<<(unsigned)blocks, EPB * NN, smem, s>>>(src, dst, tb, ncells);
   return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }
 
@@ -270,8 +292,9 @@ int launch_restrict(const MeshDims& mc, const T* fine, T* coarse, const double* 
   }
 
 int tensor3_apply(int N, long long ncells, const double* src, double* dst, const double* Mx,
-                  const double* My, const double* Mz, cudaStream_t s) {
-  DGNS_SWITCH_N(N, return launch_tensor3<double, NC>(ncells, src, dst, Mx, My, Mz, s))
+                  const double* My, const double* Mz, cudaStream_t s, bool emulated) {
+  DGNS_SWITCH_N(N, return emulated ? launch_tensor3<DF64, NC>(ncells, src, dst, Mx, My, Mz, s)
+                                   : launch_tensor3<F64, NC>(ncells, src, dst, Mx, My, Mz, s))
   return 7;
 }
 

@@ -46,7 +46,7 @@ int broadcast_cells(bool fp32, long long ncells, int nper, const void* table, vo
 // dst = (Mz (x) My (x) Mx) src per cell, square N x N matrices (mass,
 // inverse mass).  double only.
 int tensor3_apply(int N, long long ncells, const double* src, double* dst, const double* Mx,
-                  const double* My, const double* Mz, cudaStream_t s);
+                  const double* My, const double* Mz, cudaStream_t s, bool emulated = false);
 
 // Multigrid transfers between a coarse mesh mc and the fine mesh 2*mc.
 // prolongate: fine (+)= P coarse; restrict: coarse = P^T fine.
@@ -63,7 +63,7 @@ struct DivHost {
   double nbr[3], nbl[3];       // neighbour face-value coefficients
 };
 int divergence_apply(const MeshDims& m, const double* u3, double* dst, const DivHost& t,
-                     cudaStream_t s);
+                     cudaStream_t s, bool emulated = false);
 struct GradHost {
   int Nu = 0, Np = 0;
   double G[3][MAXN * MAXN];    // Nu x Np
@@ -71,7 +71,7 @@ struct GradHost {
   double nbr[3], nbl[3];
 };
 int gradient_apply(const MeshDims& m, const double* p, double* dst3, const GradHost& t,
-                   cudaStream_t s);
+                   cudaStream_t s, bool emulated = false);
 
 // Convective term with local Lax-Friedrichs flux (k_convective.cu).
 struct ConvHost {

@@ -63,9 +63,10 @@ def test_laplace_pressure_space():
     assert rel_err(host(y), dg.Laplace(s).apply(x)) <= TOL
 
 
+@pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("n,k,kw", LAP_CASES[:6])
-def test_mass_and_inverse(n, k, kw):
-    ctx = context(n, k, k, mg_precision=0, **kw)
+def test_mass_and_inverse(n, k, kw, mode):
+    ctx = context(n, k, k, mg_precision=0, fp64_mode=mode, **kw)
     s = dg.Space(_mesh(n, kw), k)
     M = dg.Mass(s)
     for ncomp in (1, 3):
@@ -92,10 +93,11 @@ def test_viscous_and_helmholtz(n, k, mode):
     assert rel_err(host(y), dg.Helmholtz(s, nu, mf).apply(u)) <= TOL
 
 
+@pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("n,ku", [((3, 2, 4), 3), ((2, 2, 2), 5), ((1, 2, 3), 2), ((2, 1, 1), 11),
                                   ((4, 4, 4), 4)])
-def test_divergence_gradient(n, ku):
-    ctx = context(n, ku, mg_precision=0)
+def test_divergence_gradient(n, ku, mode):
+    ctx = context(n, ku, mg_precision=0, fp64_mode=mode)
     m = dg.Mesh(n)
     su, sp = dg.Space(m, ku), dg.Space(m, ku - 1)
     u = random_field(su, 3, 4)
