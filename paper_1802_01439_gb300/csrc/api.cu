@@ -593,6 +593,8 @@ int dgns_create(const dgns_mesh_desc* desc, void* stream, dgns_ctx** out) {
   if (d.mg_precision != 0 && d.mg_precision != 32 && d.mg_precision != 64)
     return fail(DGNS_ERR_INVALID_ARG, "mg_precision must be 0, 32 or 64");
   if (d.fp64_mode != 0 && d.fp64_mode != 1) return fail(DGNS_ERR_INVALID_ARG, "fp64_mode must be 0 or 1");
+  if ((long long)d.n_elem[0] * d.n_elem[1] * d.n_elem[2] * 3 >= (1LL << 31))
+    return fail(DGNS_ERR_UNSUPPORTED, "meshes with 3 * cells >= 2^31 are not supported");
   const int Q = d.n_q_conv > 0 ? d.n_q_conv : (3 * (d.degree + 1)) / 2;
   if (Q != (3 * (d.degree + 1)) / 2 && Q != d.degree + 1)
     return fail(DGNS_ERR_UNSUPPORTED, "n_q_conv must be floor(3(k+1)/2) or k+1");

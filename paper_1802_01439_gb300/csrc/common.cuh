@@ -54,6 +54,45 @@ __device__ __forceinline__ long long neighbor(long long el, int ex, int ey, int 
   }
 }
 
+// Cell coordinates with 32-bit integer arithmetic (64-bit division is a long
+// integer sequence on the GPU; the library rejects meshes with 2^31 or more
+// cells in all components together).
+struct CellXYZ {
+  unsigned el;    // cell id within its component
+  unsigned comp;  // component
+  int ex, ey, ez;
+};
+
+__device__ __forceinline__ CellXYZ cell_xyz(unsigned cell, const MeshDims& m) {
+  CellXYZ c;
+  const unsigned E = (unsigned)m.E, nx = (unsigned)m.nx, ny = (unsigned)m.ny;
+  c.comp = cell / E;
+  c.el = cell - c.comp * E;
+  const unsigned t = c.el / nx;
+  c.ex = (int)(c.el - t * nx);
+  c.ez = (int)(t / ny);
+  c.ey = (int)(t - (unsigned)c.ez * ny);
+  return c;
+}
+
+// Periodic neighbour (cell id within the component) along direction D.
+template <int D>
+__device__ __forceinline__ unsigned neighbor32(const CellXYZ& c, int sgn, const MeshDims& m) {
+  if (D == 0) {
+    int v = c.ex + sgn;
+    v = v < 0 ? m.nx - 1 : (v >= m.nx ? 0 : v);
+    return c.el + (unsigned)(v - c.ex);
+  } else if (D == 1) {
+    int v = c.ey + sgn;
+    v = v < 0 ? m.ny - 1 : (v >= m.ny ? 0 : v);
+    return c.el + (unsigned)((v - c.ey) * m.nx);
+  } else {
+    int v = c.ez + sgn;
+    v = v < 0 ? m.nz - 1 : (v >= m.nz ? 0 : v);
+    return c.el + (unsigned)((v - c.ez) * m.nx * m.ny);
+  }
+}
+
 // y[i] = sum_j A[i*NI + j] x[j]   (A row-major NO x NI)
 template <class T, int NO, int NI>
 __device__ __forceinline__ void matvec(const T* A, const T (&x)[NI], T (&y)[NO]) {

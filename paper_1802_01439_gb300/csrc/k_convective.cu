@@ -35,6 +35,17 @@ struct ConvTab {
   double area[3];  // product of the tangential cell sizes of faces normal to d
 };
 
+// Threads per cell of the forward convective kernel: at least one warp, so
+// that the many small work items of a phase are spread over more lanes.
+template <int N>
+constexpr int conv_threads() {
+  return N * N < 32 ? 32 : N * N;
+}
+template <int N>
+constexpr int conv_fwd_cells_per_block() {
+  return conv_threads<N>() >= 128 ? 1 : 128 / conv_threads<N>();
+}
+
 template <int N, int Q>
 struct ConvLayout {
   static constexpr int N3 = N * N * N;
@@ -44,7 +55,7 @@ struct ConvLayout {
   static constexpr int P = 6 * Q * Q;            // one z-plane: u and the weighted u
   static constexpr int X = 9 * N * Q;            // x-tested plane
   static constexpr int Y = 6 * N * N;            // xy-tested plane
-  static constexpr int FACE = 6 * Q * N + 6 * Q * Q + 3 * Q * Q;
+  static constexpr int FACE = 6 * N * N + 6 * Q * N + 6 * Q * Q + 3 * Q * Q;
   static constexpr int U2F = U2 > FACE ? U2 : FACE;
   static constexpr int PXY = P + X + Y;
   static constexpr int UP = U > PXY ? U : PXY;   // nodal u first, plane work later
@@ -69,18 +80,20 @@ struct ConvTabT {
 };
 
 // Forward convective kernel for an arithmetic policy A (F64 or DF64): loads
-// and stores are double; all arithmetic is A's.  Loops over Gauss points are
-// kept rolled (inner loops over the node index stay unrolled): fully unrolled
-// double-float code overflows the instruction cache.
+// and stores are double; all arithmetic is A's.  Every phase is split into
+// small independent work items (one output or one short line of outputs)
+// spread over the cell's threads; the 1D tables are copied to shared memory
+// because the items index them by thread.
 template <class A, int N, int Q>
-__global__ void __launch_bounds__(conv_cells_per_block<N>() * N * N)
+__global__ void __launch_bounds__(conv_fwd_cells_per_block<N>() * conv_threads<N>())
     conv_kernel(const double* __restrict__ u3, double* __restrict__ dst3,
                 const __grid_constant__ ConvTabT<typename A::V, N, Q> tb, const MeshDims m) {
   typedef typename A::V V;
   typedef typename A::Acc Acc;
   typedef ConvLayout<N, Q> LY;
   static_assert(sizeof(V) == sizeof(double), "8-byte values");
-  constexpr int NT = N * N, N3 = N * N * N, EPB = conv_cells_per_block<N>();
+  constexpr int NT = conv_threads<N>(), N3 = N * N * N, EPB = conv_fwd_cells_per_block<N>();
+  constexpr int QQ = Q * Q, NN = N * N;
   V* sm = reinterpret_cast<V*>(dyn_smem());
   const int slot = threadIdx.x / NT;
   const int t = threadIdx.x - slot * NT;
@@ -88,8 +101,8 @@ __global__ void __launch_bounds__(conv_cells_per_block<N>() * N * N)
   const long long rem = m.E - c0;
   const int nvalid = rem < EPB ? (int)rem : EPB;
   const bool active = slot < nvalid;
-  V* sS = sm + EPB * LY::PER;    // copies of the 1D tables (work items that
-  V* sD = sS + Q * N;            // index them by thread read shared memory)
+  V* sS = sm + EPB * LY::PER;
+  V* sD = sS + Q * N;
   for (int i = threadIdx.x; i < Q * N; i += blockDim.x) {
     sS[i] = tb.S[i];
     sD[i] = tb.D[i];
@@ -103,79 +116,64 @@ __global__ void __launch_bounds__(conv_cells_per_block<N>() * N * N)
   V* sOut = sU1;   // reused after the interpolation
   V* sFace = sU2;  // reused after the cell term
 
-  long long el = 0;
-  int ex = 0, ey = 0, ez = 0;
+  unsigned el = 0;
+  CellXYZ cx{};
   if (active) {
-    el = c0 + slot;
-    ex = (int)(el % m.nx);
-    const long long tt = el / m.nx;
-    ey = (int)(tt % m.ny);
-    ez = (int)(tt / m.ny);
+    cx = cell_xyz((unsigned)(c0 + slot), m);
+    el = cx.el;
     for (int c = 0; c < 3; ++c)
-      for (int i = t; i < N3; i += NT) sU[c * N3 + i] = A::from_double(u3[(c * m.E + el) * N3 + i]);
+      for (int i = t; i < N3; i += NT) sU[c * N3 + i] = A::load(u3 + ((size_t)c * m.E + el) * N3 + i);
   }
   __syncthreads();
-  // interpolation along x: (N,N,N) -> (Q,N,N)
+  // x interpolation: item (c, line (y,z), q)
   if (active)
-    for (int it = t; it < 3 * N * N; it += NT) {
-      const int c = it / (N * N), l = it - c * N * N;
-      V x[N];
-      load_line<V, N>(sU + c * N3, l * N, 1, x);
-#pragma unroll 1
-      for (int q = 0; q < Q; ++q) {
-        Acc a;
-        A::acc_zero(a);
+    for (int it = t; it < 3 * NN * Q; it += NT) {
+      const int q = it % Q, r = it / Q;
+      const int c = r / NN, l = r - c * NN;
+      const V* x = sU + c * N3 + l * N;
+      Acc a;
+      A::acc_zero(a);
 #pragma unroll
-        for (int j = 0; j < N; ++j) A::acc_fma(a, tb.S[q * N + j], x[j]);
-        sU1[c * Q * N * N + l * Q + q] = A::acc_get(a);
-      }
+      for (int j = 0; j < N; ++j) A::acc_fma(a, sS[q * N + j], x[j]);
+      sU1[c * Q * NN + l * Q + q] = A::acc_get(a);
     }
   __syncthreads();
-  // interpolation along y: (Q,N,N) -> (Q,Q,N)
+  // y interpolation: item (c, qx, z, qy)
   if (active)
-    for (int it = t; it < 3 * Q * N; it += NT) {
-      const int c = it / (Q * N), l = it - c * Q * N;
+    for (int it = t; it < 3 * Q * N * Q; it += NT) {
+      const int qy = it % Q, r = it / Q;
+      const int c = r / (Q * N), l = r - c * Q * N;
       const int qx = l % Q, z = l / Q;
-      V x[N];
-      load_line<V, N>(sU1 + c * Q * N * N, qx + Q * N * z, Q, x);
-#pragma unroll 1
-      for (int q = 0; q < Q; ++q) {
-        Acc a;
-        A::acc_zero(a);
+      const V* x = sU1 + c * Q * NN + qx + Q * N * z;
+      Acc a;
+      A::acc_zero(a);
 #pragma unroll
-        for (int j = 0; j < N; ++j) A::acc_fma(a, tb.S[q * N + j], x[j]);
-        sU2[c * Q * Q * N + qx + Q * q + Q * Q * z] = A::acc_get(a);
-      }
+      for (int j = 0; j < N; ++j) A::acc_fma(a, sS[qy * N + j], x[Q * j]);
+      sU2[c * QQ * N + qx + Q * qy + QQ * z] = A::acc_get(a);
     }
   __syncthreads();
-
-  Acc acc[3][N];
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int z = 0; z < N; ++z) A::acc_zero(acc[c][z]);
-  const int tx = t % N, ty = t / N;
+  if (active)
+    for (int i = t; i < 3 * N3; i += NT) sOut[i] = A::zero();
 
   for (int qz = 0; qz < Q; ++qz) {
-    // P1: u and the weighted u_d w_qx w_qy w_qz h_x h_y h_z / h_d on the
-    // plane z = g_qz
+    // P1: u and the weighted u_d w_qx w_qy w_qz h_x h_y h_z / h_d on the plane
     if (active)
-      for (int it = t; it < 3 * Q * Q; it += NT) {
-        const int c = it / (Q * Q), l = it - c * Q * Q;
-        const V* src = sU2 + c * Q * Q * N + l;
+      for (int it = t; it < 3 * QQ; it += NT) {
+        const int c = it / QQ, l = it - c * QQ;
+        const V* src = sU2 + c * QQ * N + l;
         Acc a;
         A::acc_zero(a);
 #pragma unroll
-        for (int z = 0; z < N; ++z) A::acc_fma(a, tb.S[qz * N + z], src[Q * Q * z]);
+        for (int z = 0; z < N; ++z) A::acc_fma(a, sS[qz * N + z], src[QQ * z]);
         const V u = A::acc_get(a);
         const int qx = l % Q, qy = l / Q;
         const V w3 = A::mul(A::mul(tb.w[qx], tb.w[qy]), tb.w[qz]);
         sP[it] = u;
-        sP[3 * Q * Q + it] = A::mul(A::mul(w3, tb.jac[c]), u);
+        sP[3 * QQ + it] = A::mul(A::mul(w3, tb.jac[c]), u);
       }
     __syncthreads();
-    // P2: flux F_cd = u_c (weighted u_d) on x-lines, tested with D_x^T (d = x)
-    // or S_x^T (d = y, z); one work item per (c, d, qy)
+    // P2: F_cd = u_c (weighted u_d) on x-lines, tested with D_x^T (d = x) or
+    // S_x^T; item (c, d, qy)
     if (active)
       for (int it = t; it < 9 * Q; it += NT) {
         const int cd = it / Q, qy = it - cd * Q;
@@ -187,7 +185,7 @@ __global__ void __launch_bounds__(conv_cells_per_block<N>() * N * N)
 #pragma unroll 1
         for (int qx = 0; qx < Q; ++qx) {
           const int pt = qx + Q * qy;
-          const V f = A::mul(sP[c * Q * Q + pt], sP[(3 + d) * Q * Q + pt]);
+          const V f = A::mul(sP[c * QQ + pt], sP[(3 + d) * QQ + pt]);
 #pragma unroll
           for (int x = 0; x < N; ++x) A::acc_fma(a[x], T[qx * N + x], f);
         }
@@ -195,119 +193,101 @@ __global__ void __launch_bounds__(conv_cells_per_block<N>() * N * N)
         for (int x = 0; x < N; ++x) sX[cd * N * Q + x + N * qy] = A::acc_get(a[x]);
       }
     __syncthreads();
-    // P3: y tests: Y1 = S_y^T X1 + D_y^T X2, Y3 = S_y^T X3
+    // P3: Y1 = S_y^T X1 + D_y^T X2, Y3 = S_y^T X3; item (c, x, y)
     if (active)
-      for (int it = t; it < 3 * N; it += NT) {
-        const int c = it / N, x = it - c * N;
-        Acc y1[N], y3[N];
-#pragma unroll
-        for (int y = 0; y < N; ++y) {
-          A::acc_zero(y1[y]);
-          A::acc_zero(y3[y]);
-        }
+      for (int it = t; it < 3 * NN; it += NT) {
+        const int c = it / NN, r = it - c * NN;
+        const int x = r % N, y = r / N;
+        Acc y1, y3;
+        A::acc_zero(y1);
+        A::acc_zero(y3);
 #pragma unroll 1
         for (int qy = 0; qy < Q; ++qy) {
-          const V b1 = sX[(c * 3 + 0) * N * Q + x + N * qy];
-          const V b2 = sX[(c * 3 + 1) * N * Q + x + N * qy];
-          const V b3 = sX[(c * 3 + 2) * N * Q + x + N * qy];
-#pragma unroll
-          for (int y = 0; y < N; ++y) {
-            A::acc_fma(y1[y], tb.D[qy * N + y], b2);
-            A::acc_fma(y1[y], tb.S[qy * N + y], b1);
-            A::acc_fma(y3[y], tb.S[qy * N + y], b3);
-          }
+          const int o = x + N * qy;
+          A::acc_fma(y1, sD[qy * N + y], sX[(c * 3 + 1) * N * Q + o]);
+          A::acc_fma(y1, sS[qy * N + y], sX[(c * 3 + 0) * N * Q + o]);
+          A::acc_fma(y3, sS[qy * N + y], sX[(c * 3 + 2) * N * Q + o]);
         }
-#pragma unroll
-        for (int y = 0; y < N; ++y) {
-          sY[(c * 2 + 0) * N * N + x + N * y] = A::acc_get(y1[y]);
-          sY[(c * 2 + 1) * N * N + x + N * y] = A::acc_get(y3[y]);
-        }
+        sY[(c * 2 + 0) * NN + r] = A::acc_get(y1);
+        sY[(c * 2 + 1) * NN + r] = A::acc_get(y3);
       }
     __syncthreads();
-    // P4: z test accumulated in registers: acc -= S_z(qz) Y1 + D_z(qz) Y3
-    if (active) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const V y1 = sY[(c * 2 + 0) * N * N + tx + N * ty];
-        const V y3 = sY[(c * 2 + 1) * N * N + tx + N * ty];
-#pragma unroll
-        for (int z = 0; z < N; ++z) {
-          A::acc_fma(acc[c][z], A::neg(tb.D[qz * N + z]), y3);
-          A::acc_fma(acc[c][z], A::neg(tb.S[qz * N + z]), y1);
-        }
+    // P4: out -= S_z(qz) Y1 + D_z(qz) Y3; item (c, x, y, z)
+    if (active)
+      for (int it = t; it < 3 * N3; it += NT) {
+        const int c = it / N3, r = it - c * N3;
+        const int xy = r % NN, z = r / NN;
+        Acc a;
+        A::acc_set(a, sOut[it]);
+        A::acc_fma(a, A::neg(sD[qz * N + z]), sY[(c * 2 + 1) * NN + xy]);
+        A::acc_fma(a, A::neg(sS[qz * N + z]), sY[(c * 2 + 0) * NN + xy]);
+        sOut[it] = A::acc_get(a);
       }
-    }
-  }
-  __syncthreads();
-  if (active) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int z = 0; z < N; ++z) sOut[c * N3 + tx + N * ty + N * N * z] = A::acc_get(acc[c][z]);
   }
   __syncthreads();
 
   // ---------------------------------------------------------------- faces
-  V* G1 = sFace;              // [side][c][q1 + Q j2]   6 Q N
+  V* T0 = sFace;              // [side][c][j1 + N j2]   6 N N
+  V* G1 = T0 + 6 * NN;        // [side][c][q1 + Q j2]   6 Q N
   V* G2 = G1 + 6 * Q * N;     // [side][c][q1 + Q q2]   6 Q Q
-  V* H = G2 + 6 * Q * Q;      // [c][q1 + Q q2]         3 Q Q
+  V* H = G2 + 6 * QQ;         // [c][q1 + Q q2]         3 Q Q
   V* K1 = G1;                 // [c][q1 + Q j2] reuses G1
   for (int d = 0; d < 3; ++d) {
     const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
     for (int side = 1; side >= -1; side -= 2) {
-      long long nb = 0;
+      unsigned nb = 0;
       if (active) {
-        if (d == 0) nb = neighbor<0>(el, ex, ey, ez, side, m);
-        else if (d == 1) nb = neighbor<1>(el, ex, ey, ez, side, m);
-        else nb = neighbor<2>(el, ex, ey, ez, side, m);
+        if (d == 0) nb = neighbor32<0>(cx, side, m);
+        else if (d == 1) nb = neighbor32<1>(cx, side, m);
+        else nb = neighbor32<2>(cx, side, m);
       }
       const int aown = side > 0 ? N - 1 : 0, anb = side > 0 ? 0 : N - 1;
-      // F1: interpolate both traces along t1
+      // F0: the face layers of both cells
       if (active)
-        for (int it = t; it < 6 * N; it += NT) {
-          const int s = it / (3 * N), c = (it / N) % 3, j2 = it % N;
-          V v[N];
-#pragma unroll
-          for (int j1 = 0; j1 < N; ++j1)
-            v[j1] = A::from_double(s == 0 ? __ldg(u3 + (c * m.E + el) * N3 + node3(N, d, aown, t1, j1, t2, j2))
-                                          : __ldg(u3 + (c * m.E + nb) * N3 + node3(N, d, anb, t1, j1, t2, j2)));
-#pragma unroll 1
-          for (int q1 = 0; q1 < Q; ++q1) {
-            Acc a;
-            A::acc_zero(a);
-#pragma unroll
-            for (int j = 0; j < N; ++j) A::acc_fma(a, tb.S[q1 * N + j], v[j]);
-            G1[(s * 3 + c) * Q * N + q1 + Q * j2] = A::acc_get(a);
-          }
+        for (int it = t; it < 6 * NN; it += NT) {
+          const int sc = it / NN, r = it - sc * NN;
+          const int s = sc / 3, c = sc - 3 * s;
+          const int j1 = r % N, j2 = r / N;
+          T0[it] = s == 0 ? A::load(u3 + ((size_t)c * m.E + el) * N3 + node3(N, d, aown, t1, j1, t2, j2))
+                          : A::load(u3 + ((size_t)c * m.E + nb) * N3 + node3(N, d, anb, t1, j1, t2, j2));
         }
       __syncthreads();
-      // F2: along t2
+      // F1: along t1; item (sc, j2, q1)
       if (active)
-        for (int it = t; it < 6 * Q; it += NT) {
-          const int sc = it / Q, q1 = it - sc * Q;
-          V v[N];
+        for (int it = t; it < 6 * N * Q; it += NT) {
+          const int q1 = it % Q, r = it / Q;
+          const int sc = r / N, j2 = r - sc * N;
+          const V* v = T0 + sc * NN + N * j2;
+          Acc a;
+          A::acc_zero(a);
 #pragma unroll
-          for (int j2 = 0; j2 < N; ++j2) v[j2] = G1[sc * Q * N + q1 + Q * j2];
-#pragma unroll 1
-          for (int q2 = 0; q2 < Q; ++q2) {
-            Acc a;
-            A::acc_zero(a);
+          for (int j = 0; j < N; ++j) A::acc_fma(a, sS[q1 * N + j], v[j]);
+          G1[sc * Q * N + q1 + Q * j2] = A::acc_get(a);
+        }
+      __syncthreads();
+      // F2: along t2; item (sc, q1, q2)
+      if (active)
+        for (int it = t; it < 6 * QQ; it += NT) {
+          const int q2 = it % Q, r = it / Q;
+          const int sc = r / Q, q1 = r - sc * Q;
+          const V* v = G1 + sc * Q * N + q1;
+          Acc a;
+          A::acc_zero(a);
 #pragma unroll
-            for (int j = 0; j < N; ++j) A::acc_fma(a, tb.S[q2 * N + j], v[j]);
-            G2[sc * Q * Q + q1 + Q * q2] = A::acc_get(a);
-          }
+          for (int j = 0; j < N; ++j) A::acc_fma(a, sS[q2 * N + j], v[Q * j]);
+          G2[sc * QQ + q1 + Q * q2] = A::acc_get(a);
         }
       __syncthreads();
       // F3: LLF flux at the face points, weighted, signed for the own cell
       if (active)
-        for (int it = t; it < Q * Q; it += NT) {
+        for (int it = t; it < QQ; it += NT) {
           const int q1 = it % Q, q2 = it / Q;
           const int sm_ = side > 0 ? 0 : 1, sp_ = side > 0 ? 1 : 0;  // trace index of '-' / '+'
           V um[3], up[3];
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            um[c] = G2[(sm_ * 3 + c) * Q * Q + it];
-            up[c] = G2[(sp_ * 3 + c) * Q * Q + it];
+            um[c] = G2[(sm_ * 3 + c) * QQ + it];
+            up[c] = G2[(sp_ * 3 + c) * QQ + it];
           }
           const V unm = um[d], unp = up[d];
           const V am = A::absval(unm), ap = A::absval(unp);
@@ -323,44 +303,40 @@ __global__ void __launch_bounds__(conv_cells_per_block<N>() * N * N)
             A::acc_fma(f, um[c], hm);
             A::acc_fma(f, up[c], hp);
             A::acc_fma(f, lam, A::sub(um[c], up[c]));
-            H[c * Q * Q + it] = A::mul(wgt, A::acc_get(f));
+            H[c * QQ + it] = A::mul(wgt, A::acc_get(f));
           }
         }
       __syncthreads();
-      // F4: test along t2; one work item per (c, q1, j2)
+      // F4: test along t2; item (c, j2, q1)
       if (active)
         for (int it = t; it < 3 * Q * N; it += NT) {
-          const int c = it / (Q * N), r = it - c * Q * N;
-          const int j2 = r / Q, q1 = r - j2 * Q;
+          const int q1 = it % Q, r = it / Q;
+          const int c = r / N, j2 = r - c * N;
           Acc a;
           A::acc_zero(a);
 #pragma unroll 1
-          for (int q2 = 0; q2 < Q; ++q2) A::acc_fma(a, sS[q2 * N + j2], H[c * Q * Q + q1 + Q * q2]);
+          for (int q2 = 0; q2 < Q; ++q2) A::acc_fma(a, sS[q2 * N + j2], H[c * QQ + q1 + Q * q2]);
           K1[c * Q * N + q1 + Q * j2] = A::acc_get(a);
         }
       __syncthreads();
-      // F5: test along t1, add into the own face layer
+      // F5: test along t1, add into the own face layer; item (c, j2, j1)
       if (active)
-        for (int it = t; it < 3 * N; it += NT) {
-          const int c = it / N, j2 = it - c * N;
-          Acc a[N];
-#pragma unroll
-          for (int j1 = 0; j1 < N; ++j1) A::acc_set(a[j1], sOut[c * N3 + node3(N, d, aown, t1, j1, t2, j2)]);
+        for (int it = t; it < 3 * NN; it += NT) {
+          const int c = it / NN, r = it - c * NN;
+          const int j1 = r % N, j2 = r / N;
+          const int node = c * N3 + node3(N, d, aown, t1, j1, t2, j2);
+          Acc a;
+          A::acc_set(a, sOut[node]);
 #pragma unroll 1
-          for (int q1 = 0; q1 < Q; ++q1) {
-            const V h = K1[c * Q * N + q1 + Q * j2];
-#pragma unroll
-            for (int j = 0; j < N; ++j) A::acc_fma(a[j], tb.S[q1 * N + j], h);
-          }
-#pragma unroll
-          for (int j1 = 0; j1 < N; ++j1) sOut[c * N3 + node3(N, d, aown, t1, j1, t2, j2)] = A::acc_get(a[j1]);
+          for (int q1 = 0; q1 < Q; ++q1) A::acc_fma(a, sS[q1 * N + j1], K1[c * Q * N + q1 + Q * j2]);
+          sOut[node] = A::acc_get(a);
         }
       __syncthreads();
     }
   }
   if (active)
     for (int c = 0; c < 3; ++c)
-      for (int i = t; i < N3; i += NT) dst3[(c * m.E + el) * N3 + i] = A::to_double(sOut[c * N3 + i]);
+      for (int i = t; i < N3; i += NT) dst3[((size_t)c * m.E + el) * N3 + i] = A::store(sOut[c * N3 + i]);
 }
 
 template <class A, int N, int Q>
@@ -376,7 +352,7 @@ int launch_conv(const MeshDims& m, const double* u3, double* dst3, const ConvHos
     tb.jac[d] = A::make(j);
     tb.area[d] = A::make(j);
   }
-  constexpr int EPB = conv_cells_per_block<N>();
+  constexpr int EPB = conv_fwd_cells_per_block<N>();
   const size_t smem = ((size_t)EPB * ConvLayout<N, Q>::PER + 2 * Q * N) * sizeof(double);
   if (smem > 232448) return 7;
   if (cudaFuncSetAttribute(conv_kernel<A, N, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
@@ -384,7 +360,7 @@ int launch_conv(const MeshDims& m, const double* u3, double* dst3, const ConvHos
     return 2;
   if (m.E == 0) return 0;
   const long long blocks = (m.E + EPB - 1) / EPB;
-  conv_kernel<A, N, Q><<<(unsigned)blocks, EPB * N * N, smem, s>>>(u3, dst3, tb, m);
+  conv_kernel<A, N, Q><<<(unsigned)blocks, EPB * conv_threads<N>(), smem, s>>>(u3, dst3, tb, m);
   return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }
 

@@ -45,6 +45,41 @@ constexpr int cells_per_block() {
   return N * N >= 128 ? 1 : 128 / (N * N);
 }
 
+// Shared-memory layout of a staged cell: x-lines padded to an odd length so
+// that the line-per-thread accesses of all three directions hit distinct banks
+// (a cell of N = 4 floats: x-lines of stride 5, cell stride 80).
+template <int N>
+constexpr int padx() {
+  return (N % 2 == 0) ? N + 1 : N;
+}
+template <int N>
+constexpr int cell_stride() {
+  return padx<N>() * N * N;
+}
+template <int N, int D>
+__device__ __forceinline__ void sline(int l, int& base, int& stride) {
+  constexpr int P = padx<N>();
+  if (D == 0) {          // l = y + N z
+    base = l * P;
+    stride = 1;
+  } else if (D == 1) {   // l = x + N z
+    const int x = l % N, z = l / N;
+    base = x + P * N * z;
+    stride = P;
+  } else {               // l = x + N y
+    const int x = l % N, y = l / N;
+    base = x + P * y;
+    stride = P * N;
+  }
+}
+// Padded position of entry i of the block's contiguous cells.
+template <int N>
+__device__ __forceinline__ int spos(int i) {
+  constexpr int NNN = N * N * N;
+  const int cell = i / NNN, r = i - cell * NNN;
+  return cell * cell_stride<N>() + (r % N) + padx<N>() * (r / N);
+}
+
 // One line of T_d x for the own cell, with the neighbour terms.
 template <class A, int N, int D>
 __device__ __forceinline__ void sipg_line(const typename A::V* X, typename A::V* out,
@@ -53,15 +88,16 @@ __device__ __forceinline__ void sipg_line(const typename A::V* X, typename A::V*
                                           const LapTab<typename A::V, N>& tb) {
   typedef typename A::V V;
   typedef typename A::Acc Acc;
-  int base, stride;
-  line_geom<D>(l, N, N, N, base, stride);
+  int base, stride, gbase, gstride;
+  sline<N, D>(l, base, stride);
+  line_geom<D>(l, N, N, N, gbase, gstride);
   V x[N], r[N], lf[N];
   Acc y[N];
   load_line<V, N>(X, base, stride, x);
 #pragma unroll
   for (int j = 0; j < N; ++j) {
-    r[j] = A::load(nbR + base + j * stride);
-    lf[j] = A::load(nbL + base + j * stride);
+    r[j] = A::load(nbR + gbase + j * gstride);
+    lf[j] = A::load(nbL + gbase + j * gstride);
   }
 #pragma unroll
   for (int i = 0; i < N; ++i) {
@@ -88,7 +124,7 @@ __device__ __forceinline__ void sipg_line_pre(const typename A::V* X, typename A
   typedef typename A::V V;
   typedef typename A::Acc Acc;
   int base, stride;
-  line_geom<D>(l, N, N, N, base, stride);
+  sline<N, D>(l, base, stride);
   V x[N];
   Acc y[N];
   load_line<V, N>(X, base, stride, x);
@@ -137,7 +173,7 @@ __device__ __forceinline__ void mass_line(const typename A::V* in, const typenam
   typedef typename A::V V;
   typedef typename A::Acc Acc;
   int base, stride;
-  line_geom<D>(l, N, N, N, base, stride);
+  sline<N, D>(l, base, stride);
   V x[N];
   Acc y[N];
   load_line<V, N>(in, base, stride, x);
@@ -162,10 +198,11 @@ __global__ void __launch_bounds__(cells_per_block<N>() * N * N)
   typedef typename A::V V;
   typedef typename A::G G;
   constexpr int NN = N * N, NNN = NN * N, EPB = cells_per_block<N>();
+  constexpr int CS = cell_stride<N>();
   V* sX = reinterpret_cast<V*>(dyn_smem());
-  V* sA = sX + EPB * NNN;
-  V* sB = sA + EPB * NNN;
-  V* sC = sB + EPB * NNN;
+  V* sA = sX + EPB * CS;
+  V* sB = sA + EPB * CS;
+  V* sC = sB + EPB * CS;
   const int slot = threadIdx.x / NN;
   const int l = threadIdx.x - slot * NN;
   const long long c0 = (long long)blockIdx.x * EPB;
@@ -173,23 +210,17 @@ __global__ void __launch_bounds__(cells_per_block<N>() * N * N)
   const int nvalid = rem < EPB ? (int)rem : EPB;
   const G* gsrc = src + c0 * NNN;
   const bool active = slot < nvalid;
-  const int off = slot * NNN;
+  const int off = slot * CS;
   const G* nb[6] = {src, src, src, src, src, src};   // +x, -x, +y, -y, +z, -z
   if (active) {
-    const long long cell = c0 + slot;
-    const long long comp = cell / m.E;
-    const long long el = cell - comp * m.E;
-    const int ex = (int)(el % m.nx);
-    const long long t = el / m.nx;
-    const int ey = (int)(t % m.ny);
-    const int ez = (int)(t / m.ny);
-    const G* cb = src + comp * m.E * NNN;
-    nb[0] = cb + neighbor<0>(el, ex, ey, ez, +1, m) * NNN;
-    nb[1] = cb + neighbor<0>(el, ex, ey, ez, -1, m) * NNN;
-    nb[2] = cb + neighbor<1>(el, ex, ey, ez, +1, m) * NNN;
-    nb[3] = cb + neighbor<1>(el, ex, ey, ez, -1, m) * NNN;
-    nb[4] = cb + neighbor<2>(el, ex, ey, ez, +1, m) * NNN;
-    nb[5] = cb + neighbor<2>(el, ex, ey, ez, -1, m) * NNN;
+    const CellXYZ cx = cell_xyz((unsigned)(c0 + slot), m);
+    const G* cb = src + (size_t)cx.comp * (size_t)m.E * NNN;
+    nb[0] = cb + (size_t)neighbor32<0>(cx, +1, m) * NNN;
+    nb[1] = cb + (size_t)neighbor32<0>(cx, -1, m) * NNN;
+    nb[2] = cb + (size_t)neighbor32<1>(cx, +1, m) * NNN;
+    nb[3] = cb + (size_t)neighbor32<1>(cx, -1, m) * NNN;
+    nb[4] = cb + (size_t)neighbor32<2>(cx, +1, m) * NNN;
+    nb[5] = cb + (size_t)neighbor32<2>(cx, -1, m) * NNN;
   }
   if constexpr (prefetch_neighbours<N>()) {
     V r0[N], l0[N], r1[N], l1[N], r2[N], l2[N];
@@ -198,7 +229,7 @@ __global__ void __launch_bounds__(cells_per_block<N>() * N * N)
       load_nb_lines<A, N, 1>(nb[2], nb[3], l, r1, l1);
       load_nb_lines<A, N, 2>(nb[4], nb[5], l, r2, l2);
     }
-    for (int i = threadIdx.x; i < nvalid * NNN; i += blockDim.x) sX[i] = A::load(gsrc + i);
+    for (int i = threadIdx.x; i < nvalid * NNN; i += blockDim.x) sX[spos<N>(i)] = A::load(gsrc + i);
     __syncthreads();
     if (active) {
       sipg_line_pre<A, N, 0>(sX + off, sA + off, r0, l0, l, tb);
@@ -206,7 +237,7 @@ __global__ void __launch_bounds__(cells_per_block<N>() * N * N)
       sipg_line_pre<A, N, 2>(sX + off, sC + off, r2, l2, l, tb);
     }
   } else {
-    for (int i = threadIdx.x; i < nvalid * NNN; i += blockDim.x) sX[i] = A::load(gsrc + i);
+    for (int i = threadIdx.x; i < nvalid * NNN; i += blockDim.x) sX[spos<N>(i)] = A::load(gsrc + i);
     __syncthreads();
     if (active) {
       sipg_line<A, N, 0>(sX + off, sA + off, nb[0], nb[1], l, tb);
@@ -229,15 +260,16 @@ __global__ void __launch_bounds__(cells_per_block<N>() * N * N)
   __syncthreads();
   G* gdst = dst + c0 * NNN;
   for (int i = threadIdx.x; i < nvalid * NNN; i += blockDim.x) {
+    const int si = spos<N>(i);
     if constexpr (EPI == EPI_NONE) {
-      gdst[i] = A::store(sB[i]);
+      gdst[i] = A::store(sB[si]);
     } else {
       // plain float / double policies only
-      const G y = sB[i];
+      const G y = sB[si];
       if constexpr (EPI == EPI_RESID) {
         gdst[i] = ea.b[c0 * NNN + i] - y;
       } else {
-        const G x = sX[i];
+        const G x = sX[si];
         const G r = ea.b[c0 * NNN + i] - y;
         G v = fma(ea.c2 * ea.dinv[i % NNN], r, x);
         // x_{k+1} = x_k + c1 (x_k - x_{k-1}) + c2 D^-1 (b - A x_k); a null
@@ -269,7 +301,7 @@ int launch_sipg(const MeshDims& m, int ncomp, const typename A::G* src, typename
   const long long ncells = m.E * ncomp;
   if (ncells == 0) return 0;
   const long long blocks = (ncells + EPB - 1) / EPB;
-  const size_t smem = (size_t)4 * EPB * NN * N * sizeof(typename A::V);
+  const size_t smem = (size_t)4 * EPB * cell_stride<N>() * sizeof(typename A::V);
   static bool attr_done = false;
   if (!attr_done) {
     if (cudaFuncSetAttribute(sipg_kernel<A, N, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
