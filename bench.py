@@ -249,6 +249,7 @@ def gpu_arm(args, rank, world):
         line["cpu_baseline"] = cpu_baseline(sample_n=N_ELEM, repeats=5)
     if not args.no_solve and rank == 0:
         line["poisson_solve"] = poisson_solve()
+        line["bdf2_tgv"] = bdf2_timing()
     return line
 
 
@@ -285,6 +286,43 @@ def native_fp64_step(u, steps, flush):
     ctx.close()
     t = sum(ms) / len(ms)
     return {"value": round((12 * nu_ + 2 * np_) / (t * 1e-3), 1), "ms_per_step": round(t, 4), "steps": steps}
+
+
+def bdf2_timing(steps=20):
+    """The differentiated-solver workload: 32^3 cells, k_u = 4, k_p = 3,
+    dt = 1e-3, Re = 1600, Taylor-Green + 1e-3 noise; wall time of `steps` BDF2
+    steps (forward) and of the gradient of eps(u^steps) w.r.t. u^0 (forward
+    with per-step checkpoints + backward)."""
+    import torch
+
+    from paper_1802_01439_gb300 import Context, inputs
+    from paper_1802_01439_gb300.navier_stokes import DualSplitting
+    n, ku = 32, 4
+    ctx = Context(n, ku, ku - 1, nu=NU, mg_precision=32, fp64_mode=1)
+    ds = DualSplitting(ctx, 1e-3, solver_tol=1e-12)
+    pi = np.pi
+    u0 = torch.from_numpy(inputs.taylor_green((n,) * 3, (-pi,) * 3, (pi,) * 3, ctx.nodes_1d(0),
+                                              noise=1e-3, seed=0).ravel()).cuda()
+    with torch.no_grad():
+        ds.run(u0, 2, checkpoint_steps=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        u = ds.run(u0, steps, checkpoint_steps=False)
+        eps = float(ds.dissipation(u))
+        torch.cuda.synchronize()
+        fwd = time.perf_counter() - t0
+    x = u0.clone().requires_grad_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J = ds.dissipation(ds.run(x, steps))
+    J.backward()
+    torch.cuda.synchronize()
+    grad = time.perf_counter() - t0
+    ctx.close()
+    return {"workload": "32^3 cells, k_u=4, k_p=3, dt=1e-3, Re=1600, %d BDF2 steps" % steps,
+            "forward_s": round(fwd, 4), "forward_ms_per_step": round(1e3 * fwd / steps, 3),
+            "gradient_s": round(grad, 4), "eps_final": eps,
+            "velocity_dofs": 3 * ctx.n_u, "pressure_dofs": ctx.n_p}
 
 
 def poisson_solve():

@@ -19,7 +19,9 @@
  * buffers (allocated at the first such call), runs the same kernels, copies
  * the results back and synchronises the stream before returning.
  * The caller owns every vector; the library owns its tables, multigrid levels
- * and scratch.  dst must not alias any source (DGNS_ERR_ALIAS).
+ * and scratch.  dst must not alias any source (DGNS_ERR_ALIAS).  Device
+ * vectors must be 16-byte aligned (cudaMalloc and torch allocations are; a
+ * misaligned view is rejected with DGNS_ERR_INVALID_ARG).
  *
  * Errors: every entry point returns 0 on success or a DGNS_ERR_* code; no C++
  * exception crosses the ABI; dgns_last_error() gives a message for the calling

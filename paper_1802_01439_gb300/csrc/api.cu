@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <chrono>
+#include <cstdint>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -430,6 +431,7 @@ int setup_mg(dgns_ctx* c) {
     L.m.ny = mm[1];
     L.m.nz = mm[2];
     L.m.E = (long long)mm[0] * mm[1] * mm[2];
+    L.m.set_divisors();
     L.n = L.m.E * N3;
     for (int d = 0; d < 3; ++d) L.h[d] = (c->d.hi[d] - c->d.lo[d]) / mm[d];
     build_lap(s, L.h, c->d.penalty_factor, 1.0, 0.0, L.lap);
@@ -606,6 +608,7 @@ int dgns_create(const dgns_mesh_desc* desc, void* stream, dgns_ctx** out) {
   c->m.ny = d.n_elem[1];
   c->m.nz = d.n_elem[2];
   c->m.E = (long long)d.n_elem[0] * d.n_elem[1] * d.n_elem[2];
+  c->m.set_divisors();
   for (int i = 0; i < 3; ++i) c->h[i] = (d.hi[i] - d.lo[i]) / d.n_elem[i];
   c->k[0] = d.degree;
   c->k[1] = d.degree_p;
@@ -716,6 +719,8 @@ int dgns_nodes_1d(const dgns_ctx* c, int space, double* out) {
       if (!p_) return fail(DGNS_ERR_INVALID_ARG, "null pointer argument");       \
   } while (0)
 
+static bool aligned16(const void* a, const void* b) { return (((uintptr_t)a | (uintptr_t)b) & 15u) == 0; }
+
 static int lap_like(dgns_ctx* c, double* dst, const double* src, int space, int ncomp, double coef,
                     double mass_factor) {
   const size_t bytes = (size_t)c->n[space] * ncomp * sizeof(double);
@@ -725,6 +730,7 @@ static int lap_like(dgns_ctx* c, double* dst, const double* src, int space, int 
   void* d;
   DG_TRY(st.in(src, bytes, &s));
   DG_TRY(st.out(dst, bytes, &d));
+  if (!aligned16(d, s)) return fail(DGNS_ERR_INVALID_ARG, "dst and src must be 16-byte aligned");
   const LapHost* tab = &c->lap[space];
   LapHost scaled;
   if (coef != 1.0 || mass_factor != 0.0) {
@@ -767,6 +773,7 @@ int dgns_vmult_laplace_f32(dgns_ctx* c, float* dst, const float* src, int level)
   Level& L = c->levels[level];
   const size_t bytes = (size_t)L.n * sizeof(float);
   if (overlaps(dst, bytes, src, bytes)) return fail(DGNS_ERR_ALIAS, "dst overlaps src");
+  if (!aligned16(dst, src)) return fail(DGNS_ERR_INVALID_ARG, "dst and src must be 16-byte aligned");
   DG_TRY(laplace_apply(true, L.m, 1, src, dst, L.lap, EPI_NONE, EpiHost(), c->s));
   return 0;
 }

@@ -13,9 +13,35 @@
 
 namespace dgns {
 
+// Unsigned division by an invariant divisor d (1 <= d < 2^31) with a
+// multiply-high and shifts (Granlund & Montgomery 1994, Fig. 4.1):
+// l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1,
+// n / d = (t + ((n - t) >> min(l,1))) >> max(l-1,0), t = mulhi(m, n).
+struct FastDiv {
+  unsigned d = 1, m = 1, s1 = 0, s2 = 0;
+  __host__ void set(unsigned dv) {
+    d = dv;
+    unsigned l = 0;
+    while ((1ull << l) < dv) ++l;
+    m = (unsigned)((((1ull << 32) * ((1ull << l) - dv)) / dv) + 1);
+    s1 = l < 1 ? l : 1;
+    s2 = l >= 1 ? l - 1 : 0;
+  }
+  __device__ __forceinline__ unsigned div(unsigned n) const {
+    const unsigned t = __umulhi(m, n);
+    return (t + ((n - t) >> s1)) >> s2;
+  }
+};
+
 struct MeshDims {
   int nx, ny, nz;
   long long E;  // cells per component
+  FastDiv fE, fx, fy;  // division by E, nx, ny (set by set_divisors)
+  __host__ void set_divisors() {
+    fE.set((unsigned)E);
+    fx.set((unsigned)nx);
+    fy.set((unsigned)ny);
+  }
 };
 
 // Start offset and stride of line `l` (0 <= l < NI*NJ) along direction d in
@@ -66,11 +92,11 @@ struct CellXYZ {
 __device__ __forceinline__ CellXYZ cell_xyz(unsigned cell, const MeshDims& m) {
   CellXYZ c;
   const unsigned E = (unsigned)m.E, nx = (unsigned)m.nx, ny = (unsigned)m.ny;
-  c.comp = cell / E;
+  c.comp = m.fE.div(cell);
   c.el = cell - c.comp * E;
-  const unsigned t = c.el / nx;
+  const unsigned t = m.fx.div(c.el);
   c.ex = (int)(c.el - t * nx);
-  c.ez = (int)(t / ny);
+  c.ez = (int)m.fy.div(t);
   c.ey = (int)(t - (unsigned)c.ez * ny);
   return c;
 }

@@ -190,6 +190,33 @@ __device__ __forceinline__ void mass_line(const typename A::V* in, const typenam
   for (int i = 0; i < N; ++i) out[base + i * stride] = A::acc_get(y[i]);
 }
 
+// Copy of one x-line of a cell between global memory (contiguous) and the
+// padded shared layout: vector loads/stores where the line is aligned.
+template <class A, int N>
+__device__ __forceinline__ void load_xline(const typename A::G* __restrict__ g, typename A::V* sl) {
+  typedef typename A::G G;
+  if constexpr (!A::emulated && sizeof(G) == 4 && N % 4 == 0) {
+#pragma unroll
+    for (int j = 0; j < N; j += 4) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(g + j));
+      sl[j] = v.x;
+      sl[j + 1] = v.y;
+      sl[j + 2] = v.z;
+      sl[j + 3] = v.w;
+    }
+  } else if constexpr (!A::emulated && sizeof(G) == 8 && N % 2 == 0) {
+#pragma unroll
+    for (int j = 0; j < N; j += 2) {
+      const double2 v = __ldg(reinterpret_cast<const double2*>(g + j));
+      sl[j] = v.x;
+      sl[j + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < N; ++j) sl[j] = A::load(g + j);
+  }
+}
+
 template <class A, int N, int EPI>
 __global__ void __launch_bounds__(cells_per_block<N>() * N * N)
     sipg_kernel(const typename A::G* __restrict__ src, typename A::G* __restrict__ dst,
@@ -229,7 +256,7 @@ __global__ void __launch_bounds__(cells_per_block<N>() * N * N)
       load_nb_lines<A, N, 1>(nb[2], nb[3], l, r1, l1);
       load_nb_lines<A, N, 2>(nb[4], nb[5], l, r2, l2);
     }
-    for (int i = threadIdx.x; i < nvalid * NNN; i += blockDim.x) sX[spos<N>(i)] = A::load(gsrc + i);
+    if (active) load_xline<A, N>(gsrc + slot * NNN + l * N, sX + off + l * padx<N>());
     __syncthreads();
     if (active) {
       sipg_line_pre<A, N, 0>(sX + off, sA + off, r0, l0, l, tb);
@@ -237,7 +264,7 @@ __global__ void __launch_bounds__(cells_per_block<N>() * N * N)
       sipg_line_pre<A, N, 2>(sX + off, sC + off, r2, l2, l, tb);
     }
   } else {
-    for (int i = threadIdx.x; i < nvalid * NNN; i += blockDim.x) sX[spos<N>(i)] = A::load(gsrc + i);
+    if (active) load_xline<A, N>(gsrc + slot * NNN + l * N, sX + off + l * padx<N>());
     __syncthreads();
     if (active) {
       sipg_line<A, N, 0>(sX + off, sA + off, nb[0], nb[1], l, tb);
@@ -258,24 +285,38 @@ __global__ void __launch_bounds__(cells_per_block<N>() * N * N)
   __syncthreads();
   if (active) mass_line<A, N, 2, true>(sA + off, sC + off, sB + off, l, tb.M);
   __syncthreads();
-  G* gdst = dst + c0 * NNN;
-  for (int i = threadIdx.x; i < nvalid * NNN; i += blockDim.x) {
-    const int si = spos<N>(i);
+  // each thread writes its own x-line of the result
+  if (active) {
+    const int li = slot * NNN + l * N;        // block-local index of the line start
+    G* gdst = dst + c0 * NNN + li;
+    const V* yl = sB + off + l * padx<N>();
     if constexpr (EPI == EPI_NONE) {
-      gdst[i] = A::store(sB[si]);
+      if constexpr (!A::emulated && sizeof(G) == 4 && N % 4 == 0) {
+#pragma unroll
+        for (int j = 0; j < N; j += 4)
+          *reinterpret_cast<float4*>(gdst + j) = make_float4(yl[j], yl[j + 1], yl[j + 2], yl[j + 3]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < N; ++j) gdst[j] = A::store(yl[j]);
+      }
     } else {
       // plain float / double policies only
-      const G y = sB[si];
-      if constexpr (EPI == EPI_RESID) {
-        gdst[i] = ea.b[c0 * NNN + i] - y;
-      } else {
-        const G x = sX[si];
-        const G r = ea.b[c0 * NNN + i] - y;
-        G v = fma(ea.c2 * ea.dinv[i % NNN], r, x);
-        // x_{k+1} = x_k + c1 (x_k - x_{k-1}) + c2 D^-1 (b - A x_k); a null
-        // xprev stands for a zero previous iterate
-        if (ea.c1 != (G)0) v = fma(ea.c1, x - (ea.xprev ? ea.xprev[c0 * NNN + i] : (G)0), v);
-        gdst[i] = v;
+      const V* xl = sX + off + l * padx<N>();
+      const G* bl = ea.b + c0 * NNN + li;
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        const G y = yl[j];
+        if constexpr (EPI == EPI_RESID) {
+          gdst[j] = bl[j] - y;
+        } else {
+          const G x = xl[j];
+          const G r = bl[j] - y;
+          G v = fma(ea.c2 * ea.dinv[l * N + j], r, x);
+          // x_{k+1} = x_k + c1 (x_k - x_{k-1}) + c2 D^-1 (b - A x_k); a null
+          // xprev stands for a zero previous iterate
+          if (ea.c1 != (G)0) v = fma(ea.c1, x - (ea.xprev ? ea.xprev[c0 * NNN + li + j] : (G)0), v);
+          gdst[j] = v;
+        }
       }
     }
   }

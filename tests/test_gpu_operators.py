@@ -160,3 +160,12 @@ def test_laplace_smooth_field(n, k, mode):
     y = torch.empty(s.size, dtype=torch.float64, device="cuda")
     ctx.vmult_laplace(y, dev(x), space=0)
     assert rel_err(host(y), ref) <= TOL
+
+
+def test_misaligned_vector_rejected():
+    from paper_1802_01439_gb300 import DgnsError
+    ctx = context((2, 2, 2), 3, 3, mg_precision=0)
+    buf = torch.zeros(ctx.n_u + 1, dtype=torch.float64, device="cuda")
+    y = torch.empty(ctx.n_u, dtype=torch.float64, device="cuda")
+    with pytest.raises(DgnsError):
+        ctx.vmult_laplace(y, buf[1:], space=0)
