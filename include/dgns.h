@@ -142,6 +142,21 @@ int dgns_dissipation_grad(dgns_ctx* ctx, double* grad3, const double* u3);
 int dgns_axpby(dgns_ctx* ctx, double* y, const double* x, long long n, double a, double b);
 int dgns_dot(dgns_ctx* ctx, const double* a, const double* b, long long n, double* out);
 
+/* Penalty parameters of the projection step (Sec. 3.2, divergence and
+ * continuity penalty terms): per cell, with ||u||_e the volume average of the
+ * Euclidean norm of the extrapolated velocity u_ex3 (k_u+1 Gauss points) and
+ * h = V_e^(1/3):  tau_d[e] = zeta_d ||u||_e h / (k_u+1) dt,
+ * tau_c[e] = zeta_c ||u||_e dt.  Device pointers (tau arrays of n_elem
+ * doubles).  k_u <= 7. */
+int dgns_penalty_parameters(dgns_ctx* ctx, const double* u_ex3, double dt, double zeta_d, double zeta_c,
+                            double* tau_d, double* tau_c);
+/* Projection operator of the projection substep (Sec. 3.3):
+ * dst3 = (M + A_D + A_C) src3 with a_D(v,u) = (div v, tau_D div u)_e and
+ * a_C(v,u) = sum_F int {{tau_C}} (v- - v+).n (u- - u+).n.  Device pointers;
+ * k_u <= 7. */
+int dgns_vmult_projection(dgns_ctx* ctx, double* dst3, const double* src3, const double* tau_d,
+                          const double* tau_c);
+
 typedef struct {
   double rel_tol;          /* stop when ||r||_2 <= rel_tol ||b||_2 (default 1e-10) */
   double abs_tol;          /* or ||r||_2 <= abs_tol (default 0)                      */
@@ -212,6 +227,12 @@ int dgns_cg_invmass_solve(dgns_ctx* ctx, double* x3, const double* b3, double ma
  * other contexts) race on it and must be serialised by the caller. */
 int dgns_cg_invmass_solve_noalloc(dgns_ctx* ctx, double* x3, const double* b3, double mass_factor,
                                   const dgns_solve_params* params, dgns_solve_info* info);
+
+/* Projection solve (Sec. 3.3): CG preconditioned by the inverse mass
+ * matrix on (M + A_D + A_C) x3 = b3, FP64, zero initial guess; device
+ * pointers; k_u <= 7. */
+int dgns_cg_projection_solve(dgns_ctx* ctx, double* x3, const double* b3, const double* tau_d,
+                             const double* tau_c, const dgns_solve_params* params, dgns_solve_info* info);
 
 #ifdef __cplusplus
 }

@@ -420,6 +420,66 @@ class Convective:
 
 
 # ----------------------------------------------------------------------------
+# Projection substep with divergence and continuity penalty terms (Sec. 3.2,
+# the terms a_D and a_C of the projection step, and the matrix form
+# M + A_D + A_C of Sec. 3.3):
+#   a_D(v, u) = (div v, tau_D div u)_e,
+#   tau_D = zeta_D ||u_ex||_e h / (k_u + 1) dt,
+#   a_C(v, u) = sum over interior faces of (v.n, {{tau_C}} [u].n),
+#   tau_C = zeta_C ||u_ex||_e dt,
+# with ||u_ex||_e the element-wise volume average of the Euclidean norm of
+# the extrapolated velocity and h = V_e^(1/3).  Summed over both cells of a
+# face the continuity term is int {{tau_C}} (v- - v+).n (u- - u+).n.
+# ----------------------------------------------------------------------------
+def velocity_norm_average(space, U):
+    """(1/V_e) int_e |u| dx per cell, Gauss rule with k+1 points."""
+    Phi, _, W = _cell_tables(space, space.N)
+    speed = np.sqrt(sum((U[c] @ Phi.T) ** 2 for c in range(3)))
+    return (speed * W[None, :]).sum(axis=1) / np.prod(space.mesh.h)
+
+
+def penalty_parameters(space, U_ex, dt, zeta_d=1.0, zeta_c=1.0):
+    nrm = velocity_norm_average(space, U_ex)
+    h_eff = np.prod(space.mesh.h) ** (1.0 / 3.0)
+    return zeta_d * nrm * h_eff / (space.k + 1) * dt, zeta_c * nrm * dt
+
+
+class Projection:
+    """M + A_D + A_C on a velocity field (3, E, N^3) with per-cell tau_D and
+    tau_C (arrays of length E)."""
+
+    def __init__(self, space, tau_d, tau_c):
+        self.space = space
+        self.tau_d = np.asarray(tau_d, dtype=np.float64)
+        self.tau_c = np.asarray(tau_c, dtype=np.float64)
+        Phi, dPhi, W = _cell_tables(space, space.N)
+        self.Me = Phi.T @ (W[:, None] * Phi)
+        self.AD = [[dPhi[b].T @ (W[:, None] * dPhi[a]) for a in range(3)] for b in range(3)]
+        self.faces = []
+        for axis in range(3):
+            vm, _, wf = _face_tables(space, space.N, axis, 1)
+            vp, _, _ = _face_tables(space, space.N, axis, 0)
+            self.faces.append({"--": vm.T @ (wf[:, None] * vm), "-+": -(vm.T @ (wf[:, None] * vp)),
+                               "+-": -(vp.T @ (wf[:, None] * vm)), "++": vp.T @ (wf[:, None] * vp)})
+
+    def apply(self, U):
+        m = self.space.mesh
+        U = np.asarray(U, dtype=np.float64)
+        Y = np.stack([U[c] @ self.Me.T for c in range(3)])
+        for b in range(3):
+            for a in range(3):
+                Y[b] += self.tau_d[:, None] * (U[a] @ self.AD[b][a].T)
+        em = np.arange(m.E)
+        for a in range(3):
+            B = self.faces[a]
+            ep = m.neighbor(a, +1)
+            tc = 0.5 * (self.tau_c[em] + self.tau_c[ep])
+            Y[a][em] += tc[:, None] * (U[a][em] @ B["--"].T + U[a][ep] @ B["-+"].T)
+            Y[a][ep] += tc[:, None] * (U[a][em] @ B["+-"].T + U[a][ep] @ B["++"].T)
+        return Y
+
+
+# ----------------------------------------------------------------------------
 # Diagnostics of Sec. 4.2: kinetic energy and dissipation rate, with the
 # element-wise (broken) gradient and k_u + 1 Gauss points.
 # ----------------------------------------------------------------------------

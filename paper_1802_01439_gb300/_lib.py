@@ -74,6 +74,10 @@ SIGNATURES = {
     "dgns_dissipation_grad": (_I, [_P, _P, _P]),
     "dgns_axpby": (_I, [_P, _P, _P, _LL, _D, _D]),
     "dgns_dot": (_I, [_P, _P, _P, _LL, ctypes.POINTER(_D)]),
+    "dgns_penalty_parameters": (_I, [_P, _P, _D, _D, _D, _P, _P]),
+    "dgns_vmult_projection": (_I, [_P, _P, _P, _P, _P]),
+    "dgns_cg_projection_solve": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(SolveParams),
+                                      ctypes.POINTER(SolveInfo)]),
     "dgns_default_solve_params": (None, [ctypes.POINTER(SolveParams)]),
     "dgns_cg_mg_solve": (_I, [_P, _P, _P, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo)]),
     "dgns_mg_info": (_I, [_P, ctypes.POINTER(_I), _P, _P]),

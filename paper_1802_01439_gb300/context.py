@@ -182,6 +182,21 @@ class Context:
                                 ctypes.byref(out)))
         return out.value
 
+    def penalty_parameters(self, u_ex3, dt, zeta_d=1.0, zeta_c=1.0):
+        """Per-cell (tau_D, tau_C) of the projection step, device tensors."""
+        E = self.n_u // (self.degree + 1) ** 3
+        td = torch.empty(E, dtype=torch.float64, device=u_ex3.device)
+        tc = torch.empty_like(td)
+        check(self.lib.dgns_penalty_parameters(self.h, self._vec(u_ex3, 3 * self.n_u, name="u_ex3"),
+                                               float(dt), float(zeta_d), float(zeta_c), _ptr(td), _ptr(tc)))
+        return td, tc
+
+    def vmult_projection(self, dst3, src3, tau_d, tau_c):
+        n = 3 * self.n_u
+        check(self.lib.dgns_vmult_projection(self.h, self._vec(dst3, n, name="dst3"),
+                                             self._vec(src3, n, name="src3"), _ptr(tau_d), _ptr(tau_c)))
+        return dst3
+
     # ------------------------------------------------------------ solvers
     @staticmethod
     def solve_params(**kw):
@@ -216,6 +231,18 @@ class Context:
         rc = self.lib.dgns_cg_invmass_solve(self.h, self._vec(x3, n, name="x3"),
                                             self._vec(b3, n, name="b3"), float(mass_factor),
                                             ctypes.byref(p), ctypes.byref(info))
+        if raise_on_error:
+            check(rc)
+        out = self._info(info)
+        out["rc"] = rc
+        return out
+
+    def cg_projection_solve(self, x3, b3, tau_d, tau_c, raise_on_error=True, **kw):
+        p = self.solve_params(**kw)
+        info = _lib.SolveInfo()
+        n = 3 * self.n_u
+        rc = self.lib.dgns_cg_projection_solve(self.h, self._vec(x3, n, name="x3"), self._vec(b3, n, name="b3"),
+                                               _ptr(tau_d), _ptr(tau_c), ctypes.byref(p), ctypes.byref(info))
         if raise_on_error:
             check(rc)
         out = self._info(info)

@@ -663,6 +663,19 @@ int dgns_create(const dgns_mesh_desc* desc, void* stream, dgns_ctx** out) {
     for (int i = 0; i < Q; ++i) c->conv.w[i] = (double)q.w[i];
     for (int dd = 0; dd < 3; ++dd) c->conv.h[dd] = c->h[dd];
   }
+  {
+    const Space1D& su = c->sp1[0];
+    const int N = su.N;
+    Quad1D q = make_quad_1d(su, N);
+    c->proj.N = N;
+    for (int i = 0; i < N * N; ++i) {
+      c->proj.S[i] = (double)q.S[i];
+      c->proj.D[i] = (double)q.D[i];
+      c->proj.M[i] = (double)su.mass[i];
+    }
+    for (int i = 0; i < N; ++i) c->proj.w[i] = (double)q.w[i];
+    for (int dd = 0; dd < 3; ++dd) c->proj.h[dd] = c->h[dd];
+  }
   int rc = 0;
   auto bail = [&](int code) {
     free_ctx(c);
@@ -963,6 +976,103 @@ int dgns_dot(dgns_ctx* c, const double* a, const double* b, long long n, double*
   DG_TRY(read_scalars(c));
   *out = c->h_scal[S_T1];
   return 0;
+}
+
+int dgns_penalty_parameters(dgns_ctx* c, const double* u_ex3, double dt, double zeta_d, double zeta_c,
+                            double* tau_d, double* tau_c) {
+  g_err.clear();
+  if (!c) return fail(DGNS_ERR_INVALID_ARG, "ctx is null");
+  DG_NONNULL(u_ex3, tau_d, tau_c);
+  if (!is_device_ptr(u_ex3) || !is_device_ptr(tau_d) || !is_device_ptr(tau_c))
+    return fail(DGNS_ERR_INVALID_ARG, "device pointers only");
+  const double h_eff = cbrt(c->h[0] * c->h[1] * c->h[2]);
+  const double fd = zeta_d * h_eff / (c->k[0] + 1) * dt, fc = zeta_c * dt;
+  const int rc = penalty_parameters(c->m, u_ex3, tau_d, tau_c, c->proj, fd, fc, c->s);
+  if (rc == 7) return fail(DGNS_ERR_UNSUPPORTED, "projection operator: supported for k_u <= 7");
+  DG_TRY(rc);
+  return 0;
+}
+
+int dgns_vmult_projection(dgns_ctx* c, double* dst3, const double* src3, const double* tau_d,
+                          const double* tau_c) {
+  g_err.clear();
+  if (!c) return fail(DGNS_ERR_INVALID_ARG, "ctx is null");
+  DG_NONNULL(dst3, src3, tau_d, tau_c);
+  const size_t bu = (size_t)c->n[0] * 3 * sizeof(double);
+  if (overlaps(dst3, bu, src3, bu)) return fail(DGNS_ERR_ALIAS, "dst overlaps src");
+  if (!is_device_ptr(dst3) || !is_device_ptr(src3) || !is_device_ptr(tau_d) || !is_device_ptr(tau_c))
+    return fail(DGNS_ERR_INVALID_ARG, "device pointers only");
+  const int rc = projection_apply(c->m, src3, dst3, tau_d, tau_c, c->proj, c->s);
+  if (rc == 7) return fail(DGNS_ERR_UNSUPPORTED, "projection operator: supported for k_u <= 7");
+  DG_TRY(rc);
+  return 0;
+}
+
+int dgns_cg_projection_solve(dgns_ctx* c, double* x3, const double* b3, const double* tau_d,
+                             const double* tau_c, const dgns_solve_params* params, dgns_solve_info* info) {
+  g_err.clear();
+  if (!c) return fail(DGNS_ERR_INVALID_ARG, "ctx is null");
+  DG_NONNULL(x3, b3, tau_d, tau_c);
+  if (c->N[0] > 8) return fail(DGNS_ERR_UNSUPPORTED, "projection operator: supported for k_u <= 7");
+  dgns_solve_params prm;
+  if (params) prm = *params;
+  else dgns_default_solve_params(&prm);
+  if (prm.max_iter < 1) return fail(DGNS_ERR_INVALID_ARG, "invalid solve parameters");
+  const long long n = 3 * c->n[DGNS_SPACE_U];
+  const size_t bytes = (size_t)n * sizeof(double);
+  if (overlaps(x3, bytes, b3, bytes)) return fail(DGNS_ERR_ALIAS, "x overlaps b");
+  if (!is_device_ptr(x3) || !is_device_ptr(b3) || !is_device_ptr(tau_d) || !is_device_ptr(tau_c))
+    return fail(DGNS_ERR_INVALID_ARG, "device pointers only");
+  DG_TRY(alloc_cg(c, n));
+  const auto t0 = std::chrono::steady_clock::now();
+  const int N = c->N[0];
+  const double(*MI)[MAXN * MAXN] = c->minv3[0];
+  DG_CUDA(cudaMemsetAsync(x3, 0, bytes, c->s));
+  DG_CUDA(cudaMemcpyAsync(c->r, b3, bytes, cudaMemcpyDeviceToDevice, c->s));
+  DG_TRY(dot(b3, b3, n, c->red, S_T0, c->s));
+  DG_TRY(read_scalars(c));
+  const double nb = sqrt(c->h_scal[S_T0]);
+  dgns_solve_info inf{};
+  inf.initial_res = nb;
+  int status = DGNS_OK;
+  if (nb > 0.0) {
+    DG_TRY(tensor3_apply(N, 3 * c->m.E, c->r, c->z, MI[0], MI[1], MI[2], c->s));
+    DG_TRY(cg_direction(c->p, c->z, n, c->red, true, c->s));
+    DG_TRY(dot(c->r, c->z, n, c->red, S_RZ, c->s));
+    int it = 0;
+    double res = 1.0;
+    status = DGNS_ERR_NOT_CONVERGED;
+    while (it < prm.max_iter) {
+      DG_TRY(projection_apply(c->m, c->p, c->Ap, tau_d, tau_c, c->proj, c->s));
+      DG_TRY(dot(c->p, c->Ap, n, c->red, S_PAP, c->s));
+      DG_TRY(cg_update(x3, c->r, c->p, c->Ap, n, c->red, c->s));
+      DG_TRY(read_scalars(c));
+      ++it;
+      const double rr = c->h_scal[S_RR];
+      if (!std::isfinite(rr)) {
+        status = fail(DGNS_ERR_NONFINITE, "non-finite residual");
+        break;
+      }
+      res = sqrt(rr) / nb;
+      if (res <= prm.rel_tol || sqrt(rr) <= prm.abs_tol) {
+        status = DGNS_OK;
+        break;
+      }
+      DG_TRY(tensor3_apply(N, 3 * c->m.E, c->r, c->z, MI[0], MI[1], MI[2], c->s));
+      DG_TRY(dot(c->r, c->z, n, c->red, S_RZNEW, c->s));
+      DG_TRY(cg_direction(c->p, c->z, n, c->red, false, c->s));
+    }
+    inf.iterations = it;
+    inf.rel_res = res;
+    if (status == DGNS_ERR_NOT_CONVERGED) fail(status, "max_iter reached");
+  } else if (!std::isfinite(nb)) {
+    status = fail(DGNS_ERR_NONFINITE, "non-finite right-hand side");
+  }
+  DG_CUDA(cudaStreamSynchronize(c->s));
+  inf.status = status;
+  inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (info) *info = inf;
+  return status;
 }
 
 int dgns_mg_info(const dgns_ctx* c, int* n_levels, int* n_elem_per_level, double* lambda_max) {

@@ -55,6 +55,7 @@ struct dgns_ctx {
   dgns::DivHost div;
   dgns::GradHost grad;
   dgns::ConvHost conv;
+  dgns::ProjHost proj;
   // multigrid (pressure space)
   int mg_prec = 0;
   std::vector<dgns::Level> levels;

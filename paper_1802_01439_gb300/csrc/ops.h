@@ -87,4 +87,18 @@ int convective_apply(const MeshDims& m, const double* u3, double* dst3, const Co
 int convective_vjp(const MeshDims& m, const double* u3, const double* w3, double* dst3,
                    const ConvHost& t, cudaStream_t s);
 
+// Projection operator M + A_D + A_C and the penalty parameters
+// (k_projection.cu); N = k_u + 1 <= 8.
+struct ProjHost {
+  int N = 0;
+  double S[MAXN * MAXN], D[MAXN * MAXN], M[MAXN * MAXN];
+  double w[MAXN];
+  double h[3];
+};
+int projection_apply(const MeshDims& m, const double* u3, double* dst3, const double* tau_d, const double* tau_c,
+                     const ProjHost& h, cudaStream_t s);
+// tau_d = fd * avg|u|, tau_c = fc * avg|u| per cell
+int penalty_parameters(const MeshDims& m, const double* u3, double* tau_d, double* tau_c, const ProjHost& h,
+                       double fd, double fc, cudaStream_t s);
+
 }  // namespace dgns

@@ -1,0 +1,64 @@
+"""GPU vs oracle parity of the projection-step operator with the divergence
+and continuity penalty terms (Sec. 3.2) and of its penalty parameters, and the
+inverse-mass-preconditioned CG solve of the projection system (Sec. 3.3)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import dg, solvers
+from tests.gpu_common import build_lib, context, dev, host, random_field, rel_err, tgv_field
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build_lib()
+
+
+@pytest.mark.parametrize("n,k", [((3, 2, 4), 3), ((2, 2, 2), 2), ((1, 2, 3), 4), ((2, 1, 2), 7)])
+def test_penalty_parameters(n, k):
+    ctx = context(n, k, mg_precision=0)
+    s = dg.Space(dg.Mesh(n), k)
+    u = tgv_field(s, 1e-2, 1)
+    td, tc = ctx.penalty_parameters(dev(u.ravel()), 1e-3, zeta_d=1.0, zeta_c=0.7)
+    rd, rc = dg.penalty_parameters(s, u, 1e-3, zeta_d=1.0, zeta_c=0.7)
+    assert rel_err(host(td), rd) <= 1e-12 and rel_err(host(tc), rc) <= 1e-12
+
+
+@pytest.mark.parametrize("n,k", [((3, 2, 4), 3), ((2, 2, 2), 2), ((1, 2, 3), 4), ((2, 1, 2), 7),
+                                 ((4, 3, 2), 5)])
+def test_projection_operator(n, k):
+    ctx = context(n, k, mg_precision=0)
+    m = dg.Mesh(n)
+    s = dg.Space(m, k)
+    rng = np.random.default_rng(3)
+    td, tc = rng.uniform(0.1, 1.0, m.E), rng.uniform(0.1, 1.0, m.E)
+    u = random_field(s, 3, 8)
+    y = torch.empty(u.size, dtype=torch.float64, device="cuda")
+    ctx.vmult_projection(y, dev(u.ravel()), dev(td), dev(tc))
+    assert rel_err(host(y), dg.Projection(s, td, tc).apply(u)) <= 1e-12
+
+
+def test_projection_solve():
+    n, k, dt = (4, 3, 4), 3, 1e-3
+    ctx = context(n, k, mg_precision=0)
+    m = dg.Mesh(n)
+    s = dg.Space(m, k)
+    u = tgv_field(s, 1e-3, 2)
+    td, tc = dg.penalty_parameters(s, u, dt)
+    b = np.random.default_rng(4).uniform(-1, 1, 3 * s.size)
+    x = torch.zeros(3 * s.size, dtype=torch.float64, device="cuda")
+    info = ctx.cg_projection_solve(x, dev(b), dev(td), dev(tc), rel_tol=1e-12)
+    assert info["rc"] == 0 and info["iterations"] <= 20
+    P = dg.Projection(s, td, tc)
+    assert solvers.relative_residual(lambda v: P.apply(v.reshape(3, m.E, -1)).ravel(), host(x), b) <= 2e-12
+
+
+def test_projection_unsupported_degree():
+    from paper_1802_01439_gb300 import DgnsError
+    ctx = context((1, 1, 1), 8, 7, mg_precision=0)
+    x = torch.zeros(3 * ctx.n_u, dtype=torch.float64, device="cuda")
+    t = torch.ones(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(DgnsError):
+        ctx.vmult_projection(torch.empty_like(x), x, t, t)

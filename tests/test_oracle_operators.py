@@ -346,3 +346,55 @@ def test_dissipation_gradient_matches_difference_quotient():
     g = dg.dissipation_gradient(s, U, nu)
     assert abs(np.sum(g * V) - fd) < 1e-12 * abs(fd)
     assert abs(0.5 * np.sum(g * U) - dg.dissipation_rate(s, U, nu)) < 1e-13 * dg.dissipation_rate(s, U, nu)
+
+
+# --------------------------------------------------------------- projection
+def test_penalty_parameters_constant_field():
+    m = dg.Mesh((3, 2, 2))
+    s = dg.Space(m, 3)
+    U = np.stack([np.full((m.E, s.ndofs_cell), v) for v in (1.0, 2.0, -2.0)])
+    dt = 1e-3
+    tau_d, tau_c = dg.penalty_parameters(s, U, dt, zeta_d=1.0, zeta_c=0.5)
+    h = np.prod(m.h) ** (1 / 3)
+    assert np.max(np.abs(tau_d - 3.0 * h / 4 * dt)) < 1e-15
+    assert np.max(np.abs(tau_c - 1.5 * dt)) < 1e-15
+
+
+@pytest.mark.parametrize("n,k", [((2, 2, 2), 2), ((1, 2, 3), 3)])
+def test_projection_symmetric_and_mass_plus_psd(n, k):
+    m = dg.Mesh(n)
+    s = dg.Space(m, k)
+    rng = np.random.default_rng(4)
+    P = dg.Projection(s, rng.uniform(0.1, 1.0, m.E), rng.uniform(0.1, 1.0, m.E))
+    N3 = 3 * s.size
+    A = np.stack([P.apply(e.reshape(3, m.E, -1)).ravel() for e in np.eye(N3)], 1)
+    assert np.max(np.abs(A - A.T)) < 1e-13 * np.max(np.abs(A))
+    Mb = np.kron(np.eye(3), np.kron(np.eye(m.E), dg.Mass(s).Me))
+    assert np.linalg.eigvalsh(0.5 * (A + A.T) - Mb)[0] > -1e-12 * np.max(np.abs(A))
+
+
+def test_projection_penalty_energies():
+    """Sawtooth u_x = x - x_cell: div u = 1 in every cell, so u^T A_D u =
+    sum tau_D V_e; its x-jumps are h: u^T A_C u = sum_faces {{tau_C}} |F| h^2.
+    Piecewise constant u_y: no divergence, u^T A_C u = sum {{tau_C}} |F| [u_y]^2."""
+    m = dg.Mesh((3, 2, 2), lo=(0, 0, 0), hi=(1.5, 1.0, 0.6))
+    s = dg.Space(m, 3)
+    rng = np.random.default_rng(5)
+    td, tc = rng.uniform(0.1, 1.0, m.E), rng.uniform(0.1, 1.0, m.E)
+    M = dg.Mass(s)
+    X = s.node_coords()[0]
+    U = np.zeros((3, m.E, s.ndofs_cell))
+    U[0] = X - (m.lo[0] + m.ijk[0][:, None] * m.h[0])
+    P = dg.Projection(s, td, tc)
+    e = np.sum(U * P.apply(U)) - np.sum(U[0] * M.apply(U[0]))
+    Ve = np.prod(m.h)
+    ep = m.neighbor(0, +1)
+    ref = np.sum(td) * Ve + np.sum(0.5 * (tc + tc[ep])) * m.h[1] * m.h[2] * m.h[0] ** 2
+    assert abs(e - ref) < 1e-12 * ref
+    cval = rng.uniform(-1, 1, m.E)
+    U = np.zeros((3, m.E, s.ndofs_cell))
+    U[1] = np.repeat(cval[:, None], s.ndofs_cell, 1)
+    e = np.sum(U * P.apply(U)) - np.sum(U[1] * M.apply(U[1]))
+    ey = m.neighbor(1, +1)
+    ref = np.sum(0.5 * (tc + tc[ey]) * (cval - cval[ey]) ** 2) * m.h[0] * m.h[2]
+    assert abs(e - ref) < 1e-12 * abs(ref)
