@@ -4,18 +4,19 @@ Sec. 3.1 of the paper (four substeps of the dual splitting scheme with BDF
 order J = 2 and extrapolation of the convective term) in the matrix form of
 Sec. 3.3, with the readings: gamma0 = 3/2, alpha = (2, -1/2), beta = (2, -1)
 (the first step BDF1: gamma0 = alpha0 = beta0 = 1); the projection substep
-without the divergence and continuity penalty terms (plain L2 projection).
+either as the plain L2 projection or with the divergence and continuity
+penalty terms (parameters from the extrapolated velocity).
 The linear systems are solved exactly with dense factorisations (small
 meshes only): the pressure by the eigen-decomposition pseudo-inverse of the
 singular periodic Laplacian, the Helmholtz problem by a dense Cholesky solve.
 """
 import numpy as np
 
-from . import dg
+from . import dg, solvers
 
 
 class DualSplitting:
-    def __init__(self, mesh, ku, nu, dt, penalty_factor=1.0):
+    def __init__(self, mesh, ku, nu, dt, penalty_factor=1.0, projection="l2", zeta=(1.0, 1.0)):
         self.su, self.sp = dg.Space(mesh, ku), dg.Space(mesh, ku - 1)
         self.C = dg.Convective(self.su)
         self.M = dg.Mass(self.su)
@@ -23,6 +24,7 @@ class DualSplitting:
         self.G = dg.Gradient(self.su, self.sp)
         self.nu, self.dt = nu, dt
         self.pf = penalty_factor
+        self.projection, self.zeta = projection, zeta
         L = dg.Laplace(self.sp, penalty_factor).matrix()
         w, V = np.linalg.eigh(0.5 * (L + L.T))
         keep = w > 1e-10 * w[-1]
@@ -59,7 +61,20 @@ class DualSplitting:
         uh = (hist - dt * self.M.apply_inverse(cc)) / g0
         rhs = -(g0 / dt) * self.D.apply(uh)
         p = (self.Lpinv @ rhs.ravel()).reshape(rhs.shape)
-        uhh = uh - (dt / g0) * self.M.apply_inverse(self.G.apply(p))
+        if self.projection == "l2":
+            uhh = uh - (dt / g0) * self.M.apply_inverse(self.G.apply(p))
+        else:
+            # (M + A_D + A_C) uhh = M uh - (dt/gamma0) G p, penalty parameters
+            # from the extrapolated velocity (Sec. 3.2), CG with M^-1
+            u_ex = u if first else b[0] * u + b[1] * u_prev
+            td, tc = dg.penalty_parameters(self.su, u_ex, dt, *self.zeta)
+            P = dg.Projection(self.su, td, tc)
+            rhs = self.M.apply(uh) - (dt / g0) * self.G.apply(p)
+            shape = rhs.shape
+            x, _, _ = solvers.pcg(lambda v: P.apply(v.reshape(shape)).ravel(), rhs.ravel(),
+                                  precond=lambda r: self.M.apply_inverse(r.reshape(shape)).ravel(),
+                                  rel_tol=1e-14, max_iter=200)
+            uhh = x.reshape(shape)
         u_new = self.helmholtz_solve(g0 / dt, (g0 / dt) * self.M.apply(uhh))
         return u_new, c
 

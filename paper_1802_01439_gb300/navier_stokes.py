@@ -17,7 +17,8 @@ One step (BDF2 with gamma0 = 3/2, alpha = (2, -1/2), beta = (2, -1); the first
 step BDF1 with gamma0 = alpha0 = beta0 = 1):
   1. convective:  uh  = (sum_i alpha_i u^{n-i} - dt M^-1 sum_i beta_i C(u^{n-i})) / gamma0
   2. pressure:    L p = -(gamma0/dt) D uh
-  3. projection:  uhh = uh - (dt/gamma0) M^-1 G p        (plain L2 projection)
+  3. projection:  uhh = uh - (dt/gamma0) M^-1 G p        (plain L2 projection), or
+                  (M + A_D + A_C) uhh = M uh - (dt/gamma0) G p   (penalty terms)
   4. viscous:     (gamma0/dt M + V) u^{n+1} = (gamma0/dt) M uhh
 ``run`` advances several steps; with ``checkpoint=True`` each step is wrapped
 in ``torch.utils.checkpoint`` so only the step inputs are stored and the step
@@ -140,6 +141,25 @@ class _Helmholtz(torch.autograd.Function):
         return None, x, None, None
 
 
+class _Projection(torch.autograd.Function):
+    """x = (M + A_D + A_C)^-1 b with the penalty parameters held fixed."""
+
+    @staticmethod
+    def forward(fctx, dg, b, tau_d, tau_c, tol):
+        x = torch.zeros_like(b)
+        dg.cg_projection_solve(x, b.contiguous(), tau_d, tau_c, rel_tol=tol)
+        fctx.dg, fctx.tol = dg, tol
+        fctx.save_for_backward(tau_d, tau_c)
+        return x
+
+    @staticmethod
+    def backward(fctx, g):
+        tau_d, tau_c = fctx.saved_tensors
+        x = torch.zeros_like(g)
+        fctx.dg.cg_projection_solve(x, g.contiguous(), tau_d, tau_c, rel_tol=fctx.tol)
+        return None, x, None, None, None
+
+
 class _Axpby(torch.autograd.Function):
     """a x + b y (a new tensor)."""
 
@@ -184,10 +204,18 @@ class DualSplitting:
     """BDF2 dual-splitting stepper on a libdgns ``Context`` (velocity degree
     k_u, pressure degree k_p = k_u - 1, FP32 or FP64 multigrid)."""
 
-    def __init__(self, dg, dt, solver_tol=1e-12):
+    def __init__(self, dg, dt, solver_tol=1e-12, projection="l2", zeta_d=1.0, zeta_c=1.0):
+        """projection: "l2" (plain L2 projection) or "penalty" (the
+        divergence and continuity penalty terms of Sec. 3.2 with factors
+        zeta_d, zeta_c; the penalty parameters come from the extrapolated
+        velocity and are treated as constants by the reverse mode)."""
+        if projection not in ("l2", "penalty"):
+            raise ValueError(projection)
         self.dg = dg
         self.dt = float(dt)
         self.tol = float(solver_tol)
+        self.projection = projection
+        self.zeta = (float(zeta_d), float(zeta_c))
 
     def coefficients(self, first):
         if first:
@@ -204,7 +232,14 @@ class DualSplitting:
         uh = lincomb(dg, -dt / g0, _InvMass.apply(dg, cc), 1.0 / g0, hist)
         rhs = _Div.apply(dg, uh)
         p = _Poisson.apply(dg, lincomb(dg, 0.0, rhs, -g0 / dt, rhs), self.tol)
-        uhh = lincomb(dg, -dt / g0, _InvMass.apply(dg, _Grad.apply(dg, p)), 1.0, uh)
+        if self.projection == "l2":
+            uhh = lincomb(dg, -dt / g0, _InvMass.apply(dg, _Grad.apply(dg, p)), 1.0, uh)
+        else:
+            with torch.no_grad():
+                u_ex = u if first else lincomb(dg, b[0], u, b[1], u_prev)
+                tau_d, tau_c = dg.penalty_parameters(u_ex.detach().contiguous(), dt, *self.zeta)
+            rhs_p = lincomb(dg, -dt / g0, _Grad.apply(dg, p), 1.0, _Mass.apply(dg, uh))
+            uhh = _Projection.apply(dg, rhs_p, tau_d, tau_c, self.tol)
         bh = lincomb(dg, 0.0, uhh, g0 / dt, _Mass.apply(dg, uhh))
         u_new = _Helmholtz.apply(dg, bh, g0 / dt, self.tol)
         return u_new, c

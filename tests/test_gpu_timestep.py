@@ -135,3 +135,29 @@ def test_gradient_taylor_green_32c_k4_20_steps():
     directions (measured worst error 8e-6 at delta = 1e-7, falling linearly
     with delta)."""
     _fd_check(32, 4, 1.0 / 1600, 1e-3, 20, 8, 1e-7, 2e-5)
+
+
+def test_bdf2_penalty_projection_matches_oracle():
+    from paper_1802_01439_gb300.navier_stokes import DualSplitting
+    n, k, nu, dt = (4, 2, 2), 3, 1.0 / 1600, 1e-3
+    ctx = context(n, k, k - 1, mg_precision=32, nu=nu)
+    ds = DualSplitting(ctx, dt, solver_tol=1e-13, projection="penalty")
+    m = dg.Mesh(n)
+    s = dg.Space(m, k)
+    u0 = tgv_field(s, 1e-2, 4)
+    with torch.no_grad():
+        u = ds.run(dev(u0.ravel()), 3)
+    ref = timestep.DualSplitting(m, k, nu, dt, projection="penalty").run(u0, 3)
+    assert rel_err(host(u), ref) <= 1e-9
+
+
+def test_projection_solve_gradcheck():
+    from paper_1802_01439_gb300 import navier_stokes as ns
+    n, k = (2, 1, 2), 2
+    ctx, _ = _stepper(n, k, 0.05, 1e-2, prec=64)
+    s = dg.Space(dg.Mesh(n), k)
+    u = dev(tgv_field(s, 1e-1, 5).ravel())
+    td, tc = ctx.penalty_parameters(u, 0.1, 1.0, 1.0)
+    x = u.clone().requires_grad_()
+    kw = dict(eps=1e-6, atol=1e-7, rtol=1e-6, fast_mode=True)
+    assert torch.autograd.gradcheck(lambda y: ns._Projection.apply(ctx, y, td, tc, 1e-13), (x,), **kw)
