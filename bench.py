@@ -51,15 +51,21 @@ DF_FP32_PER_FP64 = 7.5
 
 
 # ----------------------------------------------------------- flop counts
-def conv_flops_per_cell(N, Q):
-    """FP64 flops (FMA = 2) of the convective kernel per cell, counted from
-    its loops (cell term by z-planes, six faces per cell)."""
+def conv_cell_flops(N, Q):
+    """FP64 flops (FMA = 2, add = 1) of the convective cell kernel per cell,
+    counted from its loops: cell term by z-planes, then the six face
+    integrals added to the face layers."""
     f = 2 * (3 * Q * N ** 3 + 3 * Q * Q * N * N)                      # interpolation x, y
     f += Q * (2 * 3 * Q * Q * N + 3 * Q * Q * (8 + 2 * 3 * N)        # plane values, flux + x test
               + 2 * 9 * N * N * Q + 2 * 6 * N ** 3)                   # y test, z accumulation
-    f += 6 * (2 * 6 * Q * N * N + 2 * 6 * Q * Q * N + 20 * Q * Q     # face traces, LLF flux
-              + 2 * 3 * Q * Q * N + 2 * 3 * Q * N * N + 3 * N * N)    # face tests
-    return f
+    return f + 6 * 3 * N * N
+
+
+def conv_face_flops(N, Q):
+    """FP64 flops of the convective face kernel per face: traces of both
+    cells at the Q^2 points, LLF flux, tests with the face-layer basis."""
+    return (2 * 6 * Q * N * N + 2 * 6 * Q * Q * N + 20 * Q * Q
+            + 2 * 3 * Q * Q * N + 2 * 3 * Q * N * N)
 
 
 def lap_flops_per_cell(N):
@@ -138,12 +144,15 @@ def gpu_arm(args, rank, world):
     d, lp = torch.empty(np_, **f64), torch.empty(np_, **f64)
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
     dofs_per_step = 12 * nu_ + 2 * np_
+    rface = torch.empty(ctx.convective_face_size(), **f64)
     ev = {k: [torch.cuda.Event(enable_timing=True) for _ in range(2)] for k in
-          ("C", "Minv", "D", "L", "G", "H")}
+          ("Cf", "Cc", "Minv", "D", "L", "G", "H")}
     tsum = {k: 0.0 for k in ev}
 
     def step(timed):
-        ops = [("C", lambda: ctx.vmult_convective(c, u)),
+        # the convective operator in its two phases (face kernel, cell kernel)
+        ops = [("Cf", lambda: ctx.convective_faces(rface, u)),
+               ("Cc", lambda: ctx.convective_cells(c, u, rface)),
                ("Minv", lambda: ctx.apply_inverse_mass(uh, c, ncomp=3, space=0)),
                ("D", lambda: ctx.vmult_divergence(d, uh)),
                ("L", lambda: ctx.vmult_laplace(lp, d, space=1)),
@@ -203,22 +212,28 @@ def gpu_arm(args, rank, world):
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e = max_over_ranks(sum(e2e_ms) / len(e2e_ms), world)
 
-    # roofline of the dominant kernel (the convective kernel): ALU bound, on
-    # the FP64 pipe (native) or on the FP32 pipe (double-float)
+    # roofline of the dominant kernel (the convective cell or face kernel):
+    # ALU bound, on the FP64 pipe (native) or on the FP32 pipe (double-float)
     N, Q = K_U + 1, (3 * (K_U + 1)) // 2
-    conv_ms = tsum["C"] / args.steps
-    conv_flops = conv_flops_per_cell(N, Q) * N_ELEM ** 3
+    E = N_ELEM ** 3
+    kern = {"Cc": ("conv_kernel", conv_cell_flops(N, Q) * E), "Cf": ("conv_face_kernel", conv_face_flops(N, Q) * 3 * E)}
+    dom = max(("Cc", "Cf"), key=lambda k: tsum[k])
+    kbase, conv_flops = kern[dom]
+    kern_ms = tsum[dom] / args.steps
     if args.fp64_mode == 1:
-        kname = "conv_kernel<DF64,4,6>"
-        achieved = DF_FP32_PER_FP64 * conv_flops / (conv_ms * 1e-3) / 1e12
+        kname = "%s<DF64,%d,%d>" % (kbase, N, Q)
+        achieved = DF_FP32_PER_FP64 * conv_flops / (kern_ms * 1e-3) / 1e12
         peak, psrc = FP32_PEAK_TFLOPS, ("FP32 ALU: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz; achieved counts "
                                         "7.5 FP32 flops of the double-float emulation per FP64 flop")
         fl = DF_FP32_PER_FP64 * conv_flops
     else:
-        kname = "conv_kernel<F64,4,6>"
-        achieved = conv_flops / (conv_ms * 1e-3) / 1e12
+        kname = "%s<F64,%d,%d>" % (kbase, N, Q)
+        achieved = conv_flops / (kern_ms * 1e-3) / 1e12
         peak, psrc = FP64_PEAK_TFLOPS, "FP64 ALU: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz"
         fl = conv_flops
+    conv_split = {"face_kernel_ms": round(tsum["Cf"] / args.steps, 4),
+                  "cell_kernel_ms": round(tsum["Cc"] / args.steps, 4)}
+    tsum["C"] = tsum.pop("Cf") + tsum.pop("Cc")
     per_op = {k: round(dofs / (tsum[k] / args.steps * 1e-3), 1) for k, dofs in
               (("C", 3 * nu_), ("Minv", 3 * nu_), ("D", 3 * nu_), ("L", np_), ("G", np_), ("H", 3 * nu_))}
     share = {k: round(tsum[k] / sum(tsum.values()), 4) for k in tsum}
@@ -227,18 +242,18 @@ def gpu_arm(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.fp64_mode == 0 else "f64 via double-float (2 x f32, 48-bit significand; "
-                 "parity <= 1e-12 with the FP64 oracle) in the convective and SIPG kernels, native f64 elsewhere",
+                 "parity <= 1e-12 with the FP64 oracle) in every kernel of the step",
         "data": "synthetic (Taylor-Green + seeded noise)",
         "config": {"workload": WORKLOAD, "n_elem": N_ELEM, "degree_u": K_U, "degree_p": K_P,
                    "dofs_per_step": dofs_per_step, "l2": "flushed (256 MiB write) before every step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "per_operator_dofs_per_s": per_op, "time_share": share,
+        "per_operator_dofs_per_s": per_op, "time_share": share, "convective_kernels": conv_split,
         "roofline": {"kernel": kname, "bound": "alu", "achieved": round(achieved, 4),
                      "peak": peak, "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
                      "traffic": None, "flops_per_launch": fl, "peak_source": psrc},
         "e2e": {"value": round(world * dofs_per_step / (e2e * 1e-3), 1), "unit": "DoFs/s",
                 "h2d_bytes_per_step": 3 * nu_ * 8, "d2h_bytes_per_step": 3 * nu_ * 8},
-        "gpu_launches": 6 * args.steps,
+        "gpu_launches": 7 * args.steps,  # face + cell convective, M^-1, D, L, G, H
         "timed_block_wall_s": round(wall, 4),
         "clocks": clk,
     }

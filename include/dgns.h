@@ -120,8 +120,25 @@ int dgns_vmult_gradient(dgns_ctx* ctx, double* dst3, const double* p);
 
 /* Convective term c_h (Sec. 3.2) with F_c = u (x) u and the local
  * Lax-Friedrichs flux, over-integrated with n_q_conv points: dst3 = C(u3),
- * the weak form (not multiplied by M^-1, not negated). */
+ * the weak form (not multiplied by M^-1, not negated).  The first call on a
+ * context allocates a device scratch buffer of 9 E (k_u+1)^2 doubles for the
+ * face integrals (DGNS_ERR_OOM if that fails); make it before capturing
+ * calls into a CUDA graph. */
 int dgns_vmult_convective(dgns_ctx* ctx, double* dst3, const double* u3);
+
+/* The two phases of dgns_vmult_convective, with a caller-owned face buffer.
+ * dgns_convective_face_size: *n = 9 E (k_u+1)^2, the doubles of rface.
+ * dgns_convective_faces: every face once (Sec. 3.2, LLF flux), rface =
+ * [d][cell e][component c][j1 + (k_u+1) j2]: the flux integral of the face
+ * between cell e and its neighbour in +x_d against the face-layer basis of
+ * cell e (j1, j2 the node indices along the two other directions, lower
+ * direction first); the neighbour's integral is its negative.
+ * dgns_convective_cells: the cell term of every cell plus the six face
+ * integrals from rface: dst3 = C(u3).  rface must come from
+ * dgns_convective_faces on the same u3. */
+int dgns_convective_face_size(const dgns_ctx* ctx, long long* n);
+int dgns_convective_faces(dgns_ctx* ctx, double* rface, const double* u3);
+int dgns_convective_cells(dgns_ctx* ctx, double* dst3, const double* u3, const double* rface);
 /* Vector-Jacobian product of the convective term: grad_u3 = (dC/du)^T w3 at
  * u3.  At LLF kinks it uses d|s|/ds = sign(s) (sign(0) = 0) and sends the
  * derivative of max(a, b) to the larger argument (half to each on a tie). */

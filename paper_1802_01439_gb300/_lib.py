@@ -69,6 +69,9 @@ SIGNATURES = {
     "dgns_vmult_divergence": (_I, [_P, _P, _P]),
     "dgns_vmult_gradient": (_I, [_P, _P, _P]),
     "dgns_vmult_convective": (_I, [_P, _P, _P]),
+    "dgns_convective_face_size": (_I, [_P, ctypes.POINTER(ctypes.c_longlong)]),
+    "dgns_convective_faces": (_I, [_P, _P, _P]),
+    "dgns_convective_cells": (_I, [_P, _P, _P, _P]),
     "dgns_vjp_convective": (_I, [_P, _P, _P, _P]),
     "dgns_dissipation": (_I, [_P, _P, ctypes.POINTER(_D)]),
     "dgns_dissipation_grad": (_I, [_P, _P, _P]),

@@ -151,6 +151,22 @@ class Context:
                                              self._vec(u3, n, name="u3")))
         return dst3
 
+    def convective_face_size(self):
+        n = ctypes.c_longlong()
+        check(self.lib.dgns_convective_face_size(self.h, ctypes.byref(n)))
+        return n.value
+
+    def convective_faces(self, rface, u3):
+        check(self.lib.dgns_convective_faces(self.h, self._vec(rface, self.convective_face_size(), name="rface"),
+                                             self._vec(u3, 3 * self.n_u, name="u3")))
+        return rface
+
+    def convective_cells(self, dst3, u3, rface):
+        n = 3 * self.n_u
+        check(self.lib.dgns_convective_cells(self.h, self._vec(dst3, n, name="dst3"), self._vec(u3, n, name="u3"),
+                                             self._vec(rface, self.convective_face_size(), name="rface")))
+        return dst3
+
     def vjp_convective(self, grad_u3, u3, w3):
         n = 3 * self.n_u
         check(self.lib.dgns_vjp_convective(self.h, self._vec(grad_u3, n, name="grad_u3"),

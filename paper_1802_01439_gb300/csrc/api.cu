@@ -376,6 +376,7 @@ void free_ctx(dgns_ctx* c) {
   cudaFree(c->z);
   cudaFree(c->p);
   cudaFree(c->Ap);
+  cudaFree(c->conv_face);
   cudaFree(c->red.part);
   cudaFree(c->red.scal);
   if (c->h_scal) cudaFreeHost(c->h_scal);
@@ -861,20 +862,79 @@ int dgns_vmult_gradient(dgns_ctx* c, double* dst3, const double* p) {
   return st.finish();
 }
 
+namespace {
+int conv_face_buffer(dgns_ctx* c) {
+  if (c->conv_face) return 0;
+  if (cudaMalloc(&c->conv_face, (size_t)9 * c->m.E * c->conv.N * c->conv.N * sizeof(double)) != cudaSuccess) {
+    c->conv_face = nullptr;
+    cudaGetLastError();
+    return fail(DGNS_ERR_OOM, "convective face buffer allocation failed");
+  }
+  return 0;
+}
+int conv_status(int rc) {
+  if (rc == 7) return fail(DGNS_ERR_UNSUPPORTED, "convective kernel: unsupported (k, n_q_conv)");
+  return rc;
+}
+}  // namespace
+
 int dgns_vmult_convective(dgns_ctx* c, double* dst3, const double* u3) {
   g_err.clear();
   if (!c) return fail(DGNS_ERR_INVALID_ARG, "ctx is null");
   DG_NONNULL(dst3, u3);
   const size_t bu = (size_t)c->n[0] * 3 * sizeof(double);
   if (overlaps(dst3, bu, u3, bu)) return fail(DGNS_ERR_ALIAS, "dst overlaps src");
+  DG_TRY(conv_face_buffer(c));
   Staged st(c);
   const void* s;
   void* d;
   DG_TRY(st.in(u3, bu, &s));
   DG_TRY(st.out(dst3, bu, &d));
-  int rc = convective_apply(c->m, (const double*)s, (double*)d, c->conv, c->d.fp64_mode == 1, c->s);
-  if (rc == 7) return fail(DGNS_ERR_UNSUPPORTED, "convective kernel: unsupported (k, n_q_conv)");
-  DG_TRY(rc);
+  DG_TRY(conv_status(convective_launch(3, c->m, (const double*)s, c->conv_face, (double*)d, c->conv,
+                                       c->d.fp64_mode == 1, c->s)));
+  return st.finish();
+}
+
+int dgns_convective_face_size(const dgns_ctx* c, long long* n) {
+  if (!c || !n) return fail(DGNS_ERR_INVALID_ARG, "null argument");
+  *n = 9LL * c->m.E * c->conv.N * c->conv.N;
+  return 0;
+}
+
+int dgns_convective_faces(dgns_ctx* c, double* rface, const double* u3) {
+  g_err.clear();
+  if (!c) return fail(DGNS_ERR_INVALID_ARG, "ctx is null");
+  DG_NONNULL(rface, u3);
+  const size_t bu = (size_t)c->n[0] * 3 * sizeof(double);
+  const size_t bf = (size_t)9 * c->m.E * c->conv.N * c->conv.N * sizeof(double);
+  if (overlaps(rface, bf, u3, bu)) return fail(DGNS_ERR_ALIAS, "rface overlaps u3");
+  Staged st(c);
+  const void* s;
+  void* f;
+  DG_TRY(st.in(u3, bu, &s));
+  DG_TRY(st.out(rface, bf, &f));
+  DG_TRY(conv_status(convective_launch(1, c->m, (const double*)s, (double*)f, nullptr, c->conv,
+                                       c->d.fp64_mode == 1, c->s)));
+  return st.finish();
+}
+
+int dgns_convective_cells(dgns_ctx* c, double* dst3, const double* u3, const double* rface) {
+  g_err.clear();
+  if (!c) return fail(DGNS_ERR_INVALID_ARG, "ctx is null");
+  DG_NONNULL(dst3, u3, rface);
+  const size_t bu = (size_t)c->n[0] * 3 * sizeof(double);
+  const size_t bf = (size_t)9 * c->m.E * c->conv.N * c->conv.N * sizeof(double);
+  if (overlaps(dst3, bu, u3, bu) || overlaps(dst3, bu, rface, bf))
+    return fail(DGNS_ERR_ALIAS, "dst3 overlaps an input");
+  Staged st(c);
+  const void* s;
+  const void* f;
+  void* d;
+  DG_TRY(st.in(u3, bu, &s));
+  DG_TRY(st.in(rface, bf, &f));
+  DG_TRY(st.out(dst3, bu, &d));
+  DG_TRY(conv_status(convective_launch(2, c->m, (const double*)s, (double*)f, (double*)d, c->conv,
+                                       c->d.fp64_mode == 1, c->s)));
   return st.finish();
 }
 

@@ -55,6 +55,7 @@ struct dgns_ctx {
   dgns::DivHost div;
   dgns::GradHost grad;
   dgns::ConvHost conv;
+  double* conv_face = nullptr;  // face integrals of the convective term, 9 E N^2
   dgns::ProjHost proj;
   // multigrid (pressure space)
   int mg_prec = 0;

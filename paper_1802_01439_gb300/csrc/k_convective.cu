@@ -10,11 +10,12 @@
 //             Q planes of constant z, evaluates the flux on the plane, applies
 //             the transposed x and y sweeps and accumulates the z contraction
 //             in registers.
-// Face terms  per face and side, traces of both cells at the Q^2 face points
-//             (LGL: the face values are the nodal values of the face layer),
-//             F* = {{u (x) u}}.n + max(|u-.n|, |u+.n|) (u- - u+), added to
-//             the own face layer with sign + (own cell is '-') or - (own
-//             cell is '+').  Each cell evaluates its six faces.
+// Face terms  per face, traces of both cells at the Q^2 face points (LGL:
+//             the face values are the nodal values of the face layer),
+//             F* = {{u (x) u}}.n + max(|u-.n|, |u+.n|) (u- - u+), tested
+//             with the face-layer basis: +R for the '-' cell, -R for the '+'
+//             cell.  A face kernel evaluates every face once and writes R;
+//             the cell kernel adds the six R of its faces on its way out.
 #include "arith.cuh"
 #include "ops.h"
 
@@ -35,11 +36,12 @@ struct ConvTab {
   double area[3];  // product of the tangential cell sizes of faces normal to d
 };
 
-// Threads per cell of the forward convective kernel: at least one warp, so
-// that the many small work items of a phase are spread over more lanes.
+// Threads per cell of the forward convective kernel: one warp up to N = 5;
+// above, more threads per cell as the cell's shared memory grows (from
+// N = 10 on one cell fills an SM's shared memory, so it gets 16 warps).
 template <int N>
 constexpr int conv_threads() {
-  return N * N < 32 ? 32 : N * N;
+  return N <= 5 ? 32 : N == 6 ? 64 : N == 7 ? 128 : N <= 9 ? 256 : 512;
 }
 template <int N>
 constexpr int conv_fwd_cells_per_block() {
@@ -51,16 +53,47 @@ struct ConvLayout {
   static constexpr int N3 = N * N * N;
   static constexpr int U = 3 * N3;               // nodal velocity
   static constexpr int U1 = 3 * Q * N * N;       // x-interpolated; later: result
-  static constexpr int U2 = 3 * Q * Q * N;       // xy-interpolated; later: face work
+  static constexpr int U2 = 3 * Q * Q * N;       // xy-interpolated
   static constexpr int P = 6 * Q * Q;            // one z-plane: u and the weighted u
   static constexpr int X = 9 * N * Q;            // x-tested plane
   static constexpr int Y = 6 * N * N;            // xy-tested plane
-  static constexpr int FACE = 6 * N * N + 6 * Q * N + 6 * Q * Q + 3 * Q * Q;
-  static constexpr int U2F = U2 > FACE ? U2 : FACE;
   static constexpr int PXY = P + X + Y;
   static constexpr int UP = U > PXY ? U : PXY;   // nodal u first, plane work later
-  static constexpr int PER = UP + U1 + U2F;
+  static constexpr int PER = UP + U1 + U2;
 };
+
+// Threads of one face of the face kernel: one warp up to N = 6, four warps
+// (one face per block) above.
+template <int N>
+constexpr int face_threads() {
+  return N <= 6 ? 32 : 128;
+}
+template <int N>
+constexpr int faces_per_block() {
+  return face_threads<N>() == 32 ? 4 : 1;
+}
+
+// Face work space; the weighted flux (3 Q^2) reuses the first sweep's
+// region and the first test sweep (3 Q N) the face layers' (Q <= 2N).
+template <int N, int Q>
+struct FaceLayout {
+  static_assert(Q <= 2 * N, "aliasing needs Q <= 2N");
+  static constexpr int T0 = 6 * N * N;  // face layers of both cells; later the first test sweep
+  static constexpr int G1 = 6 * Q * N;  // after the first sweep; later the weighted flux
+  static constexpr int G2 = 6 * Q * Q;  // traces at the face points
+  static constexpr int PER = T0 + G1 + G2;
+};
+
+// Barrier of the threads of one cell or face: a warp barrier when they are
+// exactly one warp, else a block barrier (then the block holds whole groups
+// and every thread reaches it).
+template <int NT>
+__device__ __forceinline__ void group_sync() {
+  if (NT == 32)
+    __syncwarp();
+  else
+    __syncthreads();
+}
 
 __device__ __forceinline__ int node3(int N, int d, int a, int t1, int j1, int t2, int j2) {
   int c[3];
@@ -86,7 +119,7 @@ struct ConvTabT {
 // because the items index them by thread.
 template <class A, int N, int Q>
 __global__ void __launch_bounds__(conv_fwd_cells_per_block<N>() * conv_threads<N>())
-    conv_kernel(const double* __restrict__ u3, double* __restrict__ dst3,
+    conv_kernel(const double* __restrict__ u3, const double* __restrict__ rface, double* __restrict__ dst3,
                 const __grid_constant__ ConvTabT<typename A::V, N, Q> tb, const MeshDims m) {
   typedef typename A::V V;
   typedef typename A::Acc Acc;
@@ -114,7 +147,6 @@ __global__ void __launch_bounds__(conv_fwd_cells_per_block<N>() * conv_threads<N
   V* sU1 = sU + LY::UP;
   V* sU2 = sU1 + LY::U1;
   V* sOut = sU1;   // reused after the interpolation
-  V* sFace = sU2;  // reused after the cell term
 
   unsigned el = 0;
   CellXYZ cx{};
@@ -137,7 +169,7 @@ __global__ void __launch_bounds__(conv_fwd_cells_per_block<N>() * conv_threads<N
       for (int j = 0; j < N; ++j) A::acc_fma(a, sS[q * N + j], x[j]);
       sU1[c * Q * NN + l * Q + q] = A::acc_get(a);
     }
-  __syncthreads();
+  group_sync<NT>();
   // y interpolation: item (c, qx, z, qy)
   if (active)
     for (int it = t; it < 3 * Q * N * Q; it += NT) {
@@ -151,7 +183,7 @@ __global__ void __launch_bounds__(conv_fwd_cells_per_block<N>() * conv_threads<N
       for (int j = 0; j < N; ++j) A::acc_fma(a, sS[qy * N + j], x[Q * j]);
       sU2[c * QQ * N + qx + Q * qy + QQ * z] = A::acc_get(a);
     }
-  __syncthreads();
+  group_sync<NT>();
   if (active)
     for (int i = t; i < 3 * N3; i += NT) sOut[i] = A::zero();
 
@@ -171,7 +203,7 @@ __global__ void __launch_bounds__(conv_fwd_cells_per_block<N>() * conv_threads<N
         sP[it] = u;
         sP[3 * QQ + it] = A::mul(A::mul(w3, tb.jac[c]), u);
       }
-    __syncthreads();
+    group_sync<NT>();
     // P2: F_cd = u_c (weighted u_d) on x-lines, tested with D_x^T (d = x) or
     // S_x^T; item (c, d, qy)
     if (active)
@@ -192,7 +224,7 @@ __global__ void __launch_bounds__(conv_fwd_cells_per_block<N>() * conv_threads<N
 #pragma unroll
         for (int x = 0; x < N; ++x) sX[cd * N * Q + x + N * qy] = A::acc_get(a[x]);
       }
-    __syncthreads();
+    group_sync<NT>();
     // P3: Y1 = S_y^T X1 + D_y^T X2, Y3 = S_y^T X3; item (c, x, y)
     if (active)
       for (int it = t; it < 3 * NN; it += NT) {
@@ -211,7 +243,7 @@ __global__ void __launch_bounds__(conv_fwd_cells_per_block<N>() * conv_threads<N
         sY[(c * 2 + 0) * NN + r] = A::acc_get(y1);
         sY[(c * 2 + 1) * NN + r] = A::acc_get(y3);
       }
-    __syncthreads();
+    group_sync<NT>();
     // P4: out -= S_z(qz) Y1 + D_z(qz) Y3; item (c, x, y, z)
     if (active)
       for (int it = t; it < 3 * N3; it += NT) {
@@ -224,123 +256,162 @@ __global__ void __launch_bounds__(conv_fwd_cells_per_block<N>() * conv_threads<N
         sOut[it] = A::acc_get(a);
       }
   }
-  __syncthreads();
+  group_sync<NT>();
 
-  // ---------------------------------------------------------------- faces
-  V* T0 = sFace;              // [side][c][j1 + N j2]   6 N N
-  V* G1 = T0 + 6 * NN;        // [side][c][q1 + Q j2]   6 Q N
-  V* G2 = G1 + 6 * Q * N;     // [side][c][q1 + Q q2]   6 Q Q
-  V* H = G2 + 6 * QQ;         // [c][q1 + Q q2]         3 Q Q
-  V* K1 = G1;                 // [c][q1 + Q j2] reuses G1
-  for (int d = 0; d < 3; ++d) {
-    const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
-    for (int side = 1; side >= -1; side -= 2) {
-      unsigned nb = 0;
-      if (active) {
-        if (d == 0) nb = neighbor32<0>(cx, side, m);
-        else if (d == 1) nb = neighbor32<1>(cx, side, m);
-        else nb = neighbor32<2>(cx, side, m);
-      }
-      const int aown = side > 0 ? N - 1 : 0, anb = side > 0 ? 0 : N - 1;
-      // F0: the face layers of both cells
-      if (active)
-        for (int it = t; it < 6 * NN; it += NT) {
-          const int sc = it / NN, r = it - sc * NN;
-          const int s = sc / 3, c = sc - 3 * s;
-          const int j1 = r % N, j2 = r / N;
-          T0[it] = s == 0 ? A::load(u3 + ((size_t)c * m.E + el) * N3 + node3(N, d, aown, t1, j1, t2, j2))
-                          : A::load(u3 + ((size_t)c * m.E + nb) * N3 + node3(N, d, anb, t1, j1, t2, j2));
-        }
-      __syncthreads();
-      // F1: along t1; item (sc, j2, q1)
-      if (active)
-        for (int it = t; it < 6 * N * Q; it += NT) {
-          const int q1 = it % Q, r = it / Q;
-          const int sc = r / N, j2 = r - sc * N;
-          const V* v = T0 + sc * NN + N * j2;
-          Acc a;
-          A::acc_zero(a);
-#pragma unroll
-          for (int j = 0; j < N; ++j) A::acc_fma(a, sS[q1 * N + j], v[j]);
-          G1[sc * Q * N + q1 + Q * j2] = A::acc_get(a);
-        }
-      __syncthreads();
-      // F2: along t2; item (sc, q1, q2)
-      if (active)
-        for (int it = t; it < 6 * QQ; it += NT) {
-          const int q2 = it % Q, r = it / Q;
-          const int sc = r / Q, q1 = r - sc * Q;
-          const V* v = G1 + sc * Q * N + q1;
-          Acc a;
-          A::acc_zero(a);
-#pragma unroll
-          for (int j = 0; j < N; ++j) A::acc_fma(a, sS[q2 * N + j], v[Q * j]);
-          G2[sc * QQ + q1 + Q * q2] = A::acc_get(a);
-        }
-      __syncthreads();
-      // F3: LLF flux at the face points, weighted, signed for the own cell
-      if (active)
-        for (int it = t; it < QQ; it += NT) {
-          const int q1 = it % Q, q2 = it / Q;
-          const int sm_ = side > 0 ? 0 : 1, sp_ = side > 0 ? 1 : 0;  // trace index of '-' / '+'
-          V um[3], up[3];
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            um[c] = G2[(sm_ * 3 + c) * QQ + it];
-            up[c] = G2[(sp_ * 3 + c) * QQ + it];
-          }
-          const V unm = um[d], unp = up[d];
-          const V am = A::absval(unm), ap = A::absval(unp);
-          const V lam = A::greater(am, ap) ? am : ap;
-          V wgt = A::mul(A::mul(tb.w[q1], tb.w[q2]), tb.area[d]);
-          if (side < 0) wgt = A::neg(wgt);
-          // 0.5 (u-_c un- + u+_c un+), the halving is exact
-          const V hm = A::half(unm), hp = A::half(unp);
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            Acc f;
-            A::acc_zero(f);
-            A::acc_fma(f, um[c], hm);
-            A::acc_fma(f, up[c], hp);
-            A::acc_fma(f, lam, A::sub(um[c], up[c]));
-            H[c * QQ + it] = A::mul(wgt, A::acc_get(f));
-          }
-        }
-      __syncthreads();
-      // F4: test along t2; item (c, j2, q1)
-      if (active)
-        for (int it = t; it < 3 * Q * N; it += NT) {
-          const int q1 = it % Q, r = it / Q;
-          const int c = r / N, j2 = r - c * N;
-          Acc a;
-          A::acc_zero(a);
-#pragma unroll 1
-          for (int q2 = 0; q2 < Q; ++q2) A::acc_fma(a, sS[q2 * N + j2], H[c * QQ + q1 + Q * q2]);
-          K1[c * Q * N + q1 + Q * j2] = A::acc_get(a);
-        }
-      __syncthreads();
-      // F5: test along t1, add into the own face layer; item (c, j2, j1)
-      if (active)
-        for (int it = t; it < 3 * NN; it += NT) {
-          const int c = it / NN, r = it - c * NN;
-          const int j1 = r % N, j2 = r / N;
-          const int node = c * N3 + node3(N, d, aown, t1, j1, t2, j2);
-          Acc a;
-          A::acc_set(a, sOut[node]);
-#pragma unroll 1
-          for (int q1 = 0; q1 < Q; ++q1) A::acc_fma(a, sS[q1 * N + j1], K1[c * Q * N + q1 + Q * j2]);
-          sOut[node] = A::acc_get(a);
-        }
-      __syncthreads();
+  // face integrals from the face kernel: +R on the layer N-1 (this cell is
+  // the '-' side of its face), -R of the '-' neighbour on the layer 0
+  if (active) {
+    const unsigned nbm0 = neighbor32<0>(cx, -1, m), nbm1 = neighbor32<1>(cx, -1, m), nbm2 = neighbor32<2>(cx, -1, m);
+    const size_t E = (size_t)m.E, FS = 3 * NN;
+    for (int it = t; it < 3 * N3; it += NT) {
+      const int c = it / N3, r = it - c * N3;
+      const int x = r % N, yz = r / N;
+      const int y = yz % N, z = yz / N;
+      const double* rc = rface + c * NN;
+      V v = sOut[it];
+      if (x == N - 1) v = A::add(v, A::load(rc + el * FS + y + N * z));
+      if (x == 0) v = A::sub(v, A::load(rc + nbm0 * FS + y + N * z));
+      if (y == N - 1) v = A::add(v, A::load(rc + (E + el) * FS + x + N * z));
+      if (y == 0) v = A::sub(v, A::load(rc + (E + nbm1) * FS + x + N * z));
+      if (z == N - 1) v = A::add(v, A::load(rc + (2 * E + el) * FS + x + N * y));
+      if (z == 0) v = A::sub(v, A::load(rc + (2 * E + nbm2) * FS + x + N * y));
+      dst3[((size_t)c * m.E + el) * N3 + r] = A::store(v);
     }
   }
+}
+
+// Face term of Sec. 3.2, one evaluation per interior face (the mesh is
+// periodic, so every face is interior).  Face (e, d) lies between cell e
+// ('-', its layer N-1 along d) and its + neighbour along d ('+', layer 0).
+// R = (S (x) S)^T [w1 w2 |face| F*] with F* = {{u (x) u}}.n + lambda [[u]],
+// n = +e_d, is the face integral against the '-' cell's face-layer basis;
+// the '+' cell's is -R (same trace basis, opposite normal).  Written to
+// rface[d][e][c][j1 + N j2] (j1, j2: the two tangential directions in
+// increasing order).
+template <class A, int N, int Q>
+__global__ void __launch_bounds__(faces_per_block<N>() * face_threads<N>())
+    conv_face_kernel(const double* __restrict__ u3, double* __restrict__ rface,
+                     const __grid_constant__ ConvTabT<typename A::V, N, Q> tb, const MeshDims m) {
+  typedef typename A::V V;
+  typedef typename A::Acc Acc;
+  typedef FaceLayout<N, Q> LY;
+  constexpr int FT = face_threads<N>(), FPB = faces_per_block<N>(), N3 = N * N * N, NN = N * N, QQ = Q * Q;
+  V* sm = reinterpret_cast<V*>(dyn_smem());
+  const int slot = threadIdx.x / FT;
+  const int t = threadIdx.x - slot * FT;
+  const int d = blockIdx.y;
+  const long long c0 = (long long)blockIdx.x * FPB;
+  const long long rem = m.E - c0;
+  const int nvalid = rem < FPB ? (int)rem : FPB;
+  const bool active = slot < nvalid;
+  V* sS = sm + FPB * LY::PER;
+  for (int i = threadIdx.x; i < Q * N; i += blockDim.x) sS[i] = tb.S[i];
+  __syncthreads();
+  V* T0 = sm + slot * LY::PER;   // [s][c][j1 + N j2]   s = 0: '-', 1: '+'
+  V* G1 = T0 + LY::T0;           // [s][c][q1 + Q j2]
+  V* G2 = G1 + LY::G1;           // [s][c][q1 + Q q2]
+  V* H = G1;                     // [c][q1 + Q q2]
+  V* K1 = T0;                    // [c][q1 + Q j2]
+  const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+  unsigned el = 0, nb = 0;
+  if (active) {
+    const CellXYZ cx = cell_xyz((unsigned)(c0 + slot), m);
+    el = cx.el;
+    nb = d == 0 ? neighbor32<0>(cx, 1, m) : (d == 1 ? neighbor32<1>(cx, 1, m) : neighbor32<2>(cx, 1, m));
+  }
+  // F0: the face layers of both cells
   if (active)
-    for (int c = 0; c < 3; ++c)
-      for (int i = t; i < N3; i += NT) dst3[((size_t)c * m.E + el) * N3 + i] = A::store(sOut[c * N3 + i]);
+    for (int it = t; it < 6 * NN; it += FT) {
+      const int sc = it / NN, r = it - sc * NN;
+      const int sd = sc / 3, c = sc - 3 * sd;
+      const int j1 = r % N, j2 = r / N;
+      const unsigned cell = sd == 0 ? el : nb;
+      T0[it] = A::load(u3 + ((size_t)c * m.E + cell) * N3 + node3(N, d, sd == 0 ? N - 1 : 0, t1, j1, t2, j2));
+    }
+  group_sync<FT>();
+  // F1: interpolate along t1; item (sc, j2, q1)
+  if (active)
+    for (int it = t; it < 6 * N * Q; it += FT) {
+      const int q1 = it % Q, r = it / Q;
+      const int sc = r / N, j2 = r - sc * N;
+      const V* v = T0 + sc * NN + N * j2;
+      Acc a;
+      A::acc_zero(a);
+#pragma unroll
+      for (int j = 0; j < N; ++j) A::acc_fma(a, sS[q1 * N + j], v[j]);
+      G1[sc * Q * N + q1 + Q * j2] = A::acc_get(a);
+    }
+  group_sync<FT>();
+  // F2: along t2; item (sc, q1, q2)
+  if (active)
+    for (int it = t; it < 6 * QQ; it += FT) {
+      const int q2 = it % Q, r = it / Q;
+      const int sc = r / Q, q1 = r - sc * Q;
+      const V* v = G1 + sc * Q * N + q1;
+      Acc a;
+      A::acc_zero(a);
+#pragma unroll
+      for (int j = 0; j < N; ++j) A::acc_fma(a, sS[q2 * N + j], v[Q * j]);
+      G2[sc * QQ + q1 + Q * q2] = A::acc_get(a);
+    }
+  group_sync<FT>();
+  // F3: LLF flux at the face points, times the quadrature weight
+  if (active)
+    for (int it = t; it < QQ; it += FT) {
+      const int q1 = it % Q, q2 = it / Q;
+      V um[3], up[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        um[c] = G2[c * QQ + it];
+        up[c] = G2[(3 + c) * QQ + it];
+      }
+      const V unm = d == 0 ? um[0] : (d == 1 ? um[1] : um[2]);
+      const V unp = d == 0 ? up[0] : (d == 1 ? up[1] : up[2]);
+      const V am = A::absval(unm), ap = A::absval(unp);
+      const V lam = A::greater(am, ap) ? am : ap;
+      const V wgt = A::mul(A::mul(tb.w[q1], tb.w[q2]), tb.area[d]);
+      // 0.5 (u-_c un- + u+_c un+), the halving is exact
+      const V hm = A::half(unm), hp = A::half(unp);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        Acc f;
+        A::acc_zero(f);
+        A::acc_fma(f, um[c], hm);
+        A::acc_fma(f, up[c], hp);
+        A::acc_fma(f, lam, A::sub(um[c], up[c]));
+        H[c * QQ + it] = A::mul(wgt, A::acc_get(f));
+      }
+    }
+  group_sync<FT>();
+  // F4: test along t2; item (c, j2, q1)
+  if (active)
+    for (int it = t; it < 3 * Q * N; it += FT) {
+      const int q1 = it % Q, r = it / Q;
+      const int c = r / N, j2 = r - c * N;
+      Acc a;
+      A::acc_zero(a);
+#pragma unroll 1
+      for (int q2 = 0; q2 < Q; ++q2) A::acc_fma(a, sS[q2 * N + j2], H[c * QQ + q1 + Q * q2]);
+      K1[c * Q * N + q1 + Q * j2] = A::acc_get(a);
+    }
+  group_sync<FT>();
+  // F5: test along t1, store; item (c, j2, j1)
+  if (active) {
+    double* out = rface + ((size_t)d * m.E + el) * 3 * NN;
+    for (int it = t; it < 3 * NN; it += FT) {
+      const int c = it / NN, r = it - c * NN;
+      const int j1 = r % N, j2 = r / N;
+      Acc a;
+      A::acc_zero(a);
+#pragma unroll 1
+      for (int q1 = 0; q1 < Q; ++q1) A::acc_fma(a, sS[q1 * N + j1], K1[c * Q * N + q1 + Q * j2]);
+      out[it] = A::store(A::acc_get(a));
+    }
+  }
 }
 
 template <class A, int N, int Q>
-int launch_conv(const MeshDims& m, const double* u3, double* dst3, const ConvHost& h, cudaStream_t s) {
+ConvTabT<typename A::V, N, Q> conv_tables(const ConvHost& h) {
   ConvTabT<typename A::V, N, Q> tb;
   for (int i = 0; i < Q * N; ++i) {
     tb.S[i] = A::make(h.S[i]);
@@ -352,15 +423,33 @@ int launch_conv(const MeshDims& m, const double* u3, double* dst3, const ConvHos
     tb.jac[d] = A::make(j);
     tb.area[d] = A::make(j);
   }
-  constexpr int EPB = conv_fwd_cells_per_block<N>();
+  return tb;
+}
+
+// part: bit 0 the face kernel (u3 -> rface), bit 1 the cell kernel
+// (u3, rface -> dst3).
+template <class A, int N, int Q>
+int launch_conv(int part, const MeshDims& m, const double* u3, double* rface, double* dst3, const ConvHost& h,
+                cudaStream_t s) {
+  const ConvTabT<typename A::V, N, Q> tb = conv_tables<A, N, Q>(h);
+  constexpr int EPB = conv_fwd_cells_per_block<N>(), FPB = faces_per_block<N>();
   const size_t smem = ((size_t)EPB * ConvLayout<N, Q>::PER + 2 * Q * N) * sizeof(double);
-  if (smem > 232448) return 7;
+  const size_t fsmem = ((size_t)FPB * FaceLayout<N, Q>::PER + Q * N) * sizeof(double);
+  if (smem > 232448 || fsmem > 232448) return 7;
   if (cudaFuncSetAttribute(conv_kernel<A, N, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-      cudaSuccess)
+          cudaSuccess ||
+      cudaFuncSetAttribute(conv_face_kernel<A, N, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem) !=
+          cudaSuccess)
     return 2;
   if (m.E == 0) return 0;
-  const long long blocks = (m.E + EPB - 1) / EPB;
-  conv_kernel<A, N, Q><<<(unsigned)blocks, EPB * conv_threads<N>(), smem, s>>>(u3, dst3, tb, m);
+  if (part & 1) {
+    const dim3 fgrid((unsigned)((m.E + FPB - 1) / FPB), 3);
+    conv_face_kernel<A, N, Q><<<fgrid, FPB * face_threads<N>(), fsmem, s>>>(u3, rface, tb, m);
+  }
+  if (part & 2) {
+    const long long blocks = (m.E + EPB - 1) / EPB;
+    conv_kernel<A, N, Q><<<(unsigned)blocks, EPB * conv_threads<N>(), smem, s>>>(u3, rface, dst3, tb, m);
+  }
   return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }
 
@@ -743,15 +832,16 @@ int launch_conv_vjp(const MeshDims& m, const double* u3, const double* w3, doubl
 
 // Supported: Q = floor(3N/2) (the 3/2 rule) and Q = N; arithmetic FP64 or
 // double-float (emulated = true).
-int convective_apply(const MeshDims& m, const double* u3, double* dst3, const ConvHost& t, bool emulated,
-                     cudaStream_t s) {
+int convective_launch(int part, const MeshDims& m, const double* u3, double* rface, double* dst3,
+                      const ConvHost& t, bool emulated, cudaStream_t s) {
   const int N = t.N, Q = t.Q;
-#define DGNS_CONV(NV)                                                                             \
-  if (N == NV && Q == (3 * NV) / 2)                                                               \
-    return emulated ? launch_conv<DF64, NV, (3 * NV) / 2>(m, u3, dst3, t, s)                      \
-                    : launch_conv<F64, NV, (3 * NV) / 2>(m, u3, dst3, t, s);                      \
-  if (N == NV && Q == NV)                                                                         \
-    return emulated ? launch_conv<DF64, NV, NV>(m, u3, dst3, t, s) : launch_conv<F64, NV, NV>(m, u3, dst3, t, s);
+#define DGNS_CONV(NV)                                                                                 \
+  if (N == NV && Q == (3 * NV) / 2)                                                                   \
+    return emulated ? launch_conv<DF64, NV, (3 * NV) / 2>(part, m, u3, rface, dst3, t, s)             \
+                    : launch_conv<F64, NV, (3 * NV) / 2>(part, m, u3, rface, dst3, t, s);             \
+  if (N == NV && Q == NV)                                                                             \
+    return emulated ? launch_conv<DF64, NV, NV>(part, m, u3, rface, dst3, t, s)                       \
+                    : launch_conv<F64, NV, NV>(part, m, u3, rface, dst3, t, s);
   DGNS_CONV(2)
   DGNS_CONV(3)
   DGNS_CONV(4)

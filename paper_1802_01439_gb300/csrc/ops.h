@@ -81,9 +81,11 @@ struct ConvHost {
   double w[18];          // Gauss weights on [0,1]
   double h[3];
 };
-// emulated: double-float arithmetic on the FP32 pipe (else native FP64)
-int convective_apply(const MeshDims& m, const double* u3, double* dst3, const ConvHost& t, bool emulated,
-                     cudaStream_t s);
+// part: bit 0 the face kernel (u3 -> rface: the face integrals, 9 E N^2
+// doubles, see conv_face_kernel), bit 1 the cell kernel (u3, rface -> dst3).
+// emulated: double-float arithmetic on the FP32 pipe (else native FP64).
+int convective_launch(int part, const MeshDims& m, const double* u3, double* rface, double* dst3,
+                      const ConvHost& t, bool emulated, cudaStream_t s);
 int convective_vjp(const MeshDims& m, const double* u3, const double* w3, double* dst3,
                    const ConvHost& t, cudaStream_t s);
 

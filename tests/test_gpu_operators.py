@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 import torch
 
-from oracle import dg
+from oracle import dg, rules
 from tests.gpu_common import build_lib, context, dev, host, random_field, rel_err, tgv_field
 
 pytestmark = pytest.mark.gpu
@@ -124,6 +124,49 @@ def test_convective(n, k, field, mode):
     y = torch.empty(u.size, dtype=torch.float64, device="cuda")
     ctx.vmult_convective(y, dev(u))
     assert rel_err(host(y), ref) <= TOL
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("n,k", [((3, 2, 2), 3), ((2, 1, 3), 2), ((1, 2, 1), 7)])
+def test_convective_two_phases(n, k, mode):
+    """Face kernel + cell kernel through the two-phase entry points give the
+    one-call result exactly, and the oracle's result."""
+    ctx = context(n, k, max(k - 1, 1), mg_precision=0, fp64_mode=mode)
+    s = dg.Space(dg.Mesh(n), k)
+    u = dev(tgv_field(s, 1e-2, 3))
+    rf = torch.empty(ctx.convective_face_size(), dtype=torch.float64, device="cuda")
+    assert rf.numel() == 9 * s.mesh.E * (k + 1) ** 2
+    y1 = torch.empty_like(u)
+    y2 = torch.empty_like(u)
+    ctx.convective_faces(rf, u)
+    ctx.convective_cells(y1, u, rf)
+    ctx.vmult_convective(y2, u)
+    assert torch.equal(y1, y2)
+    assert rel_err(host(y1), dg.Convective(s).apply(host(u).reshape(3, s.mesh.E, -1))) <= TOL
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_convective_face_integrals_of_a_constant_field(mode):
+    """For a constant velocity the LLF jump term vanishes and the face
+    integral is u_c u_d h_t1 h_t2 omega_j1 omega_j2 (omega: integrals of the
+    nodal basis on [0,1], i.e. the LGL weights), independent of the face."""
+    n, k = (3, 2, 4), 3
+    ctx = context(n, k, k - 1, mg_precision=0, fp64_mode=mode)
+    m = dg.Mesh(n)
+    s = dg.Space(m, k)
+    uc = np.array([0.7, -0.4, 1.3])
+    u = dev(np.repeat(uc, m.E * s.ndofs_cell))
+    rf = torch.empty(ctx.convective_face_size(), dtype=torch.float64, device="cuda")
+    ctx.convective_faces(rf, u)
+    xg, wg = rules.gauss(k + 1)
+    omega = wg @ rules.lagrange(rules.lgl_nodes(k), xg)[0]
+    got = host(rf).reshape(3, m.E, 3, k + 1, k + 1)    # [d][e][c][j2][j1]
+    for d in range(3):
+        t1, t2 = [a for a in range(3) if a != d]
+        ref = m.h[t1] * m.h[t2] * np.outer(omega, omega)   # [j2][j1] (symmetric)
+        for c in range(3):
+            want = uc[c] * uc[d] * ref
+            assert np.max(np.abs(got[d, :, c] - want)) <= 1e-13 * np.max(np.abs(want))
 
 
 def test_host_pointers_are_staged():
