@@ -56,7 +56,7 @@ def conv_cell_flops(N, Q):
     counted from its loops: cell term by z-planes, then the six face
     integrals added to the face layers."""
     f = 2 * (3 * Q * N ** 3 + 3 * Q * Q * N * N)                      # interpolation x, y
-    f += Q * (2 * 3 * Q * Q * N + 3 * Q * Q * (8 + 2 * 3 * N)        # plane values, flux + x test
+    f += Q * (2 * 3 * Q * Q * N + 9 * Q * Q * (1 + 2 * N)           # plane values, flux + x test
               + 2 * 9 * N * N * Q + 2 * 6 * N ** 3)                   # y test, z accumulation
     return f + 6 * 3 * N * N
 
@@ -64,8 +64,8 @@ def conv_cell_flops(N, Q):
 def conv_face_flops(N, Q):
     """FP64 flops of the convective face kernel per face: traces of both
     cells at the Q^2 points, LLF flux, tests with the face-layer basis."""
-    return (2 * 6 * Q * N * N + 2 * 6 * Q * Q * N + 20 * Q * Q
-            + 2 * 3 * Q * Q * N + 2 * 3 * Q * N * N)
+    return (2 * 6 * Q * N * N + 2 * 6 * Q * Q * N + 23 * Q * Q
+            + 2 * 3 * Q * Q * N + 2 * 3 * Q * N * N + 3 * N * N)
 
 
 def lap_flops_per_cell(N):

@@ -33,6 +33,7 @@ struct F32 {
   __device__ __forceinline__ static void acc_zero(Acc& a) { a = 0.0f; }
   __device__ __forceinline__ static void acc_set(Acc& a, V x) { a = x; }
   __device__ __forceinline__ static void acc_fma(Acc& a, V c, V x) { a = fmaf(c, x, a); }
+  __device__ __forceinline__ static void acc_first(Acc& a, V c, V x) { a = c * x; }
   __device__ __forceinline__ static V acc_get(const Acc& a) { return a; }
   __device__ __forceinline__ static G store(V x) { return x; }
 };
@@ -50,6 +51,7 @@ struct F64 {
   __device__ __forceinline__ static void acc_zero(Acc& a) { a = 0.0; }
   __device__ __forceinline__ static void acc_set(Acc& a, V x) { a = x; }
   __device__ __forceinline__ static void acc_fma(Acc& a, V c, V x) { a = fma(c, x, a); }
+  __device__ __forceinline__ static void acc_first(Acc& a, V c, V x) { a = c * x; }
   __device__ __forceinline__ static V acc_get(const Acc& a) { return a; }
   __device__ __forceinline__ static V add(V a, V b) { return a + b; }
   __device__ __forceinline__ static V sub(V a, V b) { return a - b; }
@@ -139,6 +141,13 @@ struct DF64 {
     two_sum(a.s, p, s, e);
     a.s = s;
     a.e = __fadd_rn(a.e, __fadd_rn(e, pe));
+  }
+  // a = c * x (the first term of a dot product: no two-sum with zero)
+  __device__ __forceinline__ static void acc_first(Acc& a, V c, V x) {
+    a.s = __fmul_rn(c.hi, x.hi);
+    float pe = __fmaf_rn(c.hi, x.hi, -a.s);
+    pe = __fmaf_rn(c.hi, x.lo, pe);
+    a.e = __fmaf_rn(c.lo, x.hi, pe);
   }
   __device__ __forceinline__ static V acc_get(const Acc& a) {
     V r;

@@ -54,7 +54,7 @@ struct ConvLayout {
   static constexpr int U = 3 * N3;               // nodal velocity
   static constexpr int U1 = 3 * Q * N * N;       // x-interpolated; later: result
   static constexpr int U2 = 3 * Q * Q * N;       // xy-interpolated
-  static constexpr int P = 6 * Q * Q;            // one z-plane: u and the weighted u
+  static constexpr int P = 3 * Q * Q;            // one z-plane: u
   static constexpr int X = 9 * N * Q;            // x-tested plane
   static constexpr int Y = 6 * N * N;            // xy-tested plane
   static constexpr int PXY = P + X + Y;
@@ -103,20 +103,24 @@ __device__ __forceinline__ int node3(int N, int d, int a, int t1, int j1, int t2
   return c[0] + N * (c[1] + N * c[2]);
 }
 
+// Tables of the forward kernels.  The quadrature weights of each direction
+// sit in that direction's test table, the cell-size factor of the flux
+// direction d (h_x h_y h_z / h_d) in the x-test table of path d, so no
+// per-point weights are multiplied.
 template <class V, int N, int Q>
 struct ConvTabT {
-  V S[Q * N];
-  V D[Q * N];
-  V w[Q];
-  V jac[3];
-  V area[3];
+  V S[Q * N];       // S[q][j] = phi_j(x_q): interpolation to the Gauss points
+  V SW[Q * N];      // w_q phi_j(x_q): test with phi
+  V DW[Q * N];      // w_q phi_j'(x_q): test with phi'
+  V TX[3][Q * N];   // x test of flux direction d: jac_d DW (d = 0) or jac_d SW
+  V area[3];        // h_x h_y h_z / h_d: face area of faces normal to d
 };
 
-// Forward convective kernel for an arithmetic policy A (F64 or DF64): loads
-// and stores are double; all arithmetic is A's.  Every phase is split into
-// small independent work items (one output or one short line of outputs)
-// spread over the cell's threads; the 1D tables are copied to shared memory
-// because the items index them by thread.
+// Forward convective cell kernel for an arithmetic policy A (F64 or DF64):
+// loads and stores are double; all arithmetic is A's.  Every phase is split
+// into small independent work items (one output or one short line of
+// outputs) spread over the cell's threads; the 1D tables are copied to
+// shared memory because the items index them by thread.
 template <class A, int N, int Q>
 __global__ void __launch_bounds__(conv_fwd_cells_per_block<N>() * conv_threads<N>())
     conv_kernel(const double* __restrict__ u3, const double* __restrict__ rface, double* __restrict__ dst3,
@@ -126,7 +130,7 @@ __global__ void __launch_bounds__(conv_fwd_cells_per_block<N>() * conv_threads<N
   typedef ConvLayout<N, Q> LY;
   static_assert(sizeof(V) == sizeof(double), "8-byte values");
   constexpr int NT = conv_threads<N>(), N3 = N * N * N, EPB = conv_fwd_cells_per_block<N>();
-  constexpr int QQ = Q * Q, NN = N * N;
+  constexpr int QQ = Q * Q, NN = N * N, QN = Q * N;
   V* sm = reinterpret_cast<V*>(dyn_smem());
   const int slot = threadIdx.x / NT;
   const int t = threadIdx.x - slot * NT;
@@ -134,11 +138,17 @@ __global__ void __launch_bounds__(conv_fwd_cells_per_block<N>() * conv_threads<N
   const long long rem = m.E - c0;
   const int nvalid = rem < EPB ? (int)rem : EPB;
   const bool active = slot < nvalid;
-  V* sS = sm + EPB * LY::PER;
-  V* sD = sS + Q * N;
-  for (int i = threadIdx.x; i < Q * N; i += blockDim.x) {
+  V* sS = sm + EPB * LY::PER;   // tables: S, SW, DW, TX[0..2]
+  V* sSW = sS + QN;
+  V* sDW = sSW + QN;
+  V* sTX = sDW + QN;
+  for (int i = threadIdx.x; i < QN; i += blockDim.x) {
     sS[i] = tb.S[i];
-    sD[i] = tb.D[i];
+    sSW[i] = tb.SW[i];
+    sDW[i] = tb.DW[i];
+    sTX[i] = tb.TX[0][i];
+    sTX[QN + i] = tb.TX[1][i];
+    sTX[2 * QN + i] = tb.TX[2][i];
   }
   V* sU = sm + slot * LY::PER;   // nodal u, dead after the x interpolation
   V* sP = sU;                    // plane work reuses it
@@ -164,9 +174,9 @@ __global__ void __launch_bounds__(conv_fwd_cells_per_block<N>() * conv_threads<N
       const int c = r / NN, l = r - c * NN;
       const V* x = sU + c * N3 + l * N;
       Acc a;
-      A::acc_zero(a);
+      A::acc_first(a, sS[q * N], x[0]);
 #pragma unroll
-      for (int j = 0; j < N; ++j) A::acc_fma(a, sS[q * N + j], x[j]);
+      for (int j = 1; j < N; ++j) A::acc_fma(a, sS[q * N + j], x[j]);
       sU1[c * Q * NN + l * Q + q] = A::acc_get(a);
     }
   group_sync<NT>();
@@ -178,46 +188,42 @@ __global__ void __launch_bounds__(conv_fwd_cells_per_block<N>() * conv_threads<N
       const int qx = l % Q, z = l / Q;
       const V* x = sU1 + c * Q * NN + qx + Q * N * z;
       Acc a;
-      A::acc_zero(a);
+      A::acc_first(a, sS[qy * N], x[0]);
 #pragma unroll
-      for (int j = 0; j < N; ++j) A::acc_fma(a, sS[qy * N + j], x[Q * j]);
+      for (int j = 1; j < N; ++j) A::acc_fma(a, sS[qy * N + j], x[Q * j]);
       sU2[c * QQ * N + qx + Q * qy + QQ * z] = A::acc_get(a);
     }
   group_sync<NT>();
-  if (active)
-    for (int i = t; i < 3 * N3; i += NT) sOut[i] = A::zero();
 
   for (int qz = 0; qz < Q; ++qz) {
-    // P1: u and the weighted u_d w_qx w_qy w_qz h_x h_y h_z / h_d on the plane
+    // P1: u on the plane; item (c, point)
     if (active)
       for (int it = t; it < 3 * QQ; it += NT) {
-        const int c = it / QQ, l = it - c * QQ;
-        const V* src = sU2 + c * QQ * N + l;
+        const V* src = sU2 + (it / QQ) * QQ * N + (it % QQ);
         Acc a;
-        A::acc_zero(a);
+        A::acc_first(a, sS[qz * N], src[0]);
 #pragma unroll
-        for (int z = 0; z < N; ++z) A::acc_fma(a, sS[qz * N + z], src[QQ * z]);
-        const V u = A::acc_get(a);
-        const int qx = l % Q, qy = l / Q;
-        const V w3 = A::mul(A::mul(tb.w[qx], tb.w[qy]), tb.w[qz]);
-        sP[it] = u;
-        sP[3 * QQ + it] = A::mul(A::mul(w3, tb.jac[c]), u);
+        for (int z = 1; z < N; ++z) A::acc_fma(a, sS[qz * N + z], src[QQ * z]);
+        sP[it] = A::acc_get(a);
       }
     group_sync<NT>();
-    // P2: F_cd = u_c (weighted u_d) on x-lines, tested with D_x^T (d = x) or
-    // S_x^T; item (c, d, qy)
+    // P2: F_cd = u_c u_d on x-lines, x test of path d; item (c, d, qy)
     if (active)
       for (int it = t; it < 9 * Q; it += NT) {
         const int cd = it / Q, qy = it - cd * Q;
         const int c = cd / 3, d = cd - 3 * c;
-        const V* T = d == 0 ? sD : sS;
+        const V* T = sTX + d * QN;
+        const V* uc = sP + c * QQ + Q * qy;
+        const V* ud = sP + d * QQ + Q * qy;
         Acc a[N];
+        {
+          const V f = A::mul(uc[0], ud[0]);
 #pragma unroll
-        for (int x = 0; x < N; ++x) A::acc_zero(a[x]);
+          for (int x = 0; x < N; ++x) A::acc_first(a[x], T[x], f);
+        }
 #pragma unroll 1
-        for (int qx = 0; qx < Q; ++qx) {
-          const int pt = qx + Q * qy;
-          const V f = A::mul(sP[c * QQ + pt], sP[(3 + d) * QQ + pt]);
+        for (int qx = 1; qx < Q; ++qx) {
+          const V f = A::mul(uc[qx], ud[qx]);
 #pragma unroll
           for (int x = 0; x < N; ++x) A::acc_fma(a[x], T[qx * N + x], f);
         }
@@ -225,39 +231,46 @@ __global__ void __launch_bounds__(conv_fwd_cells_per_block<N>() * conv_threads<N
         for (int x = 0; x < N; ++x) sX[cd * N * Q + x + N * qy] = A::acc_get(a[x]);
       }
     group_sync<NT>();
-    // P3: Y1 = S_y^T X1 + D_y^T X2, Y3 = S_y^T X3; item (c, x, y)
+    // P3: Y1 = SW_y^T X(c,0) + DW_y^T X(c,1), Y3 = SW_y^T X(c,2); item (c, x, y)
     if (active)
       for (int it = t; it < 3 * NN; it += NT) {
         const int c = it / NN, r = it - c * NN;
         const int x = r % N, y = r / N;
+        const V* X0 = sX + (c * 3 + 0) * N * Q + x;
+        const V* X1 = X0 + N * Q;
+        const V* X2 = X1 + N * Q;
         Acc y1, y3;
-        A::acc_zero(y1);
-        A::acc_zero(y3);
+        A::acc_first(y1, sDW[y], X1[0]);
+        A::acc_fma(y1, sSW[y], X0[0]);
+        A::acc_first(y3, sSW[y], X2[0]);
 #pragma unroll 1
-        for (int qy = 0; qy < Q; ++qy) {
-          const int o = x + N * qy;
-          A::acc_fma(y1, sD[qy * N + y], sX[(c * 3 + 1) * N * Q + o]);
-          A::acc_fma(y1, sS[qy * N + y], sX[(c * 3 + 0) * N * Q + o]);
-          A::acc_fma(y3, sS[qy * N + y], sX[(c * 3 + 2) * N * Q + o]);
+        for (int qy = 1; qy < Q; ++qy) {
+          const int o = N * qy;
+          A::acc_fma(y1, sDW[qy * N + y], X1[o]);
+          A::acc_fma(y1, sSW[qy * N + y], X0[o]);
+          A::acc_fma(y3, sSW[qy * N + y], X2[o]);
         }
         sY[(c * 2 + 0) * NN + r] = A::acc_get(y1);
         sY[(c * 2 + 1) * NN + r] = A::acc_get(y3);
       }
     group_sync<NT>();
-    // P4: out -= S_z(qz) Y1 + D_z(qz) Y3; item (c, x, y, z)
+    // P4: out -= SW_z(qz) Y1 + DW_z(qz) Y3; item (c, x, y, z)
     if (active)
       for (int it = t; it < 3 * N3; it += NT) {
         const int c = it / N3, r = it - c * N3;
         const int xy = r % NN, z = r / NN;
         Acc a;
-        A::acc_set(a, sOut[it]);
-        A::acc_fma(a, A::neg(sD[qz * N + z]), sY[(c * 2 + 1) * NN + xy]);
-        A::acc_fma(a, A::neg(sS[qz * N + z]), sY[(c * 2 + 0) * NN + xy]);
+        if (qz == 0)
+          A::acc_first(a, A::neg(sDW[z]), sY[(c * 2 + 1) * NN + xy]);
+        else {
+          A::acc_set(a, sOut[it]);
+          A::acc_fma(a, A::neg(sDW[qz * N + z]), sY[(c * 2 + 1) * NN + xy]);
+        }
+        A::acc_fma(a, A::neg(sSW[qz * N + z]), sY[(c * 2 + 0) * NN + xy]);
         sOut[it] = A::acc_get(a);
       }
   }
   group_sync<NT>();
-
   // face integrals from the face kernel: +R on the layer N-1 (this cell is
   // the '-' side of its face), -R of the '-' neighbour on the layer 0
   if (active) {
@@ -305,7 +318,11 @@ __global__ void __launch_bounds__(faces_per_block<N>() * face_threads<N>())
   const int nvalid = rem < FPB ? (int)rem : FPB;
   const bool active = slot < nvalid;
   V* sS = sm + FPB * LY::PER;
-  for (int i = threadIdx.x; i < Q * N; i += blockDim.x) sS[i] = tb.S[i];
+  V* sSW = sS + Q * N;
+  for (int i = threadIdx.x; i < Q * N; i += blockDim.x) {
+    sS[i] = tb.S[i];
+    sSW[i] = tb.SW[i];
+  }
   __syncthreads();
   V* T0 = sm + slot * LY::PER;   // [s][c][j1 + N j2]   s = 0: '-', 1: '+'
   V* G1 = T0 + LY::T0;           // [s][c][q1 + Q j2]
@@ -336,9 +353,9 @@ __global__ void __launch_bounds__(faces_per_block<N>() * face_threads<N>())
       const int sc = r / N, j2 = r - sc * N;
       const V* v = T0 + sc * NN + N * j2;
       Acc a;
-      A::acc_zero(a);
+      A::acc_first(a, sS[q1 * N], v[0]);
 #pragma unroll
-      for (int j = 0; j < N; ++j) A::acc_fma(a, sS[q1 * N + j], v[j]);
+      for (int j = 1; j < N; ++j) A::acc_fma(a, sS[q1 * N + j], v[j]);
       G1[sc * Q * N + q1 + Q * j2] = A::acc_get(a);
     }
   group_sync<FT>();
@@ -349,16 +366,15 @@ __global__ void __launch_bounds__(faces_per_block<N>() * face_threads<N>())
       const int sc = r / Q, q1 = r - sc * Q;
       const V* v = G1 + sc * Q * N + q1;
       Acc a;
-      A::acc_zero(a);
+      A::acc_first(a, sS[q2 * N], v[0]);
 #pragma unroll
-      for (int j = 0; j < N; ++j) A::acc_fma(a, sS[q2 * N + j], v[Q * j]);
+      for (int j = 1; j < N; ++j) A::acc_fma(a, sS[q2 * N + j], v[Q * j]);
       G2[sc * QQ + q1 + Q * q2] = A::acc_get(a);
     }
   group_sync<FT>();
-  // F3: LLF flux at the face points, times the quadrature weight
+  // F3: LLF flux at the face points (weights are in the test tables)
   if (active)
     for (int it = t; it < QQ; it += FT) {
-      const int q1 = it % Q, q2 = it / Q;
       V um[3], up[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -369,43 +385,44 @@ __global__ void __launch_bounds__(faces_per_block<N>() * face_threads<N>())
       const V unp = d == 0 ? up[0] : (d == 1 ? up[1] : up[2]);
       const V am = A::absval(unm), ap = A::absval(unp);
       const V lam = A::greater(am, ap) ? am : ap;
-      const V wgt = A::mul(A::mul(tb.w[q1], tb.w[q2]), tb.area[d]);
       // 0.5 (u-_c un- + u+_c un+), the halving is exact
       const V hm = A::half(unm), hp = A::half(unp);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         Acc f;
-        A::acc_zero(f);
-        A::acc_fma(f, um[c], hm);
+        A::acc_first(f, um[c], hm);
         A::acc_fma(f, up[c], hp);
         A::acc_fma(f, lam, A::sub(um[c], up[c]));
-        H[c * QQ + it] = A::mul(wgt, A::acc_get(f));
+        H[c * QQ + it] = A::acc_get(f);
       }
     }
   group_sync<FT>();
-  // F4: test along t2; item (c, j2, q1)
+  // F4: test along t2 (weights w_q2); item (c, j2, q1)
   if (active)
     for (int it = t; it < 3 * Q * N; it += FT) {
       const int q1 = it % Q, r = it / Q;
       const int c = r / N, j2 = r - c * N;
+      const V* h = H + c * QQ + q1;
       Acc a;
-      A::acc_zero(a);
+      A::acc_first(a, sSW[j2], h[0]);
 #pragma unroll 1
-      for (int q2 = 0; q2 < Q; ++q2) A::acc_fma(a, sS[q2 * N + j2], H[c * QQ + q1 + Q * q2]);
+      for (int q2 = 1; q2 < Q; ++q2) A::acc_fma(a, sSW[q2 * N + j2], h[Q * q2]);
       K1[c * Q * N + q1 + Q * j2] = A::acc_get(a);
     }
   group_sync<FT>();
-  // F5: test along t1, store; item (c, j2, j1)
+  // F5: test along t1 (weights w_q1), times the face area, store; item (c, j2, j1)
   if (active) {
     double* out = rface + ((size_t)d * m.E + el) * 3 * NN;
+    const V area = tb.area[d];
     for (int it = t; it < 3 * NN; it += FT) {
       const int c = it / NN, r = it - c * NN;
       const int j1 = r % N, j2 = r / N;
+      const V* k = K1 + c * Q * N + Q * j2;
       Acc a;
-      A::acc_zero(a);
+      A::acc_first(a, sSW[j1], k[0]);
 #pragma unroll 1
-      for (int q1 = 0; q1 < Q; ++q1) A::acc_fma(a, sS[q1 * N + j1], K1[c * Q * N + q1 + Q * j2]);
-      out[it] = A::store(A::acc_get(a));
+      for (int q1 = 1; q1 < Q; ++q1) A::acc_fma(a, sSW[q1 * N + j1], k[q1]);
+      out[it] = A::store(A::mul(area, A::acc_get(a)));
     }
   }
 }
@@ -413,16 +430,21 @@ __global__ void __launch_bounds__(faces_per_block<N>() * face_threads<N>())
 template <class A, int N, int Q>
 ConvTabT<typename A::V, N, Q> conv_tables(const ConvHost& h) {
   ConvTabT<typename A::V, N, Q> tb;
-  for (int i = 0; i < Q * N; ++i) {
-    tb.S[i] = A::make(h.S[i]);
-    tb.D[i] = A::make(h.D[i]);
-  }
-  for (int q = 0; q < Q; ++q) tb.w[q] = A::make(h.w[q]);
+  double jac[3];
   for (int d = 0; d < 3; ++d) {
-    const double j = h.h[0] * h.h[1] * h.h[2] / h.h[d];
-    tb.jac[d] = A::make(j);
-    tb.area[d] = A::make(j);
+    jac[d] = h.h[0] * h.h[1] * h.h[2] / h.h[d];
+    tb.area[d] = A::make(jac[d]);
   }
+  for (int q = 0; q < Q; ++q)
+    for (int j = 0; j < N; ++j) {
+      const int i = q * N + j;
+      tb.S[i] = A::make(h.S[i]);
+      tb.SW[i] = A::make(h.w[q] * h.S[i]);
+      tb.DW[i] = A::make(h.w[q] * h.D[i]);
+      tb.TX[0][i] = A::make(jac[0] * h.w[q] * h.D[i]);
+      tb.TX[1][i] = A::make(jac[1] * h.w[q] * h.S[i]);
+      tb.TX[2][i] = A::make(jac[2] * h.w[q] * h.S[i]);
+    }
   return tb;
 }
 
@@ -433,8 +455,8 @@ int launch_conv(int part, const MeshDims& m, const double* u3, double* rface, do
                 cudaStream_t s) {
   const ConvTabT<typename A::V, N, Q> tb = conv_tables<A, N, Q>(h);
   constexpr int EPB = conv_fwd_cells_per_block<N>(), FPB = faces_per_block<N>();
-  const size_t smem = ((size_t)EPB * ConvLayout<N, Q>::PER + 2 * Q * N) * sizeof(double);
-  const size_t fsmem = ((size_t)FPB * FaceLayout<N, Q>::PER + Q * N) * sizeof(double);
+  const size_t smem = ((size_t)EPB * ConvLayout<N, Q>::PER + 6 * Q * N) * sizeof(double);
+  const size_t fsmem = ((size_t)FPB * FaceLayout<N, Q>::PER + 2 * Q * N) * sizeof(double);
   if (smem > 232448 || fsmem > 232448) return 7;
   if (cudaFuncSetAttribute(conv_kernel<A, N, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
           cudaSuccess ||

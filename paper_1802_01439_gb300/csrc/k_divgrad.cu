@@ -55,10 +55,13 @@ __device__ __forceinline__ void rect_line(const typename P::V* in, const typenam
     Acc y;
     if (ADD)
       P::acc_set(y, add[bo + i * so]);
-    else
-      P::acc_zero(y);
 #pragma unroll
-    for (int j = 0; j < NI; ++j) P::acc_fma(y, A[i * NI + j], x[j]);
+    for (int j = 0; j < NI; ++j) {
+      if (ADD || j > 0)
+        P::acc_fma(y, A[i * NI + j], x[j]);
+      else
+        P::acc_first(y, A[i * NI + j], x[j]);
+    }
     out[bo + i * so] = P::acc_get(y);
   }
 }
@@ -80,9 +83,9 @@ __device__ __forceinline__ void flux_line(const typename P::V* in, const double*
 #pragma unroll
   for (int i = 0; i < NO; ++i) {
     Acc y;
-    P::acc_zero(y);
+    P::acc_first(y, A[i * NI], x[0]);
 #pragma unroll
-    for (int j = 0; j < NI; ++j) P::acc_fma(y, A[i * NI + j], x[j]);
+    for (int j = 1; j < NI; ++j) P::acc_fma(y, A[i * NI + j], x[j]);
     if (i == NO - 1) P::acc_fma(y, cr, vr);
     if (i == 0) P::acc_fma(y, cl, vl);
     out[bo + i * so] = P::acc_get(y);

@@ -101,8 +101,7 @@ __device__ __forceinline__ void sipg_line(const typename A::V* X, typename A::V*
   }
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    A::acc_zero(y[i]);
-    A::acc_fma(y[i], tb.cr[D][i], r[0]);
+    A::acc_first(y[i], tb.cr[D][i], r[0]);
     A::acc_fma(y[i], tb.cl[D][i], lf[N - 1]);
 #pragma unroll
     for (int j = 0; j < N; ++j) A::acc_fma(y[i], tb.A0[D][i * N + j], x[j]);
@@ -130,8 +129,7 @@ __device__ __forceinline__ void sipg_line_pre(const typename A::V* X, typename A
   load_line<V, N>(X, base, stride, x);
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    A::acc_zero(y[i]);
-    A::acc_fma(y[i], tb.cr[D][i], r[0]);
+    A::acc_first(y[i], tb.cr[D][i], r[0]);
     A::acc_fma(y[i], tb.cl[D][i], lf[N - 1]);
 #pragma unroll
     for (int j = 0; j < N; ++j) A::acc_fma(y[i], tb.A0[D][i * N + j], x[j]);
@@ -181,10 +179,13 @@ __device__ __forceinline__ void mass_line(const typename A::V* in, const typenam
   for (int i = 0; i < N; ++i) {
     if (ADD)
       A::acc_set(y[i], add[base + i * stride]);
-    else
-      A::acc_zero(y[i]);
 #pragma unroll
-    for (int j = 0; j < N; ++j) A::acc_fma(y[i], M[i * N + j], x[j]);
+    for (int j = 0; j < N; ++j) {
+      if (ADD || j > 0)
+        A::acc_fma(y[i], M[i * N + j], x[j]);
+      else
+        A::acc_first(y[i], M[i * N + j], x[j]);
+    }
   }
 #pragma unroll
   for (int i = 0; i < N; ++i) out[base + i * stride] = A::acc_get(y[i]);

@@ -42,9 +42,9 @@ __device__ __forceinline__ void sweep_line_p(const typename A::V* in, typename A
   Acc y[N];
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    A::acc_zero(y[i]);
+    A::acc_first(y[i], M[i * N], x[0]);
 #pragma unroll
-    for (int j = 0; j < N; ++j) A::acc_fma(y[i], M[i * N + j], x[j]);
+    for (int j = 1; j < N; ++j) A::acc_fma(y[i], M[i * N + j], x[j]);
   }
 #pragma unroll
   for (int i = 0; i < N; ++i) out[base + i * stride] = A::acc_get(y[i]);
