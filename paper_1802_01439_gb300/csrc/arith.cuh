@@ -35,6 +35,7 @@ struct F32 {
   __device__ __forceinline__ static void acc_fma(Acc& a, V c, V x) { a = fmaf(c, x, a); }
   __device__ __forceinline__ static void acc_first(Acc& a, V c, V x) { a = c * x; }
   __device__ __forceinline__ static V acc_get(const Acc& a) { return a; }
+  __device__ __forceinline__ static V acc_get_norm(const Acc& a) { return a; }
   __device__ __forceinline__ static G store(V x) { return x; }
 };
 
@@ -53,6 +54,7 @@ struct F64 {
   __device__ __forceinline__ static void acc_fma(Acc& a, V c, V x) { a = fma(c, x, a); }
   __device__ __forceinline__ static void acc_first(Acc& a, V c, V x) { a = c * x; }
   __device__ __forceinline__ static V acc_get(const Acc& a) { return a; }
+  __device__ __forceinline__ static V acc_get_norm(const Acc& a) { return a; }
   __device__ __forceinline__ static V add(V a, V b) { return a + b; }
   __device__ __forceinline__ static V sub(V a, V b) { return a - b; }
   __device__ __forceinline__ static V mul(V a, V b) { return a * b; }
@@ -149,7 +151,17 @@ struct DF64 {
     pe = __fmaf_rn(c.hi, x.lo, pe);
     a.e = __fmaf_rn(c.lo, x.hi, pe);
   }
+  // The value of an accumulator as hi + lo without renormalisation: lo holds
+  // the collected rounding errors, small against the terms but not
+  // necessarily below half an ulp of hi.  Products and sums take such values
+  // as they are; acc_get_norm renormalises where a value is compared.
   __device__ __forceinline__ static V acc_get(const Acc& a) {
+    V r;
+    r.hi = a.s;
+    r.lo = a.e;
+    return r;
+  }
+  __device__ __forceinline__ static V acc_get_norm(const Acc& a) {
     V r;
     two_sum(a.s, a.e, r.hi, r.lo);
     return r;

@@ -156,7 +156,6 @@ __global__ void __launch_bounds__(conv_fwd_cells_per_block<N>() * conv_threads<N
   V* sY = sX + LY::X;
   V* sU1 = sU + LY::UP;
   V* sU2 = sU1 + LY::U1;
-  V* sOut = sU1;   // reused after the interpolation
 
   unsigned el = 0;
   CellXYZ cx{};
@@ -195,100 +194,146 @@ __global__ void __launch_bounds__(conv_fwd_cells_per_block<N>() * conv_threads<N
     }
   group_sync<NT>();
 
+  // The plane loop: every lane keeps the same work items in all planes, so
+  // their offsets are computed once; the lane's outputs (items of P4) stay
+  // in registers until the end.
+  constexpr int R1 = (3 * QQ + NT - 1) / NT, R2 = (9 * Q + NT - 1) / NT, R3 = (3 * NN + NT - 1) / NT,
+                R4 = (3 * N3 + NT - 1) / NT;
+  int o1[R1];                                  // P1: offset of the z column in sU2
+  int o2t[R2], o2c[R2], o2d[R2], o2x[R2];      // P2: table, u_c, u_d, output offsets
+  int o3x[R3], o3y[R3];                        // P3: offset into sX, y
+  int o4y[R4], o4z[R4];                        // P4: offset into sY, z
+#pragma unroll
+  for (int r = 0; r < R1; ++r) {
+    const int it = t + NT * r;
+    o1[r] = (it / QQ) * QQ * N + (it % QQ);
+  }
+#pragma unroll
+  for (int r = 0; r < R2; ++r) {
+    const int it = t + NT * r;
+    const int cd = it / Q, qy = it - cd * Q;
+    const int c = cd / 3, d = cd - 3 * c;
+    o2t[r] = d * QN;
+    o2c[r] = c * QQ + Q * qy;
+    o2d[r] = d * QQ + Q * qy;
+    o2x[r] = cd * N * Q + N * qy;
+  }
+#pragma unroll
+  for (int r = 0; r < R3; ++r) {
+    const int it = t + NT * r;
+    const int c = it / NN, rr = it - c * NN;
+    o3x[r] = 3 * c * N * Q + rr % N;
+    o3y[r] = rr / N;
+  }
+#pragma unroll
+  for (int r = 0; r < R4; ++r) {
+    const int it = t + NT * r;
+    const int c = it / N3, rr = it - c * N3;
+    o4y[r] = 2 * c * NN + rr % NN;
+    o4z[r] = rr / NN;
+  }
+  Acc out[R4];
+
+#pragma unroll 1
   for (int qz = 0; qz < Q; ++qz) {
     // P1: u on the plane; item (c, point)
     if (active)
-      for (int it = t; it < 3 * QQ; it += NT) {
-        const V* src = sU2 + (it / QQ) * QQ * N + (it % QQ);
+#pragma unroll
+      for (int r = 0; r < R1; ++r) {
+        if ((3 * QQ) % NT != 0 && t + NT * r >= 3 * QQ) break;
+        const V* src = sU2 + o1[r];
         Acc a;
         A::acc_first(a, sS[qz * N], src[0]);
 #pragma unroll
         for (int z = 1; z < N; ++z) A::acc_fma(a, sS[qz * N + z], src[QQ * z]);
-        sP[it] = A::acc_get(a);
+        sP[t + NT * r] = A::acc_get(a);
       }
     group_sync<NT>();
     // P2: F_cd = u_c u_d on x-lines, x test of path d; item (c, d, qy)
     if (active)
-      for (int it = t; it < 9 * Q; it += NT) {
-        const int cd = it / Q, qy = it - cd * Q;
-        const int c = cd / 3, d = cd - 3 * c;
-        const V* T = sTX + d * QN;
-        const V* uc = sP + c * QQ + Q * qy;
-        const V* ud = sP + d * QQ + Q * qy;
+#pragma unroll
+      for (int r = 0; r < R2; ++r) {
+        if ((9 * Q) % NT != 0 && t + NT * r >= 9 * Q) break;
+        const V* T = sTX + o2t[r];
+        const V* uc = sP + o2c[r];
+        const V* ud = sP + o2d[r];
         Acc a[N];
         {
           const V f = A::mul(uc[0], ud[0]);
 #pragma unroll
           for (int x = 0; x < N; ++x) A::acc_first(a[x], T[x], f);
         }
-#pragma unroll 1
+#pragma unroll
         for (int qx = 1; qx < Q; ++qx) {
           const V f = A::mul(uc[qx], ud[qx]);
 #pragma unroll
           for (int x = 0; x < N; ++x) A::acc_fma(a[x], T[qx * N + x], f);
         }
 #pragma unroll
-        for (int x = 0; x < N; ++x) sX[cd * N * Q + x + N * qy] = A::acc_get(a[x]);
+        for (int x = 0; x < N; ++x) sX[o2x[r] + x] = A::acc_get(a[x]);
       }
     group_sync<NT>();
     // P3: Y1 = SW_y^T X(c,0) + DW_y^T X(c,1), Y3 = SW_y^T X(c,2); item (c, x, y)
     if (active)
-      for (int it = t; it < 3 * NN; it += NT) {
-        const int c = it / NN, r = it - c * NN;
-        const int x = r % N, y = r / N;
-        const V* X0 = sX + (c * 3 + 0) * N * Q + x;
+#pragma unroll
+      for (int r = 0; r < R3; ++r) {
+        if ((3 * NN) % NT != 0 && t + NT * r >= 3 * NN) break;
+        const V* X0 = sX + o3x[r];
         const V* X1 = X0 + N * Q;
         const V* X2 = X1 + N * Q;
+        const int y = o3y[r];
         Acc y1, y3;
         A::acc_first(y1, sDW[y], X1[0]);
         A::acc_fma(y1, sSW[y], X0[0]);
         A::acc_first(y3, sSW[y], X2[0]);
-#pragma unroll 1
+#pragma unroll
         for (int qy = 1; qy < Q; ++qy) {
           const int o = N * qy;
           A::acc_fma(y1, sDW[qy * N + y], X1[o]);
           A::acc_fma(y1, sSW[qy * N + y], X0[o]);
           A::acc_fma(y3, sSW[qy * N + y], X2[o]);
         }
-        sY[(c * 2 + 0) * NN + r] = A::acc_get(y1);
-        sY[(c * 2 + 1) * NN + r] = A::acc_get(y3);
+        const int it = t + NT * r, c = it / NN;
+        sY[(2 * c) * NN + (it - c * NN)] = A::acc_get(y1);
+        sY[(2 * c + 1) * NN + (it - c * NN)] = A::acc_get(y3);
       }
     group_sync<NT>();
-    // P4: out -= SW_z(qz) Y1 + DW_z(qz) Y3; item (c, x, y, z)
+    // P4: out -= SW_z(qz) Y1 + DW_z(qz) Y3; item (c, x, y, z), in registers
     if (active)
-      for (int it = t; it < 3 * N3; it += NT) {
-        const int c = it / N3, r = it - c * N3;
-        const int xy = r % NN, z = r / NN;
-        Acc a;
+#pragma unroll
+      for (int r = 0; r < R4; ++r) {
+        if ((3 * N3) % NT != 0 && t + NT * r >= 3 * N3) break;
+        const V* Y = sY + o4y[r];
+        const int z = o4z[r];
         if (qz == 0)
-          A::acc_first(a, A::neg(sDW[z]), sY[(c * 2 + 1) * NN + xy]);
-        else {
-          A::acc_set(a, sOut[it]);
-          A::acc_fma(a, A::neg(sDW[qz * N + z]), sY[(c * 2 + 1) * NN + xy]);
-        }
-        A::acc_fma(a, A::neg(sSW[qz * N + z]), sY[(c * 2 + 0) * NN + xy]);
-        sOut[it] = A::acc_get(a);
+          A::acc_first(out[r], A::neg(sDW[z]), Y[NN]);
+        else
+          A::acc_fma(out[r], A::neg(sDW[qz * N + z]), Y[NN]);
+        A::acc_fma(out[r], A::neg(sSW[qz * N + z]), Y[0]);
       }
+    group_sync<NT>();
   }
-  group_sync<NT>();
   // face integrals from the face kernel: +R on the layer N-1 (this cell is
   // the '-' side of its face), -R of the '-' neighbour on the layer 0
   if (active) {
     const unsigned nbm0 = neighbor32<0>(cx, -1, m), nbm1 = neighbor32<1>(cx, -1, m), nbm2 = neighbor32<2>(cx, -1, m);
     const size_t E = (size_t)m.E, FS = 3 * NN;
-    for (int it = t; it < 3 * N3; it += NT) {
-      const int c = it / N3, r = it - c * N3;
-      const int x = r % N, yz = r / N;
+#pragma unroll
+    for (int r = 0; r < R4; ++r) {
+      const int it = t + NT * r;
+      if ((3 * N3) % NT != 0 && it >= 3 * N3) break;
+      const int c = it / N3, rr = it - c * N3;
+      const int x = rr % N, yz = rr / N;
       const int y = yz % N, z = yz / N;
       const double* rc = rface + c * NN;
-      V v = sOut[it];
+      V v = A::acc_get(out[r]);
       if (x == N - 1) v = A::add(v, A::load(rc + el * FS + y + N * z));
       if (x == 0) v = A::sub(v, A::load(rc + nbm0 * FS + y + N * z));
       if (y == N - 1) v = A::add(v, A::load(rc + (E + el) * FS + x + N * z));
       if (y == 0) v = A::sub(v, A::load(rc + (E + nbm1) * FS + x + N * z));
       if (z == N - 1) v = A::add(v, A::load(rc + (2 * E + el) * FS + x + N * y));
       if (z == 0) v = A::sub(v, A::load(rc + (2 * E + nbm2) * FS + x + N * y));
-      dst3[((size_t)c * m.E + el) * N3 + r] = A::store(v);
+      dst3[((size_t)c * m.E + el) * N3 + rr] = A::store(v);
     }
   }
 }
@@ -369,7 +414,7 @@ __global__ void __launch_bounds__(faces_per_block<N>() * face_threads<N>())
       A::acc_first(a, sS[q2 * N], v[0]);
 #pragma unroll
       for (int j = 1; j < N; ++j) A::acc_fma(a, sS[q2 * N + j], v[Q * j]);
-      G2[sc * QQ + q1 + Q * q2] = A::acc_get(a);
+      G2[sc * QQ + q1 + Q * q2] = A::acc_get_norm(a);   // compared in F3
     }
   group_sync<FT>();
   // F3: LLF flux at the face points (weights are in the test tables)
