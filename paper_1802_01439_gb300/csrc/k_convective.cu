@@ -62,14 +62,19 @@ struct ConvLayout {
   static constexpr int PER = UP + U1 + U2;
 };
 
-// Threads of one face of the face kernel: one warp up to N = 6, four warps
-// (one face per block) above.
+// Face kernel groups: one warp for FPG faces up to N = 6 (two faces up to
+// N = 4, where one face has too few items per phase for 32 lanes), four
+// warps for one face above; four groups per block up to N = 6.
 template <int N>
 constexpr int face_threads() {
   return N <= 6 ? 32 : 128;
 }
 template <int N>
-constexpr int faces_per_block() {
+constexpr int faces_per_group() {
+  return N <= 4 ? 2 : 1;
+}
+template <int N>
+constexpr int face_groups_per_block() {
   return face_threads<N>() == 32 ? 4 : 1;
 }
 
@@ -345,131 +350,130 @@ __global__ void __launch_bounds__(conv_fwd_cells_per_block<N>() * conv_threads<N
 // n = +e_d, is the face integral against the '-' cell's face-layer basis;
 // the '+' cell's is -R (same trace basis, opposite normal).  Written to
 // rface[d][e][c][j1 + N j2] (j1, j2: the two tangential directions in
-// increasing order).
+// increasing order).  A group of FT threads treats FPG faces at once, so
+// that every phase has enough items for its lanes; each group keeps its own
+// copy of the two tables and synchronises only itself.
 template <class A, int N, int Q>
-__global__ void __launch_bounds__(faces_per_block<N>() * face_threads<N>())
+__global__ void __launch_bounds__(face_groups_per_block<N>() * face_threads<N>())
     conv_face_kernel(const double* __restrict__ u3, double* __restrict__ rface,
                      const __grid_constant__ ConvTabT<typename A::V, N, Q> tb, const MeshDims m) {
   typedef typename A::V V;
   typedef typename A::Acc Acc;
   typedef FaceLayout<N, Q> LY;
-  constexpr int FT = face_threads<N>(), FPB = faces_per_block<N>(), N3 = N * N * N, NN = N * N, QQ = Q * Q;
+  constexpr int FT = face_threads<N>(), FPG = faces_per_group<N>(), GPB = face_groups_per_block<N>();
+  constexpr int N3 = N * N * N, NN = N * N, QQ = Q * Q, QN = Q * N;
   V* sm = reinterpret_cast<V*>(dyn_smem());
-  const int slot = threadIdx.x / FT;
-  const int t = threadIdx.x - slot * FT;
+  const int g = threadIdx.x / FT;
+  const int t = threadIdx.x - g * FT;
   const int d = blockIdx.y;
-  const long long c0 = (long long)blockIdx.x * FPB;
-  const long long rem = m.E - c0;
-  const int nvalid = rem < FPB ? (int)rem : FPB;
-  const bool active = slot < nvalid;
-  V* sS = sm + FPB * LY::PER;
-  V* sSW = sS + Q * N;
-  for (int i = threadIdx.x; i < Q * N; i += blockDim.x) {
+  const long long f0 = ((long long)blockIdx.x * GPB + g) * FPG;
+  V* base = sm + g * (FPG * LY::PER + 2 * QN);
+  V* sS = base + FPG * LY::PER;
+  V* sSW = sS + QN;
+  for (int i = t; i < QN; i += FT) {
     sS[i] = tb.S[i];
     sSW[i] = tb.SW[i];
   }
-  __syncthreads();
-  V* T0 = sm + slot * LY::PER;   // [s][c][j1 + N j2]   s = 0: '-', 1: '+'
-  V* G1 = T0 + LY::T0;           // [s][c][q1 + Q j2]
-  V* G2 = G1 + LY::G1;           // [s][c][q1 + Q q2]
-  V* H = G1;                     // [c][q1 + Q q2]
-  V* K1 = T0;                    // [c][q1 + Q j2]
   const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
-  unsigned el = 0, nb = 0;
-  if (active) {
-    const CellXYZ cx = cell_xyz((unsigned)(c0 + slot), m);
-    el = cx.el;
-    nb = d == 0 ? neighbor32<0>(cx, 1, m) : (d == 1 ? neighbor32<1>(cx, 1, m) : neighbor32<2>(cx, 1, m));
-  }
-  // F0: the face layers of both cells
-  if (active)
-    for (int it = t; it < 6 * NN; it += FT) {
-      const int sc = it / NN, r = it - sc * NN;
-      const int sd = sc / 3, c = sc - 3 * sd;
-      const int j1 = r % N, j2 = r / N;
-      const unsigned cell = sd == 0 ? el : nb;
-      T0[it] = A::load(u3 + ((size_t)c * m.E + cell) * N3 + node3(N, d, sd == 0 ? N - 1 : 0, t1, j1, t2, j2));
+  unsigned el[FPG], nb[FPG];
+  int nact = 0;
+#pragma unroll
+  for (int f = 0; f < FPG; ++f) {
+    el[f] = nb[f] = 0;
+    if (f0 + f < m.E) {
+      const CellXYZ cx = cell_xyz((unsigned)(f0 + f), m);
+      el[f] = cx.el;
+      nb[f] = d == 0 ? neighbor32<0>(cx, 1, m) : (d == 1 ? neighbor32<1>(cx, 1, m) : neighbor32<2>(cx, 1, m));
+      nact = f + 1;
     }
+  }
+  // per face f: T0 [s][c][j1 + N j2] (s = 0: '-', 1: '+'), later K1 [c][q1 + Q j2];
+  // G1 [s][c][q1 + Q j2], later H [c][q1 + Q q2]; G2 [s][c][q1 + Q q2]
+#define FACE_T0(f) (base + (f) * LY::PER)
+#define FACE_G1(f) (base + (f) * LY::PER + LY::T0)
+#define FACE_G2(f) (base + (f) * LY::PER + LY::T0 + LY::G1)
+  // F0: the face layers of both cells
+  for (int it = t; it < nact * 6 * NN; it += FT) {
+    const int f = it / (6 * NN), i = it - f * 6 * NN;
+    const int sc = i / NN, r = i - sc * NN;
+    const int sd = sc / 3, c = sc - 3 * sd;
+    const int j1 = r % N, j2 = r / N;
+    const unsigned cell = sd == 0 ? el[f] : nb[f];
+    FACE_T0(f)[i] = A::load(u3 + ((size_t)c * m.E + cell) * N3 + node3(N, d, sd == 0 ? N - 1 : 0, t1, j1, t2, j2));
+  }
   group_sync<FT>();
   // F1: interpolate along t1; item (sc, j2, q1)
-  if (active)
-    for (int it = t; it < 6 * N * Q; it += FT) {
-      const int q1 = it % Q, r = it / Q;
-      const int sc = r / N, j2 = r - sc * N;
-      const V* v = T0 + sc * NN + N * j2;
-      Acc a;
-      A::acc_first(a, sS[q1 * N], v[0]);
+  for (int it = t; it < nact * 6 * QN; it += FT) {
+    const int f = it / (6 * QN), i = it - f * 6 * QN;
+    const int q1 = i % Q, r = i / Q;
+    const int sc = r / N, j2 = r - sc * N;
+    const V* v = FACE_T0(f) + sc * NN + N * j2;
+    Acc a;
+    A::acc_first(a, sS[q1 * N], v[0]);
 #pragma unroll
-      for (int j = 1; j < N; ++j) A::acc_fma(a, sS[q1 * N + j], v[j]);
-      G1[sc * Q * N + q1 + Q * j2] = A::acc_get(a);
-    }
+    for (int j = 1; j < N; ++j) A::acc_fma(a, sS[q1 * N + j], v[j]);
+    FACE_G1(f)[sc * QN + q1 + Q * j2] = A::acc_get(a);
+  }
   group_sync<FT>();
   // F2: along t2; item (sc, q1, q2)
-  if (active)
-    for (int it = t; it < 6 * QQ; it += FT) {
-      const int q2 = it % Q, r = it / Q;
-      const int sc = r / Q, q1 = r - sc * Q;
-      const V* v = G1 + sc * Q * N + q1;
-      Acc a;
-      A::acc_first(a, sS[q2 * N], v[0]);
+  for (int it = t; it < nact * 6 * QQ; it += FT) {
+    const int f = it / (6 * QQ), i = it - f * 6 * QQ;
+    const int q2 = i % Q, r = i / Q;
+    const int sc = r / Q, q1 = r - sc * Q;
+    const V* v = FACE_G1(f) + sc * QN + q1;
+    Acc a;
+    A::acc_first(a, sS[q2 * N], v[0]);
 #pragma unroll
-      for (int j = 1; j < N; ++j) A::acc_fma(a, sS[q2 * N + j], v[Q * j]);
-      G2[sc * QQ + q1 + Q * q2] = A::acc_get_norm(a);   // compared in F3
-    }
+    for (int j = 1; j < N; ++j) A::acc_fma(a, sS[q2 * N + j], v[Q * j]);
+    FACE_G2(f)[sc * QQ + q1 + Q * q2] = A::acc_get_norm(a);   // compared in F3
+  }
   group_sync<FT>();
-  // F3: LLF flux at the face points (weights are in the test tables)
-  if (active)
-    for (int it = t; it < QQ; it += FT) {
-      V um[3], up[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        um[c] = G2[c * QQ + it];
-        up[c] = G2[(3 + c) * QQ + it];
-      }
-      const V unm = d == 0 ? um[0] : (d == 1 ? um[1] : um[2]);
-      const V unp = d == 0 ? up[0] : (d == 1 ? up[1] : up[2]);
-      const V am = A::absval(unm), ap = A::absval(unp);
-      const V lam = A::greater(am, ap) ? am : ap;
-      // 0.5 (u-_c un- + u+_c un+), the halving is exact
-      const V hm = A::half(unm), hp = A::half(unp);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        Acc f;
-        A::acc_first(f, um[c], hm);
-        A::acc_fma(f, up[c], hp);
-        A::acc_fma(f, lam, A::sub(um[c], up[c]));
-        H[c * QQ + it] = A::acc_get(f);
-      }
-    }
+  // F3: LLF flux at the face points (weights are in the test tables); item (c, point)
+  for (int it = t; it < nact * 3 * QQ; it += FT) {
+    const int f = it / (3 * QQ), i = it - f * 3 * QQ;
+    const int c = i / QQ, pt = i - c * QQ;
+    const V* g2 = FACE_G2(f) + pt;
+    const V umc = g2[c * QQ], upc = g2[(3 + c) * QQ];
+    const V unm = g2[d * QQ], unp = g2[(3 + d) * QQ];
+    const V am = A::absval(unm), ap = A::absval(unp);
+    const V lam = A::greater(am, ap) ? am : ap;
+    // 0.5 (u-_c un- + u+_c un+) + lambda (u-_c - u+_c), the halving is exact
+    Acc fl;
+    A::acc_first(fl, umc, A::half(unm));
+    A::acc_fma(fl, upc, A::half(unp));
+    A::acc_fma(fl, lam, A::sub(umc, upc));
+    FACE_G1(f)[i] = A::acc_get(fl);
+  }
   group_sync<FT>();
   // F4: test along t2 (weights w_q2); item (c, j2, q1)
-  if (active)
-    for (int it = t; it < 3 * Q * N; it += FT) {
-      const int q1 = it % Q, r = it / Q;
-      const int c = r / N, j2 = r - c * N;
-      const V* h = H + c * QQ + q1;
-      Acc a;
-      A::acc_first(a, sSW[j2], h[0]);
-#pragma unroll 1
-      for (int q2 = 1; q2 < Q; ++q2) A::acc_fma(a, sSW[q2 * N + j2], h[Q * q2]);
-      K1[c * Q * N + q1 + Q * j2] = A::acc_get(a);
-    }
+  for (int it = t; it < nact * 3 * QN; it += FT) {
+    const int f = it / (3 * QN), i = it - f * 3 * QN;
+    const int q1 = i % Q, r = i / Q;
+    const int c = r / N, j2 = r - c * N;
+    const V* h = FACE_G1(f) + c * QQ + q1;
+    Acc a;
+    A::acc_first(a, sSW[j2], h[0]);
+#pragma unroll
+    for (int q2 = 1; q2 < Q; ++q2) A::acc_fma(a, sSW[q2 * N + j2], h[Q * q2]);
+    FACE_T0(f)[c * QN + q1 + Q * j2] = A::acc_get(a);
+  }
   group_sync<FT>();
   // F5: test along t1 (weights w_q1), times the face area, store; item (c, j2, j1)
-  if (active) {
-    double* out = rface + ((size_t)d * m.E + el) * 3 * NN;
-    const V area = tb.area[d];
-    for (int it = t; it < 3 * NN; it += FT) {
-      const int c = it / NN, r = it - c * NN;
-      const int j1 = r % N, j2 = r / N;
-      const V* k = K1 + c * Q * N + Q * j2;
-      Acc a;
-      A::acc_first(a, sSW[j1], k[0]);
-#pragma unroll 1
-      for (int q1 = 1; q1 < Q; ++q1) A::acc_fma(a, sSW[q1 * N + j1], k[q1]);
-      out[it] = A::store(A::mul(area, A::acc_get(a)));
-    }
+  const V area = tb.area[d];
+  for (int it = t; it < nact * 3 * NN; it += FT) {
+    const int f = it / (3 * NN), i = it - f * 3 * NN;
+    const int c = i / NN, r = i - c * NN;
+    const int j1 = r % N, j2 = r / N;
+    const V* k = FACE_T0(f) + c * QN + Q * j2;
+    Acc a;
+    A::acc_first(a, sSW[j1], k[0]);
+#pragma unroll
+    for (int q1 = 1; q1 < Q; ++q1) A::acc_fma(a, sSW[q1 * N + j1], k[q1]);
+    rface[((size_t)d * m.E + el[f]) * 3 * NN + i] = A::store(A::mul(area, A::acc_get(a)));
   }
+#undef FACE_T0
+#undef FACE_G1
+#undef FACE_G2
 }
 
 template <class A, int N, int Q>
@@ -499,9 +503,10 @@ template <class A, int N, int Q>
 int launch_conv(int part, const MeshDims& m, const double* u3, double* rface, double* dst3, const ConvHost& h,
                 cudaStream_t s) {
   const ConvTabT<typename A::V, N, Q> tb = conv_tables<A, N, Q>(h);
-  constexpr int EPB = conv_fwd_cells_per_block<N>(), FPB = faces_per_block<N>();
+  constexpr int EPB = conv_fwd_cells_per_block<N>(), GPB = face_groups_per_block<N>(), FPG = faces_per_group<N>();
+  constexpr int FPB = GPB * FPG;
   const size_t smem = ((size_t)EPB * ConvLayout<N, Q>::PER + 6 * Q * N) * sizeof(double);
-  const size_t fsmem = ((size_t)FPB * FaceLayout<N, Q>::PER + 2 * Q * N) * sizeof(double);
+  const size_t fsmem = (size_t)GPB * (FPG * FaceLayout<N, Q>::PER + 2 * Q * N) * sizeof(double);
   if (smem > 232448 || fsmem > 232448) return 7;
   if (cudaFuncSetAttribute(conv_kernel<A, N, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
           cudaSuccess ||
@@ -511,7 +516,7 @@ int launch_conv(int part, const MeshDims& m, const double* u3, double* rface, do
   if (m.E == 0) return 0;
   if (part & 1) {
     const dim3 fgrid((unsigned)((m.E + FPB - 1) / FPB), 3);
-    conv_face_kernel<A, N, Q><<<fgrid, FPB * face_threads<N>(), fsmem, s>>>(u3, rface, tb, m);
+    conv_face_kernel<A, N, Q><<<fgrid, GPB * face_threads<N>(), fsmem, s>>>(u3, rface, tb, m);
   }
   if (part & 2) {
     const long long blocks = (m.E + EPB - 1) / EPB;

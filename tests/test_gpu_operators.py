@@ -127,7 +127,7 @@ def test_convective(n, k, field, mode):
 
 
 @pytest.mark.parametrize("mode", [0, 1])
-@pytest.mark.parametrize("n,k", [((3, 2, 2), 3), ((2, 1, 3), 2), ((1, 2, 1), 7)])
+@pytest.mark.parametrize("n,k", [((3, 2, 2), 3), ((2, 1, 3), 2), ((1, 2, 1), 7), ((3, 1, 3), 3), ((3, 3, 1), 1)])
 def test_convective_two_phases(n, k, mode):
     """Face kernel + cell kernel through the two-phase entry points give the
     one-call result exactly, and the oracle's result."""
