@@ -46,6 +46,7 @@ struct F64 {
   static constexpr bool emulated = false;
   __device__ __forceinline__ static V from_double(double x) { return x; }
   __device__ __forceinline__ static V load(const double* p) { return __ldg(p); }
+  __device__ __forceinline__ static V split(double x) { return x; }
   __device__ __forceinline__ static double to_double(V x) { return x; }
   __host__ static V make(double x) { return x; }
   __device__ __forceinline__ static V zero() { return 0.0; }
@@ -98,8 +99,9 @@ struct DF64 {
   // (truncated), lo = the remaining 29 fraction bits rounded to a float, same
   // sign.  |hi + lo - x| <= 2^-47 |x| for 2^-74 <= |x| < 2^127; below 2^-74
   // lo is dropped (absolute error < 2^-97), below 2^-126 the value is zero.
-  __device__ __forceinline__ static V load(const double* p) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(__ldg(p));
+  __device__ __forceinline__ static V load(const double* p) { return split(__ldg(p)); }
+  __device__ __forceinline__ static V split(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const unsigned h = (unsigned)(b >> 32), l = (unsigned)b;
     const unsigned sgn = h & 0x80000000u;
     const int e = (int)((h >> 20) & 0x7FFu);

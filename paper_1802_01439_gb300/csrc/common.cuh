@@ -155,6 +155,16 @@ __device__ __forceinline__ void store_line(T* buf, int base, int stride, const T
   for (int j = 0; j < N; ++j) buf[base + j * stride] = x[j];
 }
 
+// Asynchronous 8-byte global -> shared copy (cp.async, cached in L1), the
+// commit of the copies issued so far, and the wait for all of them.  The
+// copied data is visible to other threads after the wait and a barrier.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Dynamic shared memory, aligned for double2 accesses.
 __device__ __forceinline__ unsigned char* dyn_smem() {
   extern __shared__ __align__(16) unsigned char dgns_smem[];

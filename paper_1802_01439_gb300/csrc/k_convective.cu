@@ -52,14 +52,15 @@ template <int N, int Q>
 struct ConvLayout {
   static constexpr int N3 = N * N * N;
   static constexpr int U = 3 * N3;               // nodal velocity
-  static constexpr int U1 = 3 * Q * N * N;       // x-interpolated; later: result
+  static constexpr int U1 = 3 * Q * N * N;       // x-interpolated
+  static constexpr int U1R = U1 > 18 * N * N ? U1 : 18 * N * N;  // later: the six face integrals
   static constexpr int U2 = 3 * Q * Q * N;       // xy-interpolated
   static constexpr int P = 3 * Q * Q;            // one z-plane: u
   static constexpr int X = 9 * N * Q;            // x-tested plane
   static constexpr int Y = 6 * N * N;            // xy-tested plane
   static constexpr int PXY = P + X + Y;
   static constexpr int UP = U > PXY ? U : PXY;   // nodal u first, plane work later
-  static constexpr int PER = UP + U1 + U2;
+  static constexpr int PER = UP + U1R + U2;
 };
 
 // Face kernel groups: one warp for FPG faces up to N = 6 (two faces up to
@@ -160,7 +161,7 @@ __global__ void __launch_bounds__(conv_fwd_cells_per_block<N>() * conv_threads<N
   V* sX = sP + LY::P;
   V* sY = sX + LY::X;
   V* sU1 = sU + LY::UP;
-  V* sU2 = sU1 + LY::U1;
+  V* sU2 = sU1 + LY::U1R;
 
   unsigned el = 0;
   CellXYZ cx{};
@@ -198,6 +199,21 @@ __global__ void __launch_bounds__(conv_fwd_cells_per_block<N>() * conv_threads<N
       sU2[c * QQ * N + qx + Q * qy + QQ * z] = A::acc_get(a);
     }
   group_sync<NT>();
+
+  // The face integrals of the six faces (raw doubles), fetched asynchronously
+  // into the dead x-interpolation buffer while the plane loop runs:
+  // block f = 2 d (+R of face (e, d)) and 2 d + 1 (-R of face (e-1_d, d)).
+  double* sR = reinterpret_cast<double*>(sU1);
+  if (active) {
+    const unsigned nbm[3] = {neighbor32<0>(cx, -1, m), neighbor32<1>(cx, -1, m), neighbor32<2>(cx, -1, m)};
+    for (int it = t; it < 18 * NN; it += NT) {
+      const int f = it / (3 * NN), i = it - f * 3 * NN;
+      const int dd = f >> 1;
+      const unsigned cell = (f & 1) ? nbm[dd] : el;
+      cp_async8(sR + it, rface + ((size_t)dd * m.E + cell) * 3 * NN + i);
+    }
+  }
+  cp_async_commit();
 
   // The plane loop: every lane keeps the same work items in all planes, so
   // their offsets are computed once; the lane's outputs (items of P4) stay
@@ -318,11 +334,11 @@ __global__ void __launch_bounds__(conv_fwd_cells_per_block<N>() * conv_threads<N
       }
     group_sync<NT>();
   }
+  cp_async_wait_all();
+  group_sync<NT>();
   // face integrals from the face kernel: +R on the layer N-1 (this cell is
   // the '-' side of its face), -R of the '-' neighbour on the layer 0
   if (active) {
-    const unsigned nbm0 = neighbor32<0>(cx, -1, m), nbm1 = neighbor32<1>(cx, -1, m), nbm2 = neighbor32<2>(cx, -1, m);
-    const size_t E = (size_t)m.E, FS = 3 * NN;
 #pragma unroll
     for (int r = 0; r < R4; ++r) {
       const int it = t + NT * r;
@@ -330,14 +346,14 @@ __global__ void __launch_bounds__(conv_fwd_cells_per_block<N>() * conv_threads<N
       const int c = it / N3, rr = it - c * N3;
       const int x = rr % N, yz = rr / N;
       const int y = yz % N, z = yz / N;
-      const double* rc = rface + c * NN;
+      const double* rc = sR + c * NN;
       V v = A::acc_get(out[r]);
-      if (x == N - 1) v = A::add(v, A::load(rc + el * FS + y + N * z));
-      if (x == 0) v = A::sub(v, A::load(rc + nbm0 * FS + y + N * z));
-      if (y == N - 1) v = A::add(v, A::load(rc + (E + el) * FS + x + N * z));
-      if (y == 0) v = A::sub(v, A::load(rc + (E + nbm1) * FS + x + N * z));
-      if (z == N - 1) v = A::add(v, A::load(rc + (2 * E + el) * FS + x + N * y));
-      if (z == 0) v = A::sub(v, A::load(rc + (2 * E + nbm2) * FS + x + N * y));
+      if (x == N - 1) v = A::add(v, A::split(rc[0 * 3 * NN + y + N * z]));
+      if (x == 0) v = A::sub(v, A::split(rc[1 * 3 * NN + y + N * z]));
+      if (y == N - 1) v = A::add(v, A::split(rc[2 * 3 * NN + x + N * z]));
+      if (y == 0) v = A::sub(v, A::split(rc[3 * 3 * NN + x + N * z]));
+      if (z == N - 1) v = A::add(v, A::split(rc[4 * 3 * NN + x + N * y]));
+      if (z == 0) v = A::sub(v, A::split(rc[5 * 3 * NN + x + N * y]));
       dst3[((size_t)c * m.E + el) * N3 + rr] = A::store(v);
     }
   }
