@@ -174,20 +174,26 @@ int dgns_penalty_parameters(dgns_ctx* ctx, const double* u_ex3, double dt, doubl
 int dgns_vmult_projection(dgns_ctx* ctx, double* dst3, const double* src3, const double* tau_d,
                           const double* tau_c);
 
+/* CG solves stop when ||r||_2 <= rel_tol ||r_0||_2 or ||r||_2 <= abs_tol,
+ * r_0 = b - A x_0 the initial residual (Sec. 3.3: the paper's solvers use
+ * abs_tol = 1e-12 and rel_tol = 1e-6 with x_0 extrapolated from previous
+ * time steps). */
 typedef struct {
-  double rel_tol;          /* stop when ||r||_2 <= rel_tol ||b||_2 (default 1e-10) */
-  double abs_tol;          /* or ||r||_2 <= abs_tol (default 0)                      */
+  double rel_tol;          /* default 1e-10                                         */
+  double abs_tol;          /* default 0                                             */
   int max_iter;            /* default 200                                           */
   int cheb_degree;         /* Chebyshev degree, pre and post (default 5)            */
   double smoothing_range;  /* lambda_max / lambda_min of the smoother (default 20)  */
   int cheb_coarse_iters;   /* Chebyshev steps of the coarse solve (default 20)       */
   int project_mean;        /* 1: remove the Euclidean mean of r0 and of every z      */
+  int use_initial_guess;   /* 0 (default): x_0 = 0; 1: x holds x_0 on entry (read
+                              and overwritten; host pointers are copied both ways)  */
 } dgns_solve_params;
 
 typedef struct {
   int iterations;
-  double rel_res;          /* final ||r||_2 / ||b||_2 (recursively updated)         */
-  double initial_res;      /* ||b||_2                                                */
+  double rel_res;          /* final ||r||_2 / ||r_0||_2 (recursively updated r)     */
+  double initial_res;      /* ||r_0||_2 (= ||b||_2 for x_0 = 0)                      */
   int status;
   double lambda_max_fine;  /* Chebyshev upper bound of the finest level             */
   double seconds;          /* wall time of the solve                                */
@@ -199,9 +205,9 @@ void dgns_default_solve_params(dgns_solve_params* p);
  * by one h-multigrid V-cycle per iteration with Jacobi-Chebyshev smoothing
  * (degree cheb_degree pre and post, range smoothing_range), Chebyshev coarse
  * solve, embedding prolongation and its transpose as restriction; the V-cycle
- * runs in the context's mg_precision.  Zero initial guess; x (space P) gets
- * the solution.  Returns DGNS_ERR_NOT_CONVERGED with info filled when
- * max_iter is reached. */
+ * runs in the context's mg_precision.  x (space P) gets the solution;
+ * initial guess per params->use_initial_guess.  Returns
+ * DGNS_ERR_NOT_CONVERGED with info filled when max_iter is reached. */
 int dgns_cg_mg_solve(dgns_ctx* ctx, double* x, const double* b,
                      const dgns_solve_params* params, dgns_solve_info* info);
 
@@ -219,8 +225,8 @@ int dgns_mg_prolongate_f32(dgns_ctx* ctx, float* fine, const float* coarse, int 
 int dgns_mg_restrict_f32(dgns_ctx* ctx, float* coarse, const float* fine, int level);
 
 /* Helmholtz solve (viscous substep, Sec. 3.3): CG preconditioned by the
- * inverse mass matrix on (mass_factor M + V) x3 = b3, FP64, zero initial
- * guess. */
+ * inverse mass matrix on (mass_factor M + V) x3 = b3, FP64; initial guess
+ * per params->use_initial_guess. */
 int dgns_cg_invmass_solve(dgns_ctx* ctx, double* x3, const double* b3, double mass_factor,
                           const dgns_solve_params* params, dgns_solve_info* info);
 
@@ -246,8 +252,8 @@ int dgns_cg_invmass_solve_noalloc(dgns_ctx* ctx, double* x3, const double* b3, d
                                   const dgns_solve_params* params, dgns_solve_info* info);
 
 /* Projection solve (Sec. 3.3): CG preconditioned by the inverse mass
- * matrix on (M + A_D + A_C) x3 = b3, FP64, zero initial guess; device
- * pointers; k_u <= 7. */
+ * matrix on (M + A_D + A_C) x3 = b3, FP64; initial guess per
+ * params->use_initial_guess; device pointers; k_u <= 7. */
 int dgns_cg_projection_solve(dgns_ctx* ctx, double* x3, const double* b3, const double* tau_d,
                              const double* tau_c, const dgns_solve_params* params, dgns_solve_info* info);
 

@@ -35,7 +35,7 @@ class SolveParams(ctypes.Structure):
     _fields_ = [("rel_tol", ctypes.c_double), ("abs_tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("cheb_degree", ctypes.c_int),
                 ("smoothing_range", ctypes.c_double), ("cheb_coarse_iters", ctypes.c_int),
-                ("project_mean", ctypes.c_int)]
+                ("project_mean", ctypes.c_int), ("use_initial_guess", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):

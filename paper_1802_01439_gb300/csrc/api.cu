@@ -167,6 +167,19 @@ struct Staged {
     any_host = true;
     return 0;
   }
+  // read and written: copied in like `in` and back like `out`
+  int inout(void* p, size_t bytes, void** dev) {
+    if (is_device_ptr(p)) {
+      *dev = p;
+      return 0;
+    }
+    const void* d;
+    int rc = in(p, bytes, &d);
+    if (rc) return rc;
+    outs.push_back({p, const_cast<void*>(d), bytes});
+    *dev = const_cast<void*>(d);
+    return 0;
+  }
   int grab(size_t bytes, void** buf) {
     if (slot >= 4) return fail(DGNS_ERR_INVALID_ARG, "too many host-pointer arguments");
     if (c->stage_cap[slot] < bytes) {
@@ -561,6 +574,7 @@ void dgns_default_solve_params(dgns_solve_params* p) {
   p->smoothing_range = 20.0;
   p->cheb_coarse_iters = 20;
   p->project_mean = 1;
+  p->use_initial_guess = 0;
 }
 
 const char* dgns_status_string(int s) {
@@ -1087,9 +1101,15 @@ int dgns_cg_projection_solve(dgns_ctx* c, double* x3, const double* b3, const do
   const auto t0 = std::chrono::steady_clock::now();
   const int N = c->N[0];
   const double(*MI)[MAXN * MAXN] = c->minv3[0];
-  DG_CUDA(cudaMemsetAsync(x3, 0, bytes, c->s));
   DG_CUDA(cudaMemcpyAsync(c->r, b3, bytes, cudaMemcpyDeviceToDevice, c->s));
-  DG_TRY(dot(b3, b3, n, c->red, S_T0, c->s));
+  if (prm.use_initial_guess) {
+    DG_TRY(projection_apply(c->m, x3, c->Ap, tau_d, tau_c, c->proj, c->s));
+    DG_TRY(axpby(c->r, c->Ap, n, -1.0, 1.0, c->s));
+    DG_TRY(dot(c->r, c->r, n, c->red, S_T0, c->s));
+  } else {
+    DG_CUDA(cudaMemsetAsync(x3, 0, bytes, c->s));
+    DG_TRY(dot(b3, b3, n, c->red, S_T0, c->s));
+  }
   DG_TRY(read_scalars(c));
   const double nb = sqrt(c->h_scal[S_T0]);
   dgns_solve_info inf{};
@@ -1195,17 +1215,25 @@ int dgns_cg_mg_solve(dgns_ctx* c, double* x, const double* b, const dgns_solve_p
   const void* bs;
   void* xs;
   DG_TRY(st.in(b, bytes, &bs));
-  DG_TRY(st.out(x, bytes, &xs));
+  DG_TRY(prm.use_initial_guess ? st.inout(x, bytes, &xs) : st.out(x, bytes, &xs));
   double* X = (double*)xs;
   const double* B = (const double*)bs;
   const LapHost& A = c->lap[DGNS_SPACE_P];
-  DG_CUDA(cudaMemsetAsync(X, 0, bytes, c->s));
-  DG_TRY(dot(B, B, n, c->red, S_T0, c->s));
+  if (!prm.use_initial_guess) {
+    DG_CUDA(cudaMemsetAsync(X, 0, bytes, c->s));
+    DG_TRY(dot(B, B, n, c->red, S_T0, c->s));
+  }
   if (prm.project_mean) {
     DG_TRY(sum(B, n, c->red, S_SUM, c->s));
     DG_TRY(convert_shift(B, false, c->r, false, n, &c->red, S_SUM, c->s));
   } else {
     DG_CUDA(cudaMemcpyAsync(c->r, B, bytes, cudaMemcpyDeviceToDevice, c->s));
+  }
+  if (prm.use_initial_guess) {
+    // r0 = b - A x0 (A annihilates constants, so the mean shift of b is the one of r0)
+    DG_TRY(laplace_apply(false, c->m, 1, X, c->Ap, A, EPI_NONE, EpiHost(), c->s, c->d.fp64_mode == 1));
+    DG_TRY(axpby(c->r, c->Ap, n, -1.0, 1.0, c->s));
+    DG_TRY(dot(c->r, c->r, n, c->red, S_T0, c->s));
   }
   DG_TRY(read_scalars(c));
   const double nb = sqrt(c->h_scal[S_T0]);
@@ -1273,16 +1301,22 @@ int dgns_cg_invmass_solve(dgns_ctx* c, double* x3, const double* b3, double mass
   const void* bs;
   void* xs;
   DG_TRY(st.in(b3, bytes, &bs));
-  DG_TRY(st.out(x3, bytes, &xs));
+  DG_TRY(prm.use_initial_guess ? st.inout(x3, bytes, &xs) : st.out(x3, bytes, &xs));
   double* X = (double*)xs;
   const double* B = (const double*)bs;
   LapHost H;
   build_lap(c->sp1[0], c->h, c->d.penalty_factor, c->d.nu, mass_factor, H);
   const int N = c->N[0];
   const double(*MI)[MAXN * MAXN] = c->minv3[0];
-  DG_CUDA(cudaMemsetAsync(X, 0, bytes, c->s));
   DG_CUDA(cudaMemcpyAsync(c->r, B, bytes, cudaMemcpyDeviceToDevice, c->s));
-  DG_TRY(dot(B, B, n, c->red, S_T0, c->s));
+  if (prm.use_initial_guess) {
+    DG_TRY(laplace_apply(false, c->m, 3, X, c->Ap, H, EPI_NONE, EpiHost(), c->s, c->d.fp64_mode == 1));
+    DG_TRY(axpby(c->r, c->Ap, n, -1.0, 1.0, c->s));
+    DG_TRY(dot(c->r, c->r, n, c->red, S_T0, c->s));
+  } else {
+    DG_CUDA(cudaMemsetAsync(X, 0, bytes, c->s));
+    DG_TRY(dot(B, B, n, c->red, S_T0, c->s));
+  }
   DG_TRY(read_scalars(c));
   const double nb = sqrt(c->h_scal[S_T0]);
   dgns_solve_info inf{};

@@ -116,10 +116,17 @@ extern "C" int dgns_cg_invmass_solve_noalloc(dgns_ctx* c, double* x3, const doub
   const int N = c->N[0];
   const double(*MI)[MAXN * MAXN] = c->minv3[0];
   // The scratch keeps the previous call's contents; every work vector below
-  // is written before it is read, and x (caller-owned) is cleared here.
-  NA_CUDA(cudaMemsetAsync(x3, 0, bytes, c->s));
+  // is written before it is read, and x (caller-owned) is cleared here
+  // unless it holds the initial guess.
   NA_CUDA(cudaMemcpyAsync(r, b3, bytes, cudaMemcpyDeviceToDevice, c->s));
-  NA_TRY(dot(b3, b3, n, red, S_T0, c->s));
+  if (prm.use_initial_guess) {
+    NA_TRY(laplace_apply(false, c->m, 3, x3, Ap, H, EPI_NONE, EpiHost(), c->s, c->d.fp64_mode == 1));
+    NA_TRY(axpby(r, Ap, n, -1.0, 1.0, c->s));
+    NA_TRY(dot(r, r, n, red, S_T0, c->s));
+  } else {
+    NA_CUDA(cudaMemsetAsync(x3, 0, bytes, c->s));
+    NA_TRY(dot(b3, b3, n, red, S_T0, c->s));
+  }
   NA_TRY(read_scal());
   const double nb = sqrt(hs[S_T0]);
   dgns_solve_info inf{};
@@ -133,7 +140,7 @@ extern "C" int dgns_cg_invmass_solve_noalloc(dgns_ctx* c, double* x3, const doub
     double res = 1.0;
     status = DGNS_ERR_NOT_CONVERGED;
     while (it < prm.max_iter) {
-      NA_TRY(laplace_apply(false, c->m, 3, p, Ap, H, EPI_NONE, EpiHost(), c->s));
+      NA_TRY(laplace_apply(false, c->m, 3, p, Ap, H, EPI_NONE, EpiHost(), c->s, c->d.fp64_mode == 1));
       NA_TRY(dot(p, Ap, n, red, S_PAP, c->s));
       NA_TRY(cg_update(x3, r, p, Ap, n, red, c->s));
       NA_TRY(read_scal());

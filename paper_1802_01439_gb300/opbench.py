@@ -24,7 +24,7 @@ from paper_1802_01439_gb300 import Context, inputs  # noqa: E402
 # elements per direction giving ~16.8M scalar DoFs for k = 2..11
 SWEEP_N = {2: 85, 3: 64, 4: 51, 5: 43, 6: 37, 7: 32, 8: 28, 9: 26, 10: 23, 11: 21}
 OPS = ["laplace", "laplace32", "convective", "viscous", "helmholtz", "invmass", "mass",
-       "divergence", "gradient"]
+       "divergence", "gradient", "projection"]
 
 
 def run(op, k, n, reps, warmup, ku=None, fp64_mode=0):
@@ -71,6 +71,13 @@ def run(op, k, n, reps, warmup, ku=None, fp64_mode=0):
         x, y, dofs = rng(np_, 0), torch.empty(3 * nu, **f64), np_
         fn = lambda: ctx.vmult_gradient(y, x)
         nbytes = 8 * (3 * nu + np_)
+    elif op == "projection":
+        u = torch.from_numpy(inputs.taylor_green((n,) * 3, (-np.pi,) * 3, (np.pi,) * 3, ctx.nodes_1d(0),
+                                                 noise=1e-3, seed=0).ravel()).to(dev)
+        td, tc = ctx.penalty_parameters(u, 1e-3)
+        x, y, dofs = rng(3 * nu, 0), torch.empty(3 * nu, **f64), 3 * nu
+        fn = lambda: ctx.vmult_projection(y, x, td, tc)
+        nbytes = 16 * 3 * nu
     else:
         raise ValueError(op)
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)

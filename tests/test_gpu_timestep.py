@@ -11,6 +11,8 @@ import torch
 from oracle import dg, rules, timestep
 from tests.gpu_common import build_lib, context, dev, host, random_field, rel_err, tgv_field
 
+OPTS = {"rel_tol": 1e-13, "abs_tol": 0.0}
+
 pytestmark = pytest.mark.gpu
 
 
@@ -85,10 +87,10 @@ def test_operator_gradients_gradcheck():
     assert torch.autograd.gradcheck(lambda x: ns._Mass.apply(ctx, x), (u,), **kw)
     assert torch.autograd.gradcheck(lambda x: ns._Div.apply(ctx, x), (u,), **kw)
     assert torch.autograd.gradcheck(lambda x: ns._Grad.apply(ctx, x), (p,), **kw)
-    assert torch.autograd.gradcheck(lambda x: ns._Helmholtz.apply(ctx, x, 100.0, 1e-13), (u,), **kw)
+    assert torch.autograd.gradcheck(lambda x: ns._Helmholtz.apply(ctx, x, 100.0, OPTS, None), (u,), **kw)
     assert torch.autograd.gradcheck(lambda x: ds.dissipation(x), (u,), **kw)
     pm = (p - p.mean()).detach().requires_grad_()
-    assert torch.autograd.gradcheck(lambda x: ns._Poisson.apply(ctx, x - x.mean(), 1e-13), (pm,), **kw)
+    assert torch.autograd.gradcheck(lambda x: ns._Poisson.apply(ctx, x - x.mean(), OPTS, None), (pm,), **kw)
 
 
 def _fd_check(n, k, nu, dt, steps, ndir, delta, tol, noise=1e-3, offset=0.0):
@@ -160,4 +162,63 @@ def test_projection_solve_gradcheck():
     td, tc = ctx.penalty_parameters(u, 0.1, 1.0, 1.0)
     x = u.clone().requires_grad_()
     kw = dict(eps=1e-6, atol=1e-7, rtol=1e-6, fast_mode=True)
-    assert torch.autograd.gradcheck(lambda y: ns._Projection.apply(ctx, y, td, tc, 1e-13), (x,), **kw)
+    assert torch.autograd.gradcheck(lambda y: ns._Projection.apply(ctx, y, td, tc, OPTS, None), (x,), **kw)
+
+
+@pytest.mark.parametrize("which", ["mg", "invmass", "projection"])
+def test_initial_guess(which):
+    """A solve started from an initial guess reaches the same solution as one
+    from zero; the relative criterion is taken against the initial residual;
+    the exact solution as initial guess stops after one iteration."""
+    n, k = (3, 2, 2), 3
+    ctx = context(n, k, k - 1, mg_precision=32, nu=0.05)
+    s = dg.Space(dg.Mesh(n), k)
+    if which == "mg":
+        b = dev(random_field(dg.Space(s.mesh, k - 1), 1, 3).ravel())
+        b -= b.mean()
+        solve = lambda x, **kw: ctx.cg_mg_solve(x, b, **kw)
+    elif which == "invmass":
+        b = dev(random_field(s, 3, 3).ravel())
+        solve = lambda x, **kw: ctx.cg_invmass_solve(x, b, 150.0, **kw)
+    else:
+        b = dev(random_field(s, 3, 3).ravel())
+        td, tc = ctx.penalty_parameters(dev(tgv_field(s, 1e-2, 1).ravel()), 0.1)
+        solve = lambda x, **kw: ctx.cg_projection_solve(x, b, td, tc, **kw)
+    x0 = torch.zeros_like(b)
+    i0 = solve(x0, rel_tol=1e-13)
+    xg = dev(np.random.default_rng(9).uniform(-1, 1, b.numel()))
+    if which == "mg":
+        xg -= xg.mean()
+    x1 = xg.clone()
+    i1 = solve(x1, rel_tol=1e-13, use_initial_guess=1)
+    assert i1["initial_res"] != i0["initial_res"]
+    assert rel_err(host(x1), host(x0)) <= 1e-10
+    # exact solution as the guess: the absolute criterion stops the solve
+    x2 = x0.clone()
+    i2 = solve(x2, rel_tol=1e-6, abs_tol=1e-9 * i0["initial_res"], use_initial_guess=1)
+    assert i2["iterations"] == 1 and i2["initial_res"] <= 1e-9 * i0["initial_res"]
+    assert rel_err(host(x2), host(x0)) <= 1e-11
+
+
+def test_extrapolated_guesses_accuracy():
+    """The paper's solver setting (abs 1e-12, rel 1e-6 to the initial residual)
+    with extrapolated and with zero initial guesses, against a run solved to
+    1e-13: both stay within the tolerance's reach of the reference, and the
+    extrapolated guesses end more accurate (their initial residual is
+    smaller, so the same relative reduction ends at a smaller residual)."""
+    from paper_1802_01439_gb300.navier_stokes import DualSplitting
+    n, k, nu, dt = (4, 4, 4), 3, 1.0 / 1600, 2e-3
+    ctx = context(n, k, k - 1, mg_precision=32, nu=nu)
+    s = dg.Space(dg.Mesh(n), k)
+    u0 = dev(tgv_field(s, 1e-3, 2).ravel())
+    out = {}
+    for name, tol, guess in (("ref", 1e-13, "zero"), ("zero", 1e-6, "zero"), ("extrapolate", 1e-6, "extrapolate")):
+        ds = DualSplitting(ctx, dt, solver_tol=tol, abs_tol=1e-12, projection="penalty", guess=guess)
+        ds.log = []
+        with torch.no_grad():
+            u = ds.run(u0, 6, checkpoint_steps=False)
+        assert all(i["status"] == 0 for _, i in ds.log)
+        out[name] = host(u)
+    err_zero = rel_err(out["zero"], out["ref"])
+    err_ex = rel_err(out["extrapolate"], out["ref"])
+    assert err_zero <= 1e-4 and err_ex <= 1e-5 and err_ex < err_zero

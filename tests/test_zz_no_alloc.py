@@ -31,11 +31,14 @@ def _solve(lib, ctx, fn, b, mf):
     return rc, x.cpu().numpy(), info
 
 
-def test_noalloc_matches_allocating_solve():
+@pytest.mark.parametrize("mode", [0, 1])
+def test_noalloc_matches_allocating_solve(mode):
+    """Native FP64 (mode 0) and double-float (mode 1) matvecs: both solves
+    use the context's arithmetic."""
     build_lib()
     from paper_1802_01439_gb300 import _lib
     lib = _lib.load()
-    ctx = context((4, 3, 5), 3, mg_precision=0, nu=1.0 / 1600)
+    ctx = context((4, 3, 5), 3, mg_precision=0, nu=1.0 / 1600, fp64_mode=mode)
     mf = 1.5 / 1e-3
     for seed in (1, 2):
         b = torch.from_numpy(np.random.default_rng(seed).uniform(-1, 1, 3 * ctx.n_u)).cuda()
