@@ -1076,7 +1076,7 @@ int dgns_vmult_projection(dgns_ctx* c, double* dst3, const double* src3, const d
   if (overlaps(dst3, bu, src3, bu)) return fail(DGNS_ERR_ALIAS, "dst overlaps src");
   if (!is_device_ptr(dst3) || !is_device_ptr(src3) || !is_device_ptr(tau_d) || !is_device_ptr(tau_c))
     return fail(DGNS_ERR_INVALID_ARG, "device pointers only");
-  const int rc = projection_apply(c->m, src3, dst3, tau_d, tau_c, c->proj, c->s);
+  const int rc = projection_apply(c->m, src3, dst3, tau_d, tau_c, c->proj, c->s, c->d.fp64_mode == 1);
   if (rc == 7) return fail(DGNS_ERR_UNSUPPORTED, "projection operator: supported for k_u <= 7");
   DG_TRY(rc);
   return 0;
@@ -1103,7 +1103,7 @@ int dgns_cg_projection_solve(dgns_ctx* c, double* x3, const double* b3, const do
   const double(*MI)[MAXN * MAXN] = c->minv3[0];
   DG_CUDA(cudaMemcpyAsync(c->r, b3, bytes, cudaMemcpyDeviceToDevice, c->s));
   if (prm.use_initial_guess) {
-    DG_TRY(projection_apply(c->m, x3, c->Ap, tau_d, tau_c, c->proj, c->s));
+    DG_TRY(projection_apply(c->m, x3, c->Ap, tau_d, tau_c, c->proj, c->s, c->d.fp64_mode == 1));
     DG_TRY(axpby(c->r, c->Ap, n, -1.0, 1.0, c->s));
     DG_TRY(dot(c->r, c->r, n, c->red, S_T0, c->s));
   } else {
@@ -1123,7 +1123,7 @@ int dgns_cg_projection_solve(dgns_ctx* c, double* x3, const double* b3, const do
     double res = 1.0;
     status = DGNS_ERR_NOT_CONVERGED;
     while (it < prm.max_iter) {
-      DG_TRY(projection_apply(c->m, c->p, c->Ap, tau_d, tau_c, c->proj, c->s));
+      DG_TRY(projection_apply(c->m, c->p, c->Ap, tau_d, tau_c, c->proj, c->s, c->d.fp64_mode == 1));
       DG_TRY(dot(c->p, c->Ap, n, c->red, S_PAP, c->s));
       DG_TRY(cg_update(x3, c->r, c->p, c->Ap, n, c->red, c->s));
       DG_TRY(read_scalars(c));

@@ -14,6 +14,7 @@
 // the nodal values of the face layers and the Gauss rule integrates the face
 // mass exactly, so the own face layer gets
 //   {{tau_C}} h_t1 h_t2 (Mhat (x) Mhat) (u_a(own layer) - u_a(neighbour layer)).
+#include "arith.cuh"
 #include "ops.h"
 
 namespace dgns {
@@ -26,6 +27,17 @@ struct ProjTab {
   double M[N * N];   // 1D mass
   double w[N];       // Gauss weights on [0,1]
   double h[3];
+};
+
+// Tables of the operator kernel in the arithmetic policy's value type.
+template <class V, int N>
+struct ProjTabT {
+  static constexpr bool kMM = N <= 6;   // the N^4 face-mass table fits the parameter space
+  V S[N * N], D[N * N], M[N * N];
+  V MM[kMM ? N * N * N * N : 1];   // (M (x) M)[(j1 + N j2)][(i1 + N i2)] = M[j1][i1] M[j2][i2]
+  V W3[N * N * N];       // w_qx w_qy w_qz h_x h_y h_z
+  V hinv[3];             // 1 / h_d
+  V area[3];             // face area of faces normal to d
 };
 
 template <int N>
@@ -58,134 +70,168 @@ __device__ __forceinline__ void dsweep(const double* in, const double* in2, doub
   }
 }
 
-template <int N>
+// The same sweep in an arithmetic policy: out = A in (+ A2 in2 scaled by the
+// second table, which then already carries the scale).
+template <class P, int N, int D, bool TR, bool TWO>
+__device__ __forceinline__ void psweep(const typename P::V* in, const typename P::V* in2, typename P::V* out,
+                                       int l, const typename P::V* A, const typename P::V* A2) {
+  typedef typename P::V V;
+  typedef typename P::Acc Acc;
+  int base, stride;
+  line_geom<D>(l, N, N, N, base, stride);
+  V x[N], x2[N];
+  load_line<V, N>(in, base, stride, x);
+  if (TWO) load_line<V, N>(in2, base, stride, x2);
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    Acc a;
+    P::acc_first(a, TR ? A[i] : A[i * N], x[0]);
+#pragma unroll
+    for (int j = 1; j < N; ++j) P::acc_fma(a, TR ? A[j * N + i] : A[i * N + j], x[j]);
+    if (TWO) {
+#pragma unroll
+      for (int j = 0; j < N; ++j) P::acc_fma(a, TR ? A2[j * N + i] : A2[i * N + j], x2[j]);
+    }
+    out[base + i * stride] = P::acc_get(a);
+  }
+}
+
+template <class P, int N>
 __global__ void __launch_bounds__(proj_cells_per_block<N>() * N * N)
     proj_kernel(const double* __restrict__ u3, double* __restrict__ dst3, const double* __restrict__ tau_d,
-                const double* __restrict__ tau_c, const __grid_constant__ ProjTab<N> tb, const MeshDims m) {
+                const double* __restrict__ tau_c, const __grid_constant__ ProjTabT<typename P::V, N> tb,
+                const MeshDims m) {
+  typedef typename P::V V;
+  typedef typename P::Acc Acc;
   constexpr int NT = N * N, N3 = N * N * N, EPB = proj_cells_per_block<N>();
   constexpr int PER = 27 * N3;
-  double* sm = reinterpret_cast<double*>(dyn_smem());
+  V* sm = reinterpret_cast<V*>(dyn_smem());
   const int slot = threadIdx.x / NT;
   const int l = threadIdx.x - slot * NT;
   const long long c0 = (long long)blockIdx.x * EPB;
   const long long rem = m.E - c0;
   const int nvalid = rem < EPB ? (int)rem : EPB;
   const bool active = slot < nvalid;
-  double* U = sm + slot * PER;   // 3 N3
-  double* X = U + 3 * N3;        // 4 N3: S u_x, D u_x, S u_y, S u_z (x sweeps)
-  double* Y = X + 4 * N3;        // 5 N3
-  double* Z = Y + 5 * N3;        // 6 N3: V_x V_y V_z G_x G_y G_z -> m_x m_y m_z g
-  double* T1 = Z + 6 * N3;       // 3 N3
-  double* T2 = T1 + 3 * N3;      // 3 N3
-  double* O = T2 + 3 * N3;       // 3 N3
+  V* U = sm + slot * PER;   // 3 N3
+  V* X = U + 3 * N3;        // 4 N3: S u_x, D u_x, S u_y, S u_z (x sweeps)
+  V* Y = X + 4 * N3;        // 5 N3
+  V* Z = Y + 5 * N3;        // 6 N3: V_x V_y V_z G_x G_y G_z -> m_x m_y m_z g
+  V* T1 = Z + 6 * N3;       // 3 N3
+  V* T2 = T1 + 3 * N3;      // 3 N3
+  V* O = T2 + 3 * N3;       // 3 N3
+  // D^T / h_d tables of the three combined test sweeps
+  __shared__ V sDh[3][N * N];
+  for (int i = threadIdx.x; i < 3 * N * N; i += blockDim.x)
+    sDh[i / (N * N)][i % (N * N)] = P::mul(tb.D[i % (N * N)], tb.hinv[i / (N * N)]);
   CellXYZ cx{};
   if (active) {
     cx = cell_xyz((unsigned)(c0 + slot), m);
     for (int c = 0; c < 3; ++c)
-      for (int i = l; i < N3; i += NT) U[c * N3 + i] = u3[((size_t)c * m.E + cx.el) * N3 + i];
+      for (int i = l; i < N3; i += NT) U[c * N3 + i] = P::load(u3 + ((size_t)c * m.E + cx.el) * N3 + i);
   }
   __syncthreads();
   if (active) {
-    dsweep<N, 0, false, false>(U, nullptr, X, l, tb.S, nullptr, 0.0);
-    dsweep<N, 0, false, false>(U, nullptr, X + N3, l, tb.D, nullptr, 0.0);
-    dsweep<N, 0, false, false>(U + N3, nullptr, X + 2 * N3, l, tb.S, nullptr, 0.0);
-    dsweep<N, 0, false, false>(U + 2 * N3, nullptr, X + 3 * N3, l, tb.S, nullptr, 0.0);
+    psweep<P, N, 0, false, false>(U, nullptr, X, l, tb.S, nullptr);
+    psweep<P, N, 0, false, false>(U, nullptr, X + N3, l, tb.D, nullptr);
+    psweep<P, N, 0, false, false>(U + N3, nullptr, X + 2 * N3, l, tb.S, nullptr);
+    psweep<P, N, 0, false, false>(U + 2 * N3, nullptr, X + 3 * N3, l, tb.S, nullptr);
   }
   __syncthreads();
   if (active) {
-    dsweep<N, 1, false, false>(X, nullptr, Y, l, tb.S, nullptr, 0.0);               // SS u_x
-    dsweep<N, 1, false, false>(X + N3, nullptr, Y + N3, l, tb.S, nullptr, 0.0);     // DS u_x
-    dsweep<N, 1, false, false>(X + 2 * N3, nullptr, Y + 2 * N3, l, tb.S, nullptr, 0.0);  // SS u_y
-    dsweep<N, 1, false, false>(X + 2 * N3, nullptr, Y + 3 * N3, l, tb.D, nullptr, 0.0);  // SD u_y
-    dsweep<N, 1, false, false>(X + 3 * N3, nullptr, Y + 4 * N3, l, tb.S, nullptr, 0.0);  // SS u_z
+    psweep<P, N, 1, false, false>(X, nullptr, Y, l, tb.S, nullptr);                  // SS u_x
+    psweep<P, N, 1, false, false>(X + N3, nullptr, Y + N3, l, tb.S, nullptr);        // DS u_x
+    psweep<P, N, 1, false, false>(X + 2 * N3, nullptr, Y + 2 * N3, l, tb.S, nullptr);  // SS u_y
+    psweep<P, N, 1, false, false>(X + 2 * N3, nullptr, Y + 3 * N3, l, tb.D, nullptr);  // SD u_y
+    psweep<P, N, 1, false, false>(X + 3 * N3, nullptr, Y + 4 * N3, l, tb.S, nullptr);  // SS u_z
   }
   __syncthreads();
   if (active) {
-    dsweep<N, 2, false, false>(Y, nullptr, Z, l, tb.S, nullptr, 0.0);               // V_x
-    dsweep<N, 2, false, false>(Y + 2 * N3, nullptr, Z + N3, l, tb.S, nullptr, 0.0);  // V_y
-    dsweep<N, 2, false, false>(Y + 4 * N3, nullptr, Z + 2 * N3, l, tb.S, nullptr, 0.0);  // V_z
-    dsweep<N, 2, false, false>(Y + N3, nullptr, Z + 3 * N3, l, tb.S, nullptr, 0.0);      // G_x
-    dsweep<N, 2, false, false>(Y + 3 * N3, nullptr, Z + 4 * N3, l, tb.S, nullptr, 0.0);  // G_y
-    dsweep<N, 2, false, false>(Y + 4 * N3, nullptr, Z + 5 * N3, l, tb.D, nullptr, 0.0);  // G_z
+    psweep<P, N, 2, false, false>(Y, nullptr, Z, l, tb.S, nullptr);                  // V_x
+    psweep<P, N, 2, false, false>(Y + 2 * N3, nullptr, Z + N3, l, tb.S, nullptr);    // V_y
+    psweep<P, N, 2, false, false>(Y + 4 * N3, nullptr, Z + 2 * N3, l, tb.S, nullptr);  // V_z
+    psweep<P, N, 2, false, false>(Y + N3, nullptr, Z + 3 * N3, l, tb.S, nullptr);      // G_x
+    psweep<P, N, 2, false, false>(Y + 3 * N3, nullptr, Z + 4 * N3, l, tb.S, nullptr);  // G_y
+    psweep<P, N, 2, false, false>(Y + 4 * N3, nullptr, Z + 5 * N3, l, tb.D, nullptr);  // G_z
   }
   __syncthreads();
   if (active) {
-    const double td = tau_d[cx.el];
-    const double jac = tb.h[0] * tb.h[1] * tb.h[2];
+    const V td = P::load(tau_d + cx.el);
     for (int i = l; i < N3; i += NT) {
-      const int qx = i % N, qy = (i / N) % N, qz = i / (N * N);
-      const double w = tb.w[qx] * tb.w[qy] * tb.w[qz] * jac;
-      const double div = Z[3 * N3 + i] / tb.h[0] + Z[4 * N3 + i] / tb.h[1] + Z[5 * N3 + i] / tb.h[2];
-      Z[i] *= w;
-      Z[N3 + i] *= w;
-      Z[2 * N3 + i] *= w;
-      Z[3 * N3 + i] = td * w * div;
+      const V w = tb.W3[i];
+      Acc dv;
+      P::acc_first(dv, tb.hinv[0], Z[3 * N3 + i]);
+      P::acc_fma(dv, tb.hinv[1], Z[4 * N3 + i]);
+      P::acc_fma(dv, tb.hinv[2], Z[5 * N3 + i]);
+      Z[i] = P::mul(w, Z[i]);
+      Z[N3 + i] = P::mul(w, Z[N3 + i]);
+      Z[2 * N3 + i] = P::mul(w, Z[2 * N3 + i]);
+      Z[3 * N3 + i] = P::mul(P::mul(td, w), P::acc_get(dv));
     }
   }
   __syncthreads();
-  // tests: b = x: (S^T m_x + D^T g / h_x) along x, then S^T y, S^T z
+  // tests: b = x: (S^T m_x + (D/h_x)^T g) along x, then S^T y, S^T z
   //        b = y: along y first, then x, z;  b = z: along z first, then x, y
   if (active) {
-    dsweep<N, 0, true, true>(Z, Z + 3 * N3, T1, l, tb.S, tb.D, 1.0 / tb.h[0]);
-    dsweep<N, 1, true, true>(Z + N3, Z + 3 * N3, T1 + N3, l, tb.S, tb.D, 1.0 / tb.h[1]);
-    dsweep<N, 2, true, true>(Z + 2 * N3, Z + 3 * N3, T1 + 2 * N3, l, tb.S, tb.D, 1.0 / tb.h[2]);
+    psweep<P, N, 0, true, true>(Z, Z + 3 * N3, T1, l, tb.S, sDh[0]);
+    psweep<P, N, 1, true, true>(Z + N3, Z + 3 * N3, T1 + N3, l, tb.S, sDh[1]);
+    psweep<P, N, 2, true, true>(Z + 2 * N3, Z + 3 * N3, T1 + 2 * N3, l, tb.S, sDh[2]);
   }
   __syncthreads();
   if (active) {
-    dsweep<N, 1, true, false>(T1, nullptr, T2, l, tb.S, nullptr, 0.0);
-    dsweep<N, 0, true, false>(T1 + N3, nullptr, T2 + N3, l, tb.S, nullptr, 0.0);
-    dsweep<N, 0, true, false>(T1 + 2 * N3, nullptr, T2 + 2 * N3, l, tb.S, nullptr, 0.0);
+    psweep<P, N, 1, true, false>(T1, nullptr, T2, l, tb.S, nullptr);
+    psweep<P, N, 0, true, false>(T1 + N3, nullptr, T2 + N3, l, tb.S, nullptr);
+    psweep<P, N, 0, true, false>(T1 + 2 * N3, nullptr, T2 + 2 * N3, l, tb.S, nullptr);
   }
   __syncthreads();
   if (active) {
-    dsweep<N, 2, true, false>(T2, nullptr, O, l, tb.S, nullptr, 0.0);
-    dsweep<N, 2, true, false>(T2 + N3, nullptr, O + N3, l, tb.S, nullptr, 0.0);
-    dsweep<N, 1, true, false>(T2 + 2 * N3, nullptr, O + 2 * N3, l, tb.S, nullptr, 0.0);
+    psweep<P, N, 2, true, false>(T2, nullptr, O, l, tb.S, nullptr);
+    psweep<P, N, 2, true, false>(T2 + N3, nullptr, O + N3, l, tb.S, nullptr);
+    psweep<P, N, 1, true, false>(T2 + 2 * N3, nullptr, O + 2 * N3, l, tb.S, nullptr);
   }
   __syncthreads();
   // continuity penalty: faces normal to a, component a
   if (active) {
+    const V half_tc = P::half(P::load(tau_c + cx.el));
     for (int a = 0; a < 3; ++a) {
-      const int t1 = a == 0 ? 1 : 0, t2 = a == 2 ? 1 : 2;
-      const double area = a == 0 ? tb.h[1] * tb.h[2] : (a == 1 ? tb.h[0] * tb.h[2] : tb.h[0] * tb.h[1]);
+      // node strides along a and the two tangential directions t1 < t2
+      const int sa = a == 0 ? 1 : (a == 1 ? N : N * N);
+      const int s1 = a == 0 ? N : 1, s2 = a == 2 ? N : N * N;
       for (int side = 1; side >= -1; side -= 2) {
         const unsigned nb = a == 0 ? neighbor32<0>(cx, side, m) : (a == 1 ? neighbor32<1>(cx, side, m)
                                                                           : neighbor32<2>(cx, side, m));
-        const double tbar = 0.5 * (tau_c[cx.el] + tau_c[nb]) * area;
+        // {{tau_C}} |F| (the halving is exact)
+        const V tbar = P::mul(P::add(half_tc, P::half(P::load(tau_c + nb))), tb.area[a]);
         const int aown = side > 0 ? N - 1 : 0, anb = side > 0 ? 0 : N - 1;
         // thread l handles face node (j1, j2) = (l % N, l / N): (M (x) M) jump
         const int j1 = l % N, j2 = l / N;
-        double acc = 0.0;
         const double* ua = u3 + ((size_t)a * m.E) * N3;
+        Acc acc;
 #pragma unroll
         for (int i2 = 0; i2 < N; ++i2) {
 #pragma unroll
           for (int i1 = 0; i1 < N; ++i1) {
-            int co[3], cn[3];
-            co[a] = aown;
-            co[t1] = i1;
-            co[t2] = i2;
-            cn[a] = anb;
-            cn[t1] = i1;
-            cn[t2] = i2;
-            const int io = co[0] + N * (co[1] + N * co[2]), in_ = cn[0] + N * (cn[1] + N * cn[2]);
-            const double jump = U[a * N3 + io] - __ldg(ua + (size_t)nb * N3 + in_);
-            acc = fma(tb.M[j1 * N + i1] * tb.M[j2 * N + i2], jump, acc);
+            const int io = aown * sa + i1 * s1 + i2 * s2, in_ = anb * sa + i1 * s1 + i2 * s2;
+            const V jump = P::sub(U[a * N3 + io], P::load(ua + (size_t)nb * N3 + in_));
+            const V mm = ProjTabT<V, N>::kMM ? tb.MM[(j1 + N * j2) * N * N + i1 + N * i2]
+                                             : P::mul(tb.M[j1 * N + i1], tb.M[j2 * N + i2]);
+            if (i1 == 0 && i2 == 0)
+              P::acc_first(acc, mm, jump);
+            else
+              P::acc_fma(acc, mm, jump);
           }
         }
-        int co[3];
-        co[a] = aown;
-        co[t1] = j1;
-        co[t2] = j2;
-        const int io = co[0] + N * (co[1] + N * co[2]);
-        O[a * N3 + io] = fma(tbar, acc, O[a * N3 + io]);
+        const int io = aown * sa + j1 * s1 + j2 * s2;
+        Acc o;
+        P::acc_set(o, O[a * N3 + io]);
+        P::acc_fma(o, tbar, P::acc_get(acc));
+        O[a * N3 + io] = P::acc_get(o);
       }
     }
   }
   __syncthreads();
   if (active)
     for (int c = 0; c < 3; ++c)
-      for (int i = l; i < N3; i += NT) dst3[((size_t)c * m.E + cx.el) * N3 + i] = O[c * N3 + i];
+      for (int i = l; i < N3; i += NT) dst3[((size_t)c * m.E + cx.el) * N3 + i] = P::store(O[c * N3 + i]);
 }
 
 // Volume-averaged Euclidean norm of u per cell -> penalty parameters.
@@ -250,17 +296,43 @@ ProjTab<N> make_tab(const ProjHost& h) {
   return tb;
 }
 
-template <int N>
+template <class P, int N>
+ProjTabT<typename P::V, N> make_tabT(const ProjHost& h) {
+  ProjTabT<typename P::V, N> tb;
+  for (int i = 0; i < N * N; ++i) {
+    tb.S[i] = P::make(h.S[i]);
+    tb.D[i] = P::make(h.D[i]);
+  }
+  for (int i = 0; i < N * N; ++i) tb.M[i] = P::make(h.M[i]);
+  if (ProjTabT<typename P::V, N>::kMM)
+    for (int j2 = 0; j2 < N; ++j2)
+      for (int j1 = 0; j1 < N; ++j1)
+        for (int i2 = 0; i2 < N; ++i2)
+          for (int i1 = 0; i1 < N; ++i1)
+            tb.MM[(j1 + N * j2) * N * N + i1 + N * i2] = P::make(h.M[j1 * N + i1] * h.M[j2 * N + i2]);
+  const double jac = h.h[0] * h.h[1] * h.h[2];
+  for (int qz = 0; qz < N; ++qz)
+    for (int qy = 0; qy < N; ++qy)
+      for (int qx = 0; qx < N; ++qx) tb.W3[qx + N * (qy + N * qz)] = P::make(h.w[qx] * h.w[qy] * h.w[qz] * jac);
+  for (int d = 0; d < 3; ++d) {
+    tb.hinv[d] = P::make(1.0 / h.h[d]);
+    tb.area[d] = P::make(jac / h.h[d]);
+  }
+  return tb;
+}
+
+template <class P, int N>
 int launch_proj(const MeshDims& m, const double* u3, double* dst3, const double* td, const double* tc,
                 const ProjHost& h, cudaStream_t s) {
   constexpr int EPB = proj_cells_per_block<N>();
   const size_t smem = (size_t)EPB * 27 * N * N * N * sizeof(double);
-  if (smem > 232448) return 7;
-  if (cudaFuncSetAttribute(proj_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  if (smem > 232448 - 3 * N * N * sizeof(double)) return 7;
+  if (cudaFuncSetAttribute(proj_kernel<P, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
     return 2;
   if (m.E == 0) return 0;
   const long long blocks = (m.E + EPB - 1) / EPB;
-  proj_kernel<N><<<(unsigned)blocks, EPB * N * N, smem, s>>>(u3, dst3, td, tc, make_tab<N>(h), m);
+  proj_kernel<P, N><<<(unsigned)blocks, EPB * N * N, smem, s>>>(u3, dst3, td, tc, make_tabT<P, N>(h), m);
   return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }
 
@@ -280,16 +352,20 @@ int launch_speed(const MeshDims& m, const double* u3, double* td, double* tc, co
 }  // namespace
 
 int projection_apply(const MeshDims& m, const double* u3, double* dst3, const double* tau_d, const double* tau_c,
-                     const ProjHost& h, cudaStream_t s) {
+                     const ProjHost& h, cudaStream_t s, bool emulated) {
+#define DGNS_PROJ(NV) \
+  case NV:            \
+    return emulated ? launch_proj<DF64, NV>(m, u3, dst3, tau_d, tau_c, h, s) : launch_proj<F64, NV>(m, u3, dst3, tau_d, tau_c, h, s);
   switch (h.N) {
-    case 2: return launch_proj<2>(m, u3, dst3, tau_d, tau_c, h, s);
-    case 3: return launch_proj<3>(m, u3, dst3, tau_d, tau_c, h, s);
-    case 4: return launch_proj<4>(m, u3, dst3, tau_d, tau_c, h, s);
-    case 5: return launch_proj<5>(m, u3, dst3, tau_d, tau_c, h, s);
-    case 6: return launch_proj<6>(m, u3, dst3, tau_d, tau_c, h, s);
-    case 7: return launch_proj<7>(m, u3, dst3, tau_d, tau_c, h, s);
-    case 8: return launch_proj<8>(m, u3, dst3, tau_d, tau_c, h, s);
+    DGNS_PROJ(2)
+    DGNS_PROJ(3)
+    DGNS_PROJ(4)
+    DGNS_PROJ(5)
+    DGNS_PROJ(6)
+    DGNS_PROJ(7)
+    DGNS_PROJ(8)
   }
+#undef DGNS_PROJ
   return 7;
 }
 

@@ -97,8 +97,9 @@ struct ProjHost {
   double w[MAXN];
   double h[3];
 };
+// emulated: double-float arithmetic (else native FP64)
 int projection_apply(const MeshDims& m, const double* u3, double* dst3, const double* tau_d, const double* tau_c,
-                     const ProjHost& h, cudaStream_t s);
+                     const ProjHost& h, cudaStream_t s, bool emulated = false);
 // tau_d = fd * avg|u|, tau_c = fc * avg|u| per cell
 int penalty_parameters(const MeshDims& m, const double* u3, double* tau_d, double* tau_c, const ProjHost& h,
                        double fd, double fc, cudaStream_t s);

@@ -27,9 +27,11 @@ def test_penalty_parameters(n, k):
 
 
 @pytest.mark.parametrize("n,k", [((3, 2, 4), 3), ((2, 2, 2), 2), ((1, 2, 3), 4), ((2, 1, 2), 7),
-                                 ((4, 3, 2), 5)])
-def test_projection_operator(n, k):
-    ctx = context(n, k, mg_precision=0)
+                                 ((4, 3, 2), 5), ((2, 1, 1), 6)])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_projection_operator(n, k, mode):
+    """mode 0: native FP64; mode 1: double-float arithmetic."""
+    ctx = context(n, k, mg_precision=0, fp64_mode=mode)
     m = dg.Mesh(n)
     s = dg.Space(m, k)
     rng = np.random.default_rng(3)
@@ -40,9 +42,10 @@ def test_projection_operator(n, k):
     assert rel_err(host(y), dg.Projection(s, td, tc).apply(u)) <= 1e-12
 
 
-def test_projection_solve():
+@pytest.mark.parametrize("mode", [0, 1])
+def test_projection_solve(mode):
     n, k, dt = (4, 3, 4), 3, 1e-3
-    ctx = context(n, k, mg_precision=0)
+    ctx = context(n, k, mg_precision=0, fp64_mode=mode)
     m = dg.Mesh(n)
     s = dg.Space(m, k)
     u = tgv_field(s, 1e-3, 2)
