@@ -48,6 +48,12 @@ FP32_PEAK_TFLOPS = 80.6   # 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz (probe: 73
 # an emulated FMA (2 FP64 flops) is an exact product (FMUL + 3 FFMA) plus a
 # two-sum and two adds (8 FADD) = 15 FP32 flops.
 DF_FP32_PER_FP64 = 7.5
+# DRAM bytes (read + write) of one launch of the dominant kernel, from one ncu
+# capture of the same workload (profiles/convective_k3_32c_face_cell_ncu.md),
+# keyed by (kernel, fp64_mode); None where no capture of the current kernel
+# exists.
+KERNEL_TRAFFIC = {("conv_kernel", 1): 109.6e6, ("conv_kernel", 0): None,
+                  ("conv_face_kernel", 1): 60.0e6, ("conv_face_kernel", 0): None}
 
 
 # ----------------------------------------------------------- flop counts
@@ -250,7 +256,8 @@ def gpu_arm(args, rank, world):
         "per_operator_dofs_per_s": per_op, "time_share": share, "convective_kernels": conv_split,
         "roofline": {"kernel": kname, "bound": "alu", "achieved": round(achieved, 4),
                      "peak": peak, "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                     "traffic": None, "flops_per_launch": fl, "peak_source": psrc},
+                     "traffic": KERNEL_TRAFFIC.get((kbase, args.fp64_mode)), "flops_per_launch": fl,
+                     "peak_source": psrc},
         "e2e": {"value": round(world * dofs_per_step / (e2e * 1e-3), 1), "unit": "DoFs/s",
                 "h2d_bytes_per_step": 3 * nu_ * 8, "d2h_bytes_per_step": 3 * nu_ * 8},
         "gpu_launches": 7 * args.steps,  # face + cell convective, M^-1, D, L, G, H
@@ -265,6 +272,7 @@ def gpu_arm(args, rank, world):
     if not args.no_solve and rank == 0:
         line["poisson_solve"] = poisson_solve()
         line["bdf2_tgv"] = bdf2_timing()
+        line["tgv_time_loop"] = tgv_time_loop()
     return line
 
 
@@ -338,6 +346,21 @@ def bdf2_timing(steps=20):
             "forward_s": round(fwd, 4), "forward_ms_per_step": round(1e3 * fwd / steps, 3),
             "gradient_s": round(grad, 4), "eps_final": eps,
             "velocity_dofs": 3 * ctx.n_u, "pressure_dofs": ctx.n_p}
+
+
+def tgv_time_loop(steps=100):
+    """The paper's Taylor-Green time loop on 32^3 cells, k_u = 3 (effective
+    resolution 128^3): CFL time step (Cr = 0.125), penalty projection,
+    solver tolerances abs 1e-12 / rel 1e-6 with extrapolated initial guesses;
+    wall time of `steps` steps and the solver iteration counts of the last."""
+    from paper_1802_01439_gb300.tgv import simulate
+    meta, rec = simulate(32, 3, 1e9, every=steps, max_steps=steps)
+    return {"workload": "Taylor-Green, 32^3 cells, k_u=3, k_p=2, Re=1600, Cr=0.125, penalty projection, "
+                        "abs/rel tol 1e-12/1e-6, extrapolated guesses, %d steps" % steps,
+            "dt": meta["dt"], "wall_s": round(meta["wall_s"], 4),
+            "ms_per_step": round(1e3 * meta["wall_s"] / steps, 3), "dofs": meta["dofs"],
+            "dofs_steps_per_s": round(meta["dofs_steps_per_s"], 1),
+            "iterations_last_step": rec[-1]["iterations"], "e_k": rec[-1]["e_k"], "eps": rec[-1]["eps"]}
 
 
 def poisson_solve():

@@ -80,6 +80,14 @@ __device__ __forceinline__ int spos(int i) {
   return cell * cell_stride<N>() + (r % N) + padx<N>() * (r / N);
 }
 
+// Double-float lines from N = 5 on loop over their outputs instead of
+// unrolling them: the unrolled kernel no longer fits the instruction cache
+// (measured: 12-23 % faster for k = 4..7, 4-11 % slower for k = 2, 3).
+template <class A, int N>
+constexpr bool roll_outputs() {
+  return A::emulated && N >= 5;
+}
+
 // One line of T_d x for the own cell, with the neighbour terms.
 template <class A, int N, int D>
 __device__ __forceinline__ void sipg_line(const typename A::V* X, typename A::V* out,
@@ -99,20 +107,38 @@ __device__ __forceinline__ void sipg_line(const typename A::V* X, typename A::V*
     r[j] = A::load(nbR + gbase + j * gstride);
     lf[j] = A::load(nbL + gbase + j * gstride);
   }
+  if constexpr (roll_outputs<A, N>()) {
+#pragma unroll 1
+    for (int i = 0; i < N; ++i) {
+      Acc yi;
+      A::acc_first(yi, tb.cr[D][i], r[0]);
+      A::acc_fma(yi, tb.cl[D][i], lf[N - 1]);
 #pragma unroll
-  for (int i = 0; i < N; ++i) {
-    A::acc_first(y[i], tb.cr[D][i], r[0]);
-    A::acc_fma(y[i], tb.cl[D][i], lf[N - 1]);
+      for (int j = 0; j < N; ++j) A::acc_fma(yi, tb.A0[D][i * N + j], x[j]);
+      if (i == N - 1)
 #pragma unroll
-    for (int j = 0; j < N; ++j) A::acc_fma(y[i], tb.A0[D][i * N + j], x[j]);
+        for (int j = 0; j < N; ++j) A::acc_fma(yi, tb.gr[D][j], r[j]);
+      if (i == 0)
+#pragma unroll
+        for (int j = 0; j < N; ++j) A::acc_fma(yi, tb.gl[D][j], lf[j]);
+      out[base + i * stride] = A::acc_get(yi);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      A::acc_first(y[i], tb.cr[D][i], r[0]);
+      A::acc_fma(y[i], tb.cl[D][i], lf[N - 1]);
+#pragma unroll
+      for (int j = 0; j < N; ++j) A::acc_fma(y[i], tb.A0[D][i * N + j], x[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      A::acc_fma(y[N - 1], tb.gr[D][j], r[j]);
+      A::acc_fma(y[0], tb.gl[D][j], lf[j]);
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) out[base + i * stride] = A::acc_get(y[i]);
   }
-#pragma unroll
-  for (int j = 0; j < N; ++j) {
-    A::acc_fma(y[N - 1], tb.gr[D][j], r[j]);
-    A::acc_fma(y[0], tb.gl[D][j], lf[j]);
-  }
-#pragma unroll
-  for (int i = 0; i < N; ++i) out[base + i * stride] = A::acc_get(y[i]);
 }
 
 // Same, with the neighbour lines already in registers.
@@ -127,20 +153,38 @@ __device__ __forceinline__ void sipg_line_pre(const typename A::V* X, typename A
   V x[N];
   Acc y[N];
   load_line<V, N>(X, base, stride, x);
+  if constexpr (roll_outputs<A, N>()) {
+#pragma unroll 1
+    for (int i = 0; i < N; ++i) {
+      Acc yi;
+      A::acc_first(yi, tb.cr[D][i], r[0]);
+      A::acc_fma(yi, tb.cl[D][i], lf[N - 1]);
 #pragma unroll
-  for (int i = 0; i < N; ++i) {
-    A::acc_first(y[i], tb.cr[D][i], r[0]);
-    A::acc_fma(y[i], tb.cl[D][i], lf[N - 1]);
+      for (int j = 0; j < N; ++j) A::acc_fma(yi, tb.A0[D][i * N + j], x[j]);
+      if (i == N - 1)
 #pragma unroll
-    for (int j = 0; j < N; ++j) A::acc_fma(y[i], tb.A0[D][i * N + j], x[j]);
+        for (int j = 0; j < N; ++j) A::acc_fma(yi, tb.gr[D][j], r[j]);
+      if (i == 0)
+#pragma unroll
+        for (int j = 0; j < N; ++j) A::acc_fma(yi, tb.gl[D][j], lf[j]);
+      out[base + i * stride] = A::acc_get(yi);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      A::acc_first(y[i], tb.cr[D][i], r[0]);
+      A::acc_fma(y[i], tb.cl[D][i], lf[N - 1]);
+#pragma unroll
+      for (int j = 0; j < N; ++j) A::acc_fma(y[i], tb.A0[D][i * N + j], x[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      A::acc_fma(y[N - 1], tb.gr[D][j], r[j]);
+      A::acc_fma(y[0], tb.gl[D][j], lf[j]);
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) out[base + i * stride] = A::acc_get(y[i]);
   }
-#pragma unroll
-  for (int j = 0; j < N; ++j) {
-    A::acc_fma(y[N - 1], tb.gr[D][j], r[j]);
-    A::acc_fma(y[0], tb.gl[D][j], lf[j]);
-  }
-#pragma unroll
-  for (int i = 0; i < N; ++i) out[base + i * stride] = A::acc_get(y[i]);
 }
 
 template <class A, int N, int D>
@@ -175,20 +219,37 @@ __device__ __forceinline__ void mass_line(const typename A::V* in, const typenam
   V x[N];
   Acc y[N];
   load_line<V, N>(in, base, stride, x);
+  if constexpr (roll_outputs<A, N>()) {
+#pragma unroll 1
+    for (int i = 0; i < N; ++i) {
+      Acc yi;
+      if (ADD)
+        A::acc_set(yi, add[base + i * stride]);
 #pragma unroll
-  for (int i = 0; i < N; ++i) {
-    if (ADD)
-      A::acc_set(y[i], add[base + i * stride]);
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-      if (ADD || j > 0)
-        A::acc_fma(y[i], M[i * N + j], x[j]);
-      else
-        A::acc_first(y[i], M[i * N + j], x[j]);
+      for (int j = 0; j < N; ++j) {
+        if (ADD || j > 0)
+          A::acc_fma(yi, M[i * N + j], x[j]);
+        else
+          A::acc_first(yi, M[i * N + j], x[j]);
+      }
+      out[base + i * stride] = A::acc_get(yi);
     }
-  }
+  } else {
 #pragma unroll
-  for (int i = 0; i < N; ++i) out[base + i * stride] = A::acc_get(y[i]);
+    for (int i = 0; i < N; ++i) {
+      if (ADD)
+        A::acc_set(y[i], add[base + i * stride]);
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        if (ADD || j > 0)
+          A::acc_fma(y[i], M[i * N + j], x[j]);
+        else
+          A::acc_first(y[i], M[i * N + j], x[j]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) out[base + i * stride] = A::acc_get(y[i]);
+  }
 }
 
 // Copy of one x-line of a cell between global memory (contiguous) and the

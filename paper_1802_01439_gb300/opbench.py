@@ -114,8 +114,10 @@ def main():
     if a.sweep:
         for op in a.ops.split(","):
             for k, n in SWEEP_N.items():
-                if op == "convective" and k > 9:
-                    n = {10: 20, 11: 18}[k]
+                if op == "projection" and k > 7:
+                    print(json.dumps({"op": op, "k": k, "unsupported": "the projection operator exists for k <= 7"}),
+                          flush=True)
+                    continue
                 print(json.dumps(run(op, k, n, a.reps, a.warmup, fp64_mode=a.fp64_mode)), flush=True)
         return
     n = a.n or SWEEP_N.get(a.k, 32)
