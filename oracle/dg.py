@@ -374,6 +374,35 @@ class Convective:
         return Y
 
 
+    def magnitude(self, U):
+        """The sums of apply() over the absolute values of every factor and
+        term: |C(U)| <= magnitude(U) elementwise, and magnitude(U) times the
+        unit roundoff and the length of the summation chains bounds the
+        rounding error of any evaluation order (a running error bound in the
+        sense of Higham, Accuracy and Stability of Numerical Algorithms,
+        Sec. 3.3).  The weak form nearly cancels for smooth fields, so this
+        is the scale against which two evaluations can be compared."""
+        m = self.space.mesh
+        A = np.abs(np.asarray(U, dtype=np.float64))
+        aPhi, adPhi = np.abs(self.Phi), [np.abs(t) for t in self.dPhi]
+        uq = np.stack([A[c] @ aPhi.T for c in range(3)])
+        Y = np.zeros_like(A)
+        for c in range(3):
+            for d in range(3):
+                Y[c] += (uq[c] * uq[d] * self.W[None, :]) @ adPhi[d]
+        em = np.arange(m.E)
+        for axis in range(3):
+            vm, vp, wf = self.face[axis]
+            ep = m.neighbor(axis, +1)
+            um = np.stack([A[c][em] @ np.abs(vm).T for c in range(3)])
+            up = np.stack([A[c][ep] @ np.abs(vp).T for c in range(3)])
+            lam = np.maximum(um[axis], up[axis])
+            for c in range(3):
+                Fs = (0.5 * (um[c] * um[axis] + up[c] * up[axis]) + lam * (um[c] + up[c])) * wf[None, :]
+                Y[c][em] += Fs @ np.abs(vm)
+                Y[c][ep] += Fs @ np.abs(vp)
+        return Y
+
     def vjp(self, U, Wt):
         """Vector-Jacobian product (dC/dU)^T Wt, written out pointwise.
 

@@ -398,3 +398,47 @@ def test_projection_penalty_energies():
     ey = m.neighbor(1, +1)
     ref = np.sum(0.5 * (tc + tc[ey]) * (cval - cval[ey]) ** 2) * m.h[0] * m.h[2]
     assert abs(e - ref) < 1e-12 * abs(ref)
+
+
+def test_patch_centre_equals_full_mesh_output():
+    """The basis of the full-size sampled parity tests: on the uniform periodic
+    mesh every operator couples a cell only to its face neighbours and is
+    translation invariant, so a cell's output equals the output of the centre
+    cell of a 3x3x3 periodic patch (same cell size) holding it and its
+    neighbours."""
+    from paper_1802_01439_gb300 import inputs
+    from tests.test_gpu_fullsize import CENTRE, _patch, _patch_space
+    n, ku, kp = 4, 3, 2
+    m = dg.Mesh(n)
+    su, sp = dg.Space(m, ku), dg.Space(m, kp)
+    psu, psp = _patch_space(n, ku), _patch_space(n, kp)
+    U = inputs.uniform(3, 3 * su.size).reshape(3, m.E, -1)
+    P = inputs.uniform(4, sp.size).reshape(1, m.E, -1)
+    full = {"conv": dg.Convective(su).apply(U), "div": dg.Divergence(su, sp).apply(U)[None],
+            "lap": dg.Laplace(sp).apply(P[0])[None], "grad": dg.Gradient(su, sp).apply(P[0]),
+            "helm": dg.Helmholtz(su, 1 / 1600, 1500.0).apply(U[0])[None]}
+    for e in (0, 21, m.E - 1):
+        patch = {"conv": dg.Convective(psu).apply(_patch(U, n, e))[:, CENTRE],
+                 "div": dg.Divergence(psu, psp).apply(_patch(U, n, e))[None, CENTRE],
+                 "lap": dg.Laplace(psp).apply(_patch(P, n, e)[0])[None, CENTRE],
+                 "grad": dg.Gradient(psu, psp).apply(_patch(P, n, e)[0])[:, CENTRE],
+                 "helm": dg.Helmholtz(psu, 1 / 1600, 1500.0).apply(_patch(U, n, e)[0])[None, CENTRE]}
+        for k in full:
+            assert np.max(np.abs(full[k][:, e] - patch[k])) <= 1e-13 * np.max(np.abs(full[k])), (k, e)
+
+
+def test_convective_magnitude_bounds_the_result():
+    """magnitude(U) bounds |C(U)| elementwise (triangle inequality), is
+    positive, scales quadratically, and exceeds |C(U)| clearly for a smooth
+    field, whose weak-form sums cancel."""
+    m = dg.Mesh((2, 3, 2))
+    s = dg.Space(m, 3)
+    C = dg.Convective(s)
+    U = np.random.default_rng(5).uniform(-1, 1, (3, m.E, s.ndofs_cell))
+    y, mag = C.apply(U), C.magnitude(U)
+    assert np.all(np.abs(y) <= mag * (1 + 1e-12) + 1e-300)
+    assert np.allclose(C.magnitude(2.0 * U), 4.0 * mag, rtol=1e-14, atol=0)
+    assert np.all(mag > 0)
+    # a smooth field: the weak form cancels, the magnitude does not
+    ut = np.stack(s.interpolate(dg.taylor_green))
+    assert np.max(np.abs(C.apply(ut))) < 0.5 * np.max(C.magnitude(ut))
