@@ -156,16 +156,22 @@ struct DF64 {
   // The value of an accumulator as hi + lo without renormalisation: lo holds
   // the collected rounding errors, small against the terms but not
   // necessarily below half an ulp of hi.  Products and sums take such values
-  // as they are; acc_get_norm renormalises where a value is compared.
+  // as they are; acc_get_norm renormalises (for values that are compared,
+  // and in the convective kernels, whose cancelling sums need the accuracy).
   __device__ __forceinline__ static V acc_get(const Acc& a) {
     V r;
     r.hi = a.s;
     r.lo = a.e;
     return r;
   }
+  // Renormalisation by Dekker's Fast2Sum, exact when |e| <= |s| up to the
+  // exponent (the error sum is far smaller than the running sum unless the
+  // sum cancels to its own rounding level); measured identical to the
+  // branch-free two-sum on the full-size convective parity cases.
   __device__ __forceinline__ static V acc_get_norm(const Acc& a) {
     V r;
-    two_sum(a.s, a.e, r.hi, r.lo);
+    r.hi = __fadd_rn(a.s, a.e);
+    r.lo = __fsub_rn(a.e, __fsub_rn(r.hi, a.s));
     return r;
   }
   __device__ __forceinline__ static V add(V a, V b) {
