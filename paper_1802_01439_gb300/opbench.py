@@ -24,7 +24,7 @@ from paper_1802_01439_gb300 import Context, inputs  # noqa: E402
 # elements per direction giving ~16.8M scalar DoFs for k = 2..11
 SWEEP_N = {2: 85, 3: 64, 4: 51, 5: 43, 6: 37, 7: 32, 8: 28, 9: 26, 10: 23, 11: 21}
 OPS = ["laplace", "laplace32", "convective", "viscous", "helmholtz", "invmass", "mass",
-       "divergence", "gradient", "projection"]
+       "divergence", "gradient", "projection", "helmholtz_split"]
 
 
 def run(op, k, n, reps, warmup, ku=None, fp64_mode=0):
@@ -54,6 +54,17 @@ def run(op, k, n, reps, warmup, ku=None, fp64_mode=0):
                                                  noise=1e-3, seed=0).ravel()).to(dev)
         y, dofs = torch.empty(3 * nu, **f64), 3 * nu
         fn = lambda: ctx.vmult_convective(y, u)
+        nbytes = 16 * 3 * nu
+    elif op == "helmholtz_split":
+        # the operator-by-operator Helmholtz operator: mass, viscous, then
+        # y = 1500 M x + V x in a vector update (against the fused kernel)
+        x, y, dofs = rng(3 * nu, 0), torch.empty(3 * nu, **f64), 3 * nu
+        y1 = torch.empty(3 * nu, **f64)
+
+        def fn():
+            ctx.vmult_mass(y1, x, 3, 0)
+            ctx.vmult_viscous(y, x)
+            ctx.axpby(y, y1, 1500.0, 1.0)
         nbytes = 16 * 3 * nu
     elif op in ("viscous", "helmholtz"):
         x, y, dofs = rng(3 * nu, 0), torch.empty(3 * nu, **f64), 3 * nu
@@ -100,9 +111,38 @@ def run(op, k, n, reps, warmup, ku=None, fp64_mode=0):
             "algorithmic_GBps": round(nbytes / (ms * 1e-3) / 1e9, 1)}
 
 
+def poisson(n, kp, reps, mg_precision=32, fp64_mode=1):
+    """Wall time of the pressure Poisson solve to rel. res. 1e-10 (zero initial
+    guess): b = D u_TG (k_u = k_p + 1) + 1e-3 noise, zero mean."""
+    import time
+    cu = Context(n, kp + 1, kp, mg_precision=0)
+    u = torch.from_numpy(inputs.taylor_green((n,) * 3, (-np.pi,) * 3, (np.pi,) * 3, cu.nodes_1d(0)).ravel()).cuda()
+    b = torch.empty(cu.n_p, dtype=torch.float64, device="cuda")
+    cu.vmult_divergence(b, u)
+    del u
+    cu.close()
+    b += 1e-3 * torch.from_numpy(inputs.uniform(1, b.numel())).cuda()
+    b -= b.mean()
+    ctx = Context(n, kp + 1, kp, mg_precision=mg_precision, fp64_mode=fp64_mode)
+    x = torch.zeros_like(b)
+    ctx.cg_mg_solve(x, b, rel_tol=1e-10)
+    ts = []
+    for _ in range(reps):
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = ctx.cg_mg_solve(x, b, rel_tol=1e-10)
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    ctx.close()
+    return {"op": "poisson", "n_elem": n, "k_p": kp, "mg_precision": mg_precision, "fp64_mode": fp64_mode,
+            "dofs": int(b.numel()), "seconds_min": round(min(ts), 5), "iterations": info["iterations"],
+            "rel_res": info["rel_res"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", default="laplace", choices=OPS)
+    ap.add_argument("--op", default="laplace", choices=OPS + ["poisson"])
     ap.add_argument("--k", type=int, default=3)
     ap.add_argument("--n", type=int, default=0)
     ap.add_argument("--reps", type=int, default=20)
@@ -119,6 +159,9 @@ def main():
                           flush=True)
                     continue
                 print(json.dumps(run(op, k, n, a.reps, a.warmup, fp64_mode=a.fp64_mode)), flush=True)
+        return
+    if a.op == "poisson":
+        print(json.dumps(poisson(a.n or 64, a.k, a.reps, 32 if a.fp64_mode == 1 else 64, a.fp64_mode)), flush=True)
         return
     n = a.n or SWEEP_N.get(a.k, 32)
     print(json.dumps(run(a.op, a.k, n, a.reps, a.warmup, fp64_mode=a.fp64_mode)), flush=True)

@@ -79,3 +79,37 @@ def test_null_context_is_rejected(lib):
     from paper_1802_01439_gb300 import _lib
     assert lib.dgns_vmult_laplace(None, None, None, 0) == _lib.DGNS_ERR_INVALID_ARG
     assert lib.dgns_cg_mg_solve(None, None, None, None, None) == _lib.DGNS_ERR_INVALID_ARG
+
+
+def test_create_rejects_oversized_mesh(lib):
+    """3 x cells >= 2^31 exceeds the 32-bit cell indexing of the kernels: the
+    description is rejected (unsupported) before any allocation."""
+    from paper_1802_01439_gb300 import _lib
+    d = _lib.MeshDesc()
+    lib.dgns_default_desc(ctypes.byref(d))
+    d.n_elem[0] = d.n_elem[1] = d.n_elem[2] = 900     # 7.29e8 cells, 3 x = 2.19e9
+    h = ctypes.c_void_p()
+    assert lib.dgns_create(ctypes.byref(d), None, ctypes.byref(h)) == _lib.DGNS_ERR_UNSUPPORTED
+    assert h.value is None and b"2^31" in lib.dgns_last_error()
+
+
+def test_null_arguments_of_new_entry_points(lib):
+    from paper_1802_01439_gb300 import _lib
+    E = _lib.DGNS_ERR_INVALID_ARG
+    n = ctypes.c_longlong()
+    assert lib.dgns_convective_face_size(None, ctypes.byref(n)) == E
+    assert lib.dgns_convective_faces(None, None, None) == E
+    assert lib.dgns_convective_cells(None, None, None, None) == E
+    assert lib.dgns_vmult_projection(None, None, None, None, None) == E
+    assert lib.dgns_cg_projection_solve(None, None, None, None, None, None, None) == E
+    assert lib.dgns_penalty_parameters(None, None, 1.0, 1.0, 1.0, None, None) == E
+
+
+def test_solve_params_layout(lib):
+    """The binding's SolveParams mirrors the header (the default fills every
+    field, the initial-guess switch included)."""
+    from paper_1802_01439_gb300 import _lib
+    p = _lib.SolveParams()
+    p.use_initial_guess = 7
+    lib.dgns_default_solve_params(ctypes.byref(p))
+    assert p.use_initial_guess == 0 and p.project_mean == 1 and p.abs_tol == 0.0
