@@ -212,3 +212,26 @@ def test_misaligned_vector_rejected():
     y = torch.empty(ctx.n_u, dtype=torch.float64, device="cuda")
     with pytest.raises(DgnsError):
         ctx.vmult_laplace(y, buf[1:], space=0)
+
+
+def test_pinned_host_pointers():
+    """Pinned host tensors (staged like any host memory) give the device-tensor
+    results, also through the two-phase convective entry points."""
+    n, k = (3, 2, 2), 3
+    ctx = context(n, k, k - 1, mg_precision=0, fp64_mode=1)
+    s = dg.Space(dg.Mesh(n), k)
+    u = torch.from_numpy(tgv_field(s, 1e-2, 2).ravel().copy())
+    up = u.pin_memory()
+    yp = torch.empty(u.numel(), dtype=torch.float64).pin_memory()
+    yd = torch.empty(u.numel(), dtype=torch.float64, device="cuda")
+    ctx.vmult_convective(yp, up)
+    ctx.vmult_convective(yd, u.cuda())
+    assert np.array_equal(yp.numpy(), host(yd))
+    ctx.vmult_helmholtz(yp, up, 1500.0)
+    ctx.vmult_helmholtz(yd, u.cuda(), 1500.0)
+    assert np.array_equal(yp.numpy(), host(yd))
+    rf = torch.empty(ctx.convective_face_size(), dtype=torch.float64).pin_memory()
+    ctx.convective_faces(rf, up)
+    ctx.convective_cells(yp, up, rf)
+    ctx.vmult_convective(yd, u.cuda())
+    assert np.array_equal(yp.numpy(), host(yd))
