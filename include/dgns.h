@@ -16,8 +16,11 @@
  * torch CUDA tensor) or a host pointer (pinned or pageable).  With device
  * pointers the call is enqueued on the context's stream and returns at once.
  * With host pointers the library stages the data through its own device
- * buffers (allocated at the first such call), runs the same kernels, copies
- * the results back and synchronises the stream before returning.
+ * buffers (allocated at the first such call) and runs the same kernels; a
+ * call with a host output copies the result back and returns when it is
+ * complete; a call whose only host vectors are inputs returns once they are
+ * copied (the caller may then reuse them) while its kernels run on in stream
+ * order.
  * The caller owns every vector; the library owns its tables, multigrid levels
  * and scratch.  dst must not alias any source (DGNS_ERR_ALIAS).  Device
  * vectors must be 16-byte aligned (cudaMalloc and torch allocations are; a

@@ -133,6 +133,7 @@ bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
 struct Staged {
   dgns_ctx* c;
   bool any_host = false;
+  bool in_copied = false;
   struct Out {
     void* host;
     void* dev;
@@ -150,6 +151,9 @@ struct Staged {
     int rc = grab(bytes, &buf);
     if (rc) return rc;
     DG_CUDA(cudaMemcpyAsync(buf, p, bytes, cudaMemcpyHostToDevice, c->s));
+    if (!c->stage_ev) DG_CUDA(cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming));
+    DG_CUDA(cudaEventRecord(c->stage_ev, c->s));
+    in_copied = true;
     *dev = buf;
     any_host = true;
     return 0;
@@ -195,9 +199,16 @@ struct Staged {
     *buf = c->stage[slot++];
     return 0;
   }
+  // Host outputs: copied back, complete when the call returns.  Host inputs
+  // only: the call returns once they are copied (the caller may reuse them);
+  // the kernels run on, stream-ordered before any later use of the staging
+  // buffers.
   int finish() {
     for (auto& o : outs) DG_CUDA(cudaMemcpyAsync(o.host, o.dev, o.bytes, cudaMemcpyDeviceToHost, c->s));
-    if (any_host) DG_CUDA(cudaStreamSynchronize(c->s));
+    if (!outs.empty())
+      DG_CUDA(cudaStreamSynchronize(c->s));
+    else if (in_copied)
+      DG_CUDA(cudaEventSynchronize(c->stage_ev));
     return 0;
   }
 };
@@ -394,6 +405,7 @@ void free_ctx(dgns_ctx* c) {
   cudaFree(c->red.scal);
   if (c->h_scal) cudaFreeHost(c->h_scal);
   for (int i = 0; i < 4; ++i) cudaFree(c->stage[i]);
+  if (c->stage_ev) cudaEventDestroy(c->stage_ev);
   if (c->vc_exec) cudaGraphExecDestroy(c->vc_exec);
   if (c->gs) cudaStreamDestroy(c->gs);
   delete c;

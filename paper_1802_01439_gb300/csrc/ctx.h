@@ -74,5 +74,6 @@ struct dgns_ctx {
   double vc_range = 0.0;
   // staging of host pointers
   void* stage[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t stage_ev = nullptr;  // recorded after the staging copies of host inputs
   size_t stage_cap[4] = {0, 0, 0, 0};
 };
