@@ -165,6 +165,17 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Barrier of the threads of one cell or face: a warp barrier when they are
+// exactly one warp, else a block barrier (then the block holds whole groups
+// and every thread reaches it).
+template <int NT>
+__device__ __forceinline__ void group_sync() {
+  if (NT == 32)
+    __syncwarp();
+  else
+    __syncthreads();
+}
+
 // Dynamic shared memory, aligned for double2 accesses.
 __device__ __forceinline__ unsigned char* dyn_smem() {
   extern __shared__ __align__(16) unsigned char dgns_smem[];

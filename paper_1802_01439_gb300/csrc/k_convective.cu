@@ -96,16 +96,6 @@ struct FaceLayout {
   static constexpr int PER = T0 + G1 + G2;
 };
 
-// Barrier of the threads of one cell or face: a warp barrier when they are
-// exactly one warp, else a block barrier (then the block holds whole groups
-// and every thread reaches it).
-template <int NT>
-__device__ __forceinline__ void group_sync() {
-  if (NT == 32)
-    __syncwarp();
-  else
-    __syncthreads();
-}
 
 __device__ __forceinline__ int node3(int N, int d, int a, int t1, int j1, int t2, int j2) {
   int c[3];

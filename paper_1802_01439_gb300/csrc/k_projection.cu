@@ -2,14 +2,14 @@
 // continuity penalty terms (Sec. 3.2 and the matrix form of the projection
 // step, Sec. 3.3, of arXiv:1802.01439), and the element-wise penalty
 // parameters from the volume-averaged norm of the extrapolated velocity.
-// FP64, k <= 7.
+// FP64 or double-float arithmetic, k <= 7.
 //
 // Per cell (affine, Gauss rule with k+1 points, exact for both forms):
 //   values  V_a = (S (x) S (x) S) u_a,   reference derivatives
 //   G_x = (D (x) S (x) S) u_x, G_y = (S (x) D (x) S) u_y, G_z = (S (x) S (x) D) u_z
 //   at every point: m_a = w V_a, g = tau_D w sum_a G_a / h_a  (w = quadrature
 //   weight times h_x h_y h_z); test: y_b = (S^T)^3 m_b + (1/h_b) (D_b^T ...) g,
-//   each component as one combined sweep along b followed by two S^T sweeps.
+//   arranged in phases of sweeps along one direction each (proj_kernel).
 // Faces normal to a couple only component a: with LGL nodes the traces are
 // the nodal values of the face layers and the Gauss rule integrates the face
 // mass exactly, so the own face layer gets
@@ -32,9 +32,7 @@ struct ProjTab {
 // Tables of the operator kernel in the arithmetic policy's value type.
 template <class V, int N>
 struct ProjTabT {
-  static constexpr bool kMM = N <= 6;   // the N^4 face-mass table fits the parameter space
   V S[N * N], D[N * N], M[N * N];
-  V MM[kMM ? N * N * N * N : 1];   // (M (x) M)[(j1 + N j2)][(i1 + N i2)] = M[j1][i1] M[j2][i2]
   V W3[N * N * N];       // w_qx w_qy w_qz h_x h_y h_z
   V hinv[3];             // 1 / h_d
   V area[3];             // face area of faces normal to d
@@ -96,142 +94,198 @@ __device__ __forceinline__ void psweep(const typename P::V* in, const typename P
   }
 }
 
+// Threads per cell of the operator kernel: one warp up to N = 5, then more
+// as a sweep's N^2 lines grow; cells per block fill 128 threads.
+template <int N>
+constexpr int proj_threads() {
+  return N <= 5 ? 32 : (N == 6 ? 64 : 128);
+}
+template <int N>
+constexpr int proj_op_cells_per_block() {
+  return proj_threads<N>() >= 128 ? 1 : 128 / proj_threads<N>();
+}
+// Work space per cell: two regions of 5 and 6 N^3 values, used in turn by the
+// phases (u -> x-sweeps -> y-sweeps -> z-sweeps -> tests along x, y, z).
+template <int N>
+constexpr int proj_per_cell() {
+  return 11 * N * N * N;
+}
+
+// Operator kernel.  Every phase is a set of line sweeps along one direction;
+// its work items are (sweep, line) pairs spread over the cell's threads.
+//   forward x: X = (S u_x, D u_x, S u_y, S u_z)                 R1 -> R2
+//   forward y: Y = (S X0, S X1, S X2, D X2, S X3)               R2 -> R1
+//   forward z: V_x V_y V_z = S (Y0, Y2, Y4), G_x G_y G_z =
+//              S Y1, S Y3, D Y4                                  R1 -> R2
+//   points:    m_b = W V_b, g = tau_D W sum_a G_a / h_a          in R2
+//   test x:    A = (S^T m_x + (D/h_x)^T g, S^T m_y, S^T m_z, S^T g)       R2 -> R1
+//   test y:    B = (S^T A0, S^T A1 + (D/h_y)^T A3, S^T A2, S^T A3)        R1 -> R2
+//   test z:    O = (S^T B0, S^T B1, S^T B2 + (D/h_z)^T B3)                 R2 -> R1
+// then the continuity penalty on the face layers of O and the store.
 template <class P, int N>
-__global__ void __launch_bounds__(proj_cells_per_block<N>() * N * N)
+__global__ void __launch_bounds__(proj_op_cells_per_block<N>() * proj_threads<N>())
     proj_kernel(const double* __restrict__ u3, double* __restrict__ dst3, const double* __restrict__ tau_d,
                 const double* __restrict__ tau_c, const __grid_constant__ ProjTabT<typename P::V, N> tb,
                 const MeshDims m) {
   typedef typename P::V V;
   typedef typename P::Acc Acc;
-  constexpr int NT = N * N, N3 = N * N * N, EPB = proj_cells_per_block<N>();
-  constexpr int PER = 27 * N3;
+  constexpr int NT = proj_threads<N>(), NN = N * N, N3 = N * N * N, EPB = proj_op_cells_per_block<N>();
   V* sm = reinterpret_cast<V*>(dyn_smem());
   const int slot = threadIdx.x / NT;
-  const int l = threadIdx.x - slot * NT;
+  const int t = threadIdx.x - slot * NT;
   const long long c0 = (long long)blockIdx.x * EPB;
   const long long rem = m.E - c0;
   const int nvalid = rem < EPB ? (int)rem : EPB;
   const bool active = slot < nvalid;
-  V* U = sm + slot * PER;   // 3 N3
-  V* X = U + 3 * N3;        // 4 N3: S u_x, D u_x, S u_y, S u_z (x sweeps)
-  V* Y = X + 4 * N3;        // 5 N3
-  V* Z = Y + 5 * N3;        // 6 N3: V_x V_y V_z G_x G_y G_z -> m_x m_y m_z g
-  V* T1 = Z + 6 * N3;       // 3 N3
-  V* T2 = T1 + 3 * N3;      // 3 N3
-  V* O = T2 + 3 * N3;       // 3 N3
-  // D^T / h_d tables of the three combined test sweeps
-  __shared__ V sDh[3][N * N];
-  for (int i = threadIdx.x; i < 3 * N * N; i += blockDim.x)
-    sDh[i / (N * N)][i % (N * N)] = P::mul(tb.D[i % (N * N)], tb.hinv[i / (N * N)]);
+  // tables: S, D, D/h_x, D/h_y, D/h_z, M
+  V* sS = sm + EPB * proj_per_cell<N>();
+  V* sD = sS + NN;
+  V* sDh = sD + NN;
+  V* sM = sDh + 3 * NN;
+  for (int i = threadIdx.x; i < NN; i += blockDim.x) {
+    sS[i] = tb.S[i];
+    sD[i] = tb.D[i];
+    sM[i] = tb.M[i];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) sDh[d * NN + i] = P::mul(tb.D[i], tb.hinv[d]);
+  }
+  V* R1 = sm + slot * proj_per_cell<N>();   // 5 N^3
+  V* R2 = R1 + 5 * N3;                      // 6 N^3
   CellXYZ cx{};
   if (active) {
     cx = cell_xyz((unsigned)(c0 + slot), m);
-    for (int c = 0; c < 3; ++c)
-      for (int i = l; i < N3; i += NT) U[c * N3 + i] = P::load(u3 + ((size_t)c * m.E + cx.el) * N3 + i);
+    for (int i = t; i < 3 * N3; i += NT) {
+      const int c = i / N3, r = i - c * N3;
+      R1[i] = P::load(u3 + ((size_t)c * m.E + cx.el) * N3 + r);
+    }
   }
   __syncthreads();
-  if (active) {
-    psweep<P, N, 0, false, false>(U, nullptr, X, l, tb.S, nullptr);
-    psweep<P, N, 0, false, false>(U, nullptr, X + N3, l, tb.D, nullptr);
-    psweep<P, N, 0, false, false>(U + N3, nullptr, X + 2 * N3, l, tb.S, nullptr);
-    psweep<P, N, 0, false, false>(U + 2 * N3, nullptr, X + 3 * N3, l, tb.S, nullptr);
-  }
-  __syncthreads();
-  if (active) {
-    psweep<P, N, 1, false, false>(X, nullptr, Y, l, tb.S, nullptr);                  // SS u_x
-    psweep<P, N, 1, false, false>(X + N3, nullptr, Y + N3, l, tb.S, nullptr);        // DS u_x
-    psweep<P, N, 1, false, false>(X + 2 * N3, nullptr, Y + 2 * N3, l, tb.S, nullptr);  // SS u_y
-    psweep<P, N, 1, false, false>(X + 2 * N3, nullptr, Y + 3 * N3, l, tb.D, nullptr);  // SD u_y
-    psweep<P, N, 1, false, false>(X + 3 * N3, nullptr, Y + 4 * N3, l, tb.S, nullptr);  // SS u_z
-  }
-  __syncthreads();
-  if (active) {
-    psweep<P, N, 2, false, false>(Y, nullptr, Z, l, tb.S, nullptr);                  // V_x
-    psweep<P, N, 2, false, false>(Y + 2 * N3, nullptr, Z + N3, l, tb.S, nullptr);    // V_y
-    psweep<P, N, 2, false, false>(Y + 4 * N3, nullptr, Z + 2 * N3, l, tb.S, nullptr);  // V_z
-    psweep<P, N, 2, false, false>(Y + N3, nullptr, Z + 3 * N3, l, tb.S, nullptr);      // G_x
-    psweep<P, N, 2, false, false>(Y + 3 * N3, nullptr, Z + 4 * N3, l, tb.S, nullptr);  // G_y
-    psweep<P, N, 2, false, false>(Y + 4 * N3, nullptr, Z + 5 * N3, l, tb.D, nullptr);  // G_z
-  }
-  __syncthreads();
-  if (active) {
+  if (active)   // forward x
+    for (int it = t; it < 4 * NN; it += NT) {
+      const int s = it / NN, l = it - s * NN;
+      const V* in = R1 + (s == 0 ? 0 : (s - 1) * N3);
+      psweep<P, N, 0, false, false>(in, nullptr, R2 + s * N3, l, s == 1 ? sD : sS, nullptr);
+    }
+  group_sync<NT>();
+  if (active)   // forward y
+    for (int it = t; it < 5 * NN; it += NT) {
+      const int s = it / NN, l = it - s * NN;
+      const V* in = R2 + (s < 3 ? s : s - 1) * N3;
+      psweep<P, N, 1, false, false>(in, nullptr, R1 + s * N3, l, s == 3 ? sD : sS, nullptr);
+    }
+  group_sync<NT>();
+  if (active)   // forward z
+    for (int it = t; it < 6 * NN; it += NT) {
+      const int s = it / NN, l = it - s * NN;
+      const int src = s == 0 ? 0 : s == 1 ? 2 : s == 2 ? 4 : s == 3 ? 1 : s == 4 ? 3 : 4;
+      psweep<P, N, 2, false, false>(R1 + src * N3, nullptr, R2 + s * N3, l, s == 5 ? sD : sS, nullptr);
+    }
+  group_sync<NT>();
+  if (active) {   // quadrature points
     const V td = P::load(tau_d + cx.el);
-    for (int i = l; i < N3; i += NT) {
+    for (int i = t; i < N3; i += NT) {
       const V w = tb.W3[i];
       Acc dv;
-      P::acc_first(dv, tb.hinv[0], Z[3 * N3 + i]);
-      P::acc_fma(dv, tb.hinv[1], Z[4 * N3 + i]);
-      P::acc_fma(dv, tb.hinv[2], Z[5 * N3 + i]);
-      Z[i] = P::mul(w, Z[i]);
-      Z[N3 + i] = P::mul(w, Z[N3 + i]);
-      Z[2 * N3 + i] = P::mul(w, Z[2 * N3 + i]);
-      Z[3 * N3 + i] = P::mul(P::mul(td, w), P::acc_get(dv));
+      P::acc_first(dv, tb.hinv[0], R2[3 * N3 + i]);
+      P::acc_fma(dv, tb.hinv[1], R2[4 * N3 + i]);
+      P::acc_fma(dv, tb.hinv[2], R2[5 * N3 + i]);
+      R2[i] = P::mul(w, R2[i]);
+      R2[N3 + i] = P::mul(w, R2[N3 + i]);
+      R2[2 * N3 + i] = P::mul(w, R2[2 * N3 + i]);
+      R2[3 * N3 + i] = P::mul(P::mul(td, w), P::acc_get(dv));
     }
   }
-  __syncthreads();
-  // tests: b = x: (S^T m_x + (D/h_x)^T g) along x, then S^T y, S^T z
-  //        b = y: along y first, then x, z;  b = z: along z first, then x, y
-  if (active) {
-    psweep<P, N, 0, true, true>(Z, Z + 3 * N3, T1, l, tb.S, sDh[0]);
-    psweep<P, N, 1, true, true>(Z + N3, Z + 3 * N3, T1 + N3, l, tb.S, sDh[1]);
-    psweep<P, N, 2, true, true>(Z + 2 * N3, Z + 3 * N3, T1 + 2 * N3, l, tb.S, sDh[2]);
-  }
-  __syncthreads();
-  if (active) {
-    psweep<P, N, 1, true, false>(T1, nullptr, T2, l, tb.S, nullptr);
-    psweep<P, N, 0, true, false>(T1 + N3, nullptr, T2 + N3, l, tb.S, nullptr);
-    psweep<P, N, 0, true, false>(T1 + 2 * N3, nullptr, T2 + 2 * N3, l, tb.S, nullptr);
-  }
-  __syncthreads();
-  if (active) {
-    psweep<P, N, 2, true, false>(T2, nullptr, O, l, tb.S, nullptr);
-    psweep<P, N, 2, true, false>(T2 + N3, nullptr, O + N3, l, tb.S, nullptr);
-    psweep<P, N, 1, true, false>(T2 + 2 * N3, nullptr, O + 2 * N3, l, tb.S, nullptr);
-  }
-  __syncthreads();
-  // continuity penalty: faces normal to a, component a
-  if (active) {
-    const V half_tc = P::half(P::load(tau_c + cx.el));
-    for (int a = 0; a < 3; ++a) {
-      // node strides along a and the two tangential directions t1 < t2
-      const int sa = a == 0 ? 1 : (a == 1 ? N : N * N);
-      const int s1 = a == 0 ? N : 1, s2 = a == 2 ? N : N * N;
-      for (int side = 1; side >= -1; side -= 2) {
-        const unsigned nb = a == 0 ? neighbor32<0>(cx, side, m) : (a == 1 ? neighbor32<1>(cx, side, m)
-                                                                          : neighbor32<2>(cx, side, m));
-        // {{tau_C}} |F| (the halving is exact)
-        const V tbar = P::mul(P::add(half_tc, P::half(P::load(tau_c + nb))), tb.area[a]);
-        const int aown = side > 0 ? N - 1 : 0, anb = side > 0 ? 0 : N - 1;
-        // thread l handles face node (j1, j2) = (l % N, l / N): (M (x) M) jump
-        const int j1 = l % N, j2 = l / N;
-        const double* ua = u3 + ((size_t)a * m.E) * N3;
-        Acc acc;
-#pragma unroll
-        for (int i2 = 0; i2 < N; ++i2) {
-#pragma unroll
-          for (int i1 = 0; i1 < N; ++i1) {
-            const int io = aown * sa + i1 * s1 + i2 * s2, in_ = anb * sa + i1 * s1 + i2 * s2;
-            const V jump = P::sub(U[a * N3 + io], P::load(ua + (size_t)nb * N3 + in_));
-            const V mm = ProjTabT<V, N>::kMM ? tb.MM[(j1 + N * j2) * N * N + i1 + N * i2]
-                                             : P::mul(tb.M[j1 * N + i1], tb.M[j2 * N + i2]);
-            if (i1 == 0 && i2 == 0)
-              P::acc_first(acc, mm, jump);
-            else
-              P::acc_fma(acc, mm, jump);
-          }
-        }
-        const int io = aown * sa + j1 * s1 + j2 * s2;
-        Acc o;
-        P::acc_set(o, O[a * N3 + io]);
-        P::acc_fma(o, tbar, P::acc_get(acc));
-        O[a * N3 + io] = P::acc_get(o);
-      }
+  group_sync<NT>();
+  if (active)   // test x
+    for (int it = t; it < 4 * NN; it += NT) {
+      const int s = it / NN, l = it - s * NN;
+      if (s == 0)
+        psweep<P, N, 0, true, true>(R2, R2 + 3 * N3, R1, l, sS, sDh);
+      else
+        psweep<P, N, 0, true, false>(R2 + (s == 3 ? 3 : s) * N3, nullptr, R1 + s * N3, l, sS, nullptr);
     }
-  }
-  __syncthreads();
+  group_sync<NT>();
+  if (active)   // test y
+    for (int it = t; it < 4 * NN; it += NT) {
+      const int s = it / NN, l = it - s * NN;
+      if (s == 1)
+        psweep<P, N, 1, true, true>(R1 + N3, R1 + 3 * N3, R2 + N3, l, sS, sDh + NN);
+      else
+        psweep<P, N, 1, true, false>(R1 + s * N3, nullptr, R2 + s * N3, l, sS, nullptr);
+    }
+  group_sync<NT>();
+  if (active)   // test z
+    for (int it = t; it < 3 * NN; it += NT) {
+      const int s = it / NN, l = it - s * NN;
+      if (s == 2)
+        psweep<P, N, 2, true, true>(R2 + 2 * N3, R2 + 3 * N3, R1 + 2 * N3, l, sS, sDh + 2 * NN);
+      else
+        psweep<P, N, 2, true, false>(R2 + s * N3, nullptr, R1 + s * N3, l, sS, nullptr);
+    }
+  group_sync<NT>();
+  // continuity penalty on the six faces f = 2a + (side < 0), each sum
+  // factorised: jump J = u_a(own layer) - u_a(neighbour layer) at the face
+  // nodes, T = (M (x) I) J, O += {{tau_C}} |F| (I (x) M) T on the own layer;
+  // J and T live in R2.  Faces normal to a change component a only, on the
+  // layer of their side, so the items of the last phase write disjoint entries.
+  V* sJ = R2;
+  V* sT = R2 + 6 * NN;
   if (active)
-    for (int c = 0; c < 3; ++c)
-      for (int i = l; i < N3; i += NT) dst3[((size_t)c * m.E + cx.el) * N3 + i] = P::store(O[c * N3 + i]);
+    for (int it = t; it < 6 * NN; it += NT) {
+      const int f = it / NN, r = it - f * NN;
+      const int a = f >> 1, side = (f & 1) ? -1 : 1;
+      const int sa = a == 0 ? 1 : (a == 1 ? N : NN);
+      const int s1 = a == 0 ? N : 1, s2 = a == 2 ? N : NN;
+      const unsigned nb = a == 0 ? neighbor32<0>(cx, side, m)
+                                 : (a == 1 ? neighbor32<1>(cx, side, m) : neighbor32<2>(cx, side, m));
+      const int off = (r % N) * s1 + (r / N) * s2;
+      const int aown = side > 0 ? N - 1 : 0, anb = side > 0 ? 0 : N - 1;
+      sJ[it] = P::sub(P::load(u3 + ((size_t)a * m.E + cx.el) * N3 + aown * sa + off),
+                      P::load(u3 + ((size_t)a * m.E + nb) * N3 + anb * sa + off));
+    }
+  group_sync<NT>();
+  if (active)   // T[j1 + N i2] = sum_i1 M[j1][i1] J[i1 + N i2]
+    for (int it = t; it < 6 * NN; it += NT) {
+      const int f = it / NN, r = it - f * NN;
+      const int j1 = r % N, i2 = r / N;
+      const V* J = sJ + f * NN + N * i2;
+      Acc acc;
+      P::acc_first(acc, sM[j1 * N], J[0]);
+#pragma unroll
+      for (int i1 = 1; i1 < N; ++i1) P::acc_fma(acc, sM[j1 * N + i1], J[i1]);
+      sT[it] = P::acc_get(acc);
+    }
+  group_sync<NT>();
+  if (active) {   // O += {{tau_C}} |F| sum_i2 M[j2][i2] T[j1 + N i2]
+    const V half_tc = P::half(P::load(tau_c + cx.el));
+    for (int it = t; it < 6 * NN; it += NT) {
+      const int f = it / NN, r = it - f * NN;
+      const int a = f >> 1, side = (f & 1) ? -1 : 1;
+      const int sa = a == 0 ? 1 : (a == 1 ? N : NN);
+      const int s1 = a == 0 ? N : 1, s2 = a == 2 ? N : NN;
+      const unsigned nb = a == 0 ? neighbor32<0>(cx, side, m)
+                                 : (a == 1 ? neighbor32<1>(cx, side, m) : neighbor32<2>(cx, side, m));
+      // {{tau_C}} |F| (the halving is exact)
+      const V tbar = P::mul(P::add(half_tc, P::half(P::load(tau_c + nb))), tb.area[a]);
+      const int j1 = r % N, j2 = r / N;
+      const V* T = sT + f * NN + j1;
+      Acc acc;
+      P::acc_first(acc, sM[j2 * N], T[0]);
+#pragma unroll
+      for (int i2 = 1; i2 < N; ++i2) P::acc_fma(acc, sM[j2 * N + i2], T[N * i2]);
+      const int io = a * N3 + (side > 0 ? N - 1 : 0) * sa + j1 * s1 + j2 * s2;
+      Acc o;
+      P::acc_set(o, R1[io]);
+      P::acc_fma(o, tbar, P::acc_get(acc));
+      R1[io] = P::acc_get(o);
+    }
+  }
+  group_sync<NT>();
+  if (active)
+    for (int i = t; i < 3 * N3; i += NT) {
+      const int c = i / N3, r = i - c * N3;
+      dst3[((size_t)c * m.E + cx.el) * N3 + r] = P::store(R1[i]);
+    }
 }
 
 // Volume-averaged Euclidean norm of u per cell -> penalty parameters.
@@ -304,12 +358,6 @@ ProjTabT<typename P::V, N> make_tabT(const ProjHost& h) {
     tb.D[i] = P::make(h.D[i]);
   }
   for (int i = 0; i < N * N; ++i) tb.M[i] = P::make(h.M[i]);
-  if (ProjTabT<typename P::V, N>::kMM)
-    for (int j2 = 0; j2 < N; ++j2)
-      for (int j1 = 0; j1 < N; ++j1)
-        for (int i2 = 0; i2 < N; ++i2)
-          for (int i1 = 0; i1 < N; ++i1)
-            tb.MM[(j1 + N * j2) * N * N + i1 + N * i2] = P::make(h.M[j1 * N + i1] * h.M[j2 * N + i2]);
   const double jac = h.h[0] * h.h[1] * h.h[2];
   for (int qz = 0; qz < N; ++qz)
     for (int qy = 0; qy < N; ++qy)
@@ -324,15 +372,16 @@ ProjTabT<typename P::V, N> make_tabT(const ProjHost& h) {
 template <class P, int N>
 int launch_proj(const MeshDims& m, const double* u3, double* dst3, const double* td, const double* tc,
                 const ProjHost& h, cudaStream_t s) {
-  constexpr int EPB = proj_cells_per_block<N>();
-  const size_t smem = (size_t)EPB * 27 * N * N * N * sizeof(double);
-  if (smem > 232448 - 3 * N * N * sizeof(double)) return 7;
+  constexpr int EPB = proj_op_cells_per_block<N>();
+  const size_t smem = ((size_t)EPB * proj_per_cell<N>() + 6 * N * N) * sizeof(double);
+  if (smem > 232448) return 7;
   if (cudaFuncSetAttribute(proj_kernel<P, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return 2;
   if (m.E == 0) return 0;
   const long long blocks = (m.E + EPB - 1) / EPB;
-  proj_kernel<P, N><<<(unsigned)blocks, EPB * N * N, smem, s>>>(u3, dst3, td, tc, make_tabT<P, N>(h), m);
+  proj_kernel<P, N><<<(unsigned)blocks, EPB * proj_threads<N>(), smem, s>>>(u3, dst3, td, tc, make_tabT<P, N>(h),
+                                                                             m);
   return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }
 

@@ -235,3 +235,19 @@ def test_pinned_host_pointers():
     ctx.convective_cells(yp, up, rf)
     ctx.vmult_convective(yd, u.cuda())
     assert np.array_equal(yp.numpy(), host(yd))
+
+
+@pytest.mark.parametrize("scale", [1e-15, 1.0, 1e30])
+def test_double_float_stores_across_magnitudes(scale):
+    """Small, ordinary and large vectors within the double-float range match
+    the oracle (a loaded value keeps its low half above 2^-74, so its error is
+    at most 2^-47 |x| + 2^-98 absolute: vectors down to max |x| ~ 1e-15)."""
+    n, k = (2, 3, 2), 3
+    ctx = context(n, k, mg_precision=0, fp64_mode=1)
+    s = dg.Space(dg.Mesh(n), k)
+    x = scale * random_field(s, 3, 12)
+    y = torch.empty(x.size, dtype=torch.float64, device="cuda")
+    ctx.vmult_mass(y, dev(x.ravel()), 3, 0)
+    assert rel_err(host(y), dg.Mass(s).apply(x)) <= TOL
+    ctx.apply_inverse_mass(y, dev(x.ravel()), 3, 0)
+    assert rel_err(host(y), dg.Mass(s).apply_inverse(x)) <= TOL
