@@ -52,8 +52,8 @@ DF_FP32_PER_FP64 = 7.5
 # capture of the same workload (profiles/convective_k3_32c_face_cell_ncu.md),
 # keyed by (kernel, fp64_mode); None where no capture of the current kernel
 # exists.
-KERNEL_TRAFFIC = {("conv_kernel", 1): None, ("conv_kernel", 0): None,
-                  ("conv_face_kernel", 1): None, ("conv_face_kernel", 0): None}
+KERNEL_TRAFFIC = {("conv_kernel", 1): 105.6e6, ("conv_kernel", 0): None,
+                  ("conv_face_kernel", 1): 61.8e6, ("conv_face_kernel", 0): None}
 
 
 # ----------------------------------------------------------- flop counts
