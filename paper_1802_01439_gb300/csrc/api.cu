@@ -1013,7 +1013,7 @@ int dgns_dissipation_grad(dgns_ctx* c, double* grad3, const double* u3) {
   for (int i = 0; i < 3; ++i) vol *= c->d.hi[i] - c->d.lo[i];
   LapHost K;
   build_broken_stiffness(c, 2.0 * c->d.nu / vol, K);
-  DG_TRY(laplace_apply(false, c->m, 3, s, d, K, EPI_NONE, EpiHost(), c->s));
+  DG_TRY(laplace_apply(false, c->m, 3, s, d, K, EPI_NONE, EpiHost(), c->s, c->d.fp64_mode == 1));
   return st.finish();
 }
 
@@ -1030,7 +1030,7 @@ int dgns_dissipation(dgns_ctx* c, const double* u3, double* eps_out) {
   for (int i = 0; i < 3; ++i) vol *= c->d.hi[i] - c->d.lo[i];
   LapHost K;
   build_broken_stiffness(c, c->d.nu / vol, K);
-  DG_TRY(laplace_apply(false, c->m, 3, s, c->Ap, K, EPI_NONE, EpiHost(), c->s));
+  DG_TRY(laplace_apply(false, c->m, 3, s, c->Ap, K, EPI_NONE, EpiHost(), c->s, c->d.fp64_mode == 1));
   DG_TRY(dot((const double*)s, c->Ap, n, c->red, S_T1, c->s));
   DG_TRY(read_scalars(c));
   *eps_out = c->h_scal[S_T1];
@@ -1128,7 +1128,7 @@ int dgns_cg_projection_solve(dgns_ctx* c, double* x3, const double* b3, const do
   inf.initial_res = nb;
   int status = DGNS_OK;
   if (nb > 0.0) {
-    DG_TRY(tensor3_apply(N, 3 * c->m.E, c->r, c->z, MI[0], MI[1], MI[2], c->s));
+    DG_TRY(tensor3_apply(N, 3 * c->m.E, c->r, c->z, MI[0], MI[1], MI[2], c->s, c->d.fp64_mode == 1));
     DG_TRY(cg_direction(c->p, c->z, n, c->red, true, c->s));
     DG_TRY(dot(c->r, c->z, n, c->red, S_RZ, c->s));
     int it = 0;
@@ -1150,7 +1150,7 @@ int dgns_cg_projection_solve(dgns_ctx* c, double* x3, const double* b3, const do
         status = DGNS_OK;
         break;
       }
-      DG_TRY(tensor3_apply(N, 3 * c->m.E, c->r, c->z, MI[0], MI[1], MI[2], c->s));
+      DG_TRY(tensor3_apply(N, 3 * c->m.E, c->r, c->z, MI[0], MI[1], MI[2], c->s, c->d.fp64_mode == 1));
       DG_TRY(dot(c->r, c->z, n, c->red, S_RZNEW, c->s));
       DG_TRY(cg_direction(c->p, c->z, n, c->red, false, c->s));
     }
@@ -1335,7 +1335,7 @@ int dgns_cg_invmass_solve(dgns_ctx* c, double* x3, const double* b3, double mass
   inf.initial_res = nb;
   int status = DGNS_OK;
   if (nb > 0.0) {
-    DG_TRY(tensor3_apply(N, 3 * c->m.E, c->r, c->z, MI[0], MI[1], MI[2], c->s));
+    DG_TRY(tensor3_apply(N, 3 * c->m.E, c->r, c->z, MI[0], MI[1], MI[2], c->s, c->d.fp64_mode == 1));
     DG_TRY(cg_direction(c->p, c->z, n, c->red, true, c->s));
     DG_TRY(dot(c->r, c->z, n, c->red, S_RZ, c->s));
     int it = 0;
@@ -1357,7 +1357,7 @@ int dgns_cg_invmass_solve(dgns_ctx* c, double* x3, const double* b3, double mass
         status = DGNS_OK;
         break;
       }
-      DG_TRY(tensor3_apply(N, 3 * c->m.E, c->r, c->z, MI[0], MI[1], MI[2], c->s));
+      DG_TRY(tensor3_apply(N, 3 * c->m.E, c->r, c->z, MI[0], MI[1], MI[2], c->s, c->d.fp64_mode == 1));
       DG_TRY(dot(c->r, c->z, n, c->red, S_RZNEW, c->s));
       DG_TRY(cg_direction(c->p, c->z, n, c->red, false, c->s));
     }

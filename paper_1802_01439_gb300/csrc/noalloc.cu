@@ -133,7 +133,7 @@ extern "C" int dgns_cg_invmass_solve_noalloc(dgns_ctx* c, double* x3, const doub
   inf.initial_res = nb;
   int status = DGNS_OK;
   if (nb > 0.0) {
-    NA_TRY(tensor3_apply(N, 3 * c->m.E, r, z, MI[0], MI[1], MI[2], c->s));
+    NA_TRY(tensor3_apply(N, 3 * c->m.E, r, z, MI[0], MI[1], MI[2], c->s, c->d.fp64_mode == 1));
     NA_TRY(cg_direction(p, z, n, red, true, c->s));
     NA_TRY(dot(r, z, n, red, S_RZ, c->s));
     int it = 0;
@@ -155,7 +155,7 @@ extern "C" int dgns_cg_invmass_solve_noalloc(dgns_ctx* c, double* x3, const doub
         status = DGNS_OK;
         break;
       }
-      NA_TRY(tensor3_apply(N, 3 * c->m.E, r, z, MI[0], MI[1], MI[2], c->s));
+      NA_TRY(tensor3_apply(N, 3 * c->m.E, r, z, MI[0], MI[1], MI[2], c->s, c->d.fp64_mode == 1));
       NA_TRY(dot(r, z, n, red, S_RZNEW, c->s));
       NA_TRY(cg_direction(p, z, n, red, false, c->s));
     }

@@ -41,10 +41,11 @@ def test_convective_vjp_unsupported_degree():
         ctx.vjp_convective(torch.empty_like(x), x, x.clone())
 
 
-def test_dissipation_and_gradient():
+@pytest.mark.parametrize("mode", [0, 1])
+def test_dissipation_and_gradient(mode):
     nu = 1.0 / 1600
     n, k = (3, 2, 4), 4
-    ctx = context(n, k, mg_precision=0, nu=nu)
+    ctx = context(n, k, mg_precision=0, nu=nu, fp64_mode=mode)
     s = dg.Space(dg.Mesh(n), k)
     u = tgv_field(s, 1e-2, 3)
     eps = ctx.dissipation(dev(u))
