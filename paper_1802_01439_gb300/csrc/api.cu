@@ -1073,7 +1073,7 @@ int dgns_penalty_parameters(dgns_ctx* c, const double* u_ex3, double dt, double 
     return fail(DGNS_ERR_INVALID_ARG, "device pointers only");
   const double h_eff = cbrt(c->h[0] * c->h[1] * c->h[2]);
   const double fd = zeta_d * h_eff / (c->k[0] + 1) * dt, fc = zeta_c * dt;
-  const int rc = penalty_parameters(c->m, u_ex3, tau_d, tau_c, c->proj, fd, fc, c->s);
+  const int rc = penalty_parameters(c->m, u_ex3, tau_d, tau_c, c->proj, fd, fc, c->s, c->d.fp64_mode == 1);
   if (rc == 7) return fail(DGNS_ERR_UNSUPPORTED, "projection operator: supported for k_u <= 7");
   DG_TRY(rc);
   return 0;

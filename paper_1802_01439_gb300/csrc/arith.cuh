@@ -63,6 +63,7 @@ struct F64 {
   __device__ __forceinline__ static V fmadd(V a, V b, V c) { return fma(a, b, c); }
   __device__ __forceinline__ static V half(V a) { return 0.5 * a; }
   __device__ __forceinline__ static V absval(V a) { return fabs(a); }
+  __device__ __forceinline__ static V sqrt_(V a) { return sqrt(a); }
   __device__ __forceinline__ static bool greater(V a, V b) { return a > b; }
   __device__ __forceinline__ static bool equal(V a, V b) { return a == b; }
   __device__ __forceinline__ static int sign(V a) { return a > 0.0 ? 1 : (a < 0.0 ? -1 : 0); }
@@ -206,6 +207,17 @@ struct DF64 {
     return a;
   }
   __device__ __forceinline__ static V absval(V a) { return a.hi < 0.0f ? neg(a) : a; }
+  // Square root: the float root r of hi and one Newton correction
+  // (a - r^2) / (2 r), with r^2 formed exactly by the FMA (a - r^2 is then
+  // exact up to the rounding of the small remainder); ~2^-47 relative.
+  __device__ __forceinline__ static V sqrt_(V a) {
+    if (!(a.hi > 0.0f)) return zero();
+    const float r = __fsqrt_rn(a.hi);
+    const float p = __fmul_rn(r, r);
+    const float pe = __fmaf_rn(r, r, -p);
+    const float d = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), pe), a.lo);
+    return renorm(r, __fdiv_rn(d, __fmul_rn(2.0f, r)));
+  }
   __device__ __forceinline__ static bool greater(V a, V b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
   __device__ __forceinline__ static bool equal(V a, V b) { return a.hi == b.hi && a.lo == b.lo; }
   __device__ __forceinline__ static int sign(V a) { return a.hi > 0.0f ? 1 : (a.hi < 0.0f ? -1 : 0); }

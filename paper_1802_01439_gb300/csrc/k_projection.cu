@@ -20,15 +20,6 @@
 namespace dgns {
 namespace {
 
-template <int N>
-struct ProjTab {
-  double S[N * N];   // S[q*N+j] = phi_j(g_q)
-  double D[N * N];   // D[q*N+j] = phi_j'(g_q)
-  double M[N * N];   // 1D mass
-  double w[N];       // Gauss weights on [0,1]
-  double h[3];
-};
-
 // Tables of the operator kernel in the arithmetic policy's value type.
 template <class V, int N>
 struct ProjTabT {
@@ -43,33 +34,10 @@ constexpr int proj_cells_per_block() {
   return N * N >= 64 ? 1 : 64 / (N * N);
 }
 
-// out-line (along D) = A in-line, A applied as A (TR = false: y_q = sum_j A[q][j] x_j)
-// or A^T (TR = true: y_j = sum_q A[q][j] x_q); optional second input and scale.
-template <int N, int D, bool TR, bool TWO>
-__device__ __forceinline__ void dsweep(const double* in, const double* in2, double* out, int l, const double* A,
-                                       const double* A2, double s2) {
-  int base, stride;
-  line_geom<D>(l, N, N, N, base, stride);
-  double x[N], x2[N];
-  load_line<double, N>(in, base, stride, x);
-  if (TWO) load_line<double, N>(in2, base, stride, x2);
-#pragma unroll
-  for (int i = 0; i < N; ++i) {
-    double a = 0.0;
-#pragma unroll
-    for (int j = 0; j < N; ++j) a = fma(TR ? A[j * N + i] : A[i * N + j], x[j], a);
-    if (TWO) {
-      double b = 0.0;
-#pragma unroll
-      for (int j = 0; j < N; ++j) b = fma(TR ? A2[j * N + i] : A2[i * N + j], x2[j], b);
-      a = fma(s2, b, a);
-    }
-    out[base + i * stride] = a;
-  }
-}
-
-// The same sweep in an arithmetic policy: out = A in (+ A2 in2 scaled by the
-// second table, which then already carries the scale).
+// One line sweep in an arithmetic policy, out-line (along D) = A in-line,
+// A applied as A (TR = false: y_q = sum_j A[q][j] x_j) or as A^T (TR = true:
+// y_j = sum_q A[q][j] x_q), plus A2 in2 when TWO (a second table that
+// already carries its scale).
 template <class P, int N, int D, bool TR, bool TWO>
 __device__ __forceinline__ void psweep(const typename P::V* in, const typename P::V* in2, typename P::V* out,
                                        int l, const typename P::V* A, const typename P::V* A2) {
@@ -288,67 +256,66 @@ __global__ void __launch_bounds__(proj_op_cells_per_block<N>() * proj_threads<N>
     }
 }
 
-// Volume-averaged Euclidean norm of u per cell -> penalty parameters.
-template <int N>
+// Volume-averaged Euclidean norm of u per cell -> penalty parameters, in the
+// arithmetic policy P; the per-thread partial sums are added in a fixed order
+// in FP64.  W3 carries h_x h_y h_z, divided out at the end.
+template <class P, int N>
 __global__ void __launch_bounds__(proj_cells_per_block<N>() * N * N)
     speed_kernel(const double* __restrict__ u3, double* __restrict__ tau_d, double* __restrict__ tau_c,
-                 const __grid_constant__ ProjTab<N> tb, const MeshDims m, double fd, double fc) {
+                 const __grid_constant__ ProjTabT<typename P::V, N> tb, const MeshDims m, double fd, double fc,
+                 double inv_jac) {
+  typedef typename P::V V;
+  typedef typename P::Acc Acc;
   constexpr int NT = N * N, N3 = N * N * N, EPB = proj_cells_per_block<N>();
-  constexpr int PER = 9 * N3;
-  double* sm = reinterpret_cast<double*>(dyn_smem());
+  constexpr int PER = 6 * N3;
+  V* sm = reinterpret_cast<V*>(dyn_smem());
   const int slot = threadIdx.x / NT;
   const int l = threadIdx.x - slot * NT;
   const long long c0 = (long long)blockIdx.x * EPB;
   const long long rem = m.E - c0;
   const int nvalid = rem < EPB ? (int)rem : EPB;
   const bool active = slot < nvalid;
-  double* U = sm + slot * PER;
-  double* A = U + 3 * N3;
-  double* B = A + 3 * N3;
+  V* U = sm + slot * PER;
+  V* A = U + 3 * N3;
   __shared__ double red[EPB][NT];
   const long long el = c0 + slot;
   if (active)
     for (int c = 0; c < 3; ++c)
-      for (int i = l; i < N3; i += NT) U[c * N3 + i] = u3[((size_t)c * m.E + el) * N3 + i];
+      for (int i = l; i < N3; i += NT) U[c * N3 + i] = P::load(u3 + ((size_t)c * m.E + el) * N3 + i);
   __syncthreads();
   if (active)
-    for (int c = 0; c < 3; ++c) dsweep<N, 0, false, false>(U + c * N3, nullptr, A + c * N3, l, tb.S, nullptr, 0.0);
+    for (int c = 0; c < 3; ++c) psweep<P, N, 0, false, false>(U + c * N3, nullptr, A + c * N3, l, tb.S, nullptr);
   __syncthreads();
   if (active)
-    for (int c = 0; c < 3; ++c) dsweep<N, 1, false, false>(A + c * N3, nullptr, B + c * N3, l, tb.S, nullptr, 0.0);
+    for (int c = 0; c < 3; ++c) psweep<P, N, 1, false, false>(A + c * N3, nullptr, U + c * N3, l, tb.S, nullptr);
   __syncthreads();
   if (active)
-    for (int c = 0; c < 3; ++c) dsweep<N, 2, false, false>(B + c * N3, nullptr, A + c * N3, l, tb.S, nullptr, 0.0);
+    for (int c = 0; c < 3; ++c) psweep<P, N, 2, false, false>(U + c * N3, nullptr, A + c * N3, l, tb.S, nullptr);
   __syncthreads();
   double s = 0.0;
-  if (active)
+  if (active) {
+    Acc acc;
+    P::acc_zero(acc);
     for (int i = l; i < N3; i += NT) {
-      const int qx = i % N, qy = (i / N) % N, qz = i / (N * N);
-      const double v = sqrt(A[i] * A[i] + A[N3 + i] * A[N3 + i] + A[2 * N3 + i] * A[2 * N3 + i]);
-      s = fma(tb.w[qx] * tb.w[qy] * tb.w[qz], v, s);
+      Acc q;
+      P::acc_first(q, A[i], A[i]);
+      P::acc_fma(q, A[N3 + i], A[N3 + i]);
+      P::acc_fma(q, A[2 * N3 + i], A[2 * N3 + i]);
+      P::acc_fma(acc, tb.W3[i], P::sqrt_(P::acc_get_norm(q)));
     }
+    s = P::to_double(P::acc_get_norm(acc));
+  }
   red[slot][l] = s;
   __syncthreads();
   if (active && l == 0) {
     double t = 0.0;
     for (int i = 0; i < NT; ++i) t += red[slot][i];   // fixed order
+    t *= inv_jac;
     tau_d[el] = fd * t;
     tau_c[el] = fc * t;
   }
 }
 
-template <int N>
-ProjTab<N> make_tab(const ProjHost& h) {
-  ProjTab<N> tb;
-  for (int i = 0; i < N * N; ++i) {
-    tb.S[i] = h.S[i];
-    tb.D[i] = h.D[i];
-    tb.M[i] = h.M[i];
-  }
-  for (int q = 0; q < N; ++q) tb.w[q] = h.w[q];
-  for (int d = 0; d < 3; ++d) tb.h[d] = h.h[d];
-  return tb;
-}
 
 template <class P, int N>
 ProjTabT<typename P::V, N> make_tabT(const ProjHost& h) {
@@ -385,16 +352,18 @@ int launch_proj(const MeshDims& m, const double* u3, double* dst3, const double*
   return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }
 
-template <int N>
+template <class P, int N>
 int launch_speed(const MeshDims& m, const double* u3, double* td, double* tc, const ProjHost& h, double fd,
                  double fc, cudaStream_t s) {
   constexpr int EPB = proj_cells_per_block<N>();
-  const size_t smem = (size_t)EPB * 9 * N * N * N * sizeof(double);
-  if (cudaFuncSetAttribute(speed_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  const size_t smem = (size_t)EPB * 6 * N * N * N * sizeof(double);
+  if (cudaFuncSetAttribute(speed_kernel<P, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
     return 2;
   if (m.E == 0) return 0;
   const long long blocks = (m.E + EPB - 1) / EPB;
-  speed_kernel<N><<<(unsigned)blocks, EPB * N * N, smem, s>>>(u3, td, tc, make_tab<N>(h), m, fd, fc);
+  speed_kernel<P, N><<<(unsigned)blocks, EPB * N * N, smem, s>>>(u3, td, tc, make_tabT<P, N>(h), m, fd, fc,
+                                                                  1.0 / (h.h[0] * h.h[1] * h.h[2]));
   return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }
 
@@ -419,16 +388,20 @@ int projection_apply(const MeshDims& m, const double* u3, double* dst3, const do
 }
 
 int penalty_parameters(const MeshDims& m, const double* u3, double* tau_d, double* tau_c, const ProjHost& h,
-                       double fd, double fc, cudaStream_t s) {
+                       double fd, double fc, cudaStream_t s, bool emulated) {
+#define DGNS_SPEED(NV) \
+  case NV:             \
+    return emulated ? launch_speed<DF64, NV>(m, u3, tau_d, tau_c, h, fd, fc, s) : launch_speed<F64, NV>(m, u3, tau_d, tau_c, h, fd, fc, s);
   switch (h.N) {
-    case 2: return launch_speed<2>(m, u3, tau_d, tau_c, h, fd, fc, s);
-    case 3: return launch_speed<3>(m, u3, tau_d, tau_c, h, fd, fc, s);
-    case 4: return launch_speed<4>(m, u3, tau_d, tau_c, h, fd, fc, s);
-    case 5: return launch_speed<5>(m, u3, tau_d, tau_c, h, fd, fc, s);
-    case 6: return launch_speed<6>(m, u3, tau_d, tau_c, h, fd, fc, s);
-    case 7: return launch_speed<7>(m, u3, tau_d, tau_c, h, fd, fc, s);
-    case 8: return launch_speed<8>(m, u3, tau_d, tau_c, h, fd, fc, s);
+    DGNS_SPEED(2)
+    DGNS_SPEED(3)
+    DGNS_SPEED(4)
+    DGNS_SPEED(5)
+    DGNS_SPEED(6)
+    DGNS_SPEED(7)
+    DGNS_SPEED(8)
   }
+#undef DGNS_SPEED
   return 7;
 }
 

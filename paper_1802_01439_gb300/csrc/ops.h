@@ -102,6 +102,6 @@ int projection_apply(const MeshDims& m, const double* u3, double* dst3, const do
                      const ProjHost& h, cudaStream_t s, bool emulated = false);
 // tau_d = fd * avg|u|, tau_c = fc * avg|u| per cell
 int penalty_parameters(const MeshDims& m, const double* u3, double* tau_d, double* tau_c, const ProjHost& h,
-                       double fd, double fc, cudaStream_t s);
+                       double fd, double fc, cudaStream_t s, bool emulated = false);
 
 }  // namespace dgns

@@ -17,8 +17,10 @@ def _built():
 
 
 @pytest.mark.parametrize("n,k", [((3, 2, 4), 3), ((2, 2, 2), 2), ((1, 2, 3), 4), ((2, 1, 2), 7)])
-def test_penalty_parameters(n, k):
-    ctx = context(n, k, mg_precision=0)
+@pytest.mark.parametrize("mode", [0, 1])
+def test_penalty_parameters(n, k, mode):
+    """mode 1: interpolation and norm in double-float (with its square root)."""
+    ctx = context(n, k, mg_precision=0, fp64_mode=mode)
     s = dg.Space(dg.Mesh(n), k)
     u = tgv_field(s, 1e-2, 1)
     td, tc = ctx.penalty_parameters(dev(u.ravel()), 1e-3, zeta_d=1.0, zeta_c=0.7)
