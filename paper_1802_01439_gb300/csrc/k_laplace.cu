@@ -193,10 +193,21 @@ __device__ __forceinline__ void load_nb_lines(const typename A::G* __restrict__ 
                                               typename A::V (&r)[N], typename A::V (&lf)[N]) {
   int base, stride;
   line_geom<D>(l, N, N, N, base, stride);
+  if constexpr (D == 0 && !A::emulated && sizeof(typename A::G) == 4 && N % 4 == 0) {
+    // FP32 x-lines are contiguous and 16-byte aligned: vector loads
 #pragma unroll
-  for (int j = 0; j < N; ++j) {
-    r[j] = A::load(nbR + base + j * stride);
-    lf[j] = A::load(nbL + base + j * stride);
+    for (int j = 0; j < N; j += 4) {
+      const float4 a = __ldg(reinterpret_cast<const float4*>(nbR + base + j));
+      const float4 b = __ldg(reinterpret_cast<const float4*>(nbL + base + j));
+      r[j] = a.x, r[j + 1] = a.y, r[j + 2] = a.z, r[j + 3] = a.w;
+      lf[j] = b.x, lf[j + 1] = b.y, lf[j + 2] = b.z, lf[j + 3] = b.w;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      r[j] = A::load(nbR + base + j * stride);
+      lf[j] = A::load(nbL + base + j * stride);
+    }
   }
 }
 
@@ -360,6 +371,37 @@ __global__ void __launch_bounds__(cells_per_block<N>() * N * N)
       } else {
 #pragma unroll
         for (int j = 0; j < N; ++j) gdst[j] = A::store(yl[j]);
+      }
+    } else if constexpr (sizeof(G) == 4 && N % 4 == 0) {
+      // FP32 with 16-byte aligned lines: the same update with vector accesses
+      const V* xl = sX + off + l * padx<N>();
+      const G* bl = ea.b + c0 * NNN + li;
+      const G* pl = ea.xprev ? ea.xprev + c0 * NNN + li : nullptr;
+#pragma unroll
+      for (int j = 0; j < N; j += 4) {
+        const float4 b4 = __ldg(reinterpret_cast<const float4*>(bl + j));
+        const float bb[4] = {b4.x, b4.y, b4.z, b4.w};
+        float out[4];
+        if constexpr (EPI == EPI_RESID) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) out[q] = bb[q] - yl[j + q];
+        } else {
+          const float4 d4 = __ldg(reinterpret_cast<const float4*>(ea.dinv + l * N + j));
+          const float dd[4] = {d4.x, d4.y, d4.z, d4.w};
+          float pp[4] = {0.f, 0.f, 0.f, 0.f};
+          if (ea.c1 != (G)0 && pl) {
+            const float4 p4 = __ldg(reinterpret_cast<const float4*>(pl + j));
+            pp[0] = p4.x, pp[1] = p4.y, pp[2] = p4.z, pp[3] = p4.w;
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const G x = xl[j + q];
+            G v = fma(ea.c2 * dd[q], bb[q] - yl[j + q], x);
+            if (ea.c1 != (G)0) v = fma(ea.c1, x - pp[q], v);
+            out[q] = v;
+          }
+        }
+        *reinterpret_cast<float4*>(gdst + j) = make_float4(out[0], out[1], out[2], out[3]);
       }
     } else {
       // plain float / double policies only
