@@ -64,11 +64,15 @@ typedef struct {
   double nu;             /* kinematic viscosity of the viscous operator           */
   int mg_coarse_n;       /* coarsest multigrid mesh (elements per direction)      */
   int mg_precision;      /* 32 or 64: arithmetic of the V-cycle; 0 = no multigrid */
-  int fp64_mode;         /* arithmetic of the FP64 convective and SIPG-type         */
-                         /* (Laplace, viscous, Helmholtz, the CG matvecs) kernels:  */
-                         /* 0 native FP64; 1 double-float (pairs of FP32 with a     */
-                         /* 48-bit significand on the FP32 pipe, which GB300 runs  */
-                         /* 61x faster; parity with FP64 to 1e-12 relative)        */
+  int fp64_mode;         /* arithmetic of every FP64 operator kernel (convective,   */
+                         /* SIPG-type, mass, divergence, gradient, projection,      */
+                         /* penalty parameters, dissipation, the CG matvecs and     */
+                         /* inverse-mass preconditioners): 0 native FP64;           */
+                         /* 1 double-float (pairs of FP32 with a 48-bit significand */
+                         /* on the FP32 pipe, which GB300 runs 61x faster; parity   */
+                         /* with FP64 to 1e-12 relative for vectors with max |x|    */
+                         /* between ~1e-15 and 2^127).  The multigrid V-cycle runs  */
+                         /* in mg_precision either way.                             */
 } dgns_mesh_desc;
 
 /* Defaults: 4^3 elements on [-pi,pi]^3, k_u = 3, k_p = k_u - 1, 3/2 rule,

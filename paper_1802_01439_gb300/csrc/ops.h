@@ -44,7 +44,7 @@ int broadcast_cells(bool fp32, long long ncells, int nper, const void* table, vo
                     cudaStream_t s);
 
 // dst = (Mz (x) My (x) Mx) src per cell, square N x N matrices (mass,
-// inverse mass).  double only.
+// inverse mass), double data; emulated: double-float arithmetic.
 int tensor3_apply(int N, long long ncells, const double* src, double* dst, const double* Mx,
                   const double* My, const double* Mz, cudaStream_t s, bool emulated = false);
 
