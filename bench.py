@@ -52,7 +52,7 @@ DF_FP32_PER_FP64 = 7.5
 # capture of the same workload (profiles/convective_k3_32c_face_cell_ncu.md),
 # keyed by (kernel, fp64_mode); None where no capture of the current kernel
 # exists.
-KERNEL_TRAFFIC = {("conv_kernel", 1): 105.6e6, ("conv_kernel", 0): None,
+KERNEL_TRAFFIC = {("conv_kernel", 1): None, ("conv_kernel", 0): None,
                   ("conv_face_kernel", 1): 61.8e6, ("conv_face_kernel", 0): None}
 
 
@@ -62,7 +62,7 @@ def conv_cell_flops(N, Q):
     counted from its loops: cell term by z-planes, then the six face
     integrals added to the face layers."""
     f = 2 * (3 * Q * N ** 3 + 3 * Q * Q * N * N)                      # interpolation x, y
-    f += Q * (2 * 3 * Q * Q * N + 9 * Q * Q * (1 + 2 * N)           # plane values, flux + x test
+    f += Q * (2 * 3 * Q * Q * N + Q * Q * (6 + 8 * 2 * N)           # plane values, 6 products u_c u_d, 8 x tests
               + 2 * 9 * N * N * Q + 2 * 6 * N ** 3)                   # y test, z accumulation
     return f + 6 * 3 * N * N
 

@@ -42,18 +42,32 @@ struct ConvTab {
   double area[3];  // product of the tangential cell sizes of faces normal to d
 };
 
-// Threads per cell of the forward convective kernel: one warp up to N = 5;
+// Threads per group of the forward convective kernel: one warp up to N = 5;
 // above, more threads per cell as the cell's shared memory grows (from
 // N = 10 on one cell fills an SM's shared memory, so it gets 16 warps).
 template <int N>
 constexpr int conv_threads() {
   return N <= 5 ? 32 : N == 6 ? 64 : N == 7 ? 128 : N <= 9 ? 256 : 512;
 }
+// Cells per thread group: two for N = 2, where one cell's plane phases have
+// 27, 24, 12 and 24 work items for 32 lanes.  (Two cells per warp at N = 4
+// measured 6 % slower than one: it halves the warps per SM.)
 template <int N>
-constexpr int conv_fwd_cells_per_block() {
+constexpr int conv_cells_per_group() {
+  return N == 2 ? 2 : 1;
+}
+template <int N>
+constexpr int conv_groups_per_block() {
   return conv_threads<N>() >= 128 ? 1 : 128 / conv_threads<N>();
 }
+template <int N>
+constexpr int conv_fwd_cells_per_block() {
+  return conv_groups_per_block<N>() * conv_cells_per_group<N>();
+}
 
+// Shared memory of one cell; a group's cells lie type by type
+// ([CPG x UP][CPG x U1R][CPG x U2]), so that the plane work of the group's
+// cells is contiguous.
 template <int N, int Q>
 struct ConvLayout {
   static constexpr int N3 = N * N * N;
@@ -62,7 +76,7 @@ struct ConvLayout {
   static constexpr int U1R = U1 > 18 * N * N ? U1 : 18 * N * N;  // later: the six face integrals
   static constexpr int U2 = 3 * Q * Q * N;       // xy-interpolated
   static constexpr int P = 3 * Q * Q;            // one z-plane: u
-  static constexpr int X = 9 * N * Q;            // x-tested plane
+  static constexpr int X = 8 * N * Q;            // x-tested plane (eight distinct tests)
   static constexpr int Y = 6 * N * N;            // xy-tested plane
   static constexpr int PXY = P + X + Y;
   static constexpr int UP = U > PXY ? U : PXY;   // nodal u first, plane work later
@@ -106,107 +120,123 @@ __device__ __forceinline__ int node3(int N, int d, int a, int t1, int j1, int t2
 }
 
 // Tables of the forward kernels.  The quadrature weights of each direction
-// sit in that direction's test table, the cell-size factor of the flux
-// direction d (h_x h_y h_z / h_d) in the x-test table of path d, so no
-// per-point weights are multiplied.
+// sit in that direction's test table and the cell-size factor of the flux
+// direction d (h_x h_y h_z / h_d) in the y-test table of path d, so no
+// per-point weights are multiplied and the x test of F_12 = F_21 is shared
+// by the paths (1, 2) and (2, 1).
 template <class V, int N, int Q>
 struct ConvTabT {
   V S[Q * N];       // S[q][j] = phi_j(x_q): interpolation to the Gauss points
   V SW[Q * N];      // w_q phi_j(x_q): test with phi
   V DW[Q * N];      // w_q phi_j'(x_q): test with phi'
-  V TX[3][Q * N];   // x test of flux direction d: jac_d DW (d = 0) or jac_d SW
+  V TY[3][Q * N];   // y test of flux direction d: jac_d SW (d = 0, 2) or jac_d DW (d = 1)
   V area[3];        // h_x h_y h_z / h_d: face area of faces normal to d
 };
 
+// The eight distinct x tests of a plane: test k tests F_cd = u_c u_d with
+// DW (k < 3, d = 0) or SW; the path (c, d) of the cell term reads the x test
+// xtest(c, d).
+__device__ __forceinline__ int test_c(int k) { return k < 3 ? k : (k == 3 || k == 6) ? 0 : (k == 7 ? 2 : 1); }
+__device__ __forceinline__ int test_d(int k) { return k < 3 ? 0 : (k < 5 ? 1 : 2); }
+__device__ __forceinline__ int xtest2(int c) { return c == 0 ? 6 : (c == 1 ? 5 : 7); }  // path (c, 2)
+
+// i-th of up to two values, selected without an indexed local array
+__device__ __forceinline__ unsigned pick2(int i, unsigned a, unsigned b) { return i == 0 ? a : b; }
+
 // Forward convective cell kernel for an arithmetic policy A (F64 or DF64):
-// loads and stores are double; all arithmetic is A's.  Every phase is split
-// into small independent work items (one output or one short line of
-// outputs) spread over the cell's threads; the 1D tables are copied to
-// shared memory because the items index them by thread.
+// loads and stores are double; all arithmetic is A's.  A group of NT threads
+// treats CPG cells at once; every phase is split into small independent work
+// items (one output or one short line of outputs) spread over the group's
+// threads; the 1D tables are copied to shared memory because the items index
+// them by thread.  A group past the last cell repeats the last cell and
+// stores nothing.
 template <class A, int N, int Q>
-__global__ void __launch_bounds__(conv_fwd_cells_per_block<N>() * conv_threads<N>())
+__global__ void __launch_bounds__(conv_groups_per_block<N>() * conv_threads<N>())
     conv_kernel(const double* __restrict__ u3, const double* __restrict__ rface, double* __restrict__ dst3,
                 const __grid_constant__ ConvTabT<typename A::V, N, Q> tb, const MeshDims m) {
   typedef typename A::V V;
   typedef typename A::Acc Acc;
   typedef ConvLayout<N, Q> LY;
   static_assert(sizeof(V) == sizeof(double), "8-byte values");
-  constexpr int NT = conv_threads<N>(), N3 = N * N * N, EPB = conv_fwd_cells_per_block<N>();
-  constexpr int QQ = Q * Q, NN = N * N, QN = Q * N;
+  constexpr int NT = conv_threads<N>(), CPG = conv_cells_per_group<N>();
+  constexpr int N3 = N * N * N, QQ = Q * Q, NN = N * N, QN = Q * N;
+  static_assert(CPG <= 2, "one or two cells per group");
   V* sm = reinterpret_cast<V*>(dyn_smem());
-  const int slot = threadIdx.x / NT;
-  const int t = threadIdx.x - slot * NT;
-  const long long c0 = (long long)blockIdx.x * EPB;
-  const long long rem = m.E - c0;
-  const int nvalid = rem < EPB ? (int)rem : EPB;
-  const bool active = slot < nvalid;
-  V* sS = sm + EPB * LY::PER;   // tables: S, SW, DW, TX[0..2]
+  const int g = threadIdx.x / NT;
+  const int t = threadIdx.x - g * NT;
+  const long long c0 = ((long long)blockIdx.x * conv_groups_per_block<N>() + g) * CPG;
+  const long long last = m.E - 1;
+  V* sS = sm + conv_fwd_cells_per_block<N>() * LY::PER;   // tables: S, SW, DW, TY[0..2]
   V* sSW = sS + QN;
   V* sDW = sSW + QN;
-  V* sTX = sDW + QN;
+  V* sTY = sDW + QN;
   for (int i = threadIdx.x; i < QN; i += blockDim.x) {
     sS[i] = tb.S[i];
     sSW[i] = tb.SW[i];
     sDW[i] = tb.DW[i];
-    sTX[i] = tb.TX[0][i];
-    sTX[QN + i] = tb.TX[1][i];
-    sTX[2 * QN + i] = tb.TX[2][i];
+    sTY[i] = tb.TY[0][i];
+    sTY[QN + i] = tb.TY[1][i];
+    sTY[2 * QN + i] = tb.TY[2][i];
   }
-  V* sU = sm + slot * LY::PER;   // nodal u, dead after the x interpolation
-  V* sP = sU;                    // plane work reuses it
-  V* sX = sP + LY::P;
-  V* sY = sX + LY::X;
-  V* sU1 = sU + LY::UP;
-  V* sU2 = sU1 + LY::U1R;
+  V* sUg = sm + g * CPG * LY::PER;   // nodal u of the group's cells [j][c][N3], dead after the x interpolation
+  V* sPg = sUg;                      // plane work reuses it: u [j][c][QQ]
+  V* sXg = sPg + CPG * LY::P;        // x tests [j][k][qy][x]
+  V* sYg = sXg + CPG * LY::X;        // y tests [j][c][2][y][x]
+  V* sU1g = sUg + CPG * LY::UP;      // x-interpolated, cell j at j U1R; later the face integrals
+  V* sU2g = sU1g + CPG * LY::U1R;    // xy-interpolated, cell j at j U2
 
-  unsigned el = 0;
-  CellXYZ cx{};
-  if (active) {
-    cx = cell_xyz((unsigned)(c0 + slot), m);
-    el = cx.el;
-    for (int c = 0; c < 3; ++c)
-      for (int i = t; i < N3; i += NT) sU[c * N3 + i] = A::load(u3 + ((size_t)c * m.E + el) * N3 + i);
-  }
+  // the group's cells (consecutive ids), clamped to the last cell
+  const unsigned el0 = (unsigned)(c0 < last ? c0 : last);
+  const unsigned el1 = (unsigned)(c0 + 1 < last ? c0 + 1 : last);
+  for (int c = 0; c < 3; ++c)
+    for (int it = t; it < CPG * N3; it += NT) {
+      const int j = it / N3, i = it - j * N3;
+      sUg[j * 3 * N3 + c * N3 + i] = A::load(u3 + ((size_t)c * m.E + pick2(j, el0, el1)) * N3 + i);
+    }
   __syncthreads();
-  // x interpolation: item (c, line (y,z), q)
-  if (active)
-    for (int it = t; it < 3 * NN * Q; it += NT) {
-      const int q = it % Q, r = it / Q;
-      const int c = r / NN, l = r - c * NN;
-      const V* x = sU + c * N3 + l * N;
-      Acc a;
-      A::acc_first(a, sS[q * N], x[0]);
+  // x interpolation: item (j, c, line (y,z), q)
+  for (int it = t; it < CPG * 3 * NN * Q; it += NT) {
+    const int j = it / (3 * NN * Q), l = it - j * 3 * NN * Q;
+    const int q = l % Q, r = l / Q;
+    const V* x = sUg + j * 3 * N3 + r * N;
+    Acc a;
+    A::acc_first(a, sS[q * N], x[0]);
 #pragma unroll
-      for (int j = 1; j < N; ++j) A::acc_fma(a, sS[q * N + j], x[j]);
-      sU1[c * Q * NN + l * Q + q] = A::acc_get_norm(a);
-    }
+    for (int i = 1; i < N; ++i) A::acc_fma(a, sS[q * N + i], x[i]);
+    sU1g[j * LY::U1R + l] = A::acc_get_norm(a);
+  }
   group_sync<NT>();
-  // y interpolation: item (c, qx, z, qy)
-  if (active)
-    for (int it = t; it < 3 * Q * N * Q; it += NT) {
-      const int qy = it % Q, r = it / Q;
-      const int c = r / (Q * N), l = r - c * Q * N;
-      const int qx = l % Q, z = l / Q;
-      const V* x = sU1 + c * Q * NN + qx + Q * N * z;
-      Acc a;
-      A::acc_first(a, sS[qy * N], x[0]);
+  // y interpolation: item (j, c, qx, z, qy)
+  for (int it = t; it < CPG * 3 * Q * N * Q; it += NT) {
+    const int j = it / (3 * QN * Q), l = it - j * 3 * QN * Q;
+    const int qy = l % Q, r = l / Q;
+    const int c = r / QN, ll = r - c * QN;
+    const int qx = ll % Q, z = ll / Q;
+    const V* x = sU1g + j * LY::U1R + c * Q * NN + qx + QN * z;
+    Acc a;
+    A::acc_first(a, sS[qy * N], x[0]);
 #pragma unroll
-      for (int j = 1; j < N; ++j) A::acc_fma(a, sS[qy * N + j], x[Q * j]);
-      sU2[c * QQ * N + qx + Q * qy + QQ * z] = A::acc_get_norm(a);
-    }
+    for (int i = 1; i < N; ++i) A::acc_fma(a, sS[qy * N + i], x[Q * i]);
+    sU2g[j * LY::U2 + c * QQ * N + qx + Q * qy + QQ * z] = A::acc_get_norm(a);
+  }
   group_sync<NT>();
 
-  // The face integrals of the six faces (raw doubles), fetched asynchronously
-  // into the dead x-interpolation buffer while the plane loop runs:
-  // block f = 2 d (+R of face (e, d)) and 2 d + 1 (-R of face (e-1_d, d)).
-  double* sR = reinterpret_cast<double*>(sU1);
-  if (active) {
-    const unsigned nbm0 = neighbor32<0>(cx, -1, m), nbm1 = neighbor32<1>(cx, -1, m), nbm2 = neighbor32<2>(cx, -1, m);
-    for (int it = t; it < 18 * NN; it += NT) {
-      const int f = it / (3 * NN), i = it - f * 3 * NN;
+  // The face integrals of the six faces of each cell (raw doubles), fetched
+  // asynchronously into the dead x-interpolation buffer while the plane loop
+  // runs: block f = 2 d (+R of face (e, d)) and 2 d + 1 (-R of face (e-1_d, d)).
+  {
+    const CellXYZ x0 = cell_xyz(el0, m), x1 = cell_xyz(el1, m);
+    const unsigned n00 = neighbor32<0>(x0, -1, m), n01 = neighbor32<1>(x0, -1, m), n02 = neighbor32<2>(x0, -1, m);
+    const unsigned n10 = neighbor32<0>(x1, -1, m), n11 = neighbor32<1>(x1, -1, m), n12 = neighbor32<2>(x1, -1, m);
+    for (int it = t; it < CPG * 18 * NN; it += NT) {
+      const int j = it / (18 * NN), l = it - j * 18 * NN;
+      const int f = l / (3 * NN), i = l - f * 3 * NN;
       const int dd = f >> 1;
-      const unsigned cell = (f & 1) == 0 ? el : (dd == 0 ? nbm0 : (dd == 1 ? nbm1 : nbm2));
-      cp_async8(sR + it, rface + ((size_t)dd * m.E + cell) * 3 * NN + i);
+      const unsigned cell = (f & 1) == 0 ? pick2(j, el0, el1)
+                            : dd == 0     ? pick2(j, n00, n10)
+                            : dd == 1     ? pick2(j, n01, n11)
+                                          : pick2(j, n02, n12);
+      cp_async8(reinterpret_cast<double*>(sU1g + j * LY::U1R) + l, rface + ((size_t)dd * m.E + cell) * 3 * NN + i);
     }
   }
   cp_async_commit();
@@ -214,39 +244,42 @@ __global__ void __launch_bounds__(conv_fwd_cells_per_block<N>() * conv_threads<N
   // The plane loop: every lane keeps the same work items in all planes, so
   // their offsets are computed once; the lane's outputs (items of P4) stay
   // in registers until the end.
-  constexpr int R1 = (3 * QQ + NT - 1) / NT, R2 = (9 * Q + NT - 1) / NT, R3 = (3 * NN + NT - 1) / NT,
-                R4 = (3 * N3 + NT - 1) / NT;
-  int o1[R1];                                  // P1: offset of the z column in sU2
-  int o2t[R2], o2c[R2], o2d[R2], o2x[R2];      // P2: table, u_c, u_d, output offsets
-  int o3x[R3], o3y[R3];                        // P3: offset into sX, y
-  int o4y[R4], o4z[R4];                        // P4: offset into sY, z
+  constexpr int I1 = CPG * 3 * QQ, I2 = CPG * 8 * Q, I3 = CPG * 3 * NN, I4 = CPG * 3 * N3;
+  constexpr int R1 = (I1 + NT - 1) / NT, R2 = (I2 + NT - 1) / NT, R3 = (I3 + NT - 1) / NT,
+                R4 = (I4 + NT - 1) / NT;
+  int o1[R1];                                  // P1: offset of the z column in sU2g
+  int o2t[R2], o2c[R2], o2d[R2];               // P2: table, u_c, u_d offsets
+  int o3a[R3], o3y[R3];                        // P3: X(c,0) offset in sXg; y + 16 (xtest2(c) - c)
+  int o4y[R4], o4z[R4];                        // P4: offset into sYg, z
 #pragma unroll
   for (int r = 0; r < R1; ++r) {
     const int it = t + NT * r;
-    o1[r] = (it / QQ) * QQ * N + (it % QQ);
+    const int j = it / (3 * QQ), l = it - j * 3 * QQ;
+    o1[r] = j * LY::U2 + (l / QQ) * QQ * N + (l % QQ);
   }
 #pragma unroll
   for (int r = 0; r < R2; ++r) {
     const int it = t + NT * r;
-    const int cd = it / Q, qy = it - cd * Q;
-    const int c = cd / 3, d = cd - 3 * c;
-    o2t[r] = d * QN;
-    o2c[r] = c * QQ + Q * qy;
-    o2d[r] = d * QQ + Q * qy;
-    o2x[r] = cd * N * Q + N * qy;
+    const int j = it / (8 * Q), l = it - j * 8 * Q;
+    const int k = l / Q, qy = l - k * Q;
+    o2t[r] = k < 3 ? 2 * QN : QN;   // DW or SW, relative to sS
+    o2c[r] = j * LY::P + test_c(k) * QQ + Q * qy;
+    o2d[r] = j * LY::P + test_d(k) * QQ + Q * qy;
   }
 #pragma unroll
   for (int r = 0; r < R3; ++r) {
     const int it = t + NT * r;
-    const int c = it / NN, rr = it - c * NN;
-    o3x[r] = 3 * c * N * Q + rr % N;
-    o3y[r] = rr / N;
+    const int j = it / (3 * NN), l = it - j * 3 * NN;
+    const int c = l / NN, rr = l - c * NN;
+    o3a[r] = j * 8 * QN + c * QN + rr % N;
+    o3y[r] = rr / N + 16 * (xtest2(c) - c);
   }
 #pragma unroll
   for (int r = 0; r < R4; ++r) {
     const int it = t + NT * r;
-    const int c = it / N3, rr = it - c * N3;
-    o4y[r] = 2 * c * NN + rr % NN;
+    const int j = it / (3 * N3), l = it - j * 3 * N3;
+    const int c = l / N3, rr = l - c * N3;
+    o4y[r] = (j * 3 + c) * 2 * NN + rr % NN;
     o4z[r] = rr / NN;
   }
   Acc out[R4];
@@ -256,105 +289,102 @@ __global__ void __launch_bounds__(conv_fwd_cells_per_block<N>() * conv_threads<N
 
 #pragma unroll 1
   for (int qz = 0; qz < Q; ++qz) {
-    // P1: u on the plane; item (c, point)
-    if (active)
+    // P1: u on the plane; item (j, c, point)
 #pragma unroll
-      for (int r = 0; r < R1; ++r) {
-        if ((3 * QQ) % NT != 0 && t + NT * r >= 3 * QQ) break;
-        const V* src = sU2 + o1[r];
-        Acc a;
-        A::acc_first(a, sS[qz * N], src[0]);
+    for (int r = 0; r < R1; ++r) {
+      if (I1 % NT != 0 && t + NT * r >= I1) break;
+      const V* src = sU2g + o1[r];
+      Acc a;
+      A::acc_first(a, sS[qz * N], src[0]);
 #pragma unroll
-        for (int z = 1; z < N; ++z) A::acc_fma(a, sS[qz * N + z], src[QQ * z]);
-        sP[t + NT * r] = A::acc_get_norm(a);
-      }
+      for (int z = 1; z < N; ++z) A::acc_fma(a, sS[qz * N + z], src[QQ * z]);
+      sPg[t + NT * r] = A::acc_get_norm(a);
+    }
     group_sync<NT>();
-    // P2: F_cd = u_c u_d on x-lines, x test of path d; item (c, d, qy)
-    if (active)
+    // P2: F_cd = u_c u_d on x-lines, x test k; item (j, k, qy)
 #pragma unroll
-      for (int r = 0; r < R2; ++r) {
-        if ((9 * Q) % NT != 0 && t + NT * r >= 9 * Q) break;
-        const V* T = sTX + o2t[r];
-        const V* uc = sP + o2c[r];
-        const V* ud = sP + o2d[r];
-        Acc a[N];
-        {
-          const V f = A::mul(uc[0], ud[0]);
+    for (int r = 0; r < R2; ++r) {
+      const int it = t + NT * r;
+      if (I2 % NT != 0 && it >= I2) break;
+      const V* T = sS + o2t[r];
+      const V* uc = sPg + o2c[r];
+      const V* ud = sPg + o2d[r];
+      Acc a[N];
+      {
+        const V f = A::mul(uc[0], ud[0]);
 #pragma unroll
-          for (int x = 0; x < N; ++x) A::acc_first(a[x], T[x], f);
-        }
+        for (int x = 0; x < N; ++x) A::acc_first(a[x], T[x], f);
+      }
 #pragma unroll UQ
-        for (int qx = 1; qx < Q; ++qx) {
-          const V f = A::mul(uc[qx], ud[qx]);
+      for (int qx = 1; qx < Q; ++qx) {
+        const V f = A::mul(uc[qx], ud[qx]);
 #pragma unroll
-          for (int x = 0; x < N; ++x) A::acc_fma(a[x], T[qx * N + x], f);
-        }
-#pragma unroll
-        for (int x = 0; x < N; ++x) sX[o2x[r] + x] = A::acc_get_norm(a[x]);
+        for (int x = 0; x < N; ++x) A::acc_fma(a[x], T[qx * N + x], f);
       }
-    group_sync<NT>();
-    // P3: Y1 = SW_y^T X(c,0) + DW_y^T X(c,1), Y3 = SW_y^T X(c,2); item (c, x, y)
-    if (active)
 #pragma unroll
-      for (int r = 0; r < R3; ++r) {
-        if ((3 * NN) % NT != 0 && t + NT * r >= 3 * NN) break;
-        const V* X0 = sX + o3x[r];
-        const V* X1 = X0 + N * Q;
-        const V* X2 = X1 + N * Q;
-        const int y = o3y[r];
-        Acc y1, y3;
-        A::acc_first(y1, sDW[y], X1[0]);
-        A::acc_fma(y1, sSW[y], X0[0]);
-        A::acc_first(y3, sSW[y], X2[0]);
+      for (int x = 0; x < N; ++x) sXg[it * N + x] = A::acc_get_norm(a[x]);
+    }
+    group_sync<NT>();
+    // P3: Y1 = TY0^T X(c,0) + TY1^T X(c,1), Y3 = TY2^T X(c,2); item (j, c, x, y)
+#pragma unroll
+    for (int r = 0; r < R3; ++r) {
+      if (I3 % NT != 0 && t + NT * r >= I3) break;
+      const V* X0 = sXg + o3a[r];
+      const V* X1 = X0 + 3 * QN;                  // X(c,1) = test 3 + c
+      const V* X2 = X0 + (o3y[r] >> 4) * QN;      // X(c,2)
+      const int y = o3y[r] & 15;
+      Acc y1, y3;
+      A::acc_first(y1, sTY[QN + y], X1[0]);
+      A::acc_fma(y1, sTY[y], X0[0]);
+      A::acc_first(y3, sTY[2 * QN + y], X2[0]);
 #pragma unroll UQ
-        for (int qy = 1; qy < Q; ++qy) {
-          const int o = N * qy;
-          A::acc_fma(y1, sDW[qy * N + y], X1[o]);
-          A::acc_fma(y1, sSW[qy * N + y], X0[o]);
-          A::acc_fma(y3, sSW[qy * N + y], X2[o]);
-        }
-        const int it = t + NT * r, c = it / NN;
-        sY[(2 * c) * NN + (it - c * NN)] = A::acc_get_norm(y1);
-        sY[(2 * c + 1) * NN + (it - c * NN)] = A::acc_get_norm(y3);
+      for (int qy = 1; qy < Q; ++qy) {
+        const int o = N * qy;
+        A::acc_fma(y1, sTY[QN + qy * N + y], X1[o]);
+        A::acc_fma(y1, sTY[qy * N + y], X0[o]);
+        A::acc_fma(y3, sTY[2 * QN + qy * N + y], X2[o]);
       }
+      const int it = t + NT * r, jc = it / NN;
+      sYg[2 * jc * NN + (it - jc * NN)] = A::acc_get_norm(y1);
+      sYg[(2 * jc + 1) * NN + (it - jc * NN)] = A::acc_get_norm(y3);
+    }
     group_sync<NT>();
-    // P4: out -= SW_z(qz) Y1 + DW_z(qz) Y3; item (c, x, y, z), in registers
-    if (active)
+    // P4: out -= SW_z(qz) Y1 + DW_z(qz) Y3; item (j, c, x, y, z), in registers
 #pragma unroll
-      for (int r = 0; r < R4; ++r) {
-        if ((3 * N3) % NT != 0 && t + NT * r >= 3 * N3) break;
-        const V* Y = sY + o4y[r];
-        const int z = o4z[r];
-        if (qz == 0)
-          A::acc_first(out[r], A::neg(sDW[z]), Y[NN]);
-        else
-          A::acc_fma(out[r], A::neg(sDW[qz * N + z]), Y[NN]);
-        A::acc_fma(out[r], A::neg(sSW[qz * N + z]), Y[0]);
-      }
+    for (int r = 0; r < R4; ++r) {
+      if (I4 % NT != 0 && t + NT * r >= I4) break;
+      const V* Y = sYg + o4y[r];
+      const int z = o4z[r];
+      if (qz == 0)
+        A::acc_first(out[r], A::neg(sDW[z]), Y[NN]);
+      else
+        A::acc_fma(out[r], A::neg(sDW[qz * N + z]), Y[NN]);
+      A::acc_fma(out[r], A::neg(sSW[qz * N + z]), Y[0]);
+    }
     group_sync<NT>();
   }
   cp_async_wait_all();
   group_sync<NT>();
   // face integrals from the face kernel: +R on the layer N-1 (this cell is
   // the '-' side of its face), -R of the '-' neighbour on the layer 0
-  if (active) {
 #pragma unroll
-    for (int r = 0; r < R4; ++r) {
-      const int it = t + NT * r;
-      if ((3 * N3) % NT != 0 && it >= 3 * N3) break;
-      const int c = it / N3, rr = it - c * N3;
-      const int x = rr % N, yz = rr / N;
-      const int y = yz % N, z = yz / N;
-      const double* rc = sR + c * NN;
-      V v = A::acc_get_norm(out[r]);
-      if (x == N - 1) v = A::add(v, A::split(rc[0 * 3 * NN + y + N * z]));
-      if (x == 0) v = A::sub(v, A::split(rc[1 * 3 * NN + y + N * z]));
-      if (y == N - 1) v = A::add(v, A::split(rc[2 * 3 * NN + x + N * z]));
-      if (y == 0) v = A::sub(v, A::split(rc[3 * 3 * NN + x + N * z]));
-      if (z == N - 1) v = A::add(v, A::split(rc[4 * 3 * NN + x + N * y]));
-      if (z == 0) v = A::sub(v, A::split(rc[5 * 3 * NN + x + N * y]));
-      dst3[((size_t)c * m.E + el) * N3 + rr] = A::store(v);
-    }
+  for (int r = 0; r < R4; ++r) {
+    const int it = t + NT * r;
+    if (I4 % NT != 0 && it >= I4) break;
+    const int j = it / (3 * N3), l = it - j * 3 * N3;
+    if (c0 + j > last) break;
+    const int c = l / N3, rr = l - c * N3;
+    const int x = rr % N, yz = rr / N;
+    const int y = yz % N, z = yz / N;
+    const double* rc = reinterpret_cast<const double*>(sU1g + j * LY::U1R) + c * NN;
+    V v = A::acc_get_norm(out[r]);
+    if (x == N - 1) v = A::add(v, A::split(rc[0 * 3 * NN + y + N * z]));
+    if (x == 0) v = A::sub(v, A::split(rc[1 * 3 * NN + y + N * z]));
+    if (y == N - 1) v = A::add(v, A::split(rc[2 * 3 * NN + x + N * z]));
+    if (y == 0) v = A::sub(v, A::split(rc[3 * 3 * NN + x + N * z]));
+    if (z == N - 1) v = A::add(v, A::split(rc[4 * 3 * NN + x + N * y]));
+    if (z == 0) v = A::sub(v, A::split(rc[5 * 3 * NN + x + N * y]));
+    dst3[((size_t)c * m.E + pick2(j, el0, el1)) * N3 + rr] = A::store(v);
   }
 }
 
@@ -514,9 +544,9 @@ ConvTabT<typename A::V, N, Q> conv_tables(const ConvHost& h) {
       tb.S[i] = A::make(h.S[i]);
       tb.SW[i] = A::make(h.w[q] * h.S[i]);
       tb.DW[i] = A::make(h.w[q] * h.D[i]);
-      tb.TX[0][i] = A::make(jac[0] * h.w[q] * h.D[i]);
-      tb.TX[1][i] = A::make(jac[1] * h.w[q] * h.S[i]);
-      tb.TX[2][i] = A::make(jac[2] * h.w[q] * h.S[i]);
+      tb.TY[0][i] = A::make(jac[0] * h.w[q] * h.S[i]);
+      tb.TY[1][i] = A::make(jac[1] * h.w[q] * h.D[i]);
+      tb.TY[2][i] = A::make(jac[2] * h.w[q] * h.S[i]);
     }
   return tb;
 }
@@ -544,7 +574,8 @@ int launch_conv(int part, const MeshDims& m, const double* u3, double* rface, do
   }
   if (part & 2) {
     const long long blocks = (m.E + EPB - 1) / EPB;
-    conv_kernel<A, N, Q><<<(unsigned)blocks, EPB * conv_threads<N>(), smem, s>>>(u3, rface, dst3, tb, m);
+    conv_kernel<A, N, Q><<<(unsigned)blocks, conv_groups_per_block<N>() * conv_threads<N>(), smem, s>>>(
+        u3, rface, dst3, tb, m);
   }
   return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }

@@ -114,9 +114,12 @@ def test_divergence_gradient(n, ku, mode):
 @pytest.mark.parametrize("n,k,field", [((4, 4, 4), 3, "tgv"), ((3, 2, 5), 2, "rand"),
                                        ((2, 2, 2), 5, "rand"), ((1, 1, 2), 1, "rand"),
                                        ((2, 1, 1), 11, "tgv"), ((2, 3, 2), 7, "tgv"),
-                                       ((5, 3, 2), 4, "tgv"), ((2, 2, 1), 9, "rand")])
+                                       ((5, 3, 2), 4, "tgv"), ((2, 2, 1), 9, "rand"),
+                                       ((3, 3, 3), 3, "rand"), ((3, 1, 1), 1, "tgv")])
 def test_convective(n, k, field, mode):
-    """mode 0: native FP64; mode 1: double-float arithmetic (FP32 pipe)."""
+    """mode 0: native FP64; mode 1: double-float arithmetic (FP32 pipe).  Odd
+    cell counts (27, 3) leave the last two-cell group of the k = 1 and k = 3
+    kernels half empty."""
     ctx = context(n, k, max(k - 1, 1), mg_precision=0, fp64_mode=mode)
     s = dg.Space(dg.Mesh(n), k)
     u = tgv_field(s, 1e-3, 0) if field == "tgv" else random_field(s, 3, 6)
