@@ -59,6 +59,9 @@ struct F64 {
   __device__ __forceinline__ static V add(V a, V b) { return a + b; }
   __device__ __forceinline__ static V sub(V a, V b) { return a - b; }
   __device__ __forceinline__ static V mul(V a, V b) { return a * b; }
+  __device__ __forceinline__ static V mul_nr(V a, V b) { return a * b; }
+  __device__ __forceinline__ static V add_nr(V a, V b) { return a + b; }
+  __device__ __forceinline__ static V sub_nr(V a, V b) { return a - b; }
   __device__ __forceinline__ static V neg(V a) { return -a; }
   __device__ __forceinline__ static V fmadd(V a, V b, V c) { return fma(a, b, c); }
   __device__ __forceinline__ static V half(V a) { return 0.5 * a; }
@@ -194,6 +197,25 @@ struct DF64 {
     e = __fmaf_rn(a.lo, b.hi, e);
     return renorm(p, e);
   }
+  // Product and sums without the final renormalisation (hi + lo is exact up
+  // to the product's or sum's own rounding, lo not necessarily below half an
+  // ulp of hi): for intermediates that only feed further products and sums.
+  __device__ __forceinline__ static V mul_nr(V a, V b) {
+    V r;
+    r.hi = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -r.hi);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    r.lo = __fmaf_rn(a.lo, b.hi, e);
+    return r;
+  }
+  __device__ __forceinline__ static V add_nr(V a, V b) {
+    V r;
+    float e;
+    two_sum(a.hi, b.hi, r.hi, e);
+    r.lo = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    return r;
+  }
+  __device__ __forceinline__ static V sub_nr(V a, V b) { return add_nr(a, neg(b)); }
   // a * b + c
   __device__ __forceinline__ static V fmadd(V a, V b, V c) {
     Acc t;

@@ -131,6 +131,10 @@ struct ConvTabT {
   V DW[Q * N];      // w_q phi_j'(x_q): test with phi'
   V TY[3][Q * N];   // y test of flux direction d: jac_d SW (d = 0, 2) or jac_d DW (d = 1)
   V area[3];        // h_x h_y h_z / h_d: face area of faces normal to d
+  // x tests in even-odd form, [DW, SW][T1: (Q+1)/2 x NH | T2: Q/2 x NH],
+  // NH = (N+1)/2: T1(i,x) = (T(i,x) + s T(i,N-1-x)) / 2,
+  // T2(i,x) = (T(i,x) - s T(i,N-1-x)) / 2, s = -1 for DW, +1 for SW
+  V EO[2][Q * ((N + 1) / 2)];
 };
 
 // The eight distinct x tests of a plane: test k tests F_cd = u_c u_d with
@@ -166,10 +170,12 @@ __global__ void __launch_bounds__(conv_groups_per_block<N>() * conv_threads<N>()
   const int t = threadIdx.x - g * NT;
   const long long c0 = ((long long)blockIdx.x * conv_groups_per_block<N>() + g) * CPG;
   const long long last = m.E - 1;
-  V* sS = sm + conv_fwd_cells_per_block<N>() * LY::PER;   // tables: S, SW, DW, TY[0..2]
+  constexpr int QH = (Q + 1) / 2, QF = Q / 2, NH = (N + 1) / 2, NF = N / 2;
+  V* sS = sm + conv_fwd_cells_per_block<N>() * LY::PER;   // tables: S, SW, DW, TY[0..2], EO[0..1]
   V* sSW = sS + QN;
   V* sDW = sSW + QN;
   V* sTY = sDW + QN;
+  V* sEO = sTY + 3 * QN;
   for (int i = threadIdx.x; i < QN; i += blockDim.x) {
     sS[i] = tb.S[i];
     sSW[i] = tb.SW[i];
@@ -177,6 +183,10 @@ __global__ void __launch_bounds__(conv_groups_per_block<N>() * conv_threads<N>()
     sTY[i] = tb.TY[0][i];
     sTY[QN + i] = tb.TY[1][i];
     sTY[2 * QN + i] = tb.TY[2][i];
+  }
+  for (int i = threadIdx.x; i < Q * NH; i += blockDim.x) {
+    sEO[i] = tb.EO[0][i];
+    sEO[Q * NH + i] = tb.EO[1][i];
   }
   V* sUg = sm + g * CPG * LY::PER;   // nodal u of the group's cells [j][c][N3], dead after the x interpolation
   V* sPg = sUg;                      // plane work reuses it: u [j][c][QQ]
@@ -262,7 +272,7 @@ __global__ void __launch_bounds__(conv_groups_per_block<N>() * conv_threads<N>()
     const int it = t + NT * r;
     const int j = it / (8 * Q), l = it - j * 8 * Q;
     const int k = l / Q, qy = l - k * Q;
-    o2t[r] = k < 3 ? 2 * QN : QN;   // DW or SW, relative to sS
+    o2t[r] = k < 3 ? 0 : Q * NH;    // even-odd DW or SW tables, relative to sEO
     o2c[r] = j * LY::P + test_c(k) * QQ + Q * qy;
     o2d[r] = j * LY::P + test_d(k) * QQ + Q * qy;
   }
@@ -301,28 +311,49 @@ __global__ void __launch_bounds__(conv_groups_per_block<N>() * conv_threads<N>()
       sPg[t + NT * r] = A::acc_get_norm(a);
     }
     group_sync<NT>();
-    // P2: F_cd = u_c u_d on x-lines, x test k; item (j, k, qy)
+    // P2: F_cd = u_c u_d on x-lines, x test k; item (j, k, qy).  Even-odd
+    // form: SW is symmetric and DW antisymmetric under the reflection
+    // (q, x) -> (Q-1-q, N-1-x) of the Gauss points and nodes, so with
+    // fe = f(q) + f(Q-1-q) (fe = f(q) at the middle point of odd Q) and
+    // fo = f(q) - f(Q-1-q) the test is two half-size contractions
+    // r1 = T1^T fe, r2 = T2^T fo, and out(x) = r1 + r2,
+    // out(N-1-x) = s (r1 - r2), out(middle) = r1 + r2 (one of them zero).
 #pragma unroll
     for (int r = 0; r < R2; ++r) {
       const int it = t + NT * r;
       if (I2 % NT != 0 && it >= I2) break;
-      const V* T = sS + o2t[r];
+      const V* T1 = sEO + o2t[r];
+      const V* T2 = T1 + QH * NH;
       const V* uc = sPg + o2c[r];
       const V* ud = sPg + o2d[r];
-      Acc a[N];
-      {
-        const V f = A::mul(uc[0], ud[0]);
+      V fe[QH], fo[QF];
 #pragma unroll
-        for (int x = 0; x < N; ++x) A::acc_first(a[x], T[x], f);
+      for (int i = 0; i < QF; ++i) {
+        const V f1 = A::mul_nr(uc[i], ud[i]), f2 = A::mul_nr(uc[Q - 1 - i], ud[Q - 1 - i]);
+        fe[i] = A::add_nr(f1, f2);
+        fo[i] = A::sub_nr(f1, f2);
       }
-#pragma unroll UQ
-      for (int qx = 1; qx < Q; ++qx) {
-        const V f = A::mul(uc[qx], ud[qx]);
+      if (Q % 2 == 1) fe[QH - 1] = A::mul_nr(uc[QF], ud[QF]);
+      Acc r1[NH], r2[NH];
 #pragma unroll
-        for (int x = 0; x < N; ++x) A::acc_fma(a[x], T[qx * N + x], f);
+      for (int x = 0; x < NH; ++x) {
+        A::acc_first(r1[x], T1[x], fe[0]);
+#pragma unroll
+        for (int i = 1; i < QH; ++i) A::acc_fma(r1[x], T1[i * NH + x], fe[i]);
+        A::acc_first(r2[x], T2[x], fo[0]);
+#pragma unroll
+        for (int i = 1; i < QF; ++i) A::acc_fma(r2[x], T2[i * NH + x], fo[i]);
       }
+      V* xo = sXg + it * N;
+      const bool anti = o2t[r] == 0;
 #pragma unroll
-      for (int x = 0; x < N; ++x) sXg[it * N + x] = A::acc_get_norm(a[x]);
+      for (int x = 0; x < NF; ++x) {
+        const V a = A::acc_get(r1[x]), b = A::acc_get(r2[x]);
+        xo[x] = A::add(a, b);
+        const V d = A::sub(a, b);
+        xo[N - 1 - x] = anti ? A::neg(d) : d;
+      }
+      if (N % 2 == 1) xo[NF] = A::add(A::acc_get(r1[NF]), A::acc_get(r2[NF]));
     }
     group_sync<NT>();
     // P3: Y1 = TY0^T X(c,0) + TY1^T X(c,1), Y3 = TY2^T X(c,2); item (j, c, x, y)
@@ -548,6 +579,18 @@ ConvTabT<typename A::V, N, Q> conv_tables(const ConvHost& h) {
       tb.TY[1][i] = A::make(jac[1] * h.w[q] * h.D[i]);
       tb.TY[2][i] = A::make(jac[2] * h.w[q] * h.S[i]);
     }
+  constexpr int QH = (Q + 1) / 2, NH = (N + 1) / 2;
+  for (int ty = 0; ty < 2; ++ty) {
+    const double* T = ty == 0 ? h.D : h.S;   // DW (antisymmetric), SW (symmetric), times w_q
+    const double s = ty == 0 ? -1.0 : 1.0;
+    for (int i = 0; i < Q; ++i)
+      for (int x = 0; x < NH; ++x) {
+        // rows 0..QH-1: T1, rows QH..Q-1: T2 (row i - QH)
+        const int q = i < QH ? i : i - QH;
+        const double a = h.w[q] * T[q * N + x], b = h.w[q] * T[q * N + N - 1 - x];
+        tb.EO[ty][i * NH + x] = A::make(i < QH ? 0.5 * (a + s * b) : 0.5 * (a - s * b));
+      }
+  }
   return tb;
 }
 
@@ -559,7 +602,7 @@ int launch_conv(int part, const MeshDims& m, const double* u3, double* rface, do
   const ConvTabT<typename A::V, N, Q> tb = conv_tables<A, N, Q>(h);
   constexpr int EPB = conv_fwd_cells_per_block<N>(), GPB = face_groups_per_block<N>(), FPG = faces_per_group<N>();
   constexpr int FPB = GPB * FPG;
-  const size_t smem = ((size_t)EPB * ConvLayout<N, Q>::PER + 6 * Q * N) * sizeof(double);
+  const size_t smem = ((size_t)EPB * ConvLayout<N, Q>::PER + 6 * Q * N + 2 * Q * ((N + 1) / 2)) * sizeof(double);
   const size_t fsmem = (size_t)GPB * (FPG * FaceLayout<N, Q>::PER + 2 * Q * N) * sizeof(double);
   if (smem > 232448 || fsmem > 232448) return 7;
   if (cudaFuncSetAttribute(conv_kernel<A, N, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
