@@ -53,7 +53,7 @@ DF_FP32_PER_FP64 = 7.5
 # keyed by (kernel, fp64_mode); None where no capture of the current kernel
 # exists.
 KERNEL_TRAFFIC = {("conv_kernel", 1): None, ("conv_kernel", 0): None,
-                  ("conv_face_kernel", 1): 61.8e6, ("conv_face_kernel", 0): None}
+                  ("conv_face_kernel", 1): None, ("conv_face_kernel", 0): None}
 
 
 # ----------------------------------------------------------- flop counts

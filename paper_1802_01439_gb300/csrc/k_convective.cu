@@ -83,21 +83,28 @@ struct ConvLayout {
   static constexpr int PER = UP + U1R + U2;
 };
 
-// Face kernel groups: one warp for FPG faces up to N = 6 (two faces up to
-// N = 4, where one face has too few items per phase for 32 lanes), four
-// warps for one face above; four groups per block up to N = 6.
-template <int N>
+// The face kernel's interpolation and test phases give each thread whole
+// lines in even-odd form (`lines`) in double-float arithmetic up to N = 8;
+// natively (FP64-pipe bound, where idle lanes still cost pipe time) and for
+// N > 8 (too few lines per face for the warps an SM needs) one output per
+// thread.
+template <bool EM, int N>
+constexpr bool face_lines() {
+  return EM && N <= 8;
+}
+// Face kernel groups: one warp for FPG faces (two faces up to N = 4, where
+// one face has too few items per phase for 32 lanes); with one output per
+// thread four warps for one face from N = 7 on.
+template <bool L, int N>
 constexpr int face_threads() {
-  return N <= 6 ? 32 : 128;
+  return (L || N <= 6) ? 32 : 128;
 }
 template <int N>
 constexpr int faces_per_group() {
   return N <= 4 ? 2 : 1;
 }
-template <int N>
-constexpr int face_groups_per_block() {
-  return face_threads<N>() == 32 ? 4 : 1;
-}
+template <bool L, int N, int Q>
+constexpr int face_groups_per_block();
 
 // Face work space; the weighted flux (3 Q^2) reuses the first sweep's
 // region and the first test sweep (3 Q N) the face layers' (Q <= 2N).
@@ -109,6 +116,16 @@ struct FaceLayout {
   static constexpr int G2 = 6 * Q * Q;  // traces at the face points
   static constexpr int PER = T0 + G1 + G2;
 };
+// doubles of shared memory per group: the work space of its faces, plus the
+// S and SW tables with one output per thread
+template <bool L, int N, int Q>
+constexpr int face_group_smem() {
+  return faces_per_group<N>() * FaceLayout<N, Q>::PER + (L ? 0 : 2 * Q * N);
+}
+template <bool L, int N, int Q>
+constexpr int face_groups_per_block() {
+  return face_threads<L, N>() > 32 ? 1 : face_group_smem<L, N, Q>() * 8 * 4 <= 96 * 1024 ? 4 : 2;
+}
 
 
 __device__ __forceinline__ int node3(int N, int d, int a, int t1, int j1, int t2, int j2) {
@@ -135,7 +152,94 @@ struct ConvTabT {
   // NH = (N+1)/2: T1(i,x) = (T(i,x) + s T(i,N-1-x)) / 2,
   // T2(i,x) = (T(i,x) - s T(i,N-1-x)) / 2, s = -1 for DW, +1 for SW
   V EO[2][Q * ((N + 1) / 2)];
+  // interpolation to the Gauss points in even-odd form: I1 [(Q+1)/2][NH],
+  // I1(q,j) = (S(q,j) + S(q,N-1-j)) / 2 (S(q,j) in the middle column of odd
+  // N); I2 [Q/2][N/2], I2(q,j) = (S(q,j) - S(q,N-1-j)) / 2
+  V IE[((Q + 1) / 2) * ((N + 1) / 2) + (Q / 2) * (N / 2)];
 };
+
+// v(q) = sum_j S(q,j) u(j) for one line of N values (stride si) to the Q
+// Gauss points (stride so), in even-odd form: S is symmetric under the
+// reflection (q, j) -> (Q-1-q, N-1-j), so with ue = u(j) + u(N-1-j) (u(j) at
+// the middle node of odd N) and uo = u(j) - u(N-1-j), r1 = I1 ue and
+// r2 = I2 uo give v(q) = r1 + r2, v(Q-1-q) = r1 - r2 (r1 at the middle
+// point of odd Q).  I1, I2: the tables of ConvTabT::IE.
+template <class A, int N, int Q>
+__device__ __forceinline__ void interp_eo(const typename A::V* IE, const typename A::V* u, int si,
+                                          typename A::V* v, int so) {
+  typedef typename A::V V;
+  typedef typename A::Acc Acc;
+  constexpr int NH = (N + 1) / 2, NF = N / 2, QH = (Q + 1) / 2, QF = Q / 2;
+  const V* I1 = IE;
+  const V* I2 = IE + QH * NH;
+  V ue[NH], uo[NF];
+#pragma unroll
+  for (int j = 0; j < NF; ++j) {
+    const V a = u[j * si], b = u[(N - 1 - j) * si];
+    ue[j] = A::add_nr(a, b);
+    uo[j] = A::sub_nr(a, b);
+  }
+  if (N % 2 == 1) ue[NH - 1] = u[NF * si];
+#pragma unroll
+  for (int q = 0; q < QH; ++q) {
+    Acc r1;
+    A::acc_first(r1, I1[q * NH], ue[0]);
+#pragma unroll
+    for (int j = 1; j < NH; ++j) A::acc_fma(r1, I1[q * NH + j], ue[j]);
+    if (q < QF) {
+      Acc r2;
+      A::acc_first(r2, I2[q * NF], uo[0]);
+#pragma unroll
+      for (int j = 1; j < NF; ++j) A::acc_fma(r2, I2[q * NF + j], uo[j]);
+      const V a = A::acc_get(r1), b = A::acc_get(r2);
+      v[q * so] = A::add(a, b);
+      v[(Q - 1 - q) * so] = A::sub(a, b);
+    } else {
+      v[q * so] = A::acc_get_norm(r1);
+    }
+  }
+}
+
+// out(x) = sum_q SW(q,x) h(q) for one line of Q values (stride si), in
+// even-odd form (SW symmetric): he = h(q) + h(Q-1-q) (h(q) at the middle
+// point of odd Q), ho = h(q) - h(Q-1-q), r1 = T1^T he, r2 = T2^T ho give
+// out(x) = r1 + r2, out(N-1-x) = r1 - r2 (r1 at the middle node of odd N).
+// T: ConvTabT::EO[1].
+template <class A, int N, int Q>
+__device__ __forceinline__ void test_eo(const typename A::V* T, const typename A::V* h, int si,
+                                        typename A::V (&out)[N]) {
+  typedef typename A::V V;
+  typedef typename A::Acc Acc;
+  constexpr int NH = (N + 1) / 2, NF = N / 2, QH = (Q + 1) / 2, QF = Q / 2;
+  const V* T1 = T;
+  const V* T2 = T + QH * NH;
+  V he[QH], ho[QF];
+#pragma unroll
+  for (int i = 0; i < QF; ++i) {
+    const V a = h[i * si], b = h[(Q - 1 - i) * si];
+    he[i] = A::add_nr(a, b);
+    ho[i] = A::sub_nr(a, b);
+  }
+  if (Q % 2 == 1) he[QH - 1] = h[QF * si];
+#pragma unroll
+  for (int x = 0; x < NH; ++x) {
+    Acc r1;
+    A::acc_first(r1, T1[x], he[0]);
+#pragma unroll
+    for (int i = 1; i < QH; ++i) A::acc_fma(r1, T1[i * NH + x], he[i]);
+    if (x < NF) {
+      Acc r2;
+      A::acc_first(r2, T2[x], ho[0]);
+#pragma unroll
+      for (int i = 1; i < QF; ++i) A::acc_fma(r2, T2[i * NH + x], ho[i]);
+      const V a = A::acc_get(r1), b = A::acc_get(r2);
+      out[x] = A::add(a, b);
+      out[N - 1 - x] = A::sub(a, b);
+    } else {
+      out[x] = A::acc_get_norm(r1);
+    }
+  }
+}
 
 // The eight distinct x tests of a plane: test k tests F_cd = u_c u_d with
 // DW (k < 3, d = 0) or SW; the path (c, d) of the cell term reads the x test
@@ -426,30 +530,34 @@ __global__ void __launch_bounds__(conv_groups_per_block<N>() * conv_threads<N>()
 // n = +e_d, is the face integral against the '-' cell's face-layer basis;
 // the '+' cell's is -R (same trace basis, opposite normal).  Written to
 // rface[d][e][c][j1 + N j2] (j1, j2: the two tangential directions in
-// increasing order).  A group of FT threads treats FPG faces at once, so
-// that every phase has enough items for its lanes; each group keeps its own
-// copy of the two tables and synchronises only itself.
+// increasing order).  A group of FT threads treats FPG faces at once and
+// synchronises only itself; the interpolation and test phases give each
+// thread whole lines (even-odd form, tables read from the kernel parameter:
+// every thread uses the same entry at the same time).
 template <class A, int N, int Q>
-__global__ void __launch_bounds__(face_groups_per_block<N>() * face_threads<N>())
+__global__ void __launch_bounds__(face_groups_per_block<face_lines<A::emulated, N>(), N, Q>() *
+                                  face_threads<face_lines<A::emulated, N>(), N>())
     conv_face_kernel(const double* __restrict__ u3, double* __restrict__ rface,
                      const __grid_constant__ ConvTabT<typename A::V, N, Q> tb, const MeshDims m) {
   typedef typename A::V V;
   typedef typename A::Acc Acc;
   typedef FaceLayout<N, Q> LY;
-  constexpr int FT = face_threads<N>(), FPG = faces_per_group<N>(), GPB = face_groups_per_block<N>();
+  constexpr bool L = face_lines<A::emulated, N>();
+  constexpr int FT = face_threads<L, N>(), FPG = faces_per_group<N>(), GPB = face_groups_per_block<L, N, Q>();
   constexpr int N3 = N * N * N, NN = N * N, QQ = Q * Q, QN = Q * N;
   V* sm = reinterpret_cast<V*>(dyn_smem());
   const int g = threadIdx.x / FT;
   const int t = threadIdx.x - g * FT;
   const int d = blockIdx.y;
   const long long f0 = ((long long)blockIdx.x * GPB + g) * FPG;
-  V* base = sm + g * (FPG * LY::PER + 2 * QN);
-  V* sS = base + FPG * LY::PER;
+  V* base = sm + g * face_group_smem<L, N, Q>();
+  V* sS = base + FPG * LY::PER;   // one output per thread: the tables, indexed by thread
   V* sSW = sS + QN;
-  for (int i = t; i < QN; i += FT) {
-    sS[i] = tb.S[i];
-    sSW[i] = tb.SW[i];
-  }
+  if (!L)
+    for (int i = t; i < QN; i += FT) {
+      sS[i] = tb.S[i];
+      sSW[i] = tb.SW[i];
+    }
   const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
   static_assert(FPG == 1 || FPG == 2, "one or two faces per group");
   // cells of the group's faces (scalars, not an array indexed by a runtime
@@ -487,30 +595,46 @@ __global__ void __launch_bounds__(face_groups_per_block<N>() * face_threads<N>()
     FACE_T0(f)[i] = A::load(u3 + ((size_t)c * m.E + cell) * N3 + node3(N, d, sd == 0 ? N - 1 : 0, t1, j1, t2, j2));
   }
   group_sync<FT>();
-  // F1: interpolate along t1; item (sc, j2, q1)
-  for (int it = t; it < nact * 6 * QN; it += FT) {
-    const int f = it / (6 * QN), i = it - f * 6 * QN;
-    const int q1 = i % Q, r = i / Q;
-    const int sc = r / N, j2 = r - sc * N;
-    const V* v = FACE_T0(f) + sc * NN + N * j2;
-    Acc a;
-    A::acc_first(a, sS[q1 * N], v[0]);
+  // F1: interpolate along t1
+  if (L) {   // item (f, sc, j2): one line of N values -> Q
+    for (int it = t; it < nact * 6 * N; it += FT) {
+      const int f = it / (6 * N), i = it - f * 6 * N;
+      const int sc = i / N, j2 = i - sc * N;
+      interp_eo<A, N, Q>(tb.IE, FACE_T0(f) + sc * NN + N * j2, 1, FACE_G1(f) + sc * QN + Q * j2, 1);
+    }
+  } else {   // item (f, sc, j2, q1)
+    for (int it = t; it < nact * 6 * QN; it += FT) {
+      const int f = it / (6 * QN), i = it - f * 6 * QN;
+      const int q1 = i % Q, r = i / Q;
+      const int sc = r / N, j2 = r - sc * N;
+      const V* v = FACE_T0(f) + sc * NN + N * j2;
+      Acc a;
+      A::acc_first(a, sS[q1 * N], v[0]);
 #pragma unroll
-    for (int j = 1; j < N; ++j) A::acc_fma(a, sS[q1 * N + j], v[j]);
-    FACE_G1(f)[sc * QN + q1 + Q * j2] = A::acc_get_norm(a);
+      for (int j = 1; j < N; ++j) A::acc_fma(a, sS[q1 * N + j], v[j]);
+      FACE_G1(f)[sc * QN + q1 + Q * j2] = A::acc_get_norm(a);
+    }
   }
   group_sync<FT>();
-  // F2: along t2; item (sc, q1, q2)
-  for (int it = t; it < nact * 6 * QQ; it += FT) {
-    const int f = it / (6 * QQ), i = it - f * 6 * QQ;
-    const int q2 = i % Q, r = i / Q;
-    const int sc = r / Q, q1 = r - sc * Q;
-    const V* v = FACE_G1(f) + sc * QN + q1;
-    Acc a;
-    A::acc_first(a, sS[q2 * N], v[0]);
+  // F2: along t2 (the traces are compared in F3, so they are normalised)
+  if (L) {   // item (f, sc, q1)
+    for (int it = t; it < nact * 6 * Q; it += FT) {
+      const int f = it / (6 * Q), i = it - f * 6 * Q;
+      const int sc = i / Q, q1 = i - sc * Q;
+      interp_eo<A, N, Q>(tb.IE, FACE_G1(f) + sc * QN + q1, Q, FACE_G2(f) + sc * QQ + q1, Q);
+    }
+  } else {   // item (f, sc, q1, q2)
+    for (int it = t; it < nact * 6 * QQ; it += FT) {
+      const int f = it / (6 * QQ), i = it - f * 6 * QQ;
+      const int q2 = i % Q, r = i / Q;
+      const int sc = r / Q, q1 = r - sc * Q;
+      const V* v = FACE_G1(f) + sc * QN + q1;
+      Acc a;
+      A::acc_first(a, sS[q2 * N], v[0]);
 #pragma unroll
-    for (int j = 1; j < N; ++j) A::acc_fma(a, sS[q2 * N + j], v[Q * j]);
-    FACE_G2(f)[sc * QQ + q1 + Q * q2] = A::acc_get_norm(a);   // compared in F3
+      for (int j = 1; j < N; ++j) A::acc_fma(a, sS[q2 * N + j], v[Q * j]);
+      FACE_G2(f)[sc * QQ + q1 + Q * q2] = A::acc_get_norm(a);
+    }
   }
   group_sync<FT>();
   // F3: LLF flux at the face points (weights are in the test tables); item (c, point)
@@ -530,31 +654,55 @@ __global__ void __launch_bounds__(face_groups_per_block<N>() * face_threads<N>()
     FACE_G1(f)[i] = A::acc_get_norm(fl);
   }
   group_sync<FT>();
-  // F4: test along t2 (weights w_q2); item (c, j2, q1)
-  for (int it = t; it < nact * 3 * QN; it += FT) {
-    const int f = it / (3 * QN), i = it - f * 3 * QN;
-    const int q1 = i % Q, r = i / Q;
-    const int c = r / N, j2 = r - c * N;
-    const V* h = FACE_G1(f) + c * QQ + q1;
-    Acc a;
-    A::acc_first(a, sSW[j2], h[0]);
+  // F4: test along t2 (weights w_q2)
+  if (L) {   // item (f, c, q1): Q values -> N
+    for (int it = t; it < nact * 3 * Q; it += FT) {
+      const int f = it / (3 * Q), i = it - f * 3 * Q;
+      const int c = i / Q, q1 = i - c * Q;
+      V o[N];
+      test_eo<A, N, Q>(tb.EO[1], FACE_G1(f) + c * QQ + q1, Q, o);
+      V* k = FACE_T0(f) + c * QN + q1;
 #pragma unroll
-    for (int q2 = 1; q2 < Q; ++q2) A::acc_fma(a, sSW[q2 * N + j2], h[Q * q2]);
-    FACE_T0(f)[c * QN + q1 + Q * j2] = A::acc_get_norm(a);
+      for (int j2 = 0; j2 < N; ++j2) k[Q * j2] = o[j2];
+    }
+  } else {   // item (f, c, j2, q1)
+    for (int it = t; it < nact * 3 * QN; it += FT) {
+      const int f = it / (3 * QN), i = it - f * 3 * QN;
+      const int q1 = i % Q, r = i / Q;
+      const int c = r / N, j2 = r - c * N;
+      const V* h = FACE_G1(f) + c * QQ + q1;
+      Acc a;
+      A::acc_first(a, sSW[j2], h[0]);
+#pragma unroll
+      for (int q2 = 1; q2 < Q; ++q2) A::acc_fma(a, sSW[q2 * N + j2], h[Q * q2]);
+      FACE_T0(f)[c * QN + q1 + Q * j2] = A::acc_get_norm(a);
+    }
   }
   group_sync<FT>();
-  // F5: test along t1 (weights w_q1), times the face area, store; item (c, j2, j1)
+  // F5: test along t1 (weights w_q1), times the face area, store
   const V area = tb.area[d];
-  for (int it = t; it < nact * 3 * NN; it += FT) {
-    const int f = it / (3 * NN), i = it - f * 3 * NN;
-    const int c = i / NN, r = i - c * NN;
-    const int j1 = r % N, j2 = r / N;
-    const V* k = FACE_T0(f) + c * QN + Q * j2;
-    Acc a;
-    A::acc_first(a, sSW[j1], k[0]);
+  if (L) {   // item (f, c, j2)
+    for (int it = t; it < nact * 3 * N; it += FT) {
+      const int f = it / (3 * N), i = it - f * 3 * N;
+      const int c = i / N, j2 = i - c * N;
+      V o[N];
+      test_eo<A, N, Q>(tb.EO[1], FACE_T0(f) + c * QN + Q * j2, 1, o);
+      double* dst = rface + ((size_t)d * m.E + (f == 0 ? el0 : el1)) * 3 * NN + c * NN + N * j2;
 #pragma unroll
-    for (int q1 = 1; q1 < Q; ++q1) A::acc_fma(a, sSW[q1 * N + j1], k[q1]);
-    rface[((size_t)d * m.E + (f == 0 ? el0 : el1)) * 3 * NN + i] = A::store(A::mul(area, A::acc_get_norm(a)));
+      for (int j1 = 0; j1 < N; ++j1) dst[j1] = A::store(A::mul(area, o[j1]));
+    }
+  } else {   // item (f, c, j2, j1)
+    for (int it = t; it < nact * 3 * NN; it += FT) {
+      const int f = it / (3 * NN), i = it - f * 3 * NN;
+      const int c = i / NN, r = i - c * NN;
+      const int j1 = r % N, j2 = r / N;
+      const V* k = FACE_T0(f) + c * QN + Q * j2;
+      Acc a;
+      A::acc_first(a, sSW[j1], k[0]);
+#pragma unroll
+      for (int q1 = 1; q1 < Q; ++q1) A::acc_fma(a, sSW[q1 * N + j1], k[q1]);
+      rface[((size_t)d * m.E + (f == 0 ? el0 : el1)) * 3 * NN + i] = A::store(A::mul(area, A::acc_get_norm(a)));
+    }
   }
 #undef FACE_T0
 #undef FACE_G1
@@ -591,6 +739,16 @@ ConvTabT<typename A::V, N, Q> conv_tables(const ConvHost& h) {
         tb.EO[ty][i * NH + x] = A::make(i < QH ? 0.5 * (a + s * b) : 0.5 * (a - s * b));
       }
   }
+  {
+    constexpr int NF = N / 2, QF = Q / 2;
+    for (int q = 0; q < QH; ++q)
+      for (int j = 0; j < NH; ++j)
+        tb.IE[q * NH + j] =
+            A::make(j < NF ? 0.5 * (h.S[q * N + j] + h.S[q * N + N - 1 - j]) : h.S[q * N + j]);
+    for (int q = 0; q < QF; ++q)
+      for (int j = 0; j < NF; ++j)
+        tb.IE[QH * NH + q * NF + j] = A::make(0.5 * (h.S[q * N + j] - h.S[q * N + N - 1 - j]));
+  }
   return tb;
 }
 
@@ -600,10 +758,11 @@ template <class A, int N, int Q>
 int launch_conv(int part, const MeshDims& m, const double* u3, double* rface, double* dst3, const ConvHost& h,
                 cudaStream_t s) {
   const ConvTabT<typename A::V, N, Q> tb = conv_tables<A, N, Q>(h);
-  constexpr int EPB = conv_fwd_cells_per_block<N>(), GPB = face_groups_per_block<N>(), FPG = faces_per_group<N>();
+  constexpr bool FL = face_lines<A::emulated, N>();
+  constexpr int EPB = conv_fwd_cells_per_block<N>(), GPB = face_groups_per_block<FL, N, Q>(), FPG = faces_per_group<N>();
   constexpr int FPB = GPB * FPG;
   const size_t smem = ((size_t)EPB * ConvLayout<N, Q>::PER + 6 * Q * N + 2 * Q * ((N + 1) / 2)) * sizeof(double);
-  const size_t fsmem = (size_t)GPB * (FPG * FaceLayout<N, Q>::PER + 2 * Q * N) * sizeof(double);
+  const size_t fsmem = (size_t)GPB * face_group_smem<FL, N, Q>() * sizeof(double);
   if (smem > 232448 || fsmem > 232448) return 7;
   if (cudaFuncSetAttribute(conv_kernel<A, N, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
           cudaSuccess ||
@@ -613,7 +772,7 @@ int launch_conv(int part, const MeshDims& m, const double* u3, double* rface, do
   if (m.E == 0) return 0;
   if (part & 1) {
     const dim3 fgrid((unsigned)((m.E + FPB - 1) / FPB), 3);
-    conv_face_kernel<A, N, Q><<<fgrid, GPB * face_threads<N>(), fsmem, s>>>(u3, rface, tb, m);
+    conv_face_kernel<A, N, Q><<<fgrid, GPB * face_threads<FL, N>(), fsmem, s>>>(u3, rface, tb, m);
   }
   if (part & 2) {
     const long long blocks = (m.E + EPB - 1) / EPB;
