@@ -49,11 +49,11 @@ FP32_PEAK_TFLOPS = 80.6   # 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz (probe: 73
 # two-sum and two adds (8 FADD) = 15 FP32 flops.
 DF_FP32_PER_FP64 = 7.5
 # DRAM bytes (read + write) of one launch of the dominant kernel, from one ncu
-# capture of the same workload (profiles/convective_k3_32c_face_cell_ncu.md),
+# capture of the same workload (dram__bytes_read.sum + dram__bytes_write.sum),
 # keyed by (kernel, fp64_mode); None where no capture of the current kernel
 # exists.
-KERNEL_TRAFFIC = {("conv_kernel", 1): None, ("conv_kernel", 0): None,
-                  ("conv_face_kernel", 1): None, ("conv_face_kernel", 0): None}
+KERNEL_TRAFFIC = {("conv_kernel", 1): 105.6e6, ("conv_kernel", 0): None,
+                  ("conv_face_kernel", 1): 57.2e6, ("conv_face_kernel", 0): None}
 
 
 # ----------------------------------------------------------- flop counts
