@@ -25,12 +25,56 @@
 namespace dgns {
 namespace {
 
+// Even-odd form of a centrosymmetric N x N matrix C (C(N-1-i, N-1-j) =
+// C(i, j), as the 1D mass matrix and the cell part of the 1D SIPG operator
+// on the symmetric LGL nodes): with xe(j) = x(j) + x(N-1-j) (x(j) at the
+// middle node of odd N) and xo(j) = x(j) - x(N-1-j), e = E xe, o = O xo give
+// y(i) = e(i) + o(i), y(N-1-i) = e(i) - o(i), y(middle) = e(middle);
+// E(i,j) = (C(i,j) + C(i,N-1-j)) / 2 (C(i,middle) in the middle column),
+// O(i,j) = (C(i,j) - C(i,N-1-j)) / 2.  About N^2/2 instead of N^2
+// multiply-adds per line, for 2N additions.
+template <class V, int N>
+struct EOMat {
+  V E[((N + 1) / 2) * ((N + 1) / 2)];
+  V O[(N / 2) * (N / 2)];
+};
+
 template <class V, int N>
 struct LapTab {
   V A0[3][N * N];
   V M[N * N];
   V cr[3][N], cl[3][N], gr[3][N], gl[3][N];
+  // even-odd forms (double-float sweeps): A0 and M, and the neighbour
+  // coupling columns cr, cl split the same way (vE(i) = (v(i) + v(N-1-i)) / 2,
+  // v(middle) at the middle, vO(i) = (v(i) - v(N-1-i)) / 2)
+  EOMat<V, N> A0eo[3], Meo;
+  V crE[3][(N + 1) / 2], crO[3][N / 2], clE[3][(N + 1) / 2], clO[3][N / 2];
 };
+
+// Double-float sweeps use the even-odd form; natively (FP64-pipe bound) and in
+// FP32 (the multigrid level operator, bound by the L1/shared-memory pipe) an
+// addition costs as much as a multiply-add and the direct form is kept.
+template <class A, int N>
+constexpr bool eo_sweeps() {
+  return A::emulated;
+}
+// even-odd sweeps from N = 7 on loop over their output pairs (code size)
+template <int N>
+constexpr bool eo_roll() {
+  return N >= 7;
+}
+
+// Fold of a line into its even and odd parts.
+template <class A, int N>
+__device__ __forceinline__ void eo_fold(const typename A::V (&x)[N], typename A::V (&xe)[(N + 1) / 2],
+                                        typename A::V (&xo)[N / 2]) {
+#pragma unroll
+  for (int j = 0; j < N / 2; ++j) {
+    xe[j] = A::add_nr(x[j], x[N - 1 - j]);
+    xo[j] = A::sub_nr(x[j], x[N - 1 - j]);
+  }
+  if (N % 2 == 1) xe[N / 2] = x[N / 2];
+}
 
 template <class G>
 struct EpiArgs {
@@ -88,6 +132,59 @@ constexpr bool roll_outputs() {
   return A::emulated && N >= 5;
 }
 
+// One line of T_d x in even-odd form, the neighbour lines r (+ side) and lf
+// (- side) in registers: the coupling through the neighbours' face values
+// (cr r(0) + cl lf(N-1)) goes into the even and odd sums, the coupling
+// through their face derivatives (gr . r into y(N-1), gl . lf into y(0))
+// is added to the outer pair.
+template <class A, int N, int D>
+__device__ __forceinline__ void sipg_line_eo(const typename A::V* X, typename A::V* out,
+                                             const typename A::V (&r)[N], const typename A::V (&lf)[N], int l,
+                                             const LapTab<typename A::V, N>& tb) {
+  typedef typename A::V V;
+  typedef typename A::Acc Acc;
+  constexpr int NH = (N + 1) / 2, NF = N / 2;
+  int base, stride;
+  sline<N, D>(l, base, stride);
+  V x[N], xe[NH], xo[NF];
+  load_line<V, N>(X, base, stride, x);
+  eo_fold<A, N>(x, xe, xo);
+  const V r0 = r[0], ln = lf[N - 1];
+#pragma unroll(eo_roll<N>() ? 1 : NH)
+  for (int i = 0; i < NH; ++i) {
+    Acc e;
+    A::acc_first(e, tb.crE[D][i], r0);
+    A::acc_fma(e, tb.clE[D][i], ln);
+#pragma unroll
+    for (int j = 0; j < NH; ++j) A::acc_fma(e, tb.A0eo[D].E[i * NH + j], xe[j]);
+    if (i < NF) {
+      Acc o;
+      A::acc_first(o, tb.crO[D][i], r0);
+      A::acc_fma(o, tb.clO[D][i], ln);
+#pragma unroll
+      for (int j = 0; j < NF; ++j) A::acc_fma(o, tb.A0eo[D].O[i * NF + j], xo[j]);
+      const V a = A::acc_get(e), b = A::acc_get(o);
+      V lo = A::add_nr(a, b), hi = A::sub_nr(a, b);
+      if (i == 0) {
+        Acc t, u;
+        A::acc_set(t, lo);
+        A::acc_set(u, hi);
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          A::acc_fma(t, tb.gl[D][j], lf[j]);
+          A::acc_fma(u, tb.gr[D][j], r[j]);
+        }
+        lo = A::acc_get(t);
+        hi = A::acc_get(u);
+      }
+      out[base + i * stride] = lo;
+      out[base + (N - 1 - i) * stride] = hi;
+    } else {
+      out[base + i * stride] = A::acc_get(e);
+    }
+  }
+}
+
 // One line of T_d x for the own cell, with the neighbour terms.
 template <class A, int N, int D>
 __device__ __forceinline__ void sipg_line(const typename A::V* X, typename A::V* out,
@@ -101,12 +198,16 @@ __device__ __forceinline__ void sipg_line(const typename A::V* X, typename A::V*
   line_geom<D>(l, N, N, N, gbase, gstride);
   V x[N], r[N], lf[N];
   Acc y[N];
-  load_line<V, N>(X, base, stride, x);
 #pragma unroll
   for (int j = 0; j < N; ++j) {
     r[j] = A::load(nbR + gbase + j * gstride);
     lf[j] = A::load(nbL + gbase + j * gstride);
   }
+  if constexpr (eo_sweeps<A, N>()) {
+    sipg_line_eo<A, N, D>(X, out, r, lf, l, tb);
+    return;
+  }
+  load_line<V, N>(X, base, stride, x);
   if constexpr (roll_outputs<A, N>()) {
 #pragma unroll 1
     for (int i = 0; i < N; ++i) {
@@ -148,6 +249,10 @@ __device__ __forceinline__ void sipg_line_pre(const typename A::V* X, typename A
                                               const LapTab<typename A::V, N>& tb) {
   typedef typename A::V V;
   typedef typename A::Acc Acc;
+  if constexpr (eo_sweeps<A, N>()) {
+    sipg_line_eo<A, N, D>(X, out, r, lf, l, tb);
+    return;
+  }
   int base, stride;
   sline<N, D>(l, base, stride);
   V x[N];
@@ -219,18 +324,49 @@ constexpr bool prefetch_neighbours() {
   return N <= 6;
 }
 
-// One line of out = M_d in (+ add).
+// One line of out = M_d in (+ add); in and out may coincide (the line is
+// read whole before it is written).
 template <class A, int N, int D, bool ADD>
 __device__ __forceinline__ void mass_line(const typename A::V* in, const typename A::V* add,
-                                          typename A::V* out, int l, const typename A::V* M) {
+                                          typename A::V* out, int l, const LapTab<typename A::V, N>& tb) {
   typedef typename A::V V;
   typedef typename A::Acc Acc;
+  const V* M = tb.M;
   int base, stride;
   sline<N, D>(l, base, stride);
   V x[N];
   Acc y[N];
   load_line<V, N>(in, base, stride, x);
-  if constexpr (roll_outputs<A, N>()) {
+  if constexpr (eo_sweeps<A, N>()) {
+    constexpr int NH = (N + 1) / 2, NF = N / 2;
+    V xe[NH], xo[NF];
+    eo_fold<A, N>(x, xe, xo);
+#pragma unroll(eo_roll<N>() ? 1 : NH)
+    for (int i = 0; i < NH; ++i) {
+      Acc e;
+      A::acc_first(e, tb.Meo.E[i * NH], xe[0]);
+#pragma unroll
+      for (int j = 1; j < NH; ++j) A::acc_fma(e, tb.Meo.E[i * NH + j], xe[j]);
+      if (i < NF) {
+        Acc o;
+        A::acc_first(o, tb.Meo.O[i * NF], xo[0]);
+#pragma unroll
+        for (int j = 1; j < NF; ++j) A::acc_fma(o, tb.Meo.O[i * NF + j], xo[j]);
+        const V a = A::acc_get(e), b = A::acc_get(o);
+        V lo = A::add_nr(a, b), hi = A::sub_nr(a, b);
+        if (ADD) {
+          lo = A::add_nr(lo, add[base + i * stride]);
+          hi = A::add_nr(hi, add[base + (N - 1 - i) * stride]);
+        }
+        out[base + i * stride] = lo;
+        out[base + (N - 1 - i) * stride] = hi;
+      } else {
+        V v = A::acc_get(e);
+        if (ADD) v = A::add_nr(v, add[base + i * stride]);
+        out[base + i * stride] = v;
+      }
+    }
+  } else if constexpr (roll_outputs<A, N>()) {
 #pragma unroll 1
     for (int i = 0; i < N; ++i) {
       Acc yi;
@@ -347,16 +483,16 @@ __global__ void __launch_bounds__(cells_per_block<N>() * N * N)
   }
   __syncthreads();
   if (active) {
-    mass_line<A, N, 0, false>(sB + off, nullptr, sB + off, l, tb.M);  // M_x T_y x
-    mass_line<A, N, 1, false>(sC + off, nullptr, sC + off, l, tb.M);  // M_y T_z x
+    mass_line<A, N, 0, false>(sB + off, nullptr, sB + off, l, tb);  // M_x T_y x
+    mass_line<A, N, 1, false>(sC + off, nullptr, sC + off, l, tb);  // M_y T_z x
   }
   __syncthreads();
   if (active) {
-    mass_line<A, N, 1, true>(sA + off, sB + off, sA + off, l, tb.M);  // M_y T_x x + M_x T_y x
-    mass_line<A, N, 0, false>(sC + off, nullptr, sC + off, l, tb.M);  // M_x M_y T_z x
+    mass_line<A, N, 1, true>(sA + off, sB + off, sA + off, l, tb);  // M_y T_x x + M_x T_y x
+    mass_line<A, N, 0, false>(sC + off, nullptr, sC + off, l, tb);  // M_x M_y T_z x
   }
   __syncthreads();
-  if (active) mass_line<A, N, 2, true>(sA + off, sC + off, sB + off, l, tb.M);
+  if (active) mass_line<A, N, 2, true>(sA + off, sC + off, sB + off, l, tb);
   __syncthreads();
   // each thread writes its own x-line of the result
   if (active) {
@@ -442,6 +578,28 @@ int launch_sipg(const MeshDims& m, int ncomp, const typename A::G* src, typename
     }
   }
   for (int i = 0; i < NN; ++i) tb.M[i] = A::make(h.M[i]);
+  {
+    constexpr int NH = (N + 1) / 2, NF = N / 2;
+    auto split = [&](const double* C, EOMat<typename A::V, N>& eo) {
+      for (int i = 0; i < NH; ++i)
+        for (int j = 0; j < NH; ++j)
+          eo.E[i * NH + j] = A::make(j < NF ? 0.5 * (C[i * N + j] + C[i * N + N - 1 - j]) : C[i * N + j]);
+      for (int i = 0; i < NF; ++i)
+        for (int j = 0; j < NF; ++j) eo.O[i * NF + j] = A::make(0.5 * (C[i * N + j] - C[i * N + N - 1 - j]));
+    };
+    for (int d = 0; d < 3; ++d) {
+      split(h.A0[d], tb.A0eo[d]);
+      for (int i = 0; i < NH; ++i) {
+        tb.crE[d][i] = A::make(i < NF ? 0.5 * (h.cr[d][i] + h.cr[d][N - 1 - i]) : h.cr[d][i]);
+        tb.clE[d][i] = A::make(i < NF ? 0.5 * (h.cl[d][i] + h.cl[d][N - 1 - i]) : h.cl[d][i]);
+      }
+      for (int i = 0; i < NF; ++i) {
+        tb.crO[d][i] = A::make(0.5 * (h.cr[d][i] - h.cr[d][N - 1 - i]));
+        tb.clO[d][i] = A::make(0.5 * (h.cl[d][i] - h.cl[d][N - 1 - i]));
+      }
+    }
+    split(h.M, tb.Meo);
+  }
   EpiArgs<G> ea{(const G*)eh.b, (const G*)eh.xprev, (const G*)eh.dinv, (G)eh.c1, (G)eh.c2};
   const long long ncells = m.E * ncomp;
   if (ncells == 0) return 0;
