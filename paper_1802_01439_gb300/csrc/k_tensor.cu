@@ -4,6 +4,9 @@
 // the Kronecker product of the 1D inverses, three sweeps per cell), and the
 // h-multigrid transfers (embedding of a coarse cell polynomial into its eight
 // children and the transpose).
+#include <algorithm>
+#include <cmath>
+
 #include "arith.cuh"
 #include "ops.h"
 
@@ -18,6 +21,16 @@ constexpr int tcells_per_block() {
 template <class V, int N>
 struct Tens3 {
   V Mx[N * N], My[N * N], Mz[N * N];
+  // even-odd forms of the three matrices (double-float sweeps of
+  // centrosymmetric matrices, C(N-1-i, N-1-j) = C(i, j), as the 1D mass
+  // matrix and its inverse on the symmetric LGL nodes): with
+  // xe(j) = x(j) + x(N-1-j) (x(j) at the middle of odd N) and
+  // xo(j) = x(j) - x(N-1-j), e = E xe and o = O xo give y(i) = e(i) + o(i),
+  // y(N-1-i) = e(i) - o(i), y(middle) = e(middle), with
+  // E(i,j) = (C(i,j) + C(i,N-1-j)) / 2 (C(i,middle) in the middle column) and
+  // O(i,j) = (C(i,j) - C(i,N-1-j)) / 2
+  V E[3][((N + 1) / 2) * ((N + 1) / 2)];
+  V O[3][(N / 2) * (N / 2)];
 };
 
 template <class T, int N, int D>
@@ -50,7 +63,45 @@ __device__ __forceinline__ void sweep_line_p(const typename A::V* in, typename A
   for (int i = 0; i < N; ++i) out[base + i * stride] = A::acc_get(y[i]);
 }
 
-template <class A, int N>
+template <class A, int N, int D>
+__device__ __forceinline__ void sweep_line_eo(const typename A::V* in, typename A::V* out, int l,
+                                              const typename A::V* E, const typename A::V* O) {
+  typedef typename A::V V;
+  typedef typename A::Acc Acc;
+  constexpr int NH = (N + 1) / 2, NF = N / 2;
+  int base, stride;
+  line_geom<D>(l, N, N, N, base, stride);
+  V x[N], xe[NH], xo[NF];
+  load_line<V, N>(in, base, stride, x);
+#pragma unroll
+  for (int j = 0; j < NF; ++j) {
+    xe[j] = A::add_nr(x[j], x[N - 1 - j]);
+    xo[j] = A::sub_nr(x[j], x[N - 1 - j]);
+  }
+  if (N % 2 == 1) xe[NF] = x[NF];
+#pragma unroll
+  for (int i = 0; i < NH; ++i) {
+    Acc e;
+    A::acc_first(e, E[i * NH], xe[0]);
+#pragma unroll
+    for (int j = 1; j < NH; ++j) A::acc_fma(e, E[i * NH + j], xe[j]);
+    if (i < NF) {
+      Acc o;
+      A::acc_first(o, O[i * NF], xo[0]);
+#pragma unroll
+      for (int j = 1; j < NF; ++j) A::acc_fma(o, O[i * NF + j], xo[j]);
+      const V a = A::acc_get(e), b = A::acc_get(o);
+      out[base + i * stride] = A::add_nr(a, b);
+      out[base + (N - 1 - i) * stride] = A::sub_nr(a, b);
+    } else {
+      out[base + i * stride] = A::acc_get(e);
+    }
+  }
+}
+
+// EO: the sweeps in even-odd form (double-float arithmetic, centrosymmetric
+// matrices); natively an addition costs as much as a multiply-add.
+template <class A, int N, bool EO>
 __global__ void __launch_bounds__(tcells_per_block<N>() * N * N)
     tensor3_kernel(const typename A::G* __restrict__ src, typename A::G* __restrict__ dst,
                    const __grid_constant__ Tens3<typename A::V, N> tb, const long long ncells) {
@@ -67,11 +118,19 @@ __global__ void __launch_bounds__(tcells_per_block<N>() * N * N)
   __syncthreads();
   const bool active = slot < nvalid;
   const int off = slot * NNN;
-  if (active) sweep_line_p<A, N, 0>(sX + off, sA + off, l, tb.Mx);
-  __syncthreads();
-  if (active) sweep_line_p<A, N, 1>(sA + off, sA + off, l, tb.My);
-  __syncthreads();
-  if (active) sweep_line_p<A, N, 2>(sA + off, sX + off, l, tb.Mz);
+  if constexpr (EO) {
+    if (active) sweep_line_eo<A, N, 0>(sX + off, sA + off, l, tb.E[0], tb.O[0]);
+    __syncthreads();
+    if (active) sweep_line_eo<A, N, 1>(sA + off, sA + off, l, tb.E[1], tb.O[1]);
+    __syncthreads();
+    if (active) sweep_line_eo<A, N, 2>(sA + off, sX + off, l, tb.E[2], tb.O[2]);
+  } else {
+    if (active) sweep_line_p<A, N, 0>(sX + off, sA + off, l, tb.Mx);
+    __syncthreads();
+    if (active) sweep_line_p<A, N, 1>(sA + off, sA + off, l, tb.My);
+    __syncthreads();
+    if (active) sweep_line_p<A, N, 2>(sA + off, sX + off, l, tb.Mz);
+  }
   __syncthreads();
   for (int i = threadIdx.x; i < nvalid * NNN; i += blockDim.x) dst[c0 * NNN + i] = A::store(sX[i]);
 }
@@ -79,24 +138,49 @@ __global__ void __launch_bounds__(tcells_per_block<N>() * N * N)
 template <class A, int N>
 int launch_tensor3(long long ncells, const double* src, double* dst, const double* Mx, const double* My,
                    const double* Mz, cudaStream_t s) {
-  constexpr int NN = N * N, EPB = tcells_per_block<N>();
+  constexpr int NN = N * N, EPB = tcells_per_block<N>(), NH = (N + 1) / 2, NF = N / 2;
   Tens3<typename A::V, N> tb;
   for (int i = 0; i < NN; ++i) {
     tb.Mx[i] = A::make(Mx[i]);
     tb.My[i] = A::make(My[i]);
     tb.Mz[i] = A::make(Mz[i]);
   }
+  // even-odd sweeps for double-float arithmetic when all three matrices are
+  // centrosymmetric (to 1e-14 of their largest entry)
+  bool eo = A::emulated;
+  const double* Ms[3] = {Mx, My, Mz};
+  for (int d = 0; d < 3 && eo; ++d) {
+    double mx = 0.0, dev = 0.0;
+    for (int i = 0; i < NN; ++i) {
+      mx = std::max(mx, std::fabs(Ms[d][i]));
+      dev = std::max(dev, std::fabs(Ms[d][i] - Ms[d][NN - 1 - i]));   // C(N-1-i, N-1-j) is entry NN-1-(iN+j)
+    }
+    if (dev > 1e-14 * mx) eo = false;
+  }
+  for (int d = 0; d < 3; ++d) {
+    const double* C = Ms[d];
+    for (int i = 0; i < NH; ++i)
+      for (int j = 0; j < NH; ++j)
+        tb.E[d][i * NH + j] = A::make(j < NF ? 0.5 * (C[i * N + j] + C[i * N + N - 1 - j]) : C[i * N + j]);
+    for (int i = 0; i < NF; ++i)
+      for (int j = 0; j < NF; ++j) tb.O[d][i * NF + j] = A::make(0.5 * (C[i * N + j] - C[i * N + N - 1 - j]));
+  }
   if (ncells == 0) return 0;
   const size_t smem = (size_t)2 * EPB * NN * N * sizeof(double);
   static bool attr_done = false;
   if (!attr_done) {
-    if (cudaFuncSetAttribute(tensor3_kernel<A, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(tensor3_kernel<A, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess ||
+        cudaFuncSetAttribute(tensor3_kernel<A, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
       return 2;
     attr_done = true;
   }
   const long long blocks = (ncells + EPB - 1) / EPB;
-  tensor3_kernel<A, N><<<(unsigned)blocks, EPB * NN, smem, s>>>(src, dst, tb, ncells);
+  if (eo)
+    tensor3_kernel<A, N, true><<<(unsigned)blocks, EPB * NN, smem, s>>>(src, dst, tb, ncells);
+  else
+    tensor3_kernel<A, N, false><<<(unsigned)blocks, EPB * NN, smem, s>>>(src, dst, tb, ncells);
   return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }
 
