@@ -147,6 +147,7 @@ struct ConvTabT {
   V SW[Q * N];      // w_q phi_j(x_q): test with phi
   V DW[Q * N];      // w_q phi_j'(x_q): test with phi'
   V TY[3][Q * N];   // y test of flux direction d: jac_d SW (d = 0, 2) or jac_d DW (d = 1)
+  V TYeo[3][Q * ((N + 1) / 2)];   // the same in even-odd form (layout of EO below)
   V area[3];        // h_x h_y h_z / h_d: face area of faces normal to d
   // x tests in even-odd form, [DW, SW][T1: (Q+1)/2 x NH | T2: Q/2 x NH],
   // NH = (N+1)/2: T1(i,x) = (T(i,x) + s T(i,N-1-x)) / 2,
@@ -248,6 +249,56 @@ __device__ __forceinline__ int test_c(int k) { return k < 3 ? k : (k == 3 || k =
 __device__ __forceinline__ int test_d(int k) { return k < 3 ? 0 : (k < 5 ? 1 : 2); }
 __device__ __forceinline__ int xtest2(int c) { return c == 0 ? 6 : (c == 1 ? 5 : 7); }  // path (c, 2)
 
+// x tests of the rows qy and Q-1-qy in one work item, stored folded along y
+// (sums and differences), so that the y tests run in even-odd form too: one
+// item per output pair and half the multiply-adds.  It halves the number of
+// x-test items with twice the work each; measured: 3 % faster at N = 4,
+// 5-13 % slower at N = 2, 5, 6 (more registers per lane), no gain where the
+// unpaired items fit in one round of the lanes.
+template <int N>
+constexpr bool conv_pair_rows() {
+  return N == 4;
+}
+
+// x test of one row of the plane (Q points u_c u_d -> N outputs) in even-odd
+// form with the tables T1 (x fe, (Q+1)/2 rows) and T2 (x fo, Q/2 rows):
+// out(x) = r1 + r2, out(N-1-x) = s (r1 - r2) (s = -1 for the antisymmetric
+// DW), out(middle) = r1 + r2; outputs not renormalised.
+template <class A, int N, int Q>
+__device__ __forceinline__ void xtest_row(const typename A::V* T1, const typename A::V* T2, bool anti,
+                                          const typename A::V* uc, const typename A::V* ud,
+                                          typename A::V (&out)[N]) {
+  typedef typename A::V V;
+  typedef typename A::Acc Acc;
+  constexpr int QH = (Q + 1) / 2, QF = Q / 2, NH = (N + 1) / 2, NF = N / 2;
+  V fe[QH], fo[QF];
+#pragma unroll
+  for (int i = 0; i < QF; ++i) {
+    const V f1 = A::mul_nr(uc[i], ud[i]), f2 = A::mul_nr(uc[Q - 1 - i], ud[Q - 1 - i]);
+    fe[i] = A::add_nr(f1, f2);
+    fo[i] = A::sub_nr(f1, f2);
+  }
+  if (Q % 2 == 1) fe[QH - 1] = A::mul_nr(uc[QF], ud[QF]);
+#pragma unroll
+  for (int x = 0; x < NH; ++x) {
+    Acc r1, r2;
+    A::acc_first(r1, T1[x], fe[0]);
+#pragma unroll
+    for (int i = 1; i < QH; ++i) A::acc_fma(r1, T1[i * NH + x], fe[i]);
+    A::acc_first(r2, T2[x], fo[0]);
+#pragma unroll
+    for (int i = 1; i < QF; ++i) A::acc_fma(r2, T2[i * NH + x], fo[i]);
+    const V a = A::acc_get(r1), b = A::acc_get(r2);
+    if (x < NF) {
+      out[x] = A::add_nr(a, b);
+      const V d = A::sub_nr(a, b);
+      out[N - 1 - x] = anti ? A::neg(d) : d;
+    } else {
+      out[x] = A::add_nr(a, b);
+    }
+  }
+}
+
 // i-th of up to two values, selected without an indexed local array
 __device__ __forceinline__ unsigned pick2(int i, unsigned a, unsigned b) { return i == 0 ? a : b; }
 
@@ -275,7 +326,8 @@ __global__ void __launch_bounds__(conv_groups_per_block<N>() * conv_threads<N>()
   const long long c0 = ((long long)blockIdx.x * conv_groups_per_block<N>() + g) * CPG;
   const long long last = m.E - 1;
   constexpr int QH = (Q + 1) / 2, QF = Q / 2, NH = (N + 1) / 2, NF = N / 2;
-  V* sS = sm + conv_fwd_cells_per_block<N>() * LY::PER;   // tables: S, SW, DW, TY[0..2], EO[0..1]
+  constexpr bool PR = conv_pair_rows<N>();
+  V* sS = sm + conv_fwd_cells_per_block<N>() * LY::PER;   // tables: S, SW, DW, TY[0..2] (or TYeo), EO[0..1]
   V* sSW = sS + QN;
   V* sDW = sSW + QN;
   V* sTY = sDW + QN;
@@ -284,10 +336,14 @@ __global__ void __launch_bounds__(conv_groups_per_block<N>() * conv_threads<N>()
     sS[i] = tb.S[i];
     sSW[i] = tb.SW[i];
     sDW[i] = tb.DW[i];
-    sTY[i] = tb.TY[0][i];
-    sTY[QN + i] = tb.TY[1][i];
-    sTY[2 * QN + i] = tb.TY[2][i];
+    if (!PR) {
+      sTY[i] = tb.TY[0][i];
+      sTY[QN + i] = tb.TY[1][i];
+      sTY[2 * QN + i] = tb.TY[2][i];
+    }
   }
+  if (PR)
+    for (int i = threadIdx.x; i < 3 * Q * NH; i += blockDim.x) sTY[i] = tb.TYeo[i / (Q * NH)][i % (Q * NH)];
   for (int i = threadIdx.x; i < Q * NH; i += blockDim.x) {
     sEO[i] = tb.EO[0][i];
     sEO[Q * NH + i] = tb.EO[1][i];
@@ -358,12 +414,14 @@ __global__ void __launch_bounds__(conv_groups_per_block<N>() * conv_threads<N>()
   // The plane loop: every lane keeps the same work items in all planes, so
   // their offsets are computed once; the lane's outputs (items of P4) stay
   // in registers until the end.
-  constexpr int I1 = CPG * 3 * QQ, I2 = CPG * 8 * Q, I3 = CPG * 3 * NN, I4 = CPG * 3 * N3;
+  constexpr int I1 = CPG * 3 * QQ, I2 = CPG * 8 * (PR ? QH : Q), I3 = CPG * 3 * N * (PR ? NH : N),
+                I4 = CPG * 3 * N3;
   constexpr int R1 = (I1 + NT - 1) / NT, R2 = (I2 + NT - 1) / NT, R3 = (I3 + NT - 1) / NT,
                 R4 = (I4 + NT - 1) / NT;
   int o1[R1];                                  // P1: offset of the z column in sU2g
-  int o2t[R2], o2c[R2], o2d[R2];               // P2: table, u_c, u_d offsets
-  int o3a[R3], o3y[R3];                        // P3: X(c,0) offset in sXg; y + 16 (xtest2(c) - c)
+  int o2t[R2], o2c[R2], o2d[R2], o2x[R2];      // P2: table, u_c, u_d offsets of the row, output offset
+  int o2b[R2];                                 // P2 (paired rows): offset of row Q-1-qy from row qy (0: middle)
+  int o3a[R3], o3y[R3], o3o[R3];               // P3: X(c,0) + x in sXg; y (pair) + 16 (xtest2(c) - c); Y1 + x in sYg
   int o4y[R4], o4z[R4];                        // P4: offset into sYg, z
 #pragma unroll
   for (int r = 0; r < R1; ++r) {
@@ -373,20 +431,28 @@ __global__ void __launch_bounds__(conv_groups_per_block<N>() * conv_threads<N>()
   }
 #pragma unroll
   for (int r = 0; r < R2; ++r) {
+    // item (j, k, row): with paired rows the row p < QH stands for p and Q-1-p
+    constexpr int RW = PR ? QH : Q;
     const int it = t + NT * r;
-    const int j = it / (8 * Q), l = it - j * 8 * Q;
-    const int k = l / Q, qy = l - k * Q;
+    const int j = it / (8 * RW), l = it - j * 8 * RW;
+    const int k = l / RW, p = l - k * RW;
     o2t[r] = k < 3 ? 0 : Q * NH;    // even-odd DW or SW tables, relative to sEO
-    o2c[r] = j * LY::P + test_c(k) * QQ + Q * qy;
-    o2d[r] = j * LY::P + test_d(k) * QQ + Q * qy;
+    o2c[r] = j * LY::P + test_c(k) * QQ + Q * p;
+    o2d[r] = j * LY::P + test_d(k) * QQ + Q * p;
+    o2b[r] = Q * (Q - 1 - 2 * p);
+    o2x[r] = ((j * 8 + k) * Q + p) * N;
   }
 #pragma unroll
   for (int r = 0; r < R3; ++r) {
+    // item (j, c, y, x), with paired rows y < NH stands for y and N-1-y
+    constexpr int YW = PR ? NH : N;
     const int it = t + NT * r;
-    const int j = it / (3 * NN), l = it - j * 3 * NN;
-    const int c = l / NN, rr = l - c * NN;
-    o3a[r] = j * 8 * QN + c * QN + rr % N;
-    o3y[r] = rr / N + 16 * (xtest2(c) - c);
+    const int j = it / (3 * N * YW), l = it - j * 3 * N * YW;
+    const int c = l / (N * YW), rr = l - c * N * YW;
+    const int x = rr % N, y = rr / N;
+    o3a[r] = (j * 8 + c) * QN + x;
+    o3y[r] = y + 16 * (xtest2(c) - c);
+    o3o[r] = (j * 3 + c) * 2 * NN + x;
   }
 #pragma unroll
   for (int r = 0; r < R4; ++r) {
@@ -397,9 +463,6 @@ __global__ void __launch_bounds__(conv_groups_per_block<N>() * conv_threads<N>()
     o4z[r] = rr / NN;
   }
   Acc out[R4];
-  // the inner point loops of P2 and P3 are unrolled, except for N = 5 and 6
-  // (k = 4, 5), where the rolled loops measured 5 % faster
-  constexpr int UQ = (N == 5 || N == 6) ? 1 : Q;
 
 #pragma unroll 1
   for (int qz = 0; qz < Q; ++qz) {
@@ -415,73 +478,106 @@ __global__ void __launch_bounds__(conv_groups_per_block<N>() * conv_threads<N>()
       sPg[t + NT * r] = A::acc_get_norm(a);
     }
     group_sync<NT>();
-    // P2: F_cd = u_c u_d on x-lines, x test k; item (j, k, qy).  Even-odd
-    // form: SW is symmetric and DW antisymmetric under the reflection
-    // (q, x) -> (Q-1-q, N-1-x) of the Gauss points and nodes, so with
-    // fe = f(q) + f(Q-1-q) (fe = f(q) at the middle point of odd Q) and
-    // fo = f(q) - f(Q-1-q) the test is two half-size contractions
-    // r1 = T1^T fe, r2 = T2^T fo, and out(x) = r1 + r2,
-    // out(N-1-x) = s (r1 - r2), out(middle) = r1 + r2 (one of them zero).
+    // P2: F_cd = u_c u_d on x-lines, x test k in even-odd form (xtest_row:
+    // SW is symmetric and DW antisymmetric under the reflection
+    // (q, x) -> (Q-1-q, N-1-x) of the Gauss points and nodes).  With paired
+    // rows an item tests the rows p and Q-1-p and stores their sum in row p
+    // and their difference in row (Q+1)/2 + p of the test's block (the
+    // middle row of odd Q alone, in row p); else one row per item.
 #pragma unroll
     for (int r = 0; r < R2; ++r) {
       const int it = t + NT * r;
       if (I2 % NT != 0 && it >= I2) break;
       const V* T1 = sEO + o2t[r];
       const V* T2 = T1 + QH * NH;
-      const V* uc = sPg + o2c[r];
-      const V* ud = sPg + o2d[r];
-      V fe[QH], fo[QF];
-#pragma unroll
-      for (int i = 0; i < QF; ++i) {
-        const V f1 = A::mul_nr(uc[i], ud[i]), f2 = A::mul_nr(uc[Q - 1 - i], ud[Q - 1 - i]);
-        fe[i] = A::add_nr(f1, f2);
-        fo[i] = A::sub_nr(f1, f2);
-      }
-      if (Q % 2 == 1) fe[QH - 1] = A::mul_nr(uc[QF], ud[QF]);
-      Acc r1[NH], r2[NH];
-#pragma unroll
-      for (int x = 0; x < NH; ++x) {
-        A::acc_first(r1[x], T1[x], fe[0]);
-#pragma unroll
-        for (int i = 1; i < QH; ++i) A::acc_fma(r1[x], T1[i * NH + x], fe[i]);
-        A::acc_first(r2[x], T2[x], fo[0]);
-#pragma unroll
-        for (int i = 1; i < QF; ++i) A::acc_fma(r2[x], T2[i * NH + x], fo[i]);
-      }
-      V* xo = sXg + it * N;
       const bool anti = o2t[r] == 0;
+      V xa[N];
+      xtest_row<A, N, Q>(T1, T2, anti, sPg + o2c[r], sPg + o2d[r], xa);
+      V* xo = sXg + o2x[r];
+      if (PR && (Q % 2 == 0 || o2b[r] != 0)) {
+        V xb[N];
+        xtest_row<A, N, Q>(T1, T2, anti, sPg + o2c[r] + o2b[r], sPg + o2d[r] + o2b[r], xb);
 #pragma unroll
-      for (int x = 0; x < NF; ++x) {
-        const V a = A::acc_get(r1[x]), b = A::acc_get(r2[x]);
-        xo[x] = A::add(a, b);
-        const V d = A::sub(a, b);
-        xo[N - 1 - x] = anti ? A::neg(d) : d;
+        for (int x = 0; x < N; ++x) {
+          xo[x] = A::add(xa[x], xb[x]);
+          xo[QH * N + x] = A::sub(xa[x], xb[x]);
+        }
+      } else {
+#pragma unroll
+        for (int x = 0; x < N; ++x) {
+          Acc n;
+          A::acc_set(n, xa[x]);
+          xo[x] = A::acc_get_norm(n);
+        }
       }
-      if (N % 2 == 1) xo[NF] = A::add(A::acc_get(r1[NF]), A::acc_get(r2[NF]));
     }
     group_sync<NT>();
-    // P3: Y1 = TY0^T X(c,0) + TY1^T X(c,1), Y3 = TY2^T X(c,2); item (j, c, x, y)
+    if constexpr (PR) {
+      // P3 (even-odd): Y1 = TY0^T X(c,0) + TY1^T X(c,1), Y3 = TY2^T X(c,2) from the
+      // y-folded x tests (rows q < (Q+1)/2: sums Xe, rows (Q+1)/2 + q: differences
+      // Xo); TY0, TY2 symmetric, TY1 antisymmetric: R1 = TY0_1 X0e + TY1_2 X1o,
+      // R2 = TY0_2 X0o + TY1_1 X1e give Y1(y) = R1 + R2, Y1(N-1-y) = R1 - R2;
+      // C1 = TY2_1 X2e, C2 = TY2_2 X2o give Y3 the same way; item (j, c, y < NH, x)
 #pragma unroll
-    for (int r = 0; r < R3; ++r) {
-      if (I3 % NT != 0 && t + NT * r >= I3) break;
-      const V* X0 = sXg + o3a[r];
-      const V* X1 = X0 + 3 * QN;                  // X(c,1) = test 3 + c
-      const V* X2 = X0 + (o3y[r] >> 4) * QN;      // X(c,2)
-      const int y = o3y[r] & 15;
-      Acc y1, y3;
-      A::acc_first(y1, sTY[QN + y], X1[0]);
-      A::acc_fma(y1, sTY[y], X0[0]);
-      A::acc_first(y3, sTY[2 * QN + y], X2[0]);
-#pragma unroll UQ
-      for (int qy = 1; qy < Q; ++qy) {
-        const int o = N * qy;
-        A::acc_fma(y1, sTY[QN + qy * N + y], X1[o]);
-        A::acc_fma(y1, sTY[qy * N + y], X0[o]);
-        A::acc_fma(y3, sTY[2 * QN + qy * N + y], X2[o]);
+      for (int r = 0; r < R3; ++r) {
+        if (I3 % NT != 0 && t + NT * r >= I3) break;
+        const V* X0 = sXg + o3a[r];
+        const V* X1 = X0 + 3 * QN;                  // X(c,1) = test 3 + c
+        const V* X2 = X0 + (o3y[r] >> 4) * QN;      // X(c,2)
+        const int y = o3y[r] & 15;
+        const V* J0 = sTY;
+        const V* J1 = sTY + Q * NH;
+        const V* J2 = sTY + 2 * Q * NH;
+        Acc R1, R2, C1, C2;
+        A::acc_first(R1, J0[y], X0[0]);
+        A::acc_first(R2, J1[y], X1[0]);
+        A::acc_first(C1, J2[y], X2[0]);
+        A::acc_first(C2, J2[QH * NH + y], X2[QH * N]);
+#pragma unroll
+        for (int q = 1; q < QH; ++q) {
+          A::acc_fma(R1, J0[q * NH + y], X0[q * N]);
+          A::acc_fma(R2, J1[q * NH + y], X1[q * N]);
+          A::acc_fma(C1, J2[q * NH + y], X2[q * N]);
+        }
+#pragma unroll
+        for (int q = 0; q < QF; ++q) {
+          A::acc_fma(R1, J1[(QH + q) * NH + y], X1[(QH + q) * N]);
+          A::acc_fma(R2, J0[(QH + q) * NH + y], X0[(QH + q) * N]);
+          if (q > 0) A::acc_fma(C2, J2[(QH + q) * NH + y], X2[(QH + q) * N]);
+        }
+        const V a = A::acc_get(R1), b = A::acc_get(R2), c = A::acc_get(C1), d = A::acc_get(C2);
+        V* Y1 = sYg + o3o[r];
+        Y1[N * y] = A::add(a, b);
+        Y1[NN + N * y] = A::add(c, d);
+        if (N % 2 == 0 || y < NF) {
+          Y1[N * (N - 1 - y)] = A::sub(a, b);
+          Y1[NN + N * (N - 1 - y)] = A::sub(c, d);
+        }
       }
-      const int it = t + NT * r, jc = it / NN;
-      sYg[2 * jc * NN + (it - jc * NN)] = A::acc_get_norm(y1);
-      sYg[(2 * jc + 1) * NN + (it - jc * NN)] = A::acc_get_norm(y3);
+    } else {
+      // P3: Y1 = TY0^T X(c,0) + TY1^T X(c,1), Y3 = TY2^T X(c,2); item (j, c, y, x)
+#pragma unroll
+      for (int r = 0; r < R3; ++r) {
+        if (I3 % NT != 0 && t + NT * r >= I3) break;
+        const V* X0 = sXg + o3a[r];
+        const V* X1 = X0 + 3 * QN;                  // X(c,1) = test 3 + c
+        const V* X2 = X0 + (o3y[r] >> 4) * QN;      // X(c,2)
+        const int y = o3y[r] & 15;
+        Acc y1, y3;
+        A::acc_first(y1, sTY[QN + y], X1[0]);
+        A::acc_fma(y1, sTY[y], X0[0]);
+        A::acc_first(y3, sTY[2 * QN + y], X2[0]);
+#pragma unroll
+        for (int qy = 1; qy < Q; ++qy) {
+          const int o = N * qy;
+          A::acc_fma(y1, sTY[QN + qy * N + y], X1[o]);
+          A::acc_fma(y1, sTY[qy * N + y], X0[o]);
+          A::acc_fma(y3, sTY[2 * QN + qy * N + y], X2[o]);
+        }
+        V* Y1 = sYg + o3o[r];
+        Y1[N * y] = A::acc_get_norm(y1);
+        Y1[NN + N * y] = A::acc_get_norm(y3);
+      }
     }
     group_sync<NT>();
     // P4: out -= SW_z(qz) Y1 + DW_z(qz) Y3; item (j, c, x, y, z), in registers
@@ -727,6 +823,19 @@ ConvTabT<typename A::V, N, Q> conv_tables(const ConvHost& h) {
       tb.TY[1][i] = A::make(jac[1] * h.w[q] * h.D[i]);
       tb.TY[2][i] = A::make(jac[2] * h.w[q] * h.S[i]);
     }
+  {
+    constexpr int QH0 = (Q + 1) / 2, NH0 = (N + 1) / 2;
+    for (int d = 0; d < 3; ++d) {
+      const double* T = d == 1 ? h.D : h.S;   // jac_d w (S or D): DW antisymmetric
+      const double sg = d == 1 ? -1.0 : 1.0;
+      for (int i = 0; i < Q; ++i)
+        for (int x = 0; x < NH0; ++x) {
+          const int q = i < QH0 ? i : i - QH0;
+          const double a = jac[d] * h.w[q] * T[q * N + x], b = jac[d] * h.w[q] * T[q * N + N - 1 - x];
+          tb.TYeo[d][i * NH0 + x] = A::make(i < QH0 ? 0.5 * (a + sg * b) : 0.5 * (a - sg * b));
+        }
+    }
+  }
   constexpr int QH = (Q + 1) / 2, NH = (N + 1) / 2;
   for (int ty = 0; ty < 2; ++ty) {
     const double* T = ty == 0 ? h.D : h.S;   // DW (antisymmetric), SW (symmetric), times w_q

@@ -19,6 +19,9 @@
 // and three work arrays are staged in shared memory; neighbour lines are read
 // directly from global memory (they are L2 resident).  Global loads and
 // stores of the own cells are coalesced over the block's contiguous cells.
+#include <algorithm>
+#include <cmath>
+
 #include "arith.cuh"
 #include "ops.h"
 
@@ -578,6 +581,20 @@ int launch_sipg(const MeshDims& m, int ncomp, const typename A::G* src, typename
     }
   }
   for (int i = 0; i < NN; ++i) tb.M[i] = A::make(h.M[i]);
+  if constexpr (eo_sweeps<A, N>()) {
+    // the even-odd sweeps need centrosymmetric A0 and M (always so for the
+    // operators of this library: uniform cells, LGL nodes, equal penalties on
+    // both faces); anything else is refused rather than computed wrongly
+    auto centro = [&](const double* C) {
+      double mx = 0.0, dev = 0.0;
+      for (int i = 0; i < NN; ++i) {
+        mx = std::max(mx, std::fabs(C[i]));
+        dev = std::max(dev, std::fabs(C[i] - C[NN - 1 - i]));
+      }
+      return dev <= 1e-13 * mx;
+    };
+    if (!centro(h.M) || !centro(h.A0[0]) || !centro(h.A0[1]) || !centro(h.A0[2])) return 7;
+  }
   {
     constexpr int NH = (N + 1) / 2, NF = N / 2;
     auto split = [&](const double* C, EOMat<typename A::V, N>& eo) {
