@@ -181,7 +181,9 @@ __device__ __forceinline__ void interp_eo(const typename A::V* IE, const typenam
     uo[j] = A::sub_nr(a, b);
   }
   if (N % 2 == 1) ue[NH - 1] = u[NF * si];
-#pragma unroll
+  // from N = 10 on the output pairs are looped over (registers: the cell
+  // kernel's 512-thread groups allow 128 per thread)
+#pragma unroll(N >= 10 ? 1 : QH)
   for (int q = 0; q < QH; ++q) {
     Acc r1;
     A::acc_first(r1, I1[q * NH], ue[0]);
@@ -364,32 +366,54 @@ __global__ void __launch_bounds__(conv_groups_per_block<N>() * conv_threads<N>()
       sUg[j * 3 * N3 + c * N3 + i] = A::load(u3 + ((size_t)c * m.E + pick2(j, el0, el1)) * N3 + i);
     }
   __syncthreads();
-  // x interpolation: item (j, c, line (y,z), q)
-  for (int it = t; it < CPG * 3 * NN * Q; it += NT) {
-    const int j = it / (3 * NN * Q), l = it - j * 3 * NN * Q;
-    const int q = l % Q, r = l / Q;
-    const V* x = sUg + j * 3 * N3 + r * N;
-    Acc a;
-    A::acc_first(a, sS[q * N], x[0]);
+  // double-float: whole lines in even-odd form (interp_eo, tables read from
+  // the kernel parameter), except at N = 5, 6, 7, where one output per item
+  // measured faster (k = 4: 1 %, k = 5: 5 %, k = 6: 15 %); natively (FP64-pipe
+  // bound) one output per item keeps every lane busy
+  if constexpr (A::emulated && (N < 5 || N > 7)) {
+    // x interpolation: item (j, c, line (y,z))
+    for (int it = t; it < CPG * 3 * NN; it += NT) {
+      const int j = it / (3 * NN), r = it - j * 3 * NN;
+      interp_eo<A, N, Q>(tb.IE, sUg + j * 3 * N3 + r * N, 1, sU1g + j * LY::U1R + r * Q, 1);
+    }
+    group_sync<NT>();
+    // y interpolation: item (j, c, qx, z)
+    for (int it = t; it < CPG * 3 * QN; it += NT) {
+      const int j = it / (3 * QN), r = it - j * 3 * QN;
+      const int c = r / QN, ll = r - c * QN;
+      const int qx = ll % Q, z = ll / Q;
+      interp_eo<A, N, Q>(tb.IE, sU1g + j * LY::U1R + c * Q * NN + qx + QN * z, Q,
+                         sU2g + j * LY::U2 + c * QQ * N + qx + QQ * z, Q);
+    }
+    group_sync<NT>();
+  } else {
+    // x interpolation: item (j, c, line (y,z), q)
+    for (int it = t; it < CPG * 3 * NN * Q; it += NT) {
+      const int j = it / (3 * NN * Q), l = it - j * 3 * NN * Q;
+      const int q = l % Q, r = l / Q;
+      const V* x = sUg + j * 3 * N3 + r * N;
+      Acc a;
+      A::acc_first(a, sS[q * N], x[0]);
 #pragma unroll
-    for (int i = 1; i < N; ++i) A::acc_fma(a, sS[q * N + i], x[i]);
-    sU1g[j * LY::U1R + l] = A::acc_get_norm(a);
-  }
-  group_sync<NT>();
-  // y interpolation: item (j, c, qx, z, qy)
-  for (int it = t; it < CPG * 3 * Q * N * Q; it += NT) {
-    const int j = it / (3 * QN * Q), l = it - j * 3 * QN * Q;
-    const int qy = l % Q, r = l / Q;
-    const int c = r / QN, ll = r - c * QN;
-    const int qx = ll % Q, z = ll / Q;
-    const V* x = sU1g + j * LY::U1R + c * Q * NN + qx + QN * z;
-    Acc a;
-    A::acc_first(a, sS[qy * N], x[0]);
+      for (int i = 1; i < N; ++i) A::acc_fma(a, sS[q * N + i], x[i]);
+      sU1g[j * LY::U1R + l] = A::acc_get_norm(a);
+    }
+    group_sync<NT>();
+    // y interpolation: item (j, c, qx, z, qy)
+    for (int it = t; it < CPG * 3 * Q * N * Q; it += NT) {
+      const int j = it / (3 * QN * Q), l = it - j * 3 * QN * Q;
+      const int qy = l % Q, r = l / Q;
+      const int c = r / QN, ll = r - c * QN;
+      const int qx = ll % Q, z = ll / Q;
+      const V* x = sU1g + j * LY::U1R + c * Q * NN + qx + QN * z;
+      Acc a;
+      A::acc_first(a, sS[qy * N], x[0]);
 #pragma unroll
-    for (int i = 1; i < N; ++i) A::acc_fma(a, sS[qy * N + i], x[Q * i]);
-    sU2g[j * LY::U2 + c * QQ * N + qx + Q * qy + QQ * z] = A::acc_get_norm(a);
+      for (int i = 1; i < N; ++i) A::acc_fma(a, sS[qy * N + i], x[Q * i]);
+      sU2g[j * LY::U2 + c * QQ * N + qx + Q * qy + QQ * z] = A::acc_get_norm(a);
+    }
+    group_sync<NT>();
   }
-  group_sync<NT>();
 
   // The face integrals of the six faces of each cell (raw doubles), fetched
   // asynchronously into the dead x-interpolation buffer while the plane loop
