@@ -64,10 +64,11 @@ typedef struct {
   double nu;             /* kinematic viscosity of the viscous operator           */
   int mg_coarse_n;       /* coarsest multigrid mesh (elements per direction)      */
   int mg_precision;      /* 32 or 64: arithmetic of the V-cycle; 0 = no multigrid */
-  int fp64_mode;         /* arithmetic of every FP64 operator kernel (convective,   */
-                         /* SIPG-type, mass, divergence, gradient, projection,      */
-                         /* penalty parameters, dissipation, the CG matvecs and     */
-                         /* inverse-mass preconditioners): 0 native FP64;           */
+  int fp64_mode;         /* arithmetic of every FP64 operator kernel (convective    */
+                         /* and its VJP, SIPG-type, mass, divergence, gradient,     */
+                         /* projection, penalty parameters, dissipation, the CG     */
+                         /* matvecs and inverse-mass preconditioners): 0 native     */
+                         /* FP64;                                                   */
                          /* 1 double-float (pairs of FP32 with a 48-bit significand */
                          /* on the FP32 pipe, which GB300 runs 61x faster; parity   */
                          /* with FP64 to 1e-12 relative for vectors with max |x|    */

@@ -65,6 +65,8 @@ struct F64 {
   __device__ __forceinline__ static V neg(V a) { return -a; }
   __device__ __forceinline__ static V fmadd(V a, V b, V c) { return fma(a, b, c); }
   __device__ __forceinline__ static V half(V a) { return 0.5 * a; }
+  // a * f for f a power of two, its negative or zero (exact)
+  __device__ __forceinline__ static V scale_pow2(V a, float f) { return (double)f * a; }
   __device__ __forceinline__ static V absval(V a) { return fabs(a); }
   __device__ __forceinline__ static V sqrt_(V a) { return sqrt(a); }
   __device__ __forceinline__ static bool greater(V a, V b) { return a > b; }
@@ -226,6 +228,12 @@ struct DF64 {
   __device__ __forceinline__ static V half(V a) {
     a.hi *= 0.5f;
     a.lo *= 0.5f;
+    return a;
+  }
+  // a * f for f a power of two, its negative or zero (exact)
+  __device__ __forceinline__ static V scale_pow2(V a, float f) {
+    a.hi *= f;
+    a.lo *= f;
     return a;
   }
   __device__ __forceinline__ static V absval(V a) { return a.hi < 0.0f ? neg(a) : a; }

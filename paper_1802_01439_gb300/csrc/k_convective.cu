@@ -33,15 +33,6 @@ constexpr int conv_cells_per_block() {
   return N * N >= 64 ? 1 : 64 / (N * N);
 }
 
-template <int N, int Q>
-struct ConvTab {
-  double S[Q * N];
-  double D[Q * N];
-  double w[Q];
-  double jac[3];   // h_x h_y h_z / h_d
-  double area[3];  // product of the tangential cell sizes of faces normal to d
-};
-
 // Threads per group of the forward convective kernel: one warp up to N = 5;
 // above, more threads per cell as the cell's shared memory grows (from
 // N = 10 on one cell fills an SM's shared memory, so it gets 16 warps).
@@ -487,6 +478,9 @@ __global__ void __launch_bounds__(conv_groups_per_block<N>() * conv_threads<N>()
     o4z[r] = rr / NN;
   }
   Acc out[R4];
+  // the point loop of the unpaired y tests is unrolled, except for N = 5 and
+  // 6 (k = 4, 5), where the rolled loop measured 5 % faster
+  constexpr int UQ = (N == 5 || N == 6) ? 1 : Q;
 
 #pragma unroll 1
   for (int qz = 0; qz < Q; ++qz) {
@@ -591,7 +585,7 @@ __global__ void __launch_bounds__(conv_groups_per_block<N>() * conv_threads<N>()
         A::acc_first(y1, sTY[QN + y], X1[0]);
         A::acc_fma(y1, sTY[y], X0[0]);
         A::acc_first(y3, sTY[2 * QN + y], X2[0]);
-#pragma unroll
+#pragma unroll UQ
         for (int qy = 1; qy < Q; ++qy) {
           const int o = N * qy;
           A::acc_fma(y1, sTY[QN + qy * N + y], X1[o]);
@@ -935,28 +929,42 @@ struct VjpLayout {
   static constexpr int PER = UW + L1 + L2F + P + X + Y;
 };
 
-template <int N, int Q>
+template <class V, int N, int Q>
+struct VjpTab {
+  V S[Q * N];   // phi_j(x_q)
+  V D[Q * N];   // phi_j'(x_q)
+  V w[Q];       // Gauss weights on [0, 1]
+  V jac[3];     // h_x h_y h_z / h_d
+  V area[3];    // face area of faces normal to d
+};
+
+// One cell per N^2 threads, EPB cells per block; arithmetic policy A (F64
+// or DF64), loads and stores in double.
+template <class A, int N, int Q>
 __global__ void __launch_bounds__(conv_cells_per_block<N>() * N * N)
     conv_vjp_kernel(const double* __restrict__ u3, const double* __restrict__ w3, double* __restrict__ dst3,
-                    const __grid_constant__ ConvTab<N, Q> tb, const MeshDims m) {
+                    const __grid_constant__ VjpTab<typename A::V, N, Q> tb, const MeshDims m) {
+  typedef typename A::V V;
+  typedef typename A::Acc Acc;
   typedef VjpLayout<N, Q> LY;
+  static_assert(sizeof(V) == sizeof(double), "8-byte values");
   constexpr int NT = N * N, N3 = N * N * N, EPB = conv_cells_per_block<N>();
   constexpr int QNN = Q * N * N, QQN = Q * Q * N, QQ = Q * Q;
-  double* sm = reinterpret_cast<double*>(dyn_smem());
+  V* sm = reinterpret_cast<V*>(dyn_smem());
   const int slot = threadIdx.x / NT;
   const int t = threadIdx.x - slot * NT;
   const long long c0 = (long long)blockIdx.x * EPB;
   const long long rem = m.E - c0;
   const int nvalid = rem < EPB ? (int)rem : EPB;
   const bool active = slot < nvalid;
-  double* sUW = sm + slot * LY::PER;   // u: [0, 3N3), w: [3N3, 6N3)
-  double* sL1 = sUW + LY::UW;          // u_S (3), w_S (3), w_D (3) : each Q N N
-  double* sL2 = sL1 + LY::L1;          // u_SS (3), w_DS (3), w_SD (3), w_SS (3) : each Q Q N
-  double* sP = sL2 + LY::L2F;          // u (3 Q Q), g (9 Q Q)
-  double* sX = sP + LY::P;
-  double* sY = sX + LY::X;
-  double* sOut = sL1;
-  double* sFace = sL2;
+  V* sUW = sm + slot * LY::PER;   // u: [0, 3N3), w: [3N3, 6N3)
+  V* sL1 = sUW + LY::UW;          // u_S (3), w_S (3), w_D (3) : each Q N N
+  V* sL2 = sL1 + LY::L1;          // u_SS (3), w_DS (3), w_SD (3), w_SS (3) : each Q Q N
+  V* sP = sL2 + LY::L2F;          // u (3 Q Q), g (9 Q Q)
+  V* sX = sP + LY::P;
+  V* sY = sX + LY::X;
+  V* sOut = sL1;
+  V* sFace = sL2;
 
   long long el = 0;
   int ex = 0, ey = 0, ez = 0;
@@ -968,8 +976,8 @@ __global__ void __launch_bounds__(conv_cells_per_block<N>() * N * N)
     ez = (int)(tt / m.ny);
     for (int c = 0; c < 3; ++c)
       for (int i = t; i < N3; i += NT) {
-        sUW[c * N3 + i] = u3[(c * m.E + el) * N3 + i];
-        sUW[(3 + c) * N3 + i] = w3[(c * m.E + el) * N3 + i];
+        sUW[c * N3 + i] = A::load(u3 + (c * m.E + el) * N3 + i);
+        sUW[(3 + c) * N3 + i] = A::load(w3 + (c * m.E + el) * N3 + i);
       }
   }
   __syncthreads();
@@ -977,18 +985,20 @@ __global__ void __launch_bounds__(conv_cells_per_block<N>() * N * N)
   if (active)
     for (int it = t; it < 6 * N * N; it += NT) {
       const int f = it / (N * N), l = it - f * N * N;   // f < 3: u_c, else w_(f-3)
-      double x[N];
-      load_line<double, N>(sUW + f * N3, l * N, 1, x);
+      V x[N];
+      load_line<V, N>(sUW + f * N3, l * N, 1, x);
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
-        double a = tb.S[q * N] * x[0], b = tb.D[q * N] * x[0];
+        Acc a, b;
+        A::acc_first(a, tb.S[q * N], x[0]);
+        A::acc_first(b, tb.D[q * N], x[0]);
 #pragma unroll
         for (int j = 1; j < N; ++j) {
-          a = fma(tb.S[q * N + j], x[j], a);
-          b = fma(tb.D[q * N + j], x[j], b);
+          A::acc_fma(a, tb.S[q * N + j], x[j]);
+          A::acc_fma(b, tb.D[q * N + j], x[j]);
         }
-        sL1[f * QNN + l * Q + q] = a;                     // u_S (f<3) or w_S (f>=3)
-        if (f >= 3) sL1[(f + 3) * QNN + l * Q + q] = b;    // w_D
+        sL1[f * QNN + l * Q + q] = A::acc_get_norm(a);                     // u_S (f<3) or w_S (f>=3)
+        if (f >= 3) sL1[(f + 3) * QNN + l * Q + q] = A::acc_get_norm(b);    // w_D
       }
     }
   __syncthreads();
@@ -997,43 +1007,43 @@ __global__ void __launch_bounds__(conv_cells_per_block<N>() * N * N)
     for (int it = t; it < 6 * Q * N; it += NT) {
       const int f = it / (Q * N), l = it - f * Q * N;
       const int qx = l % Q, z = l / Q;
-      double x[N];
+      V x[N];
       if (f < 3) {
-        load_line<double, N>(sL1 + f * QNN, qx + Q * N * z, Q, x);
+        load_line<V, N>(sL1 + f * QNN, qx + Q * N * z, Q, x);
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-          double a = tb.S[q * N] * x[0];
+          Acc a;
+          A::acc_first(a, tb.S[q * N], x[0]);
 #pragma unroll
-          for (int j = 1; j < N; ++j) a = fma(tb.S[q * N + j], x[j], a);
-          sL2[f * QQN + qx + Q * q + QQ * z] = a;
+          for (int j = 1; j < N; ++j) A::acc_fma(a, tb.S[q * N + j], x[j]);
+          sL2[f * QQN + qx + Q * q + QQ * z] = A::acc_get_norm(a);
         }
       } else {
         const int c = f - 3;
-        double y[N];
-        load_line<double, N>(sL1 + (3 + c) * QNN, qx + Q * N * z, Q, x);   // w_S
-        load_line<double, N>(sL1 + (6 + c) * QNN, qx + Q * N * z, Q, y);   // w_D
+        V y[N];
+        load_line<V, N>(sL1 + (3 + c) * QNN, qx + Q * N * z, Q, x);   // w_S
+        load_line<V, N>(sL1 + (6 + c) * QNN, qx + Q * N * z, Q, y);   // w_D
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-          double ds = tb.S[q * N] * y[0], sd = tb.D[q * N] * x[0], ss = tb.S[q * N] * x[0];
+          Acc ds, sd, ss;
+          A::acc_first(ds, tb.S[q * N], y[0]);
+          A::acc_first(sd, tb.D[q * N], x[0]);
+          A::acc_first(ss, tb.S[q * N], x[0]);
 #pragma unroll
           for (int j = 1; j < N; ++j) {
-            ds = fma(tb.S[q * N + j], y[j], ds);
-            sd = fma(tb.D[q * N + j], x[j], sd);
-            ss = fma(tb.S[q * N + j], x[j], ss);
+            A::acc_fma(ds, tb.S[q * N + j], y[j]);
+            A::acc_fma(sd, tb.D[q * N + j], x[j]);
+            A::acc_fma(ss, tb.S[q * N + j], x[j]);
           }
-          sL2[(3 + c) * QQN + qx + Q * q + QQ * z] = ds;
-          sL2[(6 + c) * QQN + qx + Q * q + QQ * z] = sd;
-          sL2[(9 + c) * QQN + qx + Q * q + QQ * z] = ss;
+          sL2[(3 + c) * QQN + qx + Q * q + QQ * z] = A::acc_get_norm(ds);
+          sL2[(6 + c) * QQN + qx + Q * q + QQ * z] = A::acc_get_norm(sd);
+          sL2[(9 + c) * QQN + qx + Q * q + QQ * z] = A::acc_get_norm(ss);
         }
       }
     }
   __syncthreads();
 
-  double acc[3][N];
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int z = 0; z < N; ++z) acc[c][z] = 0.0;
+  Acc acc[3][N];
   const int tx = t % N, ty = t / N;
   for (int qz = 0; qz < Q; ++qz) {
     // P1: u (3) and g_cd (9) on the plane; g_cx from w_DS, g_cy from w_SD
@@ -1041,7 +1051,7 @@ __global__ void __launch_bounds__(conv_cells_per_block<N>() * N * N)
     if (active)
       for (int it = t; it < 12 * QQ; it += NT) {
         const int f = it / QQ, l = it - f * QQ;
-        const double* src;
+        const V* src;
         bool dz = false;
         if (f < 3) {
           src = sL2 + f * QQN;
@@ -1051,15 +1061,12 @@ __global__ void __launch_bounds__(conv_cells_per_block<N>() * N * N)
           dz = d == 2;
         }
         src += l;
-        double a = 0.0;
-        if (dz) {
+        const V* T = dz ? tb.D : tb.S;
+        Acc a;
+        A::acc_first(a, T[qz * N], src[0]);
 #pragma unroll
-          for (int z = 0; z < N; ++z) a = fma(tb.D[qz * N + z], src[QQ * z], a);
-        } else {
-#pragma unroll
-          for (int z = 0; z < N; ++z) a = fma(tb.S[qz * N + z], src[QQ * z], a);
-        }
-        sP[it] = a;
+        for (int z = 1; z < N; ++z) A::acc_fma(a, T[qz * N + z], src[QQ * z]);
+        sP[it] = A::acc_get_norm(a);
       }
     __syncthreads();
     // P2: pointwise -W sum_d (g_ed + g_de) u_d, with reference derivatives
@@ -1067,63 +1074,78 @@ __global__ void __launch_bounds__(conv_cells_per_block<N>() * N * N)
     if (active)
       for (int it = t; it < QQ; it += NT) {
         const int qx = it % Q, qy = it / Q;
-        const double w3q = tb.w[qx] * tb.w[qy] * tb.w[qz];
-        double u[3], g[3][3];
+        const V w3q = A::mul(A::mul(tb.w[qx], tb.w[qy]), tb.w[qz]);
+        V u[3], g[3][3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) u[c] = sP[c * QQ + it];
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
-          for (int d = 0; d < 3; ++d) g[c][d] = tb.jac[d] * sP[(3 + 3 * c + d) * QQ + it];
+          for (int d = 0; d < 3; ++d) g[c][d] = A::mul(tb.jac[d], sP[(3 + 3 * c + d) * QQ + it]);
+        V r[3];
 #pragma unroll
         for (int e = 0; e < 3; ++e) {
-          double a = 0.0;
+          Acc a;
+          A::acc_first(a, A::add(g[e][0], g[0][e]), u[0]);
 #pragma unroll
-          for (int d = 0; d < 3; ++d) a = fma(g[e][d] + g[d][e], u[d], a);
-          sP[e * QQ + it] = -w3q * a;
+          for (int d = 1; d < 3; ++d) A::acc_fma(a, A::add(g[e][d], g[d][e]), u[d]);
+          r[e] = A::neg(A::mul(w3q, A::acc_get_norm(a)));
         }
+#pragma unroll
+        for (int e = 0; e < 3; ++e) sP[e * QQ + it] = r[e];
       }
     __syncthreads();
     // P3: x test
     if (active)
       for (int it = t; it < 3 * Q; it += NT) {
         const int c = it / Q, qy = it - c * Q;
-        double a[N];
-#pragma unroll
-        for (int x = 0; x < N; ++x) a[x] = 0.0;
+        Acc a[N];
 #pragma unroll
         for (int qx = 0; qx < Q; ++qx) {
-          const double gv = sP[c * QQ + qx + Q * qy];
+          const V gv = sP[c * QQ + qx + Q * qy];
 #pragma unroll
-          for (int x = 0; x < N; ++x) a[x] = fma(tb.S[qx * N + x], gv, a[x]);
+          for (int x = 0; x < N; ++x) {
+            if (qx == 0)
+              A::acc_first(a[x], tb.S[x], gv);
+            else
+              A::acc_fma(a[x], tb.S[qx * N + x], gv);
+          }
         }
 #pragma unroll
-        for (int x = 0; x < N; ++x) sX[c * N * Q + x + N * qy] = a[x];
+        for (int x = 0; x < N; ++x) sX[c * N * Q + x + N * qy] = A::acc_get_norm(a[x]);
       }
     __syncthreads();
     // P4: y test
     if (active)
       for (int it = t; it < 3 * N; it += NT) {
         const int c = it / N, x = it - c * N;
-        double a[N];
-#pragma unroll
-        for (int y = 0; y < N; ++y) a[y] = 0.0;
+        Acc a[N];
 #pragma unroll
         for (int qy = 0; qy < Q; ++qy) {
-          const double b = sX[c * N * Q + x + N * qy];
+          const V b = sX[c * N * Q + x + N * qy];
 #pragma unroll
-          for (int y = 0; y < N; ++y) a[y] = fma(tb.S[qy * N + y], b, a[y]);
+          for (int y = 0; y < N; ++y) {
+            if (qy == 0)
+              A::acc_first(a[y], tb.S[y], b);
+            else
+              A::acc_fma(a[y], tb.S[qy * N + y], b);
+          }
         }
 #pragma unroll
-        for (int y = 0; y < N; ++y) sY[c * N * N + x + N * y] = a[y];
+        for (int y = 0; y < N; ++y) sY[c * N * N + x + N * y] = A::acc_get_norm(a[y]);
       }
     __syncthreads();
     if (active) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const double yv = sY[c * N * N + tx + N * ty];
+        const V yv = sY[c * N * N + tx + N * ty];
 #pragma unroll
-        for (int z = 0; z < N; ++z) acc[c][z] = fma(tb.S[qz * N + z], yv, acc[c][z]);
+        for (int z = 0; z < N; ++z) {
+          if (qz == 0)
+            A::acc_first(acc[c][z], tb.S[z], yv);
+          else
+            A::acc_fma(acc[c][z], tb.S[qz * N + z], yv);
+        }
       }
     }
   }
@@ -1132,16 +1154,16 @@ __global__ void __launch_bounds__(conv_cells_per_block<N>() * N * N)
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
-      for (int z = 0; z < N; ++z) sOut[c * N3 + tx + N * ty + N * N * z] = acc[c][z];
+      for (int z = 0; z < N; ++z) sOut[c * N3 + tx + N * ty + N * N * z] = A::acc_get_norm(acc[c][z]);
   }
   __syncthreads();
 
   // ---------------------------------------------------------------- faces
   // traces: index f = (side s, field v, comp c) -> s*6 + v*3 + c, v: 0 = u, 1 = w
-  double* G1 = sFace;                 // [f][q1 + Q j2]   12 Q N
-  double* G2 = G1 + 12 * Q * N;       // [f][q1 + Q q2]   12 Q Q
-  double* H = G2 + 12 * QQ;           // [c][q1 + Q q2]   3 Q Q
-  double* K1 = G1;
+  V* G1 = sFace;                 // [f][q1 + Q j2]   12 Q N
+  V* G2 = G1 + 12 * Q * N;       // [f][q1 + Q q2]   12 Q Q
+  V* H = G2 + 12 * QQ;           // [c][q1 + Q q2]   3 Q Q
+  V* K1 = G1;
   for (int d = 0; d < 3; ++d) {
     const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
     for (int side = 1; side >= -1; side -= 2) {
@@ -1157,32 +1179,34 @@ __global__ void __launch_bounds__(conv_cells_per_block<N>() * N * N)
           const int f = it / N, j2 = it - f * N;
           const int s = f / 6, v = (f / 3) % 2, c = f % 3;
           const double* gsrc = v == 0 ? u3 : w3;
-          double val[N];
+          V val[N];
 #pragma unroll
           for (int j1 = 0; j1 < N; ++j1)
             val[j1] = s == 0 ? sUW[(v * 3 + c) * N3 + node3(N, d, aown, t1, j1, t2, j2)]
-                             : __ldg(gsrc + (c * m.E + nb) * N3 + node3(N, d, anb, t1, j1, t2, j2));
+                             : A::load(gsrc + (c * m.E + nb) * N3 + node3(N, d, anb, t1, j1, t2, j2));
 #pragma unroll
           for (int q1 = 0; q1 < Q; ++q1) {
-            double a = tb.S[q1 * N] * val[0];
+            Acc a;
+            A::acc_first(a, tb.S[q1 * N], val[0]);
 #pragma unroll
-            for (int j = 1; j < N; ++j) a = fma(tb.S[q1 * N + j], val[j], a);
-            G1[f * Q * N + q1 + Q * j2] = a;
+            for (int j = 1; j < N; ++j) A::acc_fma(a, tb.S[q1 * N + j], val[j]);
+            G1[f * Q * N + q1 + Q * j2] = A::acc_get_norm(a);
           }
         }
       __syncthreads();
       if (active)
         for (int it = t; it < 12 * Q; it += NT) {
           const int f = it / Q, q1 = it - f * Q;
-          double val[N];
+          V val[N];
 #pragma unroll
           for (int j2 = 0; j2 < N; ++j2) val[j2] = G1[f * Q * N + q1 + Q * j2];
 #pragma unroll
           for (int q2 = 0; q2 < Q; ++q2) {
-            double a = tb.S[q2 * N] * val[0];
+            Acc a;
+            A::acc_first(a, tb.S[q2 * N], val[0]);
 #pragma unroll
-            for (int j = 1; j < N; ++j) a = fma(tb.S[q2 * N + j], val[j], a);
-            G2[f * QQ + q1 + Q * q2] = a;
+            for (int j = 1; j < N; ++j) A::acc_fma(a, tb.S[q2 * N + j], val[j]);
+            G2[f * QQ + q1 + Q * q2] = A::acc_get_norm(a);   // compared below
           }
         }
       __syncthreads();
@@ -1190,103 +1214,113 @@ __global__ void __launch_bounds__(conv_cells_per_block<N>() * N * N)
         for (int it = t; it < QQ; it += NT) {
           const int q1 = it % Q, q2 = it / Q;
           const int sm_ = side > 0 ? 0 : 1, sp_ = side > 0 ? 1 : 0;  // trace side of '-' / '+'
-          double um[3], up[3], jw[3];
+          V um[3], up[3], jw[3];
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             um[c] = G2[(sm_ * 6 + c) * QQ + it];
             up[c] = G2[(sp_ * 6 + c) * QQ + it];
-            jw[c] = G2[(sm_ * 6 + 3 + c) * QQ + it] - G2[(sp_ * 6 + 3 + c) * QQ + it];
+            jw[c] = A::sub(G2[(sm_ * 6 + 3 + c) * QQ + it], G2[(sp_ * 6 + 3 + c) * QQ + it]);
           }
-          const double unm = um[d], unp = up[d];
-          const double am = fabs(unm), ap = fabs(unp);
-          const double lam = fmax(am, ap);
-          const double sgm = unm > 0.0 ? 1.0 : (unm < 0.0 ? -1.0 : 0.0);
-          const double sgp = unp > 0.0 ? 1.0 : (unp < 0.0 ? -1.0 : 0.0);
-          const double smx = am > ap ? sgm : (am == ap ? 0.5 * sgm : 0.0);
-          const double spx = ap > am ? sgp : (am == ap ? 0.5 * sgp : 0.0);
-          double jum = 0.0, jup = 0.0, jdu = 0.0;
+          const V unm = um[d], unp = up[d];
+          const V am = A::absval(unm), ap = A::absval(unp);
+          const bool mbig = A::greater(am, ap), pbig = A::greater(ap, am);
+          const V lam = mbig ? am : ap;
+          // derivative of max(|un-|, |un+|): sign to the larger side, half to
+          // each on a tie
+          const float smx = mbig ? (float)A::sign(unm) : (pbig ? 0.0f : 0.5f * (float)A::sign(unm));
+          const float spx = pbig ? (float)A::sign(unp) : (mbig ? 0.0f : 0.5f * (float)A::sign(unp));
+          Acc jum, jup, jdu;
+          A::acc_first(jum, jw[0], um[0]);
+          A::acc_first(jup, jw[0], up[0]);
+          A::acc_first(jdu, jw[0], A::sub(um[0], up[0]));
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            jum = fma(jw[c], um[c], jum);
-            jup = fma(jw[c], up[c], jup);
-            jdu = fma(jw[c], um[c] - up[c], jdu);
+          for (int c = 1; c < 3; ++c) {
+            A::acc_fma(jum, jw[c], um[c]);
+            A::acc_fma(jup, jw[c], up[c]);
+            A::acc_fma(jdu, jw[c], A::sub(um[c], up[c]));
           }
-          const double wgt = tb.w[q1] * tb.w[q2] * tb.area[d];
+          const V wgt = A::mul(A::mul(tb.w[q1], tb.w[q2]), tb.area[d]);
+          const V lead = side > 0 ? A::add(A::half(unm), lam) : A::sub(A::half(unp), lam);
+          const V extra = side > 0 ? A::add(A::half(A::acc_get_norm(jum)), A::scale_pow2(A::acc_get_norm(jdu), smx))
+                                   : A::add(A::half(A::acc_get_norm(jup)), A::scale_pow2(A::acc_get_norm(jdu), spx));
 #pragma unroll
           for (int e = 0; e < 3; ++e) {
-            double g;
-            if (side > 0) {
-              g = (0.5 * unm + lam) * jw[e];
-              if (e == d) g += 0.5 * jum + smx * jdu;
-            } else {
-              g = (0.5 * unp - lam) * jw[e];
-              if (e == d) g += 0.5 * jup + spx * jdu;
-            }
-            H[e * QQ + it] = wgt * g;
+            V g = A::mul(lead, jw[e]);
+            if (e == d) g = A::add(g, extra);
+            H[e * QQ + it] = A::mul(wgt, g);
           }
         }
       __syncthreads();
       if (active)
         for (int it = t; it < 3 * Q; it += NT) {
           const int c = it / Q, q1 = it - c * Q;
-          double a[N];
-#pragma unroll
-          for (int j = 0; j < N; ++j) a[j] = 0.0;
+          Acc a[N];
 #pragma unroll
           for (int q2 = 0; q2 < Q; ++q2) {
-            const double h = H[c * QQ + q1 + Q * q2];
+            const V h = H[c * QQ + q1 + Q * q2];
 #pragma unroll
-            for (int j = 0; j < N; ++j) a[j] = fma(tb.S[q2 * N + j], h, a[j]);
+            for (int j = 0; j < N; ++j) {
+              if (q2 == 0)
+                A::acc_first(a[j], tb.S[j], h);
+              else
+                A::acc_fma(a[j], tb.S[q2 * N + j], h);
+            }
           }
 #pragma unroll
-          for (int j2 = 0; j2 < N; ++j2) K1[c * Q * N + q1 + Q * j2] = a[j2];
+          for (int j2 = 0; j2 < N; ++j2) K1[c * Q * N + q1 + Q * j2] = A::acc_get_norm(a[j2]);
         }
       __syncthreads();
       if (active)
         for (int it = t; it < 3 * N; it += NT) {
           const int c = it / N, j2 = it - c * N;
-          double a[N];
-#pragma unroll
-          for (int j = 0; j < N; ++j) a[j] = 0.0;
+          Acc a[N];
 #pragma unroll
           for (int q1 = 0; q1 < Q; ++q1) {
-            const double h = K1[c * Q * N + q1 + Q * j2];
+            const V h = K1[c * Q * N + q1 + Q * j2];
 #pragma unroll
-            for (int j = 0; j < N; ++j) a[j] = fma(tb.S[q1 * N + j], h, a[j]);
+            for (int j = 0; j < N; ++j) {
+              if (q1 == 0)
+                A::acc_first(a[j], tb.S[j], h);
+              else
+                A::acc_fma(a[j], tb.S[q1 * N + j], h);
+            }
           }
 #pragma unroll
-          for (int j1 = 0; j1 < N; ++j1) sOut[c * N3 + node3(N, d, aown, t1, j1, t2, j2)] += a[j1];
+          for (int j1 = 0; j1 < N; ++j1) {
+            V& o = sOut[c * N3 + node3(N, d, aown, t1, j1, t2, j2)];
+            o = A::add(o, A::acc_get_norm(a[j1]));
+          }
         }
       __syncthreads();
     }
   }
   if (active)
     for (int c = 0; c < 3; ++c)
-      for (int i = t; i < N3; i += NT) dst3[(c * m.E + el) * N3 + i] = sOut[c * N3 + i];
+      for (int i = t; i < N3; i += NT) dst3[(c * m.E + el) * N3 + i] = A::store(sOut[c * N3 + i]);
 }
 
-template <int N, int Q>
+template <class A, int N, int Q>
 int launch_conv_vjp(const MeshDims& m, const double* u3, const double* w3, double* dst3, const ConvHost& h,
                     cudaStream_t s) {
-  ConvTab<N, Q> tb;
+  VjpTab<typename A::V, N, Q> tb;
   for (int i = 0; i < Q * N; ++i) {
-    tb.S[i] = h.S[i];
-    tb.D[i] = h.D[i];
+    tb.S[i] = A::make(h.S[i]);
+    tb.D[i] = A::make(h.D[i]);
   }
-  for (int q = 0; q < Q; ++q) tb.w[q] = h.w[q];
+  for (int q = 0; q < Q; ++q) tb.w[q] = A::make(h.w[q]);
   for (int d = 0; d < 3; ++d) {
-    tb.jac[d] = h.h[0] * h.h[1] * h.h[2] / h.h[d];
+    tb.jac[d] = A::make(h.h[0] * h.h[1] * h.h[2] / h.h[d]);
     tb.area[d] = tb.jac[d];
   }
   constexpr int EPB = conv_cells_per_block<N>();
   const size_t smem = (size_t)EPB * VjpLayout<N, Q>::PER * sizeof(double);
   if (smem > 232448) return 7;
-  if (cudaFuncSetAttribute(conv_vjp_kernel<N, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+  if (cudaFuncSetAttribute(conv_vjp_kernel<A, N, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return 2;
   if (m.E == 0) return 0;
   const long long blocks = (m.E + EPB - 1) / EPB;
-  conv_vjp_kernel<N, Q><<<(unsigned)blocks, EPB * N * N, smem, s>>>(u3, w3, dst3, tb, m);
+  conv_vjp_kernel<A, N, Q><<<(unsigned)blocks, EPB * N * N, smem, s>>>(u3, w3, dst3, tb, m);
   return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }
 
@@ -1322,11 +1356,15 @@ int convective_launch(int part, const MeshDims& m, const double* u3, double* rfa
 // The VJP kernel keeps u, w and their partial sweeps in shared memory:
 // k <= 7 (N <= 8).
 int convective_vjp(const MeshDims& m, const double* u3, const double* w3, double* dst3, const ConvHost& t,
-                   cudaStream_t s) {
+                   cudaStream_t s, bool emulated) {
   const int N = t.N, Q = t.Q;
 #define DGNS_CONV_VJP(NV)                                                                          \
-  if (N == NV && Q == (3 * NV) / 2) return launch_conv_vjp<NV, (3 * NV) / 2>(m, u3, w3, dst3, t, s); \
-  if (N == NV && Q == NV) return launch_conv_vjp<NV, NV>(m, u3, w3, dst3, t, s);
+  if (N == NV && Q == (3 * NV) / 2)                                                                \
+    return emulated ? launch_conv_vjp<DF64, NV, (3 * NV) / 2>(m, u3, w3, dst3, t, s)               \
+                    : launch_conv_vjp<F64, NV, (3 * NV) / 2>(m, u3, w3, dst3, t, s);               \
+  if (N == NV && Q == NV)                                                                          \
+    return emulated ? launch_conv_vjp<DF64, NV, NV>(m, u3, w3, dst3, t, s)                         \
+                    : launch_conv_vjp<F64, NV, NV>(m, u3, w3, dst3, t, s);
   DGNS_CONV_VJP(2)
   DGNS_CONV_VJP(3)
   DGNS_CONV_VJP(4)

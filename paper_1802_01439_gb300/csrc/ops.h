@@ -86,8 +86,9 @@ struct ConvHost {
 // emulated: double-float arithmetic on the FP32 pipe (else native FP64).
 int convective_launch(int part, const MeshDims& m, const double* u3, double* rface, double* dst3,
                       const ConvHost& t, bool emulated, cudaStream_t s);
+// emulated: double-float arithmetic (else native FP64)
 int convective_vjp(const MeshDims& m, const double* u3, const double* w3, double* dst3,
-                   const ConvHost& t, cudaStream_t s);
+                   const ConvHost& t, cudaStream_t s, bool emulated = false);
 
 // Projection operator M + A_D + A_C and the penalty parameters
 // (k_projection.cu); N = k_u + 1 <= 8.

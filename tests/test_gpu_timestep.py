@@ -21,10 +21,12 @@ def _built():
     build_lib()
 
 
+@pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("n,k,field", [((3, 2, 2), 3, "tgv"), ((2, 2, 3), 2, "rand"), ((1, 2, 1), 4, "rand"),
-                                       ((2, 1, 2), 7, "tgv"), ((2, 2, 2), 1, "rand")])
-def test_convective_vjp(n, k, field):
-    ctx = context(n, k, max(k - 1, 1), mg_precision=0)
+                                       ((2, 1, 2), 7, "tgv"), ((2, 2, 2), 1, "rand"), ((3, 3, 1), 5, "tgv")])
+def test_convective_vjp(n, k, field, mode):
+    """mode 0: native FP64; mode 1: double-float arithmetic."""
+    ctx = context(n, k, max(k - 1, 1), mg_precision=0, fp64_mode=mode)
     s = dg.Space(dg.Mesh(n), k)
     u = tgv_field(s, 1e-3, 0) if field == "tgv" else random_field(s, 3, 1)
     w = random_field(s, 3, 2)
