@@ -52,7 +52,42 @@ struct LapTab {
   // v(middle) at the middle, vO(i) = (v(i) - v(N-1-i)) / 2)
   EOMat<V, N> A0eo[3], Meo;
   V crE[3][(N + 1) / 2], crO[3][N / 2], clE[3][(N + 1) / 2], clO[3][N / 2];
+  double grd[3][N], gld[3][N];   // gr, gl in FP64 (double-float sweeps: native face derivatives)
 };
+
+// Neighbour data of one line in the double-float sweeps: the neighbours'
+// face values r(0) (+ side) and lf(N-1) (- side), split into double-float,
+// and the face-derivative sums gr . r and gl . lf, formed natively in FP64 on
+// the raw doubles: one split each instead of N splits and N emulated
+// multiply-adds per neighbour line (the FP64 pipe is otherwise idle here).
+template <class V>
+struct NbLine {
+  V r0, ln;
+  double dr, dl;
+};
+
+template <class A, int N, int D>
+__device__ __forceinline__ NbLine<typename A::V> load_nb_summary(const double* __restrict__ nbR,
+                                                                 const double* __restrict__ nbL, int l,
+                                                                 const LapTab<typename A::V, N>& tb) {
+  int base, stride;
+  line_geom<D>(l, N, N, N, base, stride);
+  double dr = 0.0, dl = 0.0, r0 = 0.0, ln = 0.0;
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    const double a = __ldg(nbR + base + j * stride), b = __ldg(nbL + base + j * stride);
+    if (j == 0) r0 = a;
+    if (j == N - 1) ln = b;
+    dr = fma(tb.grd[D][j], a, dr);
+    dl = fma(tb.gld[D][j], b, dl);
+  }
+  NbLine<typename A::V> s;
+  s.r0 = A::split(r0);
+  s.ln = A::split(ln);
+  s.dr = dr;
+  s.dl = dl;
+  return s;
+}
 
 // Double-float sweeps use the even-odd form; natively (FP64-pipe bound) and in
 // FP32 (the multigrid level operator, bound by the L1/shared-memory pipe) an
@@ -135,14 +170,13 @@ constexpr bool roll_outputs() {
   return A::emulated && N >= 5;
 }
 
-// One line of T_d x in even-odd form, the neighbour lines r (+ side) and lf
-// (- side) in registers: the coupling through the neighbours' face values
-// (cr r(0) + cl lf(N-1)) goes into the even and odd sums, the coupling
-// through their face derivatives (gr . r into y(N-1), gl . lf into y(0))
-// is added to the outer pair.
+// One line of T_d x in even-odd form (double-float), with the neighbour
+// data nb: the coupling through the neighbours' face values
+// (cr r(0) + cl lf(N-1)) goes into the even and odd sums, the face-derivative
+// sums (gr . r into y(N-1), gl . lf into y(0)) are added to the outer pair.
 template <class A, int N, int D>
 __device__ __forceinline__ void sipg_line_eo(const typename A::V* X, typename A::V* out,
-                                             const typename A::V (&r)[N], const typename A::V (&lf)[N], int l,
+                                             const NbLine<typename A::V>& nb, int l,
                                              const LapTab<typename A::V, N>& tb) {
   typedef typename A::V V;
   typedef typename A::Acc Acc;
@@ -152,7 +186,7 @@ __device__ __forceinline__ void sipg_line_eo(const typename A::V* X, typename A:
   V x[N], xe[NH], xo[NF];
   load_line<V, N>(X, base, stride, x);
   eo_fold<A, N>(x, xe, xo);
-  const V r0 = r[0], ln = lf[N - 1];
+  const V r0 = nb.r0, ln = nb.ln;
 #pragma unroll(eo_roll<N>() ? 1 : NH)
   for (int i = 0; i < NH; ++i) {
     Acc e;
@@ -169,16 +203,8 @@ __device__ __forceinline__ void sipg_line_eo(const typename A::V* X, typename A:
       const V a = A::acc_get(e), b = A::acc_get(o);
       V lo = A::add_nr(a, b), hi = A::sub_nr(a, b);
       if (i == 0) {
-        Acc t, u;
-        A::acc_set(t, lo);
-        A::acc_set(u, hi);
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-          A::acc_fma(t, tb.gl[D][j], lf[j]);
-          A::acc_fma(u, tb.gr[D][j], r[j]);
-        }
-        lo = A::acc_get(t);
-        hi = A::acc_get(u);
+        lo = A::add_nr(lo, A::split(nb.dl));
+        hi = A::add_nr(hi, A::split(nb.dr));
       }
       out[base + i * stride] = lo;
       out[base + (N - 1 - i) * stride] = hi;
@@ -199,49 +225,49 @@ __device__ __forceinline__ void sipg_line(const typename A::V* X, typename A::V*
   int base, stride, gbase, gstride;
   sline<N, D>(l, base, stride);
   line_geom<D>(l, N, N, N, gbase, gstride);
-  V x[N], r[N], lf[N];
-  Acc y[N];
-#pragma unroll
-  for (int j = 0; j < N; ++j) {
-    r[j] = A::load(nbR + gbase + j * gstride);
-    lf[j] = A::load(nbL + gbase + j * gstride);
-  }
   if constexpr (eo_sweeps<A, N>()) {
-    sipg_line_eo<A, N, D>(X, out, r, lf, l, tb);
-    return;
-  }
-  load_line<V, N>(X, base, stride, x);
-  if constexpr (roll_outputs<A, N>()) {
-#pragma unroll 1
-    for (int i = 0; i < N; ++i) {
-      Acc yi;
-      A::acc_first(yi, tb.cr[D][i], r[0]);
-      A::acc_fma(yi, tb.cl[D][i], lf[N - 1]);
-#pragma unroll
-      for (int j = 0; j < N; ++j) A::acc_fma(yi, tb.A0[D][i * N + j], x[j]);
-      if (i == N - 1)
-#pragma unroll
-        for (int j = 0; j < N; ++j) A::acc_fma(yi, tb.gr[D][j], r[j]);
-      if (i == 0)
-#pragma unroll
-        for (int j = 0; j < N; ++j) A::acc_fma(yi, tb.gl[D][j], lf[j]);
-      out[base + i * stride] = A::acc_get(yi);
-    }
+    sipg_line_eo<A, N, D>(X, out, load_nb_summary<A, N, D>(nbR, nbL, l, tb), l, tb);
   } else {
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      A::acc_first(y[i], tb.cr[D][i], r[0]);
-      A::acc_fma(y[i], tb.cl[D][i], lf[N - 1]);
-#pragma unroll
-      for (int j = 0; j < N; ++j) A::acc_fma(y[i], tb.A0[D][i * N + j], x[j]);
-    }
+    V x[N], r[N], lf[N];
+    Acc y[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-      A::acc_fma(y[N - 1], tb.gr[D][j], r[j]);
-      A::acc_fma(y[0], tb.gl[D][j], lf[j]);
+      r[j] = A::load(nbR + gbase + j * gstride);
+      lf[j] = A::load(nbL + gbase + j * gstride);
     }
+    load_line<V, N>(X, base, stride, x);
+    if constexpr (roll_outputs<A, N>()) {
+#pragma unroll 1
+      for (int i = 0; i < N; ++i) {
+        Acc yi;
+        A::acc_first(yi, tb.cr[D][i], r[0]);
+        A::acc_fma(yi, tb.cl[D][i], lf[N - 1]);
 #pragma unroll
-    for (int i = 0; i < N; ++i) out[base + i * stride] = A::acc_get(y[i]);
+        for (int j = 0; j < N; ++j) A::acc_fma(yi, tb.A0[D][i * N + j], x[j]);
+        if (i == N - 1)
+#pragma unroll
+          for (int j = 0; j < N; ++j) A::acc_fma(yi, tb.gr[D][j], r[j]);
+        if (i == 0)
+#pragma unroll
+          for (int j = 0; j < N; ++j) A::acc_fma(yi, tb.gl[D][j], lf[j]);
+        out[base + i * stride] = A::acc_get(yi);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        A::acc_first(y[i], tb.cr[D][i], r[0]);
+        A::acc_fma(y[i], tb.cl[D][i], lf[N - 1]);
+#pragma unroll
+        for (int j = 0; j < N; ++j) A::acc_fma(y[i], tb.A0[D][i * N + j], x[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        A::acc_fma(y[N - 1], tb.gr[D][j], r[j]);
+        A::acc_fma(y[0], tb.gl[D][j], lf[j]);
+      }
+#pragma unroll
+      for (int i = 0; i < N; ++i) out[base + i * stride] = A::acc_get(y[i]);
+    }
   }
 }
 
@@ -252,10 +278,6 @@ __device__ __forceinline__ void sipg_line_pre(const typename A::V* X, typename A
                                               const LapTab<typename A::V, N>& tb) {
   typedef typename A::V V;
   typedef typename A::Acc Acc;
-  if constexpr (eo_sweeps<A, N>()) {
-    sipg_line_eo<A, N, D>(X, out, r, lf, l, tb);
-    return;
-  }
   int base, stride;
   sline<N, D>(l, base, stride);
   V x[N];
@@ -461,7 +483,22 @@ __global__ void __launch_bounds__(cells_per_block<N>() * N * N)
     nb[4] = cb + (size_t)neighbor32<2>(cx, +1, m) * NNN;
     nb[5] = cb + (size_t)neighbor32<2>(cx, -1, m) * NNN;
   }
-  if constexpr (prefetch_neighbours<N>()) {
+  if constexpr (eo_sweeps<A, N>() && prefetch_neighbours<N>()) {
+    // double-float: the neighbour summaries of the three directions first
+    NbLine<V> n0{}, n1{}, n2{};
+    if (active) {
+      n0 = load_nb_summary<A, N, 0>(nb[0], nb[1], l, tb);
+      n1 = load_nb_summary<A, N, 1>(nb[2], nb[3], l, tb);
+      n2 = load_nb_summary<A, N, 2>(nb[4], nb[5], l, tb);
+    }
+    if (active) load_xline<A, N>(gsrc + slot * NNN + l * N, sX + off + l * padx<N>());
+    __syncthreads();
+    if (active) {
+      sipg_line_eo<A, N, 0>(sX + off, sA + off, n0, l, tb);
+      sipg_line_eo<A, N, 1>(sX + off, sB + off, n1, l, tb);
+      sipg_line_eo<A, N, 2>(sX + off, sC + off, n2, l, tb);
+    }
+  } else if constexpr (prefetch_neighbours<N>()) {
     V r0[N], l0[N], r1[N], l1[N], r2[N], l2[N];
     if (active) {
       load_nb_lines<A, N, 0>(nb[0], nb[1], l, r0, l0);
@@ -616,6 +653,11 @@ int launch_sipg(const MeshDims& m, int ncomp, const typename A::G* src, typename
       }
     }
     split(h.M, tb.Meo);
+    for (int d = 0; d < 3; ++d)
+      for (int i = 0; i < N; ++i) {
+        tb.grd[d][i] = h.gr[d][i];
+        tb.gld[d][i] = h.gl[d][i];
+      }
   }
   EpiArgs<G> ea{(const G*)eh.b, (const G*)eh.xprev, (const G*)eh.dinv, (G)eh.c1, (G)eh.c2};
   const long long ncells = m.E * ncomp;
