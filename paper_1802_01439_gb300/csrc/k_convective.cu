@@ -626,14 +626,17 @@ __global__ void __launch_bounds__(conv_groups_per_block<N>() * conv_threads<N>()
     const int x = rr % N, yz = rr / N;
     const int y = yz % N, z = yz / N;
     const double* rc = reinterpret_cast<const double*>(sU1g + j * LY::U1R) + c * NN;
-    V v = A::acc_get_norm(out[r]);
-    if (x == N - 1) v = A::add(v, A::split(rc[0 * 3 * NN + y + N * z]));
-    if (x == 0) v = A::sub(v, A::split(rc[1 * 3 * NN + y + N * z]));
-    if (y == N - 1) v = A::add(v, A::split(rc[2 * 3 * NN + x + N * z]));
-    if (y == 0) v = A::sub(v, A::split(rc[3 * 3 * NN + x + N * z]));
-    if (z == N - 1) v = A::add(v, A::split(rc[4 * 3 * NN + x + N * y]));
-    if (z == 0) v = A::sub(v, A::split(rc[5 * 3 * NN + x + N * y]));
-    dst3[((size_t)c * m.E + pick2(j, el0, el1)) * N3 + rr] = A::store(v);
+    // the face integrals arrive as doubles: added natively after the cell
+    // term's conversion (a few FP64 additions instead of splits and
+    // emulated additions)
+    double v = A::to_double(A::acc_get_norm(out[r]));
+    if (x == N - 1) v += rc[0 * 3 * NN + y + N * z];
+    if (x == 0) v -= rc[1 * 3 * NN + y + N * z];
+    if (y == N - 1) v += rc[2 * 3 * NN + x + N * z];
+    if (y == 0) v -= rc[3 * 3 * NN + x + N * z];
+    if (z == N - 1) v += rc[4 * 3 * NN + x + N * y];
+    if (z == 0) v -= rc[5 * 3 * NN + x + N * y];
+    dst3[((size_t)c * m.E + pick2(j, el0, el1)) * N3 + rr] = v;
   }
 }
 
