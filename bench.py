@@ -52,8 +52,8 @@ DF_FP32_PER_FP64 = 7.5
 # capture of the same workload (dram__bytes_read.sum + dram__bytes_write.sum),
 # keyed by (kernel, fp64_mode); None where no capture of the current kernel
 # exists.
-KERNEL_TRAFFIC = {("conv_kernel", 1): 105.6e6, ("conv_kernel", 0): None,
-                  ("conv_face_kernel", 1): 57.2e6, ("conv_face_kernel", 0): None}
+KERNEL_TRAFFIC = {("conv_kernel", 1): 108.9e6, ("conv_kernel", 0): None,
+                  ("conv_face_kernel", 1): 57.4e6, ("conv_face_kernel", 0): None}
 
 
 # ----------------------------------------------------------- flop counts
