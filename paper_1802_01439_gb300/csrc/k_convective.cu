@@ -83,16 +83,17 @@ template <bool EM, int N>
 constexpr bool face_lines() {
   return EM && N <= 8;
 }
-// Face kernel groups: one warp for FPG faces (two faces up to N = 4, where
-// one face has too few items per phase for 32 lanes); with one output per
-// thread four warps for one face from N = 7 on.
+// Face kernel groups: one warp for FPG faces (four faces up to N = 3, two at
+// N = 4, where one face has too few items per phase for 32 lanes; four at
+// N = 4 measured slower: fewer warps per SM); with one output per thread
+// four warps for one face from N = 7 on.
 template <bool L, int N>
 constexpr int face_threads() {
   return (L || N <= 6) ? 32 : 128;
 }
 template <int N>
 constexpr int faces_per_group() {
-  return N <= 4 ? 2 : 1;
+  return N <= 3 ? 4 : (N == 4 ? 2 : 1);
 }
 template <bool L, int N, int Q>
 constexpr int face_groups_per_block();
@@ -676,10 +677,10 @@ __global__ void __launch_bounds__(face_groups_per_block<face_lines<A::emulated, 
       sSW[i] = tb.SW[i];
     }
   const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
-  static_assert(FPG == 1 || FPG == 2, "one or two faces per group");
+  static_assert(FPG == 1 || FPG == 2 || FPG == 4, "one, two or four faces per group");
   // cells of the group's faces (scalars, not an array indexed by a runtime
   // face number, which would live in local memory)
-  unsigned el0 = 0, nb0 = 0, el1 = 0, nb1 = 0;
+  unsigned el0 = 0, nb0 = 0, el1 = 0, nb1 = 0, el2 = 0, nb2 = 0, el3 = 0, nb3 = 0;
   int nact = 0;
 #pragma unroll
   for (int f = 0; f < FPG; ++f) {
@@ -690,13 +691,21 @@ __global__ void __launch_bounds__(face_groups_per_block<face_lines<A::emulated, 
       if (f == 0) {
         el0 = cx.el;
         nb0 = nbf;
-      } else {
+      } else if (f == 1) {
         el1 = cx.el;
         nb1 = nbf;
+      } else if (f == 2) {
+        el2 = cx.el;
+        nb2 = nbf;
+      } else {
+        el3 = cx.el;
+        nb3 = nbf;
       }
       nact = f + 1;
     }
   }
+  auto face_el = [&](int f) { return f < 2 ? (f == 0 ? el0 : el1) : (f == 2 ? el2 : el3); };
+  auto face_nb = [&](int f) { return f < 2 ? (f == 0 ? nb0 : nb1) : (f == 2 ? nb2 : nb3); };
   // per face f: T0 [s][c][j1 + N j2] (s = 0: '-', 1: '+'), later K1 [c][q1 + Q j2];
   // G1 [s][c][q1 + Q j2], later H [c][q1 + Q q2]; G2 [s][c][q1 + Q q2]
 #define FACE_T0(f) (base + (f) * LY::PER)
@@ -708,7 +717,7 @@ __global__ void __launch_bounds__(face_groups_per_block<face_lines<A::emulated, 
     const int sc = i / NN, r = i - sc * NN;
     const int sd = sc / 3, c = sc - 3 * sd;
     const int j1 = r % N, j2 = r / N;
-    const unsigned cell = sd == 0 ? (f == 0 ? el0 : el1) : (f == 0 ? nb0 : nb1);
+    const unsigned cell = sd == 0 ? face_el(f) : face_nb(f);
     FACE_T0(f)[i] = A::load(u3 + ((size_t)c * m.E + cell) * N3 + node3(N, d, sd == 0 ? N - 1 : 0, t1, j1, t2, j2));
   }
   group_sync<FT>();
@@ -804,7 +813,7 @@ __global__ void __launch_bounds__(face_groups_per_block<face_lines<A::emulated, 
       const int c = i / N, j2 = i - c * N;
       V o[N];
       test_eo<A, N, Q>(tb.EO[1], FACE_T0(f) + c * QN + Q * j2, 1, o);
-      double* dst = rface + ((size_t)d * m.E + (f == 0 ? el0 : el1)) * 3 * NN + c * NN + N * j2;
+      double* dst = rface + ((size_t)d * m.E + face_el(f)) * 3 * NN + c * NN + N * j2;
 #pragma unroll
       for (int j1 = 0; j1 < N; ++j1) dst[j1] = A::store(A::mul(area, o[j1]));
     }
@@ -818,7 +827,7 @@ __global__ void __launch_bounds__(face_groups_per_block<face_lines<A::emulated, 
       A::acc_first(a, sSW[j1], k[0]);
 #pragma unroll
       for (int q1 = 1; q1 < Q; ++q1) A::acc_fma(a, sSW[q1 * N + j1], k[q1]);
-      rface[((size_t)d * m.E + (f == 0 ? el0 : el1)) * 3 * NN + i] = A::store(A::mul(area, A::acc_get_norm(a)));
+      rface[((size_t)d * m.E + face_el(f)) * 3 * NN + i] = A::store(A::mul(area, A::acc_get_norm(a)));
     }
   }
 #undef FACE_T0
