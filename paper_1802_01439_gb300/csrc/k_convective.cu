@@ -806,7 +806,9 @@ __global__ void __launch_bounds__(face_groups_per_block<face_lines<A::emulated, 
   }
   group_sync<FT>();
   // F5: test along t1 (weights w_q1), times the face area, store
-  const V area = tb.area[d];
+  // the face area scales the stored results in FP64 (one multiplication
+  // after the conversion instead of an emulated product)
+  const double area = A::to_double(tb.area[d]);
   if (L) {   // item (f, c, j2)
     for (int it = t; it < nact * 3 * N; it += FT) {
       const int f = it / (3 * N), i = it - f * 3 * N;
@@ -815,7 +817,7 @@ __global__ void __launch_bounds__(face_groups_per_block<face_lines<A::emulated, 
       test_eo<A, N, Q>(tb.EO[1], FACE_T0(f) + c * QN + Q * j2, 1, o);
       double* dst = rface + ((size_t)d * m.E + face_el(f)) * 3 * NN + c * NN + N * j2;
 #pragma unroll
-      for (int j1 = 0; j1 < N; ++j1) dst[j1] = A::store(A::mul(area, o[j1]));
+      for (int j1 = 0; j1 < N; ++j1) dst[j1] = area * A::to_double(o[j1]);
     }
   } else {   // item (f, c, j2, j1)
     for (int it = t; it < nact * 3 * NN; it += FT) {
@@ -827,7 +829,7 @@ __global__ void __launch_bounds__(face_groups_per_block<face_lines<A::emulated, 
       A::acc_first(a, sSW[j1], k[0]);
 #pragma unroll
       for (int q1 = 1; q1 < Q; ++q1) A::acc_fma(a, sSW[q1 * N + j1], k[q1]);
-      rface[((size_t)d * m.E + face_el(f)) * 3 * NN + i] = A::store(A::mul(area, A::acc_get_norm(a)));
+      rface[((size_t)d * m.E + face_el(f)) * 3 * NN + i] = area * A::to_double(A::acc_get_norm(a));
     }
   }
 #undef FACE_T0
