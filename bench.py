@@ -74,6 +74,24 @@ def conv_face_flops(N, Q):
             + 2 * 3 * Q * Q * N + 2 * 3 * Q * N * N + 3 * N * N)
 
 
+def step_hbm(nu, npr, ms):
+    """The whole step against the HBM roofline: algorithmic bytes (every
+    operator reads its input vector once and writes its output once: C, M^-1
+    and H on 3 velocity components, D velocity -> pressure, L on the pressure,
+    G pressure -> velocity) per step time, over the measured copy bandwidth
+    (MEASURED_PEAKS.json hbm_gbs, else the 6.8 TB/s fallback)."""
+    peak, src = 6800.0, "fallback 6.8 TB/s"
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as fh:
+            peak, src = float(json.load(fh)["hbm_gbs"]), "measured copy bandwidth (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        pass
+    nbytes = 8 * (2 * 3 * nu + 2 * 3 * nu + (3 * nu + npr) + 2 * npr + (npr + 3 * nu) + 2 * 3 * nu)
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    return {"algorithmic_bytes": nbytes, "achieved_GBps": round(gbs, 1), "peak_GBps": peak,
+            "frac": round(gbs / peak, 4), "peak_source": src}
+
+
 def lap_flops_per_cell(N):
     """8 sweeps + neighbour terms: N^2 lines x (3 (N^2 + 4N) + 5 N^2) FMA."""
     return 2 * N * N * (3 * (N * N + 4 * N) + 5 * N * N)
@@ -258,6 +276,7 @@ def gpu_arm(args, rank, world):
                      "peak": peak, "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
                      "traffic": KERNEL_TRAFFIC.get((kbase, args.fp64_mode)), "flops_per_launch": fl,
                      "peak_source": psrc},
+        "step_hbm": step_hbm(nu_, np_, ms),
         "e2e": {"value": round(world * dofs_per_step / (e2e * 1e-3), 1), "unit": "DoFs/s",
                 "h2d_bytes_per_step": 3 * nu_ * 8, "d2h_bytes_per_step": 3 * nu_ * 8},
         "gpu_launches": 7 * args.steps,  # face + cell convective, M^-1, D, L, G, H
