@@ -64,7 +64,10 @@ struct ConvLayout {
   static constexpr int N3 = N * N * N;
   static constexpr int U = 3 * N3;               // nodal velocity
   static constexpr int U1 = 3 * Q * N * N;       // x-interpolated
-  static constexpr int U1R = U1 > 18 * N * N ? U1 : 18 * N * N;  // later: the six face integrals
+  // later: the six face integrals, and from N = 11 on the folded products of
+  // the x tests (8 Q^2, see conv_split_xtest)
+  static constexpr int R = 18 * N * N + (N >= 11 ? 8 * Q * Q : 0);
+  static constexpr int U1R = U1 > R ? U1 : R;
   static constexpr int U2 = 3 * Q * Q * N;       // xy-interpolated
   static constexpr int P = 3 * Q * Q;            // one z-plane: u
   static constexpr int X = 8 * N * Q;            // x-tested plane (eight distinct tests)
@@ -252,6 +255,17 @@ __device__ __forceinline__ int xtest2(int c) { return c == 0 ? 6 : (c == 1 ? 5 :
 template <int N>
 constexpr bool conv_pair_rows() {
   return N == 4;
+}
+
+// From N = 11 on (512 threads per cell, one cell per SM) the 8 Q x-test rows
+// leave most of the SM idle, so the x tests run in two phases: the products
+// u_c u_d of every row folded into sums and differences (item
+// (k, qy, i < (Q+1)/2)), then the even-odd contraction (item (k, qy, output
+// pair)).  Measured: +4-7 % at N = 11, 12; 5-15 % slower at N = 7..10, where
+// other blocks on the SM use the issue slots of the idle warps.
+template <int N>
+constexpr bool conv_split_xtest() {
+  return N >= 11;
 }
 
 // x test of one row of the plane (Q points u_c u_d -> N outputs) in even-odd
@@ -503,6 +517,47 @@ __global__ void __launch_bounds__(conv_groups_per_block<N>() * conv_threads<N>()
     // rows an item tests the rows p and Q-1-p and stores their sum in row p
     // and their difference in row (Q+1)/2 + p of the test's block (the
     // middle row of odd Q alone, in row p); else one row per item.
+    if constexpr (conv_split_xtest<N>()) {
+      static_assert(CPG == 1, "one cell per group");
+      V* sFE = reinterpret_cast<V*>(sU1g) + 18 * NN;   // behind the face integrals
+      V* sFO = sFE + 8 * Q * QH;
+      for (int it = t; it < 8 * Q * QH; it += NT) {   // item (k, qy, i)
+        const int k = it / (Q * QH), l = it - k * Q * QH;
+        const int qy = l / QH, i = l - qy * QH;
+        const V* uc = sPg + test_c(k) * QQ + Q * qy;
+        const V* ud = sPg + test_d(k) * QQ + Q * qy;
+        if (i < QF) {
+          const V f1 = A::mul_nr(uc[i], ud[i]), f2 = A::mul_nr(uc[Q - 1 - i], ud[Q - 1 - i]);
+          sFE[it] = A::add_nr(f1, f2);
+          sFO[(k * Q + qy) * QF + i] = A::sub_nr(f1, f2);
+        } else {
+          sFE[it] = A::mul_nr(uc[QF], ud[QF]);   // middle point of odd Q
+        }
+      }
+      group_sync<NT>();
+      for (int it = t; it < 8 * Q * NH; it += NT) {   // item (k, qy, x)
+        const int k = it / (Q * NH), l = it - k * Q * NH;
+        const int qy = l / NH, x = l - qy * NH;
+        const V* T1 = sEO + (k < 3 ? 0 : Q * NH);
+        const V* T2 = T1 + QH * NH;
+        const V* fe = sFE + (k * Q + qy) * QH;
+        const V* fo = sFO + (k * Q + qy) * QF;
+        Acc r1, r2;
+        A::acc_first(r1, T1[x], fe[0]);
+#pragma unroll
+        for (int i = 1; i < QH; ++i) A::acc_fma(r1, T1[i * NH + x], fe[i]);
+        A::acc_first(r2, T2[x], fo[0]);
+#pragma unroll
+        for (int i = 1; i < QF; ++i) A::acc_fma(r2, T2[i * NH + x], fo[i]);
+        const V a = A::acc_get(r1), b = A::acc_get(r2);
+        V* xo = sXg + (k * Q + qy) * N;
+        xo[x] = A::add(a, b);
+        if (x < NF) {
+          const V d = A::sub(a, b);
+          xo[N - 1 - x] = k < 3 ? A::neg(d) : d;
+        }
+      }
+    } else
 #pragma unroll
     for (int r = 0; r < R2; ++r) {
       const int it = t + NT * r;
