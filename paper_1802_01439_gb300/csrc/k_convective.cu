@@ -16,6 +16,11 @@
 //             with the face-layer basis: +R for the '-' cell, -R for the '+'
 //             cell.  A face kernel evaluates every face once and writes R;
 //             the cell kernel adds the six R of its faces on its way out.
+// Even-odd.   On the symmetric LGL nodes and Gauss points S and S w are
+//             symmetric and D w antisymmetric under the reflection
+//             (q, j) -> (Q-1-q, N-1-j), so a line of values folds into sums and
+//             differences and every interpolation or test of a whole line
+//             is two half-size contractions (interp_eo, test_eo, xtest_row).
 //
 // Accuracy.  For smooth fields the weak-form cell and face sums nearly cancel
 // (the result is O(h) smaller than the summed terms, more so at high k), so
@@ -557,31 +562,32 @@ __global__ void __launch_bounds__(conv_groups_per_block<N>() * conv_threads<N>()
           xo[N - 1 - x] = k < 3 ? A::neg(d) : d;
         }
       }
-    } else
+    } else {
 #pragma unroll
-    for (int r = 0; r < R2; ++r) {
-      const int it = t + NT * r;
-      if (I2 % NT != 0 && it >= I2) break;
-      const V* T1 = sEO + o2t[r];
-      const V* T2 = T1 + QH * NH;
-      const bool anti = o2t[r] == 0;
-      V xa[N];
-      xtest_row<A, N, Q>(T1, T2, anti, sPg + o2c[r], sPg + o2d[r], xa);
-      V* xo = sXg + o2x[r];
-      if (PR && (Q % 2 == 0 || o2b[r] != 0)) {
-        V xb[N];
-        xtest_row<A, N, Q>(T1, T2, anti, sPg + o2c[r] + o2b[r], sPg + o2d[r] + o2b[r], xb);
+      for (int r = 0; r < R2; ++r) {
+        const int it = t + NT * r;
+        if (I2 % NT != 0 && it >= I2) break;
+        const V* T1 = sEO + o2t[r];
+        const V* T2 = T1 + QH * NH;
+        const bool anti = o2t[r] == 0;
+        V xa[N];
+        xtest_row<A, N, Q>(T1, T2, anti, sPg + o2c[r], sPg + o2d[r], xa);
+        V* xo = sXg + o2x[r];
+        if (PR && (Q % 2 == 0 || o2b[r] != 0)) {
+          V xb[N];
+          xtest_row<A, N, Q>(T1, T2, anti, sPg + o2c[r] + o2b[r], sPg + o2d[r] + o2b[r], xb);
 #pragma unroll
-        for (int x = 0; x < N; ++x) {
-          xo[x] = A::add(xa[x], xb[x]);
-          xo[QH * N + x] = A::sub(xa[x], xb[x]);
-        }
-      } else {
+          for (int x = 0; x < N; ++x) {
+            xo[x] = A::add(xa[x], xb[x]);
+            xo[QH * N + x] = A::sub(xa[x], xb[x]);
+          }
+        } else {
 #pragma unroll
-        for (int x = 0; x < N; ++x) {
-          Acc n;
-          A::acc_set(n, xa[x]);
-          xo[x] = A::acc_get_norm(n);
+          for (int x = 0; x < N; ++x) {
+            Acc n;
+            A::acc_set(n, xa[x]);
+            xo[x] = A::acc_get_norm(n);
+          }
         }
       }
     }
