@@ -19,6 +19,11 @@
 // and three work arrays are staged in shared memory; neighbour lines are read
 // directly from global memory (they are L2 resident).  Global loads and
 // stores of the own cells are coalesced over the block's contiguous cells.
+//
+// Double-float.  M and the cell part of T_d are centrosymmetric on the LGL
+// nodes, so every line sweep runs in even-odd form (about half the emulated
+// multiply-adds), and the neighbours' face-derivative sums are formed in
+// native FP64 on the loaded doubles (load_nb_summary).
 #include <algorithm>
 #include <cmath>
 
