@@ -167,14 +167,6 @@ __device__ __forceinline__ int spos(int i) {
   return cell * cell_stride<N>() + (r % N) + padx<N>() * (r / N);
 }
 
-// Double-float lines from N = 5 on loop over their outputs instead of
-// unrolling them: the unrolled kernel no longer fits the instruction cache
-// (measured: 12-23 % faster for k = 4..7, 4-11 % slower for k = 2, 3).
-template <class A, int N>
-constexpr bool roll_outputs() {
-  return A::emulated && N >= 5;
-}
-
 // One line of T_d x in even-odd form (double-float), with the neighbour
 // data nb: the coupling through the neighbours' face values
 // (cr r(0) + cl lf(N-1)) goes into the even and odd sums, the face-derivative
@@ -219,107 +211,66 @@ __device__ __forceinline__ void sipg_line_eo(const typename A::V* X, typename A:
   }
 }
 
-// One line of T_d x for the own cell, with the neighbour terms.
+// One line of T_d x in the direct form (native FP64 and FP32): the cell part,
+// the coupling through the neighbours' face values (cr r(0) + cl lf(N-1)) and
+// the face-derivative terms (gr . r into y(N-1), gl . lf into y(0)).
+template <class A, int N, int D>
+__device__ __forceinline__ void sipg_line_direct(const typename A::V (&x)[N], const typename A::V (&r)[N],
+                                                 const typename A::V (&lf)[N], typename A::V* out, int base,
+                                                 int stride, const LapTab<typename A::V, N>& tb) {
+  typedef typename A::Acc Acc;
+  Acc y[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    A::acc_first(y[i], tb.cr[D][i], r[0]);
+    A::acc_fma(y[i], tb.cl[D][i], lf[N - 1]);
+#pragma unroll
+    for (int j = 0; j < N; ++j) A::acc_fma(y[i], tb.A0[D][i * N + j], x[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    A::acc_fma(y[N - 1], tb.gr[D][j], r[j]);
+    A::acc_fma(y[0], tb.gl[D][j], lf[j]);
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) out[base + i * stride] = A::acc_get(y[i]);
+}
+
+// One line of T_d x for the own cell, with the neighbour terms read here.
 template <class A, int N, int D>
 __device__ __forceinline__ void sipg_line(const typename A::V* X, typename A::V* out,
                                           const typename A::G* __restrict__ nbR,
                                           const typename A::G* __restrict__ nbL, int l,
                                           const LapTab<typename A::V, N>& tb) {
   typedef typename A::V V;
-  typedef typename A::Acc Acc;
-  int base, stride, gbase, gstride;
-  sline<N, D>(l, base, stride);
-  line_geom<D>(l, N, N, N, gbase, gstride);
   if constexpr (eo_sweeps<A, N>()) {
     sipg_line_eo<A, N, D>(X, out, load_nb_summary<A, N, D>(nbR, nbL, l, tb), l, tb);
   } else {
+    int base, stride, gbase, gstride;
+    sline<N, D>(l, base, stride);
+    line_geom<D>(l, N, N, N, gbase, gstride);
     V x[N], r[N], lf[N];
-    Acc y[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) {
       r[j] = A::load(nbR + gbase + j * gstride);
       lf[j] = A::load(nbL + gbase + j * gstride);
     }
     load_line<V, N>(X, base, stride, x);
-    if constexpr (roll_outputs<A, N>()) {
-#pragma unroll 1
-      for (int i = 0; i < N; ++i) {
-        Acc yi;
-        A::acc_first(yi, tb.cr[D][i], r[0]);
-        A::acc_fma(yi, tb.cl[D][i], lf[N - 1]);
-#pragma unroll
-        for (int j = 0; j < N; ++j) A::acc_fma(yi, tb.A0[D][i * N + j], x[j]);
-        if (i == N - 1)
-#pragma unroll
-          for (int j = 0; j < N; ++j) A::acc_fma(yi, tb.gr[D][j], r[j]);
-        if (i == 0)
-#pragma unroll
-          for (int j = 0; j < N; ++j) A::acc_fma(yi, tb.gl[D][j], lf[j]);
-        out[base + i * stride] = A::acc_get(yi);
-      }
-    } else {
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        A::acc_first(y[i], tb.cr[D][i], r[0]);
-        A::acc_fma(y[i], tb.cl[D][i], lf[N - 1]);
-#pragma unroll
-        for (int j = 0; j < N; ++j) A::acc_fma(y[i], tb.A0[D][i * N + j], x[j]);
-      }
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        A::acc_fma(y[N - 1], tb.gr[D][j], r[j]);
-        A::acc_fma(y[0], tb.gl[D][j], lf[j]);
-      }
-#pragma unroll
-      for (int i = 0; i < N; ++i) out[base + i * stride] = A::acc_get(y[i]);
-    }
+    sipg_line_direct<A, N, D>(x, r, lf, out, base, stride, tb);
   }
 }
 
-// Same, with the neighbour lines already in registers.
+// Same (direct form), with the neighbour lines already in registers.
 template <class A, int N, int D>
 __device__ __forceinline__ void sipg_line_pre(const typename A::V* X, typename A::V* out,
                                               const typename A::V (&r)[N], const typename A::V (&lf)[N], int l,
                                               const LapTab<typename A::V, N>& tb) {
   typedef typename A::V V;
-  typedef typename A::Acc Acc;
   int base, stride;
   sline<N, D>(l, base, stride);
   V x[N];
-  Acc y[N];
   load_line<V, N>(X, base, stride, x);
-  if constexpr (roll_outputs<A, N>()) {
-#pragma unroll 1
-    for (int i = 0; i < N; ++i) {
-      Acc yi;
-      A::acc_first(yi, tb.cr[D][i], r[0]);
-      A::acc_fma(yi, tb.cl[D][i], lf[N - 1]);
-#pragma unroll
-      for (int j = 0; j < N; ++j) A::acc_fma(yi, tb.A0[D][i * N + j], x[j]);
-      if (i == N - 1)
-#pragma unroll
-        for (int j = 0; j < N; ++j) A::acc_fma(yi, tb.gr[D][j], r[j]);
-      if (i == 0)
-#pragma unroll
-        for (int j = 0; j < N; ++j) A::acc_fma(yi, tb.gl[D][j], lf[j]);
-      out[base + i * stride] = A::acc_get(yi);
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      A::acc_first(y[i], tb.cr[D][i], r[0]);
-      A::acc_fma(y[i], tb.cl[D][i], lf[N - 1]);
-#pragma unroll
-      for (int j = 0; j < N; ++j) A::acc_fma(y[i], tb.A0[D][i * N + j], x[j]);
-    }
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-      A::acc_fma(y[N - 1], tb.gr[D][j], r[j]);
-      A::acc_fma(y[0], tb.gl[D][j], lf[j]);
-    }
-#pragma unroll
-    for (int i = 0; i < N; ++i) out[base + i * stride] = A::acc_get(y[i]);
-  }
+  sipg_line_direct<A, N, D>(x, r, lf, out, base, stride, tb);
 }
 
 template <class A, int N, int D>
@@ -395,21 +346,6 @@ __device__ __forceinline__ void mass_line(const typename A::V* in, const typenam
         if (ADD) v = A::add_nr(v, add[base + i * stride]);
         out[base + i * stride] = v;
       }
-    }
-  } else if constexpr (roll_outputs<A, N>()) {
-#pragma unroll 1
-    for (int i = 0; i < N; ++i) {
-      Acc yi;
-      if (ADD)
-        A::acc_set(yi, add[base + i * stride]);
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        if (ADD || j > 0)
-          A::acc_fma(yi, M[i * N + j], x[j]);
-        else
-          A::acc_first(yi, M[i * N + j], x[j]);
-      }
-      out[base + i * stride] = A::acc_get(yi);
     }
   } else {
 #pragma unroll
