@@ -487,8 +487,7 @@ def reference_arm(args, rank, world):
     sample = "oracle (numpy/LAPACK FP64) on the full 32^3, k_u=3/k_p=2 operator set, mean of the timed steps"
     return {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "DoFs/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec * 1e3, 3),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (Taylor-Green + seeded noise)",
             "config": {"workload": WORKLOAD, "n_elem": N_ELEM, "degree_u": K_U, "degree_p": K_P},
             "cpu_baseline": {"value": round(value, 1), "unit": "DoFs/s", "cores": cores, "kind": "oracle",
