@@ -442,3 +442,67 @@ def test_convective_magnitude_bounds_the_result():
     # a smooth field: the weak form cancels, the magnitude does not
     ut = np.stack(s.interpolate(dg.taylor_green))
     assert np.max(np.abs(C.apply(ut))) < 0.5 * np.max(C.magnitude(ut))
+
+
+def _brute_force_sipg(mesh, k, penalty_factor=1.0):
+    """Global SIPG matrix entry by entry from the bilinear form (the cell
+    terms of l_h of Sec. 3.2 and, per interior face with n = +e_a,
+    -{{d_n q}} [p] - [q] {{d_n p}} + tau [q] [p], tau = pf (k+1)^2 / h_a),
+    integrated by (k+2)-point Gauss quadrature in physical coordinates over
+    every cell and face for every pair of global basis functions (tensor
+    Lagrange polynomials on each cell's LGL nodes, zero outside it).  Shares
+    nothing with the element and face matrices of dg.Laplace."""
+    N, nq = k + 1, k + 2
+    nodes = rules.lgl_nodes(k)
+    xq, wq = rules.gauss(nq)
+    V, D = rules.lagrange(nodes, xq)               # (nq, N) on [0, 1]
+    V01, D01 = rules.lagrange(nodes, [0.0, 1.0])   # face values and derivatives
+    h = mesh.h
+    nd = N ** 3
+    A = np.zeros((mesh.E * nd, mesh.E * nd))
+    loc = [(i % N, (i // N) % N, i // (N * N)) for i in range(nd)]
+    # cell terms: sum_d int (d_d phi_I)(d_d phi_J), d_d = (1/h_d) d/dxi_d
+    grads = []
+    for d in range(3):
+        g = np.zeros((nq ** 3, nd))
+        for i, (a, b, c) in enumerate(loc):
+            f = [V[:, a], V[:, b], V[:, c]]
+            f[d] = D[:, (a, b, c)[d]] / h[d]
+            g[:, i] = np.kron(f[2], np.kron(f[1], f[0]))
+        grads.append(g)
+    w3 = np.kron(wq, np.kron(wq, wq)) * np.prod(h)
+    Ke = sum(g.T @ (w3[:, None] * g) for g in grads)
+    for e in range(mesh.E):
+        A[e * nd:(e + 1) * nd, e * nd:(e + 1) * nd] += Ke
+    # faces: e- = e (its layer xi_a = 1) and e+ = its +a neighbour (xi_a = 0)
+    for a in range(3):
+        t = [b for b in range(3) if b != a]
+        wf = np.kron(wq, wq) * h[t[0]] * h[t[1]]
+        tau = penalty_factor * (k + 1) ** 2 / h[a]
+        nb = mesh.neighbor(a, +1)
+        for e in range(mesh.E):
+            jump = np.zeros((nq * nq, mesh.E * nd))
+            avg = np.zeros((nq * nq, mesh.E * nd))
+            for cell, side, sgn in ((e, 1, 1.0), (nb[e], 0, -1.0)):
+                for i, ijk in enumerate(loc):
+                    tang = np.kron(V[:, ijk[t[1]]], V[:, ijk[t[0]]])
+                    val = V01[side, ijk[a]] * tang
+                    dn = D01[side, ijk[a]] / h[a] * tang
+                    jump[:, cell * nd + i] += sgn * val
+                    avg[:, cell * nd + i] += 0.5 * dn
+            A += (-avg.T @ (wf[:, None] * jump) - jump.T @ (wf[:, None] * avg)
+                  + tau * jump.T @ (wf[:, None] * jump))
+    return A
+
+
+@pytest.mark.parametrize("n,k,lohi", [((1, 1, 1), 1, None), ((2, 1, 1), 2, None), ((2, 2, 1), 1, None),
+                                      ((1, 2, 2), 3, ((0.0, -1.0, 0.5), (1.0, 2.0, 3.0))),
+                                      ((3, 1, 1), 2, ((0.0, 0.0, 0.0), (1.5, 0.7, 2.0)))])
+def test_laplace_matches_brute_force_assembly(n, k, lohi):
+    """The oracle's element-and-face application equals the global matrix
+    built pair by pair from the bilinear form (meshes with one cell per
+    direction included: there a cell is its own periodic neighbour)."""
+    m = dg.Mesh(n) if lohi is None else dg.Mesh(n, lo=lohi[0], hi=lohi[1])
+    A = dg.Laplace(dg.Space(m, k)).matrix()
+    B = _brute_force_sipg(m, k)
+    assert np.max(np.abs(A - B)) <= 1e-12 * np.max(np.abs(B))
