@@ -506,3 +506,119 @@ def test_laplace_matches_brute_force_assembly(n, k, lohi):
     A = dg.Laplace(dg.Space(m, k)).matrix()
     B = _brute_force_sipg(m, k)
     assert np.max(np.abs(A - B)) <= 1e-12 * np.max(np.abs(B))
+
+
+def _lagrange_by_products(nodes, x):
+    """Values and first derivatives of the Lagrange polynomials of `nodes` at
+    the points x, written out as products (independent of rules.lagrange)."""
+    x = np.asarray(x, dtype=np.float64)
+    n = len(nodes)
+    val = np.zeros((len(x), n))
+    der = np.zeros((len(x), n))
+    for j in range(n):
+        others = [nodes[m] for m in range(n) if m != j]
+        den = np.prod([nodes[j] - xm for xm in others])
+        val[:, j] = np.prod([x - xm for xm in others], axis=0) / den
+        for l in range(len(others)):
+            der[:, j] += np.prod([x - xm for m, xm in enumerate(others) if m != l], axis=0) / den
+    return val, der
+
+
+def _brute_force_convective(mesh, k, U):
+    """c_h(u, phi_i) of Sec. 3.2 for every test function, by quadrature in
+    physical coordinates cell by cell and face by face:
+      cell:  -sum_d int u_c u_d d_d phi_i, by a (Q + 2)-point Gauss rule (the
+             integrand is a polynomial of degree < 2Q + 3 per direction, so
+             this is the exact integral);
+      faces: for every cell e and axis a the face between e (its layer
+             xi_a = 1) and the cell at integer offset +1 along a, n = +e_a,
+             F*_c = {{u_c u_a}} + max(|u_a^-|, |u_a^+|)(u_c^- - u_c^+), tested
+             with phi^- - phi^+; the central part again exactly (Q + 2
+             points), the dissipative part with the Q-point Gauss rule of the
+             3/2 over-integration, Q = floor(3(k+1)/2).
+    U: (3, E, N^3) nodal values, x fastest.  Shares no table with
+    dg.Convective: the basis is evaluated by products at the points of
+    numpy's Gauss-Legendre rule."""
+    N = k + 1
+    Q = (3 * N) // 2
+    nodes = np.asarray(rules.lgl_nodes(k))
+    nx, ny, nz = mesh.n
+    h = mesh.h
+
+    def rule(n):
+        x, w = np.polynomial.legendre.leggauss(n)
+        return 0.5 * (x + 1.0), 0.5 * w
+
+    def cell_of(i, j, l):
+        return (i % nx) + nx * ((j % ny) + ny * (l % nz))
+
+    def field(e, c):
+        return U[c, e].reshape(N, N, N)            # [z, y, x]
+
+    out = np.zeros_like(U)
+    xe, we = rule(Q + 2)
+    Ve, De = _lagrange_by_products(nodes, xe)
+    jac = h[0] * h[1] * h[2]
+    W3 = np.einsum("a,b,c->abc", we, we, we) * jac  # [pz, py, px]
+    # cell terms
+    for e in range(mesh.E):
+        u = [np.einsum("zyx,az,by,cx->abc", field(e, c), Ve, Ve, Ve) for c in range(3)]
+        for c in range(3):
+            for d in range(3):
+                f = u[c] * u[d] * W3
+                B = [Ve, Ve, Ve]                   # per direction x, y, z
+                B[d] = De / h[d]
+                out[c, e] -= np.einsum("abc,az,by,cx->zyx", f, B[2], B[1], B[0]).ravel()
+    # faces
+    ends_v, _ = _lagrange_by_products(nodes, np.array([0.0, 1.0]))
+    for a in range(3):
+        t1, t2 = [b for b in range(3) if b != a]
+        for part, (xf, wf) in (("central", rule(Q + 2)), ("llf", rule(Q))):
+            Vf, _ = _lagrange_by_products(nodes, xf)
+            Wf = np.outer(wf, wf) * h[t1] * h[t2]  # [p2, p1]
+
+            def trace(e, c, layer):
+                # the cell's field on its face layer xi_a = layer at the points (p2 along t2, p1 along t1)
+                T = np.moveaxis(field(e, c), [2 - a, 2 - t1, 2 - t2], [0, 1, 2])   # [a, t1, t2]
+                return np.einsum("ijk,i,pj,qk->qp", T, ends_v[layer], Vf, Vf)
+
+            def test_with(e, c, layer, g):
+                # add sum over points of g (shape [p2, p1]) times phi_i on the face layer to out[c, e]
+                R = np.einsum("qp,i,pj,qk->ijk", g, ends_v[layer], Vf, Vf)       # [a, t1, t2]
+                out[c, e] += np.moveaxis(R, [0, 1, 2], [2 - a, 2 - t1, 2 - t2]).ravel()
+
+            for e in range(mesh.E):
+                ijk = [int(v) for v in mesh.ijk[:, e]]
+                ijk[a] += 1
+                ep = cell_of(*ijk)
+                um = [trace(e, c, 1) for c in range(3)]
+                up = [trace(ep, c, 0) for c in range(3)]
+                lam = np.maximum(np.abs(um[a]), np.abs(up[a]))
+                for c in range(3):
+                    if part == "central":
+                        F = 0.5 * (um[c] * um[a] + up[c] * up[a])
+                    else:
+                        F = lam * (um[c] - up[c])
+                    test_with(e, c, 1, F * Wf)
+                    test_with(ep, c, 0, -F * Wf)
+    return out
+
+
+@pytest.mark.parametrize("n,k,lohi,field", [((1, 1, 1), 1, None, "rand"), ((2, 1, 1), 2, None, "rand"),
+                                            ((2, 2, 1), 1, None, "tgv"),
+                                            ((1, 2, 2), 3, ((0.0, -1.0, 0.5), (1.0, 2.0, 3.0)), "rand"),
+                                            ((3, 1, 2), 2, ((0.0, 0.0, 0.0), (1.5, 0.7, 2.0)), "rand")])
+def test_convective_matches_brute_force_quadrature(n, k, lohi, field):
+    """The oracle's table-based C(U) equals the weak form integrated point by
+    point in physical coordinates (exact integrals for the polynomial parts,
+    the 3/2 rule for the Lax-Friedrichs part), on meshes with one cell per
+    direction (a cell is its own periodic neighbour) and non-cubic cells."""
+    m = dg.Mesh(n) if lohi is None else dg.Mesh(n, lo=lohi[0], hi=lohi[1])
+    s = dg.Space(m, k)
+    if field == "tgv":
+        U = np.stack(s.interpolate(dg.taylor_green)) + 1e-3 * rand((3, m.E, s.ndofs_cell), 1)
+    else:
+        U = rand((3, m.E, s.ndofs_cell), 7)
+    A = dg.Convective(s).apply(U)
+    B = _brute_force_convective(m, k, U)
+    assert np.max(np.abs(A - B)) <= 1e-12 * np.max(np.abs(B))
