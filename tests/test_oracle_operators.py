@@ -622,3 +622,82 @@ def test_convective_matches_brute_force_quadrature(n, k, lohi, field):
     A = dg.Convective(s).apply(U)
     B = _brute_force_convective(m, k, U)
     assert np.max(np.abs(A - B)) <= 1e-12 * np.max(np.abs(B))
+
+
+def _brute_force_divergence(mesh, ku, kp):
+    """Global matrix of d_h(q, u) of Sec. 3.2, rows the pressure basis
+    functions, columns the velocity basis functions (component, cell, node):
+      -int grad(q) . u over every cell
+      + over every face between a cell e (its layer xi_a = 1) and the cell at
+        integer offset +1 along a: int [q] {{u_a}}, [q] = q^- - q^+,
+    with every integral taken exactly (a (k_u + 3)-point Gauss rule per
+    direction, physical coordinates).  Basis functions by products on each
+    cell's LGL nodes, zero outside it; shares no table with dg.Divergence."""
+    Nu, Np = ku + 1, kp + 1
+    nu3, np3 = Nu ** 3, Np ** 3
+    x, w = np.polynomial.legendre.leggauss(ku + 3)
+    x, w = 0.5 * (x + 1.0), 0.5 * w
+    Vu, Du = _lagrange_by_products(np.asarray(rules.lgl_nodes(ku)), x)
+    Vp, Dp = _lagrange_by_products(np.asarray(rules.lgl_nodes(kp)), x)
+    eu, _ = _lagrange_by_products(np.asarray(rules.lgl_nodes(ku)), np.array([0.0, 1.0]))
+    ep_, _ = _lagrange_by_products(np.asarray(rules.lgl_nodes(kp)), np.array([0.0, 1.0]))
+    h = mesh.h
+    nx, ny, nz = mesh.n
+    E = mesh.E
+    B = np.zeros((E * np3, 3 * E * nu3))
+
+    def tab3(T):
+        # T = (tx, ty, tz) 1D tables over the same point set -> [point, node], x fastest in both
+        return np.kron(T[2], np.kron(T[1], T[0]))
+
+    wq = np.kron(w, np.kron(w, w)) * h[0] * h[1] * h[2]
+    phi = tab3((Vu, Vu, Vu))
+    for a in range(3):
+        T = [Vp, Vp, Vp]
+        T[a] = Dp / h[a]
+        block = -(tab3(T).T @ (wq[:, None] * phi))
+        for e in range(E):
+            B[e * np3:(e + 1) * np3, (a * E + e) * nu3:(a * E + e + 1) * nu3] += block
+    for a in range(3):
+        t1, t2 = [b for b in range(3) if b != a]
+        wf = np.kron(w, w) * h[t1] * h[t2]         # face points: t1 fastest
+
+        def face_tab(V, ends, layer, N):
+            # [face point, node]: the basis on the layer xi_a = layer
+            out = np.zeros((len(w) ** 2, N ** 3))
+            for i in range(N ** 3):
+                idx = (i % N, (i // N) % N, i // (N * N))
+                out[:, i] = ends[layer, idx[a]] * np.kron(V[:, idx[t2]], V[:, idx[t1]])
+            return out
+
+        qm, qp = face_tab(Vp, ep_, 1, Np), face_tab(Vp, ep_, 0, Np)
+        um, up = face_tab(Vu, eu, 1, Nu), face_tab(Vu, eu, 0, Nu)
+        for e in range(E):
+            ijk = [int(v) for v in mesh.ijk[:, e]]
+            ijk[a] += 1
+            f = (ijk[0] % nx) + nx * ((ijk[1] % ny) + ny * (ijk[2] % nz))
+            for row_cell, q, sq in ((e, qm, 1.0), (f, qp, -1.0)):
+                for col_cell, u in ((e, um), (f, up)):
+                    B[row_cell * np3:(row_cell + 1) * np3,
+                      (a * E + col_cell) * nu3:(a * E + col_cell + 1) * nu3] += \
+                        sq * 0.5 * (q.T @ (wf[:, None] * u))
+    return B
+
+
+@pytest.mark.parametrize("n,ku,kp,lohi", [((1, 1, 1), 2, 1, None), ((2, 1, 1), 3, 2, None),
+                                          ((2, 2, 1), 1, 1, None),
+                                          ((1, 2, 2), 2, 1, ((0.0, -1.0, 0.5), (1.0, 2.0, 3.0))),
+                                          ((3, 1, 2), 3, 2, ((0.0, 0.0, 0.0), (1.5, 0.7, 2.0)))])
+def test_divergence_gradient_match_brute_force_assembly(n, ku, kp, lohi):
+    """The oracle's D equals the global matrix of d_h built pair by pair, and
+    its G equals minus that matrix's transpose (meshes with one cell per
+    direction and non-cubic cells included)."""
+    m = dg.Mesh(n) if lohi is None else dg.Mesh(n, lo=lohi[0], hi=lohi[1])
+    su, sp = dg.Space(m, ku), dg.Space(m, kp)
+    B = _brute_force_divergence(m, ku, kp)
+    U = rand((3, m.E, su.ndofs_cell), 11)
+    P = rand((m.E, sp.ndofs_cell), 12)
+    y = B @ U.ravel()
+    g = -(B.T @ P.ravel())
+    assert np.max(np.abs(dg.Divergence(su, sp).apply(U).ravel() - y)) <= 1e-12 * np.max(np.abs(y))
+    assert np.max(np.abs(dg.Gradient(su, sp).apply(P).ravel() - g)) <= 1e-12 * np.max(np.abs(g))
