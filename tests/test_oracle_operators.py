@@ -624,6 +624,20 @@ def test_convective_matches_brute_force_quadrature(n, k, lohi, field):
     assert np.max(np.abs(A - B)) <= 1e-12 * np.max(np.abs(B))
 
 
+def _face_basis(V, ends, layer, a):
+    """[face point, node] table of a cell's basis on its layer xi_a = layer:
+    V holds the N 1D functions at the face rule's points (the points of the
+    two tangential directions t1 < t2, t1 fastest), ends their values at
+    xi = 0 and 1."""
+    N = V.shape[1]
+    t1, t2 = [b for b in range(3) if b != a]
+    out = np.zeros((V.shape[0] ** 2, N ** 3))
+    for i in range(N ** 3):
+        idx = (i % N, (i // N) % N, i // (N * N))
+        out[:, i] = ends[layer, idx[a]] * np.kron(V[:, idx[t2]], V[:, idx[t1]])
+    return out
+
+
 def _brute_force_divergence(mesh, ku, kp):
     """Global matrix of d_h(q, u) of Sec. 3.2, rows the pressure basis
     functions, columns the velocity basis functions (component, cell, node):
@@ -662,16 +676,8 @@ def _brute_force_divergence(mesh, ku, kp):
         t1, t2 = [b for b in range(3) if b != a]
         wf = np.kron(w, w) * h[t1] * h[t2]         # face points: t1 fastest
 
-        def face_tab(V, ends, layer, N):
-            # [face point, node]: the basis on the layer xi_a = layer
-            out = np.zeros((len(w) ** 2, N ** 3))
-            for i in range(N ** 3):
-                idx = (i % N, (i // N) % N, i // (N * N))
-                out[:, i] = ends[layer, idx[a]] * np.kron(V[:, idx[t2]], V[:, idx[t1]])
-            return out
-
-        qm, qp = face_tab(Vp, ep_, 1, Np), face_tab(Vp, ep_, 0, Np)
-        um, up = face_tab(Vu, eu, 1, Nu), face_tab(Vu, eu, 0, Nu)
+        qm, qp = _face_basis(Vp, ep_, 1, a), _face_basis(Vp, ep_, 0, a)
+        um, up = _face_basis(Vu, eu, 1, a), _face_basis(Vu, eu, 0, a)
         for e in range(E):
             ijk = [int(v) for v in mesh.ijk[:, e]]
             ijk[a] += 1
@@ -701,3 +707,78 @@ def test_divergence_gradient_match_brute_force_assembly(n, ku, kp, lohi):
     g = -(B.T @ P.ravel())
     assert np.max(np.abs(dg.Divergence(su, sp).apply(U).ravel() - y)) <= 1e-12 * np.max(np.abs(y))
     assert np.max(np.abs(dg.Gradient(su, sp).apply(P).ravel() - g)) <= 1e-12 * np.max(np.abs(g))
+
+
+def _brute_force_projection(mesh, k, tau_d, tau_c):
+    """Global matrix of the projection operator M + A_D + A_C (Sec. 3.2 and
+    3.3), pair by pair of global basis functions phi e_c (component, cell,
+    node), every integral exact ((k + 3)-point Gauss rule, physical
+    coordinates):
+      mass:        int phi_I phi_J (same component);
+      divergence:  tau_D(e) int_e d_b phi_I d_a phi_J (row component b,
+                   column component a);
+      continuity:  over every face between a cell e (layer xi_a = 1) and the
+                   cell at integer offset +1 along a, with n = e_a:
+                   {{tau_C}} int [v . n] [u . n], [w] = w^- - w^+ (component a
+                   only)."""
+    N = k + 1
+    n3, E = N ** 3, mesh.E
+    x, w = np.polynomial.legendre.leggauss(k + 3)
+    x, w = 0.5 * (x + 1.0), 0.5 * w
+    nodes = np.asarray(rules.lgl_nodes(k))
+    V, D = _lagrange_by_products(nodes, x)
+    ends, _ = _lagrange_by_products(nodes, np.array([0.0, 1.0]))
+    h = mesh.h
+    nx, ny, nz = mesh.n
+    A = np.zeros((3 * E * n3, 3 * E * n3))
+
+    def blk(c, e):
+        return slice((c * E + e) * n3, (c * E + e + 1) * n3)
+
+    def tab3(T):
+        return np.kron(T[2], np.kron(T[1], T[0]))
+
+    wq = np.kron(w, np.kron(w, w)) * h[0] * h[1] * h[2]
+    phi = tab3((V, V, V))
+    dphi = []
+    for a in range(3):
+        T = [V, V, V]
+        T[a] = D / h[a]
+        dphi.append(tab3(T))
+    Mloc = phi.T @ (wq[:, None] * phi)
+    for e in range(E):
+        for c in range(3):
+            A[blk(c, e), blk(c, e)] += Mloc
+        for b in range(3):
+            for a in range(3):
+                A[blk(b, e), blk(a, e)] += tau_d[e] * (dphi[b].T @ (wq[:, None] * dphi[a]))
+    for a in range(3):
+        t1, t2 = [b for b in range(3) if b != a]
+        wf = np.kron(w, w) * h[t1] * h[t2]
+        vm, vp = _face_basis(V, ends, 1, a), _face_basis(V, ends, 0, a)
+        for e in range(E):
+            ijk = [int(v) for v in mesh.ijk[:, e]]
+            ijk[a] += 1
+            f = (ijk[0] % nx) + nx * ((ijk[1] % ny) + ny * (ijk[2] % nz))
+            tc = 0.5 * (tau_c[e] + tau_c[f])
+            for ci, ti, si in ((e, vm, 1.0), (f, vp, -1.0)):
+                for cj, tj, sj in ((e, vm, 1.0), (f, vp, -1.0)):
+                    A[blk(a, ci), blk(a, cj)] += tc * si * sj * (ti.T @ (wf[:, None] * tj))
+    return A
+
+
+@pytest.mark.parametrize("n,k,lohi", [((1, 1, 1), 1, None), ((2, 1, 1), 2, None), ((2, 2, 1), 1, None),
+                                      ((1, 2, 2), 2, ((0.0, -1.0, 0.5), (1.0, 2.0, 3.0))),
+                                      ((3, 1, 2), 3, ((0.0, 0.0, 0.0), (1.5, 0.7, 2.0)))])
+def test_projection_matches_brute_force_assembly(n, k, lohi):
+    """The oracle's M + A_D + A_C equals the global matrix built pair by pair
+    from the three bilinear forms, with cell-varying penalty parameters (one
+    cell per direction and non-cubic cells included)."""
+    m = dg.Mesh(n) if lohi is None else dg.Mesh(n, lo=lohi[0], hi=lohi[1])
+    s = dg.Space(m, k)
+    rng = np.random.default_rng(13)
+    td, tc = rng.uniform(0.1, 1.0, m.E), rng.uniform(0.1, 1.0, m.E)
+    B = _brute_force_projection(m, k, td, tc)
+    U = rand((3, m.E, s.ndofs_cell), 14)
+    y = B @ U.ravel()
+    assert np.max(np.abs(dg.Projection(s, td, tc).apply(U).ravel() - y)) <= 1e-12 * np.max(np.abs(y))
