@@ -92,11 +92,6 @@ def step_hbm(nu, npr, ms):
             "frac": round(gbs / peak, 4), "peak_source": src}
 
 
-def lap_flops_per_cell(N):
-    """8 sweeps + neighbour terms: N^2 lines x (3 (N^2 + 4N) + 5 N^2) FMA."""
-    return 2 * N * N * (3 * (N * N + 4 * N) + 5 * N * N)
-
-
 # ------------------------------------------------------------- clocks
 class ClockSampler:
     def __init__(self):

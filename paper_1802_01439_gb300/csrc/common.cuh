@@ -131,18 +131,6 @@ __device__ __forceinline__ void matvec(const T* A, const T (&x)[NI], T (&y)[NO])
   }
 }
 
-// y[i] = z[i] + sum_j A[i*NI + j] x[j]
-template <class T, int NO, int NI>
-__device__ __forceinline__ void matvec_add(const T* A, const T (&x)[NI], const T (&z)[NO], T (&y)[NO]) {
-#pragma unroll
-  for (int i = 0; i < NO; ++i) {
-    T acc = z[i];
-#pragma unroll
-    for (int j = 0; j < NI; ++j) acc = fma(A[i * NI + j], x[j], acc);
-    y[i] = acc;
-  }
-}
-
 template <class T, int N>
 __device__ __forceinline__ void load_line(const T* buf, int base, int stride, T (&x)[N]) {
 #pragma unroll

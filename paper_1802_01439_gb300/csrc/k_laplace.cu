@@ -159,14 +159,6 @@ __device__ __forceinline__ void sline(int l, int& base, int& stride) {
     stride = P * N;
   }
 }
-// Padded position of entry i of the block's contiguous cells.
-template <int N>
-__device__ __forceinline__ int spos(int i) {
-  constexpr int NNN = N * N * N;
-  const int cell = i / NNN, r = i - cell * NNN;
-  return cell * cell_stride<N>() + (r % N) + padx<N>() * (r / N);
-}
-
 // One line of T_d x in even-odd form (double-float), with the neighbour
 // data nb: the coupling through the neighbours' face values
 // (cr r(0) + cl lf(N-1)) goes into the even and odd sums, the face-derivative
