@@ -88,6 +88,9 @@ void dgns_default_desc(dgns_mesh_desc* desc);
  * stream).  On failure *out is NULL and nothing is leaked. */
 int dgns_create(const dgns_mesh_desc* desc, void* stream, dgns_ctx** out);
 int dgns_destroy(dgns_ctx* ctx);
+/* Later calls enqueue on `stream` (a cudaStream_t, NULL for the default
+ * stream).  Work already enqueued on the previous stream is not ordered before
+ * them: synchronise it, or make the new stream wait on an event, first. */
 int dgns_set_stream(dgns_ctx* ctx, void* stream);
 const char* dgns_status_string(int status);
 const char* dgns_last_error(void);
