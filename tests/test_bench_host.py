@@ -94,3 +94,11 @@ def test_reference_arm_line(monkeypatch):
     assert line["cpu_baseline"]["value"] == line["value"] and line["cpu_baseline"]["kind"] == "oracle"
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
     assert bench.reference_arm(argparse.Namespace(steps=1, warmup=1), 1, 2) is None   # other ranks
+
+
+def test_reference_sample_bounds_the_run():
+    # fits: the full mesh; 200 steps of 0.8 s: halved once (1/8 of the cost)
+    assert bench.reference_sample_n(32, 0.5, 100, budget=150.0) == 32
+    assert bench.reference_sample_n(32, 0.8, 200, budget=150.0) == 16
+    assert bench.reference_sample_n(32, 0.8, 100000, budget=150.0) == 8      # floor
+    assert bench.reference_sample_n(2, 10.0, 100, budget=1.0) == 2           # tiny meshes stay
