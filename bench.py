@@ -106,9 +106,10 @@ class ClockSampler:
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
             dev = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0"
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", dev, "--query-gpu=" + q, "--format=csv,noheader,nounits", "-lms", "50"],
-                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            with open(self.path, "w") as log:     # the child keeps its own descriptor
+                self.proc = subprocess.Popen(
+                    ["nvidia-smi", "-i", dev, "--query-gpu=" + q, "--format=csv,noheader,nounits", "-lms", "50"],
+                    stdout=log, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
@@ -122,7 +123,9 @@ class ClockSampler:
             self.proc.kill()
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        with open(self.path) as log:
+            lines = log.readlines()
+        for line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 8:
                 continue

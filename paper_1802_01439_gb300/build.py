@@ -47,8 +47,10 @@ def _compile(src, hdr, verbose):
     stamp = obj + ".sha"
     with open(path, "rb") as fh:
         digest = hashlib.sha256(fh.read() + hdr.encode()).hexdigest()
-    if os.path.exists(obj) and os.path.exists(stamp) and open(stamp).read() == digest:
-        return obj, False
+    if os.path.exists(obj) and os.path.exists(stamp):
+        with open(stamp) as fh:
+            if fh.read() == digest:
+                return obj, False
     cmd = [nvcc()] + ARCH + FLAGS + ["-c", path, "-o", obj]
     if verbose:
         cmd += ["-Xptxas", "-v"]

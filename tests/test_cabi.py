@@ -17,7 +17,8 @@ def lib():
 
 
 def header_functions():
-    src = open(os.path.join(ROOT, "include", "dgns.h")).read()
+    with open(os.path.join(ROOT, "include", "dgns.h")) as fh:
+        src = fh.read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(dgns_\w+)\s*\(", src)))
 

@@ -22,8 +22,11 @@ def legendre_and_derivative(k, x):
         return p0, np.zeros_like(x)
     for n in range(1, k):
         p0, p1 = p1, ((2 * n + 1) * x * p1 - n * p0) / (n + 1)
-    # (1 - x^2) P_k' = k (P_{k-1} - x P_k)
-    dp = k * (p0 - x * p1) / (1.0 - x * x)
+    # (1 - x^2) P_k' = k (P_{k-1} - x P_k) inside; P_k'(+-1) = (+-1)^(k+1) k (k+1) / 2
+    dp = np.empty_like(x)
+    inner = np.abs(x) < 1.0
+    dp[inner] = k * (p0[inner] - x[inner] * p1[inner]) / (1.0 - x[inner] ** 2)
+    dp[~inner] = np.sign(x[~inner]) ** (k + 1) * k * (k + 1) / 2.0
     return p1, dp
 
 
