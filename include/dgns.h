@@ -268,6 +268,16 @@ int dgns_cg_invmass_solve_noalloc(dgns_ctx* ctx, double* x3, const double* b3, d
 int dgns_cg_projection_solve(dgns_ctx* ctx, double* x3, const double* b3, const double* tau_d,
                              const double* tau_c, const dgns_solve_params* params, dgns_solve_info* info);
 
+/* Test hooks for the failure paths (for tests, not for production use).
+ * dgns_debug_fail_alloc(n): the n-th device allocation the library makes from
+ * now on (n >= 1; any context, any thread) fails as if the device were out of
+ * memory, and the hook disarms itself; n = 0 disarms it.  Returns
+ * DGNS_ERR_INVALID_ARG for n < 0.
+ * dgns_debug_live_allocations: device allocations the library has made and
+ * not yet freed, over all contexts. */
+int dgns_debug_fail_alloc(long long n);
+long long dgns_debug_live_allocations(void);
+
 #ifdef __cplusplus
 }
 #endif

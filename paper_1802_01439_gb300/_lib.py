@@ -55,6 +55,8 @@ SIGNATURES = {
     "dgns_create": (_I, [ctypes.POINTER(MeshDesc), _P, ctypes.POINTER(_P)]),
     "dgns_destroy": (_I, [_P]),
     "dgns_set_stream": (_I, [_P, _P]),
+    "dgns_debug_fail_alloc": (_I, [_LL]),
+    "dgns_debug_live_allocations": (_LL, []),
     "dgns_status_string": (ctypes.c_char_p, [_I]),
     "dgns_last_error": (ctypes.c_char_p, []),
     "dgns_sizes": (_I, [_P, ctypes.POINTER(_LL), ctypes.POINTER(_LL)]),

@@ -2,6 +2,7 @@
 // host/device pointer staging, operator entry points and the solvers.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <chrono>
 #include <cstdint>
 #include <cmath>
@@ -21,6 +22,34 @@ thread_local std::string g_err;
 int fail(int code, const std::string& msg) {
   g_err = msg;
   return code;
+}
+
+// Every device allocation of the library goes through dev_malloc / dev_free:
+// a test hook can make the n-th allocation from now fail as if the device
+// were out of memory, and a count of live allocations lets tests check that
+// the failure paths free what they allocated.
+std::atomic<long long> g_fail_alloc_in{0};  // 0: disarmed
+std::atomic<long long> g_live_allocs{0};
+
+cudaError_t dev_malloc_raw(void** p, size_t bytes) {
+  *p = nullptr;
+  long long n = g_fail_alloc_in.load();
+  while (n > 0 && !g_fail_alloc_in.compare_exchange_weak(n, n - 1)) {
+  }
+  if (n == 1) return cudaErrorMemoryAllocation;
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess && *p) g_live_allocs.fetch_add(1);
+  return e;
+}
+template <class T>
+cudaError_t dev_malloc(T** p, size_t bytes) {
+  void* v = nullptr;
+  const cudaError_t e = dev_malloc_raw(&v, bytes);
+  *p = static_cast<T*>(v);
+  return e;
+}
+void dev_free(void* p) {
+  if (p && cudaFree(p) == cudaSuccess) g_live_allocs.fetch_sub(1);
 }
 
 #define DG_CUDA(call)                                                                 \
@@ -189,11 +218,11 @@ struct Staged {
     if (c->stage_cap[slot] < bytes) {
       if (c->stage[slot]) {
         cudaStreamSynchronize(c->s);
-        cudaFree(c->stage[slot]);
+        dev_free(c->stage[slot]);
         c->stage[slot] = nullptr;
         c->stage_cap[slot] = 0;
       }
-      DG_CUDA(cudaMalloc(&c->stage[slot], bytes));
+      DG_CUDA(dev_malloc(&c->stage[slot], bytes));
       c->stage_cap[slot] = bytes;
     }
     *buf = c->stage[slot++];
@@ -346,8 +375,16 @@ int estimate_lambda(dgns_ctx* c, Level& L, double* lam) {
   }
   mean /= (double)n;
   for (auto& v : hb) v -= mean;
-  double* x;
-  DG_CUDA(cudaMalloc(&x, (size_t)n * sizeof(double)));
+  double* x = nullptr;
+  DG_CUDA(dev_malloc(&x, (size_t)n * sizeof(double)));
+  struct FreeOnExit {  // the early returns below must not leak x
+    double* p;
+    cudaStream_t s;
+    ~FreeOnExit() {
+      cudaStreamSynchronize(s);
+      dev_free(p);
+    }
+  } guard{x, c->s};
   DG_CUDA(cudaMemsetAsync(x, 0, (size_t)n * sizeof(double), c->s));
   DG_CUDA(cudaMemcpyAsync(c->r, hb.data(), (size_t)n * sizeof(double), cudaMemcpyHostToDevice, c->s));
   std::vector<double> alpha, beta;
@@ -370,8 +407,6 @@ int estimate_lambda(dgns_ctx* c, Level& L, double* lam) {
     if (!(c->h_scal[S_RZNEW] > 1e-300 * rz)) break;
     if ((rc = cg_direction(c->p, c->z, n, c->red, false, c->s))) break;
   }
-  cudaStreamSynchronize(c->s);
-  cudaFree(x);
   if (rc) return rc;
   const int m = (int)alpha.size();
   if (m == 0) return fail(DGNS_ERR_NONFINITE, "eigenvalue estimate: no Lanczos step");
@@ -387,24 +422,24 @@ int estimate_lambda(dgns_ctx* c, Level& L, double* lam) {
 void free_ctx(dgns_ctx* c) {
   if (!c) return;
   if (c->s) cudaStreamSynchronize(c->s);
-  for (int i = 0; i < 2; ++i) cudaFree(c->d_diag[i]);
+  for (int i = 0; i < 2; ++i) dev_free(c->d_diag[i]);
   for (auto& L : c->levels) {
-    cudaFree(L.dinv);
-    cudaFree(L.dinv64);
-    cudaFree(L.xa);
-    cudaFree(L.xb);
-    cudaFree(L.b);
-    cudaFree(L.r);
+    dev_free(L.dinv);
+    dev_free(L.dinv64);
+    dev_free(L.xa);
+    dev_free(L.xb);
+    dev_free(L.b);
+    dev_free(L.r);
   }
-  cudaFree(c->r);
-  cudaFree(c->z);
-  cudaFree(c->p);
-  cudaFree(c->Ap);
-  cudaFree(c->conv_face);
-  cudaFree(c->red.part);
-  cudaFree(c->red.scal);
+  dev_free(c->r);
+  dev_free(c->z);
+  dev_free(c->p);
+  dev_free(c->Ap);
+  dev_free(c->conv_face);
+  dev_free(c->red.part);
+  dev_free(c->red.scal);
   if (c->h_scal) cudaFreeHost(c->h_scal);
-  for (int i = 0; i < 4; ++i) cudaFree(c->stage[i]);
+  for (int i = 0; i < 4; ++i) dev_free(c->stage[i]);
   if (c->stage_ev) cudaEventDestroy(c->stage_ev);
   if (c->vc_exec) cudaGraphExecDestroy(c->vc_exec);
   if (c->gs) cudaStreamDestroy(c->gs);
@@ -419,16 +454,16 @@ int alloc_cg(dgns_ctx* c, long long n) {
     cudaGraphExecDestroy(c->vc_exec);
     c->vc_exec = nullptr;
   }
-  cudaFree(c->r);
-  cudaFree(c->z);
-  cudaFree(c->p);
-  cudaFree(c->Ap);
+  dev_free(c->r);
+  dev_free(c->z);
+  dev_free(c->p);
+  dev_free(c->Ap);
   c->r = c->z = c->p = c->Ap = nullptr;
   const size_t b = (size_t)n * sizeof(double);
-  DG_CUDA(cudaMalloc(&c->r, b));
-  DG_CUDA(cudaMalloc(&c->z, b));
-  DG_CUDA(cudaMalloc(&c->p, b));
-  DG_CUDA(cudaMalloc(&c->Ap, b));
+  DG_CUDA(dev_malloc(&c->r, b));
+  DG_CUDA(dev_malloc(&c->z, b));
+  DG_CUDA(dev_malloc(&c->p, b));
+  DG_CUDA(dev_malloc(&c->Ap, b));
   c->cg_cap = n;
   return 0;
 }
@@ -468,15 +503,15 @@ int setup_mg(dgns_ctx* c) {
       inv64[j] = 1.0 / dg[j];
       inv32[j] = (float)inv64[j];
     }
-    DG_CUDA(cudaMalloc(&L.dinv64, N3 * sizeof(double)));
+    DG_CUDA(dev_malloc(&L.dinv64, N3 * sizeof(double)));
     DG_CUDA(cudaMemcpy(L.dinv64, inv64.data(), N3 * sizeof(double), cudaMemcpyHostToDevice));
-    DG_CUDA(cudaMalloc(&L.dinv, N3 * tb));
+    DG_CUDA(dev_malloc(&L.dinv, N3 * tb));
     DG_CUDA(cudaMemcpy(L.dinv, tb == 4 ? (const void*)inv32.data() : (const void*)inv64.data(), N3 * tb,
                        cudaMemcpyHostToDevice));
-    DG_CUDA(cudaMalloc(&L.xa, L.n * tb));
-    DG_CUDA(cudaMalloc(&L.xb, L.n * tb));
-    DG_CUDA(cudaMalloc(&L.b, L.n * tb));
-    DG_CUDA(cudaMalloc(&L.r, L.n * tb));
+    DG_CUDA(dev_malloc(&L.xa, L.n * tb));
+    DG_CUDA(dev_malloc(&L.xb, L.n * tb));
+    DG_CUDA(dev_malloc(&L.b, L.n * tb));
+    DG_CUDA(dev_malloc(&L.r, L.n * tb));
   }
   vec P0 = make_prolongation_1d(s, 0), P1 = make_prolongation_1d(s, 1);
   for (int i = 0; i < N * N; ++i) {
@@ -710,12 +745,12 @@ int dgns_create(const dgns_mesh_desc* desc, void* stream, dgns_ctx** out) {
   };
   for (int sp = 0; sp < 2; ++sp) {
     const size_t b = c->diag[sp].size() * sizeof(double);
-    if (cudaMalloc(&c->d_diag[sp], b) != cudaSuccess ||
+    if (dev_malloc(&c->d_diag[sp], b) != cudaSuccess ||
         cudaMemcpy(c->d_diag[sp], c->diag[sp].data(), b, cudaMemcpyHostToDevice) != cudaSuccess)
       return bail(fail(DGNS_ERR_OOM, "table allocation failed"));
   }
-  if (cudaMalloc(&c->red.part, RED_BLOCKS * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&c->red.scal, S_NSLOTS * sizeof(double)) != cudaSuccess ||
+  if (dev_malloc(&c->red.part, RED_BLOCKS * sizeof(double)) != cudaSuccess ||
+      dev_malloc(&c->red.scal, S_NSLOTS * sizeof(double)) != cudaSuccess ||
       cudaMallocHost(&c->h_scal, S_NSLOTS * sizeof(double)) != cudaSuccess)
     return bail(fail(DGNS_ERR_OOM, "reduction buffers"));
   c->mg_prec = d.mg_precision;
@@ -737,6 +772,14 @@ int dgns_set_stream(dgns_ctx* c, void* stream) {
   c->s = (cudaStream_t)stream;
   return 0;
 }
+
+int dgns_debug_fail_alloc(long long n) {
+  if (n < 0) return fail(DGNS_ERR_INVALID_ARG, "n must be >= 0");
+  g_fail_alloc_in.store(n);
+  return 0;
+}
+
+long long dgns_debug_live_allocations(void) { return g_live_allocs.load(); }
 
 int dgns_sizes(const dgns_ctx* c, long long* nu, long long* np) {
   if (!c) return fail(DGNS_ERR_INVALID_ARG, "ctx is null");
@@ -891,7 +934,7 @@ int dgns_vmult_gradient(dgns_ctx* c, double* dst3, const double* p) {
 namespace {
 int conv_face_buffer(dgns_ctx* c) {
   if (c->conv_face) return 0;
-  if (cudaMalloc(&c->conv_face, (size_t)9 * c->m.E * c->conv.N * c->conv.N * sizeof(double)) != cudaSuccess) {
+  if (dev_malloc(&c->conv_face, (size_t)9 * c->m.E * c->conv.N * c->conv.N * sizeof(double)) != cudaSuccess) {
     c->conv_face = nullptr;
     cudaGetLastError();
     return fail(DGNS_ERR_OOM, "convective face buffer allocation failed");

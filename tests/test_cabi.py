@@ -114,3 +114,13 @@ def test_solve_params_layout(lib):
     p.use_initial_guess = 7
     lib.dgns_default_solve_params(ctypes.byref(p))
     assert p.use_initial_guess == 0 and p.project_mean == 1 and p.abs_tol == 0.0
+
+
+def test_allocation_failure_hook_arguments(lib):
+    """The failure-path hooks need no device: n < 0 is rejected, 0 disarms,
+    and nothing is allocated before any context exists."""
+    from paper_1802_01439_gb300 import _lib
+    assert lib.dgns_debug_fail_alloc(-1) == _lib.DGNS_ERR_INVALID_ARG
+    assert lib.dgns_debug_fail_alloc(3) == 0
+    assert lib.dgns_debug_fail_alloc(0) == 0
+    assert lib.dgns_debug_live_allocations() == 0

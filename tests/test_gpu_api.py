@@ -75,3 +75,48 @@ def test_destroyed_context_rejects_calls():
     ctx.close()                                       # idempotent
     with pytest.raises(DgnsError):
         ctx.vmult_laplace(torch.empty_like(x), x)
+
+
+def test_failed_create_frees_everything():
+    """Each device allocation of a context creation (tables, reduction
+    buffers, CG vectors, multigrid levels, the eigenvalue estimate's work
+    vector) is made to fail in turn: every such creation returns
+    DGNS_ERR_OOM, hands back no context and leaves no allocation behind;
+    the first n past the last allocation creates the context normally."""
+    import gc
+    from paper_1802_01439_gb300 import DgnsError, _lib
+    lib = _lib.load()
+    # contexts of earlier tests held in reference cycles must not be freed
+    # while the live count is being compared
+    gc.collect()
+    gc.disable()
+    try:
+        _fail_each_allocation(lib, DgnsError, _lib)
+    finally:
+        gc.enable()
+
+
+def _fail_each_allocation(lib, DgnsError, _lib):
+    base = lib.dgns_debug_live_allocations()
+    ctx = context((4, 4, 4), 3, mg_precision=32)
+    kept = lib.dgns_debug_live_allocations() - base
+    ctx.close()
+    assert lib.dgns_debug_live_allocations() == base and kept > 10
+    n = 1
+    try:
+        while n < 200:
+            lib.dgns_debug_fail_alloc(n)
+            try:
+                ctx = context((4, 4, 4), 3, mg_precision=32)
+            except DgnsError as err:
+                assert err.code == _lib.DGNS_ERR_OOM, err
+                assert lib.dgns_debug_live_allocations() == base, n
+                n += 1
+                continue
+            break
+    finally:
+        lib.dgns_debug_fail_alloc(0)
+    assert n > kept                     # every kept allocation failed once
+    assert lib.dgns_debug_live_allocations() == base + kept
+    ctx.close()
+    assert lib.dgns_debug_live_allocations() == base
