@@ -1,19 +1,11 @@
-"""The Taylor-Green driver: CFL time step, energy diagnostics and the kinetic
-energy budget of an early, resolved phase of the flow."""
-import math
-
+"""The Taylor-Green driver: energy diagnostics and the kinetic energy budget
+of an early, resolved phase of the flow (the CFL time step is tested on the
+CPU in tests/test_tgv_host.py)."""
 import pytest
-import torch
 
 from tests.gpu_common import build_lib
 
 pytestmark = pytest.mark.gpu
-
-
-def test_cfl_time_step_formula():
-    from paper_1802_01439_gb300.tgv import cfl_time_step
-    # Cr / k^1.5 * h / U0
-    assert cfl_time_step(3, 2 * math.pi / 8) == pytest.approx(0.125 / 3 ** 1.5 * 2 * math.pi / 8, rel=1e-15)
 
 
 def test_tgv_early_energy_budget():
