@@ -122,3 +122,23 @@ def test_helmholtz_invmass_cg():
     Hm = dg.Helmholtz(s, nu, mf)
     res = solvers.relative_residual(lambda v: Hm.apply(v.reshape(3, s.mesh.E, -1)).ravel(), host(x), b)
     assert res <= 2e-12
+
+
+@pytest.mark.parametrize("kp", [2, 3])
+def test_cg_mg_iterations_are_mesh_independent(kp):
+    """Sec. 3.3: with the multigrid V-cycle as preconditioner the pressure CG
+    needs a number of iterations that does not grow under mesh refinement
+    (the paper reports 6-12 at relative tolerance 1e-6 over its refinement
+    levels).  Mean-free random right-hand side, zero initial guess,
+    relative tolerance 1e-6, FP32 V-cycle, 8^3, 16^3 and 32^3 cells (3, 4
+    and 5 levels): the counts differ by at most 2 and none exceeds 12."""
+    its = []
+    for n in (8, 16, 32):
+        ctx = context(n, kp + 1, kp, mg_precision=32)
+        s = dg.Space(dg.Mesh(n), kp)
+        b = solvers.mean_free(np.random.default_rng(12).uniform(-1, 1, s.size))
+        x = torch.zeros(s.size, dtype=torch.float64, device="cuda")
+        info = ctx.cg_mg_solve(x, dev(b), rel_tol=1e-6)
+        assert info["rc"] == 0 and info["rel_res"] <= 1e-6
+        its.append(info["iterations"])
+    assert max(its) - min(its) <= 2 and max(its) <= 12, its
