@@ -360,6 +360,22 @@ def test_penalty_parameters_constant_field():
     assert np.max(np.abs(tau_c - 1.5 * dt)) < 1e-15
 
 
+def test_penalty_parameters_cellwise_average():
+    """||u||_e is the volume average of |u| over each cell: for
+    u = (1 + x, 0, 0) on [0, 3] x [0, 1] x [0, 2] with three cells along x
+    (|u| is linear, so the (k+1)-point Gauss rule is exact), the averages are
+    the values at the cell centres, 1.5, 2.5, 3.5, and h = (1 * 1 * 2)^(1/3)."""
+    m = dg.Mesh((3, 1, 1), lo=(0.0, 0.0, 0.0), hi=(3.0, 1.0, 2.0))
+    k, dt = 2, 1e-2
+    s = dg.Space(m, k)
+    ux = np.stack(s.interpolate(lambda x, y, z: (1.0 + x, 0 * x, 0 * x)))
+    tau_d, tau_c = dg.penalty_parameters(s, ux, dt, zeta_d=2.0, zeta_c=0.5)
+    avg = np.array([1.5, 2.5, 3.5])
+    h = 2.0 ** (1.0 / 3.0)
+    assert np.max(np.abs(tau_d - 2.0 * avg * h / (k + 1) * dt)) < 1e-15
+    assert np.max(np.abs(tau_c - 0.5 * avg * dt)) < 1e-15
+
+
 @pytest.mark.parametrize("n,k", [((2, 2, 2), 2), ((1, 2, 3), 3)])
 def test_projection_symmetric_and_mass_plus_psd(n, k):
     m = dg.Mesh(n)
