@@ -38,6 +38,32 @@ def test_conv_cell_flops_bench_value():
     assert bench.conv_cell_flops(4, 6) == 41328
 
 
+def _conv_face_flops_by_phase(N, Q):
+    """The face kernel's algorithmic FP64 flops per face (multiply-add = 2
+    flops): the traces of 3 components of both cells (the face layer's N^2
+    nodal values interpolated along one tangential direction to Q N points,
+    then along the other to Q^2, multiply-adds of N terms), the LLF flux at
+    the Q^2 points (per component: two products, their sum, the halving, the
+    jump, its product with the penalty and the final sum, 7 flops; 2 more for
+    max(|a|, |b|)), the test of the 3 flux components with the face-layer
+    basis (Q^2 -> N Q -> N^2, multiply-adds of Q terms), and the scaling of
+    the 3 N^2 results by the face area."""
+    traces = 2 * (6 * (Q * N) * N + 6 * (Q * Q) * N)
+    flux = Q * Q * (3 * 7 + 2)
+    tests = 2 * (3 * (N * Q) * Q + 3 * (N * N) * Q)
+    return traces + flux + tests + 3 * N * N
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 5, 8, 12])
+def test_conv_face_flops_match_phase_count(N):
+    Q = 3 * N // 2
+    assert bench.conv_face_flops(N, Q) == _conv_face_flops_by_phase(N, Q)
+
+
+def test_conv_face_flops_bench_value():
+    assert bench.conv_face_flops(4, 6) == 5196
+
+
 def test_step_hbm_bytes_and_fraction():
     nu, npr = 2097152, 884736           # 32^3 cells, k_u = 3 (4^3 nodes), k_p = 2 (3^3)
     r = bench.step_hbm(nu, npr, 1.0)
