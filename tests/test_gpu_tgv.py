@@ -1,6 +1,6 @@
 """The Taylor-Green driver: energy diagnostics and the kinetic energy budget
 of an early, resolved phase of the flow (the CFL time step is tested on the
-CPU in tests/test_tgv_host.py)."""
+CPU in tests/test_driver_host.py)."""
 import pytest
 
 from tests.gpu_common import build_lib
