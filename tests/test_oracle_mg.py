@@ -1,7 +1,8 @@
 """Pins of the oracle's multigrid and solver components (no GPU).
 
   transfers   prolongation reproduces polynomials exactly (it is an embedding);
-              P^T M_fine P = M_coarse (Galerkin identity of nested spaces)
+              restriction is its transpose; P^T M_fine P = M_coarse (Galerkin
+              identity of nested spaces)
   Chebyshev   on a diagonal matrix the error follows the closed form
               T_m((theta - lambda)/delta) / T_m(theta/delta)
   PCG         matches a dense solve; with the V-cycle as preconditioner the
@@ -26,6 +27,21 @@ def test_prolongation_reproduces_polynomials(k):
     c = rand(4, k)
     p = lambda x, y, z: c[0] * x ** k + c[1] * y ** k * z + c[2] * x * y * z ** (k - 1) + c[3]
     assert np.max(np.abs(T.prolongate(sc.interpolate(p)) - sf.interpolate(p))) < 1e-12
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_restriction_is_the_transpose_of_prolongation(k):
+    """restrict is a separate scatter-add; <R f, c> = <f, P c> for random
+    fine and coarse vectors (one child per direction of a coarse cell with
+    one cell along y included)."""
+    mc, mf = dg.Mesh((2, 1, 2)), dg.Mesh((4, 2, 4))
+    sc, sf = dg.Space(mc, k), dg.Space(mf, k)
+    T = mg.Transfer(sc, sf)
+    f = rand((mf.E, sf.ndofs_cell), 21)
+    c = rand((mc.E, sc.ndofs_cell), 22)
+    lhs = float(np.sum(T.restrict(f) * c))
+    rhs = float(np.sum(f * T.prolongate(c)))
+    assert abs(lhs - rhs) <= 1e-13 * np.sum(np.abs(f)) * np.max(np.abs(c))
 
 
 @pytest.mark.parametrize("k", [1, 3])
