@@ -23,7 +23,6 @@ import json
 import math
 import time
 
-import numpy as np
 import torch
 
 from . import inputs

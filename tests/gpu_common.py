@@ -3,7 +3,7 @@ move seeded inputs to the device and measure the relative max-norm error."""
 import numpy as np
 import torch
 
-from oracle import dg, rules
+from oracle import rules
 from paper_1802_01439_gb300 import inputs
 
 PI = np.pi
