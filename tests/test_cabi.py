@@ -124,3 +124,16 @@ def test_allocation_failure_hook_arguments(lib):
     assert lib.dgns_debug_fail_alloc(3) == 0
     assert lib.dgns_debug_fail_alloc(0) == 0
     assert lib.dgns_debug_live_allocations() == 0
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: without libdgns.so, loading the library and creating
+    a context raise instead of computing anything."""
+    from paper_1802_01439_gb300 import Context, _lib
+    missing = str(tmp_path / "libdgns.so")
+    with pytest.raises(RuntimeError, match="not built"):
+        _lib.load(missing)
+    monkeypatch.setattr(_lib, "LIB_PATH", missing)
+    monkeypatch.setattr(_lib, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        Context(2, 2)
