@@ -295,6 +295,21 @@ def test_taylor_green_energy_and_dissipation():
     assert abs(dg.dissipation_rate(s, U, nu) / nu - 0.75) < 1e-3
 
 
+@pytest.mark.parametrize("n", [(1, 1, 1), (2, 3, 2)])
+def test_energy_and_dissipation_exact_for_polynomials(n):
+    """u = (x^2, xy, z) on [0, 1]^3 lies in the degree-2 space, and the
+    (k+1)-point Gauss rule integrates |u|^2 and grad u : grad u exactly:
+    e_k = (1/5 + 1/9 + 1/3) / 2 = 29/90 and eps = nu (4/3 + 1/3 + 1/3 + 1)
+    = 3 nu on any mesh (the broken gradient of a smooth field is its
+    gradient)."""
+    nu = 0.01
+    m = dg.Mesh(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0))
+    s = dg.Space(m, 2)
+    U = np.stack(s.interpolate(lambda x, y, z: (x * x, x * y, z)))
+    assert abs(dg.kinetic_energy(s, U) - 29.0 / 90.0) < 1e-14
+    assert abs(dg.dissipation_rate(s, U, nu) - 3.0 * nu) < 1e-15
+
+
 @pytest.mark.parametrize("n,k,field", [((2, 2, 2), 2, "rand"), ((3, 1, 2), 3, "tgv"), ((1, 2, 1), 4, "rand")])
 def test_convective_vjp_adjoint_identity(n, k, field):
     """<w, J v> = <J^T w, v>, with J v from central differences of C, which
