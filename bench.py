@@ -473,10 +473,12 @@ def cpu_baseline(sample_n=N_ELEM, repeats=5):
 REF_BUDGET_S = 240.0   # wall time the reference arm's steps may take in total
 
 
-def reference_sample_n(n_full, t_full, nsteps, budget=REF_BUDGET_S):
+def reference_sample_n(n_full, t_full, nsteps, budget=None):
     """Cells per direction of the reference arm's per-step sample: the full
-    mesh if nsteps steps of t_full seconds fit the budget, else the mesh
-    halved per direction (cost ~ cells) until they do, 8^3 cells at least."""
+    mesh if nsteps steps of t_full seconds fit the budget (REF_BUDGET_S by
+    default), else the mesh halved per direction (cost ~ cells) until they
+    do, 8^3 cells at least."""
+    budget = REF_BUDGET_S if budget is None else budget
     n = n_full
     while n > 8 and nsteps * t_full * (n / n_full) ** 3 > budget:
         n //= 2
@@ -506,7 +508,7 @@ def reference_arm(args, rank, world):
     else:
         sample = ("oracle (numpy/LAPACK FP64), each step the k_u=3/k_p=2 operator set on a %d^3-cell sample "
                   "of the %d^3 workload (same operators and Taylor-Green input; the full mesh would take "
-                  "more than %.0f s for these steps; the smaller arrays stay in cache, so the sample runs "
+                  "more than %g s for these steps; the smaller arrays stay in cache, so the sample runs "
                   "faster per DoF than the full mesh), DoFs/s = sample DoFs / mean step time"
                   % (n, N_ELEM, REF_BUDGET_S))
     return {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "DoFs/s", "n_gpus": world,

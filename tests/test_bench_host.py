@@ -128,3 +128,13 @@ def test_reference_sample_bounds_the_run():
     assert bench.reference_sample_n(32, 0.8, 200, budget=150.0) == 16
     assert bench.reference_sample_n(32, 0.8, 100000, budget=150.0) == 8      # floor
     assert bench.reference_sample_n(2, 10.0, 100, budget=1.0) == 2           # tiny meshes stay
+
+
+def test_reference_arm_switches_to_a_sample(monkeypatch):
+    """A budget the full mesh cannot meet makes every step run on the 8^3
+    sample, and the line says so."""
+    monkeypatch.setattr(bench, "N_ELEM", 16)
+    monkeypatch.setattr(bench, "REF_BUDGET_S", 1e-9)
+    line = bench.reference_arm(argparse.Namespace(steps=1, warmup=3), 0, 1)
+    assert "8^3-cell sample of the 16^3 workload" in line["cpu_baseline"]["sample"]
+    assert line["value"] > 0 and line["config"]["n_elem"] == 16
