@@ -457,7 +457,8 @@ def oracle_threads():
         return os.cpu_count() or 1
 
 
-def cpu_baseline(sample_n=N_ELEM, repeats=5):
+def cpu_baseline(sample_n=None, repeats=5):
+    sample_n = N_ELEM if sample_n is None else sample_n
     run, dofs = oracle_step_runner(sample_n)
     run()
     t = []

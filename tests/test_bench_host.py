@@ -138,3 +138,10 @@ def test_reference_arm_switches_to_a_sample(monkeypatch):
     line = bench.reference_arm(argparse.Namespace(steps=1, warmup=3), 0, 1)
     assert "8^3-cell sample of the 16^3 workload" in line["cpu_baseline"]["sample"]
     assert line["value"] > 0 and line["config"]["n_elem"] == 16
+
+
+def test_cpu_baseline_line(monkeypatch):
+    monkeypatch.setattr(bench, "N_ELEM", 2)
+    cb = bench.cpu_baseline(repeats=1)
+    assert cb["kind"] == "oracle" and cb["value"] > 0 and cb["cores"] >= 1
+    assert cb["sample"].startswith("oracle") and "2^3 cells" in cb["sample"]
