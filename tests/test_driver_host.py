@@ -1,6 +1,6 @@
 """Host logic of the drivers (no GPU): the CFL time step of the
-Taylor-Green driver (Sec. 2 and Sec. 4.1, dt = Cr / k_u^1.5 * h / U0) and the
-mesh sizes of the degree sweep."""
+Taylor-Green driver (Sec. 2 and Sec. 4.1, dt = Cr / k_u^1.5 * h / U0), its
+kinetic-energy normalisation, and the mesh sizes of the degree sweep."""
 import math
 
 import pytest
@@ -25,3 +25,20 @@ def test_degree_sweep_sizes():
         assert n == round(256 / (k + 1))
         assert abs(n ** 3 * (k + 1) ** 3 / 2 ** 24 - 1) <= 0.05, (k, n)
     assert SWEEP_N[3] == 64 and SWEEP_N[7] == 32
+
+
+def test_kinetic_energy_normalisation():
+    """tgv.kinetic_energy = u^T M u / (2 |Omega|) on the [-pi, pi]^3 box, the
+    oracle's e_k (Sec. 4), computed through the oracle-backed test double of
+    the library's mass matrix and dot product."""
+    import numpy as np
+    import torch
+    from oracle import dg
+    from paper_1802_01439_gb300.tgv import kinetic_energy
+    from tests.host_double import OracleContext
+    m = dg.Mesh(2)
+    ctx = OracleContext(m, 3, 1.0 / 1600)
+    U = np.stack(ctx.su.interpolate(dg.taylor_green))
+    u = torch.from_numpy(U.ravel().copy())
+    assert kinetic_energy(ctx, u) == pytest.approx(dg.kinetic_energy(ctx.su, U), rel=1e-14)
+    assert kinetic_energy(ctx, 2 * u) == pytest.approx(4 * kinetic_energy(ctx, u), rel=1e-14)
