@@ -1,3 +1,6 @@
+"""Test configuration: the repository root on sys.path, the markers (`gpu`
+for tests that need a CUDA GPU, `slow` for the longer ones), and GPU tests
+skipped where no CUDA device exists."""
 import os
 import sys
 
@@ -10,7 +13,7 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
-    config.addinivalue_line("markers", "slow: longer CPU test")
+    config.addinivalue_line("markers", "slow: a longer test (tens of seconds or more)")
 
 
 def pytest_collection_modifyitems(config, items):
