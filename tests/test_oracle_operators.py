@@ -333,6 +333,26 @@ def test_convective_vjp_adjoint_identity(n, k, field):
     assert abs(lhs - rhs) < 1e-8 * np.sum(np.abs(Wt * Jv))
 
 
+@pytest.mark.parametrize("n,k", [((1, 1, 1), 2), ((2, 1, 1), 1)])
+def test_convective_vjp_against_the_full_jacobian(n, k):
+    """J^T w elementwise: the Jacobian of C built column by column from
+    central differences (a uniform offset keeps every normal velocity away
+    from the LLF kinks, so each column is exact up to the difference error)."""
+    m = dg.Mesh(n)
+    s = dg.Space(m, k)
+    C = dg.Convective(s)
+    U = rand((3, m.E, s.ndofs_cell), 31) * 0.2 + 0.7
+    W = rand(U.shape, 32)
+    eps = 1e-6
+    J = np.empty((U.size, U.size))
+    for j in range(U.size):
+        e = np.zeros(U.size)
+        e[j] = eps
+        J[:, j] = ((C.apply(U + e.reshape(U.shape)) - C.apply(U - e.reshape(U.shape))) / (2 * eps)).ravel()
+    ref = J.T @ W.ravel()
+    assert np.max(np.abs(C.vjp(U, W).ravel() - ref)) <= 1e-7 * np.max(np.abs(ref))
+
+
 def test_convective_vjp_quadratic_exact():
     """Without kinks (u.n of one sign everywhere and |u-.n| > |u+.n| on all
     faces is not needed: use a field whose LLF lambda is constant), C is
