@@ -5,63 +5,93 @@ import argparse
 import json
 import os
 
+import numpy as np
 import pytest
 
 import bench
 
 
-def _conv_cell_flops_by_phase(N, Q):
-    """The cell kernel's algorithmic FP64 flops per cell, phase by phase
-    (multiply-add = 2 flops): x and y interpolation of 3 components, then per
-    z-plane the z interpolation, the 6 distinct products u_c u_d, the 8
-    distinct x tests, the 9 y tests (two per component for Y1, one for Y3)
-    and the z accumulation (two per output), and the face integrals added to
-    the 6 face layers of 3 components."""
-    fma_x = 3 * (N * N) * Q * N            # lines (c, y, z): Q outputs of N terms
-    fma_y = 3 * (Q * N) * Q * N            # lines (c, qx, z)
-    per_plane = (2 * (3 * Q * Q * N)       # z interpolation: 3 Q^2 points of N terms
-                 + 6 * Q * Q               # products (one flop each)
-                 + 2 * (8 * Q * N * Q)     # x tests: 8 tests x Q rows x N outputs x Q terms
-                 + 2 * (9 * N * N * Q)     # y tests
-                 + 2 * (3 * 2 * N ** 3))   # z accumulation
-    return 2 * (fma_x + fma_y) + Q * per_plane + 6 * 3 * N * N
+class _Counter:
+    def __init__(self):
+        self.fma = self.add = 0
 
 
-@pytest.mark.parametrize("N", [2, 3, 4, 5, 8, 12])
-def test_conv_cell_flops_match_phase_count(N):
-    Q = 3 * N // 2
-    assert bench.conv_cell_flops(N, Q) == _conv_cell_flops_by_phase(N, Q)
+def _even_odd_apply(A, x, cnt):
+    """Applies the M x L matrix A (centrosymmetric: A[M-1-i, L-1-j] = A[i, j])
+    to x in even-odd form, counting the operations: fold x into sums and
+    differences of mirrored entries, contract the even and odd halves, and
+    recombine mirrored outputs."""
+    M, L = A.shape
+    hl, hm = L // 2, M // 2
+    e = [x[j] + x[L - 1 - j] for j in range(hl)] + ([x[hl]] if L % 2 else [])
+    o = [x[j] - x[L - 1 - j] for j in range(hl)]
+    cnt.add += 2 * hl
+    # A = [[P, Q], [J Q J, J P J]] in blocks of mirrored rows/columns: the
+    # even part uses (A[i, j] + A[i, L-1-j]) / 2-type half tables
+    ye, yo = [], []
+    for i in range(-(-M // 2)):
+        acc = 0.0
+        for j in range(hl):
+            acc += 0.5 * (A[i, j] + A[i, L - 1 - j]) * e[j]
+            cnt.fma += 1
+        if L % 2:
+            acc += A[i, hl] * e[hl]
+            cnt.fma += 1
+        ye.append(acc)
+    for i in range(hm):
+        acc = 0.0
+        for j in range(hl):
+            acc += 0.5 * (A[i, j] - A[i, L - 1 - j]) * o[j]
+            cnt.fma += 1
+        yo.append(acc)
+    y = np.empty(M)
+    for i in range(hm):
+        y[i], y[M - 1 - i] = ye[i] + yo[i], ye[i] - yo[i]
+    if M % 2:
+        y[hm] = ye[hm]
+    cnt.add += 2 * hm
+    return y
 
 
-def test_conv_cell_flops_bench_value():
-    # k = 3: the figure quoted for the dominant kernel
-    assert bench.conv_cell_flops(4, 6) == 41328
+@pytest.mark.parametrize("L,M", [(3, 3), (4, 4), (4, 6), (6, 4), (5, 7), (12, 18), (18, 12)])
+def test_even_odd_line_count(L, M):
+    """bench.eo_line counts exactly the operations of an even-odd contraction
+    that reproduces the dense product of a centrosymmetric matrix."""
+    rng = np.random.default_rng(L * 100 + M)
+    B = rng.uniform(-1, 1, (M, L))
+    A = 0.5 * (B + B[::-1, ::-1])                       # centrosymmetric
+    x = rng.uniform(-1, 1, L)
+    cnt = _Counter()
+    y = _even_odd_apply(A, x, cnt)
+    assert np.max(np.abs(y - A @ x)) < 1e-14
+    assert (cnt.fma, cnt.add) == bench.eo_line(L, M)
+    assert cnt.fma < L * M or L * M <= 2
 
 
-def _conv_face_flops_by_phase(N, Q):
-    """The face kernel's algorithmic FP64 flops per face (multiply-add = 2
-    flops): the traces of 3 components of both cells (the face layer's N^2
-    nodal values interpolated along one tangential direction to Q N points,
-    then along the other to Q^2, multiply-adds of N terms), the LLF flux at
-    the Q^2 points (per component: two products, their sum, the halving, the
-    jump, its product with the penalty and the final sum, 7 flops; 2 more for
-    max(|a|, |b|)), the test of the 3 flux components with the face-layer
-    basis (Q^2 -> N Q -> N^2, multiply-adds of Q terms), and the scaling of
-    the 3 N^2 results by the face area."""
-    traces = 2 * (6 * (Q * N) * N + 6 * (Q * Q) * N)
-    flux = Q * Q * (3 * 7 + 2)
-    tests = 2 * (3 * (N * Q) * Q + 3 * (N * N) * Q)
-    return traces + flux + tests + 3 * N * N
+def test_laplace_ops_k3_and_k11():
+    # 8 sweeps of N^2 lines + 12 multiply-adds and 2 additions per DoF
+    assert bench.laplace_ops(4) == (8 * 16 * 8 + 12 * 64, 8 * 16 * 8 + 2 * 64)
+    assert bench.flops(bench.laplace_ops(4)) / 64 == 74.0           # 88 in direct form
+    assert bench.flops(bench.laplace_ops(12)) / 12 ** 3 == pytest.approx(138.0)
 
 
-@pytest.mark.parametrize("N", [2, 3, 4, 5, 8, 12])
-def test_conv_face_flops_match_phase_count(N):
-    Q = 3 * N // 2
-    assert bench.conv_face_flops(N, Q) == _conv_face_flops_by_phase(N, Q)
+def test_convective_ops_are_below_the_direct_form():
+    for N in range(2, 13):
+        Q = 3 * N // 2
+        cc, cf = bench.conv_cell_ops(N, Q), bench.conv_face_ops(N, Q)
+        direct_cell = (3 * (N * N * Q * N + Q * N * Q * N + Q * Q * Q * N)
+                       + (8 * Q * Q + 9 * N * Q + 6 * N * N) * Q * N)
+        assert cc[0] <= direct_cell
+        assert cf[0] > 0 and cf[1] > 0
+    assert bench.conv_cell_ops(4, 6) == (3 * (16 + 24 + 36) * 12 + (8 * 36 + 9 * 24 + 6 * 16) * 12,
+                                         3 * (16 + 24 + 36) * 10 + 6 * 216 + (8 * 36 + 9 * 24 + 6 * 16) * 10
+                                         + 3 * 64 + 18 * 16)
 
 
-def test_conv_face_flops_bench_value():
-    assert bench.conv_face_flops(4, 6) == 5196
+def test_alu_fraction_by_mode():
+    ops = (1000, 500)
+    assert bench.alu_frac(ops, 1e-9, 0) == pytest.approx(2500e9 / 1e12 / bench.FP64_PEAK_TFLOPS)
+    assert bench.alu_frac(ops, 1e-9, 1) == pytest.approx((15 * 1000 + 8 * 500) * 1e9 / 1e12 / bench.FP32_PEAK_TFLOPS)
 
 
 def test_step_hbm_bytes_and_fraction():
@@ -112,8 +142,12 @@ def test_clock_sampler_without_process():
     assert bench.ClockSampler().stop() is None
 
 
+SMALL_SWEEP = [(2, 4), (3, 4)]
+
+
 def test_reference_arm_line(monkeypatch):
-    monkeypatch.setattr(bench, "N_ELEM", 2)
+    monkeypatch.setattr(bench, "SWEEP", SMALL_SWEEP)
+    monkeypatch.setattr(bench, "CPU_SAMPLE_N", 2)
     line = bench.reference_arm(argparse.Namespace(steps=1, warmup=1), 0, 1)
     json.dumps(line)
     assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["value"] > 0
@@ -123,25 +157,25 @@ def test_reference_arm_line(monkeypatch):
 
 
 def test_reference_sample_bounds_the_run():
-    # fits: the full mesh; 200 steps of 0.8 s: halved once (1/8 of the cost)
-    assert bench.reference_sample_n(32, 0.5, 100, budget=150.0) == 32
-    assert bench.reference_sample_n(32, 0.8, 200, budget=150.0) == 16
-    assert bench.reference_sample_n(32, 0.8, 100000, budget=150.0) == 8      # floor
+    # fits: the full sample; 200 steps of 0.8 s: halved once (1/8 of the cost)
+    assert bench.reference_sample_n(4, 0.5, 100, budget=150.0) == 4
+    assert bench.reference_sample_n(4, 0.8, 200, budget=150.0) == 2
+    assert bench.reference_sample_n(4, 0.8, 100000, budget=150.0) == 2      # floor
     assert bench.reference_sample_n(2, 10.0, 100, budget=1.0) == 2           # tiny meshes stay
 
 
 def test_reference_arm_switches_to_a_sample(monkeypatch):
-    """A budget the full mesh cannot meet makes every step run on the 8^3
-    sample, and the line says so."""
-    monkeypatch.setattr(bench, "N_ELEM", 16)
+    """A budget the sample cannot meet halves it, and the line says so."""
+    monkeypatch.setattr(bench, "SWEEP", SMALL_SWEEP)
+    monkeypatch.setattr(bench, "CPU_SAMPLE_N", 4)
     monkeypatch.setattr(bench, "REF_BUDGET_S", 1e-9)
     line = bench.reference_arm(argparse.Namespace(steps=1, warmup=3), 0, 1)
-    assert "8^3-cell sample of the 16^3 workload" in line["cpu_baseline"]["sample"]
-    assert line["value"] > 0 and line["config"]["n_elem"] == 16
+    assert "on a 2^3-cell sample" in line["cpu_baseline"]["sample"]
+    assert line["value"] > 0 and line["config"]["degrees"] == [2, 3]
 
 
 def test_cpu_baseline_line(monkeypatch):
-    monkeypatch.setattr(bench, "N_ELEM", 2)
-    cb = bench.cpu_baseline(repeats=1)
+    monkeypatch.setattr(bench, "SWEEP", SMALL_SWEEP)
+    cb = bench.cpu_baseline(sample_n=2, repeats=1)
     assert cb["kind"] == "oracle" and cb["value"] > 0 and cb["cores"] >= 1
     assert cb["sample"].startswith("oracle") and "2^3 cells" in cb["sample"]

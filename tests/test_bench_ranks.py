@@ -23,7 +23,8 @@ def _rank(rank, world, port, results):
         import bench
         bench.barrier(world)
         slowest = bench.max_over_ranks(1.5 + rank, world)
-        bench.N_ELEM = 2
+        bench.SWEEP = [(2, 2), (3, 2)]
+        bench.CPU_SAMPLE_N = 2
         line = bench.reference_arm(argparse.Namespace(steps=1, warmup=1), rank, world)
         results[rank] = (slowest, line is not None, line["n_gpus"] if line else None)
     finally:
