@@ -35,13 +35,17 @@ class Mesh:
     """Uniform periodic Cartesian mesh of the box [lo, hi] (Sec. 4: (2^l)^d
     elements on [-pi, pi]^3; any n per direction is allowed here)."""
 
-    def __init__(self, n, lo=(-PI, -PI, -PI), hi=(PI, PI, PI)):
+    def __init__(self, n, lo=(-PI, -PI, -PI), hi=(PI, PI, PI), dtype=np.float64):
+        """dtype: the precision of every table and product (np.float64; or
+        np.longdouble for an extended-precision evaluation of the same
+        discrete operators: lo and hi stay the given doubles)."""
         if np.isscalar(n):
             n = (n, n, n)
         self.n = tuple(int(v) for v in n)
-        self.lo = np.array(lo, dtype=np.float64)
-        self.hi = np.array(hi, dtype=np.float64)
-        self.h = (self.hi - self.lo) / np.array(self.n, dtype=np.float64)
+        self.dtype = np.dtype(dtype)
+        self.lo = np.array(lo, dtype=np.float64).astype(dtype)
+        self.hi = np.array(hi, dtype=np.float64).astype(dtype)
+        self.h = (self.hi - self.lo) / np.array(self.n, dtype=dtype)
         self.E = self.n[0] * self.n[1] * self.n[2]
         e = np.arange(self.E)
         self.ijk = np.stack([e % self.n[0], (e // self.n[0]) % self.n[1],
@@ -76,7 +80,8 @@ class Space:
         self.mesh = mesh
         self.k = int(k)
         self.N = self.k + 1
-        self.nodes = rules.lgl_nodes(self.k)
+        self.dtype = mesh.dtype
+        self.nodes = rules.lgl_nodes(self.k, self.dtype)
         self.ndofs_cell = self.N ** 3
         self.size = mesh.E * self.ndofs_cell
 
@@ -102,10 +107,11 @@ class Space:
 # ----------------------------------------------------------------------------
 class _Tables:
     def __init__(self, space, nq):
-        self.g, self.w = rules.gauss(nq)
-        self.V, self.D = rules.lagrange(space.nodes, self.g)      # (nq, N)
-        self.V0, self.D0 = rules.lagrange(space.nodes, [0.0])      # (1, N)
-        self.V1, self.D1 = rules.lagrange(space.nodes, [1.0])
+        dt = space.dtype
+        self.g, self.w = rules.gauss(nq, dt)
+        self.V, self.D = rules.lagrange(space.nodes, self.g, dt)      # (nq, N)
+        self.V0, self.D0 = rules.lagrange(space.nodes, [0.0], dt)      # (1, N)
+        self.V1, self.D1 = rules.lagrange(space.nodes, [1.0], dt)
 
 
 def _cell_tables(space, nq):
@@ -135,7 +141,7 @@ def _face_tables(space, nq, axis, side):
     val = tensor3(*Tv)
     der = tensor3(*Td)
     wt = [t.w, t.w, t.w]
-    wt[axis] = np.ones(1)
+    wt[axis] = np.ones(1, dtype=space.dtype)
     area = np.prod([h[a] for a in range(3) if a != axis])
     wf = np.kron(wt[2], np.kron(wt[1], wt[0])) * area
     return val, der, wf
@@ -197,7 +203,7 @@ class Laplace:
 
     def apply(self, X):
         """X: (E, N^3) or (ncomp, E, N^3)."""
-        X = np.asarray(X, dtype=np.float64)
+        X = np.asarray(X, dtype=self.space.dtype)
         if X.ndim == 3:
             return np.stack([self.apply(x) for x in X])
         m = self.space.mesh
@@ -348,29 +354,40 @@ class Convective:
             vp, _, _ = _face_tables(space, self.nq, axis, 0)
             self.face.append((vm, vp, wf))
 
-    def apply(self, U):
-        """U: (3, E, N^3) -> C(U): (3, E, N^3)."""
+    def apply(self, U, cells=None):
+        """U: (3, E, N^3) -> C(U): (3, E, N^3).  With `cells` (a list of cell
+        ids) only the rows of those cells are computed (the others stay zero):
+        their cell terms and the faces that touch them, in the same
+        arithmetic."""
         m = self.space.mesh
-        U = np.asarray(U, dtype=np.float64)
-        uq = np.stack([U[c] @ self.Phi.T for c in range(3)])       # (3, E, Q^3)
+        U = np.asarray(U, dtype=self.space.dtype)
+        sel = np.arange(m.E) if cells is None else np.asarray(cells)
+        uq = np.stack([U[c][sel] @ self.Phi.T for c in range(3)])  # (3, |sel|, Q^3)
         Y = np.zeros_like(U)
         for c in range(3):
             for d in range(3):
                 F = uq[c] * uq[d] * self.W[None, :]
-                Y[c] -= F @ self.dPhi[d]
-        em = np.arange(m.E)
+                Y[c][sel] -= F @ self.dPhi[d]
         for axis in range(3):
             vm, vp, wf = self.face[axis]
+            em = np.arange(m.E)
             ep = m.neighbor(axis, +1)
-            um = np.stack([U[c][em] @ vm.T for c in range(3)])     # (3, E, Q^2)
+            if cells is not None:       # faces with a selected cell on either side
+                keep = np.isin(em, sel) | np.isin(ep, sel)
+                em, ep = em[keep], ep[keep]
+            um = np.stack([U[c][em] @ vm.T for c in range(3)])     # (3, faces, Q^2)
             up = np.stack([U[c][ep] @ vp.T for c in range(3)])
             unm, unp = um[axis], up[axis]
             lam = np.maximum(np.abs(unm), np.abs(unp))
             for c in range(3):
-                Fs = 0.5 * (um[c] * unm + up[c] * unp) + lam * (um[c] - up[c])
+                Fs = (um[c] * unm + up[c] * unp) / 2 + lam * (um[c] - up[c])
                 Fs = Fs * wf[None, :]
-                Y[c][em] += Fs @ vm
-                Y[c][ep] -= Fs @ vp
+                np.add.at(Y[c], em, Fs @ vm)
+                np.subtract.at(Y[c], ep, Fs @ vp)
+        if cells is not None:
+            out = np.zeros_like(Y)
+            out[:, sel] = Y[:, sel]
+            Y = out
         return Y
 
 
