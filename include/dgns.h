@@ -72,8 +72,12 @@ typedef struct {
                          /* 1 double-float (pairs of FP32 with a 48-bit significand */
                          /* on the FP32 pipe, which GB300 runs 61x faster; parity   */
                          /* with FP64 to 1e-12 relative for vectors with max |x|    */
-                         /* between ~1e-15 and 2^127).  The multigrid V-cycle runs  */
-                         /* in mg_precision either way.                             */
+                         /* between ~1e-15 and 2^127);                              */
+                         /* 2 FP64-wide emulation: triple-float (three FP32, up to  */
+                         /* 72 significant bits, on the FP32 pipe) in the           */
+                         /* SIPG-type and mass kernels, native FP64 in all others;  */
+                         /* same input range as 1.  The multigrid V-cycle runs in   */
+                         /* mg_precision in every mode.                             */
 } dgns_mesh_desc;
 
 /* Defaults: 4^3 elements on [-pi,pi]^3, k_u = 3, k_p = k_u - 1, 3/2 rule,
@@ -108,6 +112,14 @@ int dgns_vmult_laplace(dgns_ctx* ctx, double* dst, const double* src, int space)
 /* Same operator in FP32 on multigrid level `level` (0 = coarsest, levels-1 =
  * the pressure space itself).  Device pointers only. */
 int dgns_vmult_laplace_f32(dgns_ctx* ctx, float* dst, const float* src, int level);
+/* One step of the FP32 Jacobi-Chebyshev smoother on multigrid level `level`
+ * (Sec. 3.3), fused into the level operator as the V-cycle runs it:
+ * dst = x + c1 (x - xprev) + c2 D^-1 (b - L x), with D the diagonal of the
+ * level's L (one N^3 table, identical in every cell) and xprev = NULL read
+ * as zero.  Needs mg_precision = 32; device pointers, 16-byte aligned; dst
+ * must not overlap an input. */
+int dgns_mg_chebyshev_step_f32(dgns_ctx* ctx, float* dst, const float* x, const float* xprev, const float* b,
+                               double c1, double c2, int level);
 /* Diagonal of L (the Jacobi weights of the Chebyshev smoother, Sec. 3.3). */
 int dgns_laplace_diagonal(dgns_ctx* ctx, double* dst, int space);
 
@@ -175,15 +187,28 @@ int dgns_dot(dgns_ctx* ctx, const double* a, const double* b, long long n, doubl
  * Euclidean norm of the extrapolated velocity u_ex3 (k_u+1 Gauss points) and
  * h = V_e^(1/3):  tau_d[e] = zeta_d ||u||_e h / (k_u+1) dt,
  * tau_c[e] = zeta_c ||u||_e dt.  Device pointers (tau arrays of n_elem
- * doubles).  k_u <= 7. */
+ * doubles). */
 int dgns_penalty_parameters(dgns_ctx* ctx, const double* u_ex3, double dt, double zeta_d, double zeta_c,
                             double* tau_d, double* tau_c);
 /* Projection operator of the projection substep (Sec. 3.3):
  * dst3 = (M + A_D + A_C) src3 with a_D(v,u) = (div v, tau_D div u)_e and
- * a_C(v,u) = sum_F int {{tau_C}} (v- - v+).n (u- - u+).n.  Device pointers;
- * k_u <= 7. */
+ * a_C(v,u) = sum_F int {{tau_C}} (v- - v+).n (u- - u+).n, in one fused pass
+ * over memory.  Device pointers. */
 int dgns_vmult_projection(dgns_ctx* ctx, double* dst3, const double* src3, const double* tau_d,
                           const double* tau_c);
+/* The terms of the same operator one at a time, each in its own pass over
+ * memory (the operator-by-operator evaluation that the fused operator is
+ * compared with in Sec. 4.4): terms = DGNS_PROJ_MASS (dst3 = M src3, the
+ * mass kernel; tau arrays unused, may be NULL), DGNS_PROJ_DIV
+ * (dst3 = A_D src3; tau_c unused), DGNS_PROJ_CONT (dst3 = A_C src3; tau_d
+ * unused) or DGNS_PROJ_ALL (the fused operator, as dgns_vmult_projection).
+ * Device pointers; any other terms value returns DGNS_ERR_INVALID_ARG. */
+#define DGNS_PROJ_MASS 1
+#define DGNS_PROJ_DIV 2
+#define DGNS_PROJ_CONT 4
+#define DGNS_PROJ_ALL 7
+int dgns_vmult_projection_terms(dgns_ctx* ctx, double* dst3, const double* src3, const double* tau_d,
+                                const double* tau_c, int terms);
 
 /* CG solves stop when ||r||_2 <= rel_tol ||r_0||_2 or ||r||_2 <= abs_tol,
  * r_0 = b - A x_0 the initial residual (Sec. 3.3: the paper's solvers use
@@ -242,12 +267,13 @@ int dgns_cg_invmass_solve(dgns_ctx* ctx, double* x3, const double* b3, double ma
                           const dgns_solve_params* params, dgns_solve_info* info);
 
 /* Allocation-free variant of dgns_cg_invmass_solve (the paper has no
- * counterpart: this serves callers that cannot allocate device memory, e.g.
- * code running under CUDA stream capture, applications whose memory belongs
- * to their own pool, or real-time loops that must not risk allocation
- * latency or failure).  Same arguments, same arithmetic and the same result.
- * Differences:
- *   - x3 and b3 must be device pointers (no host staging);
+ * counterpart: this serves callers that cannot let a library allocate device
+ * memory, e.g. applications whose device memory belongs to their own pool or
+ * allocator, or real-time loops that must not risk allocation latency or an
+ * out-of-memory failure in the middle of a time step).  Same arguments, same
+ * arithmetic and the same result.  Differences:
+ *   - x3 and b3 must be device pointers (no host staging), and the device that
+ *     holds the context must be current (else DGNS_ERR_INVALID_ARG);
  *   - 3 * n_u (the CG vector length) must not exceed 524288, the size of a
  *     fixed scratch array compiled into the library (four work vectors plus
  *     reduction partials, ~16 MiB held by every GPU that loads the library
@@ -256,6 +282,9 @@ int dgns_cg_invmass_solve(dgns_ctx* ctx, double* x3, const double* b3, double ma
  *     looks up the device address of that array (cudaGetSymbolAddress, once
  *     per device, under a lock); make that first call before any stream
  *     capture.
+ * Like dgns_cg_invmass_solve, it reads one block of scalars back to the host
+ * and synchronises the context's stream once per CG iteration, and returns
+ * after the solve has finished.
  * All calls share the one array and it keeps the last call's contents:
  * calls that may overlap on the GPU (other streams, other host threads,
  * other contexts) race on it and must be serialised by the caller. */
@@ -264,7 +293,7 @@ int dgns_cg_invmass_solve_noalloc(dgns_ctx* ctx, double* x3, const double* b3, d
 
 /* Projection solve (Sec. 3.3): CG preconditioned by the inverse mass
  * matrix on (M + A_D + A_C) x3 = b3, FP64; initial guess per
- * params->use_initial_guess; device pointers; k_u <= 7. */
+ * params->use_initial_guess; device pointers. */
 int dgns_cg_projection_solve(dgns_ctx* ctx, double* x3, const double* b3, const double* tau_d,
                              const double* tau_c, const dgns_solve_params* params, dgns_solve_info* info);
 

@@ -508,13 +508,18 @@ class Projection:
             self.faces.append({"--": vm.T @ (wf[:, None] * vm), "-+": -(vm.T @ (wf[:, None] * vp)),
                                "+-": -(vp.T @ (wf[:, None] * vm)), "++": vp.T @ (wf[:, None] * vp)})
 
-    def apply(self, U):
+    def apply(self, U, terms="MDC"):
+        """(M + A_D + A_C) U, or the sum of the terms named in `terms` (a
+        string of "M", "D", "C")."""
         m = self.space.mesh
         U = np.asarray(U, dtype=np.float64)
-        Y = np.stack([U[c] @ self.Me.T for c in range(3)])
-        for b in range(3):
-            for a in range(3):
-                Y[b] += self.tau_d[:, None] * (U[a] @ self.AD[b][a].T)
+        Y = np.stack([U[c] @ self.Me.T for c in range(3)]) if "M" in terms else np.zeros_like(U)
+        if "D" in terms:
+            for b in range(3):
+                for a in range(3):
+                    Y[b] += self.tau_d[:, None] * (U[a] @ self.AD[b][a].T)
+        if "C" not in terms:
+            return Y
         em = np.arange(m.E)
         for a in range(3):
             B = self.faces[a]

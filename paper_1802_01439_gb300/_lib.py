@@ -18,6 +18,8 @@ DGNS_ERR_NONFINITE = 5
 DGNS_ERR_ALIAS = 6
 DGNS_ERR_UNSUPPORTED = 7
 SPACE_U = 0
+# terms of the projection operator (dgns_vmult_projection_terms)
+PROJ_MASS, PROJ_DIV, PROJ_CONT, PROJ_ALL = 1, 2, 4, 7
 SPACE_P = 1
 MAX_LEVELS = 16
 
@@ -81,6 +83,8 @@ SIGNATURES = {
     "dgns_dot": (_I, [_P, _P, _P, _LL, ctypes.POINTER(_D)]),
     "dgns_penalty_parameters": (_I, [_P, _P, _D, _D, _D, _P, _P]),
     "dgns_vmult_projection": (_I, [_P, _P, _P, _P, _P]),
+    "dgns_vmult_projection_terms": (_I, [_P, _P, _P, _P, _P, _I]),
+    "dgns_mg_chebyshev_step_f32": (_I, [_P, _P, _P, _P, _P, _D, _D, _I]),
     "dgns_cg_projection_solve": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(SolveParams),
                                       ctypes.POINTER(SolveInfo)]),
     "dgns_default_solve_params": (None, [ctypes.POINTER(SolveParams)]),

@@ -207,10 +207,18 @@ class Context:
                                                float(dt), float(zeta_d), float(zeta_c), _ptr(td), _ptr(tc)))
         return td, tc
 
-    def vmult_projection(self, dst3, src3, tau_d, tau_c):
+    def vmult_projection(self, dst3, src3, tau_d, tau_c, terms=_lib.PROJ_ALL):
+        """dst3 = (M + A_D + A_C) src3 in one fused kernel, or one term of it
+        (terms = PROJ_MASS, PROJ_DIV, PROJ_CONT) in its own pass."""
         n = 3 * self.n_u
-        check(self.lib.dgns_vmult_projection(self.h, self._vec(dst3, n, name="dst3"),
-                                             self._vec(src3, n, name="src3"), _ptr(tau_d), _ptr(tau_c)))
+        if terms == _lib.PROJ_ALL:
+            check(self.lib.dgns_vmult_projection(self.h, self._vec(dst3, n, name="dst3"),
+                                                 self._vec(src3, n, name="src3"), _ptr(tau_d), _ptr(tau_c)))
+        else:
+            td = _ptr(tau_d) if tau_d is not None else None
+            tc = _ptr(tau_c) if tau_c is not None else None
+            check(self.lib.dgns_vmult_projection_terms(self.h, self._vec(dst3, n, name="dst3"),
+                                                       self._vec(src3, n, name="src3"), td, tc, int(terms)))
         return dst3
 
     # ------------------------------------------------------------ solvers
@@ -277,6 +285,17 @@ class Context:
         check(self.lib.dgns_mg_vcycle(self.h, self._vec(z, self.n_p, name="z"),
                                       self._vec(r, self.n_p, name="r"), ctypes.byref(p)))
         return z
+
+    def mg_chebyshev_step_f32(self, dst, x, xprev, b, c1, c2, level):
+        """dst = x + c1 (x - xprev) + c2 D^-1 (b - L x) on a multigrid level
+        (FP32 device tensors; xprev None reads as zero)."""
+        n = x.numel()
+        xp = self._vec(xprev, n, torch.float32, "xprev") if xprev is not None else None
+        check(self.lib.dgns_mg_chebyshev_step_f32(self.h, self._vec(dst, n, torch.float32, "dst"),
+                                                  self._vec(x, n, torch.float32, "x"), xp,
+                                                  self._vec(b, n, torch.float32, "b"), float(c1), float(c2),
+                                                  int(level)))
+        return dst
 
     def mg_prolongate_f32(self, fine, coarse, level):
         check(self.lib.dgns_mg_prolongate_f32(self.h, _ptr(fine), _ptr(coarse), level))

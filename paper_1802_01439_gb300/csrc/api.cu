@@ -78,6 +78,8 @@ void dev_free(void* p) {
 namespace dgns {
 
 int set_error(int code, const std::string& msg) { return fail(code, msg); }
+void clear_error() { g_err.clear(); }
+bool error_empty() { return g_err.empty(); }
 
 void build_lap(const Space1D& s, const double h[3], double pf, double coef, double mass_factor,
                LapHost& L) {
@@ -656,16 +658,19 @@ int dgns_create(const dgns_mesh_desc* desc, void* stream, dgns_ctx** out) {
   }
   if (d.mg_precision != 0 && d.mg_precision != 32 && d.mg_precision != 64)
     return fail(DGNS_ERR_INVALID_ARG, "mg_precision must be 0, 32 or 64");
-  if (d.fp64_mode != 0 && d.fp64_mode != 1) return fail(DGNS_ERR_INVALID_ARG, "fp64_mode must be 0 or 1");
+  if (d.fp64_mode < 0 || d.fp64_mode > 2) return fail(DGNS_ERR_INVALID_ARG, "fp64_mode must be 0, 1 or 2");
   if ((long long)d.n_elem[0] * d.n_elem[1] * d.n_elem[2] * 3 >= (1LL << 31))
     return fail(DGNS_ERR_UNSUPPORTED, "meshes with 3 * cells >= 2^31 are not supported");
   const int Q = d.n_q_conv > 0 ? d.n_q_conv : (3 * (d.degree + 1)) / 2;
   if (Q != (3 * (d.degree + 1)) / 2 && Q != d.degree + 1)
     return fail(DGNS_ERR_UNSUPPORTED, "n_q_conv must be floor(3(k+1)/2) or k+1");
   d.n_q_conv = Q;
+  int device = 0;
+  DG_CUDA(cudaGetDevice(&device));
   dgns_ctx* c = new dgns_ctx();
   c->d = d;
   c->s = (cudaStream_t)stream;
+  c->device = device;
   c->m.nx = d.n_elem[0];
   c->m.ny = d.n_elem[1];
   c->m.nz = d.n_elem[2];
@@ -821,7 +826,7 @@ static int lap_like(dgns_ctx* c, double* dst, const double* src, int space, int 
     build_lap(c->sp1[space], h, c->d.penalty_factor, coef, mass_factor, scaled);
     tab = &scaled;
   }
-  DG_TRY(laplace_apply(false, c->m, ncomp, s, d, *tab, EPI_NONE, EpiHost(), c->s, c->d.fp64_mode == 1));
+  DG_TRY(laplace_apply(false, c->m, ncomp, s, d, *tab, EPI_NONE, EpiHost(), c->s, c->d.fp64_mode));
   return st.finish();
 }
 
@@ -861,6 +866,32 @@ int dgns_vmult_laplace_f32(dgns_ctx* c, float* dst, const float* src, int level)
   return 0;
 }
 
+int dgns_mg_chebyshev_step_f32(dgns_ctx* c, float* dst, const float* x, const float* xprev, const float* b,
+                               double c1, double c2, int level) {
+  g_err.clear();
+  if (!c) return fail(DGNS_ERR_INVALID_ARG, "ctx is null");
+  DG_NONNULL(dst, x, b);
+  if (c->mg_prec != 32) return fail(DGNS_ERR_UNSUPPORTED, "the FP32 smoother needs mg_precision = 32");
+  if (level < 0 || level >= (int)c->levels.size())
+    return fail(DGNS_ERR_INVALID_ARG, "level out of range (multigrid disabled?)");
+  Level& L = c->levels[level];
+  const size_t bytes = (size_t)L.n * sizeof(float);
+  if (overlaps(dst, bytes, x, bytes) || overlaps(dst, bytes, b, bytes) || (xprev && overlaps(dst, bytes, xprev, bytes)))
+    return fail(DGNS_ERR_ALIAS, "dst overlaps an input");
+  if (!aligned16(dst, x) || !aligned16(b, xprev ? xprev : b))
+    return fail(DGNS_ERR_INVALID_ARG, "vectors must be 16-byte aligned");
+  if (!is_device_ptr(dst) || !is_device_ptr(x) || !is_device_ptr(b) || (xprev && !is_device_ptr(xprev)))
+    return fail(DGNS_ERR_INVALID_ARG, "device pointers only");
+  EpiHost ea;
+  ea.b = b;
+  ea.dinv = L.dinv;
+  ea.xprev = xprev;
+  ea.c1 = c1;
+  ea.c2 = c2;
+  DG_TRY(laplace_apply(true, L.m, 1, x, dst, L.lap, EPI_CHEB, ea, c->s));
+  return 0;
+}
+
 int dgns_laplace_diagonal(dgns_ctx* c, double* dst, int space) {
   g_err.clear();
   if (!c) return fail(DGNS_ERR_INVALID_ARG, "ctx is null");
@@ -889,7 +920,7 @@ static int mass_like(dgns_ctx* c, double* dst, const double* src, int ncomp, int
   DG_TRY(st.out(dst, bytes, &d));
   const double(*T)[MAXN * MAXN] = inverse ? c->minv3[space] : c->mass3[space];
   DG_TRY(tensor3_apply(c->N[space], c->m.E * ncomp, (const double*)s, (double*)d, T[0], T[1], T[2], c->s,
-                       c->d.fp64_mode == 1));
+                       c->d.fp64_mode));
   return st.finish();
 }
 
@@ -1057,7 +1088,7 @@ int dgns_dissipation_grad(dgns_ctx* c, double* grad3, const double* u3) {
   for (int i = 0; i < 3; ++i) vol *= c->d.hi[i] - c->d.lo[i];
   LapHost K;
   build_broken_stiffness(c, 2.0 * c->d.nu / vol, K);
-  DG_TRY(laplace_apply(false, c->m, 3, s, d, K, EPI_NONE, EpiHost(), c->s, c->d.fp64_mode == 1));
+  DG_TRY(laplace_apply(false, c->m, 3, s, d, K, EPI_NONE, EpiHost(), c->s, c->d.fp64_mode));
   return st.finish();
 }
 
@@ -1074,7 +1105,7 @@ int dgns_dissipation(dgns_ctx* c, const double* u3, double* eps_out) {
   for (int i = 0; i < 3; ++i) vol *= c->d.hi[i] - c->d.lo[i];
   LapHost K;
   build_broken_stiffness(c, c->d.nu / vol, K);
-  DG_TRY(laplace_apply(false, c->m, 3, s, c->Ap, K, EPI_NONE, EpiHost(), c->s, c->d.fp64_mode == 1));
+  DG_TRY(laplace_apply(false, c->m, 3, s, c->Ap, K, EPI_NONE, EpiHost(), c->s, c->d.fp64_mode));
   DG_TRY(dot((const double*)s, c->Ap, n, c->red, S_T1, c->s));
   DG_TRY(read_scalars(c));
   *eps_out = c->h_scal[S_T1];
@@ -1118,7 +1149,7 @@ int dgns_penalty_parameters(dgns_ctx* c, const double* u_ex3, double dt, double 
   const double h_eff = cbrt(c->h[0] * c->h[1] * c->h[2]);
   const double fd = zeta_d * h_eff / (c->k[0] + 1) * dt, fc = zeta_c * dt;
   const int rc = penalty_parameters(c->m, u_ex3, tau_d, tau_c, c->proj, fd, fc, c->s, c->d.fp64_mode == 1);
-  if (rc == 7) return fail(DGNS_ERR_UNSUPPORTED, "projection operator: supported for k_u <= 7");
+  if (rc == 7) return fail(DGNS_ERR_UNSUPPORTED, "projection operator: degree not supported");
   DG_TRY(rc);
   return 0;
 }
@@ -1133,7 +1164,34 @@ int dgns_vmult_projection(dgns_ctx* c, double* dst3, const double* src3, const d
   if (!is_device_ptr(dst3) || !is_device_ptr(src3) || !is_device_ptr(tau_d) || !is_device_ptr(tau_c))
     return fail(DGNS_ERR_INVALID_ARG, "device pointers only");
   const int rc = projection_apply(c->m, src3, dst3, tau_d, tau_c, c->proj, c->s, c->d.fp64_mode == 1);
-  if (rc == 7) return fail(DGNS_ERR_UNSUPPORTED, "projection operator: supported for k_u <= 7");
+  if (rc == 7) return fail(DGNS_ERR_UNSUPPORTED, "projection operator: degree not supported");
+  DG_TRY(rc);
+  return 0;
+}
+
+int dgns_vmult_projection_terms(dgns_ctx* c, double* dst3, const double* src3, const double* tau_d,
+                                const double* tau_c, int terms) {
+  g_err.clear();
+  if (!c) return fail(DGNS_ERR_INVALID_ARG, "ctx is null");
+  if (terms == DGNS_PROJ_ALL) return dgns_vmult_projection(c, dst3, src3, tau_d, tau_c);
+  if (terms != DGNS_PROJ_MASS && terms != DGNS_PROJ_DIV && terms != DGNS_PROJ_CONT)
+    return fail(DGNS_ERR_INVALID_ARG, "terms must be DGNS_PROJ_MASS, _DIV, _CONT or _ALL");
+  DG_NONNULL(dst3, src3);
+  if (terms == DGNS_PROJ_DIV) DG_NONNULL(tau_d);
+  if (terms == DGNS_PROJ_CONT) DG_NONNULL(tau_c);
+  const size_t bu = (size_t)c->n[0] * 3 * sizeof(double);
+  if (overlaps(dst3, bu, src3, bu)) return fail(DGNS_ERR_ALIAS, "dst overlaps src");
+  if (!is_device_ptr(dst3) || !is_device_ptr(src3) || (tau_d && !is_device_ptr(tau_d)) ||
+      (tau_c && !is_device_ptr(tau_c)))
+    return fail(DGNS_ERR_INVALID_ARG, "device pointers only");
+  if (terms == DGNS_PROJ_MASS) {
+    const double(*T)[MAXN * MAXN] = c->mass3[DGNS_SPACE_U];
+    DG_TRY(tensor3_apply(c->N[0], 3 * c->m.E, src3, dst3, T[0], T[1], T[2], c->s, c->d.fp64_mode));
+    return 0;
+  }
+  const int rc = projection_apply(c->m, src3, dst3, tau_d, tau_c, c->proj, c->s, c->d.fp64_mode == 1,
+                                  terms == DGNS_PROJ_DIV ? PROJ_DIV : PROJ_CONT);
+  if (rc == 7) return fail(DGNS_ERR_UNSUPPORTED, "projection operator: degree not supported");
   DG_TRY(rc);
   return 0;
 }
@@ -1143,7 +1201,6 @@ int dgns_cg_projection_solve(dgns_ctx* c, double* x3, const double* b3, const do
   g_err.clear();
   if (!c) return fail(DGNS_ERR_INVALID_ARG, "ctx is null");
   DG_NONNULL(x3, b3, tau_d, tau_c);
-  if (c->N[0] > 8) return fail(DGNS_ERR_UNSUPPORTED, "projection operator: supported for k_u <= 7");
   dgns_solve_params prm;
   if (params) prm = *params;
   else dgns_default_solve_params(&prm);
@@ -1172,7 +1229,7 @@ int dgns_cg_projection_solve(dgns_ctx* c, double* x3, const double* b3, const do
   inf.initial_res = nb;
   int status = DGNS_OK;
   if (nb > 0.0) {
-    DG_TRY(tensor3_apply(N, 3 * c->m.E, c->r, c->z, MI[0], MI[1], MI[2], c->s, c->d.fp64_mode == 1));
+    DG_TRY(tensor3_apply(N, 3 * c->m.E, c->r, c->z, MI[0], MI[1], MI[2], c->s, c->d.fp64_mode));
     DG_TRY(cg_direction(c->p, c->z, n, c->red, true, c->s));
     DG_TRY(dot(c->r, c->z, n, c->red, S_RZ, c->s));
     int it = 0;
@@ -1194,7 +1251,7 @@ int dgns_cg_projection_solve(dgns_ctx* c, double* x3, const double* b3, const do
         status = DGNS_OK;
         break;
       }
-      DG_TRY(tensor3_apply(N, 3 * c->m.E, c->r, c->z, MI[0], MI[1], MI[2], c->s, c->d.fp64_mode == 1));
+      DG_TRY(tensor3_apply(N, 3 * c->m.E, c->r, c->z, MI[0], MI[1], MI[2], c->s, c->d.fp64_mode));
       DG_TRY(dot(c->r, c->z, n, c->red, S_RZNEW, c->s));
       DG_TRY(cg_direction(c->p, c->z, n, c->red, false, c->s));
     }
@@ -1287,7 +1344,7 @@ int dgns_cg_mg_solve(dgns_ctx* c, double* x, const double* b, const dgns_solve_p
   }
   if (prm.use_initial_guess) {
     // r0 = b - A x0 (A annihilates constants, so the mean shift of b is the one of r0)
-    DG_TRY(laplace_apply(false, c->m, 1, X, c->Ap, A, EPI_NONE, EpiHost(), c->s, c->d.fp64_mode == 1));
+    DG_TRY(laplace_apply(false, c->m, 1, X, c->Ap, A, EPI_NONE, EpiHost(), c->s, c->d.fp64_mode));
     DG_TRY(axpby(c->r, c->Ap, n, -1.0, 1.0, c->s));
     DG_TRY(dot(c->r, c->r, n, c->red, S_T0, c->s));
   }
@@ -1308,7 +1365,7 @@ int dgns_cg_mg_solve(dgns_ctx* c, double* x, const double* b, const dgns_solve_p
     int it = 0;
     status = DGNS_ERR_NOT_CONVERGED;
     while (it < prm.max_iter) {
-      DG_TRY(laplace_apply(false, c->m, 1, c->p, c->Ap, A, EPI_NONE, EpiHost(), c->s, c->d.fp64_mode == 1));
+      DG_TRY(laplace_apply(false, c->m, 1, c->p, c->Ap, A, EPI_NONE, EpiHost(), c->s, c->d.fp64_mode));
       DG_TRY(dot(c->p, c->Ap, n, c->red, S_PAP, c->s));
       DG_TRY(cg_update(X, c->r, c->p, c->Ap, n, c->red, c->s));
       DG_TRY(read_scalars(c));
@@ -1366,7 +1423,7 @@ int dgns_cg_invmass_solve(dgns_ctx* c, double* x3, const double* b3, double mass
   const double(*MI)[MAXN * MAXN] = c->minv3[0];
   DG_CUDA(cudaMemcpyAsync(c->r, B, bytes, cudaMemcpyDeviceToDevice, c->s));
   if (prm.use_initial_guess) {
-    DG_TRY(laplace_apply(false, c->m, 3, X, c->Ap, H, EPI_NONE, EpiHost(), c->s, c->d.fp64_mode == 1));
+    DG_TRY(laplace_apply(false, c->m, 3, X, c->Ap, H, EPI_NONE, EpiHost(), c->s, c->d.fp64_mode));
     DG_TRY(axpby(c->r, c->Ap, n, -1.0, 1.0, c->s));
     DG_TRY(dot(c->r, c->r, n, c->red, S_T0, c->s));
   } else {
@@ -1379,14 +1436,14 @@ int dgns_cg_invmass_solve(dgns_ctx* c, double* x3, const double* b3, double mass
   inf.initial_res = nb;
   int status = DGNS_OK;
   if (nb > 0.0) {
-    DG_TRY(tensor3_apply(N, 3 * c->m.E, c->r, c->z, MI[0], MI[1], MI[2], c->s, c->d.fp64_mode == 1));
+    DG_TRY(tensor3_apply(N, 3 * c->m.E, c->r, c->z, MI[0], MI[1], MI[2], c->s, c->d.fp64_mode));
     DG_TRY(cg_direction(c->p, c->z, n, c->red, true, c->s));
     DG_TRY(dot(c->r, c->z, n, c->red, S_RZ, c->s));
     int it = 0;
     double res = 1.0;
     status = DGNS_ERR_NOT_CONVERGED;
     while (it < prm.max_iter) {
-      DG_TRY(laplace_apply(false, c->m, 3, c->p, c->Ap, H, EPI_NONE, EpiHost(), c->s, c->d.fp64_mode == 1));
+      DG_TRY(laplace_apply(false, c->m, 3, c->p, c->Ap, H, EPI_NONE, EpiHost(), c->s, c->d.fp64_mode));
       DG_TRY(dot(c->p, c->Ap, n, c->red, S_PAP, c->s));
       DG_TRY(cg_update(X, c->r, c->p, c->Ap, n, c->red, c->s));
       DG_TRY(read_scalars(c));
@@ -1401,7 +1458,7 @@ int dgns_cg_invmass_solve(dgns_ctx* c, double* x3, const double* b3, double mass
         status = DGNS_OK;
         break;
       }
-      DG_TRY(tensor3_apply(N, 3 * c->m.E, c->r, c->z, MI[0], MI[1], MI[2], c->s, c->d.fp64_mode == 1));
+      DG_TRY(tensor3_apply(N, 3 * c->m.E, c->r, c->z, MI[0], MI[1], MI[2], c->s, c->d.fp64_mode));
       DG_TRY(dot(c->r, c->z, n, c->red, S_RZNEW, c->s));
       DG_TRY(cg_direction(c->p, c->z, n, c->red, false, c->s));
     }

@@ -30,6 +30,10 @@ struct Level {
 
 // Records `msg` as the calling thread's last error and returns `code`.
 int set_error(int code, const std::string& msg);
+// Clears the calling thread's last error (entry points start with it).
+void clear_error();
+// Whether the calling thread's last error is empty.
+bool error_empty();
 // SIPG-type tables of space `s` on cells of size h: coef * (Laplace) plus
 // mass_factor * (mass), with tau = pf (k+1)^2 / h_d.
 void build_lap(const Space1D& s, const double h[3], double pf, double coef, double mass_factor,
@@ -41,6 +45,7 @@ struct dgns_ctx {
   using Level = dgns::Level;
   dgns_mesh_desc d{};
   cudaStream_t s = nullptr;
+  int device = -1;  // the CUDA device current at creation, which holds every buffer
   dgns::MeshDims m{};
   double h[3] = {0, 0, 0};
   int k[2] = {0, 0};  // degree of space U, P

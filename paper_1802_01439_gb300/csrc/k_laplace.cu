@@ -20,10 +20,11 @@
 // directly from global memory (they are L2 resident).  Global loads and
 // stores of the own cells are coalesced over the block's contiguous cells.
 //
-// Double-float.  M and the cell part of T_d are centrosymmetric on the LGL
-// nodes, so every line sweep runs in even-odd form (about half the emulated
-// multiply-adds), and the neighbours' face-derivative sums are formed in
-// native FP64 on the loaded doubles (load_nb_summary).
+// Double-float and triple-float.  M and the cell part of T_d are
+// centrosymmetric on the LGL nodes, so every line sweep runs in even-odd form
+// (about half the emulated multiply-adds), and the neighbours'
+// face-derivative sums are formed in native FP64 on the loaded doubles
+// (load_nb_summary).
 #include <algorithm>
 #include <cmath>
 
@@ -636,12 +637,13 @@ __global__ void broadcast_kernel(const T* __restrict__ table, T* __restrict__ ds
 }  // namespace
 
 int laplace_apply(bool fp32, const MeshDims& m, int ncomp, const void* src, void* dst,
-                  const LapHost& tab, int epi, const EpiHost& ea, cudaStream_t s, bool emulated) {
+                  const LapHost& tab, int epi, const EpiHost& ea, cudaStream_t s, int arith) {
 #define DGNS_CASE(NV)                                                                           \
   case NV:                                                                                      \
-    return fp32 ? launch_sipg_epi<F32, NV>(m, ncomp, src, dst, tab, epi, ea, s)                 \
-                : (emulated ? launch_sipg_epi<DF64, NV>(m, ncomp, src, dst, tab, epi, ea, s)    \
-                            : launch_sipg_epi<F64, NV>(m, ncomp, src, dst, tab, epi, ea, s));
+    return fp32                     ? launch_sipg_epi<F32, NV>(m, ncomp, src, dst, tab, epi, ea, s)  \
+           : arith == ARITH_DF64 ? launch_sipg_epi<DF64, NV>(m, ncomp, src, dst, tab, epi, ea, s) \
+           : arith == ARITH_TF64 ? launch_sipg_epi<TF64, NV>(m, ncomp, src, dst, tab, epi, ea, s) \
+                                 : launch_sipg_epi<F64, NV>(m, ncomp, src, dst, tab, epi, ea, s);
   switch (tab.N) {
     DGNS_CASE(2)
     DGNS_CASE(3)

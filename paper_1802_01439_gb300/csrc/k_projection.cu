@@ -2,7 +2,7 @@
 // continuity penalty terms (Sec. 3.2 and the matrix form of the projection
 // step, Sec. 3.3, of arXiv:1802.01439), and the element-wise penalty
 // parameters from the volume-averaged norm of the extrapolated velocity.
-// FP64 or double-float arithmetic, k <= 7.
+// FP64 or double-float arithmetic, k <= 11.
 //
 // Per cell (affine, Gauss rule with k+1 points, exact for both forms):
 //   values  V_a = (S (x) S (x) S) u_a,   reference derivatives
@@ -256,6 +256,196 @@ __global__ void __launch_bounds__(proj_op_cells_per_block<N>() * proj_threads<N>
     }
 }
 
+// The terms of the projection operator one at a time, for its
+// operator-by-operator evaluation (each term its own pass over memory, the
+// form the fused kernel is compared with; the mass term is the mass kernel).
+//
+// Divergence penalty A_D alone: reference derivatives G_a of u_a at the
+// Gauss points, g = tau_D w sum_a G_a / h_a, tested with the derivative of
+// the test function's own component:
+//   forward x: (D u_x, S u_y, S u_z)            R1 -> R2
+//   forward y: (S X0, D X1, S X2)               R2 -> R1
+//   forward z: G = (S Y0, S Y1, D Y2)           R1 -> R2, then g in R2
+//   test x:    ((D/h_x)^T g, S^T g)             R2 -> R1
+//   test y:    (S^T A0, (D/h_y)^T A1, S^T A1)   R1 -> R2
+//   test z:    (S^T B0, S^T B1, (D/h_z)^T B2)   R2 -> R1, stored
+template <int N>
+constexpr int projdiv_per_cell() {
+  return 6 * N * N * N;
+}
+template <class P, int N>
+__global__ void __launch_bounds__(proj_op_cells_per_block<N>() * proj_threads<N>())
+    projdiv_kernel(const double* __restrict__ u3, double* __restrict__ dst3, const double* __restrict__ tau_d,
+                   const __grid_constant__ ProjTabT<typename P::V, N> tb, const MeshDims m) {
+  typedef typename P::V V;
+  typedef typename P::Acc Acc;
+  constexpr int NT = proj_threads<N>(), NN = N * N, N3 = N * N * N, EPB = proj_op_cells_per_block<N>();
+  V* sm = reinterpret_cast<V*>(dyn_smem());
+  const int slot = threadIdx.x / NT;
+  const int t = threadIdx.x - slot * NT;
+  const long long c0 = (long long)blockIdx.x * EPB;
+  const long long rem = m.E - c0;
+  const int nvalid = rem < EPB ? (int)rem : EPB;
+  const bool active = slot < nvalid;
+  V* sS = sm + EPB * projdiv_per_cell<N>();   // tables: S, D, D/h_x, D/h_y, D/h_z
+  V* sD = sS + NN;
+  V* sDh = sD + NN;
+  for (int i = threadIdx.x; i < NN; i += blockDim.x) {
+    sS[i] = tb.S[i];
+    sD[i] = tb.D[i];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) sDh[d * NN + i] = P::mul(tb.D[i], tb.hinv[d]);
+  }
+  V* R1 = sm + slot * projdiv_per_cell<N>();   // 3 N^3
+  V* R2 = R1 + 3 * N3;                         // 3 N^3
+  long long el = 0;
+  if (active) {
+    el = c0 + slot;
+    for (int i = t; i < 3 * N3; i += NT) {
+      const int c = i / N3, r = i - c * N3;
+      R1[i] = P::load(u3 + ((size_t)c * m.E + el) * N3 + r);
+    }
+  }
+  __syncthreads();
+  if (active)   // forward x
+    for (int it = t; it < 3 * NN; it += NT) {
+      const int s = it / NN, l = it - s * NN;
+      psweep<P, N, 0, false, false>(R1 + s * N3, nullptr, R2 + s * N3, l, s == 0 ? sD : sS, nullptr);
+    }
+  group_sync<NT>();
+  if (active)   // forward y
+    for (int it = t; it < 3 * NN; it += NT) {
+      const int s = it / NN, l = it - s * NN;
+      psweep<P, N, 1, false, false>(R2 + s * N3, nullptr, R1 + s * N3, l, s == 1 ? sD : sS, nullptr);
+    }
+  group_sync<NT>();
+  if (active)   // forward z
+    for (int it = t; it < 3 * NN; it += NT) {
+      const int s = it / NN, l = it - s * NN;
+      psweep<P, N, 2, false, false>(R1 + s * N3, nullptr, R2 + s * N3, l, s == 2 ? sD : sS, nullptr);
+    }
+  group_sync<NT>();
+  if (active) {   // quadrature points: g = tau_D w sum_a G_a / h_a
+    const V td = P::load(tau_d + el);
+    for (int i = t; i < N3; i += NT) {
+      Acc dv;
+      P::acc_first(dv, tb.hinv[0], R2[i]);
+      P::acc_fma(dv, tb.hinv[1], R2[N3 + i]);
+      P::acc_fma(dv, tb.hinv[2], R2[2 * N3 + i]);
+      R2[i] = P::mul(P::mul(td, tb.W3[i]), P::acc_get(dv));
+    }
+  }
+  group_sync<NT>();
+  if (active)   // test x
+    for (int it = t; it < 2 * NN; it += NT) {
+      const int s = it / NN, l = it - s * NN;
+      psweep<P, N, 0, true, false>(R2, nullptr, R1 + s * N3, l, s == 0 ? sDh : sS, nullptr);
+    }
+  group_sync<NT>();
+  if (active)   // test y
+    for (int it = t; it < 3 * NN; it += NT) {
+      const int s = it / NN, l = it - s * NN;
+      psweep<P, N, 1, true, false>(R1 + (s == 0 ? 0 : N3), nullptr, R2 + s * N3, l, s == 1 ? sDh + NN : sS,
+                                   nullptr);
+    }
+  group_sync<NT>();
+  if (active)   // test z
+    for (int it = t; it < 3 * NN; it += NT) {
+      const int s = it / NN, l = it - s * NN;
+      psweep<P, N, 2, true, false>(R2 + s * N3, nullptr, R1 + s * N3, l, s == 2 ? sDh + 2 * NN : sS, nullptr);
+    }
+  group_sync<NT>();
+  if (active)
+    for (int i = t; i < 3 * N3; i += NT) {
+      const int c = i / N3, r = i - c * N3;
+      dst3[((size_t)c * m.E + el) * N3 + r] = P::store(R1[i]);
+    }
+}
+
+// Continuity penalty A_C alone: on each of the six faces of the cell the
+// jump J of the normal component between the own and the neighbour's face
+// layer, T = (M (x) I) J, and {{tau_C}} |F| (I (x) M) T on the own face layer
+// of that component; every other entry of the cell is zero.
+template <int N>
+constexpr int projcont_per_cell() {
+  return 3 * N * N * N + 12 * N * N;
+}
+template <class P, int N>
+__global__ void __launch_bounds__(proj_op_cells_per_block<N>() * proj_threads<N>())
+    projcont_kernel(const double* __restrict__ u3, double* __restrict__ dst3, const double* __restrict__ tau_c,
+                    const __grid_constant__ ProjTabT<typename P::V, N> tb, const MeshDims m) {
+  typedef typename P::V V;
+  typedef typename P::Acc Acc;
+  constexpr int NT = proj_threads<N>(), NN = N * N, N3 = N * N * N, EPB = proj_op_cells_per_block<N>();
+  V* sm = reinterpret_cast<V*>(dyn_smem());
+  const int slot = threadIdx.x / NT;
+  const int t = threadIdx.x - slot * NT;
+  const long long c0 = (long long)blockIdx.x * EPB;
+  const long long rem = m.E - c0;
+  const int nvalid = rem < EPB ? (int)rem : EPB;
+  const bool active = slot < nvalid;
+  V* sM = sm + EPB * projcont_per_cell<N>();
+  for (int i = threadIdx.x; i < NN; i += blockDim.x) sM[i] = tb.M[i];
+  V* O = sm + slot * projcont_per_cell<N>();   // 3 N^3
+  V* sJ = O + 3 * N3;                          // 6 N^2
+  V* sT = sJ + 6 * NN;                         // 6 N^2
+  CellXYZ cx{};
+  if (active) {
+    cx = cell_xyz((unsigned)(c0 + slot), m);
+    for (int i = t; i < 3 * N3; i += NT) O[i] = P::zero();
+    for (int it = t; it < 6 * NN; it += NT) {
+      const int f = it / NN, r = it - f * NN;
+      const int a = f >> 1, side = (f & 1) ? -1 : 1;
+      const int sa = a == 0 ? 1 : (a == 1 ? N : NN);
+      const int s1 = a == 0 ? N : 1, s2 = a == 2 ? N : NN;
+      const unsigned nb = a == 0 ? neighbor32<0>(cx, side, m)
+                                 : (a == 1 ? neighbor32<1>(cx, side, m) : neighbor32<2>(cx, side, m));
+      const int off = (r % N) * s1 + (r / N) * s2;
+      const int aown = side > 0 ? N - 1 : 0, anb = side > 0 ? 0 : N - 1;
+      sJ[it] = P::sub(P::load(u3 + ((size_t)a * m.E + cx.el) * N3 + aown * sa + off),
+                      P::load(u3 + ((size_t)a * m.E + nb) * N3 + anb * sa + off));
+    }
+  }
+  group_sync<NT>();
+  if (active)   // T[j1 + N i2] = sum_i1 M[j1][i1] J[i1 + N i2]
+    for (int it = t; it < 6 * NN; it += NT) {
+      const int f = it / NN, r = it - f * NN;
+      const int j1 = r % N, i2 = r / N;
+      const V* J = sJ + f * NN + N * i2;
+      Acc acc;
+      P::acc_first(acc, sM[j1 * N], J[0]);
+#pragma unroll
+      for (int i1 = 1; i1 < N; ++i1) P::acc_fma(acc, sM[j1 * N + i1], J[i1]);
+      sT[it] = P::acc_get(acc);
+    }
+  group_sync<NT>();
+  if (active) {   // O = {{tau_C}} |F| sum_i2 M[j2][i2] T[j1 + N i2] on the face layers
+    const V half_tc = P::half(P::load(tau_c + cx.el));
+    for (int it = t; it < 6 * NN; it += NT) {
+      const int f = it / NN, r = it - f * NN;
+      const int a = f >> 1, side = (f & 1) ? -1 : 1;
+      const int sa = a == 0 ? 1 : (a == 1 ? N : NN);
+      const int s1 = a == 0 ? N : 1, s2 = a == 2 ? N : NN;
+      const unsigned nb = a == 0 ? neighbor32<0>(cx, side, m)
+                                 : (a == 1 ? neighbor32<1>(cx, side, m) : neighbor32<2>(cx, side, m));
+      const V tbar = P::mul(P::add(half_tc, P::half(P::load(tau_c + nb))), tb.area[a]);
+      const int j1 = r % N, j2 = r / N;
+      const V* T = sT + f * NN + j1;
+      Acc acc;
+      P::acc_first(acc, sM[j2 * N], T[0]);
+#pragma unroll
+      for (int i2 = 1; i2 < N; ++i2) P::acc_fma(acc, sM[j2 * N + i2], T[N * i2]);
+      O[a * N3 + (side > 0 ? N - 1 : 0) * sa + j1 * s1 + j2 * s2] = P::mul(tbar, P::acc_get(acc));
+    }
+  }
+  group_sync<NT>();
+  if (active)
+    for (int i = t; i < 3 * N3; i += NT) {
+      const int c = i / N3, r = i - c * N3;
+      dst3[((size_t)c * m.E + cx.el) * N3 + r] = P::store(O[i]);
+    }
+}
+
 // Volume-averaged Euclidean norm of u per cell -> penalty parameters, in the
 // arithmetic policy P; the per-thread partial sums are added in a fixed order
 // in FP64.  W3 carries h_x h_y h_z, divided out at the end.
@@ -353,6 +543,29 @@ int launch_proj(const MeshDims& m, const double* u3, double* dst3, const double*
 }
 
 template <class P, int N>
+int launch_proj_term(int terms, const MeshDims& m, const double* u3, double* dst3, const double* td,
+                     const double* tc, const ProjHost& h, cudaStream_t s) {
+  constexpr int EPB = proj_op_cells_per_block<N>();
+  const bool div = terms == PROJ_DIV;
+  const size_t smem = div ? ((size_t)EPB * projdiv_per_cell<N>() + 5 * N * N) * sizeof(typename P::V)
+                          : ((size_t)EPB * projcont_per_cell<N>() + N * N) * sizeof(typename P::V);
+  if (smem > 232448) return 7;
+  const cudaError_t e = div ? cudaFuncSetAttribute(projdiv_kernel<P, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)smem)
+                            : cudaFuncSetAttribute(projcont_kernel<P, N>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return 2;
+  if (m.E == 0) return 0;
+  const long long blocks = (m.E + EPB - 1) / EPB;
+  if (div)
+    projdiv_kernel<P, N><<<(unsigned)blocks, EPB * proj_threads<N>(), smem, s>>>(u3, dst3, td, make_tabT<P, N>(h), m);
+  else
+    projcont_kernel<P, N><<<(unsigned)blocks, EPB * proj_threads<N>(), smem, s>>>(u3, dst3, tc, make_tabT<P, N>(h),
+                                                                                  m);
+  return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
+
+template <class P, int N>
 int launch_speed(const MeshDims& m, const double* u3, double* td, double* tc, const ProjHost& h, double fd,
                  double fc, cudaStream_t s) {
   constexpr int EPB = proj_cells_per_block<N>();
@@ -370,9 +583,13 @@ int launch_speed(const MeshDims& m, const double* u3, double* td, double* tc, co
 }  // namespace
 
 int projection_apply(const MeshDims& m, const double* u3, double* dst3, const double* tau_d, const double* tau_c,
-                     const ProjHost& h, cudaStream_t s, bool emulated) {
-#define DGNS_PROJ(NV) \
-  case NV:            \
+                     const ProjHost& h, cudaStream_t s, bool emulated, int terms) {
+  if (terms != PROJ_ALL && terms != PROJ_DIV && terms != PROJ_CONT) return 1;
+#define DGNS_PROJ(NV)                                                                                     \
+  case NV:                                                                                                \
+    if (terms != PROJ_ALL)                                                                                \
+      return emulated ? launch_proj_term<DF64, NV>(terms, m, u3, dst3, tau_d, tau_c, h, s)                \
+                      : launch_proj_term<F64, NV>(terms, m, u3, dst3, tau_d, tau_c, h, s);                \
     return emulated ? launch_proj<DF64, NV>(m, u3, dst3, tau_d, tau_c, h, s) : launch_proj<F64, NV>(m, u3, dst3, tau_d, tau_c, h, s);
   switch (h.N) {
     DGNS_PROJ(2)
@@ -382,6 +599,10 @@ int projection_apply(const MeshDims& m, const double* u3, double* dst3, const do
     DGNS_PROJ(6)
     DGNS_PROJ(7)
     DGNS_PROJ(8)
+    DGNS_PROJ(9)
+    DGNS_PROJ(10)
+    DGNS_PROJ(11)
+    DGNS_PROJ(12)
   }
 #undef DGNS_PROJ
   return 7;
@@ -400,6 +621,10 @@ int penalty_parameters(const MeshDims& m, const double* u3, double* tau_d, doubl
     DGNS_SPEED(6)
     DGNS_SPEED(7)
     DGNS_SPEED(8)
+    DGNS_SPEED(9)
+    DGNS_SPEED(10)
+    DGNS_SPEED(11)
+    DGNS_SPEED(12)
   }
 #undef DGNS_SPEED
   return 7;

@@ -166,7 +166,7 @@ int launch_tensor3(long long ncells, const double* src, double* dst, const doubl
       for (int j = 0; j < NF; ++j) tb.O[d][i * NF + j] = A::make(0.5 * (C[i * N + j] - C[i * N + N - 1 - j]));
   }
   if (ncells == 0) return 0;
-  const size_t smem = (size_t)2 * EPB * NN * N * sizeof(double);
+  const size_t smem = (size_t)2 * EPB * NN * N * sizeof(typename A::V);
   static bool attr_done = false;
   if (!attr_done) {
     if (cudaFuncSetAttribute(tensor3_kernel<A, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -376,9 +376,10 @@ int launch_restrict(const MeshDims& mc, const T* fine, T* coarse, const double* 
   }
 
 int tensor3_apply(int N, long long ncells, const double* src, double* dst, const double* Mx,
-                  const double* My, const double* Mz, cudaStream_t s, bool emulated) {
-  DGNS_SWITCH_N(N, return emulated ? launch_tensor3<DF64, NC>(ncells, src, dst, Mx, My, Mz, s)
-                                   : launch_tensor3<F64, NC>(ncells, src, dst, Mx, My, Mz, s))
+                  const double* My, const double* Mz, cudaStream_t s, int arith) {
+  DGNS_SWITCH_N(N, return arith == ARITH_DF64   ? launch_tensor3<DF64, NC>(ncells, src, dst, Mx, My, Mz, s)
+                          : arith == ARITH_TF64 ? launch_tensor3<TF64, NC>(ncells, src, dst, Mx, My, Mz, s)
+                                                : launch_tensor3<F64, NC>(ncells, src, dst, Mx, My, Mz, s))
   return 7;
 }
 

@@ -1,14 +1,15 @@
 // Allocation-free variant of the inverse-mass-preconditioned Helmholtz CG
 // solve (dgns_cg_invmass_solve_noalloc in include/dgns.h).
 //
-// Some callers cannot let a library call cudaMalloc: code running while a
-// stream is being captured into a CUDA graph (allocation is not a capturable
-// operation), applications that hand all device memory to their own pool or
-// allocator up front, and real-time loops that must not pay allocation latency
-// or risk an out-of-memory failure in the middle of a time step.  This entry
-// point serves them: its CG work vectors and reduction scratch live in one
-// file-scope __device__ array of fixed size that is part of the loaded module,
-// so the call itself allocates nothing.
+// Some callers cannot let a library call cudaMalloc: applications that hand
+// all device memory to their own pool or allocator up front (a library
+// allocation outside that pool can fail or fragment it), and real-time loops
+// that must not pay allocation latency or risk an out-of-memory failure in
+// the middle of a time step.  This entry point serves them: its CG work
+// vectors and reduction scratch live in one file-scope __device__ array of
+// fixed size that is part of the loaded module, so the call itself allocates
+// nothing.  Like the allocating solve it reads one block of scalars back to
+// the host and synchronises the context's stream once per CG iteration.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -66,10 +67,13 @@ bool on_device(const void* p) {
     if (e_ != cudaSuccess) return set_error(DGNS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
+// A failed step keeps the message its callee recorded; where there is none,
+// the step's name (and, for CUDA errors, the runtime's message) is recorded.
 #define NA_TRY(call)                                                                         \
   do {                                                                                       \
     int rc_ = (call);                                                                        \
     if (rc_ != 0) {                                                                          \
+      if (!error_empty()) return rc_;                                                        \
       if (rc_ == DGNS_ERR_CUDA)                                                              \
         return set_error(rc_, std::string(#call) + ": " + cudaGetErrorString(cudaGetLastError())); \
       return set_error(rc_, #call);                                                          \
@@ -80,7 +84,18 @@ bool on_device(const void* p) {
 
 extern "C" int dgns_cg_invmass_solve_noalloc(dgns_ctx* c, double* x3, const double* b3, double mass_factor,
                                              const dgns_solve_params* params, dgns_solve_info* info) {
+  clear_error();
   if (!c || !x3 || !b3) return set_error(DGNS_ERR_INVALID_ARG, "null argument");
+  {
+    // the scratch address is looked up on the current device, so that must
+    // be the device that holds the context (its tables, vectors and stream)
+    int dev = -1;
+    NA_CUDA(cudaGetDevice(&dev));
+    if (dev != c->device)
+      return set_error(DGNS_ERR_INVALID_ARG, "dgns_cg_invmass_solve_noalloc: the context's device (" +
+                                                 std::to_string(c->device) + ") must be current (is " +
+                                                 std::to_string(dev) + ")");
+  }
   dgns_solve_params prm;
   if (params) prm = *params;
   else dgns_default_solve_params(&prm);
@@ -120,7 +135,7 @@ extern "C" int dgns_cg_invmass_solve_noalloc(dgns_ctx* c, double* x3, const doub
   // unless it holds the initial guess.
   NA_CUDA(cudaMemcpyAsync(r, b3, bytes, cudaMemcpyDeviceToDevice, c->s));
   if (prm.use_initial_guess) {
-    NA_TRY(laplace_apply(false, c->m, 3, x3, Ap, H, EPI_NONE, EpiHost(), c->s, c->d.fp64_mode == 1));
+    NA_TRY(laplace_apply(false, c->m, 3, x3, Ap, H, EPI_NONE, EpiHost(), c->s, c->d.fp64_mode));
     NA_TRY(axpby(r, Ap, n, -1.0, 1.0, c->s));
     NA_TRY(dot(r, r, n, red, S_T0, c->s));
   } else {
@@ -133,14 +148,14 @@ extern "C" int dgns_cg_invmass_solve_noalloc(dgns_ctx* c, double* x3, const doub
   inf.initial_res = nb;
   int status = DGNS_OK;
   if (nb > 0.0) {
-    NA_TRY(tensor3_apply(N, 3 * c->m.E, r, z, MI[0], MI[1], MI[2], c->s, c->d.fp64_mode == 1));
+    NA_TRY(tensor3_apply(N, 3 * c->m.E, r, z, MI[0], MI[1], MI[2], c->s, c->d.fp64_mode));
     NA_TRY(cg_direction(p, z, n, red, true, c->s));
     NA_TRY(dot(r, z, n, red, S_RZ, c->s));
     int it = 0;
     double res = 1.0;
     status = DGNS_ERR_NOT_CONVERGED;
     while (it < prm.max_iter) {
-      NA_TRY(laplace_apply(false, c->m, 3, p, Ap, H, EPI_NONE, EpiHost(), c->s, c->d.fp64_mode == 1));
+      NA_TRY(laplace_apply(false, c->m, 3, p, Ap, H, EPI_NONE, EpiHost(), c->s, c->d.fp64_mode));
       NA_TRY(dot(p, Ap, n, red, S_PAP, c->s));
       NA_TRY(cg_update(x3, r, p, Ap, n, red, c->s));
       NA_TRY(read_scal());
@@ -155,7 +170,7 @@ extern "C" int dgns_cg_invmass_solve_noalloc(dgns_ctx* c, double* x3, const doub
         status = DGNS_OK;
         break;
       }
-      NA_TRY(tensor3_apply(N, 3 * c->m.E, r, z, MI[0], MI[1], MI[2], c->s, c->d.fp64_mode == 1));
+      NA_TRY(tensor3_apply(N, 3 * c->m.E, r, z, MI[0], MI[1], MI[2], c->s, c->d.fp64_mode));
       NA_TRY(dot(r, z, n, red, S_RZNEW, c->s));
       NA_TRY(cg_direction(p, z, n, red, false, c->s));
     }

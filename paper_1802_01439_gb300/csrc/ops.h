@@ -32,21 +32,27 @@ struct EpiHost {
   double c1 = 0.0, c2 = 0.0;
 };
 
+// Arithmetic of the FP64 operator kernels (the context's fp64_mode).
+enum Arith {
+  ARITH_F64 = 0,    // native FP64
+  ARITH_DF64 = 1,   // double-float on the FP32 pipe (48-bit significand)
+  ARITH_TF64 = 2,   // triple-float on the FP32 pipe (SIPG and mass kernels; others native FP64)
+};
+
 // dst = L src on ncomp scalar fields (cells of component c follow those of
 // component c-1); `fp32` selects float data, else double.
-// emulated (double data only): double-float arithmetic on the FP32 pipe,
-// EPI_NONE only.
+// arith (double data only): an Arith; the emulated ones take EPI_NONE only.
 int laplace_apply(bool fp32, const MeshDims& m, int ncomp, const void* src, void* dst,
-                  const LapHost& tab, int epi, const EpiHost& ea, cudaStream_t s, bool emulated = false);
+                  const LapHost& tab, int epi, const EpiHost& ea, cudaStream_t s, int arith = ARITH_F64);
 
 // dst[cell][i] = table[i] for every cell (broadcast of a per-cell pattern).
 int broadcast_cells(bool fp32, long long ncells, int nper, const void* table, void* dst,
                     cudaStream_t s);
 
 // dst = (Mz (x) My (x) Mx) src per cell, square N x N matrices (mass,
-// inverse mass), double data; emulated: double-float arithmetic.
+// inverse mass), double data; arith: an Arith.
 int tensor3_apply(int N, long long ncells, const double* src, double* dst, const double* Mx,
-                  const double* My, const double* Mz, cudaStream_t s, bool emulated = false);
+                  const double* My, const double* Mz, cudaStream_t s, int arith = ARITH_F64);
 
 // Multigrid transfers between a coarse mesh mc and the fine mesh 2*mc.
 // prolongate: fine (+)= P coarse; restrict: coarse = P^T fine.
@@ -91,16 +97,21 @@ int convective_vjp(const MeshDims& m, const double* u3, const double* w3, double
                    const ConvHost& t, cudaStream_t s, bool emulated = false);
 
 // Projection operator M + A_D + A_C and the penalty parameters
-// (k_projection.cu); N = k_u + 1 <= 8.
+// (k_projection.cu); N = k_u + 1 <= 12.
 struct ProjHost {
   int N = 0;
   double S[MAXN * MAXN], D[MAXN * MAXN], M[MAXN * MAXN];
   double w[MAXN];
   double h[3];
 };
-// emulated: double-float arithmetic (else native FP64)
+// Terms of the projection operator: the mass term (the mass kernel), the
+// divergence penalty A_D and the continuity penalty A_C; PROJ_ALL is the
+// fused operator M + A_D + A_C.
+enum ProjTerms { PROJ_MASS = 1, PROJ_DIV = 2, PROJ_CONT = 4, PROJ_ALL = 7 };
+// emulated: double-float arithmetic (else native FP64); terms: PROJ_ALL
+// (one fused kernel), PROJ_DIV or PROJ_CONT (that term alone)
 int projection_apply(const MeshDims& m, const double* u3, double* dst3, const double* tau_d, const double* tau_c,
-                     const ProjHost& h, cudaStream_t s, bool emulated = false);
+                     const ProjHost& h, cudaStream_t s, bool emulated = false, int terms = PROJ_ALL);
 // tau_d = fd * avg|u|, tau_c = fc * avg|u| per cell
 int penalty_parameters(const MeshDims& m, const double* u3, double* tau_d, double* tau_c, const ProjHost& h,
                        double fd, double fc, cudaStream_t s, bool emulated = false);

@@ -52,6 +52,46 @@ def test_level_operators_fp32(n, kp):
         assert rel_err(host(yc), T.restrict(xf0.astype(np.float64).reshape(T.fs.mesh.E, -1))) <= 1e-5
 
 
+@pytest.mark.parametrize("n,kp", [(8, 3), (6, 2), (4, 5)])
+def test_chebyshev_step_fp32(n, kp):
+    """The fused FP32 smoother step (the level operator with its Chebyshev
+    epilogue, as the V-cycle runs it) against the oracle's Chebyshev
+    iteration (Saad, Alg. 12.1) on the finest level, same interval:
+    one step from x0 at 1e-5, and five steps with the three-term
+    coefficients at 1e-4."""
+    ctx = context(n, kp + 1, kp)
+    lvl = ctx.mg_info()["levels"] - 1
+    lam = ctx.mg_info()["lambda_max"][lvl]
+    s = dg.Space(dg.Mesh(n), kp)
+    L = dg.Laplace(s)
+    inv_diag = 1.0 / L.diagonal()
+    A = L.apply
+    x0 = rand32(s.size, 31)
+    b = rand32(s.size, 32)
+    X0, B = x0.astype(np.float64).reshape(s.mesh.E, -1), b.astype(np.float64).reshape(s.mesh.E, -1)
+    rng_, lmin = 20.0, lam / 20.0
+    theta, delta = 0.5 * (lam + lmin), 0.5 * (lam - lmin)
+    sigma = theta / delta
+    f32 = dict(dtype=torch.float32, device="cuda")
+    xs = [dev(x0, torch.float32)]
+    bd = dev(b, torch.float32)
+    y = torch.empty(s.size, **f32)
+    ctx.mg_chebyshev_step_f32(y, xs[0], None, bd, 0.0, 1.0 / theta, lvl)
+    ref1 = mg.chebyshev(A, inv_diag, B, X0, lam, rng_, 1)
+    assert rel_err(host(y), ref1) <= 1e-5
+    xs.append(y)
+    rho = 1.0 / sigma
+    for k in range(1, 5):
+        rnew = 1.0 / (2.0 * sigma - rho)
+        c1, c2 = rnew * rho, 2.0 * rnew / delta
+        rho = rnew
+        nxt = torch.empty(s.size, **f32)
+        ctx.mg_chebyshev_step_f32(nxt, xs[-1], xs[-2], bd, c1, c2, lvl)
+        xs.append(nxt)
+    ref5 = mg.chebyshev(A, inv_diag, B, X0, lam, rng_, 5)
+    assert rel_err(host(xs[-1]), ref5) <= 1e-4
+
+
 def test_lambda_estimates_bound_the_spectrum():
     n, kp = 4, 2
     ctx = context(n, kp + 1, kp)

@@ -36,10 +36,11 @@ def _mesh(n, kw):
     return dg.Mesh(n, kw.get("lo", (-np.pi,) * 3), kw.get("hi", (np.pi,) * 3))
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("n,k,kw", LAP_CASES)
 def test_laplace(n, k, kw, mode):
-    """mode 0: native FP64; mode 1: double-float arithmetic (FP32 pipe)."""
+    """mode 0: native FP64; mode 1: double-float; mode 2: triple-float
+    (FP32 pipe)."""
     ctx = context(n, k, k, mg_precision=0, fp64_mode=mode, **kw)
     s = dg.Space(_mesh(n, kw), k)
     x = random_field(s, 1, 0)
@@ -63,7 +64,7 @@ def test_laplace_pressure_space():
     assert rel_err(host(y), dg.Laplace(s).apply(x)) <= TOL
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("n,k,kw", LAP_CASES[:6])
 def test_mass_and_inverse(n, k, kw, mode):
     ctx = context(n, k, k, mg_precision=0, fp64_mode=mode, **kw)
@@ -78,7 +79,7 @@ def test_mass_and_inverse(n, k, kw, mode):
         assert rel_err(host(y), M.apply_inverse(x)) <= TOL
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("n,k", [((3, 2, 4), 3), ((2, 2, 3), 5), ((1, 2, 1), 2)])
 def test_viscous_and_helmholtz(n, k, mode):
     nu = 1.0 / 1600
@@ -93,7 +94,7 @@ def test_viscous_and_helmholtz(n, k, mode):
     assert rel_err(host(y), dg.Helmholtz(s, nu, mf).apply(u)) <= TOL
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("n,ku", [((3, 2, 4), 3), ((2, 2, 2), 5), ((1, 2, 3), 2), ((2, 1, 1), 11),
                                   ((4, 4, 4), 4)])
 def test_divergence_gradient(n, ku, mode):
@@ -110,12 +111,14 @@ def test_divergence_gradient(n, ku, mode):
     assert rel_err(host(g), dg.Gradient(su, sp).apply(p)) <= TOL
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("n,k,field", [((4, 4, 4), 3, "tgv"), ((3, 2, 5), 2, "rand"),
                                        ((2, 2, 2), 5, "rand"), ((1, 1, 2), 1, "rand"),
                                        ((2, 1, 1), 11, "tgv"), ((2, 3, 2), 7, "tgv"),
                                        ((5, 3, 2), 4, "tgv"), ((2, 2, 1), 9, "rand"),
-                                       ((3, 3, 3), 3, "rand"), ((3, 1, 1), 1, "tgv")])
+                                       ((3, 3, 3), 3, "rand"), ((3, 1, 1), 1, "tgv"),
+                                       ((2, 1, 2), 6, "tgv"), ((1, 2, 2), 8, "rand"),
+                                       ((2, 2, 1), 10, "tgv")])
 def test_convective(n, k, field, mode):
     """mode 0: native FP64; mode 1: double-float arithmetic (FP32 pipe).  Odd
     cell counts (27, 3) leave the last two-cell group of the k = 1 and k = 3
@@ -129,7 +132,7 @@ def test_convective(n, k, field, mode):
     assert rel_err(host(y), ref) <= TOL
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("n,k", [((3, 2, 2), 3), ((2, 1, 3), 2), ((1, 2, 1), 7), ((3, 1, 3), 3), ((3, 3, 1), 1)])
 def test_convective_two_phases(n, k, mode):
     """Face kernel + cell kernel through the two-phase entry points give the
@@ -148,7 +151,7 @@ def test_convective_two_phases(n, k, mode):
     assert rel_err(host(y1), dg.Convective(s).apply(host(u).reshape(3, s.mesh.E, -1))) <= TOL
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_convective_face_integrals_of_a_constant_field(mode):
     """For a constant velocity the LLF jump term vanishes and the face
     integral is u_c u_d h_t1 h_t2 omega_j1 omega_j2 (omega: integrals of the
@@ -194,7 +197,7 @@ def test_alias_rejected():
         ctx.vmult_laplace(x, x, space=0)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("n,k", [((8, 8, 8), 3), ((6, 4, 4), 5)])
 def test_laplace_smooth_field(n, k, mode):
     """Smooth input: the stiffness sweeps cancel (L u ~ h^2 |terms|), the
@@ -254,3 +257,33 @@ def test_double_float_stores_across_magnitudes(scale):
     assert rel_err(host(y), dg.Mass(s).apply(x)) <= TOL
     ctx.apply_inverse_mass(y, dev(x.ravel()), 3, 0)
     assert rel_err(host(y), dg.Mass(s).apply_inverse(x)) <= TOL
+
+
+# ------------------------------------------ triple-float: FP64-wide accuracy
+@pytest.mark.parametrize("n,k,field", [((4, 4, 4), 3, "rand"), ((3, 2, 2), 5, "rand"),
+                                       ((2, 2, 1), 7, "rand"), ((8, 8, 8), 3, "smooth"),
+                                       ((4, 4, 2), 5, "smooth")])
+def test_triple_float_at_least_as_accurate_as_fp64(n, k, field):
+    """Against the oracle evaluated in extended precision (np.longdouble, its
+    own tables included), the triple-float SIPG operator (mode 2) is at least
+    as accurate as native FP64 (mode 0): both use the same FP64-rounded 1D
+    tables, so the difference is the arithmetic's own rounding.  Smooth fields
+    (sin x cos y sin z) make the stiffness sweeps cancel.  Degrees up to 7: the
+    extended-precision element matrices cost (k+1)^9 software-float
+    operations on hosts where long double is binary128."""
+    s = dg.Space(dg.Mesh(n), k)
+    se = dg.Space(dg.Mesh(n, dtype=np.longdouble), k)
+    if field == "rand":
+        x = random_field(s, 1, 9)
+    else:
+        x = s.interpolate(lambda a, b, c: np.sin(a) * np.cos(b) * np.sin(c))
+    ref = dg.Laplace(se).apply(x).astype(np.float64)
+    errs = {}
+    for mode in (0, 2):
+        ctx = context(n, k, k, mg_precision=0, fp64_mode=mode)
+        y = torch.empty(s.size, dtype=torch.float64, device="cuda")
+        ctx.vmult_laplace(y, dev(x), space=0)
+        errs[mode] = rel_err(host(y), ref)
+    print("laplace %s k=%d: native %.2e, triple-float %.2e vs extended" % (field, k, errs[0], errs[2]))
+    assert errs[2] <= TOL
+    assert errs[2] <= 1.5 * errs[0] + 1e-16
