@@ -99,6 +99,25 @@ def test_operator_gradients_gradcheck():
     assert torch.autograd.gradcheck(lambda x: ns._Poisson.apply(ctx, x - x.mean(), OPTS, None), (pm,), **kw)
 
 
+@pytest.mark.parametrize("n,k,steps", [((2, 2, 1), 2, 3), ((3, 1, 2), 3, 2)])
+def test_gradient_matches_oracle_adjoint(n, k, steps):
+    """The GPU's checkpointed reverse mode (hand-written VJP kernels, adjoint
+    solves) against the oracle's adjoint of the same BDF2 steps (dense
+    transposes of every linear map, Convective.vjp): the whole gradient of
+    eps(u^n) w.r.t. u^0, elementwise.  The GPU solves with CG to 1e-13, the
+    oracle exactly."""
+    nu, dt = 1.0 / 1600, 1e-3
+    ctx, ds = _stepper(n, k, nu, dt)
+    m = dg.Mesh(n)
+    s = dg.Space(m, k)
+    u0 = tgv_field(s, 1e-2, 0)
+    x = dev(u0.ravel()).requires_grad_()
+    ds.dissipation(ds.run(x, steps)).backward()
+    ods = timestep.DualSplitting(m, k, nu, dt)
+    ref = timestep.Adjoint(ods).gradient(u0, steps, lambda u: dg.dissipation_gradient(s, u, nu))
+    assert rel_err(host(x.grad), ref) <= 1e-9
+
+
 def _fd_check(n, k, nu, dt, steps, ndir, delta, tol, noise=1e-3, offset=0.0):
     """Central differences of J = eps(u^steps) along seeded directions against
     <grad J, v> from autograd.  J is only piecewise smooth: the LLF flux has

@@ -13,6 +13,7 @@
     the rate h^(k+1) and its kinetic energy decays like exp(-4 nu t).
 """
 import numpy as np
+import pytest
 
 from oracle import dg, timestep
 
@@ -117,3 +118,30 @@ def test_second_order_in_time_without_viscosity():
     r = [timestep.DualSplitting(m, 3, 0.0, T / n).run(u0, n) for n in (10, 20, 40)]
     ratio = np.max(np.abs(r[0] - r[1])) / np.max(np.abs(r[1] - r[2]))
     assert ratio > 3.5
+
+
+@pytest.mark.parametrize("n,k,steps", [((2, 2, 1), 2, 3), ((3, 1, 2), 3, 2)])
+def test_adjoint_matches_central_differences(n, k, steps):
+    """The oracle's reverse-mode gradient of J = eps(u^n) (the dissipation
+    rate, Sec. 4.2) against central differences of its own forward run along
+    seeded directions: <grad J, v> = (J(u0 + d v) - J(u0 - d v)) / 2d up to
+    O(d^2) and the LLF kinks (a field with 1e-2 noise keeps them away)."""
+    from paper_1802_01439_gb300 import inputs
+    from oracle import rules
+    nu, dt = 1.0 / 1600, 1e-3
+    m = dg.Mesh(n)
+    ds = timestep.DualSplitting(m, k, nu, dt)
+    u0 = inputs.taylor_green(m.n, m.lo, m.hi, rules.lgl_nodes(k), noise=1e-2, seed=0)
+    J = lambda u: dg.dissipation_rate(ds.su, u, nu)
+    g = timestep.Adjoint(ds).gradient(u0, steps, lambda u: dg.dissipation_gradient(ds.su, u, nu))
+    for seed in (1, 2, 3):
+        v = np.random.default_rng(seed).uniform(-1, 1, u0.shape)
+        d = 1e-6
+        fd = (J(ds.run(u0 + d * v, steps)) - J(ds.run(u0 - d * v, steps))) / (2 * d)
+        assert abs(fd - np.sum(g * v)) <= 1e-6 * abs(fd)
+
+
+def test_adjoint_rejects_penalty_projection():
+    ds = timestep.DualSplitting(dg.Mesh((2, 2, 1)), 2, 1.0 / 1600, 1e-3, projection="penalty")
+    with pytest.raises(ValueError):
+        timestep.Adjoint(ds)
