@@ -991,7 +991,7 @@ int dgns_vmult_convective(dgns_ctx* c, double* dst3, const double* u3) {
   DG_TRY(st.in(u3, bu, &s));
   DG_TRY(st.out(dst3, bu, &d));
   DG_TRY(conv_status(convective_launch(3, c->m, (const double*)s, c->conv_face, (double*)d, c->conv,
-                                       c->d.fp64_mode == 1, c->s)));
+                                       c->d.fp64_mode, c->s)));
   return st.finish();
 }
 
@@ -1014,7 +1014,7 @@ int dgns_convective_faces(dgns_ctx* c, double* rface, const double* u3) {
   DG_TRY(st.in(u3, bu, &s));
   DG_TRY(st.out(rface, bf, &f));
   DG_TRY(conv_status(convective_launch(1, c->m, (const double*)s, (double*)f, nullptr, c->conv,
-                                       c->d.fp64_mode == 1, c->s)));
+                                       c->d.fp64_mode, c->s)));
   return st.finish();
 }
 
@@ -1034,7 +1034,7 @@ int dgns_convective_cells(dgns_ctx* c, double* dst3, const double* u3, const dou
   DG_TRY(st.in(rface, bf, &f));
   DG_TRY(st.out(dst3, bu, &d));
   DG_TRY(conv_status(convective_launch(2, c->m, (const double*)s, (double*)f, (double*)d, c->conv,
-                                       c->d.fp64_mode == 1, c->s)));
+                                       c->d.fp64_mode, c->s)));
   return st.finish();
 }
 

@@ -89,9 +89,13 @@ struct ConvHost {
 };
 // part: bit 0 the face kernel (u3 -> rface: the face integrals, 9 E N^2
 // doubles, see conv_face_kernel), bit 1 the cell kernel (u3, rface -> dst3).
-// emulated: double-float arithmetic on the FP32 pipe (else native FP64).
+// arith: an Arith (triple-float for the 3/2 rule up to N = 11, native FP64
+// beyond).
 int convective_launch(int part, const MeshDims& m, const double* u3, double* rface, double* dst3,
-                      const ConvHost& t, bool emulated, cudaStream_t s);
+                      const ConvHost& t, int arith, cudaStream_t s);
+// The triple-float kernels (k_convective_tf64.cu); 7 where not instantiated.
+int convective_launch_tf64(int part, const MeshDims& m, const double* u3, double* rface, double* dst3,
+                           const ConvHost& t, cudaStream_t s);
 // emulated: double-float arithmetic (else native FP64)
 int convective_vjp(const MeshDims& m, const double* u3, const double* w3, double* dst3,
                    const ConvHost& t, cudaStream_t s, bool emulated = false);

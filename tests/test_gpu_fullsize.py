@@ -1,6 +1,7 @@
 """Parity at the full workload sizes, in the launch configuration bench.py
-times, in both arithmetic modes (native FP64 `fp64_mode=0`, the headline,
-and double-float `fp64_mode=1`): outputs of sampled cells against the oracle.
+times, in every arithmetic mode (native FP64 `fp64_mode=0`, double-float
+`fp64_mode=1`, triple-float `fp64_mode=2`): outputs of sampled cells against
+the oracle.
 
 Every operator couples a cell only to its six face neighbours, and on the
 uniform periodic mesh it is translation invariant, so the output of cell e of
@@ -14,9 +15,10 @@ The convective term of a smooth field is ill-conditioned: its weak-form cell
 and face sums nearly cancel, more so at high degree (the summed terms exceed
 the result by ~10^3 at k = 7 and ~10^4 at k = 11).  It is refereed by the
 oracle evaluated in extended precision (np.longdouble, tables included) on
-sampled cells.  Native FP64 must be within 1e-12 of max |C| of that referee
-at every k (it is within 1e-13: the sum-factorised evaluation cancels less
-than the oracle's dense one, whose FP64 error reaches 4e-12 at k = 11).
+sampled cells.  Native FP64 and triple-float must be within 1e-12 of max |C|
+of that referee at every k (native FP64 is within 1e-13: the sum-factorised
+evaluation cancels less than the oracle's dense one, whose FP64 error
+reaches 4e-12 at k = 11).
 Double-float must meet the same bar or, where the FP64 oracle itself does
 not, stay within 4 times the FP64 oracle's own error.  The bar relative to
 the magnitude of the summed terms (`Convective.magnitude`), the scale of the
@@ -78,7 +80,7 @@ def _vec(t, ncomp, E):
     return host(t).reshape(ncomp, E, -1)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_operator_set_32c_k3(mode):
     """The operator-set step (32^3 cells, k_u = 3, k_p = 2, Taylor-Green + 1e-3 noise):
     c = C(u) (face kernel + cell kernel), uh = M^-1 c, d = D uh, l = L d,
@@ -139,7 +141,7 @@ def _referee(n, k, U, e):
     return _REFEREE[key]
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("k", [2, 3, 4, 5, 7, 9, 11])
 def test_degree_sweep_sizes(k, mode):
     """The degree-sweep workload (~16.8M scalar DoFs per component): Laplace on
@@ -178,10 +180,10 @@ def test_degree_sweep_sizes(k, mode):
     ratio = float(np.max(np.stack([scale[cells.index(e)] for e in rcells], 1)) / np.max(np.abs(np.stack(ext, 1))))
     print("convective k=%d mode=%d: plain error vs extended %.2e (FP64 oracle %.2e), magnitude / |C| %.0f"
           % (k, mode, err_gpu, err_o64, ratio))
-    if mode == 0:
-        # native FP64: plain 1e-12 against the referee at every k (measured
-        # 5e-15 at k = 2 to 8e-14 at k = 11; the FP64 oracle's own dense
-        # evaluation is off by up to 4e-12 at k = 11)
+    if mode in (0, 2):
+        # native FP64 and triple-float: plain 1e-12 against the referee at
+        # every k (native measured 5e-15 at k = 2 to 8e-14 at k = 11; the FP64
+        # oracle's own dense evaluation is off by up to 4e-12 at k = 11)
         assert err_gpu <= TOL
     else:
         # double-float (48-bit): its own rounding reaches 3.7e-12 at k = 11;
