@@ -47,16 +47,22 @@ METRIC = "DG operator eval DoFs/s vs degree k (FP64); Poisson solve s at rel. re
 WORKLOAD = ("degree sweep k=2,3,4,5,7,9,11 at ~16.8M scalar DoFs each (85^3, 64^3, 51^3, 43^3, 32^3, "
             "26^3, 21^3 hex cells, periodic [-pi,pi]^3): SIPG Laplace vmult on uniform[-1,1] + convective "
             "vmult (floor(3(k+1)/2)-point rule, LLF flux) on Taylor-Green + 1e-3 noise")
-MODES = {0: "f64", 1: "df64"}
+MODES = {0: "f64", 1: "df64", 2: "f64_wide"}
 MODE_DTYPE = {0: "f64",
-              1: "f64 via double-float (2 x f32, 48-bit significand; parity <= 1e-12 with the FP64 oracle)"}
+              1: "f64 via double-float (2 x f32, 48-bit significand; parity <= 1e-12 with the FP64 oracle)",
+              2: "f64-wide mix: triple-float (3 x f32, up to 72-bit significand) in the SIPG, mass and low-degree "
+                 "convective face kernels, native-FP64 and triple-float blocks side by side in the k <= 3 "
+                 "convective cell kernel, native FP64 elsewhere"}
 FP64_PEAK_TFLOPS = 1.258  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25)
 FP32_PEAK_TFLOPS = 80.6   # 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz
 # FP32 flops the double-float emulation spends per FP64 operation: an
 # emulated multiply-add is an exact product (FMUL + FFMA) with two cross
 # terms (2 FFMA), a two-sum (6 FADD) and two additions: 15 flops; an
 # emulated addition is a two-sum and two additions: 8 flops.
-EMU_FP32_FLOPS = {1: (15, 8)}
+EMU_FP32_FLOPS = {1: (15, 8), 2: (51, 21)}
+# (triple-float: an emulated multiply-add is three exact products (FMUL +
+# FFMA each), four two-sums (24 FADD), six additions and three FFMA: 51
+# flops; an addition is three two-sums and three additions: 21 flops)
 # DRAM bytes (read + write) of one launch of a kernel, from one ncu capture
 # of the same launch configuration (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by (kernel, fp64 mode, k); absent where no
@@ -131,7 +137,8 @@ def flops(ops):
 
 
 def fp32_flops(ops, mode):
-    """FP32-pipe flops of the emulated FP64 operations (double-float)."""
+    """FP32-pipe flops of the emulated FP64 operations (double-float or
+    triple-float)."""
     cf, ca = EMU_FP32_FLOPS[mode]
     return cf * ops[0] + ca * ops[1]
 
@@ -319,7 +326,9 @@ def sweep_table(sw, per_k, mode):
                      "laplace_hbm_frac": round(16 * lap / 1e9 / peak, 4),
                      "convective_hbm_frac": round(16 * conv / 1e9 / peak, 4),
                      "laplace_alu_frac": round(alu_frac(lap_ops, tl * 1e-3, mode), 4),
-                     "convective_alu_frac": round(alu_frac(conv_ops, (tf + tc) * 1e-3, mode), 4)})
+                     # the FP64-wide mix runs the convective kernels on both pipes
+                     "convective_alu_frac": (None if mode == 2 else
+                                             round(alu_frac(conv_ops, (tf + tc) * 1e-3, mode), 4))})
     return rows
 
 
@@ -338,7 +347,7 @@ def dominant_roofline(sw, per_k, mode):
             if best is None or ms > best[1]:
                 best = (name, ms, ops, k, N, Q)
     name, ms, ops, k, N, Q = best
-    pol = {0: "F64", 1: "DF64"}[mode]
+    pol = {0: "F64", 1: "DF64", 2: "TF64"}[mode]
     kname = "%s<%s,%d>" % (name, pol, N) if name == "sipg_kernel" else "%s<%s,%d,%d>" % (name, pol, N, Q)
     if mode == 0:
         fl, peak = flops(ops), FP64_PEAK_TFLOPS
@@ -415,16 +424,20 @@ def gpu_arm(args, rank, world):
         "timed_block_wall_s": round(wall, 4), "clocks": clk,
     }
     if not args.no_extras:
-        other = 1 - mode
-        sw = Sweep(other, dev)
-        oms, oper_k, _, _ = run_sweep(sw, max(3, args.steps // 2), 2, flush, stream, world)
-        line["sweep_" + MODES[other]] = {
-            "dtype": MODE_DTYPE[other], "ms_per_step": round(oms, 4),
-            "value": round(sum(4 * n ** 3 * (k + 1) ** 3 for k, n in SWEEP) / (oms * 1e-3), 1),
-            "per_k": sweep_table(sw, oper_k, other), "roofline": dominant_roofline(sw, oper_k, other)}
-        sw.close()
-        del sw
+        for other in sorted(MODES):
+            if other == mode:
+                continue
+            sw = Sweep(other, dev)
+            oms, oper_k, _, _ = run_sweep(sw, max(3, args.steps // 2), 2, flush, stream, world)
+            line["sweep_" + MODES[other]] = {
+                "dtype": MODE_DTYPE[other], "ms_per_step": round(oms, 4),
+                "value": round(sum(4 * n ** 3 * (k + 1) ** 3 for k, n in SWEEP) / (oms * 1e-3), 1),
+                "per_k": sweep_table(sw, oper_k, other),
+                "roofline": dominant_roofline(sw, oper_k, other) if other != 2 else None}
+            sw.close()
+            del sw
         line["operator_set_32c_k3"] = {m: operator_set_step(dev, flush, m, 20) for m in (0, 1)}
+        line["fused_vs_split"] = fused_vs_split()
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if not args.no_solve and rank == 0:
@@ -476,6 +489,26 @@ def operator_set_step(dev, flush, mode, steps):
             "ms_per_step": round(t, 4), "steps": steps, "step_hbm": step_hbm(nu_, np_, t),
             "workload": "full operator set (C, M^-1, D, L, G, mM+V) on 32^3 cells, k_u=3, k_p=2, q_conv=6, "
                         "Taylor-Green + 1e-3 noise; L2 flushed before every step"}
+
+
+def fused_vs_split(reps=5):
+    """The paper's comparison of its optimised operators with the standard,
+    operator-by-operator evaluation (Sec. 4.4), in native FP64 for every k of
+    the sweep: the Helmholtz operator (one SIPG kernel with the mass term
+    folded in, against the mass kernel, the viscous kernel and a vector
+    update) and the projection operator (one kernel for M + A_D + A_C,
+    against M, A_D and A_C in three passes and two vector updates).  Mean
+    event times with L2 flushed; ratio = split / fused."""
+    from paper_1802_01439_gb300.opbench import run
+    out = {"workload": "3 components, ~16.8M scalar DoFs each, native FP64, L2 flushed, mean of %d" % reps}
+    for k, n in SWEEP:
+        row = {}
+        for op in ("helmholtz", "helmholtz_split", "projection", "projection_split"):
+            row[op + "_ms"] = run(op, k, n, reps, 2, fp64_mode=0)["ms_mean"]
+        row["helmholtz_ratio"] = round(row["helmholtz_split_ms"] / row["helmholtz_ms"], 3)
+        row["projection_ratio"] = round(row["projection_split_ms"] / row["projection_ms"], 3)
+        out["k%d" % k] = row
+    return out
 
 
 def bdf2_timing(steps=20):
@@ -538,6 +571,7 @@ def tgv_time_loop(steps=100):
 # the Poisson arms: (key, V-cycle precision, arithmetic of the CG matvec, what)
 POISSON_ARMS = [("mixed", 32, 0, "native FP64 CG (matvec, residual, dots, updates) + FP32 V-cycle"),
                 ("fp64", 64, 0, "native FP64 CG + FP64 V-cycle (all FP64)"),
+                ("mixed_tf64_matvec", 32, 2, "FP64 CG with a triple-float (FP64-wide) matvec + FP32 V-cycle"),
                 ("mixed_df64_matvec", 32, 1, "FP64 CG with a double-float matvec (48-bit) + FP32 V-cycle")]
 
 
@@ -578,6 +612,7 @@ def poisson_solve():
         ctx.close()
         del x
     out["speedup_mixed_vs_fp64"] = round(out["fp64"]["seconds"] / out["mixed"]["seconds"], 3)
+    out["speedup_mixed_tf64_matvec_vs_fp64"] = round(out["fp64"]["seconds"] / out["mixed_tf64_matvec"]["seconds"], 3)
     out["speedup_mixed_df64_matvec_vs_fp64"] = round(out["fp64"]["seconds"] / out["mixed_df64_matvec"]["seconds"], 3)
     return out
 
@@ -710,7 +745,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-mode", type=int, default=0, choices=sorted(MODES),
-                    help="arithmetic of the headline sweep: 0 native FP64 (default), 1 double-float")
+                    help="arithmetic of the headline sweep: 0 native FP64 (default), 1 double-float, "
+                         "2 FP64-wide mix")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -14,7 +14,9 @@
  *
  * Pointers: every vector argument is either a device pointer (cudaMalloc,
  * torch CUDA tensor) or a host pointer (pinned or pageable).  With device
- * pointers the call is enqueued on the context's stream and returns at once.
+ * pointers the call is enqueued on the context's stream and returns at once
+ * (in the emulated arithmetic modes 1 and 2 after reading back one word that
+ * describes the input's range, see fp64_mode).
  * With host pointers the library stages the data through its own device
  * buffers (allocated at the first such call) and runs the same kernels; a
  * call with a host output copies the result back and returns when it is
@@ -42,7 +44,8 @@ extern "C" {
 #define DGNS_ERR_CUDA 2          /* a CUDA runtime call failed             */
 #define DGNS_ERR_OOM 3           /* device allocation failed               */
 #define DGNS_ERR_NOT_CONVERGED 4 /* solver hit max_iter; info is filled    */
-#define DGNS_ERR_NONFINITE 5     /* NaN/Inf residual in a solver           */
+#define DGNS_ERR_NONFINITE 5     /* NaN/Inf residual in a solver, or a      */
+                                 /* non-finite input in modes 1 and 2       */
 #define DGNS_ERR_ALIAS 6         /* dst overlaps a source                  */
 #define DGNS_ERR_UNSUPPORTED 7   /* valid request this build does not do   */
 
@@ -71,13 +74,22 @@ typedef struct {
                          /* FP64;                                                   */
                          /* 1 double-float (pairs of FP32 with a 48-bit significand */
                          /* on the FP32 pipe, which GB300 runs 61x faster; parity   */
-                         /* with FP64 to 1e-12 relative for vectors with max |x|    */
-                         /* between ~1e-15 and 2^127);                              */
-                         /* 2 FP64-wide emulation: triple-float (three FP32, up to  */
-                         /* 72 significant bits, on the FP32 pipe) in the           */
-                         /* SIPG-type and mass kernels, native FP64 in all others;  */
-                         /* same input range as 1.  The multigrid V-cycle runs in   */
-                         /* mg_precision in every mode.                             */
+                         /* with FP64 to 1e-12 relative);                           */
+                         /* 2 FP64-wide: triple-float (three FP32, up to 72         */
+                         /* significant bits, on the FP32 pipe) in the SIPG-type    */
+                         /* and mass kernels and the low-degree convective face     */
+                         /* kernels, native-FP64 and triple-float blocks side by    */
+                         /* side in the k <= 3 convective cell kernel, native FP64  */
+                         /* in all others.  The emulations carry float's exponent: */
+                         /* in modes 1 and 2 every operator call and solve measures */
+                         /* its input's largest exponent (one reduction and a       */
+                         /* read-back, so these calls synchronise the stream) and   */
+                         /* scales an input outside [2^-40, 2^90] (convective term:  */
+                         /* [2^-20, 2^45]) by an exact power of two, so any FP64    */
+                         /* scale is evaluated at full accuracy.  The vector-       */
+                         /* Jacobian product, the penalty parameters and the        */
+                         /* dissipation take inputs as they are.  The multigrid     */
+                         /* V-cycle runs in mg_precision in every mode.             */
 } dgns_mesh_desc;
 
 /* Defaults: 4^3 elements on [-pi,pi]^3, k_u = 3, k_p = k_u - 1, 3/2 rule,
@@ -305,6 +317,12 @@ int dgns_cg_projection_solve(dgns_ctx* ctx, double* x3, const double* b3, const 
  * dgns_debug_live_allocations: device allocations the library has made and
  * not yet freed, over all contexts. */
 int dgns_debug_fail_alloc(long long n);
+/* Measurement hook: in fp64_mode 2 the convective cell kernel runs native-FP64
+ * and triple-float blocks side by side; of every `period` consecutive blocks
+ * the first `nnative` run native FP64.  period = 0 restores the built-in
+ * split; period = -1 runs the convective kernels in triple-float throughout.
+ * Returns DGNS_ERR_INVALID_ARG unless period >= -1 and 0 <= nnative <= period. */
+int dgns_debug_conv_mix(int period, int nnative);
 long long dgns_debug_live_allocations(void);
 
 #ifdef __cplusplus

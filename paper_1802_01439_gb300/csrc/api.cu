@@ -442,6 +442,8 @@ void free_ctx(dgns_ctx* c) {
   dev_free(c->red.scal);
   if (c->h_scal) cudaFreeHost(c->h_scal);
   for (int i = 0; i < 4; ++i) dev_free(c->stage[i]);
+  for (int i = 0; i < 3; ++i) dev_free(c->rwork[i]);
+  dev_free(c->d_expmax);
   if (c->stage_ev) cudaEventDestroy(c->stage_ev);
   if (c->vc_exec) cudaGraphExecDestroy(c->vc_exec);
   if (c->gs) cudaStreamDestroy(c->gs);
@@ -778,6 +780,13 @@ int dgns_set_stream(dgns_ctx* c, void* stream) {
   return 0;
 }
 
+int dgns_debug_conv_mix(int period, int nnative) {
+  if (period < -1 || (period > 0 && (nnative < 0 || nnative > period)))
+    return fail(DGNS_ERR_INVALID_ARG, "period >= -1 and 0 <= nnative <= period");
+  convective_set_mix(period, nnative);
+  return 0;
+}
+
 int dgns_debug_fail_alloc(long long n) {
   if (n < 0) return fail(DGNS_ERR_INVALID_ARG, "n must be >= 0");
   g_fail_alloc_in.store(n);
@@ -809,6 +818,62 @@ int dgns_nodes_1d(const dgns_ctx* c, int space, double* out) {
 
 static bool aligned16(const void* a, const void* b) { return (((uintptr_t)a | (uintptr_t)b) & 15u) == 0; }
 
+// Input range of the emulated arithmetic.  Double-float and triple-float
+// values carry float's exponent: a loaded double keeps its full significand
+// from 2^-74 up and overflows at 2^128.  In those modes every operator call
+// measures the largest exponent of its input (one reduction and a read-back
+// of one word, so these calls synchronise the stream); an input whose
+// largest entry lies outside the window [2^lo, 2^hi] (room for the
+// operator's own scaling above, and for entries 2^30 below the largest) is
+// multiplied by an exact power of two into a work buffer, the operator runs
+// on that copy and its result is scaled back (exactly, unless it leaves the
+// double range).  Native FP64 skips all of it.
+constexpr int kLinLo = -40, kLinHi = 90;     // linear operators
+constexpr int kQuadLo = -20, kQuadHi = 45;   // the convective term (quadratic)
+
+struct Ranged {
+  dgns_ctx* c;
+  explicit Ranged(dgns_ctx* ctx) : c(ctx) {}
+  bool active() const { return c->d.fp64_mode != 0; }
+  // shift (the input is to be multiplied by 2^-shift): 0 inside the window
+  int measure(const void* x, long long n, int lo, int hi, int* shift) {
+    *shift = 0;
+    if (!active() || n == 0) return 0;
+    if (!c->d_expmax) DG_CUDA(dev_malloc(&c->d_expmax, sizeof(unsigned)));
+    if (exp_max((const double*)x, n, c->d_expmax, c->s)) return fail(DGNS_ERR_CUDA, "exp_max launch");
+    unsigned e = 0;
+    DG_CUDA(cudaMemcpyAsync(&e, c->d_expmax, sizeof(unsigned), cudaMemcpyDeviceToHost, c->s));
+    DG_CUDA(cudaStreamSynchronize(c->s));
+    if (e == 2047) return fail(DGNS_ERR_NONFINITE, "input holds a non-finite value");
+    if (e == 0) return 0;                      // zero (or subnormal only): nothing to keep
+    const int E = (int)e - 1023;               // 2^E <= max |x| < 2^(E+1)
+    if (E < lo || E > hi) *shift = E;
+    return 0;
+  }
+  // dst = x * 2^k in work buffer `slot` (grown on demand)
+  int scaled(const void* x, long long n, int k, int slot, const double** dst) {
+    const size_t bytes = (size_t)n * sizeof(double);
+    if (c->rwork_cap[slot] < bytes) {
+      if (c->rwork[slot]) {
+        cudaStreamSynchronize(c->s);
+        dev_free(c->rwork[slot]);
+        c->rwork[slot] = nullptr;
+        c->rwork_cap[slot] = 0;
+      }
+      DG_CUDA(dev_malloc(&c->rwork[slot], bytes));
+      c->rwork_cap[slot] = bytes;
+    }
+    if (scale_pow2((const double*)x, (double*)c->rwork[slot], n, k, c->s)) return fail(DGNS_ERR_CUDA, "scale launch");
+    *dst = (const double*)c->rwork[slot];
+    return 0;
+  }
+  int rescale(void* y, long long n, int k) {
+    if (k == 0) return 0;
+    if (scale_pow2((const double*)y, (double*)y, n, k, c->s)) return fail(DGNS_ERR_CUDA, "scale launch");
+    return 0;
+  }
+};
+
 static int lap_like(dgns_ctx* c, double* dst, const double* src, int space, int ncomp, double coef,
                     double mass_factor) {
   const size_t bytes = (size_t)c->n[space] * ncomp * sizeof(double);
@@ -826,7 +891,17 @@ static int lap_like(dgns_ctx* c, double* dst, const double* src, int space, int 
     build_lap(c->sp1[space], h, c->d.penalty_factor, coef, mass_factor, scaled);
     tab = &scaled;
   }
+  const long long n = c->n[space] * ncomp;
+  Ranged rg(c);
+  int sh = 0;
+  DG_TRY(rg.measure(s, n, kLinLo, kLinHi, &sh));
+  if (sh) {
+    const double* sc;
+    DG_TRY(rg.scaled(s, n, -sh, 0, &sc));
+    s = sc;
+  }
   DG_TRY(laplace_apply(false, c->m, ncomp, s, d, *tab, EPI_NONE, EpiHost(), c->s, c->d.fp64_mode));
+  DG_TRY(rg.rescale(d, n, sh));
   return st.finish();
 }
 
@@ -919,8 +994,18 @@ static int mass_like(dgns_ctx* c, double* dst, const double* src, int ncomp, int
   DG_TRY(st.in(src, bytes, &s));
   DG_TRY(st.out(dst, bytes, &d));
   const double(*T)[MAXN * MAXN] = inverse ? c->minv3[space] : c->mass3[space];
+  const long long n = c->n[space] * ncomp;
+  Ranged rg(c);
+  int sh = 0;
+  DG_TRY(rg.measure(s, n, kLinLo, kLinHi, &sh));
+  if (sh) {
+    const double* sc;
+    DG_TRY(rg.scaled(s, n, -sh, 0, &sc));
+    s = sc;
+  }
   DG_TRY(tensor3_apply(c->N[space], c->m.E * ncomp, (const double*)s, (double*)d, T[0], T[1], T[2], c->s,
                        c->d.fp64_mode));
+  DG_TRY(rg.rescale(d, n, sh));
   return st.finish();
 }
 
@@ -943,7 +1028,16 @@ int dgns_vmult_divergence(dgns_ctx* c, double* dst_p, const double* u3) {
   void* d;
   DG_TRY(st.in(u3, bu, &s));
   DG_TRY(st.out(dst_p, bp, &d));
+  Ranged rg(c);
+  int sh = 0;
+  DG_TRY(rg.measure(s, 3 * c->n[0], kLinLo, kLinHi, &sh));
+  if (sh) {
+    const double* sc;
+    DG_TRY(rg.scaled(s, 3 * c->n[0], -sh, 0, &sc));
+    s = sc;
+  }
   DG_TRY(divergence_apply(c->m, (const double*)s, (double*)d, c->div, c->s, c->d.fp64_mode == 1));
+  DG_TRY(rg.rescale(d, c->n[1], sh));
   return st.finish();
 }
 
@@ -958,7 +1052,16 @@ int dgns_vmult_gradient(dgns_ctx* c, double* dst3, const double* p) {
   void* d;
   DG_TRY(st.in(p, bp, &s));
   DG_TRY(st.out(dst3, bu, &d));
+  Ranged rg(c);
+  int sh = 0;
+  DG_TRY(rg.measure(s, c->n[1], kLinLo, kLinHi, &sh));
+  if (sh) {
+    const double* sc;
+    DG_TRY(rg.scaled(s, c->n[1], -sh, 0, &sc));
+    s = sc;
+  }
   DG_TRY(gradient_apply(c->m, (const double*)s, (double*)d, c->grad, c->s, c->d.fp64_mode == 1));
+  DG_TRY(rg.rescale(d, 3 * c->n[0], sh));
   return st.finish();
 }
 
@@ -990,8 +1093,18 @@ int dgns_vmult_convective(dgns_ctx* c, double* dst3, const double* u3) {
   void* d;
   DG_TRY(st.in(u3, bu, &s));
   DG_TRY(st.out(dst3, bu, &d));
+  const long long n = 3 * c->n[0];
+  Ranged rg(c);
+  int sh = 0;
+  DG_TRY(rg.measure(s, n, kQuadLo, kQuadHi, &sh));
+  if (sh) {
+    const double* sc;
+    DG_TRY(rg.scaled(s, n, -sh, 0, &sc));
+    s = sc;
+  }
   DG_TRY(conv_status(convective_launch(3, c->m, (const double*)s, c->conv_face, (double*)d, c->conv,
                                        c->d.fp64_mode, c->s)));
+  DG_TRY(rg.rescale(d, n, 2 * sh));
   return st.finish();
 }
 
@@ -1013,8 +1126,18 @@ int dgns_convective_faces(dgns_ctx* c, double* rface, const double* u3) {
   void* f;
   DG_TRY(st.in(u3, bu, &s));
   DG_TRY(st.out(rface, bf, &f));
+  const long long n = 3 * c->n[0], nf = 9LL * c->m.E * c->conv.N * c->conv.N;
+  Ranged rg(c);
+  int sh = 0;
+  DG_TRY(rg.measure(s, n, kQuadLo, kQuadHi, &sh));
+  if (sh) {
+    const double* sc;
+    DG_TRY(rg.scaled(s, n, -sh, 0, &sc));
+    s = sc;
+  }
   DG_TRY(conv_status(convective_launch(1, c->m, (const double*)s, (double*)f, nullptr, c->conv,
                                        c->d.fp64_mode, c->s)));
+  DG_TRY(rg.rescale(f, nf, 2 * sh));
   return st.finish();
 }
 
@@ -1033,8 +1156,20 @@ int dgns_convective_cells(dgns_ctx* c, double* dst3, const double* u3, const dou
   DG_TRY(st.in(u3, bu, &s));
   DG_TRY(st.in(rface, bf, &f));
   DG_TRY(st.out(dst3, bu, &d));
+  const long long n = 3 * c->n[0], nf = 9LL * c->m.E * c->conv.N * c->conv.N;
+  Ranged rg(c);
+  int sh = 0;
+  DG_TRY(rg.measure(s, n, kQuadLo, kQuadHi, &sh));
+  if (sh) {   // the face integrals scale with the square of u
+    const double *su, *sf;
+    DG_TRY(rg.scaled(s, n, -sh, 0, &su));
+    DG_TRY(rg.scaled(f, nf, -2 * sh, 1, &sf));
+    s = su;
+    f = sf;
+  }
   DG_TRY(conv_status(convective_launch(2, c->m, (const double*)s, (double*)f, (double*)d, c->conv,
                                        c->d.fp64_mode, c->s)));
+  DG_TRY(rg.rescale(d, n, 2 * sh));
   return st.finish();
 }
 
@@ -1163,9 +1298,15 @@ int dgns_vmult_projection(dgns_ctx* c, double* dst3, const double* src3, const d
   if (overlaps(dst3, bu, src3, bu)) return fail(DGNS_ERR_ALIAS, "dst overlaps src");
   if (!is_device_ptr(dst3) || !is_device_ptr(src3) || !is_device_ptr(tau_d) || !is_device_ptr(tau_c))
     return fail(DGNS_ERR_INVALID_ARG, "device pointers only");
+  const long long n = 3 * c->n[0];
+  Ranged rg(c);
+  int sh = 0;
+  DG_TRY(rg.measure(src3, n, kLinLo, kLinHi, &sh));
+  if (sh) DG_TRY(rg.scaled(src3, n, -sh, 0, &src3));
   const int rc = projection_apply(c->m, src3, dst3, tau_d, tau_c, c->proj, c->s, c->d.fp64_mode == 1);
   if (rc == 7) return fail(DGNS_ERR_UNSUPPORTED, "projection operator: degree not supported");
   DG_TRY(rc);
+  DG_TRY(rg.rescale(dst3, n, sh));
   return 0;
 }
 
@@ -1184,15 +1325,21 @@ int dgns_vmult_projection_terms(dgns_ctx* c, double* dst3, const double* src3, c
   if (!is_device_ptr(dst3) || !is_device_ptr(src3) || (tau_d && !is_device_ptr(tau_d)) ||
       (tau_c && !is_device_ptr(tau_c)))
     return fail(DGNS_ERR_INVALID_ARG, "device pointers only");
+  const long long n = 3 * c->n[0];
+  Ranged rg(c);
+  int sh = 0;
+  DG_TRY(rg.measure(src3, n, kLinLo, kLinHi, &sh));
+  if (sh) DG_TRY(rg.scaled(src3, n, -sh, 0, &src3));
   if (terms == DGNS_PROJ_MASS) {
     const double(*T)[MAXN * MAXN] = c->mass3[DGNS_SPACE_U];
     DG_TRY(tensor3_apply(c->N[0], 3 * c->m.E, src3, dst3, T[0], T[1], T[2], c->s, c->d.fp64_mode));
-    return 0;
+  } else {
+    const int rc = projection_apply(c->m, src3, dst3, tau_d, tau_c, c->proj, c->s, c->d.fp64_mode == 1,
+                                    terms == DGNS_PROJ_DIV ? PROJ_DIV : PROJ_CONT);
+    if (rc == 7) return fail(DGNS_ERR_UNSUPPORTED, "projection operator: degree not supported");
+    DG_TRY(rc);
   }
-  const int rc = projection_apply(c->m, src3, dst3, tau_d, tau_c, c->proj, c->s, c->d.fp64_mode == 1,
-                                  terms == DGNS_PROJ_DIV ? PROJ_DIV : PROJ_CONT);
-  if (rc == 7) return fail(DGNS_ERR_UNSUPPORTED, "projection operator: degree not supported");
-  DG_TRY(rc);
+  DG_TRY(rg.rescale(dst3, n, sh));
   return 0;
 }
 
@@ -1214,14 +1361,27 @@ int dgns_cg_projection_solve(dgns_ctx* c, double* x3, const double* b3, const do
   const auto t0 = std::chrono::steady_clock::now();
   const int N = c->N[0];
   const double(*MI)[MAXN * MAXN] = c->minv3[0];
-  DG_CUDA(cudaMemcpyAsync(c->r, b3, bytes, cudaMemcpyDeviceToDevice, c->s));
+  double* X = x3;
+  const double* B = b3;
+  // emulated arithmetic: the system is scaled by an exact power of two when b
+  // lies outside the input window (the operator is linear:
+  // A (x 2^-s) = b 2^-s), and the solution scaled back
+  Ranged rg(c);
+  int sh = 0;
+  DG_TRY(rg.measure(B, n, kLinLo, kLinHi, &sh));
+  if (sh) {
+    DG_TRY(rg.scaled(B, n, -sh, 2, &B));
+    if (prm.use_initial_guess) DG_TRY(rg.rescale(X, n, -sh));
+    prm.abs_tol = ldexp(prm.abs_tol, -sh);
+  }
+  DG_CUDA(cudaMemcpyAsync(c->r, B, bytes, cudaMemcpyDeviceToDevice, c->s));
   if (prm.use_initial_guess) {
-    DG_TRY(projection_apply(c->m, x3, c->Ap, tau_d, tau_c, c->proj, c->s, c->d.fp64_mode == 1));
+    DG_TRY(projection_apply(c->m, X, c->Ap, tau_d, tau_c, c->proj, c->s, c->d.fp64_mode == 1));
     DG_TRY(axpby(c->r, c->Ap, n, -1.0, 1.0, c->s));
     DG_TRY(dot(c->r, c->r, n, c->red, S_T0, c->s));
   } else {
-    DG_CUDA(cudaMemsetAsync(x3, 0, bytes, c->s));
-    DG_TRY(dot(b3, b3, n, c->red, S_T0, c->s));
+    DG_CUDA(cudaMemsetAsync(X, 0, bytes, c->s));
+    DG_TRY(dot(B, B, n, c->red, S_T0, c->s));
   }
   DG_TRY(read_scalars(c));
   const double nb = sqrt(c->h_scal[S_T0]);
@@ -1261,6 +1421,8 @@ int dgns_cg_projection_solve(dgns_ctx* c, double* x3, const double* b3, const do
   } else if (!std::isfinite(nb)) {
     status = fail(DGNS_ERR_NONFINITE, "non-finite right-hand side");
   }
+  DG_TRY(rg.rescale(X, n, sh));
+  inf.initial_res = ldexp(inf.initial_res, sh);
   DG_CUDA(cudaStreamSynchronize(c->s));
   inf.status = status;
   inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -1331,6 +1493,17 @@ int dgns_cg_mg_solve(dgns_ctx* c, double* x, const double* b, const dgns_solve_p
   DG_TRY(prm.use_initial_guess ? st.inout(x, bytes, &xs) : st.out(x, bytes, &xs));
   double* X = (double*)xs;
   const double* B = (const double*)bs;
+  // emulated arithmetic: the system is scaled by an exact power of two when b
+  // lies outside the input window (the operator is linear:
+  // A (x 2^-s) = b 2^-s), and the solution scaled back
+  Ranged rg(c);
+  int sh = 0;
+  DG_TRY(rg.measure(B, n, kLinLo, kLinHi, &sh));
+  if (sh) {
+    DG_TRY(rg.scaled(B, n, -sh, 2, &B));
+    if (prm.use_initial_guess) DG_TRY(rg.rescale(X, n, -sh));
+    prm.abs_tol = ldexp(prm.abs_tol, -sh);
+  }
   const LapHost& A = c->lap[DGNS_SPACE_P];
   if (!prm.use_initial_guess) {
     DG_CUDA(cudaMemsetAsync(X, 0, bytes, c->s));
@@ -1388,6 +1561,8 @@ int dgns_cg_mg_solve(dgns_ctx* c, double* x, const double* b, const dgns_solve_p
     inf.rel_res = res;
     if (status == DGNS_ERR_NOT_CONVERGED) fail(status, "max_iter reached");
   }
+  DG_TRY(rg.rescale(X, n, sh));
+  inf.initial_res = ldexp(inf.initial_res, sh);
   DG_TRY(st.finish());
   DG_CUDA(cudaStreamSynchronize(c->s));
   inf.status = status;
@@ -1417,6 +1592,17 @@ int dgns_cg_invmass_solve(dgns_ctx* c, double* x3, const double* b3, double mass
   DG_TRY(prm.use_initial_guess ? st.inout(x3, bytes, &xs) : st.out(x3, bytes, &xs));
   double* X = (double*)xs;
   const double* B = (const double*)bs;
+  // emulated arithmetic: the system is scaled by an exact power of two when b
+  // lies outside the input window (the operator is linear:
+  // A (x 2^-s) = b 2^-s), and the solution scaled back
+  Ranged rg(c);
+  int sh = 0;
+  DG_TRY(rg.measure(B, n, kLinLo, kLinHi, &sh));
+  if (sh) {
+    DG_TRY(rg.scaled(B, n, -sh, 2, &B));
+    if (prm.use_initial_guess) DG_TRY(rg.rescale(X, n, -sh));
+    prm.abs_tol = ldexp(prm.abs_tol, -sh);
+  }
   LapHost H;
   build_lap(c->sp1[0], c->h, c->d.penalty_factor, c->d.nu, mass_factor, H);
   const int N = c->N[0];
@@ -1468,6 +1654,8 @@ int dgns_cg_invmass_solve(dgns_ctx* c, double* x3, const double* b3, double mass
   } else if (!std::isfinite(nb)) {
     status = fail(DGNS_ERR_NONFINITE, "non-finite right-hand side");
   }
+  DG_TRY(rg.rescale(X, n, sh));
+  inf.initial_res = ldexp(inf.initial_res, sh);
   DG_TRY(st.finish());
   DG_CUDA(cudaStreamSynchronize(c->s));
   inf.status = status;

@@ -40,5 +40,10 @@ int cheb_first(bool fp32, const void* b, const void* dinv, void* x, long long n,
                cudaStream_t s);
 // y = a x + b y
 int axpby(double* y, const double* x, long long n, double a, double b, cudaStream_t s);
+// *out (device) = largest biased exponent of |x_i| (0: all zero, 2047: an
+// entry is not finite)
+int exp_max(const double* x, long long n, unsigned* out, cudaStream_t s);
+// y = x * 2^k, exact; y may alias x
+int scale_pow2(const double* x, double* y, long long n, int k, cudaStream_t s);
 
 }  // namespace dgns

@@ -77,6 +77,11 @@ struct dgns_ctx {
   cudaGraphExec_t vc_exec = nullptr;
   int vc_key[3] = {0, 0, 0};
   double vc_range = 0.0;
+  // input range of the emulated arithmetic (fp64_mode 1, 2): the largest
+  // exponent of an input (device), and work buffers for scaled copies
+  unsigned* d_expmax = nullptr;
+  void* rwork[3] = {nullptr, nullptr, nullptr};
+  size_t rwork_cap[3] = {0, 0, 0};
   // staging of host pointers
   void* stage[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t stage_ev = nullptr;  // recorded after the staging copies of host inputs

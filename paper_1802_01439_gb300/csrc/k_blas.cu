@@ -122,6 +122,35 @@ __global__ void __launch_bounds__(RT) axpby_kernel(double* y, const double* x,
     y[i] = b == 0.0 ? a * x[i] : fma(a, x[i], b * y[i]);  // b = 0 ignores y's contents
 }
 
+// Largest biased exponent of |x_i| over the vector (integer operations on
+// the bit patterns; 0 for a zero vector, 2047 when an entry is not finite):
+// per-block maximum, then one atomic maximum per block into *out (set to 0
+// before the launch).
+__global__ void __launch_bounds__(RT) exp_max_kernel(const double* __restrict__ x, long long n,
+                                                     unsigned* __restrict__ out) {
+  unsigned e = 0;
+  const long long stride = (long long)gridDim.x * RT;
+  for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < n; i += stride) {
+    const unsigned h = (unsigned)((unsigned long long)__double_as_longlong(x[i]) >> 32);
+    e = max(e, (h >> 20) & 0x7FFu);
+  }
+  e = __reduce_max_sync(0xffffffffu, e);
+  __shared__ unsigned red[RT / 32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned m = 0;
+    for (int w = 0; w < RT / 32; ++w) m = max(m, red[w]);
+    atomicMax(out, m);
+  }
+}
+
+// y = x * 2^k (exact unless the result leaves the double range); y may be x
+__global__ void __launch_bounds__(RT) scale_pow2_kernel(const double* x, double* y, long long n, int k) {
+  const long long stride = (long long)gridDim.x * RT;
+  for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < n; i += stride) y[i] = ldexp(x[i], k);
+}
+
 inline unsigned grid_for(long long n) {
   long long b = (n + RT - 1) / RT;
   if (b > RED_BLOCKS) b = RED_BLOCKS;
@@ -198,6 +227,17 @@ int cheb_first(bool fp32, const void* b, const void* dinv, void* x, long long n,
     cheb_first_kernel<float><<<g, RT, 0, s>>>((const float*)b, (const float*)dinv, (float*)x, n, nper, (float)c);
   else
     cheb_first_kernel<double><<<g, RT, 0, s>>>((const double*)b, (const double*)dinv, (double*)x, n, nper, c);
+  return status();
+}
+
+int exp_max(const double* x, long long n, unsigned* out, cudaStream_t s) {
+  if (cudaMemsetAsync(out, 0, sizeof(unsigned), s) != cudaSuccess) return 2;
+  if (n > 0) exp_max_kernel<<<grid_for(n), RT, 0, s>>>(x, n, out);
+  return status();
+}
+
+int scale_pow2(const double* x, double* y, long long n, int k, cudaStream_t s) {
+  if (n > 0) scale_pow2_kernel<<<grid_for(n), RT, 0, s>>>(x, y, n, k);
   return status();
 }
 

@@ -331,9 +331,9 @@ __device__ __forceinline__ unsigned pick2(int i, unsigned a, unsigned b) { retur
 // them by thread.  A group past the last cell repeats the last cell and
 // stores nothing.
 template <class A, int N, int Q>
-__global__ void __launch_bounds__(conv_groups_per_block<N>() * conv_threads<N>())
-    conv_kernel(const double* __restrict__ u3, const double* __restrict__ rface, double* __restrict__ dst3,
-                const __grid_constant__ ConvTabT<typename A::V, N, Q> tb, const MeshDims m) {
+__device__ __forceinline__ void conv_cells(const double* __restrict__ u3, const double* __restrict__ rface,
+                                           double* __restrict__ dst3, const ConvTabT<typename A::V, N, Q>& tb,
+                                           const MeshDims& m, const unsigned bid) {
   typedef typename A::V V;
   typedef typename A::Acc Acc;
   typedef ConvLayout<N, Q> LY;
@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(conv_groups_per_block<N>() * conv_threads<N>()
   V* sm = reinterpret_cast<V*>(dyn_smem());
   const int g = threadIdx.x / NT;
   const int t = threadIdx.x - g * NT;
-  const long long c0 = ((long long)blockIdx.x * conv_groups_per_block<N>() + g) * CPG;
+  const long long c0 = ((long long)bid * conv_groups_per_block<N>() + g) * CPG;
   const long long last = m.E - 1;
   constexpr int QH = (Q + 1) / 2, QF = Q / 2, NH = (N + 1) / 2, NF = N / 2;
   constexpr bool PR = conv_pair_rows<N>();
@@ -708,6 +708,31 @@ __global__ void __launch_bounds__(conv_groups_per_block<N>() * conv_threads<N>()
     if (z == 0) v -= rc[5 * 3 * NN + x + N * y];
     dst3[((size_t)c * m.E + pick2(j, el0, el1)) * N3 + rr] = v;
   }
+}
+
+template <class A, int N, int Q>
+__global__ void __launch_bounds__(conv_groups_per_block<N>() * conv_threads<N>())
+    conv_kernel(const double* __restrict__ u3, const double* __restrict__ rface, double* __restrict__ dst3,
+                const __grid_constant__ ConvTabT<typename A::V, N, Q> tb, const MeshDims m) {
+  conv_cells<A, N, Q>(u3, rface, dst3, tb, m, blockIdx.x);
+}
+
+// Both pipes at once: of every `period` consecutive blocks the first
+// `nnative` run the cell kernel in native FP64 (the FP64 pipe, whose
+// instructions take few issue slots) and the others in triple-float (the
+// FP32 pipe), so that the blocks resident on an SM keep both pipes busy.
+// Both arithmetics are at least FP64-wide; the shared memory is sized for
+// the larger (triple-float) work space.
+template <int N, int Q>
+__global__ void __launch_bounds__(conv_groups_per_block<N>() * conv_threads<N>())
+    conv_kernel_mix(const double* __restrict__ u3, const double* __restrict__ rface, double* __restrict__ dst3,
+                    const __grid_constant__ ConvTabT<double, N, Q> tbn,
+                    const __grid_constant__ ConvTabT<tf64, N, Q> tbt, const MeshDims m, const int period,
+                    const int nnative) {
+  if ((int)(blockIdx.x % (unsigned)period) < nnative)
+    conv_cells<F64, N, Q>(u3, rface, dst3, tbn, m, blockIdx.x);
+  else
+    conv_cells<TF64, N, Q>(u3, rface, dst3, tbt, m, blockIdx.x);
 }
 
 // Face term of Sec. 3.2, one evaluation per interior face (the mesh is

@@ -93,9 +93,15 @@ struct ConvHost {
 // beyond).
 int convective_launch(int part, const MeshDims& m, const double* u3, double* rface, double* dst3,
                       const ConvHost& t, int arith, cudaStream_t s);
-// The triple-float kernels (k_convective_tf64.cu); 7 where not instantiated.
+// The FP64-wide kernels beyond native FP64 (k_convective_tf64.cu): the cell
+// kernel with native-FP64 and triple-float blocks side by side, the face
+// kernel native; 7 where not instantiated or not fitting.
 int convective_launch_tf64(int part, const MeshDims& m, const double* u3, double* rface, double* dst3,
                            const ConvHost& t, cudaStream_t s);
+// Split of the mixed cell kernel: of every `period` blocks the first
+// `nnative` run native FP64; period 0 restores the built-in split, period
+// -1 runs the convective kernels in triple-float throughout.
+void convective_set_mix(int period, int nnative);
 // emulated: double-float arithmetic (else native FP64)
 int convective_vjp(const MeshDims& m, const double* u3, const double* w3, double* dst3,
                    const ConvHost& t, cudaStream_t s, bool emulated = false);

@@ -243,20 +243,79 @@ def test_pinned_host_pointers():
     assert np.array_equal(yp.numpy(), host(yd))
 
 
-@pytest.mark.parametrize("scale", [1e-15, 1.0, 1e30])
-def test_double_float_stores_across_magnitudes(scale):
-    """Small, ordinary and large vectors within the double-float range match
-    the oracle (a loaded value keeps its low half above 2^-74, so its error is
-    at most 2^-47 |x| + 2^-98 absolute: vectors down to max |x| ~ 1e-15)."""
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("scale", [1e-300, 1e-20, 1e-15, 1.0, 1e30, 1e35, 1e300])
+def test_emulated_modes_across_the_fp64_range(scale, mode):
+    """Double-float and triple-float values carry float's exponent; inputs
+    whose largest entry lies outside the window the emulations keep to full
+    precision are scaled by an exact power of two inside the call, so every
+    scale FP64 holds gives the same relative accuracy (the previous build
+    measured 1.8e-10 at 1e-20 without the scaling).  Linear operators: mass,
+    inverse mass, Laplace, Helmholtz, divergence, gradient, projection."""
     n, k = (2, 3, 2), 3
-    ctx = context(n, k, mg_precision=0, fp64_mode=1)
-    s = dg.Space(dg.Mesh(n), k)
+    ctx = context(n, k, mg_precision=0, fp64_mode=mode)
+    m = dg.Mesh(n)
+    s, sp = dg.Space(m, k), dg.Space(m, k - 1)
     x = scale * random_field(s, 3, 12)
     y = torch.empty(x.size, dtype=torch.float64, device="cuda")
     ctx.vmult_mass(y, dev(x.ravel()), 3, 0)
     assert rel_err(host(y), dg.Mass(s).apply(x)) <= TOL
     ctx.apply_inverse_mass(y, dev(x.ravel()), 3, 0)
     assert rel_err(host(y), dg.Mass(s).apply_inverse(x)) <= TOL
+    ctx.vmult_laplace(y[:s.size], dev(x[0].ravel()), space=0)
+    assert rel_err(host(y[:s.size]), dg.Laplace(s).apply(x[0])) <= TOL
+    ctx.vmult_helmholtz(y, dev(x.ravel()), 1500.0)
+    assert rel_err(host(y), dg.Helmholtz(s, 1.0 / 1600, 1500.0).apply(x)) <= TOL
+    d = torch.empty(sp.size, dtype=torch.float64, device="cuda")
+    ctx.vmult_divergence(d, dev(x.ravel()))
+    assert rel_err(host(d), dg.Divergence(s, sp).apply(x)) <= TOL
+    p = scale * random_field(sp, 1, 13)
+    ctx.vmult_gradient(y, dev(p.ravel()))
+    assert rel_err(host(y), dg.Gradient(s, sp).apply(p)) <= TOL
+    td, tc = np.full(m.E, 0.3), np.full(m.E, 0.2)
+    ctx.vmult_projection(y, dev(x.ravel()), dev(td), dev(tc))
+    assert rel_err(host(y), dg.Projection(s, td, tc).apply(x)) <= TOL
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("scale", [1e-150, 1e-20, 1e20, 1e150])
+def test_emulated_convective_across_the_fp64_range(scale, mode):
+    """The convective term is quadratic: inputs are scaled into the window
+    of the emulations and the result by the square of the factor, in the
+    one-call form and in its two phases (face integrals, cell term)."""
+    n, k = (2, 2, 3), 3
+    ctx = context(n, k, mg_precision=0, fp64_mode=mode)
+    s = dg.Space(dg.Mesh(n), k)
+    u = scale * tgv_field(s, 1e-2, 3)
+    ref = dg.Convective(s).apply(u)
+    y = torch.empty(u.size, dtype=torch.float64, device="cuda")
+    ctx.vmult_convective(y, dev(u.ravel()))
+    assert rel_err(host(y), ref) <= TOL
+    rf = torch.empty(ctx.convective_face_size(), dtype=torch.float64, device="cuda")
+    ud = dev(u.ravel())
+    ctx.convective_faces(rf, ud)
+    ctx.convective_cells(y, ud, rf)
+    assert rel_err(host(y), ref) <= TOL
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("scale", [1e-250, 1e-20, 1e250])
+def test_emulated_solves_across_the_fp64_range(scale, mode):
+    """The Helmholtz and pressure solves scale the right-hand side into the
+    window and the solution back: the solution of scale * b is scale times
+    the solution of b."""
+    n, k = (4, 4, 2), 3
+    ctx = context(n, k, mg_precision=32, fp64_mode=mode)
+    b = np.random.default_rng(14).uniform(-1, 1, 3 * ctx.n_u)
+    x1, xs = (torch.zeros(3 * ctx.n_u, dtype=torch.float64, device="cuda") for _ in range(2))
+    ctx.cg_invmass_solve(x1, dev(b), 100.0, rel_tol=1e-12)
+    ctx.cg_invmass_solve(xs, dev(scale * b), 100.0, rel_tol=1e-12)
+    assert rel_err(host(xs) / scale, host(x1)) <= 1e-11
+    bp = b[:ctx.n_p] - b[:ctx.n_p].mean()
+    p1, ps = (torch.zeros(ctx.n_p, dtype=torch.float64, device="cuda") for _ in range(2))
+    ctx.cg_mg_solve(p1, dev(bp), rel_tol=1e-11)
+    ctx.cg_mg_solve(ps, dev(scale * bp), rel_tol=1e-11)
+    assert rel_err(host(ps) / scale, host(p1)) <= 1e-9
 
 
 # ------------------------------------------ triple-float: FP64-wide accuracy
