@@ -67,7 +67,7 @@ EMU_FP32_FLOPS = {1: (15, 8), 2: (51, 21)}
 # of the same launch configuration (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by (kernel, fp64 mode, k); absent where no
 # capture of the current kernel exists.
-KERNEL_TRAFFIC = {}
+KERNEL_TRAFFIC = {("conv_kernel", 0, 9): 553.0e6 + 385.4e6}   # profiles/conv_f64_k9_26c_ncu.md
 
 
 # ----------------------------------------------------------- flop counts
@@ -364,30 +364,52 @@ def dominant_roofline(sw, per_k, mode):
             "flop_count": "even-odd algorithmic count (bench.laplace_ops / conv_cell_ops / conv_face_ops)"}
 
 
-def e2e_sweep(sw, steps, warmup, world):
-    """The sweep through the public API with host buffers: every input comes
-    from pinned host memory through the C ABI's staging and every result goes
-    back to pinned host memory; the copies are inside the timing."""
+def e2e_sweep(sw, steps, warmup, world, stream):
+    """The sweep end to end through the public API: every input starts in
+    pinned host memory and every result ends there; the copies are inside
+    the timing.  The host-to-device copies of all degrees are queued on one
+    copy stream and the device-to-host copies on another, ordered against
+    the context's stream by events, so the copy engines move degree k+1's
+    inputs in and degree k-1's results out while the kernels of degree k
+    run (the library's calls with host pointers, which stage and wait per
+    call, would serialise them)."""
     import torch
     host = []
     for it in sw.items:
         nu_ = it["ctx"].n_u
         host.append((it["x"].cpu().pin_memory(), torch.empty(nu_, dtype=torch.float64).pin_memory(),
                      it["u"].cpu().pin_memory(), torch.empty(3 * nu_, dtype=torch.float64).pin_memory()))
+    h2d, d2h = torch.cuda.Stream(), torch.cuda.Stream()
+    nk = len(sw.items)
     ts = []
     for rep in range(warmup + steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for it, (xh, yh, uh, ch) in zip(sw.items, host):
-            it["ctx"].vmult_laplace(yh, xh, space=0)
-            it["ctx"].vmult_convective(ch, uh)
+        ev_in = [torch.cuda.Event() for _ in range(nk)]
+        ev_out = [torch.cuda.Event() for _ in range(nk)]
+        with torch.cuda.stream(h2d):
+            for i, (it, (xh, _, uh, _)) in enumerate(zip(sw.items, host)):
+                it["x"].copy_(xh, non_blocking=True)
+                it["u"].copy_(uh, non_blocking=True)
+                ev_in[i].record(h2d)
+        for i, it in enumerate(sw.items):
+            stream.wait_event(ev_in[i])
+            it["ctx"].vmult_laplace(it["y"], it["x"], space=0)
+            it["ctx"].vmult_convective(it["c"], it["u"])
+            ev_out[i].record(stream)
+        with torch.cuda.stream(d2h):
+            for i, (it, (_, yh, _, ch)) in enumerate(zip(sw.items, host)):
+                d2h.wait_event(ev_out[i])
+                yh.copy_(it["y"], non_blocking=True)
+                ch.copy_(it["c"], non_blocking=True)
         torch.cuda.synchronize()
         if rep >= warmup:
             ts.append(time.perf_counter() - t0)
     t = max_over_ranks(sum(ts) / len(ts), world)
     nbytes = sum(8 * 4 * it["ctx"].n_u for it in sw.items)
     return {"value": round(world * sw.dofs / t, 1), "unit": "DoFs/s", "h2d_bytes_per_step": nbytes,
-            "d2h_bytes_per_step": nbytes, "ms_per_step": round(t * 1e3, 3), "steps": steps}
+            "d2h_bytes_per_step": nbytes, "ms_per_step": round(t * 1e3, 3), "steps": steps,
+            "copies": "pinned host buffers, H2D and D2H on their own streams, overlapped with the kernels"}
 
 
 def gpu_arm(args, rank, world):
@@ -407,7 +429,7 @@ def gpu_arm(args, rank, world):
     ms = max_over_ranks(ms, world)
     table = sweep_table(sw, per_k, mode)
     roof = dominant_roofline(sw, per_k, mode)
-    e2e = e2e_sweep(sw, max(2, args.steps // 4), 1, world)
+    e2e = e2e_sweep(sw, max(2, args.steps // 4), 1, world, stream)
     sw.close()
     del sw
     line = {
