@@ -323,6 +323,22 @@ int dgns_debug_fail_alloc(long long n);
  * split; period = -1 runs the convective kernels in triple-float throughout.
  * Returns DGNS_ERR_INVALID_ARG unless period >= -1 and 0 <= nnative <= period. */
 int dgns_debug_conv_mix(int period, int nnative);
+/* Measurement hook: the kernel of the FP32 Laplace operator at k_p = 3 (the
+ * multigrid level operator and the Chebyshev step).  0: built-in; -1: one
+ * thread per x-line of a cell, data staged in shared memory by the threads;
+ * 1: one thread per cell plane, data in registers, packed FP32x2 arithmetic;
+ * 2: the same with scalar FP32 arithmetic (bit-identical results); 3: as 1
+ * with the z-direction as one reduce-scatter; 4: one thread per cell plane,
+ * data staged in shared memory by tensor copies, one stage and 12 warps per
+ * SM; 5: as 4 with two stages and 7 warps.  The built-in choice is 4 where it
+ * applies (nx divisible by 8, every vector 32-byte aligned), else 1 (every
+ * vector 32-byte aligned), else -1; 1..5 fall back the same way.  Returns
+ * DGNS_ERR_INVALID_ARG outside -1..5. */
+int dgns_debug_laplace_f32_kernel(int variant);
+/* Bounded waits of the staged FP32 Laplace kernel that gave up since the
+ * library was loaded (0 in a healthy run; a nonzero count means that kernel
+ * left results unwritten).  Synchronous device read. */
+long long dgns_debug_laplace_f32_timeouts(void);
 long long dgns_debug_live_allocations(void);
 
 #ifdef __cplusplus

@@ -59,6 +59,8 @@ SIGNATURES = {
     "dgns_set_stream": (_I, [_P, _P]),
     "dgns_debug_fail_alloc": (_I, [_LL]),
     "dgns_debug_conv_mix": (_I, [_I, _I]),
+    "dgns_debug_laplace_f32_kernel": (_I, [_I]),
+    "dgns_debug_laplace_f32_timeouts": (ctypes.c_longlong, []),
     "dgns_debug_live_allocations": (_LL, []),
     "dgns_status_string": (ctypes.c_char_p, [_I]),
     "dgns_last_error": (ctypes.c_char_p, []),

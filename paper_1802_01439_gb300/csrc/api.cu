@@ -787,6 +787,14 @@ int dgns_debug_conv_mix(int period, int nnative) {
   return 0;
 }
 
+int dgns_debug_laplace_f32_kernel(int variant) {
+  if (variant < -1 || variant > 5) return fail(DGNS_ERR_INVALID_ARG, "variant must be in -1..5");
+  laplace_plane_set_variant(variant);
+  return 0;
+}
+
+long long dgns_debug_laplace_f32_timeouts(void) { return (long long)laplace_tma_timeouts(); }
+
 int dgns_debug_fail_alloc(long long n) {
   if (n < 0) return fail(DGNS_ERR_INVALID_ARG, "n must be >= 0");
   g_fail_alloc_in.store(n);

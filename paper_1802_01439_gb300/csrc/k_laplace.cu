@@ -27,6 +27,7 @@
 // (load_nb_summary).
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "arith.cuh"
 #include "ops.h"
@@ -592,6 +593,11 @@ int launch_sipg(const MeshDims& m, int ncomp, const typename A::G* src, typename
         tb.grd[d][i] = h.gr[d][i];
         tb.gld[d][i] = h.gl[d][i];
       }
+  }
+  if constexpr (std::is_same<A, F32>::value && N == 4) {
+    // one thread per cell plane where the pointers allow 256-bit accesses
+    const int r = laplace_plane_f32(m, ncomp, src, dst, h, EPI, eh, s);
+    if (r >= 0) return r;
   }
   EpiArgs<G> ea{(const G*)eh.b, (const G*)eh.xprev, (const G*)eh.dinv, (G)eh.c1, (G)eh.c2};
   const long long ncells = m.E * ncomp;

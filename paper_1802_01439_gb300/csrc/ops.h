@@ -39,6 +39,27 @@ enum Arith {
   ARITH_TF64 = 2,   // triple-float on the FP32 pipe (SIPG and mass kernels; others native FP64)
 };
 
+// FP32 Laplace operator on cells of N = 4 with one thread per cell plane
+// (k_laplace_plane.cu).  Returns -1, doing nothing, where it does not apply
+// (N != 4, a pointer not aligned for its vector accesses, or the line kernel
+// selected by laplace_plane_set_variant(-1)); else 0, or 2 on a launch error.
+int laplace_plane_f32(const MeshDims& m, int ncomp, const float* src, float* dst, const LapHost& h, int epi,
+                      const EpiHost& eh, cudaStream_t s);
+// Kernel choice for the FP32 N = 4 operator: 0 built-in (the staged kernel
+// where it applies, else the register plane kernel), -1 the line kernel; the
+// register plane kernel with packed FP32x2 arithmetic (1), scalar (2), or
+// packed with the z-direction as one reduce-scatter (3); the staged kernel
+// with one stage and 12 warps per SM (4) or two stages and 7 warps (5), each
+// falling back to 1 where it does not apply.
+void laplace_plane_set_variant(int v);
+// The same operator with its data staged in shared memory by tensor copies
+// (k_laplace_tma.cu): nx divisible by 8 and 32-byte aligned vectors, else -1;
+// variant 0 one stage and 12 warps per SM, 1 two stages and 7 warps.
+int laplace_tma_f32(const MeshDims& m, int ncomp, const float* src, float* dst, const LapHost& h, int epi,
+                    const EpiHost& eh, cudaStream_t s, int variant);
+// Waits of the staged kernel that gave up (device counter; synchronous read).
+unsigned laplace_tma_timeouts();
+
 // dst = L src on ncomp scalar fields (cells of component c follow those of
 // component c-1); `fp32` selects float data, else double.
 // arith (double data only): an Arith; the emulated ones take EPI_NONE only.
