@@ -460,6 +460,7 @@ def gpu_arm(args, rank, world):
             del sw
         line["operator_set_32c_k3"] = {m: operator_set_step(dev, flush, m, 20) for m in (0, 1)}
         line["fused_vs_split"] = fused_vs_split()
+        line["mg_smoother_64c_k3"] = mg_smoother_step()
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if not args.no_solve and rank == 0:
@@ -595,6 +596,32 @@ POISSON_ARMS = [("mixed", 32, 0, "native FP64 CG (matvec, residual, dots, update
                 ("fp64", 64, 0, "native FP64 CG + FP64 V-cycle (all FP64)"),
                 ("mixed_tf64_matvec", 32, 2, "FP64 CG with a triple-float (FP64-wide) matvec + FP32 V-cycle"),
                 ("mixed_df64_matvec", 32, 1, "FP64 CG with a double-float matvec (48-bit) + FP32 V-cycle")]
+
+
+# DRAM bytes (read + write) of one Chebyshev step of the staged FP32 kernel at
+# 64^3 cells, k_p = 3, from one ncu capture (second launch on the finest
+# level, with a previous iterate)
+SMOOTHER_TRAFFIC = 203.45e6 + 40.50e6
+
+
+def mg_smoother_step():
+    """One Jacobi-Chebyshev smoothing step of the FP32 multigrid on the finest
+    level of the 64^3, k_p = 3 Poisson workload (Sec. 3.3; the level operator
+    with the update fused into its epilogue): x_new = x + c1 (x - x_prev) +
+    c2 D^-1 (b - L x), 16 algorithmic bytes per DoF (read x, x_prev, b; write
+    x_new).  The built-in kernel (staged by tensor copies) against the line
+    kernel it replaced, CUDA events after an L2 flush, mean of 20."""
+    from paper_1802_01439_gb300 import opbench
+    peak, src = read_peaks()
+    out = {"workload": "64^3 cells, k_p=3 (16,777,216 DoFs), FP32", "bytes_per_dof": 16}
+    for key, kern in (("staged", 0), ("line", -1)):
+        r = opbench.run("cheb32", 3, 64, 20, 3, f32_kernel=kern)
+        gbs = 16 * r["dofs"] / (r["ms_mean"] * 1e-3) / 1e9
+        out[key] = {"us": round(r["ms_mean"] * 1e3, 2), "GBps": round(gbs, 1), "frac": round(gbs / peak, 4)}
+    out["staged"]["kernel"] = "sipg_tma_kernel<EPI_CHEB, 1, packed, 12 warps, 1 stage>"
+    out["staged"]["traffic"] = SMOOTHER_TRAFFIC
+    out["peak"] = {"GBps": peak, "source": src}
+    return out
 
 
 def poisson_solve():

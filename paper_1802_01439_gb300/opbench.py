@@ -23,18 +23,20 @@ from paper_1802_01439_gb300 import Context, inputs  # noqa: E402
 
 # elements per direction giving ~16.8M scalar DoFs for k = 2..11
 SWEEP_N = {2: 85, 3: 64, 4: 51, 5: 43, 6: 37, 7: 32, 8: 28, 9: 26, 10: 23, 11: 21}
-OPS = ["laplace", "laplace32", "convective", "viscous", "helmholtz", "invmass", "mass",
+OPS = ["laplace", "laplace32", "cheb32", "convective", "viscous", "helmholtz", "invmass", "mass",
        "divergence", "gradient", "projection", "helmholtz_split", "projection_split"]
 
 
-def run(op, k, n, reps, warmup, ku=None, fp64_mode=0):
+def run(op, k, n, reps, warmup, ku=None, fp64_mode=0, f32_kernel=0):
     dev = torch.device("cuda")
     # scalar operators act on space U of a context with degree k
     kk = ku if ku is not None else k
     kp = max(kk - 1, 1)
-    mg = 32 if op == "laplace32" else 0
-    if op == "laplace32":       # FP32 level operator: pressure space of degree k
+    mg = 32 if op in ("laplace32", "cheb32") else 0
+    if op in ("laplace32", "cheb32"):   # FP32 level operator: pressure space of degree k
         ctx = Context(n, k, k, mg_precision=32, mg_coarse_n=n)
+        if ctx.lib.dgns_debug_laplace_f32_kernel(f32_kernel) != 0:
+            raise ValueError("unknown FP32 Laplace kernel %d" % f32_kernel)
     else:
         ctx = Context(n, kk, kp, mg_precision=mg, fp64_mode=fp64_mode)
     nu, np_ = ctx.n_u, ctx.n_p
@@ -49,6 +51,13 @@ def run(op, k, n, reps, warmup, ku=None, fp64_mode=0):
         y, dofs = torch.empty_like(x), np_
         fn = lambda: ctx.vmult_laplace_f32(y, x, 0)
         nbytes = 8 * np_
+    elif op == "cheb32":
+        # one Chebyshev smoothing step on the level: reads x, x_prev and b,
+        # writes x_new (16 bytes per DoF; the diagonal is one cell's table)
+        x, xp, b = rng(np_, 0).float(), rng(np_, 1).float(), rng(np_, 2).float()
+        y, dofs = torch.empty_like(x), np_
+        fn = lambda: ctx.mg_chebyshev_step_f32(y, x, xp, b, 0.37, 0.021, 0)
+        nbytes = 16 * np_
     elif op == "convective":
         u = torch.from_numpy(inputs.taylor_green((n,) * 3, (-np.pi,) * 3, (np.pi,) * 3, ctx.nodes_1d(0),
                                                  noise=1e-3, seed=0).ravel()).to(dev)
@@ -119,6 +128,8 @@ def run(op, k, n, reps, warmup, ku=None, fp64_mode=0):
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1))
     ms = float(np.mean(ts))
+    if op in ("laplace32", "cheb32"):
+        ctx.lib.dgns_debug_laplace_f32_kernel(0)
     ctx.close()
     return {"op": op, "k": k, "n_elem": n, "fp64_mode": fp64_mode, "dofs": dofs, "ms_mean": round(ms, 5),
             "ms_min": round(float(np.min(ts)), 5), "dofs_per_s": round(dofs / (ms * 1e-3), 1),
@@ -163,6 +174,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--sweep", action="store_true")
     ap.add_argument("--fp64-mode", type=int, default=0, help="0 native FP64, 1 double-float, 2 triple-float")
+    ap.add_argument("--f32-kernel", type=int, default=0,
+                    help="laplace32/cheb32: kernel of the FP32 level operator (dgns_debug_laplace_f32_kernel)")
     ap.add_argument("--ops", default="laplace,convective,laplace32,invmass,helmholtz")
     a = ap.parse_args()
     if a.sweep:
@@ -174,7 +187,10 @@ def main():
         print(json.dumps(poisson(a.n or 64, a.k, a.reps, 32 if a.fp64_mode == 1 else 64, a.fp64_mode)), flush=True)
         return
     n = a.n or SWEEP_N.get(a.k, 32)
-    print(json.dumps(run(a.op, a.k, n, a.reps, a.warmup, fp64_mode=a.fp64_mode)), flush=True)
+    r = run(a.op, a.k, n, a.reps, a.warmup, fp64_mode=a.fp64_mode, f32_kernel=a.f32_kernel)
+    if a.op in ("laplace32", "cheb32"):
+        r["f32_kernel"] = a.f32_kernel
+    print(json.dumps(r), flush=True)
 
 
 if __name__ == "__main__":
