@@ -1197,7 +1197,7 @@ int dgns_vjp_convective(dgns_ctx* c, double* grad_u3, const double* u3, const do
   DG_TRY(st.out(grad_u3, bu, &d));
   int rc = convective_vjp(c->m, (const double*)su, (const double*)sw, (double*)d, c->conv, c->s,
                           c->d.fp64_mode == 1);
-  if (rc == 7) return fail(DGNS_ERR_UNSUPPORTED, "convective VJP: supported for k <= 7");
+  if (rc == 7) return fail(DGNS_ERR_UNSUPPORTED, "convective VJP: unsupported degree or quadrature");
   DG_TRY(rc);
   return st.finish();
 }

@@ -38,27 +38,5 @@ int convective_launch(int part, const MeshDims& m, const double* u3, double* rfa
   return 7;
 }
 
-// The VJP kernel keeps u, w and their partial sweeps in shared memory:
-// k <= 7 (N <= 8).
-int convective_vjp(const MeshDims& m, const double* u3, const double* w3, double* dst3, const ConvHost& t,
-                   cudaStream_t s, bool emulated) {
-  const int N = t.N, Q = t.Q;
-#define DGNS_CONV_VJP(NV)                                                                          \
-  if (N == NV && Q == (3 * NV) / 2)                                                                \
-    return emulated ? launch_conv_vjp<DF64, NV, (3 * NV) / 2>(m, u3, w3, dst3, t, s)               \
-                    : launch_conv_vjp<F64, NV, (3 * NV) / 2>(m, u3, w3, dst3, t, s);               \
-  if (N == NV && Q == NV)                                                                          \
-    return emulated ? launch_conv_vjp<DF64, NV, NV>(m, u3, w3, dst3, t, s)                         \
-                    : launch_conv_vjp<F64, NV, NV>(m, u3, w3, dst3, t, s);
-  DGNS_CONV_VJP(2)
-  DGNS_CONV_VJP(3)
-  DGNS_CONV_VJP(4)
-  DGNS_CONV_VJP(5)
-  DGNS_CONV_VJP(6)
-  DGNS_CONV_VJP(7)
-  DGNS_CONV_VJP(8)
-#undef DGNS_CONV_VJP
-  return 7;
-}
 
 }  // namespace dgns

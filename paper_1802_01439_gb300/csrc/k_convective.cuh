@@ -1040,6 +1040,27 @@ struct VjpLayout {
   static constexpr int PER = UW + L1 + L2F + P + X + Y;
 };
 
+// Plane-first layout (from N = 9 on, where the swept layers above exceed the
+// shared memory): every quadrature plane z_q contracts u and w over z first
+// (9 fields of N^2), then over x (12 fields of Q N) and y (12 fields of Q^2),
+// the same flops as sweeping x, y, z over the whole cell, with per-plane
+// buffers only.  The result has its own region (the faces read u and w).
+template <int N, int Q>
+struct VjpLayoutPF {
+  static constexpr int N3 = N * N * N;
+  static constexpr int UW = 6 * N3;
+  static constexpr int OUT = 3 * N3;
+  static constexpr int ZB = 9 * N * N;
+  static constexpr int XB = 12 * Q * N;
+  static constexpr int P = 12 * Q * Q;
+  static constexpr int X = 3 * N * Q;
+  static constexpr int Y = 3 * N * N;
+  static constexpr int CELL = ZB + XB + P + X + Y;
+  static constexpr int FACE = 12 * Q * N + 12 * Q * Q + 3 * Q * Q;
+  static constexpr int WORK = CELL > FACE ? CELL : FACE;
+  static constexpr int PER = UW + OUT + WORK;
+};
+
 template <class V, int N, int Q>
 struct VjpTab {
   V S[Q * N];   // phi_j(x_q)
@@ -1050,15 +1071,17 @@ struct VjpTab {
 };
 
 // One cell per N^2 threads, EPB cells per block; arithmetic policy A (F64
-// or DF64), loads and stores in double.
-template <class A, int N, int Q>
+// or DF64), loads and stores in double; PF: the plane-first cell stage.
+template <class A, int N, int Q, bool PF = false>
 __global__ void __launch_bounds__(conv_cells_per_block<N>() * N * N)
     conv_vjp_kernel(const double* __restrict__ u3, const double* __restrict__ w3, double* __restrict__ dst3,
                     const __grid_constant__ VjpTab<typename A::V, N, Q> tb, const MeshDims m) {
   typedef typename A::V V;
   typedef typename A::Acc Acc;
   typedef VjpLayout<N, Q> LY;
+  typedef VjpLayoutPF<N, Q> LP;
   static_assert(sizeof(V) == sizeof(double), "8-byte values");
+  constexpr int PER = PF ? LP::PER : LY::PER;
   constexpr int NT = N * N, N3 = N * N * N, EPB = conv_cells_per_block<N>();
   constexpr int QNN = Q * N * N, QQN = Q * Q * N, QQ = Q * Q;
   V* sm = reinterpret_cast<V*>(dyn_smem());
@@ -1068,14 +1091,19 @@ __global__ void __launch_bounds__(conv_cells_per_block<N>() * N * N)
   const long long rem = m.E - c0;
   const int nvalid = rem < EPB ? (int)rem : EPB;
   const bool active = slot < nvalid;
-  V* sUW = sm + slot * LY::PER;   // u: [0, 3N3), w: [3N3, 6N3)
-  V* sL1 = sUW + LY::UW;          // u_S (3), w_S (3), w_D (3) : each Q N N
-  V* sL2 = sL1 + LY::L1;          // u_SS (3), w_DS (3), w_SD (3), w_SS (3) : each Q Q N
-  V* sP = sL2 + LY::L2F;          // u (3 Q Q), g (9 Q Q)
+  V* sUW = sm + slot * PER;       // u: [0, 3N3), w: [3N3, 6N3)
+  // whole-cell sweeps: L1 = u_S (3), w_S (3), w_D (3), each Q N N; L2 = u_SS
+  // (3), w_DS (3), w_SD (3), w_SS (3), each Q Q N; the result over L1, the
+  // faces over L2.  Plane-first: ZB, XB per plane, result and faces apart.
+  V* sL1 = sUW + LY::UW;
+  V* sL2 = sL1 + LY::L1;
+  V* sZ = sUW + LP::UW + LP::OUT;
+  V* sXB = sZ + LP::ZB;
+  V* sP = PF ? sXB + LP::XB : sL2 + LY::L2F;   // u (3 Q Q), g (9 Q Q)
   V* sX = sP + LY::P;
   V* sY = sX + LY::X;
-  V* sOut = sL1;
-  V* sFace = sL2;
+  V* sOut = PF ? sUW + LP::UW : sL1;
+  V* sFace = PF ? sZ : sL2;
 
   long long el = 0;
   int ex = 0, ey = 0, ez = 0;
@@ -1093,7 +1121,7 @@ __global__ void __launch_bounds__(conv_cells_per_block<N>() * N * N)
   }
   __syncthreads();
   // x-sweeps: u_S, w_S, w_D
-  if (active)
+  if (!PF && active)
     for (int it = t; it < 6 * N * N; it += NT) {
       const int f = it / (N * N), l = it - f * N * N;   // f < 3: u_c, else w_(f-3)
       V x[N];
@@ -1112,9 +1140,9 @@ __global__ void __launch_bounds__(conv_cells_per_block<N>() * N * N)
         if (f >= 3) sL1[(f + 3) * QNN + l * Q + q] = A::acc_get_norm(b);    // w_D
       }
     }
-  __syncthreads();
+  if (!PF) __syncthreads();
   // y-sweeps: u_SS, w_DS (from w_D), w_SD and w_SS (from w_S)
-  if (active)
+  if (!PF && active)
     for (int it = t; it < 6 * Q * N; it += NT) {
       const int f = it / (Q * N), l = it - f * Q * N;
       const int qx = l % Q, z = l / Q;
@@ -1152,14 +1180,64 @@ __global__ void __launch_bounds__(conv_cells_per_block<N>() * N * N)
         }
       }
     }
-  __syncthreads();
+  if (!PF) __syncthreads();
 
   Acc acc[3][N];
   const int tx = t % N, ty = t / N;
   for (int qz = 0; qz < Q; ++qz) {
+    if constexpr (PF) {
+      // P1, plane-first: z-contraction at z_q of u (S), w (S) and w (D) ...
+      if (active)
+        for (int it = t; it < 9 * N * N; it += NT) {
+          const int f = it / (N * N), l = it - f * (N * N);
+          const V* src = sUW + (f < 3 ? f : 3 + (f - 3) % 3) * N3 + l;
+          const V* T = f >= 6 ? tb.D : tb.S;
+          Acc a;
+          A::acc_first(a, T[qz * N], src[0]);
+#pragma unroll
+          for (int z = 1; z < N; ++z) A::acc_fma(a, T[qz * N + z], src[N * N * z]);
+          sZ[it] = A::acc_get_norm(a);
+        }
+      __syncthreads();
+      // ... then over x: u S; w_S D (-> g_cx), w_S S (-> g_cy), w_D S (-> g_cz)
+      if (active)
+        for (int it = t; it < 12 * N; it += NT) {
+          const int f = it / N, y = it - f * N;
+          const int zf = f < 3 ? f : (f < 9 ? 3 + (f - 3) % 3 : 6 + (f - 9));
+          const V* T = (f >= 3 && f < 6) ? tb.D : tb.S;
+          V x[N];
+          load_line<V, N>(sZ + zf * N * N, N * y, 1, x);
+#pragma unroll
+          for (int q = 0; q < Q; ++q) {
+            Acc a;
+            A::acc_first(a, T[q * N], x[0]);
+#pragma unroll
+            for (int j = 1; j < N; ++j) A::acc_fma(a, T[q * N + j], x[j]);
+            sXB[f * Q * N + q + Q * y] = A::acc_get_norm(a);
+          }
+        }
+      __syncthreads();
+      // ... then over y (D for g_cy), into the plane layout of P1 below
+      if (active)
+        for (int it = t; it < 12 * Q; it += NT) {
+          const int f = it / Q, qx = it - f * Q;
+          const int pf = f < 3 ? f : 3 + 3 * ((f - 3) % 3) + (f - 3) / 3;
+          const V* T = (f >= 6 && f < 9) ? tb.D : tb.S;
+          V x[N];
+          load_line<V, N>(sXB + f * Q * N, qx, Q, x);
+#pragma unroll
+          for (int q = 0; q < Q; ++q) {
+            Acc a;
+            A::acc_first(a, T[q * N], x[0]);
+#pragma unroll
+            for (int j = 1; j < N; ++j) A::acc_fma(a, T[q * N + j], x[j]);
+            sP[pf * QQ + qx + Q * q] = A::acc_get_norm(a);
+          }
+        }
+    }
     // P1: u (3) and g_cd (9) on the plane; g_cx from w_DS, g_cy from w_SD
     // (both S in z), g_cz from w_SS (D in z)
-    if (active)
+    if (!PF && active)
       for (int it = t; it < 12 * QQ; it += NT) {
         const int f = it / QQ, l = it - f * QQ;
         const V* src;
@@ -1410,7 +1488,7 @@ __global__ void __launch_bounds__(conv_cells_per_block<N>() * N * N)
       for (int i = t; i < N3; i += NT) dst3[(c * m.E + el) * N3 + i] = A::store(sOut[c * N3 + i]);
 }
 
-template <class A, int N, int Q>
+template <class A, int N, int Q, bool PF = false>
 int launch_conv_vjp(const MeshDims& m, const double* u3, const double* w3, double* dst3, const ConvHost& h,
                     cudaStream_t s) {
   VjpTab<typename A::V, N, Q> tb;
@@ -1424,14 +1502,14 @@ int launch_conv_vjp(const MeshDims& m, const double* u3, const double* w3, doubl
     tb.area[d] = tb.jac[d];
   }
   constexpr int EPB = conv_cells_per_block<N>();
-  const size_t smem = (size_t)EPB * VjpLayout<N, Q>::PER * sizeof(double);
+  const size_t smem = (size_t)EPB * (PF ? VjpLayoutPF<N, Q>::PER : VjpLayout<N, Q>::PER) * sizeof(double);
   if (smem > 232448) return 7;
-  if (cudaFuncSetAttribute(conv_vjp_kernel<A, N, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-      cudaSuccess)
+  if (cudaFuncSetAttribute(conv_vjp_kernel<A, N, Q, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
     return 2;
   if (m.E == 0) return 0;
   const long long blocks = (m.E + EPB - 1) / EPB;
-  conv_vjp_kernel<A, N, Q><<<(unsigned)blocks, EPB * N * N, smem, s>>>(u3, w3, dst3, tb, m);
+  conv_vjp_kernel<A, N, Q, PF><<<(unsigned)blocks, EPB * N * N, smem, s>>>(u3, w3, dst3, tb, m);
   return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }
 

@@ -38,12 +38,20 @@ def test_convective_vjp(n, k, field, mode):
     assert rel_err(host(g), dg.Convective(s).vjp(u, w)) <= 1e-12
 
 
-def test_convective_vjp_unsupported_degree():
-    from paper_1802_01439_gb300 import DgnsError
-    ctx = context((1, 1, 1), 9, 8, mg_precision=0)
-    x = torch.zeros(3 * ctx.n_u, dtype=torch.float64, device="cuda")
-    with pytest.raises(DgnsError):
-        ctx.vjp_convective(torch.empty_like(x), x, x.clone())
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("n,k,nq", [((1, 2, 1), 8, 0), ((2, 1, 1), 9, 0), ((1, 1, 2), 10, 0), ((1, 2, 1), 11, 0),
+                                    ((2, 1, 1), 9, 10), ((1, 1, 2), 11, 12)])
+def test_convective_vjp_high_degree(n, k, nq, mode):
+    """k = 8..11: the kernel contracts plane by plane (z first); over-integrated
+    (nq = 0: 3(k+1)/2 points) and with k + 1 points."""
+    ctx = context(n, k, k - 1, mg_precision=0, fp64_mode=mode, n_q_conv=nq)
+    s = dg.Space(dg.Mesh(n), k)
+    u = tgv_field(s, 1e-3, 0) if k % 2 else random_field(s, 3, 4)
+    w = random_field(s, 3, 5)
+    g = torch.empty(u.size, dtype=torch.float64, device="cuda")
+    ctx.vjp_convective(g, dev(u), dev(w))
+    C = dg.Convective(s, nq=nq if nq else None)
+    assert rel_err(host(g), C.vjp(u, w)) <= 1e-12
 
 
 @pytest.mark.parametrize("mode", [0, 1])
