@@ -519,17 +519,21 @@ def fused_vs_split(reps=5):
     operator-by-operator evaluation (Sec. 4.4), in native FP64 for every k of
     the sweep: the Helmholtz operator (one SIPG kernel with the mass term
     folded in, against the mass kernel, the viscous kernel and a vector
-    update) and the projection operator (one kernel for M + A_D + A_C,
-    against M, A_D and A_C in three passes and two vector updates).  Mean
-    event times with L2 flushed; ratio = split / fused."""
+    update), the projection operator (one kernel for M + A_D + A_C, against
+    M, A_D and A_C in three passes and two vector updates) and the SIPG
+    Laplacian (the fused element-centric kernel against the cell term, a
+    face kernel and a face-apply kernel; one scalar field).  Mean event
+    times with L2 flushed; ratio = split / fused."""
     from paper_1802_01439_gb300.opbench import run
-    out = {"workload": "3 components, ~16.8M scalar DoFs each, native FP64, L2 flushed, mean of %d" % reps}
+    out = {"workload": "~16.8M scalar DoFs per component (3 components, Laplace 1), native FP64, "
+                       "L2 flushed, mean of %d" % reps}
     for k, n in SWEEP:
         row = {}
-        for op in ("helmholtz", "helmholtz_split", "projection", "projection_split"):
+        for op in ("helmholtz", "helmholtz_split", "projection", "projection_split", "laplace", "laplace_split"):
             row[op + "_ms"] = run(op, k, n, reps, 2, fp64_mode=0)["ms_mean"]
         row["helmholtz_ratio"] = round(row["helmholtz_split_ms"] / row["helmholtz_ms"], 3)
         row["projection_ratio"] = round(row["projection_split_ms"] / row["projection_ms"], 3)
+        row["laplace_ratio"] = round(row["laplace_split_ms"] / row["laplace_ms"], 3)
         out["k%d" % k] = row
     return out
 

@@ -121,6 +121,15 @@ int dgns_nodes_1d(const dgns_ctx* ctx, int space, double* out);
  * equation, matrix L of Sec. 3.3) on one scalar field of `space`:
  * dst = L src.  FP64. */
 int dgns_vmult_laplace(dgns_ctx* ctx, double* dst, const double* src, int space);
+/* The same operator evaluated operator by operator, as the cell integrals
+ * and the interior-face terms of Sec. 3.2 in separate kernels (the cell
+ * stiffness term; a face kernel forming each face's jump and mean normal
+ * derivative on its lines, weighted by the tangential mass; a kernel adding
+ * the six faces' terms to every cell): the counterpart of the fused kernel
+ * behind dgns_vmult_laplace, for comparison.  Native FP64 in every
+ * fp64_mode.  Allocates a face buffer (6 n_elem_total (k+1)^2 doubles) at its
+ * first call, or when a larger space needs one. */
+int dgns_vmult_laplace_split(dgns_ctx* ctx, double* dst, const double* src, int space);
 /* Same operator in FP32 on multigrid level `level` (0 = coarsest, levels-1 =
  * the pressure space itself).  Device pointers only. */
 int dgns_vmult_laplace_f32(dgns_ctx* ctx, float* dst, const float* src, int level);

@@ -67,6 +67,7 @@ SIGNATURES = {
     "dgns_sizes": (_I, [_P, ctypes.POINTER(_LL), ctypes.POINTER(_LL)]),
     "dgns_nodes_1d": (_I, [_P, _I, _P]),
     "dgns_vmult_laplace": (_I, [_P, _P, _P, _I]),
+    "dgns_vmult_laplace_split": (_I, [_P, _P, _P, _I]),
     "dgns_vmult_laplace_f32": (_I, [_P, _P, _P, _I]),
     "dgns_laplace_diagonal": (_I, [_P, _P, _I]),
     "dgns_vmult_viscous": (_I, [_P, _P, _P]),

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libdgns.so")
-SOURCES = ["api.cu", "k_laplace.cu", "k_laplace_plane.cu", "k_laplace_tma.cu", "k_tensor.cu", "k_divgrad.cu", "k_convective.cu", "k_convective_vjp.cu", "k_convective_tf64.cu",
+SOURCES = ["api.cu", "k_laplace.cu", "k_laplace_plane.cu", "k_laplace_tma.cu", "k_laplace_split.cu", "k_tensor.cu", "k_divgrad.cu", "k_convective.cu", "k_convective_vjp.cu", "k_convective_tf64.cu",
            "k_blas.cu", "k_projection.cu", "noalloc.cu", "tables.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",

@@ -101,6 +101,14 @@ class Context:
                                           self._vec(src, n, name="src"), space))
         return dst
 
+    def vmult_laplace_split(self, dst, src, space=SPACE_P):
+        """The SIPG Laplacian as separate cell, face and face-apply kernels
+        (native FP64), for comparison with vmult_laplace."""
+        n = self.size(space)
+        check(self.lib.dgns_vmult_laplace_split(self.h, self._vec(dst, n, name="dst"),
+                                                self._vec(src, n, name="src"), space))
+        return dst
+
     def vmult_laplace_f32(self, dst, src, level):
         n = src.numel()
         check(self.lib.dgns_vmult_laplace_f32(self.h, self._vec(dst, n, torch.float32, "dst"),

@@ -438,6 +438,7 @@ void free_ctx(dgns_ctx* c) {
   dev_free(c->p);
   dev_free(c->Ap);
   dev_free(c->conv_face);
+  dev_free(c->lap_face);
   dev_free(c->red.part);
   dev_free(c->red.scal);
   if (c->h_scal) cudaFreeHost(c->h_scal);
@@ -921,6 +922,56 @@ int dgns_vmult_laplace(dgns_ctx* c, double* dst, const double* src, int space) {
   return lap_like(c, dst, src, space, 1, 1.0, 0.0);
 }
 
+static void build_broken_stiffness(const dgns_ctx* c, double coef, LapHost& L, int space);
+
+int dgns_vmult_laplace_split(dgns_ctx* c, double* dst, const double* src, int space) {
+  g_err.clear();
+  if (!c) return fail(DGNS_ERR_INVALID_ARG, "ctx is null");
+  DG_NONNULL(dst, src);
+  if (check_space(space)) return DGNS_ERR_INVALID_ARG;
+  const size_t bytes = (size_t)c->n[space] * sizeof(double);
+  if (overlaps(dst, bytes, src, bytes)) return fail(DGNS_ERR_ALIAS, "dst overlaps src");
+  const Space1D& s1 = c->sp1[space];
+  const int N = s1.N;
+  const size_t fbytes = (size_t)6 * c->m.E * N * N * sizeof(double);
+  if (c->lap_face_cap < fbytes) {
+    dev_free(c->lap_face);
+    c->lap_face = nullptr;
+    c->lap_face_cap = 0;
+    if (dev_malloc(&c->lap_face, fbytes) != cudaSuccess) {
+      c->lap_face = nullptr;
+      return fail(DGNS_ERR_OOM, "face buffer of the split SIPG evaluation");
+    }
+    c->lap_face_cap = fbytes;
+  }
+  Staged st(c);
+  const void* sv;
+  void* d;
+  DG_TRY(st.in(src, bytes, &sv));
+  DG_TRY(st.out(dst, bytes, &d));
+  if (!aligned16(d, sv)) return fail(DGNS_ERR_INVALID_ARG, "dst and src must be 16-byte aligned");
+  LapHost K;
+  build_broken_stiffness(c, 1.0, K, space);
+  SplitHost sh;
+  sh.N = N;
+  for (int i = 0; i < N; ++i) {
+    sh.d0[i] = (double)s1.d0[i];
+    sh.d1[i] = (double)s1.d1[i];
+  }
+  for (int i = 0; i < N * N; ++i) sh.M[i] = (double)s1.mass[i];
+  for (int dd = 0; dd < 3; ++dd) {
+    ld ht = 1.0L;
+    for (int e = 0; e < 3; ++e)
+      if (e != dd) ht *= (ld)c->h[e];
+    sh.ih[dd] = (double)(1.0L / (ld)c->h[dd]);
+    sh.tau[dd] = (double)((ld)c->d.penalty_factor * N * N / (ld)c->h[dd]);
+    sh.area[dd] = (double)ht;
+  }
+  DG_TRY(laplace_apply(false, c->m, 1, sv, d, K, EPI_NONE, EpiHost(), c->s, ARITH_F64));
+  DG_TRY(laplace_faces_apply(c->m, 1, (const double*)sv, c->lap_face, (double*)d, sh, c->s));
+  return st.finish();
+}
+
 int dgns_vmult_viscous(dgns_ctx* c, double* dst3, const double* src3) {
   g_err.clear();
   if (!c) return fail(DGNS_ERR_INVALID_ARG, "ctx is null");
@@ -1203,9 +1254,9 @@ int dgns_vjp_convective(dgns_ctx* c, double* grad_u3, const double* u3, const do
 }
 
 // Broken stiffness (cell terms of the SIPG form only) scaled by `coef`.
-static void build_broken_stiffness(const dgns_ctx* c, double coef, LapHost& L) {
-  build_lap(c->sp1[0], c->h, c->d.penalty_factor, coef, 0.0, L);
-  const Space1D& s = c->sp1[0];
+static void build_broken_stiffness(const dgns_ctx* c, double coef, LapHost& L, int space = DGNS_SPACE_U) {
+  build_lap(c->sp1[space], c->h, c->d.penalty_factor, coef, 0.0, L);
+  const Space1D& s = c->sp1[space];
   const int N = s.N;
   for (int d = 0; d < 3; ++d) {
     ld ht = 1.0L;

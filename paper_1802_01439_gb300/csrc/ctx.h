@@ -61,6 +61,8 @@ struct dgns_ctx {
   dgns::GradHost grad;
   dgns::ConvHost conv;
   double* conv_face = nullptr;  // face integrals of the convective term, 9 E N^2
+  double* lap_face = nullptr;   // face data of the split SIPG evaluation
+  size_t lap_face_cap = 0;      // its size in bytes
   dgns::ProjHost proj;
   // multigrid (pressure space)
   int mg_prec = 0;

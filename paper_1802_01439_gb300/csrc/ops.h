@@ -63,6 +63,18 @@ unsigned laplace_tma_timeouts();
 // dst = L src on ncomp scalar fields (cells of component c follow those of
 // component c-1); `fp32` selects float data, else double.
 // arith (double data only): an Arith; the emulated ones take EPI_NONE only.
+// Face data of the split SIPG evaluation (k_laplace_split.cu): phi_i'(0),
+// phi_i'(1), the 1D mass, and per direction 1/h_d, the penalty, the face area.
+struct SplitHost {
+  int N = 0;
+  double d0[MAXN], d1[MAXN], M[MAXN * MAXN];
+  double ih[3], tau[3], area[3];
+};
+// dst += the interior-face terms of the SIPG operator on ncomp fields of src
+// (the face kernel into fbuf, 6 N^2 doubles per cell, then the apply kernel).
+int laplace_faces_apply(const MeshDims& m, int ncomp, const double* src, double* fbuf, double* dst,
+                        const SplitHost& h, cudaStream_t s);
+
 int laplace_apply(bool fp32, const MeshDims& m, int ncomp, const void* src, void* dst,
                   const LapHost& tab, int epi, const EpiHost& ea, cudaStream_t s, int arith = ARITH_F64);
 

@@ -23,7 +23,7 @@ from paper_1802_01439_gb300 import Context, inputs  # noqa: E402
 
 # elements per direction giving ~16.8M scalar DoFs for k = 2..11
 SWEEP_N = {2: 85, 3: 64, 4: 51, 5: 43, 6: 37, 7: 32, 8: 28, 9: 26, 10: 23, 11: 21}
-OPS = ["laplace", "laplace32", "cheb32", "convective", "viscous", "helmholtz", "invmass", "mass",
+OPS = ["laplace", "laplace_split", "laplace32", "cheb32", "convective", "viscous", "helmholtz", "invmass", "mass",
        "divergence", "gradient", "projection", "helmholtz_split", "projection_split"]
 
 
@@ -42,9 +42,13 @@ def run(op, k, n, reps, warmup, ku=None, fp64_mode=0, f32_kernel=0):
     nu, np_ = ctx.n_u, ctx.n_p
     f64 = dict(dtype=torch.float64, device=dev)
     rng = lambda m, s: torch.from_numpy(inputs.uniform(s, m)).to(dev)
-    if op == "laplace":
+    if op in ("laplace", "laplace_split"):
+        # laplace_split: cell term, face kernel and face-apply kernel apart
         x, y, dofs = rng(nu, 0), torch.empty(nu, **f64), nu
-        fn = lambda: ctx.vmult_laplace(y, x, space=0)
+        if op == "laplace":
+            fn = lambda: ctx.vmult_laplace(y, x, space=0)
+        else:
+            fn = lambda: ctx.vmult_laplace_split(y, x, space=0)
         nbytes = 16 * nu
     elif op == "laplace32":
         x = rng(np_, 0).float()
