@@ -369,10 +369,12 @@ def e2e_sweep(sw, steps, warmup, world, stream):
     pinned host memory and every result ends there; the copies are inside
     the timing.  The host-to-device copies of all degrees are queued on one
     copy stream and the device-to-host copies on another, ordered against
-    the context's stream by events, so the copy engines move degree k+1's
-    inputs in and degree k-1's results out while the kernels of degree k
-    run (the library's calls with host pointers, which stage and wait per
-    call, would serialise them)."""
+    the context's stream by one event per vector, so the copy engines move
+    the next operators' inputs in and the previous operators' results out
+    while the kernels run: each operator waits only for its own input (the
+    Laplace operator for x, the convective term for u) and each result leaves
+    as soon as its operator is done (the library's calls with host pointers,
+    which stage and wait per call, would serialise them)."""
     import torch
     host = []
     for it in sw.items:
@@ -385,22 +387,25 @@ def e2e_sweep(sw, steps, warmup, world, stream):
     for rep in range(warmup + steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ev_in = [torch.cuda.Event() for _ in range(nk)]
-        ev_out = [torch.cuda.Event() for _ in range(nk)]
+        ev_x, ev_u, ev_y, ev_c = ([torch.cuda.Event() for _ in range(nk)] for _ in range(4))
         with torch.cuda.stream(h2d):
             for i, (it, (xh, _, uh, _)) in enumerate(zip(sw.items, host)):
                 it["x"].copy_(xh, non_blocking=True)
+                ev_x[i].record(h2d)
                 it["u"].copy_(uh, non_blocking=True)
-                ev_in[i].record(h2d)
+                ev_u[i].record(h2d)
         for i, it in enumerate(sw.items):
-            stream.wait_event(ev_in[i])
+            stream.wait_event(ev_x[i])
             it["ctx"].vmult_laplace(it["y"], it["x"], space=0)
+            ev_y[i].record(stream)
+            stream.wait_event(ev_u[i])
             it["ctx"].vmult_convective(it["c"], it["u"])
-            ev_out[i].record(stream)
+            ev_c[i].record(stream)
         with torch.cuda.stream(d2h):
             for i, (it, (_, yh, _, ch)) in enumerate(zip(sw.items, host)):
-                d2h.wait_event(ev_out[i])
+                d2h.wait_event(ev_y[i])
                 yh.copy_(it["y"], non_blocking=True)
+                d2h.wait_event(ev_c[i])
                 ch.copy_(it["c"], non_blocking=True)
         torch.cuda.synchronize()
         if rep >= warmup:
@@ -429,7 +434,7 @@ def gpu_arm(args, rank, world):
     ms = max_over_ranks(ms, world)
     table = sweep_table(sw, per_k, mode)
     roof = dominant_roofline(sw, per_k, mode)
-    e2e = e2e_sweep(sw, max(2, args.steps // 4), 1, world, stream)
+    e2e = e2e_sweep(sw, max(4, args.steps // 2), 2, world, stream)
     sw.close()
     del sw
     line = {
