@@ -274,6 +274,26 @@ int smooth(dgns_ctx* c, Level& L, void* x0, int steps, double range, void** resu
   const bool f32 = c->mg_prec == 32;
   const int N = c->N[DGNS_SPACE_P];
   double rho = 0, c1 = 0, c2 = 0;
+  if (f32 && steps >= 1 && steps <= SMOOTH_MAX_STEPS) {
+    // small levels: every step of the call in one launch
+    SmoothPlan plan;
+    plan.nsteps = steps;
+    plan.zero_guess = x0 == nullptr;
+    for (int k = 0; k < steps; ++k) {
+      cheb_coeffs(L.lambda_max, range, k, &rho, &c1, &c2);
+      plan.c1[k] = (float)c1;
+      plan.c2[k] = (float)c2;
+    }
+    void* out = (x0 == nullptr || x0 == L.xb) ? L.xa : L.xb;
+    const int rc = laplace_plane_smooth(L.m, (const float*)L.b, (const float*)x0, (float*)out,
+                                        (const float*)L.dinv, L.lap, plan, c->s);
+    if (rc >= 0) {
+      DG_TRY(rc);
+      *result = out;
+      return 0;
+    }
+    rho = c1 = c2 = 0;
+  }
   void* cur;
   void* oth;
   void* prev = nullptr;

@@ -32,6 +32,7 @@ using plane::Tab2;
 using plane::XNb;
 
 constexpr int PLANE_THREADS = 256;
+constexpr int SMOOTH_MAX_CELLS = 64;
 
 template <int EPI, int ZF, bool PK>
 __global__ void __launch_bounds__(PLANE_THREADS, 2)
@@ -98,6 +99,89 @@ __global__ void __launch_bounds__(PLANE_THREADS, 2)
   plane::store_plane(dst + off, O);
 }
 
+// Every Chebyshev step of one smoothing call on a level of at most 64 cells,
+// in one block (4 threads per cell) with the level in shared memory: three
+// buffers (current, previous and next iterate) of 64 floats per cell; the
+// neighbour planes come from shared memory, the arithmetic is the register
+// kernel's.  Replaces one launch per step on the coarsest levels, where every
+// launch is latency-bound.
+__global__ void __launch_bounds__(4 * SMOOTH_MAX_CELLS)
+    sipg_plane_smooth_kernel(const float* __restrict__ b, const float* __restrict__ x0, float* __restrict__ xout,
+                             const float* __restrict__ dinv, const __grid_constant__ Tab tb,
+                             const __grid_constant__ Tab2 tp, const MeshDims m, const int ncells,
+                             const __grid_constant__ SmoothPlan pl) {
+  float* sm = reinterpret_cast<float*>(dyn_smem());
+  const int c = threadIdx.x >> 2, z = threadIdx.x & 3;
+  const CellXYZ cx = cell_xyz((unsigned)c, m);
+  const int own = c * 64 + z * 16;
+  const int nb[6] = {(int)neighbor32<0>(cx, +1, m) * 64 + z * 16, (int)neighbor32<0>(cx, -1, m) * 64 + z * 16,
+                     (int)neighbor32<1>(cx, +1, m) * 64 + z * 16, (int)neighbor32<1>(cx, -1, m) * 64 + z * 16,
+                     (int)neighbor32<2>(cx, +1, m) * 64 + z * 16, (int)neighbor32<2>(cx, -1, m) * 64 + z * 16};
+  float* xc = sm;
+  float* xp = sm + ncells * 64;
+  float* xn = sm + 2 * ncells * 64;
+  float B[16], D[16];
+  plane::load_plane(b + own, B);
+  plane::load_plane(dinv + z * 16, D);
+  auto rd = [](const float* q, float (&v)[16]) {
+#pragma unroll
+    for (int i = 0; i < 16; i += 4) {
+      const float4 t = *reinterpret_cast<const float4*>(q + i);
+      v[i] = t.x, v[i + 1] = t.y, v[i + 2] = t.z, v[i + 3] = t.w;
+    }
+  };
+  auto wr = [](float* q, const float (&v)[16]) {
+#pragma unroll
+    for (int i = 0; i < 16; i += 4) *reinterpret_cast<float4*>(q + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+  };
+  int k0 = 0;
+  {
+    float X[16], Z[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) Z[i] = 0.f;
+    if (pl.zero_guess) {
+      // x_1 = c2 D^-1 b, the first step from x_0 = 0
+#pragma unroll
+      for (int i = 0; i < 16; ++i) X[i] = pl.c2[0] * D[i] * B[i];
+      k0 = 1;
+    } else {
+      plane::load_plane(x0 + own, X);
+    }
+    wr(xc + own, X);
+    wr(xp + own, Z);
+  }
+  __syncthreads();
+  for (int k = k0; k < pl.nsteps; ++k) {
+    float X[16], YP[16], YM[16], ZP[16], ZM[16], P[16];
+    rd(xc + own, X);
+    rd(xc + nb[2], YP);
+    rd(xc + nb[3], YM);
+    rd(xc + nb[4], ZP);
+    rd(xc + nb[5], ZM);
+    XNb n;
+    {
+      float Q[16];
+      rd(xc + nb[0], Q);
+      plane::xnb_from_plane(tb, Q, +1, n);
+      rd(xc + nb[1], Q);
+      plane::xnb_from_plane(tb, Q, -1, n);
+    }
+    rd(xp + own, P);
+    float2 Y[8];
+    plane::apply2<1>(tb, tp, z, X, n, YP, YM, ZP, ZM, Y);
+    const Epi e{nullptr, nullptr, nullptr, pl.c1[k], pl.c2[k]};
+    float O[16];
+    plane::epilogue2<EPI_CHEB>(e, X, Y, B, D, P, true, O);
+    wr(xn + own, O);
+    __syncthreads();
+    float* t = xp;
+    xp = xc;
+    xc = xn;
+    xn = t;
+  }
+  plane::store_plane(xout + own, *reinterpret_cast<const float(*)[16]>(xc + own));
+}
+
 std::atomic<int> g_variant{0};
 
 template <int EPI, int ZF, bool PK>
@@ -151,6 +235,22 @@ int laplace_plane_f32(const MeshDims& m, int ncomp, const float* src, float* dst
     case 3: return launch_epi<0, true>(epi, m, ncells, src, dst, tb, tp, ea, s);
   }
   return 1;
+}
+
+int laplace_plane_smooth(const MeshDims& m, const float* b, const float* x0, float* xout, const float* dinv,
+                         const LapHost& h, const SmoothPlan& plan, cudaStream_t s) {
+  const long long ncells = m.E;
+  if (h.N != 4 || g_variant.load() < 0 || ncells < 8 || ncells > SMOOTH_MAX_CELLS || ncells % 8 != 0 ||
+      plan.nsteps < 1 || plan.nsteps > SMOOTH_MAX_STEPS)
+    return -1;
+  if (!aligned32(b) || !aligned32(x0) || !aligned32(xout) || !aligned32(dinv)) return -1;
+  Tab tb;
+  plane::make_tab(h, tb);
+  Tab2 tp;
+  plane::make_tab2(tb, tp);
+  const size_t smem = (size_t)3 * ncells * 64 * sizeof(float);
+  sipg_plane_smooth_kernel<<<1, (unsigned)(4 * ncells), smem, s>>>(b, x0, xout, dinv, tb, tp, m, (int)ncells, plan);
+  return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }
 
 }  // namespace dgns

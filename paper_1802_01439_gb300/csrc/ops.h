@@ -52,6 +52,19 @@ int laplace_plane_f32(const MeshDims& m, int ncomp, const float* src, float* dst
 // with one stage and 12 warps per SM (4) or two stages and 7 warps (5), each
 // falling back to 1 where it does not apply.
 void laplace_plane_set_variant(int v);
+// A whole Chebyshev smoothing call on a level of 8..64 cells (multiple of 8)
+// at N = 4 in one block (k_laplace_plane.cu): nsteps steps with the
+// coefficients c1[k], c2[k] of step k; zero_guess: x_0 = 0 (x0 unused) and
+// the first step is x_1 = c2[0] D^-1 b.  xout may be x0.  -1 where it does
+// not apply (also under laplace_plane_set_variant(-1)).
+constexpr int SMOOTH_MAX_STEPS = 64;
+struct SmoothPlan {
+  int nsteps = 0;
+  int zero_guess = 0;
+  float c1[SMOOTH_MAX_STEPS], c2[SMOOTH_MAX_STEPS];
+};
+int laplace_plane_smooth(const MeshDims& m, const float* b, const float* x0, float* xout, const float* dinv,
+                         const LapHost& h, const SmoothPlan& plan, cudaStream_t s);
 // The same operator with its data staged in shared memory by tensor copies
 // (k_laplace_tma.cu): nx divisible by 8 and 32-byte aligned vectors, else -1;
 // variant 0 one stage and 12 warps per SM, 1 two stages and 7 warps.

@@ -181,6 +181,8 @@ def main():
     ap.add_argument("--f32-kernel", type=int, default=0,
                     help="laplace32/cheb32: kernel of the FP32 level operator (dgns_debug_laplace_f32_kernel)")
     ap.add_argument("--ops", default="laplace,convective,laplace32,invmass,helmholtz")
+    ap.add_argument("--mg-precision", type=int, default=0,
+                    help="poisson: 32 or 64 (default: 32 with --fp64-mode 1, else 64)")
     a = ap.parse_args()
     if a.sweep:
         for op in a.ops.split(","):
@@ -188,7 +190,8 @@ def main():
                 print(json.dumps(run(op, k, n, a.reps, a.warmup, fp64_mode=a.fp64_mode)), flush=True)
         return
     if a.op == "poisson":
-        print(json.dumps(poisson(a.n or 64, a.k, a.reps, 32 if a.fp64_mode == 1 else 64, a.fp64_mode)), flush=True)
+        mg = a.mg_precision or (32 if a.fp64_mode == 1 else 64)
+        print(json.dumps(poisson(a.n or 64, a.k, a.reps, mg, a.fp64_mode)), flush=True)
         return
     n = a.n or SWEEP_N.get(a.k, 32)
     r = run(a.op, a.k, n, a.reps, a.warmup, fp64_mode=a.fp64_mode, f32_kernel=a.f32_kernel)
