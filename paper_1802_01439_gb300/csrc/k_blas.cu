@@ -49,7 +49,21 @@ __global__ void __launch_bounds__(RT) sum_partial(const T* __restrict__ a, long 
                                                   double* __restrict__ part) {
   double s = 0.0;
   const long long stride = (long long)gridDim.x * RT;
-  for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < n; i += stride) s += (double)a[i];
+  if constexpr (sizeof(T) == 4) {
+    // FP32 data: a compensated (Neumaier) FP32 sum per thread, its two parts
+    // combined in FP64 for the block (one FP64 addition per thread instead of
+    // one per entry, which on this part would bind the kernel to the FP64
+    // pipe)
+    float hi = 0.f, lo = 0.f;
+    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < n; i += stride) {
+      const float v = (float)a[i], t = hi + v;
+      lo += fabsf(hi) >= fabsf(v) ? (hi - t) + v : (v - t) + hi;
+      hi = t;
+    }
+    s = (double)hi + (double)lo;
+  } else {
+    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < n; i += stride) s += (double)a[i];
+  }
   s = block_sum(s);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
@@ -99,8 +113,14 @@ template <class TI, class TO>
 __global__ void __launch_bounds__(RT) convert_shift_kernel(const TI* __restrict__ x, TO* __restrict__ y,
                                                            long long n, const double* __restrict__ scal,
                                                            int slot) {
-  const double mu = slot >= 0 ? scal[slot] / (double)n : 0.0;
   const long long stride = (long long)gridDim.x * RT;
+  if (slot < 0) {
+    // no shift: a plain conversion (an FP64 subtraction of zero per entry
+    // would cost the FP64 pipe as much as a pass over memory)
+    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < n; i += stride) y[i] = (TO)x[i];
+    return;
+  }
+  const double mu = scal[slot] / (double)n;
   for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < n; i += stride)
     y[i] = (TO)((double)x[i] - mu);
 }
