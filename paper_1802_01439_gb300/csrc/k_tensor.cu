@@ -234,16 +234,14 @@ __global__ void __launch_bounds__(tcells_per_block<N>() * N * N)
   }
 }
 
-// coarse = sum over the 8 children of (P_cz^T (x) P_cy^T (x) P_cx^T) fine_child;
-// the 8 children of the block's cells are read into shared memory in one
-// pass (one global-memory latency instead of eight)
+// coarse = sum over the 8 children of (P_cz^T (x) P_cy^T (x) P_cx^T) fine_child
 template <class T, int N>
 __global__ void __launch_bounds__(tcells_per_block<N>() * N * N)
     restrict_kernel(const T* __restrict__ fine, T* __restrict__ coarse, const __grid_constant__ Prol<T, N> tb,
                     const MeshDims mc, const long long ncoarse) {
   constexpr int NN = N * N, NNN = NN * N, EPB = tcells_per_block<N>();
-  T* sC = reinterpret_cast<T*>(dyn_smem());   // children [child][slot][NNN]
-  T* sA = sC + 8 * EPB * NNN;
+  T* sX = reinterpret_cast<T*>(dyn_smem());
+  T* sA = sX + EPB * NNN;
   T* sS = sA + EPB * NNN;
   const int slot = threadIdx.x / NN;
   const int l = threadIdx.x - slot * NN;
@@ -259,16 +257,13 @@ __global__ void __launch_bounds__(tcells_per_block<N>() * N * N)
     for (int i = l; i < NNN; i += NN) sS[off + i] = (T)0;
   }
   const long long nfx = 2 * mc.nx, nfy = 2 * mc.ny;
-  if (active)
-#pragma unroll
-    for (int child = 0; child < 8; ++child) {
-      const int cx = child & 1, cy = (child >> 1) & 1, cz = child >> 2;
-      const long long f = (2 * ci + cx) + nfx * ((2 * cj + cy) + nfy * (2 * ck + cz));
-      for (int i = l; i < NNN; i += NN) sC[(child * EPB + slot) * NNN + i] = fine[f * NNN + i];
-    }
   for (int child = 0; child < 8; ++child) {
     const int cx = child & 1, cy = (child >> 1) & 1, cz = child >> 2;
-    const T* sX = sC + child * EPB * NNN;
+    __syncthreads();
+    if (active) {
+      const long long f = (2 * ci + cx) + nfx * ((2 * cj + cy) + nfy * (2 * ck + cz));
+      for (int i = l; i < NNN; i += NN) sX[off + i] = fine[f * NNN + i];
+    }
     __syncthreads();
     if (active) {
       // transposed sweeps: y_j = sum_i P[i][j] x_i
@@ -353,7 +348,7 @@ int launch_restrict(const MeshDims& mc, const T* fine, T* coarse, const double* 
                     const double* P1, cudaStream_t s) {
   constexpr int NN = N * N, EPB = tcells_per_block<N>();
   if (mc.E == 0) return 0;
-  const size_t smem = (size_t)10 * EPB * NN * N * sizeof(T);
+  const size_t smem = (size_t)3 * EPB * NN * N * sizeof(T);
   if (cudaFuncSetAttribute(restrict_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess)
     return 2;
