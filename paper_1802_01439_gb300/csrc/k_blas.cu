@@ -4,6 +4,7 @@
 // are a significant part of the CG cost, so each pass does as much as it can),
 // precision conversions at the boundary of the mixed-precision V-cycle, and
 // the first Chebyshev step from a zero initial guess.
+#include <cstdint>
 #include "blas.h"
 
 namespace dgns {
@@ -240,10 +241,28 @@ int convert_shift(const void* x, bool x32, void* y, bool y32, long long n, const
   return status();
 }
 
+// The same for FP32 vectors in 16-byte pieces (n and nper multiples of 4,
+// 16-byte aligned vectors, n < 2^32): one 32-bit remainder per piece instead
+// of a 64-bit one per entry.
+__global__ void __launch_bounds__(RT) cheb_first4_kernel(const float4* __restrict__ b, const float* __restrict__ dinv,
+                                                         float4* __restrict__ x, unsigned n4, unsigned nper, float c) {
+  const unsigned stride = gridDim.x * RT;
+  for (unsigned i = blockIdx.x * RT + threadIdx.x; i < n4; i += stride) {
+    const unsigned k = (4u * i) % nper;
+    const float4 v = b[i];
+    x[i] = make_float4(c * dinv[k] * v.x, c * dinv[k + 1] * v.y, c * dinv[k + 2] * v.z, c * dinv[k + 3] * v.w);
+  }
+}
+
 int cheb_first(bool fp32, const void* b, const void* dinv, void* x, long long n, int nper, double c,
                cudaStream_t s) {
   const unsigned g = grid_for(n);
-  if (fp32)
+  const bool v4 = fp32 && n % 4 == 0 && nper % 4 == 0 && n < (1LL << 32) &&
+                  ((reinterpret_cast<uintptr_t>(b) | reinterpret_cast<uintptr_t>(x)) & 15) == 0;
+  if (v4)
+    cheb_first4_kernel<<<grid_for(n / 4), RT, 0, s>>>((const float4*)b, (const float*)dinv, (float4*)x,
+                                                      (unsigned)(n / 4), (unsigned)nper, (float)c);
+  else if (fp32)
     cheb_first_kernel<float><<<g, RT, 0, s>>>((const float*)b, (const float*)dinv, (float*)x, n, nper, (float)c);
   else
     cheb_first_kernel<double><<<g, RT, 0, s>>>((const double*)b, (const double*)dinv, (double*)x, n, nper, c);
