@@ -1109,10 +1109,11 @@ __global__ void __launch_bounds__(conv_cells_per_block<N>() * N * N)
   int ex = 0, ey = 0, ez = 0;
   if (active) {
     el = c0 + slot;
-    ex = (int)(el % m.nx);
-    const long long tt = el / m.nx;
-    ey = (int)(tt % m.ny);
-    ez = (int)(tt / m.ny);
+    const unsigned eu = (unsigned)el, nxu = (unsigned)m.nx, nyu = (unsigned)m.ny;
+    ex = (int)(eu % nxu);
+    const unsigned tt = eu / nxu;
+    ey = (int)(tt % nyu);
+    ez = (int)(tt / nyu);
     for (int c = 0; c < 3; ++c)
       for (int i = t; i < N3; i += NT) {
         sUW[c * N3 + i] = A::load(u3 + (c * m.E + el) * N3 + i);

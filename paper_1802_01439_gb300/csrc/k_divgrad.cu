@@ -179,10 +179,12 @@ struct CellPos {
 __device__ __forceinline__ CellPos cell_pos(long long el, const MeshDims& m) {
   CellPos p;
   p.el = el;
-  p.ex = (int)(el % m.nx);
-  const long long t = el / m.nx;
-  p.ey = (int)(t % m.ny);
-  p.ez = (int)(t / m.ny);
+  // 32-bit arithmetic (a 64-bit division is a long software sequence)
+  const unsigned eu = (unsigned)el, nxu = (unsigned)m.nx, nyu = (unsigned)m.ny;
+  p.ex = (int)(eu % nxu);
+  const unsigned t = eu / nxu;
+  p.ey = (int)(t % nyu);
+  p.ez = (int)(t / nyu);
   return p;
 }
 

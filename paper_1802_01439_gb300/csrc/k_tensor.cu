@@ -206,10 +206,12 @@ __global__ void __launch_bounds__(tcells_per_block<N>() * N * N)
   const int nfx = 2 * mc.nx, nfy = 2 * mc.ny;
   int cx = 0, cy = 0, cz = 0;
   if (active) {
-    const int fi = (int)(f % nfx);
-    const long long t = f / nfx;
-    const int fj = (int)(t % nfy);
-    const int fk = (int)(t / nfy);
+    // 32-bit arithmetic (a 64-bit division is a long software sequence)
+    const unsigned fu = (unsigned)f, nfxu = (unsigned)nfx, nfyu = (unsigned)nfy;
+    const int fi = (int)(fu % nfxu);
+    const unsigned t = fu / nfxu;
+    const int fj = (int)(t % nfyu);
+    const int fk = (int)(t / nfyu);
     cx = fi & 1;
     cy = fj & 1;
     cz = fk & 1;
@@ -250,10 +252,11 @@ __global__ void __launch_bounds__(tcells_per_block<N>() * N * N)
   const int off = slot * NNN;
   int ci = 0, cj = 0, ck = 0;
   if (active) {
-    ci = (int)(c % mc.nx);
-    const long long t = c / mc.nx;
-    cj = (int)(t % mc.ny);
-    ck = (int)(t / mc.ny);
+    const unsigned cu = (unsigned)c, nxu = (unsigned)mc.nx, nyu = (unsigned)mc.ny;
+    ci = (int)(cu % nxu);
+    const unsigned t = cu / nxu;
+    cj = (int)(t % nyu);
+    ck = (int)(t / nyu);
     for (int i = l; i < NNN; i += NN) sS[off + i] = (T)0;
   }
   const long long nfx = 2 * mc.nx, nfy = 2 * mc.ny;
