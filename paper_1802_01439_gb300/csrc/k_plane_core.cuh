@@ -361,15 +361,14 @@ __device__ __forceinline__ void reduce_scatter4(float2 (&V)[4][8]) {
     V[0][k] = add2(V[0][k], make_float2(__shfl_xor_sync(FULL, V[1][k].x, 1), __shfl_xor_sync(FULL, V[1][k].y, 1)));
 }
 
-// Packed form of apply (same arguments, same results).
-template <int ZF>
-__device__ __forceinline__ void apply2(const Tab& tb, const Tab2& tp, int z, const float (&Xs)[16], const XNb& n,
-                                       const float (&YPs)[16], const float (&YMs)[16], const float (&ZPs)[16],
-                                       const float (&ZMs)[16], float2 (&Y)[8]) {
-  float2 X[8], YP[8], YM[8];
+// Packed form of apply (same results), the neighbour planes fetched where
+// they are used: get(i, v) fills v with plane z of the +y (i = 0), -y (1),
+// +z (2) or -z (3) neighbour.
+template <int ZF, class Get>
+__device__ __forceinline__ void apply2g(const Tab& tb, const Tab2& tp, int z, const float (&Xs)[16], const XNb& n,
+                                        Get&& get, float2 (&Y)[8]) {
+  float2 X[8];
   pack(Xs, X);
-  pack(YPs, YP);
-  pack(YMs, YM);
   float2 W[8];
   {
     float2 T[8];   // T_x x: row y, output pair h
@@ -396,6 +395,14 @@ __device__ __forceinline__ void apply2(const Tab& tb, const Tab2& tp, int z, con
         for (int j = 1; j < 4; ++j) a = fma2(tp.Mb[4 * y + j], T[2 * j + h], a);
         W[2 * y + h] = a;
       }
+  }
+  float2 YP[8], YM[8];
+  {
+    float t[16];
+    get(0, t);
+    pack(t, YP);
+    get(1, t);
+    pack(t, YM);
   }
   {
     float2 T[8];   // T_y x: output row i, column pair h
@@ -442,8 +449,13 @@ __device__ __forceinline__ void apply2(const Tab& tb, const Tab2& tp, int z, con
     clz[t] = bc((z == 3 ? tb.cl[2][i] : 0.f) + (i == 0 ? tb.gl[2][z] : 0.f));
   }
   float2 ZP[8], ZM[8];
-  pack(ZPs, ZP);
-  pack(ZMs, ZM);
+  {
+    float t[16];
+    get(2, t);
+    pack(t, ZP);
+    get(3, t);
+    pack(t, ZM);
+  }
   if constexpr (ZF == 0) {
     float2 Q[8], R[8], L[8];
     mass_xy2(tp, X, Q);
@@ -477,6 +489,20 @@ __device__ __forceinline__ void apply2(const Tab& tb, const Tab2& tp, int z, con
 #pragma unroll
     for (int k = 0; k < 8; ++k) Y[k] = add2(V[0][k], S[k]);
   }
+}
+
+// Packed form of apply with the neighbour planes in registers.
+template <int ZF>
+__device__ __forceinline__ void apply2(const Tab& tb, const Tab2& tp, int z, const float (&Xs)[16], const XNb& n,
+                                       const float (&YPs)[16], const float (&YMs)[16], const float (&ZPs)[16],
+                                       const float (&ZMs)[16], float2 (&Y)[8]) {
+  apply2g<ZF>(tb, tp, z, Xs, n,
+              [&](int i, float (&v)[16]) {
+                const float(&src)[16] = i == 0 ? YPs : (i == 1 ? YMs : (i == 2 ? ZPs : ZMs));
+#pragma unroll
+                for (int k = 0; k < 16; ++k) v[k] = src[k];
+              },
+              Y);
 }
 
 // Packed form of epilogue.
