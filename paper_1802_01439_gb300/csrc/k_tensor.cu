@@ -190,135 +190,157 @@ struct Prol {
   T P[2][N * N];  // P[c][i*N+j] = phi_j((xi_i + c)/2)
 };
 
-// One block per EPB fine cells; each fine cell reads its parent.
+// Transfers per coarse cell with the 1D operators factored across the eight
+// children (prolongation: x-sweep into the two x-halves, y-sweep into four,
+// z-sweep into the eight children, written straight to the fine vector;
+// restriction in the reverse order): 14 N^4 multiply-adds per coarse cell
+// instead of 24 N^4, every coarse value read or written once.  Threads per
+// coarse cell: N^3 (N <= 5) or N^2; the 1D tables sit in shared memory
+// (items of a warp index them by different output nodes).
+template <int N>
+constexpr int xfer_threads() {
+  return N * N * N <= 128 ? N * N * N : N * N;
+}
+template <int N>
+constexpr int xfer_cells_per_block() {
+  return xfer_threads<N>() >= 256 ? 1 : 256 / xfer_threads<N>();
+}
+
 template <class T, int N, bool ADD>
-__global__ void __launch_bounds__(tcells_per_block<N>() * N * N)
-    prolong_kernel(const T* __restrict__ coarse, T* __restrict__ fine, const __grid_constant__ Prol<T, N> tb,
-                   const MeshDims mc, const long long nfine) {
-  constexpr int NN = N * N, NNN = NN * N, EPB = tcells_per_block<N>();
-  T* sX = reinterpret_cast<T*>(dyn_smem());
-  T* sA = sX + EPB * NNN;
-  const int slot = threadIdx.x / NN;
-  const int l = threadIdx.x - slot * NN;
-  const long long f = (long long)blockIdx.x * EPB + slot;
-  const bool active = f < nfine;
-  const int off = slot * NNN;
-  const int nfx = 2 * mc.nx, nfy = 2 * mc.ny;
-  int cx = 0, cy = 0, cz = 0;
+__global__ void __launch_bounds__(xfer_cells_per_block<N>() * xfer_threads<N>())
+    prolong_cell_kernel(const T* __restrict__ coarse, T* __restrict__ fine, const __grid_constant__ Prol<T, N> tb,
+                        const MeshDims mc, const long long ncoarse) {
+  constexpr int NN = N * N, N3 = NN * N, TPC = xfer_threads<N>(), CPB = xfer_cells_per_block<N>();
+  T* sP = reinterpret_cast<T*>(dyn_smem());   // P[c][j N + i], 2 N^2
+  T* sm = sP + 2 * NN;
+  const int slot = threadIdx.x / TPC, t = threadIdx.x - slot * TPC;
+  const long long c = (long long)blockIdx.x * CPB + slot;
+  const bool active = c < ncoarse;
+  T* sC = sm + slot * 7 * N3;   // coarse cell [z][y][x]
+  T* sA = sC + N3;              // [cx][z][y][x]
+  T* sB = sA + 2 * N3;          // [cx + 2 cy][z][y][x]
+  for (int i = threadIdx.x; i < 2 * NN; i += blockDim.x) sP[i] = tb.P[i / NN][i % NN];
+  if (active)
+    for (int i = t; i < N3; i += TPC) sC[i] = coarse[c * N3 + i];
+  __syncthreads();
+  if (active)
+    for (int it = t; it < 2 * N3; it += TPC) {
+      const int cx = it / N3, r = it - cx * N3, j = r % N, line = r / N;
+      const T* P = sP + cx * NN + j * N;
+      T a = P[0] * sC[line * N];
+#pragma unroll
+      for (int i = 1; i < N; ++i) a = fma(P[i], sC[line * N + i], a);
+      sA[it] = a;
+    }
+  __syncthreads();
+  if (active)
+    for (int it = t; it < 4 * N3; it += TPC) {
+      const int q = it / N3, r = it - q * N3;
+      const int cx = q & 1, cy = q >> 1;
+      const int x = r % N, j = (r / N) % N, z = r / NN;
+      const T* P = sP + cy * NN + j * N;
+      const T* src = sA + cx * N3 + x + NN * z;
+      T a = P[0] * src[0];
+#pragma unroll
+      for (int i = 1; i < N; ++i) a = fma(P[i], src[N * i], a);
+      sB[it] = a;
+    }
+  __syncthreads();
   if (active) {
-    // 32-bit arithmetic (a 64-bit division is a long software sequence)
-    const unsigned fu = (unsigned)f, nfxu = (unsigned)nfx, nfyu = (unsigned)nfy;
-    const int fi = (int)(fu % nfxu);
-    const unsigned t = fu / nfxu;
-    const int fj = (int)(t % nfyu);
-    const int fk = (int)(t / nfyu);
-    cx = fi & 1;
-    cy = fj & 1;
-    cz = fk & 1;
-    const long long p = (fi >> 1) + (long long)mc.nx * ((fj >> 1) + (long long)mc.ny * (fk >> 1));
-    for (int i = l; i < NNN; i += NN) sX[off + i] = coarse[p * NNN + i];
-  }
-  __syncthreads();
-  if (active) sweep_line<T, N, 0>(sX + off, sA + off, l, tb.P[cx]);
-  __syncthreads();
-  if (active) sweep_line<T, N, 1>(sA + off, sA + off, l, tb.P[cy]);
-  __syncthreads();
-  if (active) sweep_line<T, N, 2>(sA + off, sX + off, l, tb.P[cz]);
-  __syncthreads();
-  const long long c0 = (long long)blockIdx.x * EPB;
-  const long long rem = nfine - c0;
-  const int nvalid = rem < EPB ? (int)rem : EPB;
-  for (int i = threadIdx.x; i < nvalid * NNN; i += blockDim.x) {
-    if (ADD)
-      fine[c0 * NNN + i] += sX[i];
-    else
-      fine[c0 * NNN + i] = sX[i];
+    const unsigned cu = (unsigned)c, nxu = (unsigned)mc.nx, nyu = (unsigned)mc.ny;
+    const int ci = (int)(cu % nxu);
+    const unsigned tt = cu / nxu;
+    const int cj = (int)(tt % nyu), ck = (int)(tt / nyu);
+    const long long nfx = 2 * mc.nx, nfy = 2 * mc.ny;
+    for (int it = t; it < 8 * N3; it += TPC) {
+      const int ch = it / N3, r = it - ch * N3;
+      const int cx = ch & 1, cy = (ch >> 1) & 1, cz = ch >> 2;
+      const int xy = r % NN, j = r / NN;
+      const T* P = sP + cz * NN + j * N;
+      const T* src = sB + (cx + 2 * cy) * N3 + xy;
+      T a = P[0] * src[0];
+#pragma unroll
+      for (int i = 1; i < N; ++i) a = fma(P[i], src[NN * i], a);
+      const long long f = (2 * ci + cx) + nfx * ((2 * cj + cy) + nfy * (2 * ck + cz));
+      if (ADD)
+        fine[f * N3 + r] += a;
+      else
+        fine[f * N3 + r] = a;
+    }
   }
 }
 
-// coarse = sum over the 8 children of (P_cz^T (x) P_cy^T (x) P_cx^T) fine_child
 template <class T, int N>
-__global__ void __launch_bounds__(tcells_per_block<N>() * N * N)
-    restrict_kernel(const T* __restrict__ fine, T* __restrict__ coarse, const __grid_constant__ Prol<T, N> tb,
-                    const MeshDims mc, const long long ncoarse) {
-  constexpr int NN = N * N, NNN = NN * N, EPB = tcells_per_block<N>();
-  T* sX = reinterpret_cast<T*>(dyn_smem());
-  T* sA = sX + EPB * NNN;
-  T* sS = sA + EPB * NNN;
-  const int slot = threadIdx.x / NN;
-  const int l = threadIdx.x - slot * NN;
-  const long long c = (long long)blockIdx.x * EPB + slot;
+__global__ void __launch_bounds__(xfer_cells_per_block<N>() * xfer_threads<N>())
+    restrict_cell_kernel(const T* __restrict__ fine, T* __restrict__ coarse, const __grid_constant__ Prol<T, N> tb,
+                         const MeshDims mc, const long long ncoarse) {
+  constexpr int NN = N * N, N3 = NN * N, TPC = xfer_threads<N>(), CPB = xfer_cells_per_block<N>();
+  T* sP = reinterpret_cast<T*>(dyn_smem());
+  T* sm = sP + 2 * NN;
+  const int slot = threadIdx.x / TPC, t = threadIdx.x - slot * TPC;
+  const long long c = (long long)blockIdx.x * CPB + slot;
   const bool active = c < ncoarse;
-  const int off = slot * NNN;
-  int ci = 0, cj = 0, ck = 0;
+  T* sC = sm + slot * 14 * N3;   // children [cx + 2 cy + 4 cz][z][y][x]
+  T* sB = sC + 8 * N3;           // [cx + 2 cy][z'][y][x]
+  T* sA = sB + 4 * N3;           // [cx][z'][y'][x]
+  for (int i = threadIdx.x; i < 2 * NN; i += blockDim.x) sP[i] = tb.P[i / NN][i % NN];
   if (active) {
     const unsigned cu = (unsigned)c, nxu = (unsigned)mc.nx, nyu = (unsigned)mc.ny;
-    ci = (int)(cu % nxu);
-    const unsigned t = cu / nxu;
-    cj = (int)(t % nyu);
-    ck = (int)(t / nyu);
-    for (int i = l; i < NNN; i += NN) sS[off + i] = (T)0;
-  }
-  const long long nfx = 2 * mc.nx, nfy = 2 * mc.ny;
-  for (int child = 0; child < 8; ++child) {
-    const int cx = child & 1, cy = (child >> 1) & 1, cz = child >> 2;
-    __syncthreads();
-    if (active) {
+    const int ci = (int)(cu % nxu);
+    const unsigned tt = cu / nxu;
+    const int cj = (int)(tt % nyu), ck = (int)(tt / nyu);
+    const long long nfx = 2 * mc.nx, nfy = 2 * mc.ny;
+    for (int it = t; it < 8 * N3; it += TPC) {
+      const int ch = it / N3, r = it - ch * N3;
+      const int cx = ch & 1, cy = (ch >> 1) & 1, cz = ch >> 2;
       const long long f = (2 * ci + cx) + nfx * ((2 * cj + cy) + nfy * (2 * ck + cz));
-      for (int i = l; i < NNN; i += NN) sX[off + i] = fine[f * NNN + i];
-    }
-    __syncthreads();
-    if (active) {
-      // transposed sweeps: y_j = sum_i P[i][j] x_i
-      int base, stride;
-      line_geom<0>(l, N, N, N, base, stride);
-      T x[N], y[N];
-      load_line<T, N>(sX + off, base, stride, x);
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        T acc = tb.P[cx][j] * x[0];
-#pragma unroll
-        for (int i = 1; i < N; ++i) acc = fma(tb.P[cx][i * N + j], x[i], acc);
-        y[j] = acc;
-      }
-      store_line<T, N>(sA + off, base, stride, y);
-    }
-    __syncthreads();
-    if (active) {
-      int base, stride;
-      line_geom<1>(l, N, N, N, base, stride);
-      T x[N], y[N];
-      load_line<T, N>(sA + off, base, stride, x);
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        T acc = tb.P[cy][j] * x[0];
-#pragma unroll
-        for (int i = 1; i < N; ++i) acc = fma(tb.P[cy][i * N + j], x[i], acc);
-        y[j] = acc;
-      }
-      store_line<T, N>(sA + off, base, stride, y);
-    }
-    __syncthreads();
-    if (active) {
-      int base, stride;
-      line_geom<2>(l, N, N, N, base, stride);
-      T x[N], y[N];
-      load_line<T, N>(sA + off, base, stride, x);
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        T acc = sS[off + base + j * stride];
-#pragma unroll
-        for (int i = 0; i < N; ++i) acc = fma(tb.P[cz][i * N + j], x[i], acc);
-        y[j] = acc;
-      }
-      store_line<T, N>(sS + off, base, stride, y);
+      sC[it] = fine[f * N3 + r];
     }
   }
   __syncthreads();
-  const long long c0 = (long long)blockIdx.x * EPB;
-  const long long rem = ncoarse - c0;
-  const int nvalid = rem < EPB ? (int)rem : EPB;
-  for (int i = threadIdx.x; i < nvalid * NNN; i += blockDim.x) coarse[c0 * NNN + i] = sS[i];
+  // z: B[q][j][y][x] = sum_cz sum_i P[cz][i][j] C[q + 4 cz][i][y][x]
+  if (active)
+    for (int it = t; it < 4 * N3; it += TPC) {
+      const int q = it / N3, r = it - q * N3;
+      const int xy = r % NN, j = r / NN;
+      T a = (T)0;
+#pragma unroll
+      for (int cz = 0; cz < 2; ++cz) {
+        const T* src = sC + (q + 4 * cz) * N3 + xy;
+#pragma unroll
+        for (int i = 0; i < N; ++i) a = fma(sP[cz * NN + i * N + j], src[NN * i], a);
+      }
+      sB[it] = a;
+    }
+  __syncthreads();
+  // y: A[cx][z][j][x] = sum_cy sum_i P[cy][i][j] B[cx + 2 cy][z][i][x]
+  if (active)
+    for (int it = t; it < 2 * N3; it += TPC) {
+      const int cx = it / N3, r = it - cx * N3;
+      const int x = r % N, j = (r / N) % N, z = r / NN;
+      T a = (T)0;
+#pragma unroll
+      for (int cy = 0; cy < 2; ++cy) {
+        const T* src = sB + (cx + 2 * cy) * N3 + x + NN * z;
+#pragma unroll
+        for (int i = 0; i < N; ++i) a = fma(sP[cy * NN + i * N + j], src[N * i], a);
+      }
+      sA[it] = a;
+    }
+  __syncthreads();
+  // x: coarse[z][y][j] = sum_cx sum_i P[cx][i][j] A[cx][z][y][i]
+  if (active)
+    for (int r = t; r < N3; r += TPC) {
+      const int j = r % N, line = r / N;
+      T a = (T)0;
+#pragma unroll
+      for (int cx = 0; cx < 2; ++cx) {
+        const T* src = sA + cx * N3 + line * N;
+#pragma unroll
+        for (int i = 0; i < N; ++i) a = fma(sP[cx * NN + i * N + j], src[i], a);
+      }
+      coarse[c * N3 + r] = a;
+    }
 }
 
 template <class T, int N>
@@ -334,30 +356,30 @@ Prol<T, N> make_prol(const double* P0, const double* P1) {
 template <class T, int N>
 int launch_prolong(const MeshDims& mc, const T* coarse, T* fine, const double* P0,
                    const double* P1, bool add, cudaStream_t s) {
-  constexpr int NN = N * N, EPB = tcells_per_block<N>();
-  const long long nfine = 8 * mc.E;
-  if (nfine == 0) return 0;
-  const size_t smem = (size_t)2 * EPB * NN * N * sizeof(T);
-  auto kern = add ? prolong_kernel<T, N, true> : prolong_kernel<T, N, false>;
+  constexpr int TPC = xfer_threads<N>(), CPB = xfer_cells_per_block<N>();
+  if (mc.E == 0) return 0;
+  const size_t smem = (size_t)(2 * N * N + CPB * 7 * N * N * N) * sizeof(T);
+  auto kern = add ? prolong_cell_kernel<T, N, true> : prolong_cell_kernel<T, N, false>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return 2;
-  const long long blocks = (nfine + EPB - 1) / EPB;
-  kern<<<(unsigned)blocks, EPB * NN, smem, s>>>(coarse, fine, make_prol<T, N>(P0, P1), mc, nfine);
+  const long long blocks = (mc.E + CPB - 1) / CPB;
+  kern<<<(unsigned)blocks, CPB * TPC, smem, s>>>(coarse, fine, make_prol<T, N>(P0, P1), mc, mc.E);
   return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }
 
 template <class T, int N>
 int launch_restrict(const MeshDims& mc, const T* fine, T* coarse, const double* P0,
                     const double* P1, cudaStream_t s) {
-  constexpr int NN = N * N, EPB = tcells_per_block<N>();
+  constexpr int TPC = xfer_threads<N>(), CPB = xfer_cells_per_block<N>();
   if (mc.E == 0) return 0;
-  const size_t smem = (size_t)3 * EPB * NN * N * sizeof(T);
-  if (cudaFuncSetAttribute(restrict_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const size_t smem = (size_t)(2 * N * N + CPB * 14 * N * N * N) * sizeof(T);
+  if (smem > 232448) return 7;
+  if (cudaFuncSetAttribute(restrict_cell_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess)
     return 2;
-  const long long blocks = (mc.E + EPB - 1) / EPB;
-  restrict_kernel<T, N><<<(unsigned)blocks, EPB * NN, smem, s>>>(fine, coarse, make_prol<T, N>(P0, P1), mc,
-                                                                 mc.E);
+  const long long blocks = (mc.E + CPB - 1) / CPB;
+  restrict_cell_kernel<T, N><<<(unsigned)blocks, CPB * TPC, smem, s>>>(fine, coarse, make_prol<T, N>(P0, P1), mc,
+                                                                     mc.E);
   return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }
 
