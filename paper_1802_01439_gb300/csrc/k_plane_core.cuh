@@ -364,12 +364,12 @@ __device__ __forceinline__ void reduce_scatter4(float2 (&V)[4][8]) {
 // Packed form of apply (same results), the neighbour planes fetched where
 // they are used: get(i, v) fills v with plane z of the +y (i = 0), -y (1),
 // +z (2) or -z (3) neighbour.
-template <int ZF, class Get>
-__device__ __forceinline__ void apply2g(const Tab& tb, const Tab2& tp, int z, const float (&Xs)[16], const XNb& n,
-                                        Get&& get, float2 (&Y)[8]) {
+// The x- and y-part W = M_y T_x x + M_x T_y x (get(0), get(1) used).
+template <class Get>
+__device__ __forceinline__ void apply2_xy(const Tab2& tp, const float (&Xs)[16], const XNb& n, Get&& get,
+                                          float2 (&W)[8]) {
   float2 X[8];
   pack(Xs, X);
-  float2 W[8];
   {
     float2 T[8];   // T_x x: row y, output pair h
 #pragma unroll
@@ -438,6 +438,14 @@ __device__ __forceinline__ void apply2g(const Tab& tb, const Tab2& tp, int z, co
       }
     }
   }
+}
+
+// The z-part: Y = M_z W + M_x M_y T_z x (get(2), get(3) used).
+template <int ZF, class Get>
+__device__ __forceinline__ void apply2_z(const Tab& tb, const Tab2& tp, int z, const float (&Xs)[16],
+                                         const float2 (&W)[8], Get&& get, float2 (&Y)[8]) {
+  float2 X[8];
+  pack(Xs, X);
   // z-direction: the slot coefficients of apply, broadcast
   float2 mz[4], az[4], crz[4], clz[4];
 #pragma unroll
@@ -489,6 +497,14 @@ __device__ __forceinline__ void apply2g(const Tab& tb, const Tab2& tp, int z, co
 #pragma unroll
     for (int k = 0; k < 8; ++k) Y[k] = add2(V[0][k], S[k]);
   }
+}
+
+template <int ZF, class Get>
+__device__ __forceinline__ void apply2g(const Tab& tb, const Tab2& tp, int z, const float (&Xs)[16], const XNb& n,
+                                        Get&& get, float2 (&Y)[8]) {
+  float2 W[8];
+  apply2_xy(tp, Xs, n, get, W);
+  apply2_z<ZF>(tb, tp, z, Xs, W, get, Y);
 }
 
 // Packed form of apply with the neighbour planes in registers.
