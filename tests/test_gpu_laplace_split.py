@@ -48,3 +48,16 @@ def test_split_laplace_host_buffers_and_repeat():
         y2 = torch.empty(s.size, dtype=torch.float64)
         ctx.vmult_laplace_split(y2, xt, space)
         assert torch.equal(y, y2)
+
+
+def test_split_laplace_rejects_bad_arguments():
+    from paper_1802_01439_gb300 import DgnsError
+    ctx = context((2, 2, 2), 3, 2, mg_precision=0)
+    n = ctx.n_p
+    x = torch.zeros(2 * n, dtype=torch.float64, device="cuda")
+    rc = ctx.lib.dgns_vmult_laplace_split(ctx.h, x.data_ptr(), x.data_ptr() + 8, 1)
+    assert rc != 0                                    # dst overlaps src
+    rc = ctx.lib.dgns_vmult_laplace_split(ctx.h, x.data_ptr(), x[n:].data_ptr(), 5)
+    assert rc != 0                                    # no such space
+    with pytest.raises(DgnsError):
+        ctx.vmult_laplace_split(torch.empty(n, dtype=torch.float64, device="cuda"), x[:n] * 1.0, 5)
