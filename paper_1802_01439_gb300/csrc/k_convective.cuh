@@ -353,6 +353,25 @@ __device__ __forceinline__ void conv_cells(const double* __restrict__ u3, const 
   V* sDW = sSW + QN;
   V* sTY = sDW + QN;
   V* sEO = sTY + 3 * QN;
+  // native FP64 from N = 6 on: the quadrature planes q and Q-1-q are
+  // interpolated together from z-columns folded into sums and differences
+  // (S(Q-1-q, N-1-z) = S(q, z) on the symmetric Gauss points and LGL nodes):
+  // u(q) = E + O, u(Q-1-q) = E - O with E = ZE(q) . e, O = ZO(q) . o, about
+  // half the multiply-adds of interpolating the two planes apart (where the
+  // dead x-interpolation buffer holds the second plane: not with Q = N)
+  constexpr bool PAIR = !A::emulated && N >= 6 && CPG == 1 && LY::R + LY::P <= LY::U1R;
+  V* sZE = sEO + 2 * Q * NH;   // [q < QH][z < NH]
+  V* sZO = sZE + QH * NH;      // [q < QH][z < NF]
+  if constexpr (PAIR) {
+    for (int i = threadIdx.x; i < QH * NH; i += blockDim.x) {
+      const int q = i / NH, z = i - q * NH;
+      sZE[i] = z < NF ? A::half(A::add(tb.S[q * N + z], tb.S[q * N + N - 1 - z])) : tb.S[q * N + z];
+    }
+    for (int i = threadIdx.x; i < QH * NF; i += blockDim.x) {
+      const int q = i / NF, z = i - q * NF;
+      sZO[i] = A::half(A::sub(tb.S[q * N + z], tb.S[q * N + N - 1 - z]));
+    }
+  }
   for (int i = threadIdx.x; i < QN; i += blockDim.x) {
     sS[i] = tb.S[i];
     sSW[i] = tb.SW[i];
@@ -510,177 +529,211 @@ __device__ __forceinline__ void conv_cells(const double* __restrict__ u3, const 
   // 6 (k = 4, 5), where the rolled loop measured 5 % faster
   constexpr int UQ = (N == 5 || N == 6) ? 1 : Q;
 
+  // the second plane of a pair sits behind the face integrals (and the
+  // folded x-test products) in the dead x-interpolation buffer
+  V* sPb = sU1g + LY::R;
+  if constexpr (PAIR) {
+    // fold every z-column: e_z = u_z + u_{N-1-z} at z, o_z = u_z - u_{N-1-z} at N-1-z
+    for (int it = t; it < 3 * QQ * NF; it += NT) {
+      const int z = it % NF, col = it / NF;
+      V* col_ = sU2g + (col / QQ) * QQ * N + (col % QQ);
+      const V lo = col_[QQ * z], hi = col_[QQ * (N - 1 - z)];
+      col_[QQ * z] = A::add(lo, hi);
+      col_[QQ * (N - 1 - z)] = A::sub(lo, hi);
+    }
+    group_sync<NT>();
+  }
+
 #pragma unroll 1
-  for (int qz = 0; qz < Q; ++qz) {
-    // P1: u on the plane; item (j, c, point)
+  for (int pq = 0; pq < (PAIR ? QH : Q); ++pq) {
+    const bool two = PAIR && pq != Q - 1 - pq;
+    // P1: u on the plane (with PAIR: on the planes pq and Q-1-pq); item (j, c, point)
 #pragma unroll
     for (int r = 0; r < R1; ++r) {
       if (I1 % NT != 0 && t + NT * r >= I1) break;
       const V* src = sU2g + o1[r];
-      Acc a;
-      A::acc_first(a, sS[qz * N], src[0]);
+      if constexpr (PAIR) {
+        Acc e, o;
+        A::acc_first(e, sZE[pq * NH], src[0]);
 #pragma unroll
-      for (int z = 1; z < N; ++z) A::acc_fma(a, sS[qz * N + z], src[QQ * z]);
-      sPg[t + NT * r] = A::acc_get_norm(a);
+        for (int z = 1; z < NH; ++z) A::acc_fma(e, sZE[pq * NH + z], src[QQ * z]);
+        A::acc_first(o, sZO[pq * NF], src[QQ * (N - 1)]);
+#pragma unroll
+        for (int z = 1; z < NF; ++z) A::acc_fma(o, sZO[pq * NF + z], src[QQ * (N - 1 - z)]);
+        const V ev = A::acc_get_norm(e), od = A::acc_get_norm(o);
+        sPg[t + NT * r] = A::add(ev, od);
+        if (two) sPb[t + NT * r] = A::sub(ev, od);
+      } else {
+        Acc a;
+        A::acc_first(a, sS[pq * N], src[0]);
+#pragma unroll
+        for (int z = 1; z < N; ++z) A::acc_fma(a, sS[pq * N + z], src[QQ * z]);
+        sPg[t + NT * r] = A::acc_get_norm(a);
+      }
     }
     group_sync<NT>();
-    // P2: F_cd = u_c u_d on x-lines, x test k in even-odd form (xtest_row:
-    // SW is symmetric and DW antisymmetric under the reflection
-    // (q, x) -> (Q-1-q, N-1-x) of the Gauss points and nodes).  With paired
-    // rows an item tests the rows p and Q-1-p and stores their sum in row p
-    // and their difference in row (Q+1)/2 + p of the test's block (the
-    // middle row of odd Q alone, in row p); else one row per item.
-    if constexpr (conv_split_xtest<N>()) {
-      static_assert(CPG == 1, "one cell per group");
-      V* sFE = reinterpret_cast<V*>(sU1g) + 18 * NN;   // behind the face integrals
-      V* sFO = sFE + 8 * Q * QH;
-      for (int it = t; it < 8 * Q * QH; it += NT) {   // item (k, qy, i)
-        const int k = it / (Q * QH), l = it - k * Q * QH;
-        const int qy = l / QH, i = l - qy * QH;
-        const V* uc = sPg + test_c(k) * QQ + Q * qy;
-        const V* ud = sPg + test_d(k) * QQ + Q * qy;
-        if (i < QF) {
-          const V f1 = A::mul_nr(uc[i], ud[i]), f2 = A::mul_nr(uc[Q - 1 - i], ud[Q - 1 - i]);
-          sFE[it] = A::add_nr(f1, f2);
-          sFO[(k * Q + qy) * QF + i] = A::sub_nr(f1, f2);
-        } else {
-          sFE[it] = A::mul_nr(uc[QF], ud[QF]);   // middle point of odd Q
+#pragma unroll 1
+    for (int h = 0; h < (two ? 2 : 1); ++h) {
+      const int qz = h == 0 ? pq : Q - 1 - pq;
+      const V* sPc = h == 0 ? sPg : sPb;
+      // P2: F_cd = u_c u_d on x-lines, x test k in even-odd form (xtest_row:
+      // SW is symmetric and DW antisymmetric under the reflection
+      // (q, x) -> (Q-1-q, N-1-x) of the Gauss points and nodes).  With paired
+      // rows an item tests the rows p and Q-1-p and stores their sum in row p
+      // and their difference in row (Q+1)/2 + p of the test's block (the
+      // middle row of odd Q alone, in row p); else one row per item.
+      if constexpr (conv_split_xtest<N>()) {
+        static_assert(CPG == 1, "one cell per group");
+        V* sFE = reinterpret_cast<V*>(sU1g) + 18 * NN;   // behind the face integrals
+        V* sFO = sFE + 8 * Q * QH;
+        for (int it = t; it < 8 * Q * QH; it += NT) {   // item (k, qy, i)
+          const int k = it / (Q * QH), l = it - k * Q * QH;
+          const int qy = l / QH, i = l - qy * QH;
+          const V* uc = sPc + test_c(k) * QQ + Q * qy;
+          const V* ud = sPc + test_d(k) * QQ + Q * qy;
+          if (i < QF) {
+            const V f1 = A::mul_nr(uc[i], ud[i]), f2 = A::mul_nr(uc[Q - 1 - i], ud[Q - 1 - i]);
+            sFE[it] = A::add_nr(f1, f2);
+            sFO[(k * Q + qy) * QF + i] = A::sub_nr(f1, f2);
+          } else {
+            sFE[it] = A::mul_nr(uc[QF], ud[QF]);   // middle point of odd Q
+          }
+        }
+        group_sync<NT>();
+        for (int it = t; it < 8 * Q * NH; it += NT) {   // item (k, qy, x)
+          const int k = it / (Q * NH), l = it - k * Q * NH;
+          const int qy = l / NH, x = l - qy * NH;
+          const V* T1 = sEO + (k < 3 ? 0 : Q * NH);
+          const V* T2 = T1 + QH * NH;
+          const V* fe = sFE + (k * Q + qy) * QH;
+          const V* fo = sFO + (k * Q + qy) * QF;
+          Acc r1, r2;
+          A::acc_first(r1, T1[x], fe[0]);
+  #pragma unroll
+          for (int i = 1; i < QH; ++i) A::acc_fma(r1, T1[i * NH + x], fe[i]);
+          A::acc_first(r2, T2[x], fo[0]);
+  #pragma unroll
+          for (int i = 1; i < QF; ++i) A::acc_fma(r2, T2[i * NH + x], fo[i]);
+          const V a = A::acc_get(r1), b = A::acc_get(r2);
+          V* xo = sXg + (k * Q + qy) * N;
+          xo[x] = A::add(a, b);
+          if (x < NF) {
+            const V d = A::sub(a, b);
+            xo[N - 1 - x] = k < 3 ? A::neg(d) : d;
+          }
+        }
+      } else {
+  #pragma unroll
+        for (int r = 0; r < R2; ++r) {
+          const int it = t + NT * r;
+          if (I2 % NT != 0 && it >= I2) break;
+          const V* T1 = sEO + o2t[r];
+          const V* T2 = T1 + QH * NH;
+          const bool anti = o2t[r] == 0;
+          V xa[N];
+          xtest_row<A, N, Q>(T1, T2, anti, sPc + o2c[r], sPc + o2d[r], xa);
+          V* xo = sXg + o2x[r];
+          if (PR && (Q % 2 == 0 || o2b[r] != 0)) {
+            V xb[N];
+            xtest_row<A, N, Q>(T1, T2, anti, sPc + o2c[r] + o2b[r], sPc + o2d[r] + o2b[r], xb);
+  #pragma unroll
+            for (int x = 0; x < N; ++x) {
+              xo[x] = A::add(xa[x], xb[x]);
+              xo[QH * N + x] = A::sub(xa[x], xb[x]);
+            }
+          } else {
+  #pragma unroll
+            for (int x = 0; x < N; ++x) {
+              Acc n;
+              A::acc_set(n, xa[x]);
+              xo[x] = A::acc_get_norm(n);
+            }
+          }
         }
       }
       group_sync<NT>();
-      for (int it = t; it < 8 * Q * NH; it += NT) {   // item (k, qy, x)
-        const int k = it / (Q * NH), l = it - k * Q * NH;
-        const int qy = l / NH, x = l - qy * NH;
-        const V* T1 = sEO + (k < 3 ? 0 : Q * NH);
-        const V* T2 = T1 + QH * NH;
-        const V* fe = sFE + (k * Q + qy) * QH;
-        const V* fo = sFO + (k * Q + qy) * QF;
-        Acc r1, r2;
-        A::acc_first(r1, T1[x], fe[0]);
-#pragma unroll
-        for (int i = 1; i < QH; ++i) A::acc_fma(r1, T1[i * NH + x], fe[i]);
-        A::acc_first(r2, T2[x], fo[0]);
-#pragma unroll
-        for (int i = 1; i < QF; ++i) A::acc_fma(r2, T2[i * NH + x], fo[i]);
-        const V a = A::acc_get(r1), b = A::acc_get(r2);
-        V* xo = sXg + (k * Q + qy) * N;
-        xo[x] = A::add(a, b);
-        if (x < NF) {
-          const V d = A::sub(a, b);
-          xo[N - 1 - x] = k < 3 ? A::neg(d) : d;
-        }
-      }
-    } else {
-#pragma unroll
-      for (int r = 0; r < R2; ++r) {
-        const int it = t + NT * r;
-        if (I2 % NT != 0 && it >= I2) break;
-        const V* T1 = sEO + o2t[r];
-        const V* T2 = T1 + QH * NH;
-        const bool anti = o2t[r] == 0;
-        V xa[N];
-        xtest_row<A, N, Q>(T1, T2, anti, sPg + o2c[r], sPg + o2d[r], xa);
-        V* xo = sXg + o2x[r];
-        if (PR && (Q % 2 == 0 || o2b[r] != 0)) {
-          V xb[N];
-          xtest_row<A, N, Q>(T1, T2, anti, sPg + o2c[r] + o2b[r], sPg + o2d[r] + o2b[r], xb);
-#pragma unroll
-          for (int x = 0; x < N; ++x) {
-            xo[x] = A::add(xa[x], xb[x]);
-            xo[QH * N + x] = A::sub(xa[x], xb[x]);
+      if constexpr (PR) {
+        // P3 (even-odd): Y1 = TY0^T X(c,0) + TY1^T X(c,1), Y3 = TY2^T X(c,2) from the
+        // y-folded x tests (rows q < (Q+1)/2: sums Xe, rows (Q+1)/2 + q: differences
+        // Xo); TY0, TY2 symmetric, TY1 antisymmetric: R1 = TY0_1 X0e + TY1_2 X1o,
+        // R2 = TY0_2 X0o + TY1_1 X1e give Y1(y) = R1 + R2, Y1(N-1-y) = R1 - R2;
+        // C1 = TY2_1 X2e, C2 = TY2_2 X2o give Y3 the same way; item (j, c, y < NH, x)
+  #pragma unroll
+        for (int r = 0; r < R3; ++r) {
+          if (I3 % NT != 0 && t + NT * r >= I3) break;
+          const V* X0 = sXg + o3a[r];
+          const V* X1 = X0 + 3 * QN;                  // X(c,1) = test 3 + c
+          const V* X2 = X0 + (o3y[r] >> 4) * QN;      // X(c,2)
+          const int y = o3y[r] & 15;
+          const V* J0 = sTY;
+          const V* J1 = sTY + Q * NH;
+          const V* J2 = sTY + 2 * Q * NH;
+          Acc R1, R2, C1, C2;
+          A::acc_first(R1, J0[y], X0[0]);
+          A::acc_first(R2, J1[y], X1[0]);
+          A::acc_first(C1, J2[y], X2[0]);
+          A::acc_first(C2, J2[QH * NH + y], X2[QH * N]);
+  #pragma unroll
+          for (int q = 1; q < QH; ++q) {
+            A::acc_fma(R1, J0[q * NH + y], X0[q * N]);
+            A::acc_fma(R2, J1[q * NH + y], X1[q * N]);
+            A::acc_fma(C1, J2[q * NH + y], X2[q * N]);
           }
-        } else {
-#pragma unroll
-          for (int x = 0; x < N; ++x) {
-            Acc n;
-            A::acc_set(n, xa[x]);
-            xo[x] = A::acc_get_norm(n);
+  #pragma unroll
+          for (int q = 0; q < QF; ++q) {
+            A::acc_fma(R1, J1[(QH + q) * NH + y], X1[(QH + q) * N]);
+            A::acc_fma(R2, J0[(QH + q) * NH + y], X0[(QH + q) * N]);
+            if (q > 0) A::acc_fma(C2, J2[(QH + q) * NH + y], X2[(QH + q) * N]);
+          }
+          const V a = A::acc_get(R1), b = A::acc_get(R2), c = A::acc_get(C1), d = A::acc_get(C2);
+          V* Y1 = sYg + o3o[r];
+          Y1[N * y] = A::add(a, b);
+          Y1[NN + N * y] = A::add(c, d);
+          if (N % 2 == 0 || y < NF) {
+            Y1[N * (N - 1 - y)] = A::sub(a, b);
+            Y1[NN + N * (N - 1 - y)] = A::sub(c, d);
           }
         }
-      }
-    }
-    group_sync<NT>();
-    if constexpr (PR) {
-      // P3 (even-odd): Y1 = TY0^T X(c,0) + TY1^T X(c,1), Y3 = TY2^T X(c,2) from the
-      // y-folded x tests (rows q < (Q+1)/2: sums Xe, rows (Q+1)/2 + q: differences
-      // Xo); TY0, TY2 symmetric, TY1 antisymmetric: R1 = TY0_1 X0e + TY1_2 X1o,
-      // R2 = TY0_2 X0o + TY1_1 X1e give Y1(y) = R1 + R2, Y1(N-1-y) = R1 - R2;
-      // C1 = TY2_1 X2e, C2 = TY2_2 X2o give Y3 the same way; item (j, c, y < NH, x)
-#pragma unroll
-      for (int r = 0; r < R3; ++r) {
-        if (I3 % NT != 0 && t + NT * r >= I3) break;
-        const V* X0 = sXg + o3a[r];
-        const V* X1 = X0 + 3 * QN;                  // X(c,1) = test 3 + c
-        const V* X2 = X0 + (o3y[r] >> 4) * QN;      // X(c,2)
-        const int y = o3y[r] & 15;
-        const V* J0 = sTY;
-        const V* J1 = sTY + Q * NH;
-        const V* J2 = sTY + 2 * Q * NH;
-        Acc R1, R2, C1, C2;
-        A::acc_first(R1, J0[y], X0[0]);
-        A::acc_first(R2, J1[y], X1[0]);
-        A::acc_first(C1, J2[y], X2[0]);
-        A::acc_first(C2, J2[QH * NH + y], X2[QH * N]);
-#pragma unroll
-        for (int q = 1; q < QH; ++q) {
-          A::acc_fma(R1, J0[q * NH + y], X0[q * N]);
-          A::acc_fma(R2, J1[q * NH + y], X1[q * N]);
-          A::acc_fma(C1, J2[q * NH + y], X2[q * N]);
-        }
-#pragma unroll
-        for (int q = 0; q < QF; ++q) {
-          A::acc_fma(R1, J1[(QH + q) * NH + y], X1[(QH + q) * N]);
-          A::acc_fma(R2, J0[(QH + q) * NH + y], X0[(QH + q) * N]);
-          if (q > 0) A::acc_fma(C2, J2[(QH + q) * NH + y], X2[(QH + q) * N]);
-        }
-        const V a = A::acc_get(R1), b = A::acc_get(R2), c = A::acc_get(C1), d = A::acc_get(C2);
-        V* Y1 = sYg + o3o[r];
-        Y1[N * y] = A::add(a, b);
-        Y1[NN + N * y] = A::add(c, d);
-        if (N % 2 == 0 || y < NF) {
-          Y1[N * (N - 1 - y)] = A::sub(a, b);
-          Y1[NN + N * (N - 1 - y)] = A::sub(c, d);
+      } else {
+        // P3: Y1 = TY0^T X(c,0) + TY1^T X(c,1), Y3 = TY2^T X(c,2); item (j, c, y, x)
+  #pragma unroll
+        for (int r = 0; r < R3; ++r) {
+          if (I3 % NT != 0 && t + NT * r >= I3) break;
+          const V* X0 = sXg + o3a[r];
+          const V* X1 = X0 + 3 * QN;                  // X(c,1) = test 3 + c
+          const V* X2 = X0 + (o3y[r] >> 4) * QN;      // X(c,2)
+          const int y = o3y[r] & 15;
+          Acc y1, y3;
+          A::acc_first(y1, sTY[QN + y], X1[0]);
+          A::acc_fma(y1, sTY[y], X0[0]);
+          A::acc_first(y3, sTY[2 * QN + y], X2[0]);
+  #pragma unroll UQ
+          for (int qy = 1; qy < Q; ++qy) {
+            const int o = N * qy;
+            A::acc_fma(y1, sTY[QN + qy * N + y], X1[o]);
+            A::acc_fma(y1, sTY[qy * N + y], X0[o]);
+            A::acc_fma(y3, sTY[2 * QN + qy * N + y], X2[o]);
+          }
+          V* Y1 = sYg + o3o[r];
+          Y1[N * y] = A::acc_get_norm(y1);
+          Y1[NN + N * y] = A::acc_get_norm(y3);
         }
       }
-    } else {
-      // P3: Y1 = TY0^T X(c,0) + TY1^T X(c,1), Y3 = TY2^T X(c,2); item (j, c, y, x)
-#pragma unroll
-      for (int r = 0; r < R3; ++r) {
-        if (I3 % NT != 0 && t + NT * r >= I3) break;
-        const V* X0 = sXg + o3a[r];
-        const V* X1 = X0 + 3 * QN;                  // X(c,1) = test 3 + c
-        const V* X2 = X0 + (o3y[r] >> 4) * QN;      // X(c,2)
-        const int y = o3y[r] & 15;
-        Acc y1, y3;
-        A::acc_first(y1, sTY[QN + y], X1[0]);
-        A::acc_fma(y1, sTY[y], X0[0]);
-        A::acc_first(y3, sTY[2 * QN + y], X2[0]);
-#pragma unroll UQ
-        for (int qy = 1; qy < Q; ++qy) {
-          const int o = N * qy;
-          A::acc_fma(y1, sTY[QN + qy * N + y], X1[o]);
-          A::acc_fma(y1, sTY[qy * N + y], X0[o]);
-          A::acc_fma(y3, sTY[2 * QN + qy * N + y], X2[o]);
-        }
-        V* Y1 = sYg + o3o[r];
-        Y1[N * y] = A::acc_get_norm(y1);
-        Y1[NN + N * y] = A::acc_get_norm(y3);
+      group_sync<NT>();
+      // P4: out -= SW_z(qz) Y1 + DW_z(qz) Y3; item (j, c, x, y, z), in registers
+  #pragma unroll
+      for (int r = 0; r < R4; ++r) {
+        if (I4 % NT != 0 && t + NT * r >= I4) break;
+        const V* Y = sYg + o4y[r];
+        const int z = o4z[r];
+        if (qz == 0)
+          A::acc_first(out[r], A::neg(sDW[z]), Y[NN]);
+        else
+          A::acc_fma(out[r], A::neg(sDW[qz * N + z]), Y[NN]);
+        A::acc_fma(out[r], A::neg(sSW[qz * N + z]), Y[0]);
       }
+      group_sync<NT>();
     }
-    group_sync<NT>();
-    // P4: out -= SW_z(qz) Y1 + DW_z(qz) Y3; item (j, c, x, y, z), in registers
-#pragma unroll
-    for (int r = 0; r < R4; ++r) {
-      if (I4 % NT != 0 && t + NT * r >= I4) break;
-      const V* Y = sYg + o4y[r];
-      const int z = o4z[r];
-      if (qz == 0)
-        A::acc_first(out[r], A::neg(sDW[z]), Y[NN]);
-      else
-        A::acc_fma(out[r], A::neg(sDW[qz * N + z]), Y[NN]);
-      A::acc_fma(out[r], A::neg(sSW[qz * N + z]), Y[0]);
-    }
-    group_sync<NT>();
   }
   cp_async_wait_all();
   group_sync<NT>();
@@ -999,7 +1052,9 @@ int launch_conv(int part, const MeshDims& m, const double* u3, double* rface, do
   constexpr int EPB = conv_fwd_cells_per_block<N>(), GPB = face_groups_per_block<FL, N, Q, sizeof(V)>(),
                 FPG = faces_per_group<N>();
   constexpr int FPB = GPB * FPG;
-  const size_t smem = ((size_t)EPB * ConvLayout<N, Q>::PER + 6 * Q * N + 2 * Q * ((N + 1) / 2)) * sizeof(V);
+  // tables: S, SW, DW, TY (6 Q N), EO (2 Q (N+1)/2), and with paired planes ZE, ZO (Q N at most)
+  constexpr int TABS = (A::emulated ? 6 : 7) * Q * N + 2 * Q * ((N + 1) / 2);
+  const size_t smem = ((size_t)EPB * ConvLayout<N, Q>::PER + TABS) * sizeof(V);
   const size_t fsmem = (size_t)GPB * face_group_smem<FL, N, Q>() * sizeof(V);
   if (smem > 232448 || fsmem > 232448) return 7;
   if (cudaFuncSetAttribute(conv_kernel<A, N, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
