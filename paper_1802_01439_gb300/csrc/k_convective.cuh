@@ -88,6 +88,16 @@ struct ConvLayout {
   static constexpr int UP = even_up(U > PXY ? U : PXY);   // nodal u first, plane work later
   static constexpr int PER = UP + U1R + U2;
 };
+// Native FP64 from N = 6 on, the cell kernel takes the quadrature planes q
+// and Q-1-q together (see conv_cells); the second plane needs room behind
+// the face integrals in the x-interpolation buffer, and its y tests room in
+// its place (Q^2 >= 2 N^2: the 3/2 rule, not Q = N).
+template <bool EMULATED, int N, int Q>
+constexpr bool conv_pair_planes() {
+  return !EMULATED && N >= 6 && conv_cells_per_group<N>() == 1 &&
+         ConvLayout<N, Q>::R + ConvLayout<N, Q>::P <= ConvLayout<N, Q>::U1R &&
+         ConvLayout<N, Q>::Y <= ConvLayout<N, Q>::P;
+}
 
 // The face kernel's interpolation and test phases give each thread whole
 // lines in even-odd form (`lines`) in double-float arithmetic up to N = 8;
@@ -357,9 +367,8 @@ __device__ __forceinline__ void conv_cells(const double* __restrict__ u3, const 
   // interpolated together from z-columns folded into sums and differences
   // (S(Q-1-q, N-1-z) = S(q, z) on the symmetric Gauss points and LGL nodes):
   // u(q) = E + O, u(Q-1-q) = E - O with E = ZE(q) . e, O = ZO(q) . o, about
-  // half the multiply-adds of interpolating the two planes apart (where the
-  // dead x-interpolation buffer holds the second plane: not with Q = N)
-  constexpr bool PAIR = !A::emulated && N >= 6 && CPG == 1 && LY::R + LY::P <= LY::U1R;
+  // half the multiply-adds of interpolating the two planes apart
+  constexpr bool PAIR = conv_pair_planes<A::emulated, N, Q>();
   V* sZE = sEO + 2 * Q * NH;   // [q < QH][z < NH]
   V* sZO = sZE + QH * NH;      // [q < QH][z < NF]
   if constexpr (PAIR) {
@@ -370,6 +379,23 @@ __device__ __forceinline__ void conv_cells(const double* __restrict__ u3, const 
     for (int i = threadIdx.x; i < QH * NF; i += blockDim.x) {
       const int q = i / NF, z = i - q * NF;
       sZO[i] = A::half(A::sub(tb.S[q * N + z], tb.S[q * N + N - 1 - z]));
+    }
+  }
+  // and the z test of a plane pair in even-odd form: the y-tested values of
+  // the two planes folded into sums e and differences o; with
+  // Se = -(SW(q) + SW(Q-1-q)) / 2, So = -(SW(q) - SW(Q-1-q)) / 2 (De, Do from DW)
+  // S1 = Se e1 + Do o3 and S2 = So o1 + De e3 give out(z) = S1 + S2 and, SW
+  // symmetric and DW antisymmetric under (q, z) -> (Q-1-q, N-1-z),
+  // out(N-1-z) = S1 - S2.  Tables [Se | So | De | Do][q < QH][z < NH].
+  V* sQ4 = sZO + QH * NF;
+  if constexpr (PAIR) {
+    for (int i = threadIdx.x; i < QH * NH; i += blockDim.x) {
+      const int q = i / NH, z = i - q * NH;
+      const int a = q * N + z, b = (Q - 1 - q) * N + z;
+      sQ4[i] = A::neg(A::half(A::add(tb.SW[a], tb.SW[b])));
+      sQ4[QH * NH + i] = A::neg(A::half(A::sub(tb.SW[a], tb.SW[b])));
+      sQ4[2 * QH * NH + i] = A::neg(A::half(A::add(tb.DW[a], tb.DW[b])));
+      sQ4[3 * QH * NH + i] = A::neg(A::half(A::sub(tb.DW[a], tb.DW[b])));
     }
   }
   for (int i = threadIdx.x; i < QN; i += blockDim.x) {
@@ -524,14 +550,20 @@ __device__ __forceinline__ void conv_cells(const double* __restrict__ u3, const 
     o4y[r] = (j * 3 + c) * 2 * NN + rr % NN;
     o4z[r] = rr / NN;
   }
-  Acc out[R4];
+  Acc out[PAIR ? 1 : R4];
+  // with paired planes the z test runs after both planes' y tests, one item
+  // per (c, y, x) line, its N outputs as the pairs S1 +- S2 in registers
+  constexpr int IL = 3 * NN, RL = (IL + NT - 1) / NT;
+  Acc s1[PAIR ? RL : 1][NH], s2[PAIR ? RL : 1][NH];
   // the point loop of the unpaired y tests is unrolled, except for N = 5 and
   // 6 (k = 4, 5), where the rolled loop measured 5 % faster
   constexpr int UQ = (N == 5 || N == 6) ? 1 : Q;
 
   // the second plane of a pair sits behind the face integrals (and the
-  // folded x-test products) in the dead x-interpolation buffer
+  // folded x-test products) in the dead x-interpolation buffer; its y tests
+  // later replace it there
   V* sPb = sU1g + LY::R;
+  static_assert(!PAIR || LY::Y <= LY::P, "room for the second plane's y tests");
   if constexpr (PAIR) {
     // fold every z-column: e_z = u_z + u_{N-1-z} at z, o_z = u_z - u_{N-1-z} at N-1-z
     for (int it = t; it < 3 * QQ * NF; it += NT) {
@@ -576,6 +608,7 @@ __device__ __forceinline__ void conv_cells(const double* __restrict__ u3, const 
     for (int h = 0; h < (two ? 2 : 1); ++h) {
       const int qz = h == 0 ? pq : Q - 1 - pq;
       const V* sPc = h == 0 ? sPg : sPb;
+      V* sYc = h == 0 ? sYg : sPb;   // the second plane's y tests replace its dead u
       // P2: F_cd = u_c u_d on x-lines, x test k in even-odd form (xtest_row:
       // SW is symmetric and DW antisymmetric under the reflection
       // (q, x) -> (Q-1-q, N-1-x) of the Gauss points and nodes).  With paired
@@ -686,7 +719,7 @@ __device__ __forceinline__ void conv_cells(const double* __restrict__ u3, const 
             if (q > 0) A::acc_fma(C2, J2[(QH + q) * NH + y], X2[(QH + q) * N]);
           }
           const V a = A::acc_get(R1), b = A::acc_get(R2), c = A::acc_get(C1), d = A::acc_get(C2);
-          V* Y1 = sYg + o3o[r];
+          V* Y1 = sYc + o3o[r];
           Y1[N * y] = A::add(a, b);
           Y1[NN + N * y] = A::add(c, d);
           if (N % 2 == 0 || y < NF) {
@@ -714,23 +747,61 @@ __device__ __forceinline__ void conv_cells(const double* __restrict__ u3, const 
             A::acc_fma(y1, sTY[qy * N + y], X0[o]);
             A::acc_fma(y3, sTY[2 * QN + qy * N + y], X2[o]);
           }
-          V* Y1 = sYg + o3o[r];
+          V* Y1 = sYc + o3o[r];
           Y1[N * y] = A::acc_get_norm(y1);
           Y1[NN + N * y] = A::acc_get_norm(y3);
         }
       }
       group_sync<NT>();
-      // P4: out -= SW_z(qz) Y1 + DW_z(qz) Y3; item (j, c, x, y, z), in registers
+      if constexpr (!PAIR) {
+        // P4: out -= SW_z(qz) Y1 + DW_z(qz) Y3; item (j, c, x, y, z), in registers
   #pragma unroll
-      for (int r = 0; r < R4; ++r) {
-        if (I4 % NT != 0 && t + NT * r >= I4) break;
-        const V* Y = sYg + o4y[r];
-        const int z = o4z[r];
-        if (qz == 0)
-          A::acc_first(out[r], A::neg(sDW[z]), Y[NN]);
-        else
-          A::acc_fma(out[r], A::neg(sDW[qz * N + z]), Y[NN]);
-        A::acc_fma(out[r], A::neg(sSW[qz * N + z]), Y[0]);
+        for (int r = 0; r < R4; ++r) {
+          if (I4 % NT != 0 && t + NT * r >= I4) break;
+          const V* Y = sYg + o4y[r];
+          const int z = o4z[r];
+          if (qz == 0)
+            A::acc_first(out[r], A::neg(sDW[z]), Y[NN]);
+          else
+            A::acc_fma(out[r], A::neg(sDW[qz * N + z]), Y[NN]);
+          A::acc_fma(out[r], A::neg(sSW[qz * N + z]), Y[0]);
+        }
+        group_sync<NT>();
+      }
+    }
+    if constexpr (PAIR) {
+      // P4 of the pair (pq, Q-1-pq) in even-odd form (tables sQ4); the
+      // middle plane of odd Q alone: e = o = its y tests
+      const V* Se = sQ4 + pq * NH;
+      const V* So = Se + QH * NH;
+      const V* De = So + QH * NH;
+      const V* Do = De + QH * NH;
+  #pragma unroll
+      for (int r = 0; r < RL; ++r) {
+        const int l = t + NT * r;
+        if (IL % NT != 0 && l >= IL) break;
+        const int c = l / NN, yx = l - c * NN;
+        const V* Ya = sYg + c * 2 * NN + yx;
+        V e1 = Ya[0], o1 = Ya[0], e3 = Ya[NN], o3 = Ya[NN];
+        if (two) {
+          const V* Yb = sPb + c * 2 * NN + yx;
+          e1 = A::add(Ya[0], Yb[0]);
+          o1 = A::sub(Ya[0], Yb[0]);
+          e3 = A::add(Ya[NN], Yb[NN]);
+          o3 = A::sub(Ya[NN], Yb[NN]);
+        }
+  #pragma unroll
+        for (int z = 0; z < NH; ++z) {
+          if (pq == 0) {
+            A::acc_first(s1[r][z], Se[z], e1);
+            A::acc_first(s2[r][z], So[z], o1);
+          } else {
+            A::acc_fma(s1[r][z], Se[z], e1);
+            A::acc_fma(s2[r][z], So[z], o1);
+          }
+          A::acc_fma(s1[r][z], Do[z], o3);
+          A::acc_fma(s2[r][z], De[z], e3);
+        }
       }
       group_sync<NT>();
     }
@@ -739,6 +810,32 @@ __device__ __forceinline__ void conv_cells(const double* __restrict__ u3, const 
   group_sync<NT>();
   // face integrals from the face kernel: +R on the layer N-1 (this cell is
   // the '-' side of its face), -R of the '-' neighbour on the layer 0
+  if constexpr (PAIR) {
+    if (c0 > last) return;
+#pragma unroll
+    for (int r = 0; r < RL; ++r) {
+      const int l = t + NT * r;
+      if (IL % NT != 0 && l >= IL) break;
+      const int c = l / NN, yx = l - c * NN;
+      const int x = yx % N, y = yx / N;
+      const double* rc = reinterpret_cast<const double*>(sU1g) + c * NN;
+      double* d = dst3 + ((size_t)c * m.E + el0) * N3 + yx;
+#pragma unroll
+      for (int z = 0; z < N; ++z) {
+        const int zz = z < NH ? z : N - 1 - z;
+        const V a = A::acc_get_norm(s1[r][zz]), b = A::acc_get_norm(s2[r][zz]);
+        double v = A::to_double(z < NH ? A::add(a, b) : A::sub(a, b));
+        if (x == N - 1) v += rc[0 * 3 * NN + y + N * z];
+        if (x == 0) v -= rc[1 * 3 * NN + y + N * z];
+        if (y == N - 1) v += rc[2 * 3 * NN + x + N * z];
+        if (y == 0) v -= rc[3 * 3 * NN + x + N * z];
+        if (z == N - 1) v += rc[4 * 3 * NN + x + N * y];
+        if (z == 0) v -= rc[5 * 3 * NN + x + N * y];
+        d[NN * z] = v;
+      }
+    }
+    return;
+  }
 #pragma unroll
   for (int r = 0; r < R4; ++r) {
     const int it = t + NT * r;
@@ -1052,8 +1149,10 @@ int launch_conv(int part, const MeshDims& m, const double* u3, double* rface, do
   constexpr int EPB = conv_fwd_cells_per_block<N>(), GPB = face_groups_per_block<FL, N, Q, sizeof(V)>(),
                 FPG = faces_per_group<N>();
   constexpr int FPB = GPB * FPG;
-  // tables: S, SW, DW, TY (6 Q N), EO (2 Q (N+1)/2), and with paired planes ZE, ZO (Q N at most)
-  constexpr int TABS = (A::emulated ? 6 : 7) * Q * N + 2 * Q * ((N + 1) / 2);
+  // tables: S, SW, DW, TY (6 Q N), EO (2 Q (N+1)/2), and natively (paired
+  // planes) ZE, ZO ((Q+1)/2 N) and the z-test tables (4 (Q+1)/2 (N+1)/2)
+  constexpr int NH = (N + 1) / 2, QH = (Q + 1) / 2;
+  constexpr int TABS = 6 * Q * N + 2 * Q * NH + (conv_pair_planes<A::emulated, N, Q>() ? QH * N + 4 * QH * NH : 0);
   const size_t smem = ((size_t)EPB * ConvLayout<N, Q>::PER + TABS) * sizeof(V);
   const size_t fsmem = (size_t)GPB * face_group_smem<FL, N, Q>() * sizeof(V);
   if (smem > 232448 || fsmem > 232448) return 7;
