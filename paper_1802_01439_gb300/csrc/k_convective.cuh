@@ -369,6 +369,10 @@ __device__ __forceinline__ void conv_cells(const double* __restrict__ u3, const 
   // u(q) = E + O, u(Q-1-q) = E - O with E = ZE(q) . e, O = ZO(q) . o, about
   // half the multiply-adds of interpolating the two planes apart
   constexpr bool PAIR = conv_pair_planes<A::emulated, N, Q>();
+  // with paired planes the x-tested rows of a plane are also folded along y
+  // (sums in row q, differences in row Q-1-q) and the y tests run in even-odd
+  // form (one item per output pair, as with paired rows)
+  constexpr bool EOY = PAIR;
   V* sZE = sEO + 2 * Q * NH;   // [q < QH][z < NH]
   V* sZO = sZE + QH * NH;      // [q < QH][z < NF]
   if constexpr (PAIR) {
@@ -402,13 +406,13 @@ __device__ __forceinline__ void conv_cells(const double* __restrict__ u3, const 
     sS[i] = tb.S[i];
     sSW[i] = tb.SW[i];
     sDW[i] = tb.DW[i];
-    if (!PR) {
+    if (!PR && !EOY) {
       sTY[i] = tb.TY[0][i];
       sTY[QN + i] = tb.TY[1][i];
       sTY[2 * QN + i] = tb.TY[2][i];
     }
   }
-  if (PR)
+  if (PR || EOY)
     for (int i = threadIdx.x; i < 3 * Q * NH; i += blockDim.x) sTY[i] = tb.TYeo[i / (Q * NH)][i % (Q * NH)];
   for (int i = threadIdx.x; i < Q * NH; i += blockDim.x) {
     sEO[i] = tb.EO[0][i];
@@ -432,8 +436,9 @@ __device__ __forceinline__ void conv_cells(const double* __restrict__ u3, const 
   __syncthreads();
   // double-float: whole lines in even-odd form (interp_eo, tables read from
   // the kernel parameter), except at N = 5, 6, 7, where one output per item
-  // measured faster (k = 4: 1 %, k = 5: 5 %, k = 6: 15 %); natively (FP64-pipe
-  // bound) one output per item keeps every lane busy
+  // measured faster (k = 4: 1 %, k = 5: 5 %, k = 6: 15 %); natively with
+  // paired planes folded lines and one item per output pair; else one
+  // output per item
   if constexpr (A::emulated && (N < 5 || N > 7)) {
     // x interpolation: item (j, c, line (y,z))
     for (int it = t; it < CPG * 3 * NN; it += NT) {
@@ -448,6 +453,64 @@ __device__ __forceinline__ void conv_cells(const double* __restrict__ u3, const 
       const int qx = ll % Q, z = ll / Q;
       interp_eo<A, N, Q>(tb.IE, sU1g + j * LY::U1R + c * Q * NN + qx + QN * z, Q,
                          sU2g + j * LY::U2 + c * QQ * N + qx + QQ * z, Q);
+    }
+    group_sync<NT>();
+  } else if constexpr (PAIR) {
+    // natively with paired planes: every line folded in place into sums
+    // (index i) and differences (index N-1-i), then one item per output
+    // pair (q, Q-1-q): u(q) = E + O, u(Q-1-q) = E - O (tables ZE, ZO)
+    // x interpolation
+    for (int it = t; it < 3 * NN * NF; it += NT) {
+      const int r = it / NF, i = it - r * NF;
+      V* x = sUg + r * N;
+      const V a = x[i], b = x[N - 1 - i];
+      x[i] = A::add(a, b);
+      x[N - 1 - i] = A::sub(a, b);
+    }
+    group_sync<NT>();
+    for (int it = t; it < 3 * NN * QH; it += NT) {   // item (c, line (y,z), q < QH)
+      const int r = it / QH, q = it - r * QH;
+      const V* x = sUg + r * N;
+      Acc e, o;
+      A::acc_first(e, sZE[q * NH], x[0]);
+#pragma unroll
+      for (int i = 1; i < NH; ++i) A::acc_fma(e, sZE[q * NH + i], x[i]);
+      A::acc_first(o, sZO[q * NF], x[N - 1]);
+#pragma unroll
+      for (int i = 1; i < NF; ++i) A::acc_fma(o, sZO[q * NF + i], x[N - 1 - i]);
+      const V ev = A::acc_get_norm(e), od = A::acc_get_norm(o);
+      V* y = sU1g + r * Q;
+      y[q] = A::add(ev, od);
+      if (q != Q - 1 - q) y[Q - 1 - q] = A::sub(ev, od);
+    }
+    group_sync<NT>();
+    // y interpolation: lines (c, z, qx) of stride Q
+    for (int it = t; it < 3 * QN * NF; it += NT) {
+      const int r = it / NF, i = it - r * NF;
+      const int c = r / QN, ll = r - c * QN;
+      const int qx = ll % Q, z = ll / Q;
+      V* x = sU1g + c * Q * NN + qx + QN * z;
+      const V a = x[Q * i], b = x[Q * (N - 1 - i)];
+      x[Q * i] = A::add(a, b);
+      x[Q * (N - 1 - i)] = A::sub(a, b);
+    }
+    group_sync<NT>();
+    for (int it = t; it < 3 * QN * QH; it += NT) {   // item (c, qx, z, qy < QH)
+      const int qy = it % QH, r = it / QH;
+      const int c = r / QN, ll = r - c * QN;
+      const int qx = ll % Q, z = ll / Q;
+      const V* x = sU1g + c * Q * NN + qx + QN * z;
+      Acc e, o;
+      A::acc_first(e, sZE[qy * NH], x[0]);
+#pragma unroll
+      for (int i = 1; i < NH; ++i) A::acc_fma(e, sZE[qy * NH + i], x[Q * i]);
+      A::acc_first(o, sZO[qy * NF], x[Q * (N - 1)]);
+#pragma unroll
+      for (int i = 1; i < NF; ++i) A::acc_fma(o, sZO[qy * NF + i], x[Q * (N - 1 - i)]);
+      const V ev = A::acc_get_norm(e), od = A::acc_get_norm(o);
+      V* y = sU2g + c * QQ * N + qx + QQ * z;
+      y[Q * qy] = A::add(ev, od);
+      if (qy != Q - 1 - qy) y[Q * (Q - 1 - qy)] = A::sub(ev, od);
     }
     group_sync<NT>();
   } else {
@@ -502,7 +565,7 @@ __device__ __forceinline__ void conv_cells(const double* __restrict__ u3, const 
   // The plane loop: every lane keeps the same work items in all planes, so
   // their offsets are computed once; the lane's outputs (items of P4) stay
   // in registers until the end.
-  constexpr int I1 = CPG * 3 * QQ, I2 = CPG * 8 * (PR ? QH : Q), I3 = CPG * 3 * N * (PR ? NH : N),
+  constexpr int I1 = CPG * 3 * QQ, I2 = CPG * 8 * (PR ? QH : Q), I3 = CPG * 3 * N * (PR || EOY ? NH : N),
                 I4 = CPG * 3 * N3;
   constexpr int R1 = (I1 + NT - 1) / NT, R2 = (I2 + NT - 1) / NT, R3 = (I3 + NT - 1) / NT,
                 R4 = (I4 + NT - 1) / NT;
@@ -533,7 +596,7 @@ __device__ __forceinline__ void conv_cells(const double* __restrict__ u3, const 
 #pragma unroll
   for (int r = 0; r < R3; ++r) {
     // item (j, c, y, x), with paired rows y < NH stands for y and N-1-y
-    constexpr int YW = PR ? NH : N;
+    constexpr int YW = PR || EOY ? NH : N;
     const int it = t + NT * r;
     const int j = it / (3 * N * YW), l = it - j * 3 * N * YW;
     const int c = l / (N * YW), rr = l - c * N * YW;
@@ -685,10 +748,24 @@ __device__ __forceinline__ void conv_cells(const double* __restrict__ u3, const 
         }
       }
       group_sync<NT>();
-      if constexpr (PR) {
+      if constexpr (EOY) {
+        // fold every x-tested column along y: row q <- X(q) + X(Q-1-q),
+        // row Q-1-q <- X(q) - X(Q-1-q) (the middle row of odd Q unchanged)
+        for (int it = t; it < 8 * QF * N; it += NT) {
+          const int k = it / (QF * N), l = it - k * QF * N;
+          const int p = l / N, x = l - p * N;
+          V* ra = sXg + (k * Q + p) * N + x;
+          V* rb = sXg + (k * Q + Q - 1 - p) * N + x;
+          const V va = *ra, vb = *rb;
+          *ra = A::add(va, vb);
+          *rb = A::sub(va, vb);
+        }
+        group_sync<NT>();
+      }
+      if constexpr (PR || EOY) {
         // P3 (even-odd): Y1 = TY0^T X(c,0) + TY1^T X(c,1), Y3 = TY2^T X(c,2) from the
-        // y-folded x tests (rows q < (Q+1)/2: sums Xe, rows (Q+1)/2 + q: differences
-        // Xo); TY0, TY2 symmetric, TY1 antisymmetric: R1 = TY0_1 X0e + TY1_2 X1o,
+        // y-folded x tests (rows q < (Q+1)/2: sums Xe; differences Xo in rows
+        // (Q+1)/2 + q with paired rows, else Q-1-q); TY0, TY2 symmetric, TY1 antisymmetric: R1 = TY0_1 X0e + TY1_2 X1o,
         // R2 = TY0_2 X0o + TY1_1 X1e give Y1(y) = R1 + R2, Y1(N-1-y) = R1 - R2;
         // C1 = TY2_1 X2e, C2 = TY2_2 X2o give Y3 the same way; item (j, c, y < NH, x)
   #pragma unroll
@@ -705,7 +782,7 @@ __device__ __forceinline__ void conv_cells(const double* __restrict__ u3, const 
           A::acc_first(R1, J0[y], X0[0]);
           A::acc_first(R2, J1[y], X1[0]);
           A::acc_first(C1, J2[y], X2[0]);
-          A::acc_first(C2, J2[QH * NH + y], X2[QH * N]);
+          A::acc_first(C2, J2[QH * NH + y], X2[(PR ? QH : Q - 1) * N]);
   #pragma unroll
           for (int q = 1; q < QH; ++q) {
             A::acc_fma(R1, J0[q * NH + y], X0[q * N]);
@@ -714,9 +791,10 @@ __device__ __forceinline__ void conv_cells(const double* __restrict__ u3, const 
           }
   #pragma unroll
           for (int q = 0; q < QF; ++q) {
-            A::acc_fma(R1, J1[(QH + q) * NH + y], X1[(QH + q) * N]);
-            A::acc_fma(R2, J0[(QH + q) * NH + y], X0[(QH + q) * N]);
-            if (q > 0) A::acc_fma(C2, J2[(QH + q) * NH + y], X2[(QH + q) * N]);
+            const int o = (PR ? QH + q : Q - 1 - q) * N;
+            A::acc_fma(R1, J1[(QH + q) * NH + y], X1[o]);
+            A::acc_fma(R2, J0[(QH + q) * NH + y], X0[o]);
+            if (q > 0) A::acc_fma(C2, J2[(QH + q) * NH + y], X2[o]);
           }
           const V a = A::acc_get(R1), b = A::acc_get(R2), c = A::acc_get(C1), d = A::acc_get(C2);
           V* Y1 = sYc + o3o[r];
