@@ -146,6 +146,30 @@ constexpr int face_groups_per_block() {
 }
 
 
+// One output pair of an even-odd contraction of a folded line v (stride s,
+// length LL: sums at i, differences at LL-1-i): e = sum_{i < NE} te[i ts] v(i),
+// o = sum_{i < NO} to[i os] v(LL-1-i).
+template <class A, int LL, int NE, int NO>
+__device__ __forceinline__ void fold_dot(const typename A::V* te, int ts, const typename A::V* to, int os,
+                                         const typename A::V* v, int s, typename A::V& e, typename A::V& o) {
+  typename A::Acc a, b;
+  A::acc_first(a, te[0], v[0]);
+#pragma unroll
+  for (int i = 1; i < NE; ++i) A::acc_fma(a, te[i * ts], v[i * s]);
+  A::acc_first(b, to[0], v[(LL - 1) * s]);
+#pragma unroll
+  for (int i = 1; i < NO; ++i) A::acc_fma(b, to[i * os], v[(LL - 1 - i) * s]);
+  e = A::acc_get_norm(a);
+  o = A::acc_get_norm(b);
+}
+// the pair (x[0], x[k]) -> (x[0] + x[k], x[0] - x[k]) in place
+template <class A>
+__device__ __forceinline__ void fold_pair(typename A::V* x, int k) {
+  const typename A::V a = x[0], b = x[k];
+  x[0] = A::add(a, b);
+  x[k] = A::sub(a, b);
+}
+
 __device__ __forceinline__ int node3(int N, int d, int a, int t1, int j1, int t2, int j2) {
   int c[3];
   c[d] = a;
@@ -912,29 +936,29 @@ __device__ __forceinline__ void conv_cells(const double* __restrict__ u3, const 
         d[NN * z] = v;
       }
     }
-    return;
-  }
+  } else {
 #pragma unroll
-  for (int r = 0; r < R4; ++r) {
-    const int it = t + NT * r;
-    if (I4 % NT != 0 && it >= I4) break;
-    const int j = it / (3 * N3), l = it - j * 3 * N3;
-    if (c0 + j > last) break;
-    const int c = l / N3, rr = l - c * N3;
-    const int x = rr % N, yz = rr / N;
-    const int y = yz % N, z = yz / N;
-    const double* rc = reinterpret_cast<const double*>(sU1g + j * LY::U1R) + c * NN;
-    // the face integrals arrive as doubles: added natively after the cell
-    // term's conversion (a few FP64 additions instead of splits and
-    // emulated additions)
-    double v = A::to_double(A::acc_get_norm(out[r]));
-    if (x == N - 1) v += rc[0 * 3 * NN + y + N * z];
-    if (x == 0) v -= rc[1 * 3 * NN + y + N * z];
-    if (y == N - 1) v += rc[2 * 3 * NN + x + N * z];
-    if (y == 0) v -= rc[3 * 3 * NN + x + N * z];
-    if (z == N - 1) v += rc[4 * 3 * NN + x + N * y];
-    if (z == 0) v -= rc[5 * 3 * NN + x + N * y];
-    dst3[((size_t)c * m.E + pick2(j, el0, el1)) * N3 + rr] = v;
+    for (int r = 0; r < R4; ++r) {
+      const int it = t + NT * r;
+      if (I4 % NT != 0 && it >= I4) break;
+      const int j = it / (3 * N3), l = it - j * 3 * N3;
+      if (c0 + j > last) break;
+      const int c = l / N3, rr = l - c * N3;
+      const int x = rr % N, yz = rr / N;
+      const int y = yz % N, z = yz / N;
+      const double* rc = reinterpret_cast<const double*>(sU1g + j * LY::U1R) + c * NN;
+      // the face integrals arrive as doubles: added natively after the cell
+      // term's conversion (a few FP64 additions instead of splits and
+      // emulated additions)
+      double v = A::to_double(A::acc_get_norm(out[r]));
+      if (x == N - 1) v += rc[0 * 3 * NN + y + N * z];
+      if (x == 0) v -= rc[1 * 3 * NN + y + N * z];
+      if (y == N - 1) v += rc[2 * 3 * NN + x + N * z];
+      if (y == 0) v -= rc[3 * 3 * NN + x + N * z];
+      if (z == N - 1) v += rc[4 * 3 * NN + x + N * y];
+      if (z == 0) v -= rc[5 * 3 * NN + x + N * y];
+      dst3[((size_t)c * m.E + pick2(j, el0, el1)) * N3 + rr] = v;
+    }
   }
 }
 
@@ -994,11 +1018,41 @@ __global__ void __launch_bounds__(face_groups_per_block<face_lines<A::emulated, 
   V* base = sm + g * face_group_smem<L, N, Q>();
   V* sS = base + FPG * LY::PER;   // one output per thread: the tables, indexed by thread
   V* sSW = sS + QN;
-  if (!L)
+  // natively from N = 6 on every contraction runs in even-odd form: the
+  // lines folded in place into sums (index i) and differences (index
+  // L-1-i), then one item per output pair (o, M-1-o) computes E + O and
+  // E - O.  Tables (in place of S, SW): interpolation ZE [QH][NH] =
+  // (S(q,j) + S(q,N-1-j)) / 2 (S(q,j) in the middle column of odd N),
+  // ZO [QH][NF] = (S(q,j) - S(q,N-1-j)) / 2; test TE [QH][NH] =
+  // (SW(q,x) + SW(Q-1-q,x)) / 2 (SW in the middle row of odd Q),
+  // TO [QF][NH] = (SW(q,x) - SW(Q-1-q,x)) / 2 (S, SW symmetric under
+  // (q, j) -> (Q-1-q, N-1-j), so the second output of a pair is E - O).
+  constexpr bool EF = !A::emulated && N >= 6;
+  constexpr int NH = (N + 1) / 2, NF = N / 2, QH = (Q + 1) / 2, QF = Q / 2;
+  V* sZE = sS;
+  V* sZO = sS + QH * NH;
+  V* sTE = sSW;
+  V* sTO = sSW + QH * NH;
+  if constexpr (EF) {
+    for (int i = t; i < QH * NH; i += FT) {
+      const int q = i / NH, j = i - q * NH;
+      sZE[i] = j < NF ? A::half(A::add(tb.S[q * N + j], tb.S[q * N + N - 1 - j])) : tb.S[q * N + j];
+      sTE[i] = q < QF ? A::half(A::add(tb.SW[q * N + j], tb.SW[(Q - 1 - q) * N + j])) : tb.SW[q * N + j];
+    }
+    for (int i = t; i < QH * NF; i += FT) {
+      const int q = i / NF, j = i - q * NF;
+      sZO[i] = A::half(A::sub(tb.S[q * N + j], tb.S[q * N + N - 1 - j]));
+    }
+    for (int i = t; i < QF * NH; i += FT) {
+      const int q = i / NH, j = i - q * NH;
+      sTO[i] = A::half(A::sub(tb.SW[q * N + j], tb.SW[(Q - 1 - q) * N + j]));
+    }
+  } else if (!L) {
     for (int i = t; i < QN; i += FT) {
       sS[i] = tb.S[i];
       sSW[i] = tb.SW[i];
     }
+  }
   const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
   static_assert(FPG == 1 || FPG == 2 || FPG == 4, "one, two or four faces per group");
   // cells of the group's faces (scalars, not an array indexed by a runtime
@@ -1045,7 +1099,24 @@ __global__ void __launch_bounds__(face_groups_per_block<face_lines<A::emulated, 
   }
   group_sync<FT>();
   // F1: interpolate along t1
-  if (L) {   // item (f, sc, j2): one line of N values -> Q
+  if constexpr (EF) {   // lines (f, sc, j2) folded, then item (f, sc, j2, q1 < QH)
+    for (int it = t; it < nact * 6 * N * NF; it += FT) {
+      const int r = it / NF, j = it - r * NF;   // r = (f, sc, j2)
+      const int f = r / (6 * N);
+      fold_pair<A>(FACE_T0(f) + (r - f * 6 * N) * N + j, N - 1 - 2 * j);
+    }
+    group_sync<FT>();
+    for (int it = t; it < nact * 6 * N * QH; it += FT) {
+      const int q1 = it % QH, r = it / QH;
+      const int f = r / (6 * N), l = r - f * 6 * N;
+      const int sc = l / N, j2 = l - sc * N;
+      V e, o;
+      fold_dot<A, N, NH, NF>(sZE + q1 * NH, 1, sZO + q1 * NF, 1, FACE_T0(f) + l * N, 1, e, o);
+      V* g = FACE_G1(f) + sc * QN + Q * j2;
+      g[q1] = A::add(e, o);
+      if (q1 != Q - 1 - q1) g[Q - 1 - q1] = A::sub(e, o);
+    }
+  } else if constexpr (L) {   // item (f, sc, j2): one line of N values -> Q
     for (int it = t; it < nact * 6 * N; it += FT) {
       const int f = it / (6 * N), i = it - f * 6 * N;
       const int sc = i / N, j2 = i - sc * N;
@@ -1066,7 +1137,25 @@ __global__ void __launch_bounds__(face_groups_per_block<face_lines<A::emulated, 
   }
   group_sync<FT>();
   // F2: along t2 (the traces are compared in F3, so they are normalised)
-  if (L) {   // item (f, sc, q1)
+  if constexpr (EF) {   // columns (f, sc, q1) folded, then item (f, sc, q1, q2 < QH)
+    for (int it = t; it < nact * 6 * Q * NF; it += FT) {
+      const int r = it / NF, j = it - r * NF;   // r = (f, sc, q1)
+      const int f = r / (6 * Q), l = r - f * 6 * Q;
+      const int sc = l / Q, q1 = l - sc * Q;
+      fold_pair<A>(FACE_G1(f) + sc * QN + q1 + Q * j, Q * (N - 1 - 2 * j));
+    }
+    group_sync<FT>();
+    for (int it = t; it < nact * 6 * Q * QH; it += FT) {
+      const int q2 = it % QH, r = it / QH;
+      const int f = r / (6 * Q), l = r - f * 6 * Q;
+      const int sc = l / Q, q1 = l - sc * Q;
+      V e, o;
+      fold_dot<A, N, NH, NF>(sZE + q2 * NH, 1, sZO + q2 * NF, 1, FACE_G1(f) + sc * QN + q1, Q, e, o);
+      V* g = FACE_G2(f) + sc * QQ + q1;
+      g[Q * q2] = A::add(e, o);
+      if (q2 != Q - 1 - q2) g[Q * (Q - 1 - q2)] = A::sub(e, o);
+    }
+  } else if constexpr (L) {   // item (f, sc, q1)
     for (int it = t; it < nact * 6 * Q; it += FT) {
       const int f = it / (6 * Q), i = it - f * 6 * Q;
       const int sc = i / Q, q1 = i - sc * Q;
@@ -1104,7 +1193,25 @@ __global__ void __launch_bounds__(face_groups_per_block<face_lines<A::emulated, 
   }
   group_sync<FT>();
   // F4: test along t2 (weights w_q2)
-  if (L) {   // item (f, c, q1): Q values -> N
+  if constexpr (EF) {   // flux columns (f, c, q1) folded, then item (f, c, q1, j2 < NH)
+    for (int it = t; it < nact * 3 * Q * QF; it += FT) {
+      const int r = it / QF, i = it - r * QF;   // r = (f, c, q1)
+      const int f = r / (3 * Q), l = r - f * 3 * Q;
+      const int c = l / Q, q1 = l - c * Q;
+      fold_pair<A>(FACE_G1(f) + c * QQ + q1 + Q * i, Q * (Q - 1 - 2 * i));
+    }
+    group_sync<FT>();
+    for (int it = t; it < nact * 3 * Q * NH; it += FT) {
+      const int j2 = it % NH, r = it / NH;
+      const int f = r / (3 * Q), l = r - f * 3 * Q;
+      const int c = l / Q, q1 = l - c * Q;
+      V e, o;
+      fold_dot<A, Q, QH, QF>(sTE + j2, NH, sTO + j2, NH, FACE_G1(f) + c * QQ + q1, Q, e, o);
+      V* k = FACE_T0(f) + c * QN + q1;
+      k[Q * j2] = A::add(e, o);
+      if (j2 != N - 1 - j2) k[Q * (N - 1 - j2)] = A::sub(e, o);
+    }
+  } else if constexpr (L) {   // item (f, c, q1): Q values -> N
     for (int it = t; it < nact * 3 * Q; it += FT) {
       const int f = it / (3 * Q), i = it - f * 3 * Q;
       const int c = i / Q, q1 = i - c * Q;
@@ -1132,7 +1239,23 @@ __global__ void __launch_bounds__(face_groups_per_block<face_lines<A::emulated, 
   // the face area scales the stored results in FP64 (one multiplication
   // after the conversion instead of an emulated product)
   const double area = A::to_double(tb.area[d]);
-  if (L) {   // item (f, c, j2)
+  if constexpr (EF) {   // rows (f, c, j2) folded, then item (f, c, j2, j1 < NH)
+    for (int it = t; it < nact * 3 * N * QF; it += FT) {
+      const int r = it / QF, i = it - r * QF;   // r = (f, c, j2)
+      const int f = r / (3 * N), l = r - f * 3 * N;
+      fold_pair<A>(FACE_T0(f) + l * Q + i, Q - 1 - 2 * i);
+    }
+    group_sync<FT>();
+    for (int it = t; it < nact * 3 * N * NH; it += FT) {
+      const int j1 = it % NH, r = it / NH;
+      const int f = r / (3 * N), l = r - f * 3 * N;   // l = (c, j2)
+      V e, o;
+      fold_dot<A, Q, QH, QF>(sTE + j1, NH, sTO + j1, NH, FACE_T0(f) + l * Q, 1, e, o);
+      double* dst = rface + ((size_t)d * m.E + face_el(f)) * 3 * NN + l * N;
+      dst[j1] = area * A::to_double(A::add(e, o));
+      if (j1 != N - 1 - j1) dst[N - 1 - j1] = area * A::to_double(A::sub(e, o));
+    }
+  } else if constexpr (L) {   // item (f, c, j2)
     for (int it = t; it < nact * 3 * N; it += FT) {
       const int f = it / (3 * N), i = it - f * 3 * N;
       const int c = i / N, j2 = i - c * N;
