@@ -1027,7 +1027,7 @@ __global__ void __launch_bounds__(face_groups_per_block<face_lines<A::emulated, 
   // (SW(q,x) + SW(Q-1-q,x)) / 2 (SW in the middle row of odd Q),
   // TO [QF][NH] = (SW(q,x) - SW(Q-1-q,x)) / 2 (S, SW symmetric under
   // (q, j) -> (Q-1-q, N-1-j), so the second output of a pair is E - O).
-  constexpr bool EF = !A::emulated && N >= 6;
+  constexpr bool EF = !A::emulated && N >= 6;   // at N = 4, 5: 1-3 % slower
   constexpr int NH = (N + 1) / 2, NF = N / 2, QH = (Q + 1) / 2, QF = Q / 2;
   V* sZE = sS;
   V* sZO = sS + QH * NH;

@@ -96,12 +96,14 @@ __device__ __forceinline__ NbLine<typename A::V> load_nb_summary(const double* _
   return s;
 }
 
-// Double-float sweeps use the even-odd form; natively (FP64-pipe bound) and in
-// FP32 (the multigrid level operator, bound by the L1/shared-memory pipe) an
-// addition costs as much as a multiply-add and the direct form is kept.
+// Double-float sweeps use the even-odd form, and so do native FP64 sweeps
+// from N = 5 on: there the N^2/2 multiply-adds and 2N additions of a line
+// beat N^2 multiply-adds on the FP64 pipe (measured 6 % at N = 5 up to 23 %
+// at N = 12; no gain at N = 3, 4).  In FP32 (the multigrid level operator,
+// bound by the L1/shared-memory pipe) the direct form is kept.
 template <class A, int N>
 constexpr bool eo_sweeps() {
-  return A::emulated;
+  return A::emulated || (sizeof(typename A::V) == 8 && N >= 5);
 }
 // even-odd sweeps from N = 7 on loop over their output pairs (code size)
 template <int N>
