@@ -49,13 +49,14 @@ void convective_set_mix(int period, int nnative) {
 
 // Which FP64-wide arrangement runs each convective kernel (3/2 rule), from
 // the measured times at ~16.8M DoFs on GB300: the face kernel in
-// triple-float where it beat native FP64 (k = 2, 3, 4, 5, 9: 3.49 vs 4.18,
-// 4.25 vs 4.62, 3.22 vs 4.09, 3.96 vs 5.15, 3.62 vs 3.85 ms), the cell kernel
+// triple-float where it beat native FP64 (k = 2, 3, 4, 5: 3.58 vs 4.17,
+// 4.34 vs 4.61, 3.31 vs 4.09, 4.04 vs 4.11 ms; at k = 9 the even-odd native
+// kernel now wins, 2.98 vs 3.72 ms), the cell kernel
 // with mixed blocks where that beat native (k = 2: 3 of every 5 blocks
 // native, 5.48 vs 7.29 ms; k = 3: 3 of 4, 9.77 vs 11.59 ms); native FP64
 // elsewhere (triple-float alone was 0.6-0.95 of native from k = 3 on, the
 // mixed cell kernel slower from k = 4 on).
-constexpr bool tf64_faces(int N) { return (N >= 3 && N <= 6) || N == 10; }
+constexpr bool tf64_faces(int N) { return N >= 3 && N <= 6; }
 constexpr bool mixed_cells(int N) { return N == 3 || N == 4; }
 
 template <int N, int Q>
