@@ -349,6 +349,13 @@ int dgns_debug_laplace_f32_kernel(int variant);
  * left results unwritten).  Synchronous device read. */
 long long dgns_debug_laplace_f32_timeouts(void);
 long long dgns_debug_live_allocations(void);
+/* Test hook: y[i] = (double) x[i] for n device floats, by the conversion the
+ * FP32 multigrid preconditioner uses on its output (on the bit patterns for
+ * normal floats and zeros, by the hardware for the others; exact either way).
+ * x, y: device pointers owned by the caller, n >= 0.  Runs on the default
+ * stream and synchronises it.  Returns DGNS_ERR_INVALID_ARG for n < 0 or a
+ * null pointer with n > 0, DGNS_ERR_CUDA on a launch error. */
+int dgns_debug_widen_f32(const float* x, double* y, long long n);
 
 #ifdef __cplusplus
 }

@@ -62,6 +62,7 @@ SIGNATURES = {
     "dgns_debug_laplace_f32_kernel": (_I, [_I]),
     "dgns_debug_laplace_f32_timeouts": (ctypes.c_longlong, []),
     "dgns_debug_live_allocations": (_LL, []),
+    "dgns_debug_widen_f32": (_I, [_P, _P, _LL]),
     "dgns_status_string": (ctypes.c_char_p, [_I]),
     "dgns_last_error": (ctypes.c_char_p, []),
     "dgns_sizes": (_I, [_P, ctypes.POINTER(_LL), ctypes.POINTER(_LL)]),

@@ -547,7 +547,10 @@ int setup_mg(dgns_ctx* c) {
   return 0;
 }
 
-int precondition(dgns_ctx* c, const double* r, double* z, const dgns_solve_params* prm, long long n) {
+// z = M^-1 r; with dot_slot >= 0 also scal[dot_slot] = (r, z) (in the
+// FP32 V-cycle's last pass over z, summed as dot() sums it).
+int precondition(dgns_ctx* c, const double* r, double* z, const dgns_solve_params* prm, long long n,
+                 int dot_slot = -1) {
   if (c->mg_prec == 0 || c->levels.empty()) {
     DG_CUDA(cudaMemcpyAsync(z, r, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
   } else {
@@ -559,32 +562,35 @@ int precondition(dgns_ctx* c, const double* r, double* z, const dgns_solve_param
     if (prm->project_mean) {
       if (f32) DG_TRY(sum_f32((const float*)x, n, c->red, S_SUM, c->s));
       else DG_TRY(sum((const double*)x, n, c->red, S_SUM, c->s));
-      DG_TRY(convert_shift(x, f32, z, false, n, &c->red, S_SUM, c->s));
-      return 0;
     }
-    DG_TRY(convert_shift(x, f32, z, false, n, nullptr, 0, c->s));
+    const int shift = prm->project_mean ? S_SUM : -1;
+    if (f32 && dot_slot >= 0) return widen_shift_dot((const float*)x, z, n, c->red, shift, r, dot_slot, c->s);
+    DG_TRY(convert_shift(x, f32, z, false, n, shift >= 0 ? &c->red : nullptr, shift, c->s));
+    if (dot_slot >= 0) DG_TRY(dot(r, z, n, c->red, dot_slot, c->s));
     return 0;
   }
   if (prm->project_mean) {
     DG_TRY(sum(z, n, c->red, S_SUM, c->s));
     DG_TRY(convert_shift(z, false, z, false, n, &c->red, S_SUM, c->s));
   }
+  if (dot_slot >= 0) DG_TRY(dot(r, z, n, c->red, dot_slot, c->s));
   return 0;
 }
 
-// The CG preconditioner r -> z on the context's work vectors, replayed from a
-// CUDA graph: one V-cycle is ~10 launches per level, and on the coarse levels
-// launch latency dominates.  The first call for a parameter set runs eagerly
-// (it also sets kernel attributes), then captures the same sequence.
+// The CG preconditioner r -> z on the context's work vectors, with
+// scal[S_RZNEW] = (r, z), replayed from a CUDA graph: one V-cycle is ~10
+// launches per level, and on the coarse levels launch latency dominates.
+// The first call for a parameter set runs eagerly (it also sets kernel
+// attributes), then captures the same sequence.
 int precondition_cg(dgns_ctx* c, const dgns_solve_params* prm, long long n) {
-  if (c->mg_prec == 0 || c->levels.empty()) return precondition(c, c->r, c->z, prm, n);
+  if (c->mg_prec == 0 || c->levels.empty()) return precondition(c, c->r, c->z, prm, n, S_RZNEW);
   const bool same = c->vc_exec && c->vc_key[0] == prm->cheb_degree && c->vc_key[1] == prm->cheb_coarse_iters &&
                     c->vc_key[2] == prm->project_mean && c->vc_range == prm->smoothing_range;
   if (same) {
     DG_CUDA(cudaGraphLaunch(c->vc_exec, c->s));
     return 0;
   }
-  DG_TRY(precondition(c, c->r, c->z, prm, n));
+  DG_TRY(precondition(c, c->r, c->z, prm, n, S_RZNEW));
   if (!c->gs) DG_CUDA(cudaStreamCreateWithFlags(&c->gs, cudaStreamNonBlocking));
   if (c->vc_exec) {
     cudaGraphExecDestroy(c->vc_exec);
@@ -593,7 +599,7 @@ int precondition_cg(dgns_ctx* c, const dgns_solve_params* prm, long long n) {
   cudaStream_t saved = c->s;
   DG_CUDA(cudaStreamBeginCapture(c->gs, cudaStreamCaptureModeThreadLocal));
   c->s = c->gs;
-  const int rc = precondition(c, c->r, c->z, prm, n);
+  const int rc = precondition(c, c->r, c->z, prm, n, S_RZNEW);
   c->s = saved;
   cudaGraph_t g = nullptr;
   const cudaError_t e = cudaStreamEndCapture(c->gs, &g);
@@ -823,6 +829,14 @@ int dgns_debug_fail_alloc(long long n) {
 }
 
 long long dgns_debug_live_allocations(void) { return g_live_allocs.load(); }
+
+int dgns_debug_widen_f32(const float* x, double* y, long long n) {
+  if (n < 0 || (n > 0 && (!x || !y))) return fail(DGNS_ERR_INVALID_ARG, "widen: bad arguments");
+  if (n == 0) return 0;
+  DG_TRY(convert_shift(x, true, y, false, n, nullptr, -1, 0));
+  DG_CUDA(cudaStreamSynchronize(0));
+  return 0;
+}
 
 int dgns_sizes(const dgns_ctx* c, long long* nu, long long* np) {
   if (!c) return fail(DGNS_ERR_INVALID_ARG, "ctx is null");
@@ -1610,9 +1624,9 @@ int dgns_cg_mg_solve(dgns_ctx* c, double* x, const double* b, const dgns_solve_p
     inf.rel_res = 0.0;
     if (!std::isfinite(nb)) status = fail(DGNS_ERR_NONFINITE, "non-finite right-hand side");
   } else {
-    DG_TRY(precondition_cg(c, &prm, n));
+    DG_TRY(precondition_cg(c, &prm, n));   // scal[S_RZNEW] = (r, z)
     DG_TRY(cg_direction(c->p, c->z, n, c->red, true, c->s));
-    DG_TRY(dot(c->r, c->z, n, c->red, S_RZ, c->s));
+    DG_TRY(scal_rotate(c->red, c->s));
     double res = 1.0;
     int it = 0;
     status = DGNS_ERR_NOT_CONVERGED;
@@ -1632,8 +1646,7 @@ int dgns_cg_mg_solve(dgns_ctx* c, double* x, const double* b, const dgns_solve_p
         status = DGNS_OK;
         break;
       }
-      DG_TRY(precondition_cg(c, &prm, n));
-      DG_TRY(dot(c->r, c->z, n, c->red, S_RZNEW, c->s));
+      DG_TRY(precondition_cg(c, &prm, n));   // scal[S_RZNEW] = (r, z)
       DG_TRY(cg_direction(c->p, c->z, n, c->red, false, c->s));
     }
     inf.iterations = it;

@@ -35,6 +35,12 @@ int cg_direction(double* p, const double* z, long long n, Reducer& R, bool first
 // y = x - scal[slot] / n  (no shift when R is null), with precision conversion
 int convert_shift(const void* x, bool x32, void* y, bool y32, long long n, const Reducer* R,
                   int slot, cudaStream_t s);
+// z = (double) x - scal[shift_slot] / n (no shift when shift_slot < 0) and
+// scal[dot_slot] = (r, z), summed as dot() sums it
+int widen_shift_dot(const float* x, double* z, long long n, Reducer& R, int shift_slot, const double* r,
+                    int dot_slot, cudaStream_t s);
+// scal[S_RZ] = scal[S_RZNEW]
+int scal_rotate(Reducer& R, cudaStream_t s);
 // x = c * dinv[i % nper] * b
 int cheb_first(bool fp32, const void* b, const void* dinv, void* x, long long n, int nper, double c,
                cudaStream_t s);

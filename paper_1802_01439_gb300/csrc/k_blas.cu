@@ -109,6 +109,32 @@ __global__ void __launch_bounds__(RT) cg_direction_kernel(double* __restrict__ p
 
 __global__ void rotate_kernel(double* scal) { scal[S_RZ] = scal[S_RZNEW]; }
 
+// float -> double without the FP64 pipe (on this part a hardware conversion
+// costs the FP64 pipe about as much as an FP64 addition).  For a normal
+// float the double has the same sign and significand bits and the exponent
+// rebiased from 127 to 1023 (IEEE 754 binary32 -> binary64), so the
+// conversion is exact and done on the bit patterns; zeros keep their sign.
+// Subnormals, infinities and NaNs take the hardware conversion.
+__device__ __forceinline__ double widen_f32(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) {
+    if ((u & 0x7fffffffu) == 0u) return __longlong_as_double((long long)((unsigned long long)u << 32));
+    return (double)f;
+  }
+  const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                               ((unsigned long long)(e + 896u) << 52) |
+                               ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)b);
+}
+template <class TO, class TI>
+__device__ __forceinline__ TO convert_to(TI v) {
+  if constexpr (sizeof(TI) == 4 && sizeof(TO) == 8)
+    return widen_f32(v);
+  else
+    return (TO)v;
+}
+
 // y = (double) x - mean, mean = scal[slot] / n  (or no shift when slot < 0)
 template <class TI, class TO>
 __global__ void __launch_bounds__(RT) convert_shift_kernel(const TI* __restrict__ x, TO* __restrict__ y,
@@ -118,12 +144,32 @@ __global__ void __launch_bounds__(RT) convert_shift_kernel(const TI* __restrict_
   if (slot < 0) {
     // no shift: a plain conversion (an FP64 subtraction of zero per entry
     // would cost the FP64 pipe as much as a pass over memory)
-    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < n; i += stride) y[i] = (TO)x[i];
+    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < n; i += stride) y[i] = convert_to<TO>(x[i]);
     return;
   }
   const double mu = scal[slot] / (double)n;
   for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < n; i += stride)
-    y[i] = (TO)((double)x[i] - mu);
+    y[i] = (TO)(convert_to<double>(x[i]) - mu);
+}
+
+// z = (double) x - mean (mean = scal[slot] / n; none when slot < 0) and the
+// partial sums of (r, z) in the order of dot_partial (same grid, same
+// per-thread order), so the sum equals that of a separate dot pass
+__global__ void __launch_bounds__(RT) widen_shift_dot_kernel(const float* __restrict__ x, double* __restrict__ z,
+                                                             const double* __restrict__ r, long long n,
+                                                             const double* __restrict__ scal, int slot,
+                                                             double* __restrict__ part) {
+  const double mu = slot < 0 ? 0.0 : scal[slot] / (double)n;
+  double s = 0.0;
+  const long long stride = (long long)gridDim.x * RT;
+  for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < n; i += stride) {
+    double zi = widen_f32(x[i]);
+    if (slot >= 0) zi -= mu;
+    z[i] = zi;
+    s = fma(r[i], zi, s);
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
 // x = c * dinv[i % nper] * b  (first Chebyshev step from a zero guess)
@@ -222,6 +268,19 @@ int cg_update(double* x, double* r, const double* p, const double* Ap, long long
 int cg_direction(double* p, const double* z, long long n, Reducer& R, bool first, cudaStream_t s) {
   cg_direction_kernel<<<grid_for(n), RT, 0, s>>>(p, z, n, R.scal, first ? 1 : 0);
   if (!first) rotate_kernel<<<1, 1, 0, s>>>(R.scal);
+  return status();
+}
+
+int widen_shift_dot(const float* x, double* z, long long n, Reducer& R, int shift_slot, const double* r,
+                    int dot_slot, cudaStream_t s) {
+  const unsigned g = grid_for(n);
+  widen_shift_dot_kernel<<<g, RT, 0, s>>>(x, z, r, n, R.scal, shift_slot, R.part);
+  finish_sum<<<1, RT, 0, s>>>(R.part, (int)g, R.scal, dot_slot);
+  return status();
+}
+
+int scal_rotate(Reducer& R, cudaStream_t s) {
+  rotate_kernel<<<1, 1, 0, s>>>(R.scal);
   return status();
 }
 

@@ -182,3 +182,28 @@ def test_cg_mg_iterations_are_mesh_independent(kp):
         assert info["rc"] == 0 and info["rel_res"] <= 1e-6
         its.append(info["iterations"])
     assert max(its) - min(its) <= 2 and max(its) <= 12, its
+
+
+def test_widen_f32_is_exact():
+    """The FP32 -> FP64 conversion at the V-cycle's exit (done on the bit
+    patterns for normal floats and zeros) gives the IEEE 754 value of every
+    float: random normal floats over the whole exponent range, signed zeros,
+    the extreme normals, subnormals, infinities and a NaN."""
+    ctx = context(2, 2)
+    rng = np.random.default_rng(11)
+    bits = rng.integers(0, 2 ** 32, 200000, dtype=np.uint64).astype(np.uint32)
+    special = np.array([0.0, -0.0, 1.0, -1.0, np.finfo(np.float32).max, -np.finfo(np.float32).max,
+                        np.finfo(np.float32).tiny, -np.finfo(np.float32).tiny, 1e-40, -3e-45,
+                        np.inf, -np.inf, np.nan], dtype=np.float32)
+    x = np.concatenate([bits.view(np.float32), special])
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty(x.size, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    assert ctx.lib.dgns_debug_widen_f32(xd.data_ptr(), yd.data_ptr(), x.size) == 0
+    y = yd.cpu().numpy()
+    ref = x.astype(np.float64)
+    fin = ~np.isnan(ref)
+    assert np.array_equal(y[fin].view(np.uint64), ref[fin].view(np.uint64))
+    assert np.all(np.isnan(y[~fin]))
+    assert ctx.lib.dgns_debug_widen_f32(xd.data_ptr(), yd.data_ptr(), -1) != 0
+    assert ctx.lib.dgns_debug_widen_f32(xd.data_ptr(), yd.data_ptr(), 0) == 0
