@@ -121,13 +121,15 @@ def conv_cell_ops(N, Q):
 def conv_face_ops(N, Q):
     """Convective face term per face: traces of 3 components of both cells
     at the Q^2 face points (the face layer's N^2 nodal values, sweeps of N and
-    Q lines N -> Q), the LLF flux (per point 3 x (2 products, sum, halving,
-    jump, product with the penalty, sum) + max(|a|, |b|): 3 multiply-adds and
-    17 additions or products), and the test of the 3 flux components back to
-    the N^2 layer (Q and N lines Q -> N)."""
+    Q lines N -> Q), the LLF flux (per point and component a product, a
+    multiply-add for the average of u_c u_n, the jump and a multiply-add with
+    the penalty: 6 multiply-adds and 6 additions or products per point; the
+    halving of the average belongs to the face-area factor and
+    max(|a|, |b|) is a comparison), and the test of the 3 flux components
+    back to the N^2 layer (Q and N lines Q -> N)."""
     ops = (0, 0)
     ops = _add(ops, eo_line(N, Q), 6 * (N + Q))
-    ops = _add(ops, (3 * Q * Q, 17 * Q * Q))
+    ops = _add(ops, (6 * Q * Q, 6 * Q * Q))
     ops = _add(ops, eo_line(Q, N), 3 * (Q + N))
     return ops
 

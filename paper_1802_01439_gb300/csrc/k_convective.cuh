@@ -1182,14 +1182,37 @@ __global__ void __launch_bounds__(face_groups_per_block<face_lines<A::emulated, 
     const V* g2 = FACE_G2(f) + pt;
     const V umc = g2[c * QQ], upc = g2[(3 + c) * QQ];
     const V unm = g2[d * QQ], unp = g2[(3 + d) * QQ];
-    const V am = A::absval(unm), ap = A::absval(unp);
-    const V lam = A::greater(am, ap) ? am : ap;
-    // 0.5 (u-_c un- + u+_c un+) + lambda (u-_c - u+_c), the halving is exact
-    Acc fl;
-    A::acc_first(fl, umc, A::half(unm));
-    A::acc_fma(fl, upc, A::half(unp));
-    A::acc_fma(fl, lam, A::sub(umc, upc));
-    FACE_G1(f)[i] = A::acc_get_norm(fl);
+    if constexpr (!A::emulated) {
+      // natively twice the flux, u-_c un- + u+_c un+ + 2 lambda (u-_c - u+_c),
+      // in four FP64 operations: lambda = max(|un-|, |un+|) by an integer
+      // comparison (the bit patterns of non-negative doubles order as their
+      // values), 2 lambda by an exponent increment (normal numbers; else an
+      // addition), and the halving moved into the face area of F5.  Scaling
+      // by 2 commutes with every rounding, so the results are those of the
+      // halved form.
+      const long long bm = __double_as_longlong(unm) & 0x7fffffffffffffffLL;
+      const long long bp = __double_as_longlong(unp) & 0x7fffffffffffffffLL;
+      const long long bl = bm > bp ? bm : bp;
+      const long long ex = bl >> 52;
+      double lam2;
+      if (ex != 0 && ex < 2046) {
+        lam2 = __longlong_as_double(bl + (1LL << 52));
+      } else {
+        const double l = __longlong_as_double(bl);
+        lam2 = l + l;
+      }
+      const double t = fma(upc, unp, umc * unm);
+      FACE_G1(f)[i] = fma(lam2, umc - upc, t);
+    } else {
+      const V am = A::absval(unm), ap = A::absval(unp);
+      const V lam = A::greater(am, ap) ? am : ap;
+      // 0.5 (u-_c un- + u+_c un+) + lambda (u-_c - u+_c), the halving is exact
+      Acc fl;
+      A::acc_first(fl, umc, A::half(unm));
+      A::acc_fma(fl, upc, A::half(unp));
+      A::acc_fma(fl, lam, A::sub(umc, upc));
+      FACE_G1(f)[i] = A::acc_get_norm(fl);
+    }
   }
   group_sync<FT>();
   // F4: test along t2 (weights w_q2)
@@ -1238,7 +1261,7 @@ __global__ void __launch_bounds__(face_groups_per_block<face_lines<A::emulated, 
   // F5: test along t1 (weights w_q1), times the face area, store
   // the face area scales the stored results in FP64 (one multiplication
   // after the conversion instead of an emulated product)
-  const double area = A::to_double(tb.area[d]);
+  const double area = A::to_double(tb.area[d]) * (A::emulated ? 1.0 : 0.5);   // natively F3 doubled the flux
   if constexpr (EF) {   // rows (f, c, j2) folded, then item (f, c, j2, j1 < NH)
     for (int it = t; it < nact * 3 * N * QF; it += FT) {
       const int r = it / QF, i = it - r * QF;   // r = (f, c, j2)

@@ -83,6 +83,8 @@ def test_convective_ops_are_below_the_direct_form():
                        + (8 * Q * Q + 9 * N * Q + 6 * N * N) * Q * N)
         assert cc[0] <= direct_cell
         assert cf[0] > 0 and cf[1] > 0
+    # face: traces 6 (N + Q) lines N -> Q, flux 6 + 6 per point, tests 3 (Q + N) lines Q -> N
+    assert bench.conv_face_ops(4, 6) == (6 * 10 * 12 + 6 * 36 + 3 * 10 * 12, 6 * 10 * 10 + 6 * 36 + 3 * 10 * 10)
     assert bench.conv_cell_ops(4, 6) == (3 * (16 + 24 + 36) * 12 + (8 * 36 + 9 * 24 + 6 * 16) * 12,
                                          3 * (16 + 24 + 36) * 10 + 6 * 216 + (8 * 36 + 9 * 24 + 6 * 16) * 10
                                          + 3 * 64 + 18 * 16)
