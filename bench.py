@@ -67,7 +67,7 @@ EMU_FP32_FLOPS = {1: (15, 8), 2: (51, 21)}
 # of the same launch configuration (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by (kernel, fp64 mode, k); absent where no
 # capture of the current kernel exists.
-KERNEL_TRAFFIC = {("conv_kernel", 0, 9): 551.2e6 + 385.6e6}   # profiles/conv_f64_k9_26c_ncu.md
+KERNEL_TRAFFIC = {}   # (kernel, fp64_mode, k) -> DRAM bytes per launch from an ncu capture of the current kernel
 
 
 # ----------------------------------------------------------- flop counts

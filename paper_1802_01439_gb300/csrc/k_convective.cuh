@@ -42,12 +42,21 @@ constexpr int conv_cells_per_block() {
   return N * N >= 64 ? 1 : 64 / (N * N);
 }
 
+// Native FP64 at N = 10: the cell's buffers alias by phase (ConvLayout,
+// compact), so that two cells of 8 warps share an SM instead of one of 16;
+// one computes while the other waits at its phase barriers.
+template <bool EM, int N>
+constexpr bool conv_compact() {
+  return !EM && N == 10;
+}
 // Threads per group of the forward convective kernel: one warp up to N = 5;
 // above, more threads per cell as the cell's shared memory grows (from
-// N = 10 on one cell fills an SM's shared memory, so it gets 16 warps).
-template <int N>
+// N = 10 on one cell fills an SM's shared memory, so it gets 16 warps; 8 in
+// the compact layout).  EM: emulated arithmetic (the default for callers
+// without an arithmetic).
+template <int N, bool EM = true>
 constexpr int conv_threads() {
-  return N <= 5 ? 32 : N == 6 ? 64 : N == 7 ? 128 : N <= 9 ? 256 : 512;
+  return N <= 5 ? 32 : N == 6 ? 64 : N == 7 ? 128 : (N <= 9 || conv_compact<EM, N>()) ? 256 : 512;
 }
 // Cells per thread group: two for N = 2, where one cell's plane phases have
 // 27, 24, 12 and 24 work items for 32 lanes.  (Two cells per warp at N = 4
@@ -56,13 +65,13 @@ template <int N>
 constexpr int conv_cells_per_group() {
   return N == 2 ? 2 : 1;
 }
-template <int N>
+template <int N, bool EM = true>
 constexpr int conv_groups_per_block() {
-  return conv_threads<N>() >= 128 ? 1 : 128 / conv_threads<N>();
+  return conv_threads<N, EM>() >= 128 ? 1 : 128 / conv_threads<N, EM>();
 }
-template <int N>
+template <int N, bool EM = true>
 constexpr int conv_fwd_cells_per_block() {
-  return conv_groups_per_block<N>() * conv_cells_per_group<N>();
+  return conv_groups_per_block<N, EM>() * conv_cells_per_group<N>();
 }
 
 // Shared memory of one cell; a group's cells lie type by type
@@ -71,7 +80,7 @@ constexpr int conv_fwd_cells_per_block() {
 // Region sizes are even, so that with 12-byte (triple-float) values the
 // raw doubles of the face integrals in U1R stay 8-byte aligned.
 constexpr int even_up(int v) { return v + (v & 1); }
-template <int N, int Q>
+template <int N, int Q, bool CMP = false>
 struct ConvLayout {
   static constexpr int N3 = N * N * N;
   static constexpr int U = 3 * N3;               // nodal velocity
@@ -86,7 +95,12 @@ struct ConvLayout {
   static constexpr int Y = 6 * N * N;            // xy-tested plane
   static constexpr int PXY = P + X + Y;
   static constexpr int UP = even_up(U > PXY ? U : PXY);   // nodal u first, plane work later
-  static constexpr int PER = UP + U1R + U2;
+  // Compact (one cell per group): [W | U2], W = max(U1, PXY + R + P).  The
+  // x-interpolated values lie at 0 in W; in the plane loop W holds the plane
+  // work (PXY) and behind it the face integrals and the second plane; the
+  // nodal u lies at the start of U2's region (dead before U2 is written).
+  static constexpr int W = even_up(U1 > PXY + R + P ? U1 : PXY + R + P);
+  static constexpr int PER = CMP ? W + U2 : UP + U1R + U2;
 };
 // Native FP64 from N = 6 on, the cell kernel takes the quadrature planes q
 // and Q-1-q together (see conv_cells); the second plane needs room behind
@@ -95,7 +109,7 @@ struct ConvLayout {
 template <bool EMULATED, int N, int Q>
 constexpr bool conv_pair_planes() {
   return !EMULATED && N >= 6 && conv_cells_per_group<N>() == 1 &&
-         ConvLayout<N, Q>::R + ConvLayout<N, Q>::P <= ConvLayout<N, Q>::U1R &&
+         (conv_compact<EMULATED, N>() || ConvLayout<N, Q>::R + ConvLayout<N, Q>::P <= ConvLayout<N, Q>::U1R) &&
          ConvLayout<N, Q>::Y <= ConvLayout<N, Q>::P;
 }
 
@@ -370,19 +384,21 @@ __device__ __forceinline__ void conv_cells(const double* __restrict__ u3, const 
                                            const MeshDims& m, const unsigned bid) {
   typedef typename A::V V;
   typedef typename A::Acc Acc;
-  typedef ConvLayout<N, Q> LY;
+  constexpr bool CMP = conv_compact<A::emulated, N>();
+  typedef ConvLayout<N, Q, CMP> LY;
   static_assert(sizeof(V) % 4 == 0 && sizeof(V) <= 12, "two or three 4-byte words per value");
-  constexpr int NT = conv_threads<N>(), CPG = conv_cells_per_group<N>();
+  constexpr int NT = conv_threads<N, A::emulated>(), CPG = conv_cells_per_group<N>();
+  static_assert(!CMP || CPG == 1, "the compact layout holds one cell per group");
   constexpr int N3 = N * N * N, QQ = Q * Q, NN = N * N, QN = Q * N;
   static_assert(CPG <= 2, "one or two cells per group");
   V* sm = reinterpret_cast<V*>(dyn_smem());
   const int g = threadIdx.x / NT;
   const int t = threadIdx.x - g * NT;
-  const long long c0 = ((long long)bid * conv_groups_per_block<N>() + g) * CPG;
+  const long long c0 = ((long long)bid * conv_groups_per_block<N, A::emulated>() + g) * CPG;
   const long long last = m.E - 1;
   constexpr int QH = (Q + 1) / 2, QF = Q / 2, NH = (N + 1) / 2, NF = N / 2;
   constexpr bool PR = conv_pair_rows<N>();
-  V* sS = sm + conv_fwd_cells_per_block<N>() * LY::PER;   // tables: S, SW, DW, TY[0..2] (or TYeo), EO[0..1]
+  V* sS = sm + conv_fwd_cells_per_block<N, A::emulated>() * LY::PER;   // tables: S, SW, DW, TY[0..2] (or TYeo), EO[0..1]
   V* sSW = sS + QN;
   V* sDW = sSW + QN;
   V* sTY = sDW + QN;
@@ -442,12 +458,16 @@ __device__ __forceinline__ void conv_cells(const double* __restrict__ u3, const 
     sEO[i] = tb.EO[0][i];
     sEO[Q * NH + i] = tb.EO[1][i];
   }
-  V* sUg = sm + g * CPG * LY::PER;   // nodal u of the group's cells [j][c][N3], dead after the x interpolation
-  V* sPg = sUg;                      // plane work reuses it: u [j][c][QQ]
-  V* sXg = sPg + CPG * LY::P;        // x tests [j][k][qy][x]
-  V* sYg = sXg + CPG * LY::X;        // y tests [j][c][2][y][x]
-  V* sU1g = sUg + CPG * LY::UP;      // x-interpolated, cell j at j U1R; later the face integrals
-  V* sU2g = sU1g + CPG * LY::U1R;    // xy-interpolated, cell j at j U2
+  V* base = sm + g * CPG * LY::PER;
+  V* sUg = base + (CMP ? LY::W : 0);   // nodal u of the group's cells [j][c][N3], dead after the x interpolation
+  V* sPg = base;                       // plane work: u [j][c][QQ]
+  V* sXg = sPg + CPG * LY::P;          // x tests [j][k][qy][x]
+  V* sYg = sXg + CPG * LY::X;          // y tests [j][c][2][y][x]
+  V* sU1g = base + (CMP ? 0 : CPG * LY::UP);   // x-interpolated, cell j at j U1R
+  V* sU2g = base + (CMP ? LY::W : CPG * (LY::UP + LY::U1R));   // xy-interpolated, cell j at j U2
+  // the face integrals (cell j at j U1R), in the plane loop; then the x-test
+  // products (from N = 11 on) and the second plane of a pair
+  V* sRg = CMP ? base + LY::PXY : sU1g;
 
   // the group's cells (consecutive ids), clamped to the last cell
   const unsigned el0 = (unsigned)(c0 < last ? c0 : last);
@@ -581,7 +601,7 @@ __device__ __forceinline__ void conv_cells(const double* __restrict__ u3, const 
                             : dd == 0     ? pick2(j, n00, n10)
                             : dd == 1     ? pick2(j, n01, n11)
                                           : pick2(j, n02, n12);
-      cp_async8(reinterpret_cast<double*>(sU1g + j * LY::U1R) + l, rface + ((size_t)dd * m.E + cell) * 3 * NN + i);
+      cp_async8(reinterpret_cast<double*>(sRg + j * LY::U1R) + l, rface + ((size_t)dd * m.E + cell) * 3 * NN + i);
     }
   }
   cp_async_commit();
@@ -649,7 +669,7 @@ __device__ __forceinline__ void conv_cells(const double* __restrict__ u3, const 
   // the second plane of a pair sits behind the face integrals (and the
   // folded x-test products) in the dead x-interpolation buffer; its y tests
   // later replace it there
-  V* sPb = sU1g + LY::R;
+  V* sPb = sRg + LY::R;
   static_assert(!PAIR || LY::Y <= LY::P, "room for the second plane's y tests");
   if constexpr (PAIR) {
     // fold every z-column: e_z = u_z + u_{N-1-z} at z, o_z = u_z - u_{N-1-z} at N-1-z
@@ -704,7 +724,7 @@ __device__ __forceinline__ void conv_cells(const double* __restrict__ u3, const 
       // middle row of odd Q alone, in row p); else one row per item.
       if constexpr (conv_split_xtest<N>()) {
         static_assert(CPG == 1, "one cell per group");
-        V* sFE = reinterpret_cast<V*>(sU1g) + 18 * NN;   // behind the face integrals
+        V* sFE = sRg + 18 * NN;   // behind the face integrals
         V* sFO = sFE + 8 * Q * QH;
         for (int it = t; it < 8 * Q * QH; it += NT) {   // item (k, qy, i)
           const int k = it / (Q * QH), l = it - k * Q * QH;
@@ -920,7 +940,7 @@ __device__ __forceinline__ void conv_cells(const double* __restrict__ u3, const 
       if (IL % NT != 0 && l >= IL) break;
       const int c = l / NN, yx = l - c * NN;
       const int x = yx % N, y = yx / N;
-      const double* rc = reinterpret_cast<const double*>(sU1g) + c * NN;
+      const double* rc = reinterpret_cast<const double*>(sRg) + c * NN;
       double* d = dst3 + ((size_t)c * m.E + el0) * N3 + yx;
 #pragma unroll
       for (int z = 0; z < N; ++z) {
@@ -946,7 +966,7 @@ __device__ __forceinline__ void conv_cells(const double* __restrict__ u3, const 
       const int c = l / N3, rr = l - c * N3;
       const int x = rr % N, yz = rr / N;
       const int y = yz % N, z = yz / N;
-      const double* rc = reinterpret_cast<const double*>(sU1g + j * LY::U1R) + c * NN;
+      const double* rc = reinterpret_cast<const double*>(sRg + j * LY::U1R) + c * NN;
       // the face integrals arrive as doubles: added natively after the cell
       // term's conversion (a few FP64 additions instead of splits and
       // emulated additions)
@@ -963,7 +983,7 @@ __device__ __forceinline__ void conv_cells(const double* __restrict__ u3, const 
 }
 
 template <class A, int N, int Q>
-__global__ void __launch_bounds__(conv_groups_per_block<N>() * conv_threads<N>())
+__global__ void __launch_bounds__(conv_groups_per_block<N, A::emulated>() * conv_threads<N, A::emulated>())
     conv_kernel(const double* __restrict__ u3, const double* __restrict__ rface, double* __restrict__ dst3,
                 const __grid_constant__ ConvTabT<typename A::V, N, Q> tb, const MeshDims m) {
   conv_cells<A, N, Q>(u3, rface, dst3, tb, m, blockIdx.x);
@@ -981,6 +1001,8 @@ __global__ void __launch_bounds__(conv_groups_per_block<N>() * conv_threads<N>()
                     const __grid_constant__ ConvTabT<double, N, Q> tbn,
                     const __grid_constant__ ConvTabT<tf64, N, Q> tbt, const MeshDims m, const int period,
                     const int nnative) {
+  static_assert(conv_threads<N, false>() == conv_threads<N, true>() && !conv_compact<false, N>(),
+                "both arithmetics with the same block geometry");
   if ((int)(blockIdx.x % (unsigned)period) < nnative)
     conv_cells<F64, N, Q>(u3, rface, dst3, tbn, m, blockIdx.x);
   else
@@ -1370,14 +1392,14 @@ int launch_conv(int part, const MeshDims& m, const double* u3, double* rface, do
   const ConvTabT<typename A::V, N, Q> tb = conv_tables<A, N, Q>(h);
   constexpr bool FL = face_lines<A::emulated, N>();
   typedef typename A::V V;
-  constexpr int EPB = conv_fwd_cells_per_block<N>(), GPB = face_groups_per_block<FL, N, Q, sizeof(V)>(),
+  constexpr int EPB = conv_fwd_cells_per_block<N, A::emulated>(), GPB = face_groups_per_block<FL, N, Q, sizeof(V)>(),
                 FPG = faces_per_group<N>();
   constexpr int FPB = GPB * FPG;
   // tables: S, SW, DW, TY (6 Q N), EO (2 Q (N+1)/2), and natively (paired
   // planes) ZE, ZO ((Q+1)/2 N) and the z-test tables (4 (Q+1)/2 (N+1)/2)
   constexpr int NH = (N + 1) / 2, QH = (Q + 1) / 2;
   constexpr int TABS = 6 * Q * N + 2 * Q * NH + (conv_pair_planes<A::emulated, N, Q>() ? QH * N + 4 * QH * NH : 0);
-  const size_t smem = ((size_t)EPB * ConvLayout<N, Q>::PER + TABS) * sizeof(V);
+  const size_t smem = ((size_t)EPB * ConvLayout<N, Q, conv_compact<A::emulated, N>()>::PER + TABS) * sizeof(V);
   const size_t fsmem = (size_t)GPB * face_group_smem<FL, N, Q>() * sizeof(V);
   if (smem > 232448 || fsmem > 232448) return 7;
   if (cudaFuncSetAttribute(conv_kernel<A, N, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
@@ -1392,7 +1414,7 @@ int launch_conv(int part, const MeshDims& m, const double* u3, double* rface, do
   }
   if (part & 2) {
     const long long blocks = (m.E + EPB - 1) / EPB;
-    conv_kernel<A, N, Q><<<(unsigned)blocks, conv_groups_per_block<N>() * conv_threads<N>(), smem, s>>>(
+    conv_kernel<A, N, Q><<<(unsigned)blocks, conv_groups_per_block<N, A::emulated>() * conv_threads<N, A::emulated>(), smem, s>>>(
         u3, rface, dst3, tb, m);
   }
   return cudaGetLastError() == cudaSuccess ? 0 : 2;

@@ -68,8 +68,10 @@ int launch_wide(int part, const MeshDims& m, const double* u3, double* rface, do
     if (rc) return rc;
   }
   if (!(part & 2)) return 0;
-  return mixed_cells(N) ? launch_conv_mix<N, Q>(2, m, u3, rface, dst3, t, s)
-                        : launch_conv<F64, N, Q>(2, m, u3, rface, dst3, t, s);
+  if constexpr (mixed_cells(N))   // (the mixed kernel's geometry is that of N = 3, 4)
+    return launch_conv_mix<N, Q>(2, m, u3, rface, dst3, t, s);
+  else
+    return launch_conv<F64, N, Q>(2, m, u3, rface, dst3, t, s);
 }
 
 // The 3/2 rule (Q = floor(3N/2)); returns 7 for other N or Q (the caller
