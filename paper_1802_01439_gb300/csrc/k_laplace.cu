@@ -131,9 +131,24 @@ struct EpiArgs {
   G c1, c2;
 };
 
-template <int N>
+// Cells per block (N^2 threads each).  Natively in FP64 (F64 = true) the
+// counts fill the warps: on the FP64 pipe a warp instruction costs the same
+// with idle lanes, and N^2 threads leave part of the last warp idle
+// (N = 6: 3 cells in 4 warps, 84 % of the lanes busy; 8 cells in 9 warps,
+// all busy).
+template <int N, bool F64 = false>
 constexpr int cells_per_block() {
+  if constexpr (F64) {
+    if constexpr (N == 6) return 8;
+    if constexpr (N == 7) return 4;
+    if constexpr (N == 9) return 3;
+    if constexpr (N == 10) return 2;
+  }
   return N * N >= 128 ? 1 : 128 / (N * N);
+}
+template <class A>
+constexpr bool native64() {
+  return !A::emulated && sizeof(typename A::V) == 8;
 }
 
 // Shared-memory layout of a staged cell: x-lines padded to an odd length so
@@ -389,13 +404,13 @@ __device__ __forceinline__ void load_xline(const typename A::G* __restrict__ g, 
 }
 
 template <class A, int N, int EPI>
-__global__ void __launch_bounds__(cells_per_block<N>() * N * N)
+__global__ void __launch_bounds__(cells_per_block<N, native64<A>()>() * N * N)
     sipg_kernel(const typename A::G* __restrict__ src, typename A::G* __restrict__ dst,
                 const __grid_constant__ LapTab<typename A::V, N> tb, const MeshDims m, const long long ncells,
                 const EpiArgs<typename A::G> ea) {
   typedef typename A::V V;
   typedef typename A::G G;
-  constexpr int NN = N * N, NNN = NN * N, EPB = cells_per_block<N>();
+  constexpr int NN = N * N, NNN = NN * N, EPB = cells_per_block<N, native64<A>()>();
   constexpr int CS = cell_stride<N>();
   V* sX = reinterpret_cast<V*>(dyn_smem());
   V* sA = sX + EPB * CS;
@@ -543,7 +558,7 @@ template <class A, int N, int EPI>
 int launch_sipg(const MeshDims& m, int ncomp, const typename A::G* src, typename A::G* dst, const LapHost& h,
                 const EpiHost& eh, cudaStream_t s) {
   typedef typename A::G G;
-  constexpr int NN = N * N, EPB = cells_per_block<N>();
+  constexpr int NN = N * N, EPB = cells_per_block<N, native64<A>()>();
   LapTab<typename A::V, N> tb;
   for (int d = 0; d < 3; ++d) {
     for (int i = 0; i < NN; ++i) tb.A0[d][i] = A::make(h.A0[d][i]);
