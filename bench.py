@@ -67,8 +67,8 @@ EMU_FP32_FLOPS = {1: (15, 8), 2: (51, 21)}
 # of the same launch configuration (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by (kernel, fp64 mode, k); absent where no
 # capture of the current kernel exists.
-# (kernel, fp64_mode, k) -> DRAM bytes per launch from an ncu capture of the
-# current kernel: profiles/conv_f64_k9_26c_ncu.md, profiles/conv_f64_k11_21c_ncu.md
+# (kernel, fp64_mode, k) -> DRAM bytes (read + write) per launch from one ncu
+# capture of the current kernel: k = 9 on 26^3 cells, k = 11 on 21^3 cells
 KERNEL_TRAFFIC = {("conv_kernel", 0, 9): 551.5e6 + 384.6e6, ("conv_kernel", 0, 11): 483.0e6 + 345.9e6}
 
 
