@@ -80,14 +80,14 @@ constexpr int conv_fwd_cells_per_block() {
 // Region sizes are even, so that with 12-byte (triple-float) values the
 // raw doubles of the face integrals in U1R stay 8-byte aligned.
 constexpr int even_up(int v) { return v + (v & 1); }
-template <int N, int Q, bool CMP = false>
+template <int N, int Q, bool CMP = false, bool SPLIT = (N >= 11)>
 struct ConvLayout {
   static constexpr int N3 = N * N * N;
   static constexpr int U = 3 * N3;               // nodal velocity
   static constexpr int U1 = 3 * Q * N * N;       // x-interpolated
-  // later: the six face integrals, and from N = 11 on the folded products of
-  // the x tests (8 Q^2, see conv_split_xtest)
-  static constexpr int R = 18 * N * N + (N >= 11 ? 8 * Q * Q : 0);
+  // later: the six face integrals, and with the two-phase x tests the folded
+  // products (8 Q^2, see conv_split_xtest)
+  static constexpr int R = 18 * N * N + (SPLIT ? 8 * Q * Q : 0);
   static constexpr int U1R = even_up(U1 > R ? U1 : R);
   static constexpr int U2 = even_up(3 * Q * Q * N);   // xy-interpolated
   static constexpr int P = 3 * Q * Q;            // one z-plane: u
@@ -323,10 +323,14 @@ constexpr bool conv_pair_rows() {
 // u_c u_d of every row folded into sums and differences (item
 // (k, qy, i < (Q+1)/2)), then the even-odd contraction (item (k, qy, output
 // pair)).  Measured: +4-7 % at N = 11, 12; 5-15 % slower at N = 7..10, where
-// other blocks on the SM use the issue slots of the idle warps.
-template <int N>
+// other blocks on the SM use the issue slots of the idle warps.  Natively
+// also at N = 4, with the y tests in even-odd form after a fold pass instead
+// of paired rows: the paired-row items keep 24 of 32 lanes busy, the two
+// phases nearly all (cell + face operator 15.86 -> 14.68 ms at 16.8M DoFs,
+// the same results to the bit).  EM: emulated arithmetic.
+template <int N, bool EM = true>
 constexpr bool conv_split_xtest() {
-  return N >= 11;
+  return N >= 11 || (!EM && N == 4);
 }
 
 // x test of one row of the plane (Q points u_c u_d -> N outputs) in even-odd
@@ -385,7 +389,7 @@ __device__ __forceinline__ void conv_cells(const double* __restrict__ u3, const 
   typedef typename A::V V;
   typedef typename A::Acc Acc;
   constexpr bool CMP = conv_compact<A::emulated, N>();
-  typedef ConvLayout<N, Q, CMP> LY;
+  typedef ConvLayout<N, Q, CMP, conv_split_xtest<N, A::emulated>()> LY;
   static_assert(sizeof(V) % 4 == 0 && sizeof(V) <= 12, "two or three 4-byte words per value");
   constexpr int NT = conv_threads<N, A::emulated>(), CPG = conv_cells_per_group<N>();
   static_assert(!CMP || CPG == 1, "the compact layout holds one cell per group");
@@ -397,7 +401,7 @@ __device__ __forceinline__ void conv_cells(const double* __restrict__ u3, const 
   const long long c0 = ((long long)bid * conv_groups_per_block<N, A::emulated>() + g) * CPG;
   const long long last = m.E - 1;
   constexpr int QH = (Q + 1) / 2, QF = Q / 2, NH = (N + 1) / 2, NF = N / 2;
-  constexpr bool PR = conv_pair_rows<N>();
+  constexpr bool PR = conv_pair_rows<N>() && !conv_split_xtest<N, A::emulated>();
   V* sS = sm + conv_fwd_cells_per_block<N, A::emulated>() * LY::PER;   // tables: S, SW, DW, TY[0..2] (or TYeo), EO[0..1]
   V* sSW = sS + QN;
   V* sDW = sSW + QN;
@@ -409,10 +413,10 @@ __device__ __forceinline__ void conv_cells(const double* __restrict__ u3, const 
   // u(q) = E + O, u(Q-1-q) = E - O with E = ZE(q) . e, O = ZO(q) . o, about
   // half the multiply-adds of interpolating the two planes apart
   constexpr bool PAIR = conv_pair_planes<A::emulated, N, Q>();
-  // with paired planes the x-tested rows of a plane are also folded along y
-  // (sums in row q, differences in row Q-1-q) and the y tests run in even-odd
-  // form (one item per output pair, as with paired rows)
-  constexpr bool EOY = PAIR;
+  // with paired planes (and natively at N = 4) the x-tested rows of a plane
+  // are also folded along y (sums in row q, differences in row Q-1-q) and the
+  // y tests run in even-odd form (one item per output pair, as with paired rows)
+  constexpr bool EOY = PAIR || (!A::emulated && N == 4);
   V* sZE = sEO + 2 * Q * NH;   // [q < QH][z < NH]
   V* sZO = sZE + QH * NH;      // [q < QH][z < NF]
   if constexpr (PAIR) {
@@ -722,7 +726,7 @@ __device__ __forceinline__ void conv_cells(const double* __restrict__ u3, const 
       // rows an item tests the rows p and Q-1-p and stores their sum in row p
       // and their difference in row (Q+1)/2 + p of the test's block (the
       // middle row of odd Q alone, in row p); else one row per item.
-      if constexpr (conv_split_xtest<N>()) {
+      if constexpr (conv_split_xtest<N, A::emulated>()) {
         static_assert(CPG == 1, "one cell per group");
         V* sFE = sRg + 18 * NN;   // behind the face integrals
         V* sFO = sFE + 8 * Q * QH;
@@ -1003,6 +1007,13 @@ __global__ void __launch_bounds__(conv_groups_per_block<N>() * conv_threads<N>()
                     const int nnative) {
   static_assert(conv_threads<N, false>() == conv_threads<N, true>() && !conv_compact<false, N>(),
                 "both arithmetics with the same block geometry");
+  // the shared memory is sized for the triple-float blocks; the native blocks
+  // (with their own layout) must fit in it
+  static_assert((conv_fwd_cells_per_block<N>() * ConvLayout<N, Q, false, conv_split_xtest<N, false>()>::PER +
+                 6 * Q * N + 2 * Q * ((N + 1) / 2)) * sizeof(double) <=
+                    (conv_fwd_cells_per_block<N>() * ConvLayout<N, Q>::PER + 6 * Q * N + 2 * Q * ((N + 1) / 2)) *
+                        sizeof(tf64),
+                "native blocks fit in the triple-float shared memory");
   if ((int)(blockIdx.x % (unsigned)period) < nnative)
     conv_cells<F64, N, Q>(u3, rface, dst3, tbn, m, blockIdx.x);
   else
@@ -1399,7 +1410,9 @@ int launch_conv(int part, const MeshDims& m, const double* u3, double* rface, do
   // planes) ZE, ZO ((Q+1)/2 N) and the z-test tables (4 (Q+1)/2 (N+1)/2)
   constexpr int NH = (N + 1) / 2, QH = (Q + 1) / 2;
   constexpr int TABS = 6 * Q * N + 2 * Q * NH + (conv_pair_planes<A::emulated, N, Q>() ? QH * N + 4 * QH * NH : 0);
-  const size_t smem = ((size_t)EPB * ConvLayout<N, Q, conv_compact<A::emulated, N>()>::PER + TABS) * sizeof(V);
+  const size_t smem =
+      ((size_t)EPB * ConvLayout<N, Q, conv_compact<A::emulated, N>(), conv_split_xtest<N, A::emulated>()>::PER + TABS) *
+      sizeof(V);
   const size_t fsmem = (size_t)GPB * face_group_smem<FL, N, Q>() * sizeof(V);
   if (smem > 232448 || fsmem > 232448) return 7;
   if (cudaFuncSetAttribute(conv_kernel<A, N, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=

@@ -135,7 +135,7 @@ struct EpiArgs {
 // counts fill the warps: on the FP64 pipe a warp instruction costs the same
 // with idle lanes, and N^2 threads leave part of the last warp idle
 // (N = 6: 3 cells in 4 warps, 84 % of the lanes busy; 8 cells in 9 warps,
-// all busy).
+// all busy; N = 12: 1 cell in 5 warps, 90 %; 2 cells in 9 warps, all busy).
 template <int N, bool F64 = false>
 constexpr int cells_per_block() {
   if constexpr (F64) {
@@ -143,6 +143,7 @@ constexpr int cells_per_block() {
     if constexpr (N == 7) return 4;
     if constexpr (N == 9) return 3;
     if constexpr (N == 10) return 2;
+    if constexpr (N == 12) return 2;
   }
   return N * N >= 128 ? 1 : 128 / (N * N);
 }
