@@ -133,6 +133,28 @@ def test_cg_mg_solve(prec, n, kp):
                                      host(x), b) <= 1.5e-10
 
 
+@pytest.mark.parametrize("prec", [32, 64])
+def test_cg_mg_solve_without_mean_projection(prec):
+    """project_mean = 0: the V-cycle output keeps its constant component (the
+    null space of the periodic operator), so the solve still converges to the
+    relative tolerance and its solution differs from the projected one by a
+    constant only (the V-cycle exit then widens and sums (r, z) unshifted)."""
+    n, kp = 8, 3
+    ctx = context(n, kp + 1, kp, mg_precision=prec)
+    s = dg.Space(dg.Mesh(n), kp)
+    b = solvers.mean_free(np.random.default_rng(12).uniform(-1, 1, s.size))
+    xs = []
+    for pm in (1, 0):
+        x = torch.zeros(s.size, dtype=torch.float64, device="cuda")
+        info = ctx.cg_mg_solve(x, dev(b), rel_tol=1e-10, project_mean=pm)
+        assert info["rc"] == 0 and info["rel_res"] <= 1e-10 and info["iterations"] <= 30
+        xs.append(host(x))
+    L = dg.Laplace(s)
+    assert solvers.relative_residual(lambda v: L.apply(v.reshape(s.mesh.E, -1)).ravel(), xs[1], b) <= 1.5e-10
+    d = (xs[1] - xs[1].mean()) - (xs[0] - xs[0].mean())
+    assert np.max(np.abs(d)) <= 1e-6 * np.max(np.abs(xs[0]))
+
+
 def test_cg_not_converged_is_reported():
     ctx = context(4, 3, 2)
     s = dg.Space(dg.Mesh(4), 2)
