@@ -1005,7 +1005,8 @@ __global__ void __launch_bounds__(conv_groups_per_block<N>() * conv_threads<N>()
                     const __grid_constant__ ConvTabT<double, N, Q> tbn,
                     const __grid_constant__ ConvTabT<tf64, N, Q> tbt, const MeshDims m, const int period,
                     const int nnative) {
-  static_assert(conv_threads<N, false>() == conv_threads<N, true>() && !conv_compact<false, N>(),
+  static_assert(conv_threads<N, false>() == conv_threads<N, true>() && !conv_compact<false, N>() &&
+                    conv_groups_per_block<N, false>() == conv_groups_per_block<N, true>(),
                 "both arithmetics with the same block geometry");
   // the shared memory is sized for the triple-float blocks; the native blocks
   // (with their own layout) must fit in it
