@@ -375,7 +375,7 @@ __device__ __forceinline__ void xtest_row(const typename A::V* T1, const typenam
 // i-th of up to two values, selected without an indexed local array
 __device__ __forceinline__ unsigned pick2(int i, unsigned a, unsigned b) { return i == 0 ? a : b; }
 
-// Forward convective cell kernel for an arithmetic policy A (F64 or DF64):
+// Forward convective cell kernel for an arithmetic policy A (F64, DF64 or TF64):
 // loads and stores are double; all arithmetic is A's.  A group of NT threads
 // treats CPG cells at once; every phase is split into small independent work
 // items (one output or one short line of outputs) spread over the group's

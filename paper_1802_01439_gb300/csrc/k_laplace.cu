@@ -223,7 +223,7 @@ __device__ __forceinline__ void sipg_line_eo(const typename A::V* X, typename A:
   }
 }
 
-// One line of T_d x in the direct form (native FP64 and FP32): the cell part,
+// One line of T_d x in the direct form (FP32, and native FP64 below N = 5): the cell part,
 // the coupling through the neighbours' face values (cr r(0) + cl lf(N-1)) and
 // the face-derivative terms (gr . r into y(N-1), gl . lf into y(0)).
 template <class A, int N, int D>
