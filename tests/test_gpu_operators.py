@@ -133,6 +133,22 @@ def test_convective(n, k, field, mode):
 
 
 @pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("n,k", [((3, 2, 2), 3), ((2, 3, 1), 5), ((2, 1, 2), 7), ((2, 2, 1), 9), ((2, 1, 1), 11)])
+def test_convective_k_plus_1_points(n, k, mode):
+    """The convective term with k + 1 Gauss points per direction instead of
+    the 3/2 rule (n_q_conv = k + 1): the kernels' layouts without paired
+    planes, the k = 9 cell kernel in its phase-aliased layout, and in mode 2
+    the native kernels (the FP64-wide arrangements cover the 3/2 rule)."""
+    ctx = context(n, k, k - 1, mg_precision=0, fp64_mode=mode, n_q_conv=k + 1)
+    s = dg.Space(dg.Mesh(n), k)
+    u = tgv_field(s, 1e-3, 1) if k % 2 else random_field(s, 3, 7)
+    ref = dg.Convective(s, nq=k + 1).apply(u)
+    y = torch.empty(u.size, dtype=torch.float64, device="cuda")
+    ctx.vmult_convective(y, dev(u))
+    assert rel_err(host(y), ref) <= TOL
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("n,k", [((3, 2, 2), 3), ((2, 1, 3), 2), ((1, 2, 1), 7), ((3, 1, 3), 3), ((3, 3, 1), 1)])
 def test_convective_two_phases(n, k, mode):
     """Face kernel + cell kernel through the two-phase entry points give the
